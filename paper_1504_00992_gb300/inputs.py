@@ -1,0 +1,150 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests/benchmarks and the
+oracle.
+
+This module holds none of the bond update's arithmetic: it builds the
+caller-side inputs of the method (Hamiltonian bond terms and their Trotter
+gates, initial product states, random Vidal-form tensors and synthetic theta
+matrices with a prescribed singular spectrum).  Random numbers come from
+NumPy's PCG64 generator seeded by the caller.
+
+Conventions
+  * local basis index i = 0..d-1 is the spin projection m = s - i with
+    s = (d - 1) / 2 (index 0 is "up");
+  * a two-site operator is a (d_l d_r) x (d_l d_r) matrix with <ij|O|i'j'> at
+    [i*d_r + j, i'*d_r + j'];
+  * complex arrays are numpy complex128 (interleaved re, im in memory).
+"""
+import numpy as np
+
+
+def spin_ops(d):
+    """(Sx, Sy, Sz) for spin s = (d-1)/2 in the basis m = s, s-1, ..., -s."""
+    s = (d - 1) / 2.0
+    m = s - np.arange(d)
+    sz = np.diag(m).astype(np.complex128)
+    sp = np.zeros((d, d), dtype=np.complex128)   # S+ |m> = sqrt(s(s+1) - m(m+1)) |m+1>
+    for i in range(1, d):
+        mm = m[i]
+        sp[i - 1, i] = np.sqrt(s * (s + 1) - mm * (mm + 1))
+    sm = sp.conj().T
+    sx = 0.5 * (sp + sm)
+    sy = -0.5j * (sp - sm)
+    return sx, sy, sz
+
+
+def pauli():
+    sx = np.array([[0, 1], [1, 0]], dtype=np.complex128)
+    sy = np.array([[0, -1j], [1j, 0]], dtype=np.complex128)
+    sz = np.array([[1, 0], [0, -1]], dtype=np.complex128)
+    return sx, sy, sz
+
+
+def xxz_bond_terms(N, d=2, J=1.0, Delta=0.5):
+    """h_b = J (Sx Sx + Sy Sy + Delta Sz Sz) on bond (b, b+1), b = 0..N-2."""
+    sx, sy, sz = spin_ops(d)
+    h = J * (np.kron(sx, sx) + np.kron(sy, sy) + Delta * np.kron(sz, sz))
+    return [h.copy() for _ in range(N - 1)]
+
+
+def tfim_bond_terms(Js, h=1.0):
+    """Transverse-field Ising, H = -sum_b J_b Z_b Z_{b+1} - h sum_i X_i
+    (Pauli operators).  The field on an inner site is split 1/2 : 1/2 between
+    its two bonds; the end sites carry their full field on their only bond."""
+    sx, _, sz = pauli()
+    N = len(Js) + 1
+    eye = np.eye(2, dtype=np.complex128)
+    out = []
+    for b, Jb in enumerate(Js):
+        wl = 1.0 if b == 0 else 0.5
+        wr = 1.0 if b + 1 == N - 1 else 0.5
+        out.append(-Jb * np.kron(sz, sz) - h * (wl * np.kron(sx, eye) + wr * np.kron(eye, sx)))
+    return out
+
+
+def tfim_bond_terms_dJ(N):
+    """d h_b / d J_b = -Z Z (the same for every bond)."""
+    _, _, sz = pauli()
+    return [-np.kron(sz, sz) for _ in range(N - 1)]
+
+
+def unitary_from_hermitian(h, tau):
+    """exp(-i h tau) through the eigendecomposition of the Hermitian h."""
+    e, V = np.linalg.eigh(h)
+    return (V * np.exp(-1j * tau * e)) @ V.conj().T
+
+
+def trotter_gates(bond_terms, tau):
+    return [unitary_from_hermitian(h, tau) for h in bond_terms]
+
+
+def neel_state(N, d=2):
+    """Site k in m = +s for even k, m = -s for odd k."""
+    out = []
+    for k in range(N):
+        v = np.zeros(d, dtype=np.complex128)
+        v[0 if k % 2 == 0 else d - 1] = 1.0
+        out.append(v)
+    return out
+
+
+def random_unitary(dim, rng):
+    """Haar-random unitary (QR of a complex Gaussian with the phase fix)."""
+    Z = (rng.standard_normal((dim, dim)) + 1j * rng.standard_normal((dim, dim))) / np.sqrt(2.0)
+    Q, R = np.linalg.qr(Z)
+    ph = np.diag(R) / np.abs(np.diag(R))
+    return Q * ph[None, :]
+
+
+def random_bond(dl, dr, chi_l, chi_m, chi_r, rng, decay=4.0):
+    """Random operands of one bond update: Gamma_l (dl, chi_l, chi_m),
+    Gamma_r (dr, chi_m, chi_r), positive descending lambdas normalised to
+    sum(lambda^2) = 1, and a Haar-random two-site gate."""
+    def lam(c):
+        v = np.exp(-np.arange(c) / max(c / decay, 1e-300)) * (1.0 + 0.1 * rng.random(c))
+        v = np.sort(v)[::-1]
+        return v / np.sqrt(np.sum(v ** 2))
+
+    gl = (rng.standard_normal((dl, chi_l, chi_m)) + 1j * rng.standard_normal((dl, chi_l, chi_m)))
+    gr = (rng.standard_normal((dr, chi_m, chi_r)) + 1j * rng.standard_normal((dr, chi_m, chi_r)))
+    return {
+        "gamma_l": gl, "gamma_r": gr,
+        "lam_l": lam(chi_l), "lam_m": lam(chi_m), "lam_r": lam(chi_r),
+        "gate": random_unitary(dl * dr, rng),
+    }
+
+
+def exp_spectrum(n, scale=15.0):
+    """sigma_k = exp(-(k-1)/scale), k = 1..n."""
+    return np.exp(-np.arange(n) / scale)
+
+
+def _reflector_apply_left(X, v):
+    """(I - 2 v v^H / v^H v) X."""
+    return X - np.outer(v, (2.0 / np.vdot(v, v).real) * (v.conj() @ X))
+
+
+def synthetic_theta(m, n, sigma, seed, reflectors=4):
+    """theta = U diag(sigma) V^H with U, V products of `reflectors` Householder
+    reflectors built from complex Gaussian vectors (exactly unitary, O(mn)
+    work each).  len(sigma) <= min(m, n)."""
+    rng = np.random.default_rng(seed)
+    r = len(sigma)
+    X = np.zeros((m, n), dtype=np.complex128)
+    X[np.arange(r), np.arange(r)] = sigma
+    for _ in range(reflectors):
+        v = rng.standard_normal(m) + 1j * rng.standard_normal(m)
+        X = _reflector_apply_left(X, v)
+    Xt = X.conj().T                               # apply V^H from the right via its adjoint
+    for _ in range(reflectors):
+        v = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+        Xt = _reflector_apply_left(Xt, v)
+    return np.ascontiguousarray(Xt.conj().T)
+
+
+def haar_theta(m, n, sigma, seed):
+    """theta = U diag(sigma) V^H with Haar-random U (m x r) and V (n x r)."""
+    rng = np.random.default_rng(seed)
+    r = len(sigma)
+    U = random_unitary(m, rng)[:, :r]
+    V = random_unitary(n, rng)[:, :r]
+    return (U * sigma[None, :]) @ V.conj().T
