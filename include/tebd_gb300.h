@@ -1,0 +1,225 @@
+/*
+ * tebd_gb300.h -- C ABI of the GB300 (sm_103a) TEBD two-site bond update with
+ * reduced-rank randomized SVD (RRSVD).
+ *
+ * Method: Tamascelli, Rosenbach, Plenio, "Improved scaling of Time-Evolving
+ * Block-Decimation algorithm through Reduced-Rank Randomized Singular Value
+ * Decomposition" (arXiv:1504.00992).
+ *
+ * Conventions shared by every call
+ *   - Complex numbers are two doubles (re, im), interleaved, i.e. the memory
+ *     layout of C99 `double _Complex` and numpy complex128.  Every complex
+ *     pointer below is typed `double*` and points at the real part of the
+ *     first element.
+ *   - Matrices are row-major.
+ *   - Local basis of a site: index i = 0..d-1.  A two-site operator (gate)
+ *     of sites (b, b+1) is a (d_b d_{b+1}) x (d_b d_{b+1}) complex matrix
+ *     with <i j|G|i' j'> at row i*d_{b+1} + j, column i'*d_{b+1} + j'.
+ *   - Vidal form (Section II.A, Eq. defmps): Gamma[s] is a complex array
+ *     [d_s][chi_{s-1}][chi_s]; lambda[b] (bond b between sites b and b+1,
+ *     b = 0..N-2) holds chi_b Schmidt values, descending, sum of squares 1.
+ *     The two outer bonds have dimension 1 and lambda = 1.
+ *   - The blocked theta matrix of bond b (Section II.B) has row
+ *     i*chi_{b-1} + alpha and column j*chi_{b+1} + beta.
+ *   - Status: every call returns an int, TEBD_OK (0) on success or one of
+ *     the negative codes below.  Errors are sticky per handle (the first one
+ *     is kept and described by *_last_error) until the handle is destroyed.
+ *     No exception crosses the ABI.  One host thread per handle.
+ *   - Streams: device work is enqueued on the handle's CUDA stream (default
+ *     stream 0 until tebd_set_stream / the stream argument says otherwise).
+ *     Calls with host outputs synchronise that stream before returning.
+ *   - Ownership: the library copies every host input before the call
+ *     returns; the caller keeps its buffers.  Outputs go to caller buffers.
+ *     Device pointers passed to rrsvd_execute stay owned by the caller.
+ *
+ * The sketch matrix Omega (Alg. 1 step 1) is drawn from Philox4x64-10
+ * (Salmon et al., SC'11): element (r, c) of the n x l matrix uses counter
+ * (r*l + c, bond, sweep, chain) and key (seed, 0); the 64-bit words w0, w1
+ * become u = ((w >> 12) + 0.5) 2^-52 and Box-Muller gives
+ * Re = sqrt(-2 ln u1) cos(2 pi u2), Im = sqrt(-2 ln u1) sin(2 pi u2).
+ * `sweep` counts the tebd_step_* calls made on the handle so far; `chain` is
+ * the chain (or instance) index.
+ */
+#ifndef TEBD_GB300_H
+#define TEBD_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  TEBD_OK = 0,
+  TEBD_EINVAL = -1,    /* bad argument (size, index, pointer, call order) */
+  TEBD_ENOMEM = -2,    /* device or host allocation failed */
+  TEBD_ECUDA = -3,     /* a CUDA runtime call or kernel launch failed */
+  TEBD_ENUMERIC = -4,  /* non-finite input, or theta with zero norm */
+  TEBD_ETIMEOUT = -5,  /* a bounded device wait gave up */
+  TEBD_ENOTIMPL = -6,  /* mode not built */
+  TEBD_ESTATE = -7     /* call out of order (e.g. a step before its gates) */
+};
+
+/* Arithmetic of the RRSVD sketch (Alg. 1 GEMMs).  TEBD_PREC_FP64 is the
+ * plain path: every step in FP64. */
+enum { TEBD_PREC_FP64 = 0 };
+
+/* ------------------------------------------------------------------------
+ * TEBD handle: an N-site chain in Vidal form resident on the device.
+ * ---------------------------------------------------------------------- */
+typedef struct tebd_s* tebd_t;
+
+typedef struct {
+  int N;                /* sites, >= 2 */
+  int d;                /* local dimension of every site (used if d_site == NULL), 2..64 */
+  const int* d_site;    /* optional: per-site local dimensions, length N */
+  int chi_max;          /* bond-dimension cap of every bond (used if chi_bond == NULL) */
+  const int* chi_bond;  /* optional: per-bond caps, length N-1 */
+  int p;                /* RRSVD oversampling, >= 0 */
+  int q;                /* RRSVD power iterations, >= 0 */
+  uint64_t seed;        /* Philox key word 0 */
+  int precision;        /* TEBD_PREC_* */
+  double sv_cutoff;     /* keep s_i > sv_cutoff * s_1 among the first k; <= 0 selects 1e-14 */
+  int chain;            /* chain index entering the Philox counter (default 0) */
+} tebd_desc_t;
+
+/* Section II (Eq. defmps, deftheta, defupdatetheta) with the RRSVD of
+ * Section IV.  Creates a handle for an N-site chain with uniform local
+ * dimension d, bond cap chi_max, oversampling p and q power iterations.
+ * The state is |0...0> until set.  Device memory is sized once here from
+ * the caps (the bond dimension of bond b never exceeds
+ * min(chi_max, prod_{s<=b} d_s, prod_{s>b} d_s)).
+ * Errors: TEBD_EINVAL (N < 2, d < 2 or > 64, chi_max < 1, p < 0, q < 0,
+ * out == NULL), TEBD_ENOMEM, TEBD_ECUDA.  On error *out is NULL. */
+int tebd_create(int N, int d, int chi_max, int p, int q, uint64_t seed, tebd_t* out);
+
+/* As tebd_create, with per-site d, per-bond caps, precision and cutoff. */
+int tebd_create_ex(const tebd_desc_t* desc, tebd_t* out);
+
+/* Frees all device and host memory of the handle (NULL is accepted). */
+int tebd_destroy(tebd_t h);
+
+/* Device work of later calls goes to `cuda_stream` (a cudaStream_t). */
+int tebd_set_stream(tebd_t h, void* cuda_stream);
+
+/* Product state: psi is N blocks of d_s complex amplitudes (host), each
+ * normalised by the library.  Resets bond dimensions to 1 and the sweep
+ * counter and discarded-weight accumulators to 0.
+ * Errors: TEBD_EINVAL (NULL), TEBD_ENUMERIC (a zero or non-finite block). */
+int tebd_set_product_state(tebd_t h, const double* psi);
+
+/* Arbitrary Vidal-form state (host arrays, copied): gamma[s] points at a
+ * [d_s][chi[s-1]][chi[s]] complex array (chi[-1] = chi[N-1] = 1 implied),
+ * lambda[b] at chi[b] doubles, chi has N-1 entries each within the bond's cap.
+ * Errors: TEBD_EINVAL. */
+int tebd_set_mps(tebd_t h, const double* const* gamma, const double* const* lambda, const int* chi);
+
+/* Copies the state out (checkpoint): chi[] receives N-1 bond dimensions;
+ * gamma[s] / lambda[b] must have room for the caps' sizes
+ * (d_s * cap_{s-1} * cap_s complex, cap_b doubles); the data are written
+ * densely with the current dimensions.  Any of the three may be NULL. */
+int tebd_get_mps(tebd_t h, double* const* gamma, double* const* lambda, int* chi);
+
+/* Gates of one parity (Eq. defst3rd: even bonds b % 2 == 0 form F, odd form
+ * G).  `gates` holds N-1 complex matrices back to back, gate b of size
+ * (d_b d_{b+1})^2; only bonds with b % 2 == parity are read.  Copied to the
+ * device.  Errors: TEBD_EINVAL (parity not 0/1, NULL), TEBD_ENUMERIC
+ * (non-finite entry). */
+int tebd_set_gates(tebd_t h, int parity, const double* gates);
+
+/* One sweep over all bonds of the parity (Section II.C): for each such bond,
+ * theta = lambda Gamma lambda Gamma lambda, gate, RRSVD truncation to
+ * chi' <= min(cap, m, n) kept values, lambda' = s / ||s||, Gamma rebuilt,
+ * discarded weight accumulated.  All bonds of the parity run in one batched
+ * launch sequence; asynchronous on the handle's stream.
+ * Errors: TEBD_ESTATE (gates of that parity not set), TEBD_ECUDA.  A theta
+ * with zero norm is reported by the next synchronising call as
+ * TEBD_ENUMERIC. */
+int tebd_step_even(tebd_t h);
+int tebd_step_odd(tebd_t h);
+
+/* <O_site> = sum lam_l[a]^2 lam_r[c]^2 conj(Gamma^i[a,c]) O[i,i'] Gamma^i'[a,c]
+ * (Vidal canonical form).  op: d x d complex (host); out: one complex (host,
+ * 2 doubles).  Synchronises.  Errors: TEBD_EINVAL, TEBD_ENUMERIC (a step
+ * met a zero theta). */
+int tebd_expect(tebd_t h, int site, const double* op, double* out);
+
+/* Schmidt values of a bond: out must hold the bond's cap doubles; *chi gets
+ * the current dimension.  Synchronises. */
+int tebd_get_lambda(tebd_t h, int bond, double* out, int* chi);
+
+/* out[0] = sum over all bond updates of w_b (Eq. defdiscweigt),
+ * out[1] = prod (1 - w_b).  Synchronises. */
+int tebd_discarded_weight(tebd_t h, double* out);
+
+/* Number of tebd_step_* calls made (the Philox sweep counter). */
+int tebd_sweep_count(tebd_t h, int64_t* out);
+
+/* Reverse-mode derivative of a time-evolved observable with respect to the
+ * gates.  Not built: returns TEBD_ENOTIMPL. */
+int tebd_backward(tebd_t h, const double* obs_cotangent, double* dgates_even, double* dgates_odd);
+
+/* Text of the first error recorded on the handle ("" if none). */
+const char* tebd_last_error(tebd_t h);
+
+/* ------------------------------------------------------------------------
+ * Standalone RRSVD truncation of caller-given matrices (Section IV: Alg. 1
+ * followed by B = Q^H A, B = U~ S V^H, U = Q U~), batched over instances.
+ * ---------------------------------------------------------------------- */
+typedef struct rrsvd_plan_s* rrsvd_plan_t;
+
+/* Plan for `batch` complex m x n matrices truncated to k = min(k_max, m, n)
+ * singular triplets with sketch width l = min(k + p, m, n) and q power
+ * iterations.  Instance t of a call uses Philox counter chain = chain0 + t,
+ * bond 0, sweep 0.  Errors: TEBD_EINVAL (m, n, batch < 1, k_max < 1, p < 0,
+ * q < 0), TEBD_ENOTIMPL (precision). */
+int rrsvd_plan_create(int m, int n, int k_max, int p, int q, int batch, int precision, uint64_t seed,
+                      rrsvd_plan_t* out);
+int rrsvd_plan_destroy(rrsvd_plan_t plan);
+
+/* Device workspace (bytes) that rrsvd_execute needs, and the plan's k, l. */
+int rrsvd_workspace_size(rrsvd_plan_t plan, size_t* bytes);
+int rrsvd_plan_dims(rrsvd_plan_t plan, int* k, int* l);
+
+/* Truncates theta (device, batch x m x n complex, contiguous) into
+ *   sigma (device, batch x k doubles, descending, zero past the kept rank),
+ *   U     (device, batch x m x k complex; may be NULL),
+ *   Vh    (device, batch x k x n complex; may be NULL),
+ *   w     (device, batch doubles: 1 - sum_{kept} s^2 / ||theta||_F^2; may be NULL),
+ *   rank  (device, batch ints: kept count chi' (s_i > 1e-14 s_1); may be NULL),
+ * using `workspace` (device, >= rrsvd_workspace_size bytes, 256-byte
+ * aligned).  theta is only read.  Asynchronous on `stream`.
+ * Errors: TEBD_EINVAL (NULL theta/sigma/workspace, small workspace, chain0 < 0),
+ * TEBD_ECUDA. */
+int rrsvd_execute(rrsvd_plan_t plan, const double* theta, int64_t chain0, double* sigma, double* U, double* Vh,
+                  double* w, int* rank, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Same truncation from and to HOST buffers (same shapes): copies theta to
+ * the device, runs, and copies the results back, all on `stream`, and
+ * synchronises.  Device staging buffers and workspace are allocated on the
+ * first call and kept by the plan. */
+int rrsvd_execute_host(rrsvd_plan_t plan, const double* theta, int64_t chain0, double* sigma, double* U,
+                       double* Vh, double* w, int* rank, void* stream);
+
+const char* rrsvd_last_error(rrsvd_plan_t plan);
+
+
+/* ------------------------------------------------------------------------
+ * Kernel timing (tracing aid).  When enabled, every kernel launch of the
+ * library is bracketed by CUDA events on its stream, grouped by kernel class
+ * (e.g. "k_zgemm[sketch]", "k_qr", "k_jacobi").  Process-wide; not to be
+ * enabled while a stream is being captured into a CUDA graph.
+ * ---------------------------------------------------------------------- */
+int tebd_profiler_enable(int enable);
+/* Drops all accumulated timings. */
+int tebd_profiler_reset(void);
+/* Waits for the recorded events, then writes up to max_entries classes:
+ * names (64 chars each, NUL-terminated), total milliseconds and launch
+ * counts; *count receives the number of classes (may exceed max_entries). */
+int tebd_profiler_read(int max_entries, char* names, double* total_ms, int64_t* launches, int* count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TEBD_GB300_H */

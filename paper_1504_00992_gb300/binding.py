@@ -1,0 +1,371 @@
+"""Thin ctypes binding of libtebd_gb300.so (include/tebd_gb300.h).
+
+Every function here marshals arguments and calls the C ABI function of the
+same name; all arithmetic of the bond update runs in the library's CUDA
+kernels.  There is no fallback: if the library is missing, or no CUDA device
+is present when a compute call is made, an exception is raised.
+
+Arrays: host complex data are numpy complex128 (interleaved re, im), device
+data are passed as raw integer addresses (e.g. torch.Tensor.data_ptr()).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+TEBD_OK = 0
+TEBD_EINVAL = -1
+TEBD_ENOMEM = -2
+TEBD_ECUDA = -3
+TEBD_ENUMERIC = -4
+TEBD_ETIMEOUT = -5
+TEBD_ENOTIMPL = -6
+TEBD_ESTATE = -7
+TEBD_PREC_FP64 = 0
+
+_CODES = {0: "TEBD_OK", -1: "TEBD_EINVAL", -2: "TEBD_ENOMEM", -3: "TEBD_ECUDA", -4: "TEBD_ENUMERIC",
+          -5: "TEBD_ETIMEOUT", -6: "TEBD_ENOTIMPL", -7: "TEBD_ESTATE"}
+
+
+class TebdError(RuntimeError):
+    def __init__(self, code, msg=""):
+        self.code = code
+        super().__init__(f"{_CODES.get(code, code)}: {msg}")
+
+
+class TebdDesc(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("d", ctypes.c_int), ("d_site", ctypes.POINTER(ctypes.c_int)),
+                ("chi_max", ctypes.c_int), ("chi_bond", ctypes.POINTER(ctypes.c_int)),
+                ("p", ctypes.c_int), ("q", ctypes.c_int), ("seed", ctypes.c_uint64),
+                ("precision", ctypes.c_int), ("sv_cutoff", ctypes.c_double), ("chain", ctypes.c_int)]
+
+
+_LIB = None
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_i64 = ctypes.c_int64
+_u64 = ctypes.c_uint64
+_d = ctypes.c_double
+_pd = ctypes.POINTER(ctypes.c_double)
+_pi = ctypes.POINTER(ctypes.c_int)
+_SIGS = {
+    "tebd_create": (_i, [_i, _i, _i, _i, _i, _u64, ctypes.POINTER(_vp)]),
+    "tebd_create_ex": (_i, [ctypes.POINTER(TebdDesc), ctypes.POINTER(_vp)]),
+    "tebd_destroy": (_i, [_vp]),
+    "tebd_set_stream": (_i, [_vp, _vp]),
+    "tebd_set_product_state": (_i, [_vp, _pd]),
+    "tebd_set_mps": (_i, [_vp, ctypes.POINTER(_pd), ctypes.POINTER(_pd), _pi]),
+    "tebd_get_mps": (_i, [_vp, ctypes.POINTER(_pd), ctypes.POINTER(_pd), _pi]),
+    "tebd_set_gates": (_i, [_vp, _i, _pd]),
+    "tebd_step_even": (_i, [_vp]),
+    "tebd_step_odd": (_i, [_vp]),
+    "tebd_expect": (_i, [_vp, _i, _pd, _pd]),
+    "tebd_get_lambda": (_i, [_vp, _i, _pd, _pi]),
+    "tebd_discarded_weight": (_i, [_vp, _pd]),
+    "tebd_sweep_count": (_i, [_vp, ctypes.POINTER(_i64)]),
+    "tebd_backward": (_i, [_vp, _pd, _pd, _pd]),
+    "tebd_last_error": (ctypes.c_char_p, [_vp]),
+    "rrsvd_plan_create": (_i, [_i, _i, _i, _i, _i, _i, _i, _u64, ctypes.POINTER(_vp)]),
+    "rrsvd_plan_destroy": (_i, [_vp]),
+    "rrsvd_workspace_size": (_i, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
+    "rrsvd_plan_dims": (_i, [_vp, _pi, _pi]),
+    "rrsvd_execute": (_i, [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_size_t, _vp]),
+    "rrsvd_execute_host": (_i, [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "rrsvd_last_error": (ctypes.c_char_p, [_vp]),
+    "tebd_profiler_enable": (_i, [_i]),
+    "tebd_profiler_reset": (_i, []),
+    "tebd_profiler_read": (_i, [_i, ctypes.c_char_p, _pd, ctypes.POINTER(_i64), _pi]),
+}
+
+
+def header_functions():
+    """Names of the functions declared in include/tebd_gb300.h."""
+    import re
+    path = os.path.join(_build.ROOT, "include", "tebd_gb300.h")
+    txt = open(path).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(tebd_\w+|rrsvd_\w+)\s*\(", txt)))
+
+
+def load(path=None):
+    """Load the library (built in-tree by __graft_entry__.build())."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = path or _build.lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build()")
+    L = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _LIB = L
+    return L
+
+
+def _c128(x):
+    return np.ascontiguousarray(np.asarray(x, dtype=np.complex128))
+
+
+def _dp(a):
+    return a.ctypes.data_as(_pd)
+
+
+# ------------------------------------------------------------------ TEBD
+def _check(h, rc):
+    if rc != TEBD_OK:
+        msg = load().tebd_last_error(h) if h else b""
+        raise TebdError(rc, (msg or b"").decode())
+
+
+def tebd_create(N, d, chi_max, p, q, seed):
+    h = _vp()
+    rc = load().tebd_create(N, d, chi_max, p, q, seed, ctypes.byref(h))
+    if rc != TEBD_OK:
+        raise TebdError(rc, "tebd_create")
+    return h
+
+
+def tebd_create_ex(N, d_site, chi_bond, p, q, seed, precision=TEBD_PREC_FP64, sv_cutoff=0.0, chain=0):
+    ds = (ctypes.c_int * N)(*[int(x) for x in d_site])
+    cb = (ctypes.c_int * (N - 1))(*[int(x) for x in chi_bond])
+    desc = TebdDesc(N, int(d_site[0]), ds, int(max(chi_bond)), cb, p, q, seed, precision, sv_cutoff, chain)
+    h = _vp()
+    rc = load().tebd_create_ex(ctypes.byref(desc), ctypes.byref(h))
+    if rc != TEBD_OK:
+        raise TebdError(rc, "tebd_create_ex")
+    return h
+
+
+def tebd_destroy(h):
+    load().tebd_destroy(h)
+
+
+def tebd_set_stream(h, stream_ptr):
+    _check(h, load().tebd_set_stream(h, _vp(int(stream_ptr))))
+
+
+def tebd_set_product_state(h, psis):
+    flat = _c128(np.concatenate([np.ravel(np.asarray(v, dtype=np.complex128)) for v in psis]))
+    _check(h, load().tebd_set_product_state(h, _dp(flat.view(np.float64))))
+
+
+def tebd_set_mps(h, gammas, lambdas):
+    gs = [_c128(g) for g in gammas]
+    ls = [np.ascontiguousarray(np.asarray(l, dtype=np.float64)) for l in lambdas]
+    chi = (ctypes.c_int * len(ls))(*[len(l) for l in ls])
+    gp = (_pd * len(gs))(*[_dp(g.view(np.float64)) for g in gs])
+    lp = (_pd * len(ls))(*[_dp(l) for l in ls])
+    _check(h, load().tebd_set_mps(h, gp, lp, chi))
+
+
+def tebd_get_mps(h, dims, caps):
+    """dims: local dimensions (N); caps: bond capacities (N-1).  Returns
+    (gammas, lambdas) with the current bond dimensions."""
+    N = len(dims)
+    ext = [1] + list(caps) + [1]
+    gbufs = [np.zeros(dims[s] * ext[s] * ext[s + 1], dtype=np.complex128) for s in range(N)]
+    lbufs = [np.zeros(c, dtype=np.float64) for c in caps]
+    chi = (ctypes.c_int * (N - 1))()
+    gp = (_pd * N)(*[_dp(g.view(np.float64)) for g in gbufs])
+    lp = (_pd * (N - 1))(*[_dp(l) for l in lbufs])
+    _check(h, load().tebd_get_mps(h, gp, lp, chi))
+    ce = [1] + list(chi) + [1]
+    gammas = [gbufs[s][: dims[s] * ce[s] * ce[s + 1]].reshape(dims[s], ce[s], ce[s + 1]) for s in range(N)]
+    lambdas = [lbufs[b][: ce[b + 1]] for b in range(N - 1)]
+    return gammas, lambdas
+
+
+def tebd_set_gates(h, parity, gates):
+    flat = _c128(np.concatenate([np.ravel(_c128(g)) for g in gates]))
+    _check(h, load().tebd_set_gates(h, parity, _dp(flat.view(np.float64))))
+
+
+def tebd_step_even(h):
+    _check(h, load().tebd_step_even(h))
+
+
+def tebd_step_odd(h):
+    _check(h, load().tebd_step_odd(h))
+
+
+def tebd_expect(h, site, op):
+    o = _c128(op)
+    out = np.zeros(2, dtype=np.float64)
+    _check(h, load().tebd_expect(h, site, _dp(o.view(np.float64)), _dp(out)))
+    return complex(out[0], out[1])
+
+
+def tebd_get_lambda(h, bond, cap):
+    out = np.zeros(cap, dtype=np.float64)
+    chi = ctypes.c_int()
+    _check(h, load().tebd_get_lambda(h, bond, _dp(out), ctypes.byref(chi)))
+    return out[: chi.value].copy()
+
+
+def tebd_discarded_weight(h):
+    out = np.zeros(2, dtype=np.float64)
+    _check(h, load().tebd_discarded_weight(h, _dp(out)))
+    return float(out[0]), float(out[1])
+
+
+def tebd_sweep_count(h):
+    c = ctypes.c_int64()
+    _check(h, load().tebd_sweep_count(h, ctypes.byref(c)))
+    return c.value
+
+
+def tebd_backward(h, obs_cotangent=None, dgates_even=None, dgates_odd=None):
+    rc = load().tebd_backward(h, None, None, None)
+    _check(h, rc)
+
+
+def tebd_last_error(h):
+    return (load().tebd_last_error(h) or b"").decode()
+
+
+# ------------------------------------------------------------------ RRSVD
+def _pcheck(plan, rc):
+    if rc != TEBD_OK:
+        msg = load().rrsvd_last_error(plan) if plan else b""
+        raise TebdError(rc, (msg or b"").decode())
+
+
+def rrsvd_plan_create(m, n, k_max, p, q, batch, precision=TEBD_PREC_FP64, seed=0):
+    h = _vp()
+    rc = load().rrsvd_plan_create(m, n, k_max, p, q, batch, precision, seed, ctypes.byref(h))
+    if rc != TEBD_OK:
+        raise TebdError(rc, "rrsvd_plan_create")
+    return h
+
+
+def rrsvd_plan_destroy(plan):
+    load().rrsvd_plan_destroy(plan)
+
+
+def rrsvd_workspace_size(plan):
+    s = ctypes.c_size_t()
+    _pcheck(plan, load().rrsvd_workspace_size(plan, ctypes.byref(s)))
+    return s.value
+
+
+def rrsvd_plan_dims(plan):
+    k, l = ctypes.c_int(), ctypes.c_int()
+    _pcheck(plan, load().rrsvd_plan_dims(plan, ctypes.byref(k), ctypes.byref(l)))
+    return k.value, l.value
+
+
+def rrsvd_execute(plan, theta_ptr, chain0, sigma_ptr, U_ptr, Vh_ptr, w_ptr, rank_ptr, ws_ptr, ws_bytes, stream_ptr=0):
+    """Device-pointer call (integers, 0 for NULL)."""
+    def vp(x):
+        return _vp(int(x)) if x else None
+    _pcheck(plan, load().rrsvd_execute(plan, vp(theta_ptr), chain0, vp(sigma_ptr), vp(U_ptr), vp(Vh_ptr), vp(w_ptr),
+                                       vp(rank_ptr), vp(ws_ptr), ws_bytes, vp(stream_ptr)))
+
+
+def rrsvd_execute_host(plan, theta, chain0, sigma, U=None, Vh=None, w=None, rank=None, stream_ptr=0):
+    """Host-buffer call: theta (batch, m, n) complex128 in, results written
+    into the given numpy arrays (contiguous; pinned memory recommended)."""
+    def hp(a):
+        return _vp(a.ctypes.data) if a is not None else None
+    _pcheck(plan, load().rrsvd_execute_host(plan, hp(theta), chain0, hp(sigma), hp(U), hp(Vh), hp(w), hp(rank),
+                                            _vp(int(stream_ptr)) if stream_ptr else None))
+
+
+def rrsvd_last_error(plan):
+    return (load().rrsvd_last_error(plan) or b"").decode()
+
+
+# ------------------------------------------------------------------ kernel timing
+def tebd_profiler_enable(on=True):
+    load().tebd_profiler_enable(1 if on else 0)
+
+
+def tebd_profiler_reset():
+    load().tebd_profiler_reset()
+
+
+def tebd_profiler_read():
+    """{kernel class: (total ms, launches)} accumulated since the last reset."""
+    L = load()
+    cnt = ctypes.c_int()
+    L.tebd_profiler_read(0, None, None, None, ctypes.byref(cnt))
+    n = cnt.value
+    if n == 0:
+        return {}
+    names = ctypes.create_string_buffer(64 * n)
+    ms = np.zeros(n, dtype=np.float64)
+    nl = np.zeros(n, dtype=np.int64)
+    L.tebd_profiler_read(n, names, _dp(ms), nl.ctypes.data_as(ctypes.POINTER(_i64)), ctypes.byref(cnt))
+    out = {}
+    for i in range(n):
+        nm = names.raw[64 * i: 64 * (i + 1)].split(b"\0", 1)[0].decode()
+        out[nm] = (float(ms[i]), int(nl[i]))
+    return out
+
+
+# ------------------------------------------------------------------ convenience wrappers
+class Tebd:
+    """Owning wrapper of a tebd_t handle (the calls above, bound to one chain)."""
+
+    def __init__(self, N, d, chi_max, p, q, seed=0, d_site=None, chi_bond=None, sv_cutoff=0.0, chain=0,
+                 stream=None):
+        self.N = N
+        self.dims = list(d_site) if d_site is not None else [d] * N
+        self.chi_bond = list(chi_bond) if chi_bond is not None else [chi_max] * (N - 1)
+        if d_site is None and chi_bond is None and sv_cutoff == 0.0 and chain == 0:
+            self.h = tebd_create(N, d, chi_max, p, q, seed)
+        else:
+            self.h = tebd_create_ex(N, self.dims, self.chi_bond, p, q, seed, TEBD_PREC_FP64, sv_cutoff, chain)
+        caps = []
+        for b in range(N - 1):
+            left = int(np.prod([float(x) for x in self.dims[: b + 1]]))
+            right = int(np.prod([float(x) for x in self.dims[b + 1:]]))
+            caps.append(int(min(self.chi_bond[b], left, right)))
+        self.caps = caps
+        if stream is not None:
+            tebd_set_stream(self.h, stream)
+
+    def close(self):
+        if self.h:
+            tebd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_product_state(self, psis):
+        tebd_set_product_state(self.h, psis)
+
+    def set_mps(self, gammas, lambdas):
+        tebd_set_mps(self.h, gammas, lambdas)
+
+    def get_mps(self):
+        return tebd_get_mps(self.h, self.dims, self.caps)
+
+    def set_gates(self, parity, gates):
+        tebd_set_gates(self.h, parity, gates)
+
+    def step_even(self):
+        tebd_step_even(self.h)
+
+    def step_odd(self):
+        tebd_step_odd(self.h)
+
+    def expect(self, site, op):
+        return tebd_expect(self.h, site, op)
+
+    def get_lambda(self, bond):
+        return tebd_get_lambda(self.h, bond, self.caps[bond])
+
+    def discarded_weight(self):
+        return tebd_discarded_weight(self.h)
+
+    def sweeps(self):
+        return tebd_sweep_count(self.h)

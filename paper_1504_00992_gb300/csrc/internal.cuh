@@ -1,0 +1,102 @@
+// Internal descriptors and launch entry points of the bond-update pipeline.
+//
+// One "problem" is one bond update (TEBD) or one given matrix (standalone
+// RRSVD).  Its sizes live on the device (Dims) because bond dimensions change
+// from sweep to sweep without the host reading them back; its buffers
+// (ProbPtr) are carved once from a workspace sized by the capacities.
+// Every matrix is row-major and compact: its leading dimension is its actual
+// column count.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace tg {
+
+struct Dims {
+  int m, n;        // theta rows (d_l chi_l) and columns (d_r chi_r)
+  int k, l;        // target rank min(chi_cap, m, n) and sketch width min(k + p, m, n)
+  int dl, dr;      // local dimensions of the two sites
+  int cl, cm, cr;  // bond dimensions left of, between and right of the two sites
+  int bond;        // bond index (Philox counter word 1)
+  int active;      // 0: skip this problem
+  int pad;
+};
+
+struct ProbPtr {
+  // operands of the theta contraction (TEBD only)
+  const cplx* gl;     // Gamma[b]   [dl][cap_l][cap_m]
+  const cplx* gr;     // Gamma[b+1] [dr][cap_m][cap_r]
+  const double* laml; // lambda left  (cap_l)
+  const double* lamm; // lambda middle (cap_m)
+  const double* lamr; // lambda right (cap_r)
+  const cplx* gate;   // (dl dr)^2
+  int cap_l, cap_m, cap_r, pad0;
+  // RRSVD buffers
+  const cplx* theta;  // m x n (read only for the sketches)
+  cplx* omega;        // n x l
+  cplx* Y;            // m x l   (QR input, overwritten by reflectors)
+  cplx* Q;            // m x l
+  cplx* Yt;           // n x l   (QR input, overwritten by reflectors)
+  cplx* Qt;           // n x l
+  cplx* R;            // l x l   (R factor of B^H, then Jacobi working matrix)
+  cplx* J;            // l x l   (accumulated Jacobi rotations)
+  cplx* Jk;           // l x k   (sorted leading columns of J)
+  cplx* Wk;           // l x k   (sorted leading normalised columns of R J)
+  cplx* U;            // m x k   (Q Jk)
+  cplx* V;            // n x k   (Qt Wk)
+  double* sigma;      // l       (sorted descending)
+  double* part;       // NPART partial sums of |theta|^2
+  double* scal;       // per-problem scalars: [0] ||theta||_F^2, [1] w, [2] kept rank
+};
+
+enum { NPART = 64 };
+
+// GEMM stages of the pipeline (op(A) op(B) -> C).
+enum GemmStage { G_Y0 = 0, G_YT = 1, G_Y = 2, G_BH = 3, G_U = 4, G_V = 5 };
+// QR stages: which buffer is factored and where Q goes.
+enum QrStage { QR_Y = 0, QR_YT = 1, QR_BH = 2 };
+
+// Capacities (maxima over the batch) used to size grids.
+struct Caps {
+  int m, n, k, l;
+  int cl, cr, dl, dr;
+};
+
+// --- launchers (kernels.cu) ---------------------------------------------
+cudaError_t launch_omega(const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, uint64_t seed,
+                         uint64_t sweep, int64_t chain0, int chain_stride, cudaStream_t st);
+cudaError_t launch_zgemm(int stage, const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap,
+                         cudaStream_t st);
+cudaError_t launch_qr(int stage, const Dims* dims, const ProbPtr* ptrs, int batch, cudaStream_t st);
+cudaError_t launch_jacobi(const Dims* dims, const ProbPtr* ptrs, int batch, int* status, cudaStream_t st);
+cudaError_t launch_frob2(const Dims* dims, const ProbPtr* ptrs, int batch, cudaStream_t st);
+cudaError_t launch_theta(const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, cudaStream_t st);
+
+// standalone RRSVD epilogue: sigma/U/Vh/w/rank into caller buffers
+cudaError_t launch_rrsvd_finalize(const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, double cutoff,
+                                  double* sigma, double* Vh, double* w, int* rank, int* status, cudaStream_t st);
+
+// the whole RRSVD from theta to (sigma, Jk, Wk, U, V): Alg. 1 + steps i-iii
+cudaError_t run_rrsvd(const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, int q, uint64_t seed,
+                      uint64_t sweep, int64_t chain0, int chain_stride, int* status, cudaStream_t st);
+
+// --- TEBD-specific (tebd_kernels.cu) -------------------------------------
+struct ChainDev {
+  int N;
+  int* chi_ext;          // N+1 bond dims, chi_ext[0] = chi_ext[N] = 1, chi_ext[b+1] = chi of bond b
+  const int* chi_cap;    // N-1 user caps (k <= chi_cap[b])
+  const int* dsite;      // N local dims
+  double** lam_ext;      // N+1 pointers, outer ones point at a constant 1.0
+  cplx** gamma;          // N pointers
+  const int* cap_ext;    // N+1 capacities of the bonds (outer = 1)
+};
+
+cudaError_t launch_plan(const ChainDev& ch, int parity, int p, Dims* dims, ProbPtr* ptrs, int batch,
+                        cudaStream_t st);
+cudaError_t launch_rebuild(const ChainDev& ch, const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap,
+                           double cutoff, double* wacc, int* status, cudaStream_t st);
+cudaError_t launch_expect(const ChainDev& ch, int site, const cplx* op, int d, cplx* out, cudaStream_t st);
+
+}  // namespace tg

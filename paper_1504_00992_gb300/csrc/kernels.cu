@@ -1,0 +1,525 @@
+// RRSVD kernels, plain FP64 (sm_103a).
+//
+// Section IV of the paper: Alg. 1 (Gaussian sketch Y0 = A Omega, QR, and q
+// power iterations A^H Q -> QR -> A Q~ -> QR) followed by B = Q^H A, the SVD
+// of the small B and U = Q U~.  B is formed as its adjoint B^H = A^H Q
+// (n x l); the SVD of B comes from the QR factorisation B^H = Qb Rb followed
+// by a one-sided Jacobi SVD of Rb (Rb J = W S): then U~ = J and V = Qb W.
+//
+// On GB300 FP64 runs at about 1 TFLOP/s for the whole chip (2 FMA per clock
+// per SM), so every FP64 kernel here is bound by the FP64 pipe; the designs
+// spread independent work over as many SMs as possible rather than chase
+// memory reuse.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "internal.cuh"
+#include "profiler.cuh"
+
+namespace tg {
+
+// ---------------------------------------------------------------------------
+// Omega: n x l complex Gaussian, column-major; element (r, c) uses Philox
+// counter (r*l + c, bond, sweep, chain).
+// ---------------------------------------------------------------------------
+__global__ void k_omega(const Dims* __restrict__ dims, const ProbPtr* __restrict__ ptrs, uint64_t seed,
+                        uint64_t sweep, int64_t chain0, int chain_stride) {
+  const int p = blockIdx.y;
+  const Dims D = dims[p];
+  if (!D.active) return;
+  cplx* om = ptrs[p].omega;
+  const int64_t total = (int64_t)D.n * D.l;
+  const uint64_t chain = (uint64_t)(chain0 + (int64_t)p * chain_stride);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / D.l), c = (int)(e % D.l);
+    om[(int64_t)c * D.n + r] = gauss_c((uint64_t)e, (uint64_t)D.bond, sweep, chain, seed, 0);
+  }
+}
+
+cudaError_t launch_omega(const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, uint64_t seed,
+                         uint64_t sweep, int64_t chain0, int chain_stride, cudaStream_t st) {
+  const int64_t total = (int64_t)cap.n * cap.l;
+  int bx = (int)((total + 255) / 256);
+  if (bx > 64) bx = 64;
+  if (bx < 1) bx = 1;
+  ProfScope ps("k_omega", st);
+  k_omega<<<dim3(bx, batch), 256, 0, st>>>(dims, ptrs, seed, sweep, chain0, chain_stride);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Batched complex GEMM C = op(A) op(B), FP64.
+// Operands are addressed by (row stride, column stride) so the same kernel
+// serves row- and column-major buffers; loads map consecutive threads onto the
+// unit-stride direction.
+// ---------------------------------------------------------------------------
+struct GemmOp {
+  int M, N, K;
+  const cplx* A; int64_t ars, acs;
+  const cplx* B; int64_t brs, bcs;
+  cplx* C; int64_t crs, ccs;
+};
+
+template <int STAGE>
+__device__ __forceinline__ GemmOp gemm_of(const Dims& D, const ProbPtr& P) {
+  GemmOp g;
+  if (STAGE == G_Y0 || STAGE == G_Y) {  // Y = A Omega  /  Y = A Q~   (m x l, column-major)
+    g.M = D.m; g.N = D.l; g.K = D.n;
+    g.A = P.theta; g.ars = D.n; g.acs = 1;
+    g.B = (STAGE == G_Y0) ? P.omega : P.Qt; g.brs = 1; g.bcs = D.n;
+    g.C = P.Y; g.crs = 1; g.ccs = D.m;
+  } else if (STAGE == G_YT || STAGE == G_BH) {  // Y~ = A^H Q (n x l, column-major)
+    g.M = D.n; g.N = D.l; g.K = D.m;
+    g.A = P.theta; g.ars = 1; g.acs = D.n;       // op(A)(r, k) = conj(A[k][r])
+    g.B = P.Q; g.brs = 1; g.bcs = D.m;
+    g.C = P.Yt; g.crs = 1; g.ccs = D.n;
+  } else if (STAGE == G_U) {  // U = Q Jk (m x k, row-major)
+    g.M = D.m; g.N = D.k; g.K = D.l;
+    g.A = P.Q; g.ars = 1; g.acs = D.m;
+    g.B = P.Jk; g.brs = 1; g.bcs = D.l;
+    g.C = P.U; g.crs = D.k; g.ccs = 1;
+  } else {  // G_V: V = Qb Wk, stored conjugated as Vh (k x n, row-major)
+    g.M = D.n; g.N = D.k; g.K = D.l;
+    g.A = P.Qt; g.ars = 1; g.acs = D.n;
+    g.B = P.Wk; g.brs = 1; g.bcs = D.l;
+    g.C = P.V; g.crs = 1; g.ccs = D.n;
+  }
+  return g;
+}
+
+template <int STAGE>
+struct StageFlags {
+  static constexpr bool conjA = (STAGE == G_YT || STAGE == G_BH);
+  static constexpr bool conjC = (STAGE == G_V);
+};
+
+template <int T, int STAGE>
+__global__ void __launch_bounds__(256) k_zgemm(const Dims* __restrict__ dims, const ProbPtr* __restrict__ ptrs) {
+  constexpr int TK = 16;
+  constexpr int S = T / 16;  // outputs per thread along each direction
+  __shared__ cplx As[TK][T + 1];
+  __shared__ cplx Bs[TK][T + 1];
+  const int p = blockIdx.z;
+  const Dims D = dims[p];
+  if (!D.active) return;
+  const GemmOp g = gemm_of<STAGE>(D, ptrs[p]);
+  const int tm = blockIdx.y * T, tn = blockIdx.x * T;
+  if (tm >= g.M || tn >= g.N) return;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const bool ccol = (g.crs == 1);
+  cplx acc[S][S];
+#pragma unroll
+  for (int i = 0; i < S; ++i)
+#pragma unroll
+    for (int j = 0; j < S; ++j) acc[i][j] = cmk(0.0, 0.0);
+
+  for (int k0 = 0; k0 < g.K; k0 += TK) {
+    // A tile: op(A)(tm + r, k0 + kk) -> As[kk][r]
+    for (int e = tid; e < T * TK; e += 256) {
+      int r, kk;
+      if (g.acs == 1) { kk = e % TK; r = e / TK; } else { r = e % T; kk = e / T; }
+      const int gr = tm + r, gk = k0 + kk;
+      cplx v = cmk(0.0, 0.0);
+      if (gr < g.M && gk < g.K) {
+        v = g.A[(int64_t)gr * g.ars + (int64_t)gk * g.acs];
+        if (StageFlags<STAGE>::conjA) v.y = -v.y;
+      }
+      As[kk][r] = v;
+    }
+    // B tile: B(k0 + kk, tn + c) -> Bs[kk][c]
+    for (int e = tid; e < T * TK; e += 256) {
+      int c, kk;
+      if (g.brs == 1) { kk = e % TK; c = e / TK; } else { c = e % T; kk = e / T; }
+      const int gc = tn + c, gk = k0 + kk;
+      cplx v = cmk(0.0, 0.0);
+      if (gc < g.N && gk < g.K) v = g.B[(int64_t)gk * g.brs + (int64_t)gc * g.bcs];
+      Bs[kk][c] = v;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < TK; ++kk) {
+      cplx a[S], b[S];
+#pragma unroll
+      for (int i = 0; i < S; ++i) a[i] = As[kk][(ccol ? tx : ty) + 16 * i];
+#pragma unroll
+      for (int j = 0; j < S; ++j) b[j] = Bs[kk][(ccol ? ty : tx) + 16 * j];
+#pragma unroll
+      for (int i = 0; i < S; ++i)
+#pragma unroll
+        for (int j = 0; j < S; ++j) cfma(acc[i][j], a[i], b[j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < S; ++i)
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      const int r = tm + (ccol ? tx : ty) + 16 * i, c = tn + (ccol ? ty : tx) + 16 * j;
+      if (r < g.M && c < g.N) {
+        cplx v = acc[i][j];
+        if (StageFlags<STAGE>::conjC) v.y = -v.y;
+        g.C[(int64_t)r * g.crs + (int64_t)c * g.ccs] = v;
+      }
+    }
+}
+
+template <int STAGE>
+static cudaError_t launch_zgemm_stage(int rows, int cols, const Dims* dims, const ProbPtr* ptrs, int batch,
+                                     cudaStream_t st) {
+  // Prefer 32x32 tiles when they already give two CTAs per SM; otherwise
+  // 16x16 tiles spread small problems over more SMs.
+  const int t32 = ((rows + 31) / 32) * ((cols + 31) / 32) * batch;
+  if (t32 >= 2 * 152) {
+    dim3 grid((cols + 31) / 32, (rows + 31) / 32, batch);
+    k_zgemm<32, STAGE><<<grid, 256, 0, st>>>(dims, ptrs);
+  } else {
+    dim3 grid((cols + 15) / 16, (rows + 15) / 16, batch);
+    k_zgemm<16, STAGE><<<grid, 256, 0, st>>>(dims, ptrs);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zgemm(int stage, const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap,
+                         cudaStream_t st) {
+  ProfScope ps((stage == G_U || stage == G_V) ? "k_zgemm[uv]" : "k_zgemm[sketch]", st);
+  switch (stage) {
+    case G_Y0: return launch_zgemm_stage<G_Y0>(cap.m, cap.l, dims, ptrs, batch, st);
+    case G_YT: return launch_zgemm_stage<G_YT>(cap.n, cap.l, dims, ptrs, batch, st);
+    case G_Y: return launch_zgemm_stage<G_Y>(cap.m, cap.l, dims, ptrs, batch, st);
+    case G_BH: return launch_zgemm_stage<G_BH>(cap.n, cap.l, dims, ptrs, batch, st);
+    case G_U: return launch_zgemm_stage<G_U>(cap.m, cap.k, dims, ptrs, batch, st);
+    case G_V: return launch_zgemm_stage<G_V>(cap.n, cap.k, dims, ptrs, batch, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------
+// Householder QR with explicit Q (Golub & Van Loan 5.2.1 and 5.1.6).
+// One CTA per problem; the M x L input is column-major and is overwritten by
+// the reflectors v_j (v_j stored in column j from row j down; R above the
+// diagonal, R_jj kept aside).  H_j = I - tau_j v_j v_j^H with
+// alpha_j = -e^{i arg x_0} ||x||, v_0 = x_0 - alpha_j, tau_j = 1/(||x|| (||x|| + |x_0|)).
+// Q = H_0 ... H_{L-1} [I; 0] is accumulated backwards into the output.
+// ---------------------------------------------------------------------------
+enum { QR_MAXL = 512 };
+
+template <int QS>
+__global__ void __launch_bounds__(256) k_qr(const Dims* __restrict__ dims, const ProbPtr* __restrict__ ptrs) {
+  __shared__ double red[32];
+  __shared__ double tau[QR_MAXL];
+  __shared__ cplx alph[QR_MAXL];
+  const int p = blockIdx.x;
+  const Dims D = dims[p];
+  if (!D.active) return;
+  const ProbPtr P = ptrs[p];
+  const int M = (QS == QR_Y) ? D.m : D.n;
+  const int L = D.l;
+  cplx* A = (QS == QR_Y) ? P.Y : P.Yt;
+  cplx* Qo = (QS == QR_Y) ? P.Q : P.Qt;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+
+  for (int j = 0; j < L; ++j) {
+    cplx* aj = A + (int64_t)j * M;
+    double s = 0.0;
+    for (int r = j + tid; r < M; r += blockDim.x) s += cabs2(aj[r]);
+    s = block_sum(s, red);
+    if (tid == 0) {
+      const cplx x0 = aj[j];
+      const double ax0 = sqrt(cabs2(x0)), nx = sqrt(s);
+      if (nx == 0.0) {
+        tau[j] = 0.0;
+        alph[j] = cmk(0.0, 0.0);
+      } else {
+        const cplx ph = (ax0 > 0.0) ? cscale(x0, 1.0 / ax0) : cmk(1.0, 0.0);
+        alph[j] = cscale(ph, -nx);
+        aj[j] = cscale(ph, ax0 + nx);  // v_0 = x_0 - alpha
+        tau[j] = 1.0 / (nx * (nx + ax0));
+      }
+    }
+    __syncthreads();
+    const double t = tau[j];
+    if (t != 0.0) {
+      for (int c = j + 1 + warp; c < L; c += nw) {
+        cplx* ac = A + (int64_t)c * M;
+        cplx sd = cmk(0.0, 0.0);
+        for (int r = j + lane; r < M; r += 32) cfma_conj(sd, aj[r], ac[r]);
+        sd = cscale(warp_sum(sd), t);
+        for (int r = j + lane; r < M; r += 32) {
+          const cplx v = aj[r];
+          ac[r] = csub(ac[r], cmul(v, sd));
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // R (upper triangle, column-major L x L) for the factorisation of B^H
+  if (QS == QR_BH) {
+    for (int e = tid; e < L * L; e += blockDim.x) {
+      const int c = e / L, i = e % L;
+      cplx v = cmk(0.0, 0.0);
+      if (i < c) v = A[(int64_t)c * M + i];
+      else if (i == c) v = alph[c];
+      P.R[(int64_t)c * L + i] = v;
+    }
+  }
+  // Q = [I; 0], then Q <- H_j Q for j = L-1 .. 0 (only columns c >= j change)
+  for (int64_t e = tid; e < (int64_t)M * L; e += blockDim.x) {
+    const int c = (int)(e / M), r = (int)(e % M);
+    Qo[e] = cmk(r == c ? 1.0 : 0.0, 0.0);
+  }
+  __syncthreads();
+  for (int j = L - 1; j >= 0; --j) {
+    const double t = tau[j];
+    if (t == 0.0) continue;  // uniform across the block
+    const cplx* aj = A + (int64_t)j * M;
+    for (int c = j + warp; c < L; c += nw) {
+      cplx* qc = Qo + (int64_t)c * M;
+      cplx sd = cmk(0.0, 0.0);
+      for (int r = j + lane; r < M; r += 32) cfma_conj(sd, aj[r], qc[r]);
+      sd = cscale(warp_sum(sd), t);
+      for (int r = j + lane; r < M; r += 32) qc[r] = csub(qc[r], cmul(aj[r], sd));
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_qr(int stage, const Dims* dims, const ProbPtr* ptrs, int batch, cudaStream_t st) {
+  ProfScope ps("k_qr", st);
+  switch (stage) {
+    case QR_Y: k_qr<QR_Y><<<batch, 256, 0, st>>>(dims, ptrs); break;
+    case QR_YT: k_qr<QR_YT><<<batch, 256, 0, st>>>(dims, ptrs); break;
+    case QR_BH: k_qr<QR_BH><<<batch, 256, 0, st>>>(dims, ptrs); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// One-sided (Hestenes) Jacobi SVD of the L x L factor Rb, column-major, in
+// place: columns a, b are rotated by the 2x2 unitary that diagonalises their
+// Gram matrix [[|x_a|^2, g], [g*, |x_b|^2]], g = x_a^H x_b, until every pair
+// is orthogonal to tol = 4 eps sqrt(L).  Pairs follow the round-robin
+// (circle) ordering, L/2 disjoint pairs per round, one warp per pair.
+// Output: sigma sorted descending (ties by lower index), Jk = leading k
+// columns of J in that order, Wk = matching columns of Rb J divided by sigma.
+// ---------------------------------------------------------------------------
+enum { JAC_MAXSWEEPS = 60 };
+
+__global__ void __launch_bounds__(256) k_jacobi(const Dims* __restrict__ dims, const ProbPtr* __restrict__ ptrs,
+                                                int* status) {
+  __shared__ double sv[QR_MAXL];
+  __shared__ int perm[QR_MAXL];
+  __shared__ int rotated;
+  const int p = blockIdx.x;
+  const Dims D = dims[p];
+  if (!D.active) return;
+  const ProbPtr P = ptrs[p];
+  const int L = D.l, K = D.k;
+  cplx* X = P.R;
+  cplx* J = P.J;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  for (int e = tid; e < L * L; e += blockDim.x) J[e] = cmk((e / L) == (e % L) ? 1.0 : 0.0, 0.0);
+  const int Lp = (L + 1) & ~1;
+  const double tol = 4.0 * 2.220446049250313e-16 * sqrt((double)L);
+  int sweep = 0;
+  for (; sweep < JAC_MAXSWEEPS; ++sweep) {
+    if (tid == 0) rotated = 0;
+    __syncthreads();
+    for (int rnd = 0; rnd < Lp - 1; ++rnd) {
+      for (int pi = warp; pi < Lp / 2; pi += nw) {
+        int a, b;
+        if (pi == 0) { a = Lp - 1; b = rnd; }
+        else { a = (rnd + pi) % (Lp - 1); b = (rnd - pi + (Lp - 1)) % (Lp - 1); }
+        if (a > b) { const int t = a; a = b; b = t; }
+        if (b >= L) continue;
+        cplx* xa = X + (int64_t)a * L;
+        cplx* xb = X + (int64_t)b * L;
+        double aa = 0.0, bb = 0.0;
+        cplx g = cmk(0.0, 0.0);
+        for (int r = lane; r < L; r += 32) {
+          const cplx u = xa[r], v = xb[r];
+          aa += cabs2(u);
+          bb += cabs2(v);
+          cfma_conj(g, u, v);
+        }
+        aa = warp_sum(aa);
+        bb = warp_sum(bb);
+        g = warp_sum(g);
+        const double ag = sqrt(cabs2(g));
+        if (!(ag > tol * sqrt(aa * bb)) || ag == 0.0) continue;
+        // rotation: x_a' = c x_a - s e* x_b, x_b' = s e x_a + c x_b, e = g/|g|
+        const cplx e = cscale(g, 1.0 / ag);
+        const double zeta = (bb - aa) / (2.0 * ag);
+        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+        const cplx se = cscale(e, s), sec = cconj(se);
+        for (int r = lane; r < L; r += 32) {
+          const cplx u = xa[r], v = xb[r];
+          xa[r] = csub(cscale(u, c), cmul(sec, v));
+          xb[r] = cadd(cmul(se, u), cscale(v, c));
+        }
+        cplx* ja = J + (int64_t)a * L;
+        cplx* jb = J + (int64_t)b * L;
+        for (int r = lane; r < L; r += 32) {
+          const cplx u = ja[r], v = jb[r];
+          ja[r] = csub(cscale(u, c), cmul(sec, v));
+          jb[r] = cadd(cmul(se, u), cscale(v, c));
+        }
+        if (lane == 0) rotated = 1;
+      }
+      __syncthreads();
+    }
+    const int any = rotated;
+    __syncthreads();
+    if (!any) break;
+  }
+  if (sweep == JAC_MAXSWEEPS && tid == 0) atomicOr(status, 2);  // not converged (non-fatal)
+  // singular values = column norms
+  for (int c = warp; c < L; c += nw) {
+    const cplx* xc = X + (int64_t)c * L;
+    double s = 0.0;
+    for (int r = lane; r < L; r += 32) s += cabs2(xc[r]);
+    s = warp_sum(s);
+    if (lane == 0) sv[c] = sqrt(s);
+  }
+  __syncthreads();
+  for (int c = tid; c < L; c += blockDim.x) {
+    const double s = sv[c];
+    int rk = 0;
+    for (int j = 0; j < L; ++j) {
+      const double t = sv[j];
+      rk += (t > s) || (t == s && j < c);
+    }
+    perm[rk] = c;
+  }
+  __syncthreads();
+  for (int i = tid; i < L; i += blockDim.x) P.sigma[i] = sv[perm[i]];
+  for (int e = tid; e < K * L; e += blockDim.x) {
+    const int t = e / L, r = e % L;
+    const int c = perm[t];
+    const double s = sv[c];
+    P.Jk[e] = J[(int64_t)c * L + r];
+    P.Wk[e] = (s > 0.0) ? cscale(X[(int64_t)c * L + r], 1.0 / s) : cmk(0.0, 0.0);
+  }
+}
+
+cudaError_t launch_jacobi(const Dims* dims, const ProbPtr* ptrs, int batch, int* status, cudaStream_t st) {
+  ProfScope ps("k_jacobi", st);
+  k_jacobi<<<batch, 256, 0, st>>>(dims, ptrs, status);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// ||theta||_F^2 in NPART fixed partial sums per problem (deterministic order).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_frob2(const Dims* __restrict__ dims, const ProbPtr* __restrict__ ptrs) {
+  __shared__ double red[32];
+  const int p = blockIdx.y;
+  const Dims D = dims[p];
+  if (!D.active) return;
+  const ProbPtr P = ptrs[p];
+  const int64_t total = (int64_t)D.m * D.n;
+  const int64_t chunk = (total + NPART - 1) / NPART;
+  const int64_t lo = chunk * blockIdx.x, hi = min(total, lo + chunk);
+  double s = 0.0;
+  for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) s += cabs2(P.theta[e]);
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) P.part[blockIdx.x] = s;
+}
+
+cudaError_t launch_frob2(const Dims* dims, const ProbPtr* ptrs, int batch, cudaStream_t st) {
+  ProfScope ps("k_frob2", st);
+  k_frob2<<<dim3(NPART, batch), 256, 0, st>>>(dims, ptrs);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Standalone epilogue: kept rank chi' = #{i < k : s_i > cutoff s_1},
+// w = 1 - sum_{i < chi'} s_i^2 / ||theta||_F^2, sigma (zero past chi'),
+// U columns and Vh rows past chi' zeroed.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_rrsvd_finalize(const Dims* __restrict__ dims,
+                                                        const ProbPtr* __restrict__ ptrs, double cutoff,
+                                                        double* sigma, double* w, int* rank, int* status) {
+  __shared__ int s_rank;
+  __shared__ double s_w;
+  const int p = blockIdx.x;
+  const Dims D = dims[p];
+  if (!D.active) return;
+  const ProbPtr P = ptrs[p];
+  const int K = D.k;
+  if (threadIdx.x == 0) {
+    double nf = 0.0;
+    for (int i = 0; i < NPART; ++i) nf += P.part[i];
+    const double s0 = P.sigma[0];
+    int r = 0;
+    double kept = 0.0;
+    bool finite = isfinite(nf) && isfinite(s0);
+    if (finite && s0 > 0.0) {
+      while (r < K && P.sigma[r] > cutoff * s0) {
+        kept += P.sigma[r] * P.sigma[r];
+        ++r;
+      }
+    }
+    if (!finite || r == 0) atomicOr(status, 1);
+    s_rank = r;
+    s_w = (nf > 0.0) ? 1.0 - kept / nf : 0.0;
+    P.scal[0] = nf;
+    P.scal[1] = s_w;
+    P.scal[2] = (double)r;
+  }
+  __syncthreads();
+  const int r = s_rank;
+  for (int i = threadIdx.x; i < K; i += blockDim.x) sigma[(int64_t)p * K + i] = (i < r) ? P.sigma[i] : 0.0;
+  if (threadIdx.x == 0) {
+    if (w) w[p] = s_w;
+    if (rank) rank[p] = r;
+  }
+  if (r < K) {
+    if (P.U)
+      for (int64_t e = threadIdx.x; e < (int64_t)D.m * K; e += blockDim.x)
+        if ((int)(e % K) >= r) P.U[e] = cmk(0.0, 0.0);
+    if (P.V)
+      for (int64_t e = (int64_t)r * D.n + threadIdx.x; e < (int64_t)K * D.n; e += blockDim.x) P.V[e] = cmk(0.0, 0.0);
+  }
+}
+
+cudaError_t launch_rrsvd_finalize(const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, double cutoff,
+                                  double* sigma, double* Vh, double* w, int* rank, int* status, cudaStream_t st) {
+  (void)cap;
+  (void)Vh;
+  ProfScope ps("k_rrsvd_finalize", st);
+  k_rrsvd_finalize<<<batch, 256, 0, st>>>(dims, ptrs, cutoff, sigma, w, rank, status);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// The RRSVD from theta (already in place) to sigma, Jk, Wk, U, Vh.
+// ---------------------------------------------------------------------------
+#define TG_TRY(x)                        \
+  do {                                   \
+    cudaError_t e_ = (x);                \
+    if (e_ != cudaSuccess) return e_;    \
+  } while (0)
+
+cudaError_t run_rrsvd(const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, int q, uint64_t seed,
+                      uint64_t sweep, int64_t chain0, int chain_stride, int* status, cudaStream_t st) {
+  TG_TRY(launch_omega(dims, ptrs, batch, cap, seed, sweep, chain0, chain_stride, st));
+  TG_TRY(launch_zgemm(G_Y0, dims, ptrs, batch, cap, st));  // Y0 = A Omega
+  TG_TRY(launch_qr(QR_Y, dims, ptrs, batch, st));           // Y0 = Q0 R0
+  for (int j = 0; j < q; ++j) {
+    TG_TRY(launch_zgemm(G_YT, dims, ptrs, batch, cap, st)); // Y~ = A^H Q
+    TG_TRY(launch_qr(QR_YT, dims, ptrs, batch, st));        // Y~ = Q~ R~
+    TG_TRY(launch_zgemm(G_Y, dims, ptrs, batch, cap, st));  // Y = A Q~
+    TG_TRY(launch_qr(QR_Y, dims, ptrs, batch, st));         // Y = Q R
+  }
+  TG_TRY(launch_zgemm(G_BH, dims, ptrs, batch, cap, st));   // B^H = A^H Q
+  TG_TRY(launch_qr(QR_BH, dims, ptrs, batch, st));          // B^H = Qb Rb
+  TG_TRY(launch_jacobi(dims, ptrs, batch, status, st));     // Rb J = W S
+  TG_TRY(launch_zgemm(G_U, dims, ptrs, batch, cap, st));    // U = Q J_k
+  TG_TRY(launch_zgemm(G_V, dims, ptrs, batch, cap, st));    // V = Qb W_k  (stored as V^H)
+  TG_TRY(launch_frob2(dims, ptrs, batch, st));
+  return cudaSuccess;
+}
+
+}  // namespace tg

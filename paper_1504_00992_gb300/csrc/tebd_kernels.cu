@@ -1,0 +1,282 @@
+// TEBD two-site update kernels, plain FP64 (sm_103a): theta contraction with
+// the gate fused in its epilogue, the per-sweep size plan, the Vidal-form
+// rebuild after truncation, and one-site expectation values.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "internal.cuh"
+#include "profiler.cuh"
+
+namespace tg {
+
+// ---------------------------------------------------------------------------
+// Sizes of every bond of one parity from the current bond dimensions.
+//   m = d_b chi_{b-1}, n = d_{b+1} chi_{b+1}, k = min(cap_b, m, n),
+//   l = min(k + p, m, n)   (sketch width; exact when it reaches min(m, n)).
+// ---------------------------------------------------------------------------
+__global__ void k_plan(ChainDev ch, int parity, int p, Dims* dims, int batch) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= batch) return;
+  const int b = parity + 2 * t;
+  Dims D;
+  D.dl = ch.dsite[b];
+  D.dr = ch.dsite[b + 1];
+  D.cl = ch.chi_ext[b];
+  D.cm = ch.chi_ext[b + 1];
+  D.cr = ch.chi_ext[b + 2];
+  D.m = D.dl * D.cl;
+  D.n = D.dr * D.cr;
+  int k = ch.chi_cap[b];
+  k = min(k, min(D.m, D.n));
+  D.k = k;
+  D.l = min(k + p, min(D.m, D.n));
+  D.bond = b;
+  D.active = (D.cm > 0) ? 1 : 0;
+  D.pad = 0;
+  dims[t] = D;
+}
+
+cudaError_t launch_plan(const ChainDev& ch, int parity, int p, Dims* dims, ProbPtr* ptrs, int batch,
+                        cudaStream_t st) {
+  (void)ptrs;
+  ProfScope ps("k_plan", st);
+  k_plan<<<(batch + 127) / 128, 128, 0, st>>>(ch, parity, p, dims, batch);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// theta~ of each bond (Eq. deftheta then Eq. defupdatetheta):
+//   C[(i',a),(j',c)] = sum_g (lam_l[a] Gl[i'][a][g] lam_m[g]) (Gr[j'][g][c] lam_r[c])
+//   theta~[i*cl + a][j*cr + c] = sum_{i'j'} G[(i dr + j), (i' dr + j')] C[(i',a),(j',c)]
+// A CTA owns an (alpha, beta) block with every i, j (the gate mixes only the
+// physical indices), so the gate is applied from shared memory right after
+// the contraction.  Tile: dl*TA <= 32 rows (TA >= 1), dr*TB <= 32 columns.
+// ---------------------------------------------------------------------------
+enum { TH_TK = 16, TH_MAXR = 64 };
+
+__global__ void __launch_bounds__(256) k_theta(const Dims* __restrict__ dims, const ProbPtr* __restrict__ ptrs) {
+  extern __shared__ cplx th_sm[];
+  const int p = blockIdx.z;
+  const Dims D = dims[p];
+  if (!D.active) return;
+  const ProbPtr P = ptrs[p];
+  const int dl = D.dl, dr = D.dr, cl = D.cl, cm = D.cm, cr = D.cr;
+  const int TA = max(1, 32 / dl), TB = max(1, 32 / dr);
+  const int a0 = blockIdx.y * TA, b0 = blockIdx.x * TB;
+  if (a0 >= cl || b0 >= cr) return;
+  const int ta = min(TA, cl - a0), tb = min(TB, cr - b0);
+  const int rows = dl * ta, cols = dr * tb;  // <= 64 each
+  cplx* Ls = th_sm;                          // [TH_TK][TH_MAXR]
+  cplx* Rs = Ls + TH_TK * TH_MAXR;           // [TH_TK][TH_MAXR]
+  cplx* Cs = Rs + TH_TK * TH_MAXR;           // [rows][cols]
+  const int tid = threadIdx.x;
+  const int nout = rows * cols;
+  cplx acc[16];
+#pragma unroll
+  for (int s = 0; s < 16; ++s) acc[s] = cmk(0.0, 0.0);
+  const cplx* gl = P.gl;
+  const cplx* gr = P.gr;
+  for (int g0 = 0; g0 < cm; g0 += TH_TK) {
+    // L rows (i', a): lam_l[a] Gl[i'][a0+a][g] lam_m[g]; g fastest
+    for (int e = tid; e < TH_TK * rows; e += 256) {
+      const int kk = e % TH_TK, ri = e / TH_TK;
+      const int ip = ri / ta, a = ri % ta, g = g0 + kk;
+      cplx v = cmk(0.0, 0.0);
+      if (g < cm) {
+        v = gl[((int64_t)ip * P.cap_l + a0 + a) * P.cap_m + g];
+        v = cscale(v, P.laml[a0 + a] * P.lamm[g]);
+      }
+      Ls[kk * TH_MAXR + ri] = v;
+    }
+    // R columns (j', c): Gr[j'][g][b0+c] lam_r[c]; c fastest
+    for (int e = tid; e < TH_TK * cols; e += 256) {
+      const int c = e % tb, rest = e / tb;
+      const int jp = rest % dr, kk = rest / dr;
+      const int g = g0 + kk;
+      cplx v = cmk(0.0, 0.0);
+      if (g < cm) {
+        v = gr[((int64_t)jp * P.cap_m + g) * P.cap_r + b0 + c];
+        v = cscale(v, P.lamr[b0 + c]);
+      }
+      Rs[kk * TH_MAXR + jp * tb + c] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < 16; ++s) {
+      const int o = tid + 256 * s;
+      if (o < nout) {
+        const int ri = o / cols, ci = o % cols;
+        cplx a = acc[s];
+#pragma unroll 4
+        for (int kk = 0; kk < TH_TK; ++kk) cfma(a, Ls[kk * TH_MAXR + ri], Rs[kk * TH_MAXR + ci]);
+        acc[s] = a;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int s = 0; s < 16; ++s) {
+    const int o = tid + 256 * s;
+    if (o < nout) Cs[o] = acc[s];
+  }
+  __syncthreads();
+  // gate: rows of Cs are (i', a) = i'*ta + a, columns (j', c) = j'*tb + c
+  const int dd = dl * dr;
+  cplx* th = const_cast<cplx*>(P.theta);
+  for (int o = tid; o < nout; o += 256) {
+    const int ri = o / cols, ci = o % cols;
+    const int i = ri / ta, a = ri % ta, j = ci / tb, c = ci % tb;
+    const cplx* grow = P.gate + (int64_t)(i * dr + j) * dd;
+    cplx v = cmk(0.0, 0.0);
+    for (int ip = 0; ip < dl; ++ip)
+      for (int jp = 0; jp < dr; ++jp) cfma(v, grow[ip * dr + jp], Cs[(ip * ta + a) * cols + jp * tb + c]);
+    th[(int64_t)(i * cl + a0 + a) * D.n + j * cr + b0 + c] = v;
+  }
+}
+
+cudaError_t launch_theta(const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, cudaStream_t st) {
+  const int TA = (cap.dl >= 32) ? 1 : 32 / cap.dl;
+  const int TB = (cap.dr >= 32) ? 1 : 32 / cap.dr;
+  dim3 grid((cap.cr + TB - 1) / TB, (cap.cl + TA - 1) / TA, batch);
+  const size_t smem = sizeof(cplx) * (2 * TH_TK * TH_MAXR + TH_MAXR * TH_MAXR);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_theta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr_set = true;
+  }
+  ProfScope ps("k_theta", st);
+  k_theta<<<grid, 256, smem, st>>>(dims, ptrs);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Rebuild after truncation (Eq. defdiscweigt and the Vidal extraction):
+//   chi' = #{i < k : s_i > cutoff s_1}, lambda'[b] = s / ||s_kept||,
+//   w = 1 - sum_kept s^2 / ||theta~||_F^2,
+//   Gamma'[b]^i[a][g]   = U[(i*cl + a)][g] / lam_l[a],
+//   Gamma'[b+1]^j[g][c] = Vh[g][(j*cr + c)] / lam_r[c]   (divide only if lam > 0).
+// One CTA per bond.  A zero or non-finite theta~ leaves the bond unchanged
+// and raises status bit 1.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_rebuild(ChainDev ch, const Dims* __restrict__ dims,
+                                                 const ProbPtr* __restrict__ ptrs, double cutoff, double* wout,
+                                                 int* status) {
+  __shared__ int s_rank;
+  __shared__ double s_inv;
+  const int p = blockIdx.x;
+  const Dims D = dims[p];
+  if (!D.active) return;
+  const ProbPtr P = ptrs[p];
+  if (threadIdx.x == 0) {
+    double nf = 0.0;
+    for (int i = 0; i < NPART; ++i) nf += P.part[i];
+    const double s0 = P.sigma[0];
+    int r = 0;
+    double kept = 0.0;
+    const bool finite = isfinite(nf) && isfinite(s0);
+    if (finite && s0 > 0.0) {
+      while (r < D.k && P.sigma[r] > cutoff * s0) {
+        kept += P.sigma[r] * P.sigma[r];
+        ++r;
+      }
+    }
+    if (!finite || r == 0 || !isfinite(kept)) {
+      atomicOr(status, 1);
+      r = 0;
+    }
+    s_rank = r;
+    s_inv = (r > 0) ? 1.0 / sqrt(kept) : 0.0;
+    wout[p] = (r > 0 && nf > 0.0) ? 1.0 - kept / nf : 0.0;
+  }
+  __syncthreads();
+  const int r = s_rank;
+  if (r == 0) return;
+  const int b = D.bond;
+  double* lam = ch.lam_ext[b + 1];
+  const int capm = P.cap_m;
+  for (int i = threadIdx.x; i < capm; i += blockDim.x) lam[i] = (i < r) ? P.sigma[i] * s_inv : 0.0;
+  cplx* gl = const_cast<cplx*>(P.gl);
+  cplx* gr = const_cast<cplx*>(P.gr);
+  const int dl = D.dl, dr = D.dr, cl = D.cl, cr = D.cr, K = D.k;
+  for (int64_t e = threadIdx.x; e < (int64_t)dl * cl * r; e += blockDim.x) {
+    const int g = (int)(e % r);
+    const int row = (int)(e / r);  // i*cl + a
+    const int a = row % cl, i = row / cl;
+    const double ll = P.laml[a];
+    const cplx u = P.U[(int64_t)row * K + g];
+    gl[((int64_t)i * P.cap_l + a) * capm + g] = (ll > 0.0) ? cscale(u, 1.0 / ll) : cmk(0.0, 0.0);
+  }
+  for (int64_t e = threadIdx.x; e < (int64_t)dr * r * cr; e += blockDim.x) {
+    const int c = (int)(e % cr);
+    const int rest = (int)(e / cr);
+    const int g = rest % r, j = rest / r;
+    const double lr = P.lamr[c];
+    const cplx v = P.V[(int64_t)g * D.n + j * cr + c];
+    gr[((int64_t)j * capm + g) * P.cap_r + c] = (lr > 0.0) ? cscale(v, 1.0 / lr) : cmk(0.0, 0.0);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) ch.chi_ext[b + 1] = r;
+}
+
+// Accumulates the discarded weights of one sweep in bond order.
+__global__ void k_wacc(const double* wout, int batch, const Dims* dims, double* wacc) {
+  double s = wacc[0], pr = wacc[1];
+  for (int p = 0; p < batch; ++p) {
+    if (!dims[p].active) continue;
+    s += wout[p];
+    pr *= (1.0 - wout[p]);
+  }
+  wacc[0] = s;
+  wacc[1] = pr;
+}
+
+cudaError_t launch_rebuild(const ChainDev& ch, const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap,
+                           double cutoff, double* wacc, int* status, cudaStream_t st) {
+  (void)cap;
+  // wout scratch lives right after the two accumulators
+  double* wout = wacc + 2;
+  ProfScope ps("k_rebuild", st);
+  k_rebuild<<<batch, 256, 0, st>>>(ch, dims, ptrs, cutoff, wout, status);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_wacc<<<1, 1, 0, st>>>(wout, batch, dims, wacc);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// <O_site> = sum_{a,c} lam_l[a]^2 lam_r[c]^2 sum_{i,i'} conj(G^i[a][c]) O[i][i'] G^{i'}[a][c]
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_expect(ChainDev ch, int site, const cplx* __restrict__ op, int d,
+                                                cplx* out) {
+  __shared__ double red[32];
+  const int cl = ch.chi_ext[site], cr = ch.chi_ext[site + 1];
+  const int capl = ch.cap_ext[site], capr = ch.cap_ext[site + 1];
+  const double* ll = ch.lam_ext[site];
+  const double* lr = ch.lam_ext[site + 1];
+  const cplx* G = ch.gamma[site];
+  double sr = 0.0, si = 0.0;
+  for (int64_t e = threadIdx.x; e < (int64_t)cl * cr; e += blockDim.x) {
+    const int a = (int)(e / cr), c = (int)(e % cr);
+    const double wgt = ll[a] * ll[a] * lr[c] * lr[c];
+    for (int i = 0; i < d; ++i) {
+      const cplx gi = G[((int64_t)i * capl + a) * capr + c];
+      cplx og = cmk(0.0, 0.0);
+      for (int ip = 0; ip < d; ++ip) cfma(og, op[i * d + ip], G[((int64_t)ip * capl + a) * capr + c]);
+      cplx t = cmk(0.0, 0.0);
+      cfma_conj(t, gi, og);
+      sr += wgt * t.x;
+      si += wgt * t.y;
+    }
+  }
+  sr = block_sum(sr, red);
+  si = block_sum(si, red);
+  if (threadIdx.x == 0) *out = cmk(sr, si);
+}
+
+cudaError_t launch_expect(const ChainDev& ch, int site, const cplx* op, int d, cplx* out, cudaStream_t st) {
+  ProfScope ps("k_expect", st);
+  k_expect<<<1, 256, 0, st>>>(ch, site, op, d, out);
+  return cudaGetLastError();
+}
+
+}  // namespace tg

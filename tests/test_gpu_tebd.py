@@ -1,0 +1,161 @@
+"""Parity of the CUDA TEBD bond update (Section II.B with the RRSVD of
+Section IV) with the CPU oracle on identical gates and Omega.  Compared
+quantities are gauge invariant: Schmidt values, the truncated theta rebuilt
+from the updated tensors, discarded weights and observables."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import tebd as T
+from paper_1504_00992_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _theta_k(gammas, lambdas, b):
+    """Truncated theta of bond b rebuilt from Vidal tensors (no gate)."""
+    N = len(gammas)
+    ll = lambdas[b - 1] if b > 0 else np.ones(1)
+    lr = lambdas[b + 1] if b + 1 < N - 1 else np.ones(1)
+    return T.theta_matrix(T.theta_tensor(gammas[b], ll, lambdas[b], gammas[b + 1], lr))
+
+
+@pytest.mark.parametrize("dl,dr,cl,cm,cr,chi,p,q", [
+    (2, 2, 16, 16, 16, 20, 4, 2),
+    (2, 2, 32, 32, 32, 32, 10, 2),     # the XXZ chain's saturated bond (theta 64 x 64)
+    (3, 3, 9, 12, 7, 12, 5, 1),        # ragged, spin 1
+    (4, 2, 5, 8, 11, 8, 3, 2),         # uneven local dimensions, truncating
+    (2, 2, 1, 1, 1, 4, 2, 2),          # product state bond
+])
+def test_single_bond_update_matches_oracle(lib, dl, dr, cl, cm, cr, chi, p, q):
+    from paper_1504_00992_gb300 import binding as B
+    rng = np.random.default_rng(dl * 1000 + cl)
+    bd = I.random_bond(dl, dr, cl, cm, cr, rng)
+    # chain of 4 sites whose bond 1 is updated by an odd sweep; the outer
+    # sites are wide enough to carry bond dimensions cl and cr
+    d0, d3 = max(2, cl), max(2, cr)
+    d_site = [d0, dl, dr, d3]
+    g0 = rng.standard_normal((d0, 1, cl)) + 1j * rng.standard_normal((d0, 1, cl))
+    g3 = rng.standard_normal((d3, cr, 1)) + 1j * rng.standard_normal((d3, cr, 1))
+    gammas = [g0, bd["gamma_l"], bd["gamma_r"], g3]
+    lambdas = [bd["lam_l"], bd["lam_m"], bd["lam_r"]]
+    caps = [cl, chi, cr]
+    sim = B.Tebd(4, 2, 0, p, q, seed=77, d_site=d_site, chi_bond=caps)
+    sim.set_mps(gammas, lambdas)
+    gates = [np.eye(d0 * dl), bd["gate"], np.eye(dr * d3)]
+    sim.set_gates(1, gates)
+    sim.step_odd()
+    g_gpu, l_gpu = sim.get_mps()
+    w_gpu = sim.discarded_weight()
+    sim.close()
+    ref = T.VidalMPS(gammas, lambdas)
+    info = T.bond_update(ref, 1, bd["gate"], chi, p, q, 77, 0)
+    lam_o = ref.lam[1]
+    r = min(len(lam_o), len(l_gpu[1]))
+    assert abs(len(lam_o) - len(l_gpu[1])) <= 1
+    assert np.abs(l_gpu[1][:r] - lam_o[:r]).max() <= 1e-10 * lam_o[0]
+    tk_g = _theta_k(g_gpu, l_gpu, 1)
+    tk_o = _theta_k(ref.gamma, ref.lam, 1)
+    if tk_g.shape == tk_o.shape:
+        assert np.linalg.norm(tk_g - tk_o) <= 1e-10 * np.linalg.norm(tk_o)
+    assert abs(w_gpu[0] - info["w"]) <= 1e-12
+
+
+def _run_pair(N, d, hs, dt, steps, chi, p, q, seed, psi0=None, rng_gates=None):
+    from paper_1504_00992_gb300 import binding as B
+    if rng_gates is None:
+        ge, go = I.trotter_gates(hs, dt / 2), I.trotter_gates(hs, dt)
+    else:
+        ge, go = rng_gates
+    psi0 = psi0 or I.neel_state(N, d)
+    sim = B.Tebd(N, d, chi, p, q, seed)
+    sim.set_product_state(psi0)
+    sim.set_gates(0, ge)
+    sim.set_gates(1, go)
+    ref = T.TEBD(T.product_state(psi0), chi, p, q, seed)
+    ref.set_gates(0, ge)
+    ref.set_gates(1, go)
+    for _ in range(steps):
+        sim.step_even(); sim.step_odd(); sim.step_even()
+        ref.second_order_step()
+    return sim, ref
+
+
+def test_xxz_chain_n20_matches_oracle_and_state_vector(lib):
+    """The XXZ chain N=20, d=2, J=1, Delta=0.5, dt=0.01, 100 Strang steps,
+    chi_max=32, p=10, q=2, Neel state, seed 0: observables within 1e-8 of the
+    oracle after 100 steps, Schmidt values within 1e-10 (normwise), and
+    within 1e-8 of the stored exact state-vector values."""
+    N, d = 20, 2
+    hs = I.xxz_bond_terms(N, d, 1.0, 0.5)
+    sim, ref = _run_pair(N, d, hs, 0.01, 100, 32, 10, 2, 0)
+    _, _, sz = I.spin_ops(d)
+    got = np.array([sim.expect(k, sz).real for k in range(N)])
+    exp = np.array([ref.expect(k, sz).real for k in range(N)])
+    assert np.abs(got - exp).max() <= 1e-8
+    for b in range(N - 1):
+        lg, lo = sim.get_lambda(b), ref.mps.lam[b]
+        r = min(len(lg), len(lo))
+        assert np.abs(lg[:r] - lo[:r]).max() <= 1e-10
+        assert np.sum(lg[r:] ** 2) + np.sum(lo[r:] ** 2) <= 1e-20
+    ws, wp = sim.discarded_weight()
+    assert abs(ws - ref.w_sum) <= 1e-12 and ws < 1e-15
+    golden = np.loadtxt(os.path.join(HERE, "golden", "c1_xxz_n20_sz_t1.txt"))
+    assert np.abs(got - golden[:, 1]).max() <= 1e-8
+    assert sim.sweeps() == 300
+    sim.close()
+
+
+def test_random_gates_spin1_truncating(lib):
+    N, d = 6, 3
+    rng = np.random.default_rng(11)
+    ge = [I.random_unitary(d * d, rng) for _ in range(N - 1)]
+    go = [I.random_unitary(d * d, rng) for _ in range(N - 1)]
+    sim, ref = _run_pair(N, d, None, None, 4, 5, 3, 2, 5, rng_gates=(ge, go))
+    sx, _, sz = I.spin_ops(d)
+    for k in range(N):
+        for op in (sx, sz):
+            assert abs(sim.expect(k, op) - ref.expect(k, op)) <= 1e-8
+    ws, _ = sim.discarded_weight()
+    assert ws > 1e-6 and abs(ws - ref.w_sum) <= 1e-10
+    sim.close()
+
+
+def test_call_order_and_input_errors(lib):
+    from paper_1504_00992_gb300 import binding as B
+    sim = B.Tebd(4, 2, 4, 2, 1, 0)
+    with pytest.raises(B.TebdError) as ei:
+        sim.step_even()
+    assert ei.value.code == B.TEBD_ESTATE
+    sim.close()
+    sim = B.Tebd(4, 2, 4, 2, 1, 0)
+    g = [np.eye(4) for _ in range(3)]
+    g[0] = g[0].astype(complex)
+    g[0][0, 0] = np.nan
+    with pytest.raises(B.TebdError) as ei:
+        sim.set_gates(0, g)
+    assert ei.value.code == B.TEBD_ENUMERIC
+    sim.close()
+    sim = B.Tebd(4, 2, 4, 2, 1, 0)
+    with pytest.raises(B.TebdError) as ei:
+        sim.expect(7, np.eye(2))
+    assert ei.value.code == B.TEBD_EINVAL
+    sim.close()
+    sim = B.Tebd(4, 2, 4, 2, 1, 0)
+    with pytest.raises(B.TebdError) as ei:
+        sim.set_product_state([np.zeros(2), np.ones(2), np.ones(2), np.ones(2)])
+    assert ei.value.code == B.TEBD_ENUMERIC
+    sim.close()
+
+
+def test_zero_gate_reports_numeric(lib):
+    from paper_1504_00992_gb300 import binding as B
+    sim = B.Tebd(4, 2, 4, 2, 1, 0)
+    sim.set_gates(0, [np.zeros((4, 4)), np.eye(4), np.zeros((4, 4))])
+    sim.step_even()
+    with pytest.raises(B.TebdError) as ei:
+        sim.discarded_weight()
+    assert ei.value.code == B.TEBD_ENUMERIC
+    sim.close()

@@ -1,0 +1,42 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every function
+declared in include/tebd_gb300.h (no compute calls: no GPU needed)."""
+import ctypes
+import subprocess
+
+import pytest
+
+from paper_1504_00992_gb300 import binding
+from paper_1504_00992_gb300 import build as B
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    return B.build()
+
+
+def test_library_exports_every_declared_function(libpath):
+    L = ctypes.CDLL(libpath)
+    names = binding.header_functions()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(L, name), name
+    assert set(names) == set(binding._SIGS), set(names) ^ set(binding._SIGS)
+
+
+def test_library_is_built_for_sm_103a(libpath):
+    out = subprocess.run(["cuobjdump", "--list-elf", libpath], capture_output=True, text=True).stdout
+    assert "sm_103a" in out
+
+
+def test_argument_errors_need_no_device(libpath):
+    L = binding.load(libpath)
+    h = ctypes.c_void_p()
+    assert L.tebd_create(1, 2, 4, 2, 1, 0, ctypes.byref(h)) == binding.TEBD_EINVAL
+    assert L.tebd_create(4, 1, 4, 2, 1, 0, ctypes.byref(h)) == binding.TEBD_EINVAL
+    assert L.tebd_create(4, 2, 0, 2, 1, 0, ctypes.byref(h)) == binding.TEBD_EINVAL
+    assert L.tebd_create(4, 2, 4, -1, 1, 0, ctypes.byref(h)) == binding.TEBD_EINVAL
+    assert L.tebd_create(4, 2, 4, 2, 1, 0, None) == binding.TEBD_EINVAL
+    assert L.rrsvd_plan_create(0, 4, 2, 1, 1, 1, 0, 0, ctypes.byref(h)) == binding.TEBD_EINVAL
+    assert L.rrsvd_plan_create(4, 4, 2, 1, 1, 1, 7, 0, ctypes.byref(h)) == binding.TEBD_ENOTIMPL
+    assert L.tebd_destroy(None) == binding.TEBD_OK
+    assert L.rrsvd_plan_destroy(None) == binding.TEBD_OK
