@@ -108,18 +108,51 @@ def test_xxz_chain_n20_matches_oracle_and_state_vector(lib):
     sim.close()
 
 
-def test_random_gates_spin1_truncating(lib):
-    N, d = 6, 3
-    rng = np.random.default_rng(11)
-    ge = [I.random_unitary(d * d, rng) for _ in range(N - 1)]
-    go = [I.random_unitary(d * d, rng) for _ in range(N - 1)]
-    sim, ref = _run_pair(N, d, None, None, 4, 5, 3, 2, 5, rng_gates=(ge, go))
+def test_spin1_xxz_truncating_matches_oracle(lib):
+    """Spin-1 XXZ chain N=8 truncated to chi=6 (discarded weight ~2e-3): the
+    truncation is well conditioned (the oracle against itself with another
+    Householder QR agrees to 2e-11), so GPU and oracle must agree to 1e-8."""
+    N, d = 8, 3
+    hs = I.xxz_bond_terms(N, d, 1.0, 0.5)
+    sim, ref = _run_pair(N, d, hs, 0.1, 10, 6, 4, 2, 5)
     sx, _, sz = I.spin_ops(d)
     for k in range(N):
         for op in (sx, sz):
             assert abs(sim.expect(k, op) - ref.expect(k, op)) <= 1e-8
-    ws, _ = sim.discarded_weight()
-    assert ws > 1e-6 and abs(ws - ref.w_sum) <= 1e-10
+    ws, wp = sim.discarded_weight()
+    assert ws > 1e-4 and abs(ws - ref.w_sum) <= 1e-10
+    assert abs(wp - ref.norm_prod) <= 1e-10
+    for b in range(N - 1):
+        lg, lo = sim.get_lambda(b), ref.mps.lam[b]
+        assert len(lg) == len(lo) and np.abs(lg - lo).max() <= 1e-9
+    sim.close()
+
+
+def test_random_gates_first_sweeps(lib):
+    """Haar-random spin-1 gates: the first even and odd sweeps from a product
+    state (no truncation yet) agree with the oracle to rounding.  Later
+    sweeps of this chain truncate nearly flat spectra, where any rounding
+    difference is amplified by the vanishing gap at the cut, so the result is
+    not unique and is not compared."""
+    N, d = 6, 3
+    rng = np.random.default_rng(11)
+    ge = [I.random_unitary(d * d, rng) for _ in range(N - 1)]
+    go = [I.random_unitary(d * d, rng) for _ in range(N - 1)]
+    from paper_1504_00992_gb300 import binding as B
+    psi0 = I.neel_state(N, d)
+    sim = B.Tebd(N, d, 9, 3, 2, 5)
+    sim.set_product_state(psi0)
+    sim.set_gates(0, ge)
+    sim.set_gates(1, go)
+    ref = T.TEBD(T.product_state(psi0), 9, 3, 2, 5)
+    ref.set_gates(0, ge)
+    ref.set_gates(1, go)
+    sim.step_even(); ref.step_even()
+    sim.step_odd(); ref.step_odd()
+    sx, _, sz = I.spin_ops(d)
+    for k in range(N):
+        for op in (sx, sz):
+            assert abs(sim.expect(k, op) - ref.expect(k, op)) <= 1e-12
     sim.close()
 
 
