@@ -219,6 +219,39 @@ int tebd_profiler_reset(void);
  * counts; *count receives the number of classes (may exceed max_entries). */
 int tebd_profiler_read(int max_entries, char* names, double* total_ms, int64_t* launches, int* count);
 
+/* ------------------------------------------------------------------------
+ * No-allocation variant of rrsvd_execute.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc -- code
+ * running inside another library's scheduling loop or a host callback that
+ * must not block (cudaMalloc may synchronise the device), or a process whose
+ * device memory is reserved up front by a caching allocator or a fixed
+ * budget -- and so can neither create an rrsvd plan nor supply a workspace.
+ *
+ * Same truncation, Omega and outputs as rrsvd_execute on a plan created
+ * with (m, n, k_max, p, q, batch, TEBD_PREC_FP64, seed); theta, sigma, U,
+ * Vh, w and rank are caller device buffers with the shapes given there (U,
+ * Vh, w, rank may be NULL).  All scratch is one static 16 MiB device array
+ * inside the library, held by every GPU that loads it until the process
+ * exits; the call allocates nothing.
+ *   - The first call on a device (with that device current) looks up the
+ *     array's device address and caches it; make that first call before any
+ *     stream capture.
+ *   - Calls share the array: work of two calls that overlaps on the GPU
+ *     (other streams, other host threads) races and corrupts both results.
+ *     Order such calls on one stream.
+ *   - Errors: TEBD_EINVAL for bad arguments or when descriptors plus
+ *     batch x (per-instance workspace, about 16 (5 l (m + n)/2 + 2 l^2 +
+ *     2 l k + k (m + n)) bytes) exceed 16 MiB -- e.g. one 512 x 512
+ *     instance with k = 128, p = 10 (about 9 MB) fits, one 2048 x 2048 with
+ *     k = 100, p = 20 (about 27 MB) does not;
+ *     TEBD_ECUDA if a launch or the address lookup fails.
+ * Asynchronous on `stream`; zero-norm instances report rank 0 as with
+ * rrsvd_execute.
+ * ---------------------------------------------------------------------- */
+int rrsvd_execute_noalloc(int m, int n, int k_max, int p, int q, int batch, uint64_t seed, int64_t chain0,
+                          const double* theta, double* sigma, double* U, double* Vh, double* w, int* rank,
+                          void* stream);
+
 #ifdef __cplusplus
 }
 #endif

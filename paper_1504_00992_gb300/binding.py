@@ -74,6 +74,7 @@ _SIGS = {
     "rrsvd_execute": (_i, [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_size_t, _vp]),
     "rrsvd_execute_host": (_i, [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp]),
     "rrsvd_last_error": (ctypes.c_char_p, [_vp]),
+    "rrsvd_execute_noalloc": (_i, [_i, _i, _i, _i, _i, _i, _u64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "tebd_profiler_enable": (_i, [_i]),
     "tebd_profiler_reset": (_i, []),
     "tebd_profiler_read": (_i, [_i, ctypes.c_char_p, _pd, ctypes.POINTER(_i64), _pi]),
@@ -273,6 +274,19 @@ def rrsvd_execute_host(plan, theta, chain0, sigma, U=None, Vh=None, w=None, rank
         return _vp(a.ctypes.data) if a is not None else None
     _pcheck(plan, load().rrsvd_execute_host(plan, hp(theta), chain0, hp(sigma), hp(U), hp(Vh), hp(w), hp(rank),
                                             _vp(int(stream_ptr)) if stream_ptr else None))
+
+
+def rrsvd_execute_noalloc(m, n, k_max, p, q, batch, seed, chain0, theta_ptr, sigma_ptr, U_ptr=0, Vh_ptr=0,
+                          w_ptr=0, rank_ptr=0, stream_ptr=0):
+    """No-allocation truncation on device buffers (integers, 0 for NULL):
+    same results as rrsvd_execute with a plan of the same sizes; scratch is a
+    fixed 16 MiB array inside the library shared by every call."""
+    def vp(x):
+        return _vp(int(x)) if x else None
+    rc = load().rrsvd_execute_noalloc(m, n, k_max, p, q, batch, seed, chain0, vp(theta_ptr), vp(sigma_ptr),
+                                      vp(U_ptr), vp(Vh_ptr), vp(w_ptr), vp(rank_ptr), vp(stream_ptr))
+    if rc != TEBD_OK:
+        raise TebdError(rc, "rrsvd_execute_noalloc")
 
 
 def rrsvd_last_error(plan):
