@@ -304,7 +304,11 @@ def main():
         traffic = None
         tp = os.path.join(ROOT, "profiles", "traffic.json")
         if os.path.exists(tp):
-            traffic = json.load(open(tp)).get(dom)
+            import hashlib
+            rec = json.load(open(tp))
+            src = open(os.path.join(ROOT, "paper_1504_00992_gb300", "csrc", "kernels.cu"), "rb").read()
+            if hashlib.sha256(src).hexdigest()[:16] == rec.get("_kernels_cu_sha256_16") and batch == 152:
+                traffic = rec.get(dom)   # counters taken on this exact kernel source
         roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "peak_source": "FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (derived)"}
