@@ -61,9 +61,14 @@ enum {
   TEBD_ESTATE = -7     /* call out of order (e.g. a step before its gates) */
 };
 
-/* Arithmetic of the RRSVD sketch (Alg. 1 GEMMs).  TEBD_PREC_FP64 is the
- * plain path: every step in FP64. */
-enum { TEBD_PREC_FP64 = 0 };
+/* Arithmetic of the RRSVD sketch (Alg. 1 GEMMs).
+ *   TEBD_PREC_FP64: the plain path, every step in FP64.
+ *   TEBD_PREC_TF32: Y0 = A Omega and power rounds 1..q-1 on the tensor cores
+ *     in TF32 with FP32 accumulation and FP32 QR; power round q (Y0 when
+ *     q = 0) as the refinement pass in split 3xTF32 products (FP32-level
+ *     accuracy); the last QR, B = Q^H A, the small SVD and lambda in FP64.
+ *     Standalone RRSVD plans only. */
+enum { TEBD_PREC_FP64 = 0, TEBD_PREC_TF32 = 2 };
 
 /* ------------------------------------------------------------------------
  * TEBD handle: an N-site chain in Vidal form resident on the device.
@@ -172,8 +177,10 @@ typedef struct rrsvd_plan_s* rrsvd_plan_t;
 /* Plan for `batch` complex m x n matrices truncated to k = min(k_max, m, n)
  * singular triplets with sketch width l = min(k + p, m, n) and q power
  * iterations.  Instance t of a call uses Philox counter chain = chain0 + t,
- * bond 0, sweep 0.  Errors: TEBD_EINVAL (m, n, batch < 1, k_max < 1, p < 0,
- * q < 0), TEBD_ENOTIMPL (precision). */
+ * bond 0, sweep 0.  precision: TEBD_PREC_FP64 or TEBD_PREC_TF32 (the
+ * workspace then also holds TF32 copies of theta, about 4 m n 8 bytes per
+ * instance).  Errors: TEBD_EINVAL (m, n, batch < 1, k_max < 1, p < 0,
+ * q < 0), TEBD_ENOTIMPL (precision, or l > 512). */
 int rrsvd_plan_create(int m, int n, int k_max, int p, int q, int batch, int precision, uint64_t seed,
                       rrsvd_plan_t* out);
 int rrsvd_plan_destroy(rrsvd_plan_t plan);
@@ -191,7 +198,8 @@ int rrsvd_plan_dims(rrsvd_plan_t plan, int* k, int* l);
  * using `workspace` (device, >= rrsvd_workspace_size bytes, 256-byte
  * aligned).  theta is only read.  Asynchronous on `stream`.
  * Errors: TEBD_EINVAL (NULL theta/sigma/workspace, small workspace, chain0 < 0),
- * TEBD_ECUDA. */
+ * TEBD_ECUDA.  A bounded tensor-core pipeline wait that expires (TF32 plans)
+ * is reported by the next rrsvd_execute_host as TEBD_ETIMEOUT. */
 int rrsvd_execute(rrsvd_plan_t plan, const double* theta, int64_t chain0, double* sigma, double* U, double* Vh,
                   double* w, int* rank, void* workspace, size_t workspace_bytes, void* stream);
 

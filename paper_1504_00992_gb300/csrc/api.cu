@@ -12,6 +12,7 @@
 
 #include "../../include/tebd_gb300.h"
 #include "internal.cuh"
+#include "mixed.cuh"
 #include "profiler.cuh"
 
 using namespace tg;
@@ -570,10 +571,13 @@ struct rrsvd_plan_s {
   Caps cap{};
   WsLayout lay{};
   size_t per = 0, ws_bytes = 0;
-  char* meta = nullptr;  // device: dims, ptrs, status
+  char* meta = nullptr;  // device: dims, ptrs, status, tensor-core error flag
   Dims* dims = nullptr;
   ProbPtr* ptrs = nullptr;
   int* status = nullptr;
+  int* tcerr = nullptr;
+  size_t mixed_off = 0;  // start of the mixed-precision arrays in the workspace
+  MixedSizes ms{};
   // host-path staging (allocated on first use)
   char* stage = nullptr;
   size_t stage_bytes = 0;
@@ -612,7 +616,7 @@ extern "C" int rrsvd_plan_create(int m, int n, int k_max, int p, int q, int batc
   if (!out) return TEBD_EINVAL;
   *out = nullptr;
   if (m < 1 || n < 1 || k_max < 1 || p < 0 || q < 0 || batch < 1) return TEBD_EINVAL;
-  if (precision != TEBD_PREC_FP64) return TEBD_ENOTIMPL;
+  if (precision != TEBD_PREC_FP64 && precision != TEBD_PREC_TF32) return TEBD_ENOTIMPL;
   rrsvd_plan_s* P = new rrsvd_plan_s();
   P->m = m; P->n = n; P->p = p; P->q = q; P->batch = batch; P->precision = precision; P->seed = seed;
   P->k = std::min(k_max, std::min(m, n));
@@ -623,11 +627,17 @@ extern "C" int rrsvd_plan_create(int m, int n, int k_max, int p, int q, int batc
   P->lay = ws_layout(m, n, P->k, P->l, true, true);
   P->per = P->lay.total;
   P->ws_bytes = P->per * (size_t)batch;
-  const size_t meta = align_up(sizeof(Dims) * batch) + align_up(sizeof(ProbPtr) * batch) + ALIGN;
+  if (precision == TEBD_PREC_TF32) {
+    P->ms = mixed_sizes(m, n, P->k, P->l);
+    P->mixed_off = P->ws_bytes;
+    P->ws_bytes += mixed_bytes(P->ms, batch);
+  }
+  const size_t meta = align_up(sizeof(Dims) * batch) + align_up(sizeof(ProbPtr) * batch) + 2 * ALIGN;
   if (cudaMalloc(&P->meta, meta) != cudaSuccess) { cudaGetLastError(); delete P; return TEBD_ENOMEM; }
   P->dims = (Dims*)P->meta;
   P->ptrs = (ProbPtr*)(P->meta + align_up(sizeof(Dims) * batch));
   P->status = (int*)(P->meta + align_up(sizeof(Dims) * batch) + align_up(sizeof(ProbPtr) * batch));
+  P->tcerr = (int*)((char*)P->status + ALIGN);
   std::vector<Dims> hd(batch);
   for (int i = 0; i < batch; ++i) {
     Dims& D = hd[i];
@@ -635,7 +645,7 @@ extern "C" int rrsvd_plan_create(int m, int n, int k_max, int p, int q, int batc
     D.m = m; D.n = n; D.k = P->k; D.l = P->l; D.bond = 0; D.active = 1;
   }
   if (cudaMemcpy(P->dims, hd.data(), sizeof(Dims) * batch, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemset(P->status, 0, sizeof(int)) != cudaSuccess) {
+      cudaMemset(P->status, 0, 2 * ALIGN) != cudaSuccess) {
     cudaFree(P->meta);
     delete P;
     return TEBD_ECUDA;
@@ -683,7 +693,13 @@ extern "C" int rrsvd_execute(rrsvd_plan_t P, const double* theta, int64_t chain0
                                                      (size_t)P->m * P->k, (cplx*)Vh, (size_t)P->k * P->n);
   }
   CU_OR(P, cudaGetLastError());
-  CU_OR(P, run_rrsvd(P->dims, P->ptrs, P->batch, P->cap, P->q, P->seed, 0, chain0, 1, P->status, st));
+  if (P->precision == TEBD_PREC_TF32) {
+    const MixedPtrs mp = mixed_carve((char*)workspace + P->mixed_off, P->ms, P->batch);
+    CU_OR(P, run_rrsvd_mixed(P->dims, P->ptrs, P->batch, P->cap, mp, P->q, P->seed, 0, chain0, 1, P->status,
+                             P->tcerr, st));
+  } else {
+    CU_OR(P, run_rrsvd(P->dims, P->ptrs, P->batch, P->cap, P->q, P->seed, 0, chain0, 1, P->status, st));
+  }
   CU_OR(P, launch_rrsvd_finalize(P->dims, P->ptrs, P->batch, P->cap, 1e-14, sigma, Vh, w, rank, P->status, st));
   return TEBD_OK;
 }
@@ -724,9 +740,11 @@ extern "C" int rrsvd_execute_host(rrsvd_plan_t P, const double* theta, int64_t c
   if (Vh) CU_OR(P, cudaMemcpyAsync(Vh, d_v, c * (size_t)P->k * P->n * B, cudaMemcpyDeviceToHost, st));
   if (w) CU_OR(P, cudaMemcpyAsync(w, d_w, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
   if (rank) CU_OR(P, cudaMemcpyAsync(rank, d_r, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
-  int stv = 0;
+  int stv = 0, tce = 0;
   CU_OR(P, cudaMemcpyAsync(&stv, P->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CU_OR(P, cudaMemcpyAsync(&tce, P->tcerr, sizeof(int), cudaMemcpyDeviceToHost, st));
   CU_OR(P, cudaStreamSynchronize(st));
+  if (tce) { P->err.set(TEBD_ETIMEOUT, "a tensor-core pipeline wait expired"); return P->err.code; }
   if (stv & 1) { P->err.set(TEBD_ENUMERIC, "an instance had a zero or non-finite theta"); return P->err.code; }
   return TEBD_OK;
 }

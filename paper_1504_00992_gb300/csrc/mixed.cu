@@ -1,0 +1,430 @@
+// Mixed-precision RRSVD (sm_103a): Alg. 1 with its products on the tensor
+// cores, then the FP64 projection and small SVD of Section IV.
+//
+//   Y0 = A Omega and power rounds 1..q-1  : TF32 tensor-core products (FP32
+//                                           accumulation), FP32 Householder QR;
+//   power round q (Y0 if q = 0)            : the refinement pass, 3xTF32 split
+//                                           products (FP32-level accuracy);
+//   last QR                                : FP64 Householder;
+//   B^H = A^H Q, QR of B^H, Jacobi SVD, U, V: FP64 (the existing kernels).
+//
+// Complex products use the real embedding: A (M x K complex) becomes the
+// M x 2K real matrix of interleaved (Re, Im) entries, and X (K x l complex)
+// becomes Bt (2l x 2K real, K-major) with rows
+//   2c   : ( Re X[j][c], -Im X[j][c] )  and  2c+1 : ( Im X[j][c], Re X[j][c] ),
+// so that real column 2c / 2c+1 of A Bt^T is Re / Im of (A X)[:, c].  A^H is
+// stored once as its own N x 2M copy with the conjugate folded in.  Rows of
+// every real operand are zero-padded to a multiple of 32 floats (128 bytes:
+// one TMA box, aligned x coordinates).
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <mutex>
+
+#include "internal.cuh"
+#include "mixed.cuh"
+#include "profiler.cuh"
+#include "tc_gemm.cuh"
+
+namespace tg {
+
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// ---------------------------------------------------------------------------
+// theta (FP64, m x n row-major, per instance) -> forward copy thf (m x K1)
+// and, when requested, the TF32 remainder thf_lo.
+// ---------------------------------------------------------------------------
+__global__ void k_conv_fwd(const MixedPtrs mp, const ProbPtr* __restrict__ ptrs, int m, int n, int K1, int want_lo) {
+  const int z = blockIdx.y;
+  const cplx* th = ptrs[z].theta;
+  float* hi = mp.thf_hi + (size_t)z * m * K1;
+  float* lo = mp.thf_lo + (size_t)z * m * K1;
+  const int64_t half = K1 / 2;  // complex columns incl. padding
+  const int64_t total = (int64_t)m * half;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / half), c = (int)(e % half);
+    float2 h = make_float2(0.f, 0.f), w = make_float2(0.f, 0.f);
+    if (c < n) {
+      const cplx v = th[(int64_t)r * n + c];
+      const float hr = tf32_rna((float)v.x), hm = tf32_rna((float)v.y);
+      h = make_float2(hr, hm);
+      w = make_float2(tf32_rna((float)(v.x - (double)hr)), tf32_rna((float)(v.y - (double)hm)));
+    }
+    reinterpret_cast<float2*>(hi)[e] = h;
+    if (want_lo) reinterpret_cast<float2*>(lo)[e] = w;
+  }
+}
+
+// theta -> adjoint copy tha (n x K2): tha[c][2r] = Re theta[r][c],
+// tha[c][2r+1] = -Im theta[r][c]; 32 x 32 complex tiles through shared memory.
+__global__ void __launch_bounds__(256) k_conv_adj(const MixedPtrs mp, const ProbPtr* __restrict__ ptrs, int m, int n,
+                                                  int K2, int want_lo) {
+  __shared__ cplx tile[32][33];
+  const int z = blockIdx.z;
+  const cplx* th = ptrs[z].theta;
+  float2* hi = reinterpret_cast<float2*>(mp.tha_hi + (size_t)z * n * K2);
+  float2* lo = reinterpret_cast<float2*>(mp.tha_lo + (size_t)z * n * K2);
+  const int half = K2 / 2;
+  const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;  // r over theta rows (incl. padding), c over theta columns
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int i = ty; i < 32; i += 8) {
+    const int r = r0 + i, c = c0 + tx;
+    tile[i][tx] = (r < m && c < n) ? th[(int64_t)r * n + c] : cmk(0.0, 0.0);
+  }
+  __syncthreads();
+  for (int i = ty; i < 32; i += 8) {
+    const int c = c0 + i, r = r0 + tx;  // output row c, complex column r
+    if (c < n && r < half) {
+      const cplx v = tile[tx][i];
+      const float hr = tf32_rna((float)v.x), hm = tf32_rna((float)(-v.y));
+      hi[(int64_t)c * half + r] = make_float2(hr, hm);
+      if (want_lo)
+        lo[(int64_t)c * half + r] =
+            make_float2(tf32_rna((float)(v.x - (double)hr)), tf32_rna((float)(-v.y - (double)hm)));
+    }
+  }
+}
+
+// Omega (Philox, as in the FP64 path) written directly as Bt (Np x K1), and
+// its TF32 remainder when the sketch itself is the refinement pass (q = 0).
+__global__ void k_omega_bt(const MixedPtrs mp, const Dims* __restrict__ dims, int n, int l, int Np, int K1,
+                           uint64_t seed, uint64_t sweep, int64_t chain0, int chain_stride, int want_lo) {
+  const int z = blockIdx.y;
+  const Dims D = dims[z];
+  float* bt = mp.bt_hi + (size_t)z * Np * K1;
+  float* btl = mp.bt_lo + (size_t)z * Np * K1;
+  const int half = K1 / 2;
+  const int64_t total = (int64_t)(Np / 2) * half;  // (row pair c, complex column j)
+  const uint64_t chain = (uint64_t)(chain0 + (int64_t)z * chain_stride);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e / half), j = (int)(e % half);
+    float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f), al = a, bl = a;
+    if (c < l && j < n) {
+      const cplx w = gauss_c((uint64_t)j * l + c, (uint64_t)D.bond, sweep, chain, seed, 0);
+      const float re = tf32_rna((float)w.x), im = tf32_rna((float)w.y);
+      a = make_float2(re, -im);
+      b = make_float2(im, re);
+      const float rl = tf32_rna((float)(w.x - (double)re)), il = tf32_rna((float)(w.y - (double)im));
+      al = make_float2(rl, -il);
+      bl = make_float2(il, rl);
+    }
+    reinterpret_cast<float2*>(bt + (size_t)(2 * c) * K1)[j] = a;
+    reinterpret_cast<float2*>(bt + (size_t)(2 * c + 1) * K1)[j] = b;
+    if (want_lo) {
+      reinterpret_cast<float2*>(btl + (size_t)(2 * c) * K1)[j] = al;
+      reinterpret_cast<float2*>(btl + (size_t)(2 * c + 1) * K1)[j] = bl;
+    }
+  }
+}
+
+// X (complex FP32, column-major Kc x l, instance stride Kc*l) -> Bt (Np x Kp)
+// and optionally its TF32 remainder.
+__global__ void k_conv_bt(const float2* __restrict__ X, float* bt_hi, float* bt_lo, int Kc, int l, int Np, int Kp,
+                          int want_lo) {
+  const int z = blockIdx.y;
+  const float2* x = X + (size_t)z * Kc * l;
+  float* bh = bt_hi + (size_t)z * Np * Kp;
+  float* bl = bt_lo + (size_t)z * Np * Kp;
+  const int half = Kp / 2;
+  const int64_t total = (int64_t)(Np / 2) * half;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e / half), j = (int)(e % half);
+    float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f), al = a, bl2 = a;
+    if (c < l && j < Kc) {
+      const float2 v = x[(int64_t)c * Kc + j];
+      const float re = tf32_rna(v.x), im = tf32_rna(v.y);
+      a = make_float2(re, -im);
+      b = make_float2(im, re);
+      const float rl = tf32_rna(v.x - re), il = tf32_rna(v.y - im);
+      al = make_float2(rl, -il);
+      bl2 = make_float2(il, rl);
+    }
+    reinterpret_cast<float2*>(bh + (size_t)(2 * c) * Kp)[j] = a;
+    reinterpret_cast<float2*>(bh + (size_t)(2 * c + 1) * Kp)[j] = b;
+    if (want_lo) {
+      reinterpret_cast<float2*>(bl + (size_t)(2 * c) * Kp)[j] = al;
+      reinterpret_cast<float2*>(bl + (size_t)(2 * c + 1) * Kp)[j] = bl2;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Householder QR with explicit Q in FP32 (same algorithm as the FP64 kernel:
+// alpha = -e^{i arg x0} ||x||, v0 = x0 - alpha, tau = 1/(||x|| (||x|| + |x0|))).
+// Input M x L column-major (overwritten), output Q M x L column-major.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 fmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ void ffma_conj(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(-a.y, b.x, acc.y);
+}
+__device__ __forceinline__ float fwarp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void __launch_bounds__(256) k_qr_f32(float2* Abase, float2* Qbase, int M, int L) {
+  __shared__ float red[32];
+  __shared__ float tau[512];
+  const int z = blockIdx.x;
+  float2* A = Abase + (size_t)z * M * L;
+  float2* Qo = Qbase + (size_t)z * M * L;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  for (int j = 0; j < L; ++j) {
+    float2* aj = A + (int64_t)j * M;
+    float s = 0.f;
+    for (int r = j + tid; r < M; r += blockDim.x) s += aj[r].x * aj[r].x + aj[r].y * aj[r].y;
+    s = fwarp_sum(s);
+    __syncthreads();
+    if (lane == 0) red[warp] = s;
+    __syncthreads();
+    if (tid == 0) {
+      float t = 0.f;
+      for (int w = 0; w < nw; ++w) t += red[w];
+      const float2 x0 = aj[j];
+      const float ax0 = sqrtf(x0.x * x0.x + x0.y * x0.y), nx = sqrtf(t);
+      if (nx == 0.f) {
+        tau[j] = 0.f;
+      } else {
+        const float2 ph = (ax0 > 0.f) ? make_float2(x0.x / ax0, x0.y / ax0) : make_float2(1.f, 0.f);
+        aj[j] = make_float2(ph.x * (ax0 + nx), ph.y * (ax0 + nx));
+        tau[j] = 1.f / (nx * (nx + ax0));
+      }
+    }
+    __syncthreads();
+    const float t = tau[j];
+    if (t != 0.f) {
+      for (int c = j + 1 + warp; c < L; c += nw) {
+        float2* ac = A + (int64_t)c * M;
+        float2 sd = make_float2(0.f, 0.f);
+        for (int r = j + lane; r < M; r += 32) ffma_conj(sd, aj[r], ac[r]);
+        sd.x = fwarp_sum(sd.x) * t;
+        sd.y = fwarp_sum(sd.y) * t;
+        for (int r = j + lane; r < M; r += 32) {
+          const float2 p = fmul(aj[r], sd);
+          ac[r] = make_float2(ac[r].x - p.x, ac[r].y - p.y);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  for (int64_t e = tid; e < (int64_t)M * L; e += blockDim.x) {
+    const int c = (int)(e / M), r = (int)(e % M);
+    Qo[e] = make_float2(r == c ? 1.f : 0.f, 0.f);
+  }
+  __syncthreads();
+  for (int j = L - 1; j >= 0; --j) {
+    const float t = tau[j];
+    if (t == 0.f) continue;
+    const float2* aj = A + (int64_t)j * M;
+    for (int c = j + warp; c < L; c += nw) {
+      float2* qc = Qo + (int64_t)c * M;
+      float2 sd = make_float2(0.f, 0.f);
+      for (int r = j + lane; r < M; r += 32) ffma_conj(sd, aj[r], qc[r]);
+      sd.x = fwarp_sum(sd.x) * t;
+      sd.y = fwarp_sum(sd.y) * t;
+      for (int r = j + lane; r < M; r += 32) {
+        const float2 p = fmul(aj[r], sd);
+        qc[r] = make_float2(qc[r].x - p.x, qc[r].y - p.y);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Yf (FP32) -> the FP64 buffer of the final QR.
+__global__ void k_f32_to_f64(const float2* __restrict__ Yf, const ProbPtr* __restrict__ ptrs, int m, int l) {
+  const int z = blockIdx.y;
+  const float2* y = Yf + (size_t)z * m * l;
+  cplx* Y = ptrs[z].Y;
+  const int64_t total = (int64_t)m * l;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+    Y[e] = cmk((double)y[e].x, (double)y[e].y);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static std::mutex mu;
+  static EncodeTiledFn fn = nullptr;
+  std::lock_guard<std::mutex> g(mu);
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+// 3-D map over (K-padded row, row, instance) of FP32 data with a box of
+// 32 x box_rows x 1 and 128-byte swizzle.
+static bool make_map(CUtensorMap* m, const float* base, int Kp, int rows, int batch, int box_rows) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)batch};
+  cuuint64_t strides[2] = {(cuuint64_t)Kp * 4, (cuuint64_t)rows * Kp * 4};
+  cuuint32_t box[3] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)base, dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+MixedSizes mixed_sizes(int m, int n, int k, int l) {
+  MixedSizes s;
+  s.K1 = ((2 * n + TC_BK - 1) / TC_BK) * TC_BK;
+  s.K2 = ((2 * m + TC_BK - 1) / TC_BK) * TC_BK;
+  s.Np = ((2 * l + 15) / 16) * 16;
+  s.BN = s.Np <= TC_MAXBN ? s.Np : TC_MAXBN;
+  const int Kmax = s.K1 > s.K2 ? s.K1 : s.K2;
+  const size_t f = sizeof(float);
+  s.thf = (size_t)m * s.K1 * f;
+  s.tha = (size_t)n * s.K2 * f;
+  s.bt = (size_t)s.Np * Kmax * f;
+  s.yf = (size_t)m * l * sizeof(float2);
+  s.ytf = (size_t)n * l * sizeof(float2);
+  (void)k;
+  return s;
+}
+
+static size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+size_t mixed_bytes(const MixedSizes& s, int batch) {
+  return 2 * up256(s.thf * batch) + 2 * up256(s.tha * batch) + 2 * up256(s.bt * batch) + 2 * up256(s.yf * batch) +
+         2 * up256(s.ytf * batch);
+}
+
+MixedPtrs mixed_carve(char* base, const MixedSizes& s, int batch) {
+  MixedPtrs p;
+  size_t o = 0;
+  p.thf_hi = (float*)(base + o); o += up256(s.thf * batch);
+  p.thf_lo = (float*)(base + o); o += up256(s.thf * batch);
+  p.tha_hi = (float*)(base + o); o += up256(s.tha * batch);
+  p.tha_lo = (float*)(base + o); o += up256(s.tha * batch);
+  p.bt_hi = (float*)(base + o); o += up256(s.bt * batch);
+  p.bt_lo = (float*)(base + o); o += up256(s.bt * batch);
+  p.Yf = (float2*)(base + o); o += up256(s.yf * batch);
+  p.Qf = (float2*)(base + o); o += up256(s.yf * batch);
+  p.Ytf = (float2*)(base + o); o += up256(s.ytf * batch);
+  p.Qtf = (float2*)(base + o); o += up256(s.ytf * batch);
+  return p;
+}
+
+#define MX_TRY(x)                     \
+  do {                                \
+    cudaError_t e_ = (x);             \
+    if (e_ != cudaSuccess) return e_; \
+  } while (0)
+
+static int grid1d(int64_t total) {
+  int64_t b = (total + 255) / 256;
+  if (b > 1024) b = 1024;
+  return (int)(b < 1 ? 1 : b);
+}
+
+// One tensor-core product: out (rows x l complex, per instance) from
+// A (rows x Kp) and Bt (Np x Kp); npass 1 or 3.
+static cudaError_t tc_product(const float* A0, const float* A1, const float* B0, const float* B1, int rows, int Kp,
+                              const MixedSizes& s, int l, int npass, float2* out, int batch, int* err,
+                              cudaStream_t st) {
+  CUtensorMap ma0, ma1, mb0, mb1;
+  if (!make_map(&ma0, A0, Kp, rows, batch, TC_BM) || !make_map(&ma1, A1, Kp, rows, batch, TC_BM) ||
+      !make_map(&mb0, B0, Kp, s.Np, batch, s.BN) || !make_map(&mb1, B1, Kp, s.Np, batch, s.BN))
+    return cudaErrorInvalidValue;
+  TcArgs a;
+  a.M = rows;
+  a.Kp = Kp;
+  a.BN = s.BN;
+  a.l = l;
+  a.npass = npass;
+  a.out = out;
+  a.out_stride = (int64_t)rows * l;
+  a.err = err;
+  const size_t sm = tc_smem_bytes(s.BN);
+  static int attr_done = 0;
+  if (!attr_done) {
+    MX_TRY(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes(TC_MAXBN)));
+    attr_done = 1;
+  }
+  dim3 grid((rows + TC_BM - 1) / TC_BM, (s.Np + s.BN - 1) / s.BN, batch);
+  ProfScope ps(npass == 1 ? "k_tc_gemm[tf32]" : "k_tc_gemm[3xtf32]", st);
+  k_tc_gemm<<<grid, 128, sm, st>>>(ma0, ma1, mb0, mb1, a);
+  return cudaGetLastError();
+}
+
+static cudaError_t qr_f32(float2* A, float2* Q, int M, int L, int batch, cudaStream_t st) {
+  ProfScope ps("k_qr_f32", st);
+  k_qr_f32<<<batch, 256, 0, st>>>(A, Q, M, L);
+  return cudaGetLastError();
+}
+
+static cudaError_t conv_bt(const float2* X, const MixedPtrs& mp, int Kc, int l, int Kp, const MixedSizes& s, int lo,
+                           int batch, cudaStream_t st) {
+  ProfScope ps("k_conv_bt", st);
+  k_conv_bt<<<dim3(grid1d((int64_t)(s.Np / 2) * (Kp / 2)), batch), 256, 0, st>>>(X, mp.bt_hi, mp.bt_lo, Kc, l, s.Np,
+                                                                                   Kp, lo);
+  return cudaGetLastError();
+}
+
+cudaError_t run_rrsvd_mixed(const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, const MixedPtrs& mp,
+                            int q, uint64_t seed, uint64_t sweep, int64_t chain0, int chain_stride, int* status,
+                            int* err, cudaStream_t st) {
+  const int m = cap.m, n = cap.n, k = cap.k, l = cap.l;
+  const MixedSizes s = mixed_sizes(m, n, k, l);
+  {
+    ProfScope ps("k_conv_theta", st);
+    k_conv_fwd<<<dim3(grid1d((int64_t)m * (s.K1 / 2)), batch), 256, 0, st>>>(mp, ptrs, m, n, s.K1, 1);
+    MX_TRY(cudaGetLastError());
+    k_conv_adj<<<dim3((s.K2 / 2 + 31) / 32, (n + 31) / 32, batch), 256, 0, st>>>(mp, ptrs, m, n, s.K2, 1);
+    MX_TRY(cudaGetLastError());
+  }
+  {
+    ProfScope ps("k_omega_bt", st);
+    k_omega_bt<<<dim3(grid1d((int64_t)(s.Np / 2) * (s.K1 / 2)), batch), 256, 0, st>>>(mp, dims, n, l, s.Np, s.K1, seed,
+                                                                                      sweep, chain0, chain_stride,
+                                                                                      q == 0 ? 1 : 0);
+    MX_TRY(cudaGetLastError());
+  }
+  // Y0 = A Omega: TF32, or the refinement pass when q == 0
+  const int p0 = (q == 0) ? 3 : 1;
+  MX_TRY(tc_product(mp.thf_hi, mp.thf_lo, mp.bt_hi, mp.bt_lo, m, s.K1, s, l, p0, mp.Yf, batch, err, st));
+  for (int j = 1; j <= q; ++j) {
+    const int np = (j == q) ? 3 : 1;
+    MX_TRY(qr_f32(mp.Yf, mp.Qf, m, l, batch, st));                                 // Y = Q R
+    MX_TRY(conv_bt(mp.Qf, mp, m, l, s.K2, s, np == 3, batch, st));
+    MX_TRY(tc_product(mp.tha_hi, mp.tha_lo, mp.bt_hi, mp.bt_lo, n, s.K2, s, l, np, mp.Ytf, batch, err, st));  // A^H Q
+    MX_TRY(qr_f32(mp.Ytf, mp.Qtf, n, l, batch, st));                              // = Q~ R~
+    MX_TRY(conv_bt(mp.Qtf, mp, n, l, s.K1, s, np == 3, batch, st));
+    MX_TRY(tc_product(mp.thf_hi, mp.thf_lo, mp.bt_hi, mp.bt_lo, m, s.K1, s, l, np, mp.Yf, batch, err, st));  // A Q~
+  }
+  {
+    ProfScope ps("k_f32_to_f64", st);
+    k_f32_to_f64<<<dim3(grid1d((int64_t)m * l), batch), 256, 0, st>>>(mp.Yf, ptrs, m, l);
+    MX_TRY(cudaGetLastError());
+  }
+  MX_TRY(launch_qr(QR_Y, dims, ptrs, batch, st));           // last QR in FP64
+  MX_TRY(launch_zgemm(G_BH, dims, ptrs, batch, cap, st));   // B^H = A^H Q (FP64)
+  MX_TRY(launch_qr(QR_BH, dims, ptrs, batch, st));
+  MX_TRY(launch_jacobi(dims, ptrs, batch, status, st));
+  MX_TRY(launch_zgemm(G_U, dims, ptrs, batch, cap, st));
+  MX_TRY(launch_zgemm(G_V, dims, ptrs, batch, cap, st));
+  MX_TRY(launch_frob2(dims, ptrs, batch, st));
+  return cudaSuccess;
+}
+
+}  // namespace tg

@@ -1,0 +1,43 @@
+// Buffers and entry of the mixed-precision RRSVD (mixed.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "internal.cuh"
+
+namespace tg {
+
+// Padded sizes of the real-embedded operands of one instance.
+struct MixedSizes {
+  int K1;        // 2n rounded up to 32: row length of theta's forward copy and of Bt for A X
+  int K2;        // 2m rounded up to 32: row length of the adjoint copy and of Bt for A^H X
+  int Np;        // 2l rounded up to 16: rows of Bt (tensor-core N)
+  int BN;        // tensor-core tile width, min(Np, 256)
+  size_t thf, tha, bt, yf, ytf;  // bytes per instance
+};
+
+// Batch-major arrays (instance z at base + z * per-instance size).
+struct MixedPtrs {
+  float* thf_hi;  // m x K1, TF32-rounded theta (Re, Im interleaved)
+  float* thf_lo;  // TF32 remainder of theta
+  float* tha_hi;  // n x K2, TF32-rounded theta^H
+  float* tha_lo;
+  float* bt_hi;   // Np x K (K1 or K2), real embedding of the right operand
+  float* bt_lo;
+  float2* Yf;     // m x l complex FP32, column-major
+  float2* Qf;
+  float2* Ytf;    // n x l
+  float2* Qtf;
+};
+
+MixedSizes mixed_sizes(int m, int n, int k, int l);
+size_t mixed_bytes(const MixedSizes& s, int batch);
+MixedPtrs mixed_carve(char* base, const MixedSizes& s, int batch);
+
+// Alg. 1 with tensor-core products and the FP64 projection / small SVD;
+// uniform sizes over the batch (cap holds them).
+cudaError_t run_rrsvd_mixed(const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, const MixedPtrs& mp,
+                            int q, uint64_t seed, uint64_t sweep, int64_t chain0, int chain_stride, int* status,
+                            int* err, cudaStream_t st);
+
+}  // namespace tg

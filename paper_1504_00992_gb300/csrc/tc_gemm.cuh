@@ -1,0 +1,233 @@
+// Tensor-core GEMM for the low-precision sketch products (sm_103a tcgen05).
+//
+// Computes, per instance z of a batch, C = sum_pass A_pass * B_pass^T with
+//   A: M x Kp real FP32 holding TF32-rounded values, K-major (row-major),
+//   B: Np x Kp real FP32 (TF32-rounded), K-major,
+// FP32 accumulation in tensor memory, and writes complex FP32 columns:
+//   out[c * M + r] = (C[r][2c], C[r][2c+1])  for c < l, r < M
+// (the real embedding of a complex product puts Re and Im of output column
+// c in adjacent real columns 2c, 2c+1).
+//
+// npass = 1: A0 B0^T (one TF32 product).  npass = 3: A0 B0^T + A0 B1^T +
+// A1 B0^T (the "3xTF32" split product, FP32-level accuracy).
+//
+// Structure (one CTA = 128 rows x up to 256 columns, 4 warps):
+//   warp 0 / one lane : TMA producer (cp.async.bulk.tensor.3d into a ring of
+//                       STAGES shared-memory slots, 128-byte swizzle),
+//   warp 1 / one lane : MMA issuer (tcgen05.mma.cta_group::1.kind::tf32,
+//                       4 x K=8 per 128-byte slot), frees slots with
+//                       tcgen05.commit -> mbarrier,
+//   all 4 warps       : epilogue, tcgen05.ld 32x32b from the accumulator
+//                       (warp w owns TMEM lanes 32w..32w+31 = tile rows).
+// Every mbarrier wait is bounded; on expiry the kernel raises *err, skips
+// the remaining work, waits (bounded) for its own copies and frees TMEM.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tg {
+
+enum { TC_BM = 128, TC_BK = 32, TC_STAGES = 4, TC_MAXBN = 256, TC_TMEM_COLS = 256 };
+
+struct TcArgs {
+  int M;          // rows of A and of the output
+  int Kp;         // padded reduction length (multiple of TC_BK)
+  int BN;         // columns per CTA (multiple of 16, <= 256)
+  int l;          // complex output columns
+  int npass;      // 1 or 3
+  float2* out;    // complex output, column-major M x l, instance stride out_stride
+  int64_t out_stride;
+  int* err;       // error flag (timeouts)
+};
+
+__device__ __forceinline__ uint32_t tc_smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void tc_mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc_smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void tc_mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc_smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool tc_mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(tc_smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait on a phase of an mbarrier; returns false (and raises *err /
+// the CTA abort flag) when the limit expires or another thread gave up.
+__device__ __forceinline__ bool tc_mbar_wait(uint64_t* bar, uint32_t parity, int* err, volatile int* abort_flag) {
+  for (uint32_t i = 0; i < (1u << 24); ++i) {
+    if (tc_mbar_try_wait(bar, parity)) return true;
+    if ((i & 1023u) == 1023u && *abort_flag) return false;
+  }
+  *abort_flag = 1;
+  atomicExch(err, 1);
+  return false;
+}
+__device__ __forceinline__ void tc_tma_load_3d(void* dst, const CUtensorMap* tm, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+          "r"(tc_smem_u32(dst)),
+      "l"((uint64_t)tm), "r"(x), "r"(y), "r"(z), "r"(tc_smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms of
+// 1024 bytes stacked along M/N (stride byte offset 1024), descriptor version 1.
+__device__ __forceinline__ uint64_t tc_desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;             // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset
+  d |= (uint64_t)1 << 46;             // version
+  d |= (uint64_t)2 << 61;             // 128-byte swizzle
+  return d;
+}
+// Instruction descriptor, kind::tf32: D = F32, A = B = TF32, both K-major.
+__host__ __device__ constexpr uint32_t tc_idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__global__ void __launch_bounds__(128, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
+              const __grid_constant__ CUtensorMap tmB0, const __grid_constant__ CUtensorMap tmB1, TcArgs a) {
+  extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
+  const uint32_t bytesA = TC_BM * TC_BK * 4;     // 16 KB
+  const uint32_t bytesB = (uint32_t)a.BN * TC_BK * 4;
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + TC_STAGES * bytesA;
+  uint64_t* full = (uint64_t*)(sB + TC_STAGES * bytesB);
+  uint64_t* empty = full + TC_STAGES;
+  uint64_t* accf = empty + TC_STAGES;
+  uint32_t* tmem_holder = (uint32_t*)(accf + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_holder + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * a.BN, z = blockIdx.z;
+  const int KB = a.Kp / TC_BK;
+  const int iters = a.npass * KB;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_smem_u32(tmem_holder)),
+                 "r"((uint32_t)TC_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 32) {
+    for (int s = 0; s < TC_STAGES; ++s) {
+      tc_mbar_init(&full[s], 1);
+      tc_mbar_init(&empty[s], 1);
+    }
+    tc_mbar_init(accf, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_holder;
+
+  if (warp == 0 && lane == 0) {
+    // ---- producer
+    int issued = 0;
+    for (int it = 0; it < iters; ++it) {
+      const int s = it % TC_STAGES;
+      const uint32_t r = (uint32_t)(it / TC_STAGES);
+      if (it >= TC_STAGES && !tc_mbar_wait(&empty[s], (r & 1u) ^ 1u, a.err, abort_flag)) break;
+      const int pass = it / KB, kb = it % KB;
+      const CUtensorMap* ta = (pass == 2) ? &tmA1 : &tmA0;
+      const CUtensorMap* tb = (pass == 1) ? &tmB1 : &tmB0;
+      tc_mbar_expect_tx(&full[s], bytesA + bytesB);
+      tc_tma_load_3d(sA + s * bytesA, ta, kb * TC_BK, m0, z, &full[s]);
+      tc_tma_load_3d(sB + s * bytesB, tb, kb * TC_BK, n0, z, &full[s]);
+      issued = it + 1;
+    }
+    // make sure every copy this thread issued has landed before teardown
+    if (*abort_flag) {
+      for (int it = (issued > TC_STAGES ? issued - TC_STAGES : 0); it < issued; ++it)
+        for (uint32_t i = 0; i < (1u << 22); ++i)
+          if (tc_mbar_try_wait(&full[it % TC_STAGES], (uint32_t)(it / TC_STAGES) & 1u)) break;
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer
+    const uint32_t idesc = tc_idesc_tf32(TC_BM, a.BN);
+    bool ok = true;
+    for (int it = 0; it < iters; ++it) {
+      const int s = it % TC_STAGES;
+      const uint32_t r = (uint32_t)(it / TC_STAGES);
+      if (!tc_mbar_wait(&full[s], r & 1u, a.err, abort_flag)) { ok = false; break; }
+      tc_fence_after();
+      const uint32_t aa = tc_smem_u32(sA + s * bytesA), bb = tc_smem_u32(sB + s * bytesB);
+#pragma unroll
+      for (int kk = 0; kk < TC_BK / 8; ++kk) {
+        const uint64_t ad = tc_desc_sw128(aa + kk * 32), bd = tc_desc_sw128(bb + kk * 32);
+        const uint32_t acc = (it > 0 || kk > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+            : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       tc_smem_u32(&empty[s]))
+                   : "memory");
+    }
+    if (ok)
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       tc_smem_u32(accf))
+                   : "memory");
+    else
+      *abort_flag = 1;
+  }
+  __syncwarp();
+  // ---- epilogue: every thread owns one row of the tile
+  const bool have = tc_mbar_wait(accf, 0, a.err, abort_flag);
+  tc_fence_after();
+  if (have) {
+    const int row = m0 + warp * 32 + lane;
+    float2* out = a.out + a.out_stride * z;
+    for (int c0 = 0; c0 < a.BN; c0 += 16) {
+      uint32_t v[16];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(taddr)
+          : "memory");
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (row < a.M) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int cc = (n0 + c0) / 2 + j;
+          if (cc < a.l) out[(int64_t)cc * a.M + row] = make_float2(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]));
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)TC_TMEM_COLS)
+                 : "memory");
+  }
+}
+
+inline size_t tc_smem_bytes(int BN) {
+  return 1024 + (size_t)TC_STAGES * (TC_BM * TC_BK * 4 + (size_t)BN * TC_BK * 4) + (2 * TC_STAGES + 1) * 8 + 16;
+}
+
+}  // namespace tg

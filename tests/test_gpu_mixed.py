@@ -1,0 +1,82 @@
+"""The mixed-precision RRSVD form (TEBD_PREC_TF32): TF32 tensor-core sketch
+and power iterations, 3xTF32 refinement of the last power round, FP64 last
+QR / projection / small SVD.
+
+Its stated tolerances: with Omega rounded to TF32 and the sketch in TF32 the
+mixed form is a different (equally valid) randomized truncation than the FP64
+oracle, so it is held to the FP64 method's accuracy, not to its rounding
+(exact spectra are known by construction):
+  * max_i |s_i(mixed) - s_i(exact)| <= max_i |s_i(oracle) - s_i(exact)| + 1e-8 s_1;
+  * excess error (||A - A_k||_F - ||A - A_k(exact)||_F) / ||A||_F no more
+    than 1e-8 above the oracle's;
+  * where the FP64 method meets the 1e-8 bar, the mixed form meets it too;
+  * the returned factors are orthonormal to 1e-12 (FP64 last QR and Jacobi).
+"""
+import numpy as np
+import pytest
+
+from oracle import rrsvd as R
+from oracle.philox import gaussian_omega
+from paper_1504_00992_gb300 import inputs as I
+from tests.gpu_util import rrsvd_device, truncated
+
+pytestmark = pytest.mark.gpu
+SEED = 4321
+
+
+@pytest.mark.parametrize("m,n,k,p,q,scale", [
+    (400, 400, 60, 20, 2, 12.0),   # the single-bond stress spectrum shape, reduced
+    (300, 200, 40, 10, 1, 8.0),    # ragged: no size is a multiple of 128 / 32
+    (130, 70, 20, 6, 0, 4.0),      # q = 0: the sketch itself is the refinement pass
+    (96, 96, 24, 8, 2, 5.0),
+])
+def test_mixed_form_meets_its_tolerances(lib, m, n, k, p, q, scale):
+    from paper_1504_00992_gb300 import binding as B
+    batch = 3
+    sig = I.exp_spectrum(min(m, n), scale)
+    theta = np.stack([I.synthetic_theta(m, n, sig, seed=200 + t) for t in range(batch)])
+    plan = B.rrsvd_plan_create(m, n, k, p, q, batch, B.TEBD_PREC_TF32, SEED)
+    try:
+        res = rrsvd_device(B, plan, theta, chain0=2)
+    finally:
+        B.rrsvd_plan_destroy(plan)
+    kk, l = R.sketch_sizes(m, n, k, p)
+    opt = np.sqrt(np.sum(sig[kk:] ** 2))
+    for t in range(batch):
+        A = theta[t]
+        nA = np.linalg.norm(A)
+        s = res["sigma"][t]
+        assert res["rank"][t] == kk
+        Uk, sk, Vhk, w = R.rrsvd_truncate(A, gaussian_omega(n, l, SEED, chain=2 + t), kk, q)
+        err_o = np.abs(sk - sig[:kk]).max()
+        err_m = np.abs(s - sig[:kk]).max()
+        assert err_m <= err_o + 1e-8 * sig[0]
+        if err_o <= 1e-8:
+            assert err_m <= 1e-8
+        exc_o = (np.linalg.norm(A - truncated(Uk, sk, Vhk)) - opt) / nA
+        exc_m = (np.linalg.norm(A - truncated(res["U"][t], s, res["Vh"][t])) - opt) / nA
+        assert exc_m <= exc_o + 1e-8
+        U = res["U"][t]
+        assert np.abs(U.conj().T @ U - np.eye(kk)).max() < 1e-12
+        V = res["Vh"][t]
+        assert np.abs(V @ V.conj().T - np.eye(kk)).max() < 1e-12
+        assert abs(res["w"][t] - w) <= 1e-8 + abs(w - (np.sum(sig[kk:] ** 2) / np.sum(sig ** 2)))
+
+
+def test_mixed_form_full_size_sampled(lib):
+    """2000 x 2000, k=100, p=20, q=2 (the single-bond stress workload), two
+    instances: kept singular values within 1e-8 of the exact spectrum."""
+    from paper_1504_00992_gb300 import binding as B
+    m = n = 2000
+    sig = I.exp_spectrum(n)
+    theta = np.stack([I.synthetic_theta(m, n, sig, seed=t) for t in range(2)])
+    plan = B.rrsvd_plan_create(m, n, 100, 20, 2, 2, B.TEBD_PREC_TF32, SEED)
+    try:
+        res = rrsvd_device(B, plan, theta)
+    finally:
+        B.rrsvd_plan_destroy(plan)
+    for t in range(2):
+        assert np.abs(res["sigma"][t] - sig[:100]).max() <= 1e-8
+        opt = np.sqrt(np.sum(sig[100:] ** 2))
+        err = np.linalg.norm(theta[t] - truncated(res["U"][t], res["sigma"][t], res["Vh"][t]))
+        assert (err - opt) / np.linalg.norm(theta[t]) <= 1e-8
