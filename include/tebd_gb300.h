@@ -86,7 +86,16 @@ typedef struct {
   uint64_t seed;        /* Philox key word 0 */
   int precision;        /* TEBD_PREC_* */
   double sv_cutoff;     /* keep s_i > sv_cutoff * s_1 among the first k; <= 0 selects 1e-14 */
-  int chain;            /* chain index entering the Philox counter (default 0) */
+  int chain;            /* chain index entering the Philox counter (default 0); with
+                           tebd_create_multi, chain c uses chain + c */
+  int use_graph;        /* nonzero: each sweep is captured once into a CUDA graph and
+                           replayed (not while the kernel profiler is enabled); the
+                           legacy stream 0 cannot be captured, so such a handle then
+                           runs on a blocking stream of its own */
+  int autotune;         /* nonzero: at creation, time the 16x16 and 32x32 GEMM tiles of
+                           every stage at the capacity sizes and keep the faster */
+  size_t workspace_budget; /* bytes of per-bond workspace one wave may use (0 = all bonds
+                              of a parity in one wave); larger batches run in waves */
 } tebd_desc_t;
 
 /* Section II (Eq. defmps, deftheta, defupdatetheta) with the RRSVD of
@@ -102,15 +111,32 @@ int tebd_create(int N, int d, int chi_max, int p, int q, uint64_t seed, tebd_t* 
 /* As tebd_create, with per-site d, per-bond caps, precision and cutoff. */
 int tebd_create_ex(const tebd_desc_t* desc, tebd_t* out);
 
+/* Many independent chains in one handle (Section II.C sweeps, batched over
+ * chains): descs[c] describes chain c (N, d, caps, chain index); p, q, seed
+ * and precision must agree, use_graph / autotune / workspace_budget are read
+ * from descs[0].  tebd_step_even/odd then update the bonds of that parity of
+ * every chain in one launch sequence (in waves when a workspace budget is
+ * set); the per-chain calls (state, gates, expect, lambda, weights, MPS)
+ * act on the chain chosen by tebd_select_chain (default 0).
+ * Errors: TEBD_EINVAL (n_chains < 1, inconsistent p/q/seed/precision, as
+ * tebd_create_ex), TEBD_ENOMEM, TEBD_ECUDA. */
+int tebd_create_multi(int n_chains, const tebd_desc_t* descs, tebd_t* out);
+int tebd_num_chains(tebd_t h, int* out);
+int tebd_select_chain(tebd_t h, int chain);
+
+/* Device bytes held by the handle and the number of waves per parity. */
+int tebd_workspace_info(tebd_t h, size_t* arena_bytes, int* waves_even, int* waves_odd);
+
 /* Frees all device and host memory of the handle (NULL is accepted). */
 int tebd_destroy(tebd_t h);
 
 /* Device work of later calls goes to `cuda_stream` (a cudaStream_t). */
 int tebd_set_stream(tebd_t h, void* cuda_stream);
 
-/* Product state: psi is N blocks of d_s complex amplitudes (host), each
- * normalised by the library.  Resets bond dimensions to 1 and the sweep
- * counter and discarded-weight accumulators to 0.
+/* Product state of the selected chain: psi is N blocks of d_s complex
+ * amplitudes (host), each normalised by the library.  Resets the chain's bond
+ * dimensions to 1 and its discarded-weight accumulators, and the handle's
+ * sweep counter, to 0.
  * Errors: TEBD_EINVAL (NULL), TEBD_ENUMERIC (a zero or non-finite block). */
 int tebd_set_product_state(tebd_t h, const double* psi);
 

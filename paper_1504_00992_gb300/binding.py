@@ -40,7 +40,8 @@ class TebdDesc(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int), ("d", ctypes.c_int), ("d_site", ctypes.POINTER(ctypes.c_int)),
                 ("chi_max", ctypes.c_int), ("chi_bond", ctypes.POINTER(ctypes.c_int)),
                 ("p", ctypes.c_int), ("q", ctypes.c_int), ("seed", ctypes.c_uint64),
-                ("precision", ctypes.c_int), ("sv_cutoff", ctypes.c_double), ("chain", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("sv_cutoff", ctypes.c_double), ("chain", ctypes.c_int),
+                ("use_graph", ctypes.c_int), ("autotune", ctypes.c_int), ("workspace_budget", ctypes.c_size_t)]
 
 
 _LIB = None
@@ -54,6 +55,10 @@ _pi = ctypes.POINTER(ctypes.c_int)
 _SIGS = {
     "tebd_create": (_i, [_i, _i, _i, _i, _i, _u64, ctypes.POINTER(_vp)]),
     "tebd_create_ex": (_i, [ctypes.POINTER(TebdDesc), ctypes.POINTER(_vp)]),
+    "tebd_create_multi": (_i, [_i, ctypes.POINTER(TebdDesc), ctypes.POINTER(_vp)]),
+    "tebd_num_chains": (_i, [_vp, _pi]),
+    "tebd_select_chain": (_i, [_vp, _i]),
+    "tebd_workspace_info": (_i, [_vp, ctypes.POINTER(ctypes.c_size_t), _pi, _pi]),
     "tebd_destroy": (_i, [_vp]),
     "tebd_set_stream": (_i, [_vp, _vp]),
     "tebd_set_product_state": (_i, [_vp, _pd]),
@@ -131,15 +136,59 @@ def tebd_create(N, d, chi_max, p, q, seed):
     return h
 
 
-def tebd_create_ex(N, d_site, chi_bond, p, q, seed, precision=TEBD_PREC_FP64, sv_cutoff=0.0, chain=0):
+_KEEP = []
+
+
+def _desc(N, d_site, chi_bond, p, q, seed, precision=TEBD_PREC_FP64, sv_cutoff=0.0, chain=0, use_graph=0,
+          autotune=0, workspace_budget=0):
     ds = (ctypes.c_int * N)(*[int(x) for x in d_site])
     cb = (ctypes.c_int * (N - 1))(*[int(x) for x in chi_bond])
-    desc = TebdDesc(N, int(d_site[0]), ds, int(max(chi_bond)), cb, p, q, seed, precision, sv_cutoff, chain)
+    _KEEP.append((ds, cb))
+    return TebdDesc(N, int(d_site[0]), ds, int(max(chi_bond)), cb, p, q, seed, precision, sv_cutoff, chain,
+                    use_graph, autotune, workspace_budget)
+
+
+def tebd_create_ex(N, d_site, chi_bond, p, q, seed, precision=TEBD_PREC_FP64, sv_cutoff=0.0, chain=0, use_graph=0,
+                   autotune=0, workspace_budget=0):
+    desc = _desc(N, d_site, chi_bond, p, q, seed, precision, sv_cutoff, chain, use_graph, autotune,
+                 workspace_budget)
     h = _vp()
     rc = load().tebd_create_ex(ctypes.byref(desc), ctypes.byref(h))
+    _KEEP.clear()
     if rc != TEBD_OK:
         raise TebdError(rc, "tebd_create_ex")
     return h
+
+
+def tebd_create_multi(chains, p, q, seed, precision=TEBD_PREC_FP64, sv_cutoff=0.0, chain=0, use_graph=0,
+                      autotune=0, workspace_budget=0):
+    """chains: list of (N, d_site list, chi_bond list)."""
+    arr = (TebdDesc * len(chains))()
+    for c, (N, d_site, chi_bond) in enumerate(chains):
+        arr[c] = _desc(N, d_site, chi_bond, p, q, seed, precision, sv_cutoff, chain, use_graph, autotune,
+                       workspace_budget)
+    h = _vp()
+    rc = load().tebd_create_multi(len(chains), arr, ctypes.byref(h))
+    _KEEP.clear()
+    if rc != TEBD_OK:
+        raise TebdError(rc, "tebd_create_multi")
+    return h
+
+
+def tebd_num_chains(h):
+    n = ctypes.c_int()
+    _check(h, load().tebd_num_chains(h, ctypes.byref(n)))
+    return n.value
+
+
+def tebd_select_chain(h, chain):
+    _check(h, load().tebd_select_chain(h, chain))
+
+
+def tebd_workspace_info(h):
+    b, we, wo = ctypes.c_size_t(), ctypes.c_int(), ctypes.c_int()
+    _check(h, load().tebd_workspace_info(h, ctypes.byref(b), ctypes.byref(we), ctypes.byref(wo)))
+    return b.value, we.value, wo.value
 
 
 def tebd_destroy(h):
@@ -327,14 +376,16 @@ class Tebd:
     """Owning wrapper of a tebd_t handle (the calls above, bound to one chain)."""
 
     def __init__(self, N, d, chi_max, p, q, seed=0, d_site=None, chi_bond=None, sv_cutoff=0.0, chain=0,
-                 stream=None):
+                 stream=None, use_graph=0, autotune=0):
         self.N = N
         self.dims = list(d_site) if d_site is not None else [d] * N
         self.chi_bond = list(chi_bond) if chi_bond is not None else [chi_max] * (N - 1)
-        if d_site is None and chi_bond is None and sv_cutoff == 0.0 and chain == 0:
+        if d_site is None and chi_bond is None and sv_cutoff == 0.0 and chain == 0 and not use_graph \
+                and not autotune:
             self.h = tebd_create(N, d, chi_max, p, q, seed)
         else:
-            self.h = tebd_create_ex(N, self.dims, self.chi_bond, p, q, seed, TEBD_PREC_FP64, sv_cutoff, chain)
+            self.h = tebd_create_ex(N, self.dims, self.chi_bond, p, q, seed, TEBD_PREC_FP64, sv_cutoff, chain,
+                                    use_graph, autotune)
         caps = []
         for b in range(N - 1):
             left = int(np.prod([float(x) for x in self.dims[: b + 1]]))
@@ -384,3 +435,68 @@ class Tebd:
 
     def sweeps(self):
         return tebd_sweep_count(self.h)
+
+
+def _caps(dims, chi_bond):
+    caps = []
+    N = len(dims)
+    for b in range(N - 1):
+        left = float(np.prod([float(x) for x in dims[: b + 1]]))
+        right = float(np.prod([float(x) for x in dims[b + 1:]]))
+        caps.append(int(min(chi_bond[b], left, right)))
+    return caps
+
+
+class MultiTebd:
+    """Many chains in one handle; per-chain calls take the chain index."""
+
+    def __init__(self, chains, p, q, seed=0, use_graph=0, autotune=0, workspace_budget=0, stream=None):
+        self.chains = [(N, list(ds), list(cb)) for N, ds, cb in chains]
+        self.h = tebd_create_multi(self.chains, p, q, seed, use_graph=use_graph, autotune=autotune,
+                                   workspace_budget=workspace_budget)
+        self.caps = [_caps(ds, cb) for _, ds, cb in self.chains]
+        if stream is not None:
+            tebd_set_stream(self.h, stream)
+
+    def close(self):
+        if self.h:
+            tebd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _sel(self, c):
+        tebd_select_chain(self.h, c)
+
+    def set_product_state(self, c, psis):
+        self._sel(c)
+        tebd_set_product_state(self.h, psis)
+
+    def set_gates(self, c, parity, gates):
+        self._sel(c)
+        tebd_set_gates(self.h, parity, gates)
+
+    def step_even(self):
+        tebd_step_even(self.h)
+
+    def step_odd(self):
+        tebd_step_odd(self.h)
+
+    def expect(self, c, site, op):
+        self._sel(c)
+        return tebd_expect(self.h, site, op)
+
+    def get_lambda(self, c, bond):
+        self._sel(c)
+        return tebd_get_lambda(self.h, bond, self.caps[c][bond])
+
+    def discarded_weight(self, c):
+        self._sel(c)
+        return tebd_discarded_weight(self.h)
+
+    def workspace_info(self):
+        return tebd_workspace_info(self.h)

@@ -7,6 +7,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -99,47 +101,62 @@ bool all_finite(const double* x, size_t n) {
 }  // namespace
 
 // ===========================================================================
-// TEBD handle
+// TEBD handle: one or many chains, all bonds of a parity updated together
 // ===========================================================================
+struct ChainH {
+  int N = 0;
+  int64_t chain_index = 0;  // Philox chain word
+  std::vector<int> d, chi_cap, cap_ext;
+  std::vector<size_t> gamma_off, lam_off, gate_off;
+  size_t gamma_lo = 0, gamma_hi = 0;  // the chain's Gamma block in the arena
+  size_t tab_off = 0, int_off = 0;
+  std::vector<cplx*> gamma_ptr;       // N
+  std::vector<double*> lam_ptr;       // N+1, outer ones -> the constant 1.0
+  int* chi_ext = nullptr;             // device, N+1
+  int* dsite_dev = nullptr;
+  int* cap_ext_dev = nullptr;
+  cplx** gamma_tab = nullptr;
+  double** lam_tab = nullptr;
+  bool gates_set[2] = {false, false};
+  ChainDev dev{};
+};
+
+struct Wave {
+  int first = 0, count = 0;
+  Caps cap{};
+  int tiles[6] = {0, 0, 0, 0, 0, 0};
+};
+
 struct ParitySet {
   int batch = 0;
   Dims* dims = nullptr;     // device
   ProbPtr* ptrs = nullptr;  // device
-  Caps cap{};
-  std::vector<int> bonds;
+  std::vector<std::pair<int, int>> bonds;  // (chain slot, bond)
+  std::vector<Wave> waves;
 };
 
 struct tebd_s {
   ErrState err;
-  int N = 0, p = 0, q = 0, precision = 0;
+  int p = 0, q = 0, precision = 0;
   uint64_t seed = 0;
   double cutoff = 1e-14;
-  int64_t chain = 0;
   int64_t sweeps = 0;
   cudaStream_t stream = 0;
-  bool gates_set[2] = {false, false};
-  std::vector<int> d, chi_cap, cap_ext;
-  std::vector<size_t> gamma_off, lam_off, gate_off;
-  size_t gamma_bytes = 0;
+  std::vector<ChainH> ch;
+  int cur = 0;
   char* arena = nullptr;
   size_t arena_bytes = 0;
-  // device views
-  cplx** gamma_tab = nullptr;
-  double** lam_tab = nullptr;
-  int* chi_ext = nullptr;
-  int* chi_cap_dev = nullptr;
-  int* dsite_dev = nullptr;
-  int* cap_ext_dev = nullptr;
+  ParitySet par[2];
   int* status = nullptr;
-  double* wacc = nullptr;  // [0] sum w, [1] prod(1-w), [2..] per-sweep w
-  cplx* gates = nullptr;
+  double* wacc = nullptr;   // 2 per chain: sum w, prod (1 - w)
+  double* wout = nullptr;   // per problem of the larger parity
+  uint64_t* sweep_dev = nullptr;
   cplx* op_dev = nullptr;
   cplx* out_dev = nullptr;
-  std::vector<cplx*> gamma_ptr;
-  std::vector<double*> lam_ptr;  // N+1 (outer ones -> one_lam)
   double* one_lam = nullptr;
-  ParitySet par[2];
-  ChainDev ch{};
+  bool use_graph = false;
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  cudaStream_t own_stream = nullptr;  // used for graphs when the caller gives the legacy stream 0
 };
 
 static int tebd_check_status(tebd_t h) {
@@ -150,97 +167,206 @@ static int tebd_check_status(tebd_t h) {
   return h->err.code;
 }
 
-extern "C" int tebd_create_ex(const tebd_desc_t* desc, tebd_t* out) {
+static void tebd_free(tebd_s* h) {
+  for (int i = 0; i < 2; ++i)
+    if (h->gexec[i]) cudaGraphExecDestroy(h->gexec[i]);
+  if (h->arena) cudaFree(h->arena);
+  if (h->own_stream) cudaStreamDestroy(h->own_stream);
+  delete h;
+}
+
+// GEMM tile autotuner: times the 16x16 and 32x32 variants of every GEMM stage
+// on the wave's capacity sizes (the saturated regime) and keeps the faster.
+// Results are cached per (stage, rows, cols, inner, batch) for the process.
+static std::map<std::vector<long long>, int> g_tile_cache;
+static std::mutex g_tile_mu;
+
+static int tune_wave(const ParitySet& ps, Wave& w, cudaStream_t st, Dims* scratch_dims, const int p_os) {
+  // capacity-sized descriptors of the wave's problems
+  std::vector<Dims> hd(w.count);
+  std::vector<ProbPtr> hp(w.count);
+  if (cudaMemcpy(hp.data(), ps.ptrs + w.first, sizeof(ProbPtr) * w.count, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return -1;
+  for (int i = 0; i < w.count; ++i) {
+    Dims& D = hd[i];
+    memset(&D, 0, sizeof D);
+    D.dl = hp[i].dl_s; D.dr = hp[i].dr_s;
+    D.cl = hp[i].cap_l; D.cm = hp[i].cap_m; D.cr = hp[i].cap_r;
+    D.m = D.dl * D.cl; D.n = D.dr * D.cr;
+    D.k = std::min(hp[i].chicap, std::min(D.m, D.n));
+    D.l = std::min(D.k + p_os, std::min(D.m, D.n));
+    D.active = 1;
+  }
+  if (cudaMemcpy(scratch_dims, hd.data(), sizeof(Dims) * w.count, cudaMemcpyHostToDevice) != cudaSuccess) return -1;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int inner[6] = {w.cap.n, w.cap.m, w.cap.n, w.cap.m, w.cap.l, w.cap.l};
+  for (int stage = 0; stage < 6; ++stage) {
+    std::vector<long long> key = {stage, w.cap.m, w.cap.n, w.cap.l, w.cap.k, inner[stage], w.count};
+    {
+      std::lock_guard<std::mutex> g(g_tile_mu);
+      auto it = g_tile_cache.find(key);
+      if (it != g_tile_cache.end()) { w.tiles[stage] = it->second; continue; }
+    }
+    float best = 1e30f;
+    int pick = 0;
+    for (int tile : {16, 32}) {
+      launch_zgemm_tile(stage, tile, scratch_dims, ps.ptrs + w.first, w.count, w.cap, st);  // warm-up
+      cudaEventRecord(e0, st);
+      for (int r = 0; r < 2; ++r) launch_zgemm_tile(stage, tile, scratch_dims, ps.ptrs + w.first, w.count, w.cap, st);
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) { best = ms; pick = tile; }
+    }
+    w.tiles[stage] = pick;
+    std::lock_guard<std::mutex> g(g_tile_mu);
+    g_tile_cache[key] = pick;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+static int tebd_reset_state(tebd_t h, int slot, const double* psi);
+
+extern "C" int tebd_create_multi(int n_chains, const tebd_desc_t* descs, tebd_t* out) {
   if (!out) return TEBD_EINVAL;
   *out = nullptr;
-  if (!desc) return TEBD_EINVAL;
-  const int N = desc->N;
-  if (N < 2 || desc->p < 0 || desc->q < 0) return TEBD_EINVAL;
-  if (desc->precision != TEBD_PREC_FP64) return TEBD_ENOTIMPL;
+  if (n_chains < 1 || !descs) return TEBD_EINVAL;
+  const tebd_desc_t& d0 = descs[0];
+  if (d0.p < 0 || d0.q < 0) return TEBD_EINVAL;
+  if (d0.precision != TEBD_PREC_FP64) return TEBD_ENOTIMPL;
+  for (int c = 0; c < n_chains; ++c) {
+    const tebd_desc_t& dc = descs[c];
+    if (dc.N < 2 || dc.p != d0.p || dc.q != d0.q || dc.seed != d0.seed || dc.precision != d0.precision)
+      return TEBD_EINVAL;
+  }
   tebd_s* h = new tebd_s();
-  h->N = N;
-  h->p = desc->p;
-  h->q = desc->q;
-  h->seed = desc->seed;
-  h->precision = desc->precision;
-  h->cutoff = desc->sv_cutoff > 0 ? desc->sv_cutoff : 1e-14;
-  h->chain = desc->chain;
-  h->d.resize(N);
-  for (int s = 0; s < N; ++s) {
-    const int ds = desc->d_site ? desc->d_site[s] : desc->d;
-    if (ds < 2 || ds > 64) { delete h; return TEBD_EINVAL; }
-    h->d[s] = ds;
+  h->p = d0.p;
+  h->q = d0.q;
+  h->seed = d0.seed;
+  h->precision = d0.precision;
+  h->cutoff = d0.sv_cutoff > 0 ? d0.sv_cutoff : 1e-14;
+  h->use_graph = d0.use_graph != 0;
+  if (h->use_graph) {
+    // the legacy default stream cannot be captured: run on a blocking stream
+    // of our own (it still orders with stream 0)
+    if (cudaStreamCreate(&h->own_stream) != cudaSuccess) { cudaGetLastError(); delete h; return TEBD_ECUDA; }
+    h->stream = h->own_stream;
   }
-  h->chi_cap.resize(N - 1);
-  for (int b = 0; b < N - 1; ++b) {
-    const int c = desc->chi_bond ? desc->chi_bond[b] : desc->chi_max;
-    if (c < 1) { delete h; return TEBD_EINVAL; }
-    h->chi_cap[b] = c;
-  }
-  // capacities: chi_b <= min(cap_b, prod_{s<=b} d_s, prod_{s>b} d_s)
-  h->cap_ext.assign(N + 1, 1);
-  for (int b = 0; b < N - 1; ++b) {
-    double left = 1, right = 1;
-    for (int s = 0; s <= b; ++s) left = std::min(left * h->d[s], 1e9);
-    for (int s = b + 1; s < N; ++s) right = std::min(right * h->d[s], 1e9);
-    h->cap_ext[b + 1] = (int)std::min<double>(h->chi_cap[b], std::min(left, right));
-  }
-  // --- sizes of every device buffer
+  h->ch.resize(n_chains);
   size_t off = 0;
-  h->gamma_off.resize(N);
-  for (int s = 0; s < N; ++s) {
-    h->gamma_off[s] = off;
-    off += align_up(sizeof(cplx) * (size_t)h->d[s] * h->cap_ext[s] * h->cap_ext[s + 1]);
-  }
-  h->gamma_bytes = off;
-  h->lam_off.resize(N - 1);
-  for (int b = 0; b < N - 1; ++b) {
-    h->lam_off[b] = off;
-    off += align_up(sizeof(double) * h->cap_ext[b + 1]);
+  for (int c = 0; c < n_chains; ++c) {
+    const tebd_desc_t& dc = descs[c];
+    ChainH& C = h->ch[c];
+    const int N = dc.N;
+    C.N = N;
+    C.chain_index = (n_chains == 1) ? dc.chain : (int64_t)dc.chain + c;
+    C.d.resize(N);
+    for (int s = 0; s < N; ++s) {
+      const int ds = dc.d_site ? dc.d_site[s] : dc.d;
+      if (ds < 2 || ds > 64) { delete h; return TEBD_EINVAL; }
+      C.d[s] = ds;
+    }
+    C.chi_cap.resize(N - 1);
+    for (int b = 0; b < N - 1; ++b) {
+      const int cc = dc.chi_bond ? dc.chi_bond[b] : dc.chi_max;
+      if (cc < 1) { delete h; return TEBD_EINVAL; }
+      C.chi_cap[b] = cc;
+    }
+    // chi_b <= min(cap_b, prod_{s<=b} d_s, prod_{s>b} d_s)
+    C.cap_ext.assign(N + 1, 1);
+    for (int b = 0; b < N - 1; ++b) {
+      double left = 1, right = 1;
+      for (int s = 0; s <= b; ++s) left = std::min(left * C.d[s], 1e9);
+      for (int s = b + 1; s < N; ++s) right = std::min(right * C.d[s], 1e9);
+      C.cap_ext[b + 1] = (int)std::min<double>(C.chi_cap[b], std::min(left, right));
+    }
+    C.gamma_off.resize(N);
+    C.gamma_lo = off;
+    for (int s = 0; s < N; ++s) {
+      C.gamma_off[s] = off;
+      off += align_up(sizeof(cplx) * (size_t)C.d[s] * C.cap_ext[s] * C.cap_ext[s + 1]);
+    }
+    C.gamma_hi = off;
+    C.lam_off.resize(N - 1);
+    for (int b = 0; b < N - 1; ++b) {
+      C.lam_off[b] = off;
+      off += align_up(sizeof(double) * C.cap_ext[b + 1]);
+    }
+    C.gate_off.resize(N - 1);
+    for (int b = 0; b < N - 1; ++b) {
+      C.gate_off[b] = off;
+      const size_t dd = (size_t)C.d[b] * C.d[b + 1];
+      off += align_up(sizeof(cplx) * dd * dd);
+    }
+    C.tab_off = off;
+    off += align_up(sizeof(cplx*) * N) + align_up(sizeof(double*) * (N + 1));
+    C.int_off = off;
+    off += 3 * align_up(sizeof(int) * (N + 1));
   }
   const size_t one_off = off; off += ALIGN;
-  h->gate_off.resize(N - 1);
-  for (int b = 0; b < N - 1; ++b) {
-    h->gate_off[b] = off;
-    const size_t dd = (size_t)h->d[b] * h->d[b + 1];
-    off += align_up(sizeof(cplx) * dd * dd);
-  }
-  const size_t tab_off = off;
-  off += align_up(sizeof(cplx*) * N) + align_up(sizeof(double*) * (N + 1));
-  const size_t int_off = off;
-  off += 4 * align_up(sizeof(int) * (N + 1));
   const size_t st_off = off; off += ALIGN;
-  const size_t wacc_off = off; off += align_up(sizeof(double) * (2 + N));
+  const size_t wacc_off = off; off += align_up(sizeof(double) * 2 * n_chains);
+  const size_t sweep_off = off; off += ALIGN;
   const size_t op_off = off; off += align_up(sizeof(cplx) * 64 * 64) + ALIGN;
-  // per-parity problem descriptors and shared workspace
+  // problems of each parity, chain-major, and their waves under the budget
+  const size_t budget = d0.workspace_budget;
   size_t ws_max = 0;
   std::vector<WsLayout> lay[2];
+  std::vector<size_t> pbytes[2];
+  int max_batch = 0;
   for (int par = 0; par < 2; ++par) {
     ParitySet& ps = h->par[par];
-    Caps c{};
-    for (int b = par; b < N - 1; b += 2) {
-      const int mc = h->d[b] * h->cap_ext[b], nc = h->d[b + 1] * h->cap_ext[b + 2];
-      const int kc = std::min(h->cap_ext[b + 1], std::min(mc, nc));
-      const int lc = std::min(kc + h->p, std::min(mc, nc));
-      if (lc > 512) { delete h; return TEBD_ENOTIMPL; }
-      ps.bonds.push_back(b);
-      lay[par].push_back(ws_layout(mc, nc, kc, lc, true, true));
-      c.m = std::max(c.m, mc); c.n = std::max(c.n, nc); c.k = std::max(c.k, kc); c.l = std::max(c.l, lc);
-      c.cl = std::max(c.cl, h->cap_ext[b]); c.cr = std::max(c.cr, h->cap_ext[b + 2]);
-      c.dl = std::max(c.dl, h->d[b]); c.dr = std::max(c.dr, h->d[b + 1]);
+    for (int c = 0; c < n_chains; ++c) {
+      const ChainH& C = h->ch[c];
+      for (int b = par; b < C.N - 1; b += 2) {
+        const int mc = C.d[b] * C.cap_ext[b], nc = C.d[b + 1] * C.cap_ext[b + 2];
+        const int kc = std::min(C.cap_ext[b + 1], std::min(mc, nc));
+        const int lc = std::min(kc + h->p, std::min(mc, nc));
+        if (lc > 512) { delete h; return TEBD_ENOTIMPL; }
+        ps.bonds.push_back({c, b});
+        lay[par].push_back(ws_layout(mc, nc, kc, lc, true, true));
+        pbytes[par].push_back(align_up(sizeof(cplx) * (size_t)mc * nc) + lay[par].back().total);
+      }
     }
     ps.batch = (int)ps.bonds.size();
-    ps.cap = c;
-    size_t tot = 0;
-    for (size_t i = 0; i < ps.bonds.size(); ++i) {
-      const int b = ps.bonds[i];
-      tot += align_up(sizeof(cplx) * (size_t)h->d[b] * h->cap_ext[b] * h->d[b + 1] * h->cap_ext[b + 2]);
-      tot += lay[par][i].total;
+    max_batch = std::max(max_batch, ps.batch);
+    size_t acc = 0;
+    Wave w;
+    w.first = 0;
+    for (int i = 0; i < ps.batch; ++i) {
+      if (w.count > 0 && budget > 0 && acc + pbytes[par][i] > budget) {
+        ps.waves.push_back(w);
+        ws_max = std::max(ws_max, acc);
+        w = Wave();
+        w.first = i;
+        acc = 0;
+      }
+      const int c = ps.bonds[i].first, b = ps.bonds[i].second;
+      const ChainH& C = h->ch[c];
+      const int mc = C.d[b] * C.cap_ext[b], nc = C.d[b + 1] * C.cap_ext[b + 2];
+      const int kc = std::min(C.cap_ext[b + 1], std::min(mc, nc));
+      const int lc = std::min(kc + h->p, std::min(mc, nc));
+      Caps& cp = w.cap;
+      cp.m = std::max(cp.m, mc); cp.n = std::max(cp.n, nc); cp.k = std::max(cp.k, kc); cp.l = std::max(cp.l, lc);
+      cp.cl = std::max(cp.cl, C.cap_ext[b]); cp.cr = std::max(cp.cr, C.cap_ext[b + 2]);
+      cp.dl = std::max(cp.dl, C.d[b]); cp.dr = std::max(cp.dr, C.d[b + 1]);
+      acc += pbytes[par][i];
+      w.count++;
     }
-    ws_max = std::max(ws_max, tot);
+    if (w.count > 0) {
+      ps.waves.push_back(w);
+      ws_max = std::max(ws_max, acc);
+    }
   }
+  const size_t wout_off = off; off += align_up(sizeof(double) * std::max(1, max_batch));
   const size_t desc_off = off;
-  off += 2 * (align_up(sizeof(Dims) * N) + align_up(sizeof(ProbPtr) * N));
+  const size_t desc_per = align_up(sizeof(Dims) * std::max(1, max_batch)) + align_up(sizeof(ProbPtr) * std::max(1, max_batch));
+  off += 2 * desc_per + align_up(sizeof(Dims) * std::max(1, max_batch));  // + autotuner scratch dims
   const size_t ws_off = off;
   off += ws_max;
   h->arena_bytes = off;
@@ -250,95 +376,107 @@ extern "C" int tebd_create_ex(const tebd_desc_t* desc, tebd_t* out) {
     return TEBD_ENOMEM;
   }
   char* A = h->arena;
-  h->gamma_ptr.resize(N);
-  for (int s = 0; s < N; ++s) h->gamma_ptr[s] = (cplx*)(A + h->gamma_off[s]);
+  if (cudaMemset(A, 0, h->arena_bytes - ws_max) != cudaSuccess) { tebd_free(h); return TEBD_ECUDA; }
   h->one_lam = (double*)(A + one_off);
-  h->lam_ptr.resize(N + 1);
-  h->lam_ptr[0] = h->one_lam;
-  h->lam_ptr[N] = h->one_lam;
-  for (int b = 0; b < N - 1; ++b) h->lam_ptr[b + 1] = (double*)(A + h->lam_off[b]);
-  h->gates = (cplx*)(A + h->gate_off[0]);
-  h->gamma_tab = (cplx**)(A + tab_off);
-  h->lam_tab = (double**)(A + tab_off + align_up(sizeof(cplx*) * N));
-  h->chi_ext = (int*)(A + int_off);
-  h->chi_cap_dev = (int*)(A + int_off + align_up(sizeof(int) * (N + 1)));
-  h->dsite_dev = (int*)(A + int_off + 2 * align_up(sizeof(int) * (N + 1)));
-  h->cap_ext_dev = (int*)(A + int_off + 3 * align_up(sizeof(int) * (N + 1)));
   h->status = (int*)(A + st_off);
   h->wacc = (double*)(A + wacc_off);
+  h->sweep_dev = (uint64_t*)(A + sweep_off);
   h->op_dev = (cplx*)(A + op_off);
   h->out_dev = (cplx*)(A + op_off + align_up(sizeof(cplx) * 64 * 64));
-  char* ws = A + ws_off;
-  for (int par = 0; par < 2; ++par) {
-    ParitySet& ps = h->par[par];
-    ps.dims = (Dims*)(A + desc_off + par * (align_up(sizeof(Dims) * N) + align_up(sizeof(ProbPtr) * N)));
-    ps.ptrs = (ProbPtr*)((char*)ps.dims + align_up(sizeof(Dims) * N));
-    std::vector<ProbPtr> hp(ps.batch);
-    size_t o = 0;
-    for (int i = 0; i < ps.batch; ++i) {
-      const int b = ps.bonds[i];
-      ProbPtr& P = hp[i];
-      memset(&P, 0, sizeof P);
-      P.gl = h->gamma_ptr[b];
-      P.gr = h->gamma_ptr[b + 1];
-      P.laml = h->lam_ptr[b];
-      P.lamm = h->lam_ptr[b + 1];
-      P.lamr = h->lam_ptr[b + 2];
-      P.gate = (const cplx*)(A + h->gate_off[b]);
-      P.cap_l = h->cap_ext[b];
-      P.cap_m = h->cap_ext[b + 1];
-      P.cap_r = h->cap_ext[b + 2];
-      P.theta = (const cplx*)(ws + o);
-      o += align_up(sizeof(cplx) * (size_t)h->d[b] * h->cap_ext[b] * h->d[b + 1] * h->cap_ext[b + 2]);
-      fill_ptrs(P, ws + o, lay[par][i]);
-      o += lay[par][i].total;
-    }
-    if (ps.batch > 0 &&
-        cudaMemcpy(ps.ptrs, hp.data(), sizeof(ProbPtr) * ps.batch, cudaMemcpyHostToDevice) != cudaSuccess) {
-      cudaFree(h->arena);
-      delete h;
-      return TEBD_ECUDA;
-    }
+  h->wout = (double*)(A + wout_off);
+  bool ok = true;
+  for (int c = 0; c < n_chains && ok; ++c) {
+    ChainH& C = h->ch[c];
+    const int N = C.N;
+    C.gamma_ptr.resize(N);
+    for (int s = 0; s < N; ++s) C.gamma_ptr[s] = (cplx*)(A + C.gamma_off[s]);
+    C.lam_ptr.resize(N + 1);
+    C.lam_ptr[0] = h->one_lam;
+    C.lam_ptr[N] = h->one_lam;
+    for (int b = 0; b < N - 1; ++b) C.lam_ptr[b + 1] = (double*)(A + C.lam_off[b]);
+    C.gamma_tab = (cplx**)(A + C.tab_off);
+    C.lam_tab = (double**)(A + C.tab_off + align_up(sizeof(cplx*) * N));
+    C.chi_ext = (int*)(A + C.int_off);
+    C.dsite_dev = (int*)(A + C.int_off + align_up(sizeof(int) * (N + 1)));
+    C.cap_ext_dev = (int*)(A + C.int_off + 2 * align_up(sizeof(int) * (N + 1)));
+    ok = cudaMemcpy(C.gamma_tab, C.gamma_ptr.data(), sizeof(cplx*) * N, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(C.lam_tab, C.lam_ptr.data(), sizeof(double*) * (N + 1), cudaMemcpyHostToDevice) ==
+             cudaSuccess &&
+         cudaMemcpy(C.dsite_dev, C.d.data(), sizeof(int) * N, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(C.cap_ext_dev, C.cap_ext.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice) == cudaSuccess;
+    C.dev.N = N;
+    C.dev.chi_ext = C.chi_ext;
+    C.dev.dsite = C.dsite_dev;
+    C.dev.lam_ext = C.lam_tab;
+    C.dev.gamma = C.gamma_tab;
+    C.dev.cap_ext = C.cap_ext_dev;
   }
-  std::vector<int> dsite(h->d), capv(h->chi_cap);
   const double one = 1.0;
-  bool ok = cudaMemcpy(h->gamma_tab, h->gamma_ptr.data(), sizeof(cplx*) * N, cudaMemcpyHostToDevice) == cudaSuccess &&
-            cudaMemcpy(h->lam_tab, h->lam_ptr.data(), sizeof(double*) * (N + 1), cudaMemcpyHostToDevice) ==
-                cudaSuccess &&
-            cudaMemcpy(h->dsite_dev, dsite.data(), sizeof(int) * N, cudaMemcpyHostToDevice) == cudaSuccess &&
-            cudaMemcpy(h->chi_cap_dev, capv.data(), sizeof(int) * (N - 1), cudaMemcpyHostToDevice) ==
-                cudaSuccess &&
-            cudaMemcpy(h->cap_ext_dev, h->cap_ext.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice) ==
-                cudaSuccess &&
-            cudaMemcpy(h->one_lam, &one, sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess;
-  if (!ok) {
-    cudaFree(h->arena);
-    delete h;
-    return TEBD_ECUDA;
+  ok = ok && cudaMemcpy(h->one_lam, &one, sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess;
+  char* ws = A + ws_off;
+  for (int par = 0; par < 2 && ok; ++par) {
+    ParitySet& ps = h->par[par];
+    ps.dims = (Dims*)(A + desc_off + par * desc_per);
+    ps.ptrs = (ProbPtr*)((char*)ps.dims + align_up(sizeof(Dims) * std::max(1, max_batch)));
+    std::vector<ProbPtr> hp(ps.batch);
+    for (const Wave& w : ps.waves) {
+      size_t o = 0;
+      for (int i = w.first; i < w.first + w.count; ++i) {
+        const int c = ps.bonds[i].first, b = ps.bonds[i].second;
+        ChainH& C = h->ch[c];
+        ProbPtr& P = hp[i];
+        memset(&P, 0, sizeof P);
+        P.gl = C.gamma_ptr[b];
+        P.gr = C.gamma_ptr[b + 1];
+        P.laml = C.lam_ptr[b];
+        P.lamm = C.lam_ptr[b + 1];
+        P.lamr = C.lam_ptr[b + 2];
+        P.gate = (const cplx*)(A + C.gate_off[b]);
+        P.cap_l = C.cap_ext[b];
+        P.cap_m = C.cap_ext[b + 1];
+        P.cap_r = C.cap_ext[b + 2];
+        P.chi_l = C.chi_ext + b;
+        P.chi_m = C.chi_ext + b + 1;
+        P.chi_r = C.chi_ext + b + 2;
+        P.dl_s = C.d[b];
+        P.dr_s = C.d[b + 1];
+        P.chicap = C.chi_cap[b];
+        P.bond_s = b;
+        P.chain_s = (int)C.chain_index;
+        P.slot = c;
+        P.theta = (const cplx*)(ws + o);
+        o += align_up(sizeof(cplx) * (size_t)C.d[b] * C.cap_ext[b] * C.d[b + 1] * C.cap_ext[b + 2]);
+        fill_ptrs(P, ws + o, lay[par][i]);
+        o += lay[par][i].total;
+      }
+    }
+    if (ps.batch > 0)
+      ok = cudaMemcpy(ps.ptrs, hp.data(), sizeof(ProbPtr) * ps.batch, cudaMemcpyHostToDevice) == cudaSuccess;
   }
-  h->ch.N = N;
-  h->ch.chi_ext = h->chi_ext;
-  h->ch.chi_cap = h->chi_cap_dev;
-  h->ch.dsite = h->dsite_dev;
-  h->ch.lam_ext = h->lam_tab;
-  h->ch.gamma = h->gamma_tab;
-  h->ch.cap_ext = h->cap_ext_dev;
-  // |0...0>
-  std::vector<double> psi;
-  for (int s = 0; s < N; ++s) {
-    psi.push_back(1.0);
-    psi.push_back(0.0);
-    for (int i = 1; i < h->d[s]; ++i) { psi.push_back(0.0); psi.push_back(0.0); }
+  if (!ok) { tebd_free(h); return TEBD_ECUDA; }
+  // every chain starts in |0...0>
+  for (int c = 0; c < n_chains; ++c) {
+    std::vector<double> psi;
+    for (int s = 0; s < h->ch[c].N; ++s) {
+      psi.push_back(1.0);
+      psi.push_back(0.0);
+      for (int i = 1; i < h->ch[c].d[s]; ++i) { psi.push_back(0.0); psi.push_back(0.0); }
+    }
+    const int rc = tebd_reset_state(h, c, psi.data());
+    if (rc != TEBD_OK) { tebd_free(h); return rc; }
   }
-  int rc = tebd_set_product_state(h, psi.data());
-  if (rc != TEBD_OK) {
-    cudaFree(h->arena);
-    delete h;
-    return rc;
+  if (d0.autotune) {
+    Dims* scratch = (Dims*)(A + desc_off + 2 * desc_per);
+    for (int par = 0; par < 2; ++par)
+      for (Wave& w : h->par[par].waves)
+        if (tune_wave(h->par[par], w, h->stream, scratch, h->p) != 0) { tebd_free(h); return TEBD_ECUDA; }
+    if (cudaDeviceSynchronize() != cudaSuccess) { tebd_free(h); return TEBD_ECUDA; }
   }
   *out = h;
   return TEBD_OK;
 }
+
+extern "C" int tebd_create_ex(const tebd_desc_t* desc, tebd_t* out) { return tebd_create_multi(1, desc, out); }
 
 extern "C" int tebd_create(int N, int d, int chi_max, int p, int q, uint64_t seed, tebd_t* out) {
   tebd_desc_t desc;
@@ -355,26 +493,40 @@ extern "C" int tebd_create(int N, int d, int chi_max, int p, int q, uint64_t see
 
 extern "C" int tebd_destroy(tebd_t h) {
   if (!h) return TEBD_OK;
-  if (h->arena) cudaFree(h->arena);
-  delete h;
+  tebd_free(h);
   return TEBD_OK;
 }
 
 extern "C" int tebd_set_stream(tebd_t h, void* s) {
   if (!h) return TEBD_EINVAL;
+  if (!s && h->own_stream) s = h->own_stream;
+  if ((cudaStream_t)s != h->stream)
+    for (int i = 0; i < 2; ++i)
+      if (h->gexec[i]) { cudaGraphExecDestroy(h->gexec[i]); h->gexec[i] = nullptr; }
   h->stream = (cudaStream_t)s;
   return TEBD_OK;
 }
 
-extern "C" int tebd_set_product_state(tebd_t h, const double* psi) {
+extern "C" int tebd_num_chains(tebd_t h, int* out) {
+  if (!h || !out) return TEBD_EINVAL;
+  *out = (int)h->ch.size();
+  return TEBD_OK;
+}
+
+extern "C" int tebd_select_chain(tebd_t h, int chain) {
   if (!h) return TEBD_EINVAL;
-  if (h->err.code) return h->err.code;
-  if (!psi) { h->err.set(TEBD_EINVAL, "psi is NULL"); return h->err.code; }
-  const int N = h->N;
-  std::vector<char> gam(h->gamma_bytes, 0);
+  if (chain < 0 || chain >= (int)h->ch.size()) { h->err.set(TEBD_EINVAL, "chain %d out of range", chain); return h->err.code; }
+  h->cur = chain;
+  return TEBD_OK;
+}
+
+static int tebd_reset_state(tebd_t h, int slot, const double* psi) {
+  ChainH& C = h->ch[slot];
+  const int N = C.N;
+  std::vector<char> gam(C.gamma_hi - C.gamma_lo, 0);
   size_t o = 0;
   for (int s = 0; s < N; ++s) {
-    const int ds = h->d[s];
+    const int ds = C.d[s];
     double nrm = 0.0;
     for (int i = 0; i < 2 * ds; ++i) nrm += psi[o + i] * psi[o + i];
     if (!(nrm > 0.0) || !isfinite(nrm)) {
@@ -382,82 +534,96 @@ extern "C" int tebd_set_product_state(tebd_t h, const double* psi) {
       return h->err.code;
     }
     nrm = 1.0 / sqrt(nrm);
-    cplx* g = (cplx*)(gam.data() + h->gamma_off[s]);
-    const size_t stride = (size_t)h->cap_ext[s] * h->cap_ext[s + 1];
+    cplx* g = (cplx*)(gam.data() + (C.gamma_off[s] - C.gamma_lo));
+    const size_t stride = (size_t)C.cap_ext[s] * C.cap_ext[s + 1];
     for (int i = 0; i < ds; ++i) g[i * stride] = cmk(psi[o + 2 * i] * nrm, psi[o + 2 * i + 1] * nrm);
     o += 2 * ds;
   }
-  CU_OR(h, cudaMemcpyAsync(h->arena, gam.data(), h->gamma_bytes, cudaMemcpyHostToDevice, h->stream));
+  CU_OR(h, cudaMemcpyAsync(h->arena + C.gamma_lo, gam.data(), gam.size(), cudaMemcpyHostToDevice, h->stream));
   for (int b = 0; b < N - 1; ++b) {
-    std::vector<double> lam(h->cap_ext[b + 1], 0.0);
+    std::vector<double> lam(C.cap_ext[b + 1], 0.0);
     lam[0] = 1.0;
-    CU_OR(h, cudaMemcpyAsync(h->lam_ptr[b + 1], lam.data(), sizeof(double) * lam.size(), cudaMemcpyHostToDevice,
+    CU_OR(h, cudaMemcpyAsync(C.lam_ptr[b + 1], lam.data(), sizeof(double) * lam.size(), cudaMemcpyHostToDevice,
                              h->stream));
   }
   std::vector<int> chi(N + 1, 1);
-  CU_OR(h, cudaMemcpyAsync(h->chi_ext, chi.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice, h->stream));
+  CU_OR(h, cudaMemcpyAsync(C.chi_ext, chi.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice, h->stream));
   const double w0[2] = {0.0, 1.0};
-  CU_OR(h, cudaMemcpyAsync(h->wacc, w0, sizeof w0, cudaMemcpyHostToDevice, h->stream));
+  CU_OR(h, cudaMemcpyAsync(h->wacc + 2 * slot, w0, sizeof w0, cudaMemcpyHostToDevice, h->stream));
   CU_OR(h, cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
+  CU_OR(h, cudaMemsetAsync(h->sweep_dev, 0, sizeof(uint64_t), h->stream));
   CU_OR(h, cudaStreamSynchronize(h->stream));
   h->sweeps = 0;
   return TEBD_OK;
+}
+
+extern "C" int tebd_set_product_state(tebd_t h, const double* psi) {
+  if (!h) return TEBD_EINVAL;
+  if (h->err.code) return h->err.code;
+  if (!psi) { h->err.set(TEBD_EINVAL, "psi is NULL"); return h->err.code; }
+  return tebd_reset_state(h, h->cur, psi);
 }
 
 extern "C" int tebd_set_mps(tebd_t h, const double* const* gamma, const double* const* lambda, const int* chi) {
   if (!h) return TEBD_EINVAL;
   if (h->err.code) return h->err.code;
   if (!gamma || !lambda || !chi) { h->err.set(TEBD_EINVAL, "NULL argument"); return h->err.code; }
-  const int N = h->N;
+  ChainH& C = h->ch[h->cur];
+  const int N = C.N;
   std::vector<int> ce(N + 1, 1);
   for (int b = 0; b < N - 1; ++b) {
-    if (chi[b] < 1 || chi[b] > h->cap_ext[b + 1]) {
-      h->err.set(TEBD_EINVAL, "bond %d: chi %d outside [1, %d]", b, chi[b], h->cap_ext[b + 1]);
+    if (chi[b] < 1 || chi[b] > C.cap_ext[b + 1]) {
+      h->err.set(TEBD_EINVAL, "bond %d: chi %d outside [1, %d]", b, chi[b], C.cap_ext[b + 1]);
       return h->err.code;
     }
     ce[b + 1] = chi[b];
   }
-  std::vector<char> gam(h->gamma_bytes, 0);
+  std::vector<char> gam(C.gamma_hi - C.gamma_lo, 0);
   for (int s = 0; s < N; ++s) {
     if (!gamma[s]) { h->err.set(TEBD_EINVAL, "gamma[%d] is NULL", s); return h->err.code; }
-    cplx* g = (cplx*)(gam.data() + h->gamma_off[s]);
-    const int cl = ce[s], cr = ce[s + 1], capl = h->cap_ext[s], capr = h->cap_ext[s + 1];
-    for (int i = 0; i < h->d[s]; ++i)
+    cplx* g = (cplx*)(gam.data() + (C.gamma_off[s] - C.gamma_lo));
+    const int cl = ce[s], cr = ce[s + 1], capl = C.cap_ext[s], capr = C.cap_ext[s + 1];
+    for (int i = 0; i < C.d[s]; ++i)
       for (int a = 0; a < cl; ++a)
         for (int c = 0; c < cr; ++c) {
           const size_t src = 2 * (((size_t)i * cl + a) * cr + c);
           g[((size_t)i * capl + a) * capr + c] = cmk(gamma[s][src], gamma[s][src + 1]);
         }
   }
-  CU_OR(h, cudaMemcpyAsync(h->arena, gam.data(), h->gamma_bytes, cudaMemcpyHostToDevice, h->stream));
+  CU_OR(h, cudaMemcpyAsync(h->arena + C.gamma_lo, gam.data(), gam.size(), cudaMemcpyHostToDevice, h->stream));
   for (int b = 0; b < N - 1; ++b) {
     if (!lambda[b]) { h->err.set(TEBD_EINVAL, "lambda[%d] is NULL", b); return h->err.code; }
-    std::vector<double> lam(h->cap_ext[b + 1], 0.0);
+    std::vector<double> lam(C.cap_ext[b + 1], 0.0);
     for (int i = 0; i < chi[b]; ++i) lam[i] = lambda[b][i];
-    CU_OR(h, cudaMemcpyAsync(h->lam_ptr[b + 1], lam.data(), sizeof(double) * lam.size(), cudaMemcpyHostToDevice,
+    CU_OR(h, cudaMemcpyAsync(C.lam_ptr[b + 1], lam.data(), sizeof(double) * lam.size(), cudaMemcpyHostToDevice,
                              h->stream));
   }
-  CU_OR(h, cudaMemcpyAsync(h->chi_ext, ce.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice, h->stream));
+  CU_OR(h, cudaMemcpyAsync(C.chi_ext, ce.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice, h->stream));
+  const double w0[2] = {0.0, 1.0};
+  CU_OR(h, cudaMemcpyAsync(h->wacc + 2 * h->cur, w0, sizeof w0, cudaMemcpyHostToDevice, h->stream));
+  CU_OR(h, cudaMemsetAsync(h->sweep_dev, 0, sizeof(uint64_t), h->stream));
   CU_OR(h, cudaStreamSynchronize(h->stream));
+  h->sweeps = 0;
   return TEBD_OK;
 }
 
 extern "C" int tebd_get_mps(tebd_t h, double* const* gamma, double* const* lambda, int* chi) {
   if (!h) return TEBD_EINVAL;
   if (tebd_check_status(h)) return h->err.code;
-  const int N = h->N;
+  ChainH& C = h->ch[h->cur];
+  const int N = C.N;
   std::vector<int> ce(N + 1);
-  CU_OR(h, cudaMemcpy(ce.data(), h->chi_ext, sizeof(int) * (N + 1), cudaMemcpyDeviceToHost));
+  CU_OR(h, cudaMemcpy(ce.data(), C.chi_ext, sizeof(int) * (N + 1), cudaMemcpyDeviceToHost));
   if (chi)
     for (int b = 0; b < N - 1; ++b) chi[b] = ce[b + 1];
   if (gamma) {
-    std::vector<char> gam(h->gamma_bytes);
-    CU_OR(h, cudaMemcpy(gam.data(), h->arena, h->gamma_bytes, cudaMemcpyDeviceToHost));
+    std::vector<char> gam(C.gamma_hi - C.gamma_lo);
+    CU_OR(h, cudaMemcpy(gam.data(), h->arena + C.gamma_lo, gam.size(), cudaMemcpyDeviceToHost));
     for (int s = 0; s < N; ++s) {
       if (!gamma[s]) continue;
-      const cplx* g = (const cplx*)(gam.data() + h->gamma_off[s]);
-      const int cl = ce[s], cr = ce[s + 1], capl = h->cap_ext[s], capr = h->cap_ext[s + 1];
-      for (int i = 0; i < h->d[s]; ++i)
+      const cplx* g = (const cplx*)(gam.data() + (C.gamma_off[s] - C.gamma_lo));
+      const int cl = ce[s], cr = ce[s + 1], capl = C.cap_ext[s], capr = C.cap_ext[s + 1];
+      for (int i = 0; i < C.d[s]; ++i)
         for (int a = 0; a < cl; ++a)
           for (int c = 0; c < cr; ++c) {
             const cplx v = g[((size_t)i * capl + a) * capr + c];
@@ -470,7 +636,7 @@ extern "C" int tebd_get_mps(tebd_t h, double* const* gamma, double* const* lambd
   if (lambda)
     for (int b = 0; b < N - 1; ++b) {
       if (!lambda[b]) continue;
-      CU_OR(h, cudaMemcpy(lambda[b], h->lam_ptr[b + 1], sizeof(double) * ce[b + 1], cudaMemcpyDeviceToHost));
+      CU_OR(h, cudaMemcpy(lambda[b], C.lam_ptr[b + 1], sizeof(double) * ce[b + 1], cudaMemcpyDeviceToHost));
     }
   return TEBD_OK;
 }
@@ -479,35 +645,76 @@ extern "C" int tebd_set_gates(tebd_t h, int parity, const double* gates) {
   if (!h) return TEBD_EINVAL;
   if (h->err.code) return h->err.code;
   if ((parity != 0 && parity != 1) || !gates) { h->err.set(TEBD_EINVAL, "bad parity or NULL gates"); return h->err.code; }
+  ChainH& C = h->ch[h->cur];
   size_t o = 0;
-  for (int b = 0; b < h->N - 1; ++b) {
-    const size_t dd = (size_t)h->d[b] * h->d[b + 1];
+  for (int b = 0; b < C.N - 1; ++b) {
+    const size_t dd = (size_t)C.d[b] * C.d[b + 1];
     if (b % 2 == parity) {
       if (!all_finite(gates + o, 2 * dd * dd)) {
         h->err.set(TEBD_ENUMERIC, "gate of bond %d has a non-finite entry", b);
         return h->err.code;
       }
-      CU_OR(h, cudaMemcpyAsync(h->arena + h->gate_off[b], gates + o, sizeof(cplx) * dd * dd, cudaMemcpyHostToDevice,
+      CU_OR(h, cudaMemcpyAsync(h->arena + C.gate_off[b], gates + o, sizeof(cplx) * dd * dd, cudaMemcpyHostToDevice,
                                h->stream));
     }
     o += 2 * dd * dd;
   }
   CU_OR(h, cudaStreamSynchronize(h->stream));
-  h->gates_set[parity] = true;
+  C.gates_set[parity] = true;
   return TEBD_OK;
+}
+
+// The launch sequence of one sweep: per wave, sizes -> theta -> RRSVD ->
+// rebuild -> weights; then the device sweep counter advances.
+static cudaError_t enqueue_sweep(tebd_t h, int parity) {
+  ParitySet& ps = h->par[parity];
+  for (const Wave& w : ps.waves) {
+    Dims* dims = ps.dims + w.first;
+    ProbPtr* ptrs = ps.ptrs + w.first;
+    const bool tuned = w.tiles[0] != 0;
+    cudaError_t e;
+    if ((e = launch_plan(ptrs, dims, w.count, h->p, h->stream)) != cudaSuccess) return e;
+    if ((e = launch_theta(dims, ptrs, w.count, w.cap, h->stream)) != cudaSuccess) return e;
+    if ((e = run_rrsvd(dims, ptrs, w.count, w.cap, h->q, h->seed, 0, 0, -1, h->status, h->stream, h->sweep_dev,
+                       tuned ? w.tiles : nullptr)) != cudaSuccess)
+      return e;
+    if ((e = launch_rebuild(dims, ptrs, w.count, h->cutoff, h->wout + w.first, h->status, h->stream)) != cudaSuccess)
+      return e;
+    if ((e = launch_wacc(dims, ptrs, h->wout + w.first, w.count, h->wacc, h->stream)) != cudaSuccess) return e;
+  }
+  return launch_sweep_tick(h->sweep_dev, h->stream);
 }
 
 static int tebd_step(tebd_t h, int parity) {
   if (!h) return TEBD_EINVAL;
   if (h->err.code) return h->err.code;
-  if (!h->gates_set[parity]) { h->err.set(TEBD_ESTATE, "gates of parity %d not set", parity); return h->err.code; }
-  ParitySet& ps = h->par[parity];
-  if (ps.batch > 0) {
-    CU_OR(h, launch_plan(h->ch, parity, h->p, ps.dims, ps.ptrs, ps.batch, h->stream));
-    CU_OR(h, launch_theta(ps.dims, ps.ptrs, ps.batch, ps.cap, h->stream));
-    CU_OR(h, run_rrsvd(ps.dims, ps.ptrs, ps.batch, ps.cap, h->q, h->seed, (uint64_t)h->sweeps, h->chain, 0,
-                       h->status, h->stream));
-    CU_OR(h, launch_rebuild(h->ch, ps.dims, ps.ptrs, ps.batch, ps.cap, h->cutoff, h->wacc, h->status, h->stream));
+  for (size_t c = 0; c < h->ch.size(); ++c)
+    if (!h->ch[c].gates_set[parity]) {
+      h->err.set(TEBD_ESTATE, "gates of parity %d not set (chain %d)", parity, (int)c);
+      return h->err.code;
+    }
+  if (h->use_graph && !prof_on()) {
+    if (!h->gexec[parity]) {
+      cudaGraph_t g = nullptr;
+      CU_OR(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+      const cudaError_t e = enqueue_sweep(h, parity);
+      const cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
+      if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        h->err.set(TEBD_ECUDA, "sweep capture failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+        return h->err.code;
+      }
+      const cudaError_t e3 = cudaGraphInstantiate(&h->gexec[parity], g, 0);
+      cudaGraphDestroy(g);
+      if (e3 != cudaSuccess) {
+        h->gexec[parity] = nullptr;
+        h->err.set(TEBD_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e3));
+        return h->err.code;
+      }
+    }
+    CU_OR(h, cudaGraphLaunch(h->gexec[parity], h->stream));
+  } else {
+    CU_OR(h, enqueue_sweep(h, parity));
   }
   h->sweeps++;
   return TEBD_OK;
@@ -519,10 +726,11 @@ extern "C" int tebd_step_odd(tebd_t h) { return tebd_step(h, 1); }
 extern "C" int tebd_expect(tebd_t h, int site, const double* op, double* out) {
   if (!h) return TEBD_EINVAL;
   if (h->err.code) return h->err.code;
-  if (site < 0 || site >= h->N || !op || !out) { h->err.set(TEBD_EINVAL, "bad site or NULL pointer"); return h->err.code; }
-  const int d = h->d[site];
+  ChainH& C = h->ch[h->cur];
+  if (site < 0 || site >= C.N || !op || !out) { h->err.set(TEBD_EINVAL, "bad site or NULL pointer"); return h->err.code; }
+  const int d = C.d[site];
   CU_OR(h, cudaMemcpyAsync(h->op_dev, op, sizeof(cplx) * d * d, cudaMemcpyHostToDevice, h->stream));
-  CU_OR(h, launch_expect(h->ch, site, h->op_dev, d, h->out_dev, h->stream));
+  CU_OR(h, launch_expect(C.dev, site, h->op_dev, d, h->out_dev, h->stream));
   CU_OR(h, cudaMemcpyAsync(out, h->out_dev, sizeof(cplx), cudaMemcpyDeviceToHost, h->stream));
   return tebd_check_status(h);
 }
@@ -530,10 +738,11 @@ extern "C" int tebd_expect(tebd_t h, int site, const double* op, double* out) {
 extern "C" int tebd_get_lambda(tebd_t h, int bond, double* out, int* chi) {
   if (!h) return TEBD_EINVAL;
   if (h->err.code) return h->err.code;
-  if (bond < 0 || bond >= h->N - 1 || !out) { h->err.set(TEBD_EINVAL, "bad bond or NULL pointer"); return h->err.code; }
+  ChainH& C = h->ch[h->cur];
+  if (bond < 0 || bond >= C.N - 1 || !out) { h->err.set(TEBD_EINVAL, "bad bond or NULL pointer"); return h->err.code; }
   int c = 0;
-  CU_OR(h, cudaMemcpyAsync(&c, h->chi_ext + bond + 1, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-  CU_OR(h, cudaMemcpyAsync(out, h->lam_ptr[bond + 1], sizeof(double) * h->cap_ext[bond + 1], cudaMemcpyDeviceToHost,
+  CU_OR(h, cudaMemcpyAsync(&c, C.chi_ext + bond + 1, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CU_OR(h, cudaMemcpyAsync(out, C.lam_ptr[bond + 1], sizeof(double) * C.cap_ext[bond + 1], cudaMemcpyDeviceToHost,
                            h->stream));
   if (tebd_check_status(h)) return h->err.code;
   if (chi) *chi = c;
@@ -544,13 +753,21 @@ extern "C" int tebd_discarded_weight(tebd_t h, double* out) {
   if (!h) return TEBD_EINVAL;
   if (h->err.code) return h->err.code;
   if (!out) { h->err.set(TEBD_EINVAL, "NULL pointer"); return h->err.code; }
-  CU_OR(h, cudaMemcpyAsync(out, h->wacc, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CU_OR(h, cudaMemcpyAsync(out, h->wacc + 2 * h->cur, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   return tebd_check_status(h);
 }
 
 extern "C" int tebd_sweep_count(tebd_t h, int64_t* out) {
   if (!h || !out) return TEBD_EINVAL;
   *out = h->sweeps;
+  return TEBD_OK;
+}
+
+extern "C" int tebd_workspace_info(tebd_t h, size_t* arena_bytes, int* waves_even, int* waves_odd) {
+  if (!h) return TEBD_EINVAL;
+  if (arena_bytes) *arena_bytes = h->arena_bytes;
+  if (waves_even) *waves_even = (int)h->par[0].waves.size();
+  if (waves_odd) *waves_odd = (int)h->par[1].waves.size();
   return TEBD_OK;
 }
 

@@ -21,7 +21,7 @@ struct Dims {
   int cl, cm, cr;  // bond dimensions left of, between and right of the two sites
   int bond;        // bond index (Philox counter word 1)
   int active;      // 0: skip this problem
-  int pad;
+  int chain;       // Philox chain index (counter word 3) of chain-driven launches
 };
 
 struct ProbPtr {
@@ -33,6 +33,16 @@ struct ProbPtr {
   const double* lamr; // lambda right (cap_r)
   const cplx* gate;   // (dl dr)^2
   int cap_l, cap_m, cap_r, pad0;
+  // static description of a chain bond (TEBD only): where its bond
+  // dimensions live on the device and its fixed sizes
+  int* chi_l;         // bond dimension left of the two sites
+  int* chi_m;         // bond dimension between them (rewritten by the rebuild)
+  int* chi_r;
+  int dl_s, dr_s;     // local dimensions
+  int chicap;         // user cap on the kept rank
+  int bond_s;         // bond index within its chain
+  int chain_s;        // Philox chain index of the chain
+  int slot;           // chain slot in the handle (discarded-weight accumulators)
   // RRSVD buffers
   const cplx* theta;  // m x n (read only for the sketches)
   cplx* omega;        // n x l
@@ -65,8 +75,11 @@ struct Caps {
 };
 
 // --- launchers (kernels.cu) ---------------------------------------------
+// chain_stride >= 0: instance p uses Philox chain chain0 + p * chain_stride and
+// the host-given sweep; chain_stride < 0: dims[p].chain and *sweep_dev.
 cudaError_t launch_omega(const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, uint64_t seed,
-                         uint64_t sweep, int64_t chain0, int chain_stride, cudaStream_t st);
+                         uint64_t sweep, int64_t chain0, int chain_stride, cudaStream_t st,
+                         const uint64_t* sweep_dev = nullptr);
 cudaError_t launch_zgemm(int stage, const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap,
                          cudaStream_t st);
 cudaError_t launch_qr(int stage, const Dims* dims, const ProbPtr* ptrs, int batch, cudaStream_t st);
@@ -80,23 +93,32 @@ cudaError_t launch_rrsvd_finalize(const Dims* dims, const ProbPtr* ptrs, int bat
 
 // the whole RRSVD from theta to (sigma, Jk, Wk, U, V): Alg. 1 + steps i-iii
 cudaError_t run_rrsvd(const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, int q, uint64_t seed,
-                      uint64_t sweep, int64_t chain0, int chain_stride, int* status, cudaStream_t st);
+                      uint64_t sweep, int64_t chain0, int chain_stride, int* status, cudaStream_t st,
+                      const uint64_t* sweep_dev = nullptr, const int* tiles = nullptr);
+
+// GEMM tile choice per stage (16 or 32); tiles == nullptr picks by grid size.
+cudaError_t launch_zgemm_tile(int stage, int tile, const Dims* dims, const ProbPtr* ptrs, int batch,
+                              const Caps& cap, cudaStream_t st);
 
 // --- TEBD-specific (tebd_kernels.cu) -------------------------------------
 struct ChainDev {
   int N;
   int* chi_ext;          // N+1 bond dims, chi_ext[0] = chi_ext[N] = 1, chi_ext[b+1] = chi of bond b
-  const int* chi_cap;    // N-1 user caps (k <= chi_cap[b])
   const int* dsite;      // N local dims
   double** lam_ext;      // N+1 pointers, outer ones point at a constant 1.0
   cplx** gamma;          // N pointers
   const int* cap_ext;    // N+1 capacities of the bonds (outer = 1)
 };
 
-cudaError_t launch_plan(const ChainDev& ch, int parity, int p, Dims* dims, ProbPtr* ptrs, int batch,
+// per-bond sizes of a wave of problems from the current bond dimensions
+cudaError_t launch_plan(const ProbPtr* ptrs, Dims* dims, int batch, int p, cudaStream_t st);
+// truncation, renormalisation and Gamma rebuild; w of problem i goes to wout[i]
+cudaError_t launch_rebuild(const Dims* dims, const ProbPtr* ptrs, int batch, double cutoff, double* wout,
+                           int* status, cudaStream_t st);
+// adds the w of a wave into the per-slot accumulators (2 doubles per chain slot)
+cudaError_t launch_wacc(const Dims* dims, const ProbPtr* ptrs, const double* wout, int batch, double* wacc,
                         cudaStream_t st);
-cudaError_t launch_rebuild(const ChainDev& ch, const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap,
-                           double cutoff, double* wacc, int* status, cudaStream_t st);
+cudaError_t launch_sweep_tick(uint64_t* sweep_dev, cudaStream_t st);
 cudaError_t launch_expect(const ChainDev& ch, int site, const cplx* op, int d, cplx* out, cudaStream_t st);
 
 }  // namespace tg

@@ -23,13 +23,14 @@ namespace tg {
 // counter (r*l + c, bond, sweep, chain).
 // ---------------------------------------------------------------------------
 __global__ void k_omega(const Dims* __restrict__ dims, const ProbPtr* __restrict__ ptrs, uint64_t seed,
-                        uint64_t sweep, int64_t chain0, int chain_stride) {
+                        uint64_t sweep, int64_t chain0, int chain_stride, const uint64_t* sweep_dev) {
   const int p = blockIdx.y;
   const Dims D = dims[p];
   if (!D.active) return;
   cplx* om = ptrs[p].omega;
   const int64_t total = (int64_t)D.n * D.l;
-  const uint64_t chain = (uint64_t)(chain0 + (int64_t)p * chain_stride);
+  const uint64_t chain = chain_stride >= 0 ? (uint64_t)(chain0 + (int64_t)p * chain_stride) : (uint64_t)D.chain;
+  if (sweep_dev) sweep = *sweep_dev;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int r = (int)(e / D.l), c = (int)(e % D.l);
     om[(int64_t)c * D.n + r] = gauss_c((uint64_t)e, (uint64_t)D.bond, sweep, chain, seed, 0);
@@ -37,13 +38,14 @@ __global__ void k_omega(const Dims* __restrict__ dims, const ProbPtr* __restrict
 }
 
 cudaError_t launch_omega(const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, uint64_t seed,
-                         uint64_t sweep, int64_t chain0, int chain_stride, cudaStream_t st) {
+                         uint64_t sweep, int64_t chain0, int chain_stride, cudaStream_t st,
+                         const uint64_t* sweep_dev) {
   const int64_t total = (int64_t)cap.n * cap.l;
   int bx = (int)((total + 255) / 256);
   if (bx > 64) bx = 64;
   if (bx < 1) bx = 1;
   ProfScope ps("k_omega", st);
-  k_omega<<<dim3(bx, batch), 256, 0, st>>>(dims, ptrs, seed, sweep, chain0, chain_stride);
+  k_omega<<<dim3(bx, batch), 256, 0, st>>>(dims, ptrs, seed, sweep, chain0, chain_stride, sweep_dev);
   return cudaGetLastError();
 }
 
@@ -165,11 +167,11 @@ __global__ void __launch_bounds__(256) k_zgemm(const Dims* __restrict__ dims, co
 
 template <int STAGE>
 static cudaError_t launch_zgemm_stage(int rows, int cols, const Dims* dims, const ProbPtr* ptrs, int batch,
-                                     cudaStream_t st) {
-  // Prefer 32x32 tiles when they already give two CTAs per SM; otherwise
-  // 16x16 tiles spread small problems over more SMs.
+                                     cudaStream_t st, int tile = 0) {
+  // Default: 32x32 tiles when they already give two CTAs per SM; otherwise
+  // 16x16 tiles spread small problems over more SMs.  tile = 16 / 32 forces.
   const int t32 = ((rows + 31) / 32) * ((cols + 31) / 32) * batch;
-  if (t32 >= 2 * 152) {
+  if (tile == 32 || (tile == 0 && t32 >= 2 * 152)) {
     dim3 grid((cols + 31) / 32, (rows + 31) / 32, batch);
     k_zgemm<32, STAGE><<<grid, 256, 0, st>>>(dims, ptrs);
   } else {
@@ -179,18 +181,23 @@ static cudaError_t launch_zgemm_stage(int rows, int cols, const Dims* dims, cons
   return cudaGetLastError();
 }
 
-cudaError_t launch_zgemm(int stage, const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap,
-                         cudaStream_t st) {
+cudaError_t launch_zgemm_tile(int stage, int tile, const Dims* dims, const ProbPtr* ptrs, int batch,
+                              const Caps& cap, cudaStream_t st) {
   ProfScope ps((stage == G_U || stage == G_V) ? "k_zgemm[uv]" : "k_zgemm[sketch]", st);
   switch (stage) {
-    case G_Y0: return launch_zgemm_stage<G_Y0>(cap.m, cap.l, dims, ptrs, batch, st);
-    case G_YT: return launch_zgemm_stage<G_YT>(cap.n, cap.l, dims, ptrs, batch, st);
-    case G_Y: return launch_zgemm_stage<G_Y>(cap.m, cap.l, dims, ptrs, batch, st);
-    case G_BH: return launch_zgemm_stage<G_BH>(cap.n, cap.l, dims, ptrs, batch, st);
-    case G_U: return launch_zgemm_stage<G_U>(cap.m, cap.k, dims, ptrs, batch, st);
-    case G_V: return launch_zgemm_stage<G_V>(cap.n, cap.k, dims, ptrs, batch, st);
+    case G_Y0: return launch_zgemm_stage<G_Y0>(cap.m, cap.l, dims, ptrs, batch, st, tile);
+    case G_YT: return launch_zgemm_stage<G_YT>(cap.n, cap.l, dims, ptrs, batch, st, tile);
+    case G_Y: return launch_zgemm_stage<G_Y>(cap.m, cap.l, dims, ptrs, batch, st, tile);
+    case G_BH: return launch_zgemm_stage<G_BH>(cap.n, cap.l, dims, ptrs, batch, st, tile);
+    case G_U: return launch_zgemm_stage<G_U>(cap.m, cap.k, dims, ptrs, batch, st, tile);
+    case G_V: return launch_zgemm_stage<G_V>(cap.n, cap.k, dims, ptrs, batch, st, tile);
   }
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_zgemm(int stage, const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap,
+                         cudaStream_t st) {
+  return launch_zgemm_tile(stage, 0, dims, ptrs, batch, cap, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -503,21 +510,23 @@ cudaError_t launch_rrsvd_finalize(const Dims* dims, const ProbPtr* ptrs, int bat
   } while (0)
 
 cudaError_t run_rrsvd(const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, int q, uint64_t seed,
-                      uint64_t sweep, int64_t chain0, int chain_stride, int* status, cudaStream_t st) {
-  TG_TRY(launch_omega(dims, ptrs, batch, cap, seed, sweep, chain0, chain_stride, st));
-  TG_TRY(launch_zgemm(G_Y0, dims, ptrs, batch, cap, st));  // Y0 = A Omega
-  TG_TRY(launch_qr(QR_Y, dims, ptrs, batch, st));           // Y0 = Q0 R0
+                      uint64_t sweep, int64_t chain0, int chain_stride, int* status, cudaStream_t st,
+                      const uint64_t* sweep_dev, const int* tiles) {
+  auto T = [&](int stage) { return tiles ? tiles[stage] : 0; };
+  TG_TRY(launch_omega(dims, ptrs, batch, cap, seed, sweep, chain0, chain_stride, st, sweep_dev));
+  TG_TRY(launch_zgemm_tile(G_Y0, T(G_Y0), dims, ptrs, batch, cap, st));  // Y0 = A Omega
+  TG_TRY(launch_qr(QR_Y, dims, ptrs, batch, st));                          // Y0 = Q0 R0
   for (int j = 0; j < q; ++j) {
-    TG_TRY(launch_zgemm(G_YT, dims, ptrs, batch, cap, st)); // Y~ = A^H Q
-    TG_TRY(launch_qr(QR_YT, dims, ptrs, batch, st));        // Y~ = Q~ R~
-    TG_TRY(launch_zgemm(G_Y, dims, ptrs, batch, cap, st));  // Y = A Q~
-    TG_TRY(launch_qr(QR_Y, dims, ptrs, batch, st));         // Y = Q R
+    TG_TRY(launch_zgemm_tile(G_YT, T(G_YT), dims, ptrs, batch, cap, st)); // Y~ = A^H Q
+    TG_TRY(launch_qr(QR_YT, dims, ptrs, batch, st));                       // Y~ = Q~ R~
+    TG_TRY(launch_zgemm_tile(G_Y, T(G_Y), dims, ptrs, batch, cap, st));   // Y = A Q~
+    TG_TRY(launch_qr(QR_Y, dims, ptrs, batch, st));                        // Y = Q R
   }
-  TG_TRY(launch_zgemm(G_BH, dims, ptrs, batch, cap, st));   // B^H = A^H Q
-  TG_TRY(launch_qr(QR_BH, dims, ptrs, batch, st));          // B^H = Qb Rb
-  TG_TRY(launch_jacobi(dims, ptrs, batch, status, st));     // Rb J = W S
-  TG_TRY(launch_zgemm(G_U, dims, ptrs, batch, cap, st));    // U = Q J_k
-  TG_TRY(launch_zgemm(G_V, dims, ptrs, batch, cap, st));    // V = Qb W_k  (stored as V^H)
+  TG_TRY(launch_zgemm_tile(G_BH, T(G_BH), dims, ptrs, batch, cap, st));   // B^H = A^H Q
+  TG_TRY(launch_qr(QR_BH, dims, ptrs, batch, st));                         // B^H = Qb Rb
+  TG_TRY(launch_jacobi(dims, ptrs, batch, status, st));                    // Rb J = W S
+  TG_TRY(launch_zgemm_tile(G_U, T(G_U), dims, ptrs, batch, cap, st));     // U = Q J_k
+  TG_TRY(launch_zgemm_tile(G_V, T(G_V), dims, ptrs, batch, cap, st));     // V = Qb W_k  (stored as V^H)
   TG_TRY(launch_frob2(dims, ptrs, batch, st));
   return cudaSuccess;
 }

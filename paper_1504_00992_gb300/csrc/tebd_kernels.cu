@@ -10,37 +10,35 @@
 namespace tg {
 
 // ---------------------------------------------------------------------------
-// Sizes of every bond of one parity from the current bond dimensions.
+// Sizes of every bond of a wave from the current bond dimensions:
 //   m = d_b chi_{b-1}, n = d_{b+1} chi_{b+1}, k = min(cap_b, m, n),
 //   l = min(k + p, m, n)   (sketch width; exact when it reaches min(m, n)).
+// Bonds of one parity share no site, so their updates are independent.
 // ---------------------------------------------------------------------------
-__global__ void k_plan(ChainDev ch, int parity, int p, Dims* dims, int batch) {
+__global__ void k_plan(const ProbPtr* __restrict__ ptrs, Dims* dims, int batch, int p) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= batch) return;
-  const int b = parity + 2 * t;
+  const ProbPtr P = ptrs[t];
   Dims D;
-  D.dl = ch.dsite[b];
-  D.dr = ch.dsite[b + 1];
-  D.cl = ch.chi_ext[b];
-  D.cm = ch.chi_ext[b + 1];
-  D.cr = ch.chi_ext[b + 2];
+  D.dl = P.dl_s;
+  D.dr = P.dr_s;
+  D.cl = *P.chi_l;
+  D.cm = *P.chi_m;
+  D.cr = *P.chi_r;
   D.m = D.dl * D.cl;
   D.n = D.dr * D.cr;
-  int k = ch.chi_cap[b];
-  k = min(k, min(D.m, D.n));
+  const int k = min(P.chicap, min(D.m, D.n));
   D.k = k;
   D.l = min(k + p, min(D.m, D.n));
-  D.bond = b;
+  D.bond = P.bond_s;
+  D.chain = P.chain_s;
   D.active = (D.cm > 0) ? 1 : 0;
-  D.pad = 0;
   dims[t] = D;
 }
 
-cudaError_t launch_plan(const ChainDev& ch, int parity, int p, Dims* dims, ProbPtr* ptrs, int batch,
-                        cudaStream_t st) {
-  (void)ptrs;
+cudaError_t launch_plan(const ProbPtr* ptrs, Dims* dims, int batch, int p, cudaStream_t st) {
   ProfScope ps("k_plan", st);
-  k_plan<<<(batch + 127) / 128, 128, 0, st>>>(ch, parity, p, dims, batch);
+  k_plan<<<(batch + 127) / 128, 128, 0, st>>>(ptrs, dims, batch, p);
   return cudaGetLastError();
 }
 
@@ -158,9 +156,8 @@ cudaError_t launch_theta(const Dims* dims, const ProbPtr* ptrs, int batch, const
 // One CTA per bond.  A zero or non-finite theta~ leaves the bond unchanged
 // and raises status bit 1.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_rebuild(ChainDev ch, const Dims* __restrict__ dims,
-                                                 const ProbPtr* __restrict__ ptrs, double cutoff, double* wout,
-                                                 int* status) {
+__global__ void __launch_bounds__(256) k_rebuild(const Dims* __restrict__ dims, const ProbPtr* __restrict__ ptrs,
+                                                 double cutoff, double* wout, int* status) {
   __shared__ int s_rank;
   __shared__ double s_inv;
   const int p = blockIdx.x;
@@ -191,8 +188,7 @@ __global__ void __launch_bounds__(256) k_rebuild(ChainDev ch, const Dims* __rest
   __syncthreads();
   const int r = s_rank;
   if (r == 0) return;
-  const int b = D.bond;
-  double* lam = ch.lam_ext[b + 1];
+  double* lam = const_cast<double*>(P.lamm);
   const int capm = P.cap_m;
   for (int i = threadIdx.x; i < capm; i += blockDim.x) lam[i] = (i < r) ? P.sigma[i] * s_inv : 0.0;
   cplx* gl = const_cast<cplx*>(P.gl);
@@ -215,31 +211,39 @@ __global__ void __launch_bounds__(256) k_rebuild(ChainDev ch, const Dims* __rest
     gr[((int64_t)j * capm + g) * P.cap_r + c] = (lr > 0.0) ? cscale(v, 1.0 / lr) : cmk(0.0, 0.0);
   }
   __syncthreads();
-  if (threadIdx.x == 0) ch.chi_ext[b + 1] = r;
+  if (threadIdx.x == 0) *P.chi_m = r;
 }
 
-// Accumulates the discarded weights of one sweep in bond order.
-__global__ void k_wacc(const double* wout, int batch, const Dims* dims, double* wacc) {
-  double s = wacc[0], pr = wacc[1];
+cudaError_t launch_rebuild(const Dims* dims, const ProbPtr* ptrs, int batch, double cutoff, double* wout,
+                           int* status, cudaStream_t st) {
+  ProfScope ps("k_rebuild", st);
+  k_rebuild<<<batch, 256, 0, st>>>(dims, ptrs, cutoff, wout, status);
+  return cudaGetLastError();
+}
+
+// Adds the discarded weights of a wave, in problem order, into the per-chain
+// accumulators wacc[2 slot] (sum of w) and wacc[2 slot + 1] (product of 1 - w).
+__global__ void k_wacc(const Dims* dims, const ProbPtr* ptrs, const double* wout, int batch, double* wacc) {
   for (int p = 0; p < batch; ++p) {
     if (!dims[p].active) continue;
-    s += wout[p];
-    pr *= (1.0 - wout[p]);
+    const int s = ptrs[p].slot;
+    wacc[2 * s] += wout[p];
+    wacc[2 * s + 1] *= (1.0 - wout[p]);
   }
-  wacc[0] = s;
-  wacc[1] = pr;
 }
 
-cudaError_t launch_rebuild(const ChainDev& ch, const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap,
-                           double cutoff, double* wacc, int* status, cudaStream_t st) {
-  (void)cap;
-  // wout scratch lives right after the two accumulators
-  double* wout = wacc + 2;
-  ProfScope ps("k_rebuild", st);
-  k_rebuild<<<batch, 256, 0, st>>>(ch, dims, ptrs, cutoff, wout, status);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  k_wacc<<<1, 1, 0, st>>>(wout, batch, dims, wacc);
+cudaError_t launch_wacc(const Dims* dims, const ProbPtr* ptrs, const double* wout, int batch, double* wacc,
+                        cudaStream_t st) {
+  k_wacc<<<1, 1, 0, st>>>(dims, ptrs, wout, batch, wacc);
+  return cudaGetLastError();
+}
+
+// The sweep counter of the Philox sketch lives on the device so that a
+// captured sweep can be replayed.
+__global__ void k_sweep_tick(uint64_t* sweep_dev) { *sweep_dev += 1; }
+
+cudaError_t launch_sweep_tick(uint64_t* sweep_dev, cudaStream_t st) {
+  k_sweep_tick<<<1, 1, 0, st>>>(sweep_dev);
   return cudaGetLastError();
 }
 
