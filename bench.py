@@ -310,6 +310,68 @@ def roofline(res, batch):
             "peak_source": "FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (derived)"}
 
 
+def run_tebd_many(B, I, torch, n_chains=256, steps=10, warm=2, unbatched_chains=16, unbatched_steps=3):
+    """Many-chain batch: the chains of I.many_chain_specs (seed 0), dt = 0.01,
+    p = 10, q = 1, all bonds of a parity of all chains per launch sequence,
+    sweeps replayed from CUDA graphs, tiles autotuned, 16 GB wave budget.
+    Compared with the same chains stepped one handle at a time."""
+    specs = I.many_chain_specs(n_chains, 0)
+    dt, p, q = 0.01, 10, 1
+
+    def setup(sim_set_state, sim_set_gates, subset):
+        for c, (N, d, chi, delta) in enumerate(subset):
+            hs = I.xxz_bond_terms(N, d, 1.0, delta)
+            sim_set_state(c, I.neel_state(N, d))
+            sim_set_gates(c, 0, I.trotter_gates(hs, dt / 2))
+            sim_set_gates(c, 1, I.trotter_gates(hs, dt))
+
+    def updates(subset, steps_):
+        return steps_ * sum(2 * ((N - 1 + 1) // 2) + (N - 1) // 2 for N, _, _, _ in subset)
+
+    chains = [(N, [d] * N, [chi] * (N - 1)) for N, d, chi, _ in specs]
+    sim = B.MultiTebd(chains, p, q, 0, use_graph=1, autotune=1, workspace_budget=16 << 30)
+    setup(sim.set_product_state, sim.set_gates, specs)
+    for _ in range(warm):
+        sim.step_even(); sim.step_odd(); sim.step_even()
+    sim.discarded_weight(0)   # synchronises
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        sim.step_even(); sim.step_odd(); sim.step_even()
+    sim.discarded_weight(0)
+    el = time.perf_counter() - t0
+    info = sim.workspace_info()
+    sim.close()
+    batched = updates(specs, steps) / el
+    # unbatched: the first chains, each in its own handle, stepped in turn
+    sub = specs[:unbatched_chains]
+    sims = []
+    for N, d, chi, delta in sub:
+        s1 = B.Tebd(N, d, chi, p, q, 0)
+        sims.append(s1)
+    setup(lambda c, psi: sims[c].set_product_state(psi), lambda c, par, g: sims[c].set_gates(par, g), sub)
+    for s1 in sims:
+        for _ in range(warm):
+            s1.step_even(); s1.step_odd(); s1.step_even()
+    sims[0].discarded_weight()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(unbatched_steps):
+        for s1 in sims:
+            s1.step_even(); s1.step_odd(); s1.step_even()
+    for s1 in sims:
+        s1.discarded_weight()
+    el2 = time.perf_counter() - t0
+    for s1 in sims:
+        s1.close()
+    unbatched = updates(sub, unbatched_steps) / el2
+    return {"value": batched, "unit": "bond updates/s", "chains": n_chains, "steps_timed": steps,
+            "unbatched_value": unbatched, "unbatched_chains": unbatched_chains, "speedup_vs_unbatched":
+            batched / unbatched, "arena_bytes": info[0], "waves": [info[1], info[2]],
+            "workload": "256 XXZ chains, N~U{16..128}, d in {2,3,4}, chi_max in {32,64,128}, Delta~U[0,1], "
+                        "dt=0.01, p=10, q=1, Neel; FP64 path, graphs + autotuned tiles + 16 GB wave budget, "
+                        "after 2 warm-up steps"}
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -347,9 +409,10 @@ def main():
     k, l = head["k"], head["l"]
     gemm_f, qr_f, uv_f = flops_rrsvd(M, N_, k, l, Q_PI)
 
-    tebd = None
+    tebd = many = None
     if not args.no_tebd:
         tebd = run_tebd_c1(B, I, torch)
+        many = run_tebd_many(B, I, torch)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -378,7 +441,8 @@ def main():
                 "speedup_vs_plain_fp64": (head["value"] / results["fp64"]["value"]) if "fp64" in results else None,
                 "roofline": roof, "kernel_time_ms": shares, "gpu_launches": launches,
                 "flops_per_update": {"gemm": gemm_f, "qr": qr_f, "uv": uv_f},
-                "cpu_baseline": cpu, "e2e": e2e, "clocks": head["clocks"], "tebd_c1": tebd}
+                "cpu_baseline": cpu, "e2e": e2e, "clocks": head["clocks"], "tebd_c1": tebd,
+                "tebd_many_chains": many}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

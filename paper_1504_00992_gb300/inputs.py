@@ -148,3 +148,17 @@ def haar_theta(m, n, sigma, seed):
     U = random_unitary(m, rng)[:, :r]
     V = random_unitary(n, rng)[:, :r]
     return (U * sigma[None, :]) @ V.conj().T
+
+
+def many_chain_specs(count=256, seed=0):
+    """Uneven XXZ chains of the many-chain batch: N ~ U{16..128},
+    d in {2, 3, 4}, chi_max in {32, 64, 128}, Delta ~ U[0, 1]; returns a list of
+    (N, d, chi_max, Delta)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        N = int(rng.integers(16, 129))
+        d = int(rng.choice([2, 3, 4]))
+        chi = int(rng.choice([32, 64, 128]))
+        out.append((N, d, chi, float(rng.random())))
+    return out
