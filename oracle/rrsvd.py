@@ -119,3 +119,47 @@ def exact_truncate(A, k, cutoff=1e-14):
     U, s, Vh = dense_svd(A)
     Uk, sk, Vhk = truncate(U, s, Vh, k, cutoff)
     return Uk, sk, Vhk, discarded_weight(sk, frob2(A))
+
+
+def probe_omega(n, r, t, seed, bond=0, sweep=0, chain=0):
+    """Probe matrix of accuracy-check round t (n x r): Philox stream 1, probe
+    element (j, c) at counter index (t n + j) r + c."""
+    from .philox import gaussian_omega
+    full = gaussian_omega(1, (t + 1) * n * r, seed, bond, sweep, chain, stream=1).ravel()
+    return full[t * n * r:(t + 1) * n * r].reshape(n, r)
+
+
+def accuracy_check(A, Q, r, eps, l_max, seed, bond=0, sweep=0, chain=0):
+    """Alg. 2 (accuracy check): while the largest probe residual
+    max_i ||(I - Q Q^H) A w_i|| exceeds eps, append the r probe images A Omega_r
+    to Q and re-orthonormalise (l += r); stop when the check passes or when
+    l + r would exceed l_max (the paper's l <= n - r, with n >= l_max).
+    Returns (Q, rounds, last MAX)."""
+    t = 0
+    while True:
+        Om = probe_omega(A.shape[1], r, t, seed, bond, sweep, chain)
+        Br = A @ Om
+        D = Br - Q @ (Q.conj().T @ Br)
+        mx = float(np.max(np.linalg.norm(D, axis=0)))
+        t += 1
+        if mx > eps:
+            Q = _qr_q(np.concatenate([Q, Br], axis=1))
+        if not (mx > eps and Q.shape[1] + r <= l_max):
+            return Q, t, mx
+
+
+def rrsvd_fixed_precision(A, Omega, q, r, eps, l_max, p, seed, bond=0, sweep=0, chain=0):
+    """Alg. 1 steps 1-3, the accuracy check of Alg. 2 on Q0, the q power
+    iterations of Alg. 1 on the (possibly enlarged) basis, then steps i-iii.
+    The kept rank follows the basis: k = l - p.  Returns (U, s, Vh, l, k,
+    exact Frobenius residual of the final Q)."""
+    Q = _qr_q(A @ Omega)
+    Q, _, _ = accuracy_check(A, Q, r, eps, l_max, seed, bond, sweep, chain)
+    for _ in range(q):
+        Qt = _qr_q(A.conj().T @ Q)
+        Q = _qr_q(A @ Qt)
+    B = Q.conj().T @ A
+    Ut, s, Vh = np.linalg.svd(B, full_matrices=False)
+    l = Q.shape[1]
+    resid = np.sqrt(max(frob2(A) - frob2(B), 0.0))   # ||(I - Q Q^H) A||_F = sqrt(||A||^2 - ||Q^H A||^2)
+    return Q @ Ut, s, Vh, l, max(l - p, 1), resid
