@@ -211,6 +211,25 @@ int rrsvd_plan_create(int m, int n, int k_max, int p, int q, int batch, int prec
                       rrsvd_plan_t* out);
 int rrsvd_plan_destroy(rrsvd_plan_t plan);
 
+/* Fixed-precision plan (Alg. 1 with the accuracy check of Alg. 2, Thm 2):
+ * after Y0 = A Omega and its QR, rounds of check_r Gaussian probes (Philox
+ * key word 1 = 1; element (j, c) of round t at counter (t n + j) check_r + c)
+ * measure MAX = max_i ||(I - Q Q^H) A w_i||; while MAX > check_eps the probe
+ * images A w_i join the basis (re-orthonormalised, l += check_r), up to
+ * l_max columns.  The q power iterations and the projection then act on the
+ * enlarged basis and each instance keeps up to k = l - p values (its basis
+ * width is read back with rrsvd_plan_widths).  Outputs use the capacity
+ * k_cap = max(l_max - p, min(k_max, m, n)) (rrsvd_plan_dims), zero past each
+ * instance's kept rank.  FP64 only.  check_r = 0 gives rrsvd_plan_create.
+ * Errors: as rrsvd_plan_create; TEBD_EINVAL for check_r < 0 or
+ * check_eps <= 0 with check_r > 0; TEBD_ENOTIMPL for TF32 with a check. */
+int rrsvd_plan_create_ex(int m, int n, int k_max, int p, int q, int batch, int precision, uint64_t seed,
+                         int check_r, double check_eps, int l_max, rrsvd_plan_t* out);
+
+/* Basis width l of every instance after the last execute (host array of
+ * `batch` ints); synchronises with the device. */
+int rrsvd_plan_widths(rrsvd_plan_t plan, int* l_out);
+
 /* Device workspace (bytes) that rrsvd_execute needs, and the plan's k, l. */
 int rrsvd_workspace_size(rrsvd_plan_t plan, size_t* bytes);
 int rrsvd_plan_dims(rrsvd_plan_t plan, int* k, int* l);

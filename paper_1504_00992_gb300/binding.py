@@ -75,6 +75,8 @@ _SIGS = {
     "tebd_last_error": (ctypes.c_char_p, [_vp]),
     "rrsvd_plan_create": (_i, [_i, _i, _i, _i, _i, _i, _i, _u64, ctypes.POINTER(_vp)]),
     "rrsvd_plan_destroy": (_i, [_vp]),
+    "rrsvd_plan_create_ex": (_i, [_i, _i, _i, _i, _i, _i, _i, _u64, _i, _d, _i, ctypes.POINTER(_vp)]),
+    "rrsvd_plan_widths": (_i, [_vp, _pi]),
     "rrsvd_workspace_size": (_i, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
     "rrsvd_plan_dims": (_i, [_vp, _pi, _pi]),
     "rrsvd_execute": (_i, [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_size_t, _vp]),
@@ -291,6 +293,22 @@ def rrsvd_plan_create(m, n, k_max, p, q, batch, precision=TEBD_PREC_FP64, seed=0
     if rc != TEBD_OK:
         raise TebdError(rc, "rrsvd_plan_create")
     return h
+
+
+def rrsvd_plan_create_ex(m, n, k_max, p, q, batch, precision=TEBD_PREC_FP64, seed=0, check_r=0, check_eps=0.0,
+                         l_max=0):
+    h = _vp()
+    rc = load().rrsvd_plan_create_ex(m, n, k_max, p, q, batch, precision, seed, check_r, check_eps, l_max,
+                                     ctypes.byref(h))
+    if rc != TEBD_OK:
+        raise TebdError(rc, "rrsvd_plan_create_ex")
+    return h
+
+
+def rrsvd_plan_widths(plan, batch):
+    out = (ctypes.c_int * batch)()
+    _pcheck(plan, load().rrsvd_plan_widths(plan, out))
+    return list(out)
 
 
 def rrsvd_plan_destroy(plan):

@@ -50,10 +50,10 @@ struct ErrState {
 
 // Per-problem RRSVD workspace layout (byte offsets from a base).
 struct WsLayout {
-  size_t omega, Y, Q, Yt, Qt, R, J, Jk, Wk, U, V, sigma, part, scal, total;
+  size_t omega, Y, Q, Yt, Qt, R, J, Jk, Wk, U, V, sigma, part, scal, Dr, total;
 };
 
-WsLayout ws_layout(int m, int n, int k, int l, bool own_U, bool own_V) {
+WsLayout ws_layout(int m, int n, int k, int l, bool own_U, bool own_V, int r = 0) {
   WsLayout w;
   size_t o = 0;
   const size_t c = sizeof(cplx);
@@ -71,6 +71,7 @@ WsLayout ws_layout(int m, int n, int k, int l, bool own_U, bool own_V) {
   w.sigma = o; o += align_up(sizeof(double) * (size_t)l);
   w.part = o; o += align_up(sizeof(double) * NPART);
   w.scal = o; o += align_up(sizeof(double) * 4);
+  w.Dr = o; o += align_up(c * (size_t)m * r);
   w.total = o;
   return w;
 }
@@ -90,6 +91,7 @@ void fill_ptrs(ProbPtr& P, char* base, const WsLayout& w) {
   P.sigma = (double*)(base + w.sigma);
   P.part = (double*)(base + w.part);
   P.scal = (double*)(base + w.scal);
+  P.Dr = (cplx*)(base + w.Dr);
 }
 
 bool all_finite(const double* x, size_t n) {
@@ -795,6 +797,9 @@ struct rrsvd_plan_s {
   int* tcerr = nullptr;
   size_t mixed_off = 0;  // start of the mixed-precision arrays in the workspace
   MixedSizes ms{};
+  // accuracy check (Alg. 2); check_r == 0: fixed rank
+  int check_r = 0, l_max = 0, rounds = 0, k0 = 0, l0 = 0;
+  double eps = 0.0;
   // host-path staging (allocated on first use)
   char* stage = nullptr;
   size_t stage_bytes = 0;
@@ -824,24 +829,37 @@ __global__ void k_rrsvd_bind(ProbPtr* ptrs, int batch, char* ws, size_t per, WsL
   P.sigma = (double*)(base + lay.sigma);
   P.part = (double*)(base + lay.part);
   P.scal = (double*)(base + lay.scal);
+  P.Dr = (cplx*)(base + lay.Dr);
   ptrs[p] = P;
 }
 }  // namespace tg
 
-extern "C" int rrsvd_plan_create(int m, int n, int k_max, int p, int q, int batch, int precision, uint64_t seed,
-                                 rrsvd_plan_t* out) {
+extern "C" int rrsvd_plan_create_ex(int m, int n, int k_max, int p, int q, int batch, int precision,
+                                    uint64_t seed, int check_r, double check_eps, int l_max, rrsvd_plan_t* out) {
   if (!out) return TEBD_EINVAL;
   *out = nullptr;
-  if (m < 1 || n < 1 || k_max < 1 || p < 0 || q < 0 || batch < 1) return TEBD_EINVAL;
+  if (m < 1 || n < 1 || k_max < 1 || p < 0 || q < 0 || batch < 1 || check_r < 0) return TEBD_EINVAL;
   if (precision != TEBD_PREC_FP64 && precision != TEBD_PREC_TF32) return TEBD_ENOTIMPL;
+  if (check_r > 0 && (precision != TEBD_PREC_FP64 || !(check_eps > 0.0))) return check_eps > 0.0 ? TEBD_ENOTIMPL : TEBD_EINVAL;
   rrsvd_plan_s* P = new rrsvd_plan_s();
   P->m = m; P->n = n; P->p = p; P->q = q; P->batch = batch; P->precision = precision; P->seed = seed;
   P->k = std::min(k_max, std::min(m, n));
   P->l = std::min(P->k + p, std::min(m, n));
+  P->k0 = P->k;
+  P->l0 = P->l;
+  if (check_r > 0) {
+    P->check_r = check_r;
+    P->eps = check_eps;
+    P->l_max = std::min(std::max(l_max, P->l), std::min(m, n));
+    P->rounds = (P->l_max - P->l0) / check_r + 1;
+    P->l = P->l_max;                           // capacities
+    P->k = std::max(1, P->l_max - p);
+    if (P->k < P->k0) P->k = P->k0;
+  }
   if (P->l > 512) { delete P; return TEBD_ENOTIMPL; }
-  P->cap.m = m; P->cap.n = n; P->cap.k = P->k; P->cap.l = P->l;
+  P->cap.m = m; P->cap.n = n; P->cap.k = P->k; P->cap.l = P->l; P->cap.r = check_r;
   // workspace always holds U and Vh so that either may be NULL at execute
-  P->lay = ws_layout(m, n, P->k, P->l, true, true);
+  P->lay = ws_layout(m, n, P->k, P->l, true, true, check_r);
   P->per = P->lay.total;
   P->ws_bytes = P->per * (size_t)batch;
   if (precision == TEBD_PREC_TF32) {
@@ -871,6 +889,11 @@ extern "C" int rrsvd_plan_create(int m, int n, int k_max, int p, int q, int batc
   return TEBD_OK;
 }
 
+extern "C" int rrsvd_plan_create(int m, int n, int k_max, int p, int q, int batch, int precision, uint64_t seed,
+                                 rrsvd_plan_t* out) {
+  return rrsvd_plan_create_ex(m, n, k_max, p, q, batch, precision, seed, 0, 0.0, 0, out);
+}
+
 extern "C" int rrsvd_plan_destroy(rrsvd_plan_t P) {
   if (!P) return TEBD_OK;
   if (P->meta) cudaFree(P->meta);
@@ -882,6 +905,14 @@ extern "C" int rrsvd_plan_destroy(rrsvd_plan_t P) {
 extern "C" int rrsvd_workspace_size(rrsvd_plan_t P, size_t* bytes) {
   if (!P || !bytes) return TEBD_EINVAL;
   *bytes = P->ws_bytes;
+  return TEBD_OK;
+}
+
+extern "C" int rrsvd_plan_widths(rrsvd_plan_t P, int* l_out) {
+  if (!P || !l_out) return TEBD_EINVAL;
+  std::vector<Dims> hd(P->batch);
+  CU_OR(P, cudaMemcpy(hd.data(), P->dims, sizeof(Dims) * P->batch, cudaMemcpyDeviceToHost));
+  for (int i = 0; i < P->batch; ++i) l_out[i] = hd[i].l;
   return TEBD_OK;
 }
 
@@ -903,13 +934,27 @@ extern "C" int rrsvd_execute(rrsvd_plan_t P, const double* theta, int64_t chain0
   }
   if (((uintptr_t)workspace) % ALIGN) { P->err.set(TEBD_EINVAL, "workspace not 256-byte aligned"); return P->err.code; }
   cudaStream_t st = (cudaStream_t)stream;
+  const bool checked = P->check_r > 0;
   {
   ProfScope ps("k_rrsvd_bind", st);
   k_rrsvd_bind<<<(P->batch + 127) / 128, 128, 0, st>>>(P->ptrs, P->batch, (char*)workspace, P->per, P->lay,
-                                                     (const cplx*)theta, (size_t)P->m * P->n, (cplx*)U,
-                                                     (size_t)P->m * P->k, (cplx*)Vh, (size_t)P->k * P->n);
+                                                     (const cplx*)theta, (size_t)P->m * P->n,
+                                                     checked ? nullptr : (cplx*)U, (size_t)P->m * P->k, (cplx*)Vh,
+                                                     (size_t)P->k * P->n);
   }
   CU_OR(P, cudaGetLastError());
+  if (checked) {
+    Dims t;
+    memset(&t, 0, sizeof t);
+    t.m = P->m; t.n = P->n; t.k = P->k0; t.l = P->l0; t.active = 1; t.r = P->check_r;
+    t.chk = (P->l0 + P->check_r <= P->l_max) ? 1 : 0;
+    CU_OR(P, launch_checked_init(P->dims, P->batch, t, st));
+    CU_OR(P, run_rrsvd_checked(P->dims, P->ptrs, P->batch, P->cap, P->q, P->rounds, P->eps, P->l_max, P->p, P->seed,
+                               chain0, P->status, st));
+    CU_OR(P, launch_finalize_checked(P->dims, P->ptrs, P->batch, P->k, 1e-14, sigma, U, w, rank, nullptr, P->status,
+                                     st));
+    return TEBD_OK;
+  }
   if (P->precision == TEBD_PREC_TF32) {
     const MixedPtrs mp = mixed_carve((char*)workspace + P->mixed_off, P->ms, P->batch);
     CU_OR(P, run_rrsvd_mixed(P->dims, P->ptrs, P->batch, P->cap, mp, P->q, P->seed, 0, chain0, 1, P->status,

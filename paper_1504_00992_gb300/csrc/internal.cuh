@@ -22,6 +22,9 @@ struct Dims {
   int bond;        // bond index (Philox counter word 1)
   int active;      // 0: skip this problem
   int chain;       // Philox chain index (counter word 3) of chain-driven launches
+  int r;           // accuracy check: probes per round (0 = no check)
+  int chk;         // accuracy check still running for this problem
+  int qflag;       // this round extended the basis: re-orthonormalise it
 };
 
 struct ProbPtr {
@@ -59,12 +62,15 @@ struct ProbPtr {
   double* sigma;      // l       (sorted descending)
   double* part;       // NPART partial sums of |theta|^2
   double* scal;       // per-problem scalars: [0] ||theta||_F^2, [1] w, [2] kept rank
+  cplx* Dr;           // m x r: Q Q^H A Omega_r of the accuracy check
 };
 
 enum { NPART = 64 };
 
 // GEMM stages of the pipeline (op(A) op(B) -> C).
-enum GemmStage { G_Y0 = 0, G_YT = 1, G_Y = 2, G_BH = 3, G_U = 4, G_V = 5 };
+enum GemmStage { G_Y0 = 0, G_YT = 1, G_Y = 2, G_BH = 3, G_U = 4, G_V = 5,
+                 // accuracy check: Br = A Omega_r (into Y after the basis), C1 = Q^H Br, Dr = Q C1
+                 G_PR = 6, G_PQ = 7, G_PD = 8 };
 // QR stages: which buffer is factored and where Q goes.
 enum QrStage { QR_Y = 0, QR_YT = 1, QR_BH = 2 };
 
@@ -72,6 +78,7 @@ enum QrStage { QR_Y = 0, QR_YT = 1, QR_BH = 2 };
 struct Caps {
   int m, n, k, l;
   int cl, cr, dl, dr;
+  int r;  // accuracy-check probes per round
 };
 
 // --- launchers (kernels.cu) ---------------------------------------------
@@ -82,7 +89,8 @@ cudaError_t launch_omega(const Dims* dims, const ProbPtr* ptrs, int batch, const
                          const uint64_t* sweep_dev = nullptr);
 cudaError_t launch_zgemm(int stage, const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap,
                          cudaStream_t st);
-cudaError_t launch_qr(int stage, const Dims* dims, const ProbPtr* ptrs, int batch, cudaStream_t st);
+cudaError_t launch_qr(int stage, const Dims* dims, const ProbPtr* ptrs, int batch, cudaStream_t st,
+                      int only_flagged = 0);
 cudaError_t launch_jacobi(const Dims* dims, const ProbPtr* ptrs, int batch, int* status, cudaStream_t st);
 cudaError_t launch_frob2(const Dims* dims, const ProbPtr* ptrs, int batch, cudaStream_t st);
 cudaError_t launch_theta(const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, cudaStream_t st);
@@ -95,6 +103,22 @@ cudaError_t launch_rrsvd_finalize(const Dims* dims, const ProbPtr* ptrs, int bat
 cudaError_t run_rrsvd(const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, int q, uint64_t seed,
                       uint64_t sweep, int64_t chain0, int chain_stride, int* status, cudaStream_t st,
                       const uint64_t* sweep_dev = nullptr, const int* tiles = nullptr);
+
+// Accuracy check (Alg. 2) rounds between Alg. 1 step 3 and the power
+// iterations: rounds = host bound on the number of rounds; l grows on the
+// device; eps the threshold; stream-1 Philox probes.
+cudaError_t run_accuracy_check(const Dims* dims_mut, const ProbPtr* ptrs, int batch, const Caps& cap, int rounds,
+                               double eps, int l_max, int p, uint64_t seed, uint64_t sweep, int64_t chain0,
+                               int chain_stride, cudaStream_t st);
+// the whole fixed-precision RRSVD (Alg. 1 + Alg. 2 + steps i-iii), FP64
+cudaError_t run_rrsvd_checked(Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, int q, int rounds,
+                              double eps, int l_max, int p, uint64_t seed, int64_t chain0, int* status,
+                              cudaStream_t st);
+
+cudaError_t launch_finalize_checked(const Dims* dims, const ProbPtr* ptrs, int batch, int kcap, double cutoff,
+                                    double* sigma, double* Uout, double* w, int* rank, int* lw, int* status,
+                                    cudaStream_t st);
+cudaError_t launch_checked_init(Dims* dims, int batch, const Dims& tmpl, cudaStream_t st);
 
 // GEMM tile choice per stage (16 or 32); tiles == nullptr picks by grid size.
 cudaError_t launch_zgemm_tile(int stage, int tile, const Dims* dims, const ProbPtr* ptrs, int batch,

@@ -80,18 +80,33 @@ __device__ __forceinline__ GemmOp gemm_of(const Dims& D, const ProbPtr& P) {
     g.A = P.Q; g.ars = 1; g.acs = D.m;
     g.B = P.Jk; g.brs = 1; g.bcs = D.l;
     g.C = P.U; g.crs = D.k; g.ccs = 1;
-  } else {  // G_V: V = Qb Wk, stored conjugated as Vh (k x n, row-major)
+  } else if (STAGE == G_V) {  // V = Qb Wk, stored conjugated as Vh (k x n, row-major)
     g.M = D.n; g.N = D.k; g.K = D.l;
     g.A = P.Qt; g.ars = 1; g.acs = D.n;
     g.B = P.Wk; g.brs = 1; g.bcs = D.l;
     g.C = P.V; g.crs = 1; g.ccs = D.n;
+  } else if (STAGE == G_PR) {  // Br = A Omega_r -> columns l .. l+r-1 of Y (m x r)
+    g.M = D.m; g.N = D.r; g.K = D.n;
+    g.A = P.theta; g.ars = D.n; g.acs = 1;
+    g.B = P.omega; g.brs = 1; g.bcs = D.n;
+    g.C = P.Y + (int64_t)D.l * D.m; g.crs = 1; g.ccs = D.m;
+  } else if (STAGE == G_PQ) {  // C1 = Q^H Br (l x r, column-major in R)
+    g.M = D.l; g.N = D.r; g.K = D.m;
+    g.A = P.Q; g.ars = D.m; g.acs = 1;          // op(A)(i, k) = conj(Q[k][i])
+    g.B = P.Y + (int64_t)D.l * D.m; g.brs = 1; g.bcs = D.m;
+    g.C = P.R; g.crs = 1; g.ccs = D.l;
+  } else {  // G_PD: Dr = Q C1 (m x r)
+    g.M = D.m; g.N = D.r; g.K = D.l;
+    g.A = P.Q; g.ars = 1; g.acs = D.m;
+    g.B = P.R; g.brs = 1; g.bcs = D.l;
+    g.C = P.Dr; g.crs = 1; g.ccs = D.m;
   }
   return g;
 }
 
 template <int STAGE>
 struct StageFlags {
-  static constexpr bool conjA = (STAGE == G_YT || STAGE == G_BH);
+  static constexpr bool conjA = (STAGE == G_YT || STAGE == G_BH || STAGE == G_PQ);
   static constexpr bool conjC = (STAGE == G_V);
 };
 
@@ -104,6 +119,7 @@ __global__ void __launch_bounds__(256) k_zgemm(const Dims* __restrict__ dims, co
   const int p = blockIdx.z;
   const Dims D = dims[p];
   if (!D.active) return;
+  if ((STAGE == G_PR || STAGE == G_PQ || STAGE == G_PD) && !D.chk) return;
   const GemmOp g = gemm_of<STAGE>(D, ptrs[p]);
   const int tm = blockIdx.y * T, tn = blockIdx.x * T;
   if (tm >= g.M || tn >= g.N) return;
@@ -191,6 +207,9 @@ cudaError_t launch_zgemm_tile(int stage, int tile, const Dims* dims, const ProbP
     case G_BH: return launch_zgemm_stage<G_BH>(cap.n, cap.l, dims, ptrs, batch, st, tile);
     case G_U: return launch_zgemm_stage<G_U>(cap.m, cap.k, dims, ptrs, batch, st, tile);
     case G_V: return launch_zgemm_stage<G_V>(cap.n, cap.k, dims, ptrs, batch, st, tile);
+    case G_PR: return launch_zgemm_stage<G_PR>(cap.m, cap.r, dims, ptrs, batch, st, tile);
+    case G_PQ: return launch_zgemm_stage<G_PQ>(cap.l, cap.r, dims, ptrs, batch, st, tile);
+    case G_PD: return launch_zgemm_stage<G_PD>(cap.m, cap.r, dims, ptrs, batch, st, tile);
   }
   return cudaErrorInvalidValue;
 }
@@ -211,13 +230,15 @@ cudaError_t launch_zgemm(int stage, const Dims* dims, const ProbPtr* ptrs, int b
 enum { QR_MAXL = 512 };
 
 template <int QS>
-__global__ void __launch_bounds__(256) k_qr(const Dims* __restrict__ dims, const ProbPtr* __restrict__ ptrs) {
+__global__ void __launch_bounds__(256) k_qr(const Dims* __restrict__ dims, const ProbPtr* __restrict__ ptrs,
+                                            int only_flagged) {
   __shared__ double red[32];
   __shared__ double tau[QR_MAXL];
   __shared__ cplx alph[QR_MAXL];
   const int p = blockIdx.x;
   const Dims D = dims[p];
   if (!D.active) return;
+  if (only_flagged && !D.qflag) return;
   const ProbPtr P = ptrs[p];
   const int M = (QS == QR_Y) ? D.m : D.n;
   const int L = D.l;
@@ -292,12 +313,13 @@ __global__ void __launch_bounds__(256) k_qr(const Dims* __restrict__ dims, const
   }
 }
 
-cudaError_t launch_qr(int stage, const Dims* dims, const ProbPtr* ptrs, int batch, cudaStream_t st) {
+cudaError_t launch_qr(int stage, const Dims* dims, const ProbPtr* ptrs, int batch, cudaStream_t st,
+                      int only_flagged) {
   ProfScope ps("k_qr", st);
   switch (stage) {
-    case QR_Y: k_qr<QR_Y><<<batch, 256, 0, st>>>(dims, ptrs); break;
-    case QR_YT: k_qr<QR_YT><<<batch, 256, 0, st>>>(dims, ptrs); break;
-    case QR_BH: k_qr<QR_BH><<<batch, 256, 0, st>>>(dims, ptrs); break;
+    case QR_Y: k_qr<QR_Y><<<batch, 256, 0, st>>>(dims, ptrs, only_flagged); break;
+    case QR_YT: k_qr<QR_YT><<<batch, 256, 0, st>>>(dims, ptrs, only_flagged); break;
+    case QR_BH: k_qr<QR_BH><<<batch, 256, 0, st>>>(dims, ptrs, only_flagged); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

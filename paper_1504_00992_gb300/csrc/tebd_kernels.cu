@@ -33,6 +33,9 @@ __global__ void k_plan(const ProbPtr* __restrict__ ptrs, Dims* dims, int batch, 
   D.bond = P.bond_s;
   D.chain = P.chain_s;
   D.active = (D.cm > 0) ? 1 : 0;
+  D.r = 0;
+  D.chk = 0;
+  D.qflag = 0;
   dims[t] = D;
 }
 
