@@ -162,3 +162,16 @@ def many_chain_specs(count=256, seed=0):
         chi = int(rng.choice([32, 64, 128]))
         out.append((N, d, chi, float(rng.random())))
     return out
+
+
+def gate_derivative(h, tau, dh):
+    """Frechet derivative of the gate G = exp(-i tau h) along dh (h Hermitian), the
+    caller-side chain rule from gate cotangents to Hamiltonian couplings: with
+    h = W diag(e) W^H, dG = W [ (W^H dh W) o Phi ] W^H, Phi_ij the divided
+    difference of exp(-i tau e) between e_i and e_j."""
+    e, W = np.linalg.eigh(h)
+    f = np.exp(-1j * tau * e)
+    de = e[:, None] - e[None, :]
+    same = np.abs(de) < 1e-12 * max(1.0, np.abs(e).max())
+    Phi = np.where(same, -1j * tau * f[:, None] * np.ones_like(de), (f[:, None] - f[None, :]) / np.where(same, 1.0, de))
+    return W @ ((W.conj().T @ dh @ W) * Phi) @ W.conj().T
