@@ -187,9 +187,30 @@ int tebd_discarded_weight(tebd_t h, double* out);
 /* Number of tebd_step_* calls made (the Philox sweep counter). */
 int tebd_sweep_count(tebd_t h, int64_t* out);
 
-/* Reverse-mode derivative of a time-evolved observable with respect to the
- * gates.  Not built: returns TEBD_ENOTIMPL. */
-int tebd_backward(tebd_t h, const double* obs_cotangent, double* dgates_even, double* dgates_odd);
+/* Recording for the reverse pass (single-chain handles): while on, every
+ * tebd_step_* first stores a device checkpoint of the chain's tensors,
+ * Schmidt values, gates and bond dimensions (one allocation per sweep,
+ * freed by the next tebd_record(h, 1) or tebd_destroy).  Turning it on
+ * clears earlier checkpoints.  Errors: TEBD_ENOTIMPL (several chains),
+ * TEBD_ENOMEM. */
+int tebd_record(tebd_t h, int on);
+
+/* Gradient of L = Re <O_site> in the current state (O: d x d complex, host;
+ * its Hermitian part is used) with respect to the gate matrices of the
+ * recorded sweeps, summed over every application of each parity:
+ * dgates_even / dgates_odd receive N-1 complex blocks in the tebd_set_gates
+ * layout (bonds of the other parity zero; either may be NULL).  The
+ * cotangent convention is G_bar = dL/dRe G + i dL/dIm G, so that
+ * dL = Re sum conj(G_bar) dG.  Each recorded sweep is recomputed from its
+ * checkpoint, then its bond updates are differentiated in reverse: the
+ * Vidal extraction, the renormalisation, the truncated SVD the RRSVD
+ * approximates (Omega held fixed; 1/(s_j^2 - s_i^2) broadened with 1e-12,
+ * 1/s with 1e-20; the coupling to discarded singular vectors is neglected),
+ * the gate and the contraction.  The forward state, sweep counter and
+ * discarded weights are restored afterwards.  Synchronises.
+ * Errors: TEBD_EINVAL, TEBD_ESTATE (nothing recorded), TEBD_ENOTIMPL
+ * (several chains), TEBD_ENOMEM, TEBD_ECUDA. */
+int tebd_backward(tebd_t h, int site, const double* op, double* dgates_even, double* dgates_odd);
 
 /* Text of the first error recorded on the handle ("" if none). */
 const char* tebd_last_error(tebd_t h);

@@ -71,7 +71,8 @@ _SIGS = {
     "tebd_get_lambda": (_i, [_vp, _i, _pd, _pi]),
     "tebd_discarded_weight": (_i, [_vp, _pd]),
     "tebd_sweep_count": (_i, [_vp, ctypes.POINTER(_i64)]),
-    "tebd_backward": (_i, [_vp, _pd, _pd, _pd]),
+    "tebd_backward": (_i, [_vp, _i, _pd, _pd, _pd]),
+    "tebd_record": (_i, [_vp, _i]),
     "tebd_last_error": (ctypes.c_char_p, [_vp]),
     "rrsvd_plan_create": (_i, [_i, _i, _i, _i, _i, _i, _i, _u64, ctypes.POINTER(_vp)]),
     "rrsvd_plan_destroy": (_i, [_vp]),
@@ -271,9 +272,28 @@ def tebd_sweep_count(h):
     return c.value
 
 
-def tebd_backward(h, obs_cotangent=None, dgates_even=None, dgates_odd=None):
-    rc = load().tebd_backward(h, None, None, None)
-    _check(h, rc)
+def tebd_record(h, on=True):
+    _check(h, load().tebd_record(h, 1 if on else 0))
+
+
+def tebd_backward(h, site, op, dims):
+    """Gate cotangents of L = Re <op_site>: returns (even, odd), each a list of
+    N-1 complex (d_b d_{b+1})^2 matrices (zero for the other parity)."""
+    sizes = [(dims[b] * dims[b + 1]) for b in range(len(dims) - 1)]
+    tot = sum(x * x for x in sizes)
+    ge = np.zeros(tot, dtype=np.complex128)
+    go = np.zeros(tot, dtype=np.complex128)
+    o = _c128(op)
+    _check(h, load().tebd_backward(h, site, _dp(o.view(np.float64)), _dp(ge.view(np.float64)),
+                                   _dp(go.view(np.float64))))
+    out = []
+    for arr in (ge, go):
+        mats, off = [], 0
+        for x in sizes:
+            mats.append(arr[off:off + x * x].reshape(x, x).copy())
+            off += x * x
+        out.append(mats)
+    return out[0], out[1]
 
 
 def tebd_last_error(h):
@@ -453,6 +473,12 @@ class Tebd:
 
     def sweeps(self):
         return tebd_sweep_count(self.h)
+
+    def record(self, on=True):
+        tebd_record(self.h, on)
+
+    def backward(self, site, op):
+        return tebd_backward(self.h, site, op, self.dims)
 
 
 def _caps(dims, chi_bond):

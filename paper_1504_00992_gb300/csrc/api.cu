@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "../../include/tebd_gb300.h"
+#include "adjoint.cuh"
 #include "internal.cuh"
 #include "mixed.cuh"
 #include "profiler.cuh"
@@ -159,7 +160,28 @@ struct tebd_s {
   bool use_graph = false;
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
   cudaStream_t own_stream = nullptr;  // used for graphs when the caller gives the legacy stream 0
+  // reverse pass: checkpoints of the chain's state before every recorded sweep
+  bool recording = false;
+  struct Ckpt {
+    int parity;
+    int64_t sweep;
+    char* buf;
+  };
+  std::vector<Ckpt> ckpts;
+  char* adj_arena = nullptr;
+  AdjPtr* adj_dev[2] = {nullptr, nullptr};
+  cplx* gbar0 = nullptr;  // cotangent state (Gamma block, then lambdas)
+  size_t cot_bytes = 0;
 };
+
+static size_t chain_region_end(const ChainH& C) {
+  return C.int_off + 3 * align_up(sizeof(int) * (C.N + 1));
+}
+
+static void free_ckpts(tebd_s* h) {
+  for (auto& c : h->ckpts) cudaFree(c.buf);
+  h->ckpts.clear();
+}
 
 static int tebd_check_status(tebd_t h) {
   int st = 0;
@@ -170,6 +192,8 @@ static int tebd_check_status(tebd_t h) {
 }
 
 static void tebd_free(tebd_s* h) {
+  free_ckpts(h);
+  if (h->adj_arena) cudaFree(h->adj_arena);
   for (int i = 0; i < 2; ++i)
     if (h->gexec[i]) cudaGraphExecDestroy(h->gexec[i]);
   if (h->arena) cudaFree(h->arena);
@@ -695,6 +719,18 @@ static int tebd_step(tebd_t h, int parity) {
       h->err.set(TEBD_ESTATE, "gates of parity %d not set (chain %d)", parity, (int)c);
       return h->err.code;
     }
+  if (h->recording) {
+    const ChainH& C = h->ch[0];
+    const size_t bytes = chain_region_end(C) - C.gamma_lo;
+    char* buf = nullptr;
+    if (cudaMalloc(&buf, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      h->err.set(TEBD_ENOMEM, "checkpoint of %zu bytes failed", bytes);
+      return h->err.code;
+    }
+    h->ckpts.push_back({parity, h->sweeps, buf});
+    CU_OR(h, cudaMemcpyAsync(buf, h->arena + C.gamma_lo, bytes, cudaMemcpyDeviceToDevice, h->stream));
+  }
   if (h->use_graph && !prof_on()) {
     if (!h->gexec[parity]) {
       cudaGraph_t g = nullptr;
@@ -773,9 +809,219 @@ extern "C" int tebd_workspace_info(tebd_t h, size_t* arena_bytes, int* waves_eve
   return TEBD_OK;
 }
 
-extern "C" int tebd_backward(tebd_t h, const double*, double*, double*) {
+// Adjoint scratch and cotangent buffers of a single-chain handle (capacity sizes).
+static int tebd_adj_alloc(tebd_t h) {
+  if (h->adj_arena) return TEBD_OK;
+  const ChainH& C = h->ch[0];
+  const int N = C.N;
+  const size_t c16 = sizeof(cplx), c8 = sizeof(double);
+  // cotangent state: Gamma_bar per site, lambda_bar per bond
+  std::vector<size_t> goff(N), loff(N - 1);
+  size_t off = 0;
+  for (int s = 0; s < N; ++s) {
+    goff[s] = off;
+    off += align_up(c16 * (size_t)C.d[s] * C.cap_ext[s] * C.cap_ext[s + 1]);
+  }
+  for (int b = 0; b < N - 1; ++b) {
+    loff[b] = off;
+    off += align_up(c8 * C.cap_ext[b + 1]);
+  }
+  const size_t cot_bytes = off;
+  struct Sz { size_t th, ur, vr, kk, pb, rb, sb, xb, yb, zb, gb; };
+  std::vector<Sz> sz[2];
+  std::vector<size_t> poff[2];
+  for (int par = 0; par < 2; ++par)
+    for (const auto& bb : h->par[par].bonds) {
+      const int b = bb.second;
+      const size_t m = (size_t)C.d[b] * C.cap_ext[b], n = (size_t)C.d[b + 1] * C.cap_ext[b + 2];
+      const size_t kc = std::min<size_t>(C.cap_ext[b + 1], std::min(m, n)), cm = C.cap_ext[b + 1];
+      const size_t dd = (size_t)C.d[b] * C.d[b + 1];
+      Sz z{align_up(c16 * m * n), align_up(c16 * m * kc), align_up(c16 * n * kc), align_up(c16 * kc * kc),
+           align_up(c16 * m * cm), align_up(c16 * cm * n), align_up(c8 * kc), align_up(c8 * C.cap_ext[b]),
+           align_up(c8 * cm), align_up(c8 * C.cap_ext[b + 2]), align_up(c16 * dd * dd)};
+      sz[par].push_back(z);
+      poff[par].push_back(off);
+      off += 3 * z.th + 2 * z.ur + 2 * z.vr + 3 * z.kk + z.pb + z.rb + z.sb + z.xb + z.yb + z.zb + z.gb;
+    }
+  const size_t desc_off = off;
+  for (int par = 0; par < 2; ++par) off += align_up(sizeof(AdjPtr) * std::max<size_t>(1, h->par[par].bonds.size()));
+  if (cudaMalloc(&h->adj_arena, off) != cudaSuccess) {
+    cudaGetLastError();
+    h->adj_arena = nullptr;
+    h->err.set(TEBD_ENOMEM, "reverse-pass buffers of %zu bytes failed", off);
+    return h->err.code;
+  }
+  char* A = h->adj_arena;
+  h->gbar0 = (cplx*)A;
+  h->cot_bytes = cot_bytes;
+  size_t doff = desc_off;
+  for (int par = 0; par < 2; ++par) {
+    ParitySet& ps = h->par[par];
+    std::vector<AdjPtr> hp(ps.bonds.size());
+    for (size_t i = 0; i < ps.bonds.size(); ++i) {
+      const int b = ps.bonds[i].second;
+      const Sz& z = sz[par][i];
+      char* q = A + poff[par][i];
+      AdjPtr& P = hp[i];
+      P.th0 = (cplx*)q; q += z.th;
+      P.Mbar = (cplx*)q; q += z.th;
+      P.Tbar = (cplx*)q; q += z.th;
+      P.Ubar = (cplx*)q; q += z.ur;
+      P.T1 = (cplx*)q; q += z.ur;
+      P.Vbar = (cplx*)q; q += z.vr;
+      P.Pv = (cplx*)q; q += z.vr;
+      P.Gu = (cplx*)q; q += z.kk;
+      P.Gv = (cplx*)q; q += z.kk;
+      P.Cm = (cplx*)q; q += z.kk;
+      P.Pbar = (cplx*)q; q += z.pb;
+      P.Rbar = (cplx*)q; q += z.rb;
+      P.Sbar = (double*)q; q += z.sb;
+      P.xbar = (double*)q; q += z.xb;
+      P.ybar = (double*)q; q += z.yb;
+      P.zbar = (double*)q; q += z.zb;
+      P.Gbar = (cplx*)q; q += z.gb;
+      P.gbar_l = (cplx*)(A + goff[b]);
+      P.gbar_r = (cplx*)(A + goff[b + 1]);
+      P.lbar = (double*)(A + loff[b]);
+      P.lbar_l = b > 0 ? (double*)(A + loff[b - 1]) : nullptr;
+      P.lbar_r = b + 1 < N - 1 ? (double*)(A + loff[b + 1]) : nullptr;
+    }
+    h->adj_dev[par] = (AdjPtr*)(A + doff);
+    doff += align_up(sizeof(AdjPtr) * std::max<size_t>(1, ps.bonds.size()));
+    if (!hp.empty() && cudaMemcpy(h->adj_dev[par], hp.data(), sizeof(AdjPtr) * hp.size(), cudaMemcpyHostToDevice) !=
+                           cudaSuccess) {
+      h->err.set(TEBD_ECUDA, "reverse-pass descriptors upload failed");
+      return h->err.code;
+    }
+  }
+  return TEBD_OK;
+}
+
+extern "C" int tebd_record(tebd_t h, int on) {
   if (!h) return TEBD_EINVAL;
-  return TEBD_ENOTIMPL;
+  if (h->err.code) return h->err.code;
+  if (h->ch.size() != 1) { h->err.set(TEBD_ENOTIMPL, "recording needs a single-chain handle"); return h->err.code; }
+  if (on) {
+    CU_OR(h, cudaStreamSynchronize(h->stream));
+    free_ckpts(h);
+    if (tebd_adj_alloc(h) != TEBD_OK) return h->err.code;
+  }
+  h->recording = on != 0;
+  return TEBD_OK;
+}
+
+extern "C" int tebd_backward(tebd_t h, int site, const double* op, double* dgates_even, double* dgates_odd) {
+  if (!h) return TEBD_EINVAL;
+  if (h->err.code) return h->err.code;
+  if (h->ch.size() != 1) { h->err.set(TEBD_ENOTIMPL, "the reverse pass needs a single-chain handle"); return h->err.code; }
+  ChainH& C = h->ch[0];
+  const int N = C.N;
+  if (site < 0 || site >= N || !op) { h->err.set(TEBD_EINVAL, "bad site or NULL op"); return h->err.code; }
+  if (h->ckpts.empty()) { h->err.set(TEBD_ESTATE, "no recorded sweeps"); return h->err.code; }
+  if (tebd_adj_alloc(h) != TEBD_OK) return h->err.code;
+  if (tebd_check_status(h)) return h->err.code;
+  cudaStream_t st = h->stream;
+  const size_t rbytes = chain_region_end(C) - C.gamma_lo;
+  char* region = h->arena + C.gamma_lo;
+  // keep the final state, sweep counter and weights to restore them afterwards
+  char* save = nullptr;
+  if (cudaMalloc(&save, rbytes + 2 * ALIGN + align_up(sizeof(double) * 2 * h->ch.size())) != cudaSuccess) {
+    cudaGetLastError();
+    h->err.set(TEBD_ENOMEM, "reverse-pass save buffer failed");
+    return h->err.code;
+  }
+  int rc = TEBD_OK;
+  do {
+    if (cudaMemcpyAsync(save, region, rbytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(save + rbytes, h->sweep_dev, sizeof(uint64_t), cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(save + rbytes + ALIGN, h->wacc, sizeof(double) * 2 * h->ch.size(), cudaMemcpyDeviceToDevice,
+                        st) != cudaSuccess ||
+        cudaMemsetAsync(h->gbar0, 0, h->cot_bytes, st) != cudaSuccess) { rc = TEBD_ECUDA; break; }
+    for (int par = 0; par < 2 && rc == TEBD_OK; ++par) {
+      std::vector<AdjPtr> hp(h->par[par].bonds.size());
+      if (!hp.empty() && cudaMemcpy(hp.data(), h->adj_dev[par], sizeof(AdjPtr) * hp.size(), cudaMemcpyDeviceToHost) != cudaSuccess) rc = TEBD_ECUDA;
+      for (size_t i = 0; i < hp.size() && rc == TEBD_OK; ++i) {
+        const int b = h->par[par].bonds[i].second;
+        const size_t dd = (size_t)C.d[b] * C.d[b + 1];
+        if (cudaMemsetAsync(hp[i].Gbar, 0, sizeof(cplx) * dd * dd, st) != cudaSuccess) rc = TEBD_ECUDA;
+      }
+    }
+    if (rc) break;
+    // L = Re <O_site> with the Hermitian part of O
+    const int d = C.d[site];
+    std::vector<cplx> oh(d * d);
+    for (int i = 0; i < d; ++i)
+      for (int j = 0; j < d; ++j)
+        oh[i * d + j] = cmk(0.5 * (op[2 * (i * d + j)] + op[2 * (j * d + i)]),
+                            0.5 * (op[2 * (i * d + j) + 1] - op[2 * (j * d + i) + 1]));
+    std::vector<int> ce(N + 1);
+    if (cudaMemcpyAsync(h->op_dev, oh.data(), sizeof(cplx) * d * d, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(ce.data(), C.chi_ext, sizeof(int) * (N + 1), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) { rc = TEBD_ECUDA; break; }
+    // cotangent buffers of site and its bonds: the Gamma block comes first,
+    // then the lambdas in bond order (same layout as tebd_adj_alloc)
+    std::vector<size_t> goff(N), loff(N - 1);
+    size_t off = 0;
+    for (int s = 0; s < N; ++s) { goff[s] = off; off += align_up(sizeof(cplx) * (size_t)C.d[s] * C.cap_ext[s] * C.cap_ext[s + 1]); }
+    for (int b = 0; b < N - 1; ++b) { loff[b] = off; off += align_up(sizeof(double) * C.cap_ext[b + 1]); }
+    char* cb = (char*)h->gbar0;
+    if (launch_adj_expect(C.gamma_ptr[site], d, ce[site], ce[site + 1], C.cap_ext[site], C.cap_ext[site + 1],
+                          C.lam_ptr[site], C.lam_ptr[site + 1], h->op_dev, (cplx*)(cb + goff[site]),
+                          site > 0 ? (double*)(cb + loff[site - 1]) : nullptr,
+                          site < N - 1 ? (double*)(cb + loff[site]) : nullptr, st) != cudaSuccess) { rc = TEBD_ECUDA; break; }
+    for (int k = (int)h->ckpts.size() - 1; k >= 0 && rc == TEBD_OK; --k) {
+      const tebd_s::Ckpt& ck = h->ckpts[k];
+      const uint64_t sw = (uint64_t)ck.sweep;
+      if (cudaMemcpyAsync(region, ck.buf, rbytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+          cudaMemcpyAsync(h->sweep_dev, &sw, sizeof sw, cudaMemcpyHostToDevice, st) != cudaSuccess) { rc = TEBD_ECUDA; break; }
+      ParitySet& ps = h->par[ck.parity];
+      for (const Wave& w : ps.waves) {
+        Dims* dims = ps.dims + w.first;
+        ProbPtr* ptrs = ps.ptrs + w.first;
+        AdjPtr* adj = h->adj_dev[ck.parity] + w.first;
+        const bool tuned = w.tiles[0] != 0;
+        if (launch_plan(ptrs, dims, w.count, h->p, st) != cudaSuccess ||
+            launch_theta(dims, ptrs, w.count, w.cap, st, 1) != cudaSuccess ||
+            launch_adj_keep_theta(dims, ptrs, adj, w.count, st) != cudaSuccess ||
+            launch_theta(dims, ptrs, w.count, w.cap, st) != cudaSuccess ||
+            run_rrsvd(dims, ptrs, w.count, w.cap, h->q, h->seed, 0, 0, -1, h->status, st, h->sweep_dev,
+                      tuned ? w.tiles : nullptr) != cudaSuccess ||
+            launch_rebuild(dims, ptrs, w.count, h->cutoff, h->wout + w.first, h->status, st) != cudaSuccess ||
+            launch_adj_bond(dims, ptrs, adj, w.count, region, region + rbytes, ck.buf, h->cutoff, 1e-12, 1e-20,
+                            st) != cudaSuccess ||
+            launch_adj_accum(dims, adj, w.count, st) != cudaSuccess) { rc = TEBD_ECUDA; break; }
+      }
+    }
+    if (rc) break;
+    // gate cotangents, summed over the applications of each parity
+    for (int par = 0; par < 2 && rc == TEBD_OK; ++par) {
+      double* out = par == 0 ? dgates_even : dgates_odd;
+      if (!out) continue;
+      std::vector<AdjPtr> hp(h->par[par].bonds.size());
+      if (!hp.empty() && cudaMemcpy(hp.data(), h->adj_dev[par], sizeof(AdjPtr) * hp.size(), cudaMemcpyDeviceToHost) != cudaSuccess) { rc = TEBD_ECUDA; break; }
+      size_t o = 0;
+      std::vector<size_t> boff(N - 1);
+      for (int b = 0; b < N - 1; ++b) { boff[b] = o; o += 2 * (size_t)C.d[b] * C.d[b + 1] * C.d[b] * C.d[b + 1]; }
+      memset(out, 0, sizeof(double) * o);
+      for (size_t i = 0; i < hp.size(); ++i) {
+        const int b = h->par[par].bonds[i].second;
+        const size_t dd = (size_t)C.d[b] * C.d[b + 1];
+        if (cudaMemcpy(out + boff[b], hp[i].Gbar, sizeof(cplx) * dd * dd, cudaMemcpyDeviceToHost) != cudaSuccess) { rc = TEBD_ECUDA; break; }
+      }
+    }
+  } while (0);
+  // restore the forward state whatever happened above
+  cudaMemcpyAsync(region, save, rbytes, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(h->sweep_dev, save + rbytes, sizeof(uint64_t), cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(h->wacc, save + rbytes + ALIGN, sizeof(double) * 2 * h->ch.size(), cudaMemcpyDeviceToDevice, st);
+  const cudaError_t e = cudaStreamSynchronize(st);
+  cudaFree(save);
+  if (rc == TEBD_OK && e != cudaSuccess) rc = TEBD_ECUDA;
+  if (rc != TEBD_OK) {
+    h->err.set(rc, "reverse pass failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return h->err.code;
+  }
+  return tebd_check_status(h);
 }
 
 extern "C" const char* tebd_last_error(tebd_t h) { return h ? h->err.msg.c_str() : "NULL handle"; }

@@ -93,7 +93,9 @@ cudaError_t launch_qr(int stage, const Dims* dims, const ProbPtr* ptrs, int batc
                       int only_flagged = 0);
 cudaError_t launch_jacobi(const Dims* dims, const ProbPtr* ptrs, int batch, int* status, cudaStream_t st);
 cudaError_t launch_frob2(const Dims* dims, const ProbPtr* ptrs, int batch, cudaStream_t st);
-cudaError_t launch_theta(const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, cudaStream_t st);
+// identity_gate = 1 writes the pre-gate theta (reverse pass)
+cudaError_t launch_theta(const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, cudaStream_t st,
+                         int identity_gate = 0);
 
 // standalone RRSVD epilogue: sigma/U/Vh/w/rank into caller buffers
 cudaError_t launch_rrsvd_finalize(const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, double cutoff,

@@ -55,7 +55,8 @@ cudaError_t launch_plan(const ProbPtr* ptrs, Dims* dims, int batch, int p, cudaS
 // ---------------------------------------------------------------------------
 enum { TH_TK = 16, TH_MAXR = 64 };
 
-__global__ void __launch_bounds__(256) k_theta(const Dims* __restrict__ dims, const ProbPtr* __restrict__ ptrs) {
+__global__ void __launch_bounds__(256) k_theta(const Dims* __restrict__ dims, const ProbPtr* __restrict__ ptrs,
+                                               int identity_gate) {
   extern __shared__ cplx th_sm[];
   const int p = blockIdx.z;
   const Dims D = dims[p];
@@ -129,13 +130,17 @@ __global__ void __launch_bounds__(256) k_theta(const Dims* __restrict__ dims, co
     const int i = ri / ta, a = ri % ta, j = ci / tb, c = ci % tb;
     const cplx* grow = P.gate + (int64_t)(i * dr + j) * dd;
     cplx v = cmk(0.0, 0.0);
-    for (int ip = 0; ip < dl; ++ip)
-      for (int jp = 0; jp < dr; ++jp) cfma(v, grow[ip * dr + jp], Cs[(ip * ta + a) * cols + jp * tb + c]);
+    if (identity_gate)
+      v = Cs[(i * ta + a) * cols + j * tb + c];
+    else
+      for (int ip = 0; ip < dl; ++ip)
+        for (int jp = 0; jp < dr; ++jp) cfma(v, grow[ip * dr + jp], Cs[(ip * ta + a) * cols + jp * tb + c]);
     th[(int64_t)(i * cl + a0 + a) * D.n + j * cr + b0 + c] = v;
   }
 }
 
-cudaError_t launch_theta(const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, cudaStream_t st) {
+cudaError_t launch_theta(const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, cudaStream_t st,
+                         int identity_gate) {
   const int TA = (cap.dl >= 32) ? 1 : 32 / cap.dl;
   const int TB = (cap.dr >= 32) ? 1 : 32 / cap.dr;
   dim3 grid((cap.cr + TB - 1) / TB, (cap.cl + TA - 1) / TA, batch);
@@ -146,7 +151,7 @@ cudaError_t launch_theta(const Dims* dims, const ProbPtr* ptrs, int batch, const
     attr_set = true;
   }
   ProfScope ps("k_theta", st);
-  k_theta<<<grid, 256, smem, st>>>(dims, ptrs);
+  k_theta<<<grid, 256, smem, st>>>(dims, ptrs, identity_gate);
   return cudaGetLastError();
 }
 
