@@ -204,8 +204,8 @@ int tebd_record(tebd_t h, int on);
  * dL = Re sum conj(G_bar) dG.  Each recorded sweep is recomputed from its
  * checkpoint, then its bond updates are differentiated in reverse: the
  * Vidal extraction, the renormalisation, the truncated SVD the RRSVD
- * approximates (Omega held fixed; 1/(s_j^2 - s_i^2) broadened with 1e-12,
- * 1/s with 1e-20; the coupling to discarded singular vectors is neglected),
+ * approximates (Omega held fixed; 1/(s_j^2 - s_i^2) and 1/s broadened as
+ * x/(x^2 + 1e-24); the coupling to discarded singular vectors is neglected),
  * the gate and the contraction.  The forward state, sweep counter and
  * discarded weights are restored afterwards.  Synchronises.
  * Errors: TEBD_EINVAL, TEBD_ESTATE (nothing recorded), TEBD_ENOTIMPL

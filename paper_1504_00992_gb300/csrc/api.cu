@@ -987,7 +987,7 @@ extern "C" int tebd_backward(tebd_t h, int site, const double* op, double* dgate
             run_rrsvd(dims, ptrs, w.count, w.cap, h->q, h->seed, 0, 0, -1, h->status, st, h->sweep_dev,
                       tuned ? w.tiles : nullptr) != cudaSuccess ||
             launch_rebuild(dims, ptrs, w.count, h->cutoff, h->wout + w.first, h->status, st) != cudaSuccess ||
-            launch_adj_bond(dims, ptrs, adj, w.count, region, region + rbytes, ck.buf, h->cutoff, 1e-12, 1e-20,
+            launch_adj_bond(dims, ptrs, adj, w.count, region, region + rbytes, ck.buf, h->cutoff, 1e-24, 1e-24,
                             st) != cudaSuccess ||
             launch_adj_accum(dims, adj, w.count, st) != cudaSuccess) { rc = TEBD_ECUDA; break; }
       }
