@@ -62,6 +62,29 @@ def dist_env():
     return rank, world, local
 
 
+def replica_offset(rank):
+    """First Philox chain index of a rank's instances: ranks draw disjoint
+    ranges (replicas share no data; there is no exchange between them)."""
+    return rank * 10_000_000
+
+
+def max_over_ranks(x, world, device=None):
+    """The slowest rank's value (whole-job timing); identity for one rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = device if (device is not None and dist.get_backend() == "nccl") else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, seconds):
+    """Units processed by all ranks divided by the slowest rank's time."""
+    return units_per_rank * world / seconds
+
+
 def flops_rrsvd(m, n, k, l, q):
     """Algorithmic flops of one RRSVD truncation (complex MAC = 8 flop)."""
     gemm = (2 * q + 2) * 8.0 * m * n * l                      # A Omega, q x (A^H Q, A Q~), A^H Q for B^H
@@ -202,7 +225,7 @@ def measure(B, torch, dev, theta, sig, batch, prec, args, rank, world, local):
     rk = torch.zeros(batch, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
     sp = stream.cuda_stream
-    inst0 = rank * 10_000_000
+    inst0 = replica_offset(rank)
 
     def step(s):
         B.rrsvd_execute(plan, theta.data_ptr(), inst0 + s * batch, sg.data_ptr(), U.data_ptr(), Vh.data_ptr(),
@@ -238,14 +261,12 @@ def measure(B, torch, dev, theta, sig, batch, prec, args, rank, world, local):
     B.tebd_profiler_enable(False)
     prof = B.tebd_profiler_read()
     clocks = sampler.stop()
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dev)
     B.rrsvd_plan_destroy(plan)
     del ws, U, Vh
     torch.cuda.empty_cache()
-    return {"prec": prec, "code": code, "value": args.steps * batch * world / (ms / 1e3), "ms": ms, "prof": prof,
+    return {"prec": prec, "code": code, "value": whole_job_rate(args.steps * batch, world, ms / 1e3), "ms": ms,
+            "prof": prof,
             "clocks": clocks, "sig_err": sig_err, "excess_err": float(excess), "k": k, "l": l}
 
 
@@ -261,7 +282,7 @@ def e2e_measure(B, torch, theta, batch, code, args, rank, world):
     w_h = torch.empty(batch, dtype=torch.float64, pin_memory=True)
     rk_h = torch.empty(batch, dtype=torch.int32, pin_memory=True)
     sp = torch.cuda.current_stream().cuda_stream
-    inst0 = rank * 10_000_000 + 5_000_000
+    inst0 = replica_offset(rank) + 5_000_000
     hp = B.rrsvd_plan_create(M, N_, K_MAX, P_OS, Q_PI, batch, code, SEED)
     B.rrsvd_execute_host(hp, th_h.numpy(), inst0, sg_h.numpy(), U_h.numpy(), Vh_h.numpy(), w_h.numpy(),
                          rk_h.numpy(), sp)   # first call allocates the staging buffers
@@ -271,15 +292,12 @@ def e2e_measure(B, torch, theta, batch, code, args, rank, world):
     for s in range(args.e2e_steps):
         B.rrsvd_execute_host(hp, th_h.numpy(), inst0 + (s + 1) * batch, sg_h.numpy(), U_h.numpy(), Vh_h.numpy(),
                              w_h.numpy(), rk_h.numpy(), sp)
-    el = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([el], dtype=torch.float64, device=theta.device)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        el = float(t.item())
+    el = max_over_ranks(time.perf_counter() - t0, world, theta.device)
     B.rrsvd_plan_destroy(hp)
     bi = th_h.numel() * 16
     bo = sg_h.numel() * 8 + U_h.numel() * 16 + Vh_h.numel() * 16 + w_h.numel() * 8 + rk_h.numel() * 4
-    return {"value": args.e2e_steps * batch * world / el, "unit": "bond updates/s", "h2d_bytes_per_step": bi,
+    return {"value": whole_job_rate(args.e2e_steps * batch, world, el), "unit": "bond updates/s",
+            "h2d_bytes_per_step": bi,
             "d2h_bytes_per_step": bo}
 
 
