@@ -122,6 +122,10 @@ cudaError_t launch_finalize_checked(const Dims* dims, const ProbPtr* ptrs, int b
                                     cudaStream_t st);
 cudaError_t launch_checked_init(Dims* dims, int batch, const Dims& tmpl, cudaStream_t st);
 
+// Double-float (FP32-pair) variant of the FP64 GEMM for G_BH, G_U, G_V.
+cudaError_t launch_zgemm_df(int stage, const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap,
+                            cudaStream_t st);
+
 // GEMM tile choice per stage (16 or 32); tiles == nullptr picks by grid size.
 cudaError_t launch_zgemm_tile(int stage, int tile, const Dims* dims, const ProbPtr* ptrs, int batch,
                               const Caps& cap, cudaStream_t st);

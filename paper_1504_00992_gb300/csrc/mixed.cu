@@ -6,7 +6,9 @@
 //   power round q (Y0 if q = 0)            : the refinement pass, 3xTF32 split
 //                                           products (FP32-level accuracy);
 //   last QR                                : FP64 Householder;
-//   B^H = A^H Q, QR of B^H, Jacobi SVD, U, V: FP64 (the existing kernels).
+//   B^H = A^H Q, U = Q J_k, V = Qb W_k      : double-float GEMM on the FP32 pipes
+//                                           (FP32 pairs, ~1e-12 relative);
+//   QR of B^H, Jacobi SVD                   : FP64 (the existing kernels).
 //
 // Complex products use the real embedding: A (M x K complex) becomes the
 // M x 2K real matrix of interleaved (Re, Im) entries, and X (K x l complex)
@@ -418,11 +420,11 @@ cudaError_t run_rrsvd_mixed(const Dims* dims, const ProbPtr* ptrs, int batch, co
     MX_TRY(cudaGetLastError());
   }
   MX_TRY(launch_qr(QR_Y, dims, ptrs, batch, st));           // last QR in FP64
-  MX_TRY(launch_zgemm(G_BH, dims, ptrs, batch, cap, st));   // B^H = A^H Q (FP64)
+  MX_TRY(launch_zgemm_df(G_BH, dims, ptrs, batch, cap, st));   // B^H = A^H Q (double-float)
   MX_TRY(launch_qr(QR_BH, dims, ptrs, batch, st));
   MX_TRY(launch_jacobi(dims, ptrs, batch, status, st));
-  MX_TRY(launch_zgemm(G_U, dims, ptrs, batch, cap, st));
-  MX_TRY(launch_zgemm(G_V, dims, ptrs, batch, cap, st));
+  MX_TRY(launch_zgemm_df(G_U, dims, ptrs, batch, cap, st));
+  MX_TRY(launch_zgemm_df(G_V, dims, ptrs, batch, cap, st));
   MX_TRY(launch_frob2(dims, ptrs, batch, st));
   return cudaSuccess;
 }

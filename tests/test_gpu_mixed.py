@@ -10,7 +10,8 @@ oracle, so it is held to the FP64 method's accuracy, not to its rounding
   * excess error (||A - A_k||_F - ||A - A_k(exact)||_F) / ||A||_F no more
     than 1e-8 above the oracle's;
   * where the FP64 method meets the 1e-8 bar, the mixed form meets it too;
-  * the returned factors are orthonormal to 1e-12 (FP64 last QR and Jacobi).
+  * the returned factors are orthonormal to 1e-11 (FP64 last QR and Jacobi,
+    double-float U = Q J_k and V = Qb W_k).
 """
 import numpy as np
 import pytest
@@ -57,9 +58,9 @@ def test_mixed_form_meets_its_tolerances(lib, m, n, k, p, q, scale):
         exc_m = (np.linalg.norm(A - truncated(res["U"][t], s, res["Vh"][t])) - opt) / nA
         assert exc_m <= exc_o + 1e-8
         U = res["U"][t]
-        assert np.abs(U.conj().T @ U - np.eye(kk)).max() < 1e-12
+        assert np.abs(U.conj().T @ U - np.eye(kk)).max() < 1e-11
         V = res["Vh"][t]
-        assert np.abs(V @ V.conj().T - np.eye(kk)).max() < 1e-12
+        assert np.abs(V @ V.conj().T - np.eye(kk)).max() < 1e-11
         assert abs(res["w"][t] - w) <= 1e-8 + abs(w - (np.sum(sig[kk:] ** 2) / np.sum(sig ** 2)))
 
 
