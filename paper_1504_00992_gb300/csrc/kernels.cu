@@ -356,8 +356,10 @@ cudaError_t launch_zgemm(int stage, const Dims* dims, const ProbPtr* ptrs, int b
 // ---------------------------------------------------------------------------
 enum { QR_MAXL = 512 };
 
+enum { QR_THREADS = 1024, JAC_THREADS = 512 };
+
 template <int QS>
-__global__ void __launch_bounds__(256) k_qr(const Dims* __restrict__ dims, const ProbPtr* __restrict__ ptrs,
+__global__ void __launch_bounds__(QR_THREADS) k_qr(const Dims* __restrict__ dims, const ProbPtr* __restrict__ ptrs,
                                             int only_flagged) {
   __shared__ double red[32];
   __shared__ double tau[QR_MAXL];
@@ -444,9 +446,9 @@ cudaError_t launch_qr(int stage, const Dims* dims, const ProbPtr* ptrs, int batc
                       int only_flagged) {
   ProfScope ps("k_qr", st);
   switch (stage) {
-    case QR_Y: k_qr<QR_Y><<<batch, 256, 0, st>>>(dims, ptrs, only_flagged); break;
-    case QR_YT: k_qr<QR_YT><<<batch, 256, 0, st>>>(dims, ptrs, only_flagged); break;
-    case QR_BH: k_qr<QR_BH><<<batch, 256, 0, st>>>(dims, ptrs, only_flagged); break;
+    case QR_Y: k_qr<QR_Y><<<batch, QR_THREADS, 0, st>>>(dims, ptrs, only_flagged); break;
+    case QR_YT: k_qr<QR_YT><<<batch, QR_THREADS, 0, st>>>(dims, ptrs, only_flagged); break;
+    case QR_BH: k_qr<QR_BH><<<batch, QR_THREADS, 0, st>>>(dims, ptrs, only_flagged); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -469,8 +471,8 @@ cudaError_t launch_qr(int stage, const Dims* dims, const ProbPtr* ptrs, int batc
 // ---------------------------------------------------------------------------
 enum { JAC_MAXSWEEPS = 60 };
 
-__global__ void __launch_bounds__(256) k_jacobi(const Dims* __restrict__ dims, const ProbPtr* __restrict__ ptrs,
-                                                int* status) {
+__global__ void __launch_bounds__(JAC_THREADS) k_jacobi(const Dims* __restrict__ dims,
+                                                        const ProbPtr* __restrict__ ptrs, int* status) {
   __shared__ double sv[QR_MAXL];
   __shared__ double nrm[QR_MAXL];
   __shared__ int perm[QR_MAXL];
@@ -585,7 +587,7 @@ __global__ void __launch_bounds__(256) k_jacobi(const Dims* __restrict__ dims, c
 
 cudaError_t launch_jacobi(const Dims* dims, const ProbPtr* ptrs, int batch, int* status, cudaStream_t st) {
   ProfScope ps("k_jacobi", st);
-  k_jacobi<<<batch, 256, 0, st>>>(dims, ptrs, status);
+  k_jacobi<<<batch, JAC_THREADS, 0, st>>>(dims, ptrs, status);
   return cudaGetLastError();
 }
 

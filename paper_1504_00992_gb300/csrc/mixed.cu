@@ -173,7 +173,7 @@ __device__ __forceinline__ float fwarp_sum(float v) {
   return v;
 }
 
-__global__ void __launch_bounds__(256) k_qr_f32(float2* Abase, float2* Qbase, int M, int L) {
+__global__ void __launch_bounds__(1024) k_qr_f32(float2* Abase, float2* Qbase, int M, int L) {
   __shared__ float red[32];
   __shared__ float tau[512];
   const int z = blockIdx.x;
@@ -371,7 +371,7 @@ static cudaError_t tc_product(const float* A0, const float* A1, const float* B0,
 
 static cudaError_t qr_f32(float2* A, float2* Q, int M, int L, int batch, cudaStream_t st) {
   ProfScope ps("k_qr_f32", st);
-  k_qr_f32<<<batch, 256, 0, st>>>(A, Q, M, L);
+  k_qr_f32<<<batch, 1024, 0, st>>>(A, Q, M, L);
   return cudaGetLastError();
 }
 
