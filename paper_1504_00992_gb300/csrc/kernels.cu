@@ -204,8 +204,10 @@ static cudaError_t launch_zgemm_stage(int rows, int cols, const Dims* dims, cons
 // x y is formed error-free up to the cross terms, p = xh yh exactly split by
 // FMA into (ph, pe), plus xh yl + xl yh; sums use Knuth's TwoSum on the high
 // parts with the error terms gathered in a low accumulator (Dekker 1971;
-// Knuth TAOCP vol. 2, 4.2.2).  GB300 runs FP32 at 64x its FP64 rate, so this
-// is several times faster than DFMA at ~1e-12 relative accuracy for K ~ 2000.
+// Knuth TAOCP vol. 2, 4.2.2); every 16-deep slice of the sum is accumulated
+// afresh and merged with a renormalising add, which keeps the error near u^2
+// (~1e-14 relative) instead of K u^2.  GB300 runs FP32 at 64x its FP64 rate,
+// so this is several times faster than DFMA.
 // ---------------------------------------------------------------------------
 struct df2 { float h, l; };
 
@@ -224,6 +226,17 @@ __device__ __forceinline__ void df_fma(df2& acc, float xh, float xl, float yh, f
   const float e = (acc.h - (t - z)) + (ph - z);
   acc.h = t;
   acc.l += e + pe + pc;
+}
+
+// acc += part, renormalised (Dekker's add), so the low word stays below one
+// ulp of the high word over long sums.
+__device__ __forceinline__ void df_merge(df2& acc, df2 part) {
+  const float s = acc.h + part.h;
+  const float v = s - acc.h;
+  float e = (acc.h - (s - v)) + (part.h - v);
+  e += acc.l + part.l;
+  acc.h = s + e;
+  acc.l = e - (acc.h - s);
 }
 
 template <int STAGE>
@@ -272,6 +285,12 @@ __global__ void __launch_bounds__(256) k_zgemm_df(const Dims* __restrict__ dims,
       Bs[kk][c] = f;
     }
     __syncthreads();
+    // each TK-deep slice is summed afresh and merged into the running sums
+    df2 pr[S][S], pi[S][S];
+#pragma unroll
+    for (int i = 0; i < S; ++i)
+#pragma unroll
+      for (int j = 0; j < S; ++j) { pr[i][j] = {0.f, 0.f}; pi[i][j] = {0.f, 0.f}; }
 #pragma unroll 2
     for (int kk = 0; kk < TK; ++kk) {
       float4 a[S], b[S];
@@ -284,12 +303,19 @@ __global__ void __launch_bounds__(256) k_zgemm_df(const Dims* __restrict__ dims,
 #pragma unroll
         for (int j = 0; j < S; ++j) {
           // re += ar br - ai bi ; im += ar bi + ai br
-          df_fma(ar[i][j], a[i].x, a[i].y, b[j].x, b[j].y);
-          df_fma(ar[i][j], -a[i].z, -a[i].w, b[j].z, b[j].w);
-          df_fma(ai[i][j], a[i].x, a[i].y, b[j].z, b[j].w);
-          df_fma(ai[i][j], a[i].z, a[i].w, b[j].x, b[j].y);
+          df_fma(pr[i][j], a[i].x, a[i].y, b[j].x, b[j].y);
+          df_fma(pr[i][j], -a[i].z, -a[i].w, b[j].z, b[j].w);
+          df_fma(pi[i][j], a[i].x, a[i].y, b[j].z, b[j].w);
+          df_fma(pi[i][j], a[i].z, a[i].w, b[j].x, b[j].y);
         }
     }
+#pragma unroll
+    for (int i = 0; i < S; ++i)
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        df_merge(ar[i][j], pr[i][j]);
+        df_merge(ai[i][j], pi[i][j]);
+      }
     __syncthreads();
   }
 #pragma unroll
@@ -463,13 +489,23 @@ cudaError_t launch_qr(int stage, const Dims* dims, const ProbPtr* ptrs, int batc
 // instead of 11-17 on decaying spectra.  Columns whose squared norm is below
 // (L eps)^2 ||X||_F^2 are treated as zero: rotating them only chases rounding
 // noise, and they lie far below the kept-value cutoff.  Pairs follow the
-// round-robin (circle) ordering, L/2 disjoint pairs per round, one warp per
-// pair.  With X J = W S:  Rb = J S W^H, so B = W S (Qb J)^H, i.e.
+// round-robin (circle) ordering, L/2 disjoint pairs per round, one group of
+// JAC_G = 8 lanes per pair (four pairs per warp): the FP64 square roots and
+// divisions of each rotation are then repeated on 8 lanes rather than 32,
+// which halves the FP64-pipe work of a sweep.  With X J = W S:
+// Rb = J S W^H, so B = W S (Qb J)^H, i.e.
 // U~ = W (normalised columns of X J) and V = Qb J.
 // Output: sigma sorted descending (ties by lower index), Jk = the leading k
 // columns of W (for U = Q Jk), Wk = the matching columns of J (for V = Qb Wk).
 // ---------------------------------------------------------------------------
-enum { JAC_MAXSWEEPS = 60 };
+enum { JAC_MAXSWEEPS = 60, JAC_G = 8 };
+
+// sum over the JAC_G lanes of this lane's group (the group's lanes all call it)
+__device__ __forceinline__ double grp_sum(double v, unsigned mask) {
+#pragma unroll
+  for (int o = JAC_G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
+  return v;
+}
 
 __global__ void __launch_bounds__(JAC_THREADS) k_jacobi(const Dims* __restrict__ dims,
                                                         const ProbPtr* __restrict__ ptrs, int* status) {
@@ -486,6 +522,9 @@ __global__ void __launch_bounds__(JAC_THREADS) k_jacobi(const Dims* __restrict__
   cplx* X = P.R;
   cplx* J = P.J;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int gl = lane & (JAC_G - 1);                      // lane within its group
+  const int grp = tid / JAC_G, ngrp = blockDim.x / JAC_G;  // group index, groups per CTA
+  const unsigned gmask = ((1u << JAC_G) - 1u) << (lane & ~(JAC_G - 1));
   double f2 = 0.0;
   for (int e = tid; e < L * L; e += blockDim.x) {
     J[e] = cmk((e / L) == (e % L) ? 1.0 : 0.0, 0.0);
@@ -510,40 +549,42 @@ __global__ void __launch_bounds__(JAC_THREADS) k_jacobi(const Dims* __restrict__
     if (tid == 0) rotated = 0;
     __syncthreads();
     for (int rnd = 0; rnd < Lp - 1; ++rnd) {
-      for (int pi = warp; pi < Lp / 2; pi += nw) {
+      for (int pi = grp; pi < Lp / 2; pi += ngrp) {
         int a, b;
         if (pi == 0) { a = Lp - 1; b = rnd; }
         else { a = (rnd + pi) % (Lp - 1); b = (rnd - pi + (Lp - 1)) % (Lp - 1); }
         if (a > b) { const int t = a; a = b; b = t; }
-        if (b >= L) continue;
+        if (b >= L) continue;  // uniform over the group
         cplx* xa = X + (int64_t)a * L;
         cplx* xb = X + (int64_t)b * L;
         const double aa = nrm[a], bb = nrm[b];
         if (aa <= small || bb <= small) continue;
         cplx g = cmk(0.0, 0.0);
-        for (int r = lane; r < L; r += 32) cfma_conj(g, xa[r], xb[r]);
-        g = warp_sum(g);
-        const double ag = sqrt(cabs2(g));
-        if (!(ag > tol * sqrt(aa * bb)) || ag == 0.0) continue;
+        for (int r = gl; r < L; r += JAC_G) cfma_conj(g, xa[r], xb[r]);
+        g.x = grp_sum(g.x, gmask);
+        g.y = grp_sum(g.y, gmask);
+        const double ag2 = cabs2(g);
+        if (!(ag2 > tol * tol * (aa * bb)) || ag2 == 0.0) continue;
+        const double ag = sqrt(ag2);
         // rotation: x_a' = c x_a - s e* x_b, x_b' = s e x_a + c x_b, e = g/|g|
         const cplx e = cscale(g, 1.0 / ag);
         const double zeta = (bb - aa) / (2.0 * ag);
         const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
         const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
         const cplx se = cscale(e, s), sec = cconj(se);
-        for (int r = lane; r < L; r += 32) {
+        for (int r = gl; r < L; r += JAC_G) {
           const cplx u = xa[r], v = xb[r];
           xa[r] = csub(cscale(u, c), cmul(sec, v));
           xb[r] = cadd(cmul(se, u), cscale(v, c));
         }
         cplx* ja = J + (int64_t)a * L;
         cplx* jb = J + (int64_t)b * L;
-        for (int r = lane; r < L; r += 32) {
+        for (int r = gl; r < L; r += JAC_G) {
           const cplx u = ja[r], v = jb[r];
           ja[r] = csub(cscale(u, c), cmul(sec, v));
           jb[r] = cadd(cmul(se, u), cscale(v, c));
         }
-        if (lane == 0) {
+        if (gl == 0) {
           nrm[a] = aa - t * ag;
           nrm[b] = bb + t * ag;
           rotated = 1;

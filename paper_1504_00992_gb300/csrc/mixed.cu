@@ -2,12 +2,16 @@
 // cores, then the FP64 projection and small SVD of Section IV.
 //
 //   Y0 = A Omega and power rounds 1..q-1  : TF32 tensor-core products (FP32
-//                                           accumulation), FP32 Householder QR;
+//                                           accumulation), FP32 Householder QR
+//                                           (blocked when it fits in shared memory);
 //   power round q (Y0 if q = 0)            : the refinement pass, 3xTF32 split
 //                                           products (FP32-level accuracy);
-//   last QR                                : FP64 Householder;
+//   last QR                                : FP32 blocked Householder and an
+//                                           FP64-accurate re-orthonormalisation
+//                                           (qr_blocked.cu), or FP64 Householder
+//                                           when l > 128;
 //   B^H = A^H Q, U = Q J_k, V = Qb W_k      : double-float GEMM on the FP32 pipes
-//                                           (FP32 pairs, ~1e-12 relative);
+//                                           (FP32 pairs, ~1e-14 relative);
 //   QR of B^H, Jacobi SVD                   : FP64 (the existing kernels).
 //
 // Complex products use the real embedding: A (M x K complex) becomes the
@@ -300,6 +304,7 @@ MixedSizes mixed_sizes(int m, int n, int k, int l) {
   s.bt = (size_t)s.Np * Kmax * f;
   s.yf = (size_t)m * l * sizeof(float2);
   s.ytf = (size_t)n * l * sizeof(float2);
+  s.df = (size_t)l * l * sizeof(float2);
   (void)k;
   return s;
 }
@@ -308,7 +313,7 @@ static size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 size_t mixed_bytes(const MixedSizes& s, int batch) {
   return 2 * up256(s.thf * batch) + 2 * up256(s.tha * batch) + 2 * up256(s.bt * batch) + 2 * up256(s.yf * batch) +
-         2 * up256(s.ytf * batch);
+         2 * up256(s.ytf * batch) + up256(s.df * batch);
 }
 
 MixedPtrs mixed_carve(char* base, const MixedSizes& s, int batch) {
@@ -324,6 +329,7 @@ MixedPtrs mixed_carve(char* base, const MixedSizes& s, int batch) {
   p.Qf = (float2*)(base + o); o += up256(s.yf * batch);
   p.Ytf = (float2*)(base + o); o += up256(s.ytf * batch);
   p.Qtf = (float2*)(base + o); o += up256(s.ytf * batch);
+  p.Df = (float2*)(base + o); o += up256(s.df * batch);
   return p;
 }
 
@@ -371,6 +377,7 @@ static cudaError_t tc_product(const float* A0, const float* A1, const float* B0,
 
 static cudaError_t qr_f32(float2* A, float2* Q, int M, int L, int batch, cudaStream_t st) {
   ProfScope ps("k_qr_f32", st);
+  if (qr_blk_f32_fits(M, L)) return launch_qr_blk_f32(A, Q, M, L, batch, st);
   k_qr_f32<<<batch, 1024, 0, st>>>(A, Q, M, L);
   return cudaGetLastError();
 }
@@ -414,13 +421,20 @@ cudaError_t run_rrsvd_mixed(const Dims* dims, const ProbPtr* ptrs, int batch, co
     MX_TRY(conv_bt(mp.Qtf, mp, n, l, s.K1, s, np == 3, batch, st));
     MX_TRY(tc_product(mp.thf_hi, mp.thf_lo, mp.bt_hi, mp.bt_lo, m, s.K1, s, l, np, mp.Yf, batch, err, st));  // A Q~
   }
-  {
-    ProfScope ps("k_f32_to_f64", st);
-    k_f32_to_f64<<<dim3(grid1d((int64_t)m * l), batch), 256, 0, st>>>(mp.Yf, ptrs, m, l);
-    MX_TRY(cudaGetLastError());
+  if (reorth_fits(m, l)) {
+    // last QR: FP32 Householder, then the FP64-accurate re-orthonormalisation
+    MX_TRY(qr_f32(mp.Yf, mp.Qf, m, l, batch, st));
+    MX_TRY(launch_reorth(mp.Qf, mp.Df, ptrs, m, l, batch, status, st));
+    MX_TRY(launch_proj_df(ptrs, mp.Qf, mp.Df, m, n, l, batch, st));  // B^H = A^H Q
+  } else {
+    {
+      ProfScope ps("k_f32_to_f64", st);
+      k_f32_to_f64<<<dim3(grid1d((int64_t)m * l), batch), 256, 0, st>>>(mp.Yf, ptrs, m, l);
+      MX_TRY(cudaGetLastError());
+    }
+    MX_TRY(launch_qr(QR_Y, dims, ptrs, batch, st));          // last QR in FP64
+    MX_TRY(launch_zgemm_df(G_BH, dims, ptrs, batch, cap, st));  // B^H = A^H Q (double-float)
   }
-  MX_TRY(launch_qr(QR_Y, dims, ptrs, batch, st));           // last QR in FP64
-  MX_TRY(launch_zgemm_df(G_BH, dims, ptrs, batch, cap, st));   // B^H = A^H Q (double-float)
   MX_TRY(launch_qr(QR_BH, dims, ptrs, batch, st));
   MX_TRY(launch_jacobi(dims, ptrs, batch, status, st));
   MX_TRY(launch_zgemm_df(G_U, dims, ptrs, batch, cap, st));

@@ -13,7 +13,7 @@ struct MixedSizes {
   int K2;        // 2m rounded up to 32: row length of the adjoint copy and of Bt for A^H X
   int Np;        // 2l rounded up to 16: rows of Bt (tensor-core N)
   int BN;        // tensor-core tile width, min(Np, 256)
-  size_t thf, tha, bt, yf, ytf;  // bytes per instance
+  size_t thf, tha, bt, yf, ytf, df;  // bytes per instance
 };
 
 // Batch-major arrays (instance z at base + z * per-instance size).
@@ -28,11 +28,26 @@ struct MixedPtrs {
   float2* Qf;
   float2* Ytf;    // n x l
   float2* Qtf;
+  float2* Df;     // l x l correction of the re-orthonormalisation
 };
 
 MixedSizes mixed_sizes(int m, int n, int k, int l);
 size_t mixed_bytes(const MixedSizes& s, int batch);
 MixedPtrs mixed_carve(char* base, const MixedSizes& s, int batch);
+
+// Blocked FP32 Householder QR (qr_blocked.cu): A (M x L column-major per
+// instance, overwritten) -> Q; usable when qr_blk_f32_fits(M, L).
+bool qr_blk_f32_fits(int M, int L);
+cudaError_t launch_qr_blk_f32(float2* A, float2* Q, int M, int L, int batch, cudaStream_t st);
+// Q_f (FP32, M x L) -> ptrs[z].Q (FP64) orthonormal to ~1e-13, spanning
+// range(Q_f); uses ptrs[z].R as scratch; usable when reorth_fits(M, L).
+bool reorth_fits(int M, int L);
+cudaError_t launch_reorth(const float2* Qf, float2* Dbuf, const ProbPtr* ptrs, int M, int L, int batch, int* status,
+                          cudaStream_t st);
+// B^H = A^H Q_f (I + D) into ptrs[z].Yt (n x l column-major): double-float
+// product with the FP32 Q_f, then the correction; after launch_reorth.
+cudaError_t launch_proj_df(const ProbPtr* ptrs, const float2* Qf, const float2* Dbuf, int m, int n, int l, int batch,
+                           cudaStream_t st);
 
 // Alg. 1 with tensor-core products and the FP64 projection / small SVD;
 // uniform sizes over the batch (cap holds them).

@@ -1,0 +1,750 @@
+// Blocked Householder QR in FP32 and the FP64-accurate re-orthonormalisation
+// of its Q (sm_103a), used by the mixed-precision RRSVD.
+//
+// k_qr_blk_f32: the same reflectors as the unblocked kernels (alpha =
+// -e^{i arg x0} ||x||, v0 = x0 - alpha, tau = 1/(||x|| (||x|| + |x0|)),
+// H = I - tau v v^H), grouped in panels of QB_NB columns (compact WY form,
+// Schreiber & Van Loan 1989; Golub & Van Loan 5.2.3):
+//   H_0 ... H_{nb-1} = I - V T V^H,  T upper triangular,
+//   T[i][i] = tau_i,  T[0:i, i] = -tau_i T[0:i, 0:i] (V[:, 0:i]^H v_i).
+// A panel is factored in shared memory; the trailing columns get
+// A <- A - V T^H (V^H A) in two streaming passes instead of one pass per
+// reflector, and Q = H_0 ... H_{L-1} [I; 0] is accumulated panel by panel
+// backwards with Q <- Q - V T (V^H Q).  One CTA per instance.
+//
+// Re-orthonormalisation: the FP32 Q_f has ||Q_f^H Q_f - I|| ~ 1e-6.  With
+// E = Q_f^H Q_f - I formed exactly enough in double-float arithmetic (FP32
+// products split error-free by FMA, TwoSum accumulation), the symmetric
+// (Loewdin) orthonormalisation Q = Q_f (I + E)^{-1/2} is evaluated from the
+// binomial series (I + E)^{-1/2} = I - E/2 + 3 E^2 / 8 - ..., whose first
+// dropped term is of order ||E||^3 ~ 1e-18.  Q spans range(Q_f) and is
+// orthonormal to ~1e-13: the "last QR in FP64" of the mixed form at FP32 cost.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "internal.cuh"
+#include "mixed.cuh"
+#include "profiler.cuh"
+
+namespace tg {
+
+enum { QB_THREADS = 512, QB_WARPS = QB_THREADS / 32, QB_NB = 8, QB_CW = 4, QB_RED = 64 };
+
+__device__ __forceinline__ float qb_wsum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Shared-memory layout of k_qr_blk_f32 (bytes), shared with the host check.
+__host__ __device__ inline size_t qb_smem_bytes(int M, int L) {
+  const int npan = (L + QB_NB - 1) / QB_NB;
+  return sizeof(float2) * ((size_t)QB_NB * M + 2 * (size_t)QB_NB * L + (size_t)npan * QB_NB * QB_NB) +
+         sizeof(float) * ((size_t)L + QB_WARPS * QB_RED + QB_RED);
+}
+
+// C[j0:M, c0:L) <- C - V op(T) (V^H C), op(T) = T^H (trans) or T.  V holds jb
+// reflectors in shared memory (local row r = global row j0 + r, zero above
+// each reflector's first row).  All threads of the CTA call it.
+__device__ void qb_apply(float2* C, int M, int j0, int jb, int c0, int L, const float2* Vs, int ldv,
+                         const float2* Tp, bool trans, float2* W, float2* W2) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int Mr = M - j0, ncol = L - c0;
+  if (ncol <= 0) return;
+  for (int e = tid; e < QB_NB * ncol; e += QB_THREADS) W[(e / ncol) * L + c0 + e % ncol] = make_float2(0.f, 0.f);
+  __syncthreads();
+  const int ncg = (ncol + QB_CW - 1) / QB_CW;
+  const int rs = ncg >= QB_WARPS ? 1 : QB_WARPS / ncg;
+  const int ntask = ncg * rs;
+  // pass 1: W = V^H C
+  for (int t = warp; t < ntask; t += QB_WARPS) {
+    const int cg = t % ncg, h = t / ncg;
+    const int cb = c0 + cg * QB_CW;
+    const int nc = min(QB_CW, L - cb);
+    float2 acc[QB_NB][QB_CW];
+#pragma unroll
+    for (int i = 0; i < QB_NB; ++i)
+#pragma unroll
+      for (int w = 0; w < QB_CW; ++w) acc[i][w] = make_float2(0.f, 0.f);
+    for (int r = h * 32 + lane; r < Mr; r += 32 * rs) {
+      float2 v[QB_NB];
+#pragma unroll
+      for (int i = 0; i < QB_NB; ++i) v[i] = (i < jb) ? Vs[i * ldv + r] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int w = 0; w < QB_CW; ++w) {
+        if (w < nc) {
+          const float2 a = C[(size_t)(cb + w) * M + j0 + r];
+#pragma unroll
+          for (int i = 0; i < QB_NB; ++i) {
+            acc[i][w].x = fmaf(v[i].x, a.x, fmaf(v[i].y, a.y, acc[i][w].x));
+            acc[i][w].y = fmaf(v[i].x, a.y, fmaf(-v[i].y, a.x, acc[i][w].y));
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < QB_NB; ++i)
+#pragma unroll
+      for (int w = 0; w < QB_CW; ++w) {
+        const float sx = qb_wsum(acc[i][w].x), sy = qb_wsum(acc[i][w].y);
+        if (lane == ((i * QB_CW + w) & 31) && i < jb && w < nc) {
+          atomicAdd(&W[i * L + cb + w].x, sx);
+          atomicAdd(&W[i * L + cb + w].y, sy);
+        }
+      }
+  }
+  __syncthreads();
+  // W2 = op(T) W
+  for (int e = tid; e < jb * ncol; e += QB_THREADS) {
+    const int i = e / ncol, c = c0 + e % ncol;
+    float2 s = make_float2(0.f, 0.f);
+    if (trans) {
+      for (int a = 0; a <= i; ++a) {  // conj(T[a][i]) W[a][c]
+        const float2 t = Tp[a * QB_NB + i], w = W[a * L + c];
+        s.x = fmaf(t.x, w.x, fmaf(t.y, w.y, s.x));
+        s.y = fmaf(t.x, w.y, fmaf(-t.y, w.x, s.y));
+      }
+    } else {
+      for (int b = i; b < jb; ++b) {  // T[i][b] W[b][c]
+        const float2 t = Tp[i * QB_NB + b], w = W[b * L + c];
+        s.x = fmaf(t.x, w.x, fmaf(-t.y, w.y, s.x));
+        s.y = fmaf(t.x, w.y, fmaf(t.y, w.x, s.y));
+      }
+    }
+    W2[i * L + c] = s;
+  }
+  __syncthreads();
+  // pass 2: C -= V W2
+  for (int t = warp; t < ntask; t += QB_WARPS) {
+    const int cg = t % ncg, h = t / ncg;
+    const int cb = c0 + cg * QB_CW;
+    const int nc = min(QB_CW, L - cb);
+    float2 w2[QB_NB][QB_CW];
+#pragma unroll
+    for (int i = 0; i < QB_NB; ++i)
+#pragma unroll
+      for (int w = 0; w < QB_CW; ++w)
+        w2[i][w] = (i < jb && w < nc) ? W2[i * L + cb + w] : make_float2(0.f, 0.f);
+    for (int r = h * 32 + lane; r < Mr; r += 32 * rs) {
+      float2 v[QB_NB];
+#pragma unroll
+      for (int i = 0; i < QB_NB; ++i) v[i] = (i < jb) ? Vs[i * ldv + r] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int w = 0; w < QB_CW; ++w) {
+        if (w < nc) {
+          float2* cp = C + (size_t)(cb + w) * M + j0 + r;
+          float2 a = *cp;
+#pragma unroll
+          for (int i = 0; i < QB_NB; ++i) {
+            a.x = fmaf(-v[i].x, w2[i][w].x, fmaf(v[i].y, w2[i][w].y, a.x));
+            a.y = fmaf(-v[i].x, w2[i][w].y, fmaf(-v[i].y, w2[i][w].x, a.y));
+          }
+          *cp = a;
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// A: M x L column-major per instance (overwritten by R and the reflectors);
+// Q: M x L column-major output.  Requires M >= L and qb_smem_bytes(M, L) of
+// dynamic shared memory.
+__global__ void __launch_bounds__(QB_THREADS) k_qr_blk_f32(float2* Abase, float2* Qbase, int M, int L) {
+  extern __shared__ __align__(16) unsigned char qb_raw[];
+  const int ldv = M;
+  const int npan = (L + QB_NB - 1) / QB_NB;
+  float2* Vs = reinterpret_cast<float2*>(qb_raw);
+  float2* W = Vs + (size_t)QB_NB * ldv;
+  float2* W2 = W + QB_NB * L;
+  float2* Tall = W2 + QB_NB * L;
+  float* tau = reinterpret_cast<float*>(Tall + npan * QB_NB * QB_NB);
+  float* red = tau + L;
+  float* fin = red + QB_WARPS * QB_RED;
+  const int z = blockIdx.x;
+  float2* A = Abase + (size_t)z * M * L;
+  float2* Qo = Qbase + (size_t)z * M * L;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  for (int p = 0; p < npan; ++p) {
+    const int j0 = p * QB_NB, jb = min(QB_NB, L - j0), Mr = M - j0;
+    for (int e = tid; e < jb * Mr; e += QB_THREADS) {
+      const int i = e / Mr, r = e % Mr;
+      Vs[i * ldv + r] = A[(size_t)(j0 + i) * M + j0 + r];
+    }
+    __syncthreads();
+    // --- panel factorisation in shared memory
+    for (int i = 0; i < jb; ++i) {
+      const int j = j0 + i;
+      float s = 0.f;
+      for (int r = i + tid; r < Mr; r += QB_THREADS) {
+        const float2 v = Vs[i * ldv + r];
+        s = fmaf(v.x, v.x, fmaf(v.y, v.y, s));
+      }
+      s = qb_wsum(s);
+      if (lane == 0) red[warp] = s;
+      __syncthreads();
+      if (tid == 0) {
+        float t = 0.f;
+        for (int w = 0; w < QB_WARPS; ++w) t += red[w];
+        const float2 x0 = Vs[i * ldv + i];
+        const float ax0 = sqrtf(x0.x * x0.x + x0.y * x0.y), nx = sqrtf(t);
+        if (nx == 0.f) {
+          tau[j] = 0.f;
+        } else {
+          const float2 ph = (ax0 > 0.f) ? make_float2(x0.x / ax0, x0.y / ax0) : make_float2(1.f, 0.f);
+          Vs[i * ldv + i] = make_float2(ph.x * (ax0 + nx), ph.y * (ax0 + nx));
+          tau[j] = 1.f / (nx * (nx + ax0));
+        }
+      }
+      __syncthreads();
+      const float tj = tau[j];
+      const int nc = jb - 1 - i;
+      if (tj != 0.f && nc > 0) {
+        float2 acc[QB_NB - 1];
+#pragma unroll
+        for (int c = 0; c < QB_NB - 1; ++c) acc[c] = make_float2(0.f, 0.f);
+        for (int r = i + tid; r < Mr; r += QB_THREADS) {
+          const float2 v = Vs[i * ldv + r];
+#pragma unroll
+          for (int c = 0; c < QB_NB - 1; ++c)
+            if (c < nc) {
+              const float2 a = Vs[(i + 1 + c) * ldv + r];
+              acc[c].x = fmaf(v.x, a.x, fmaf(v.y, a.y, acc[c].x));
+              acc[c].y = fmaf(v.x, a.y, fmaf(-v.y, a.x, acc[c].y));
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < QB_NB - 1; ++c) {
+          const float sx = qb_wsum(acc[c].x), sy = qb_wsum(acc[c].y);
+          if (lane == 0 && c < nc) {
+            red[warp * QB_RED + 2 * c] = sx;
+            red[warp * QB_RED + 2 * c + 1] = sy;
+          }
+        }
+        __syncthreads();
+        if (tid < 2 * nc) {
+          float t = 0.f;
+          for (int w = 0; w < QB_WARPS; ++w) t += red[w * QB_RED + tid];
+          fin[tid] = t * tj;
+        }
+        __syncthreads();
+        for (int r = i + tid; r < Mr; r += QB_THREADS) {
+          const float2 v = Vs[i * ldv + r];
+#pragma unroll
+          for (int c = 0; c < QB_NB - 1; ++c)
+            if (c < nc) {
+              const float sx = fin[2 * c], sy = fin[2 * c + 1];
+              float2* ap = &Vs[(i + 1 + c) * ldv + r];
+              ap->x -= v.x * sx - v.y * sy;
+              ap->y -= v.x * sy + v.y * sx;
+            }
+        }
+        __syncthreads();
+      }
+    }
+    // --- panel (R part and reflectors) back to global memory, then clear
+    // the R part so that Vs holds V with its zeros
+    for (int e = tid; e < jb * Mr; e += QB_THREADS) {
+      const int i = e / Mr, r = e % Mr;
+      A[(size_t)(j0 + i) * M + j0 + r] = Vs[i * ldv + r];
+    }
+    __syncthreads();
+    for (int e = tid; e < jb * jb; e += QB_THREADS) {
+      const int i = e / jb, r = e % jb;
+      if (r < i) Vs[i * ldv + r] = make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    // --- T of this panel from S[a][b] = V_a^H V_b (a < b)
+    {
+      float2 sab[QB_NB * (QB_NB - 1) / 2];
+#pragma unroll
+      for (int q = 0; q < QB_NB * (QB_NB - 1) / 2; ++q) sab[q] = make_float2(0.f, 0.f);
+      for (int r = 1 + tid; r < Mr; r += QB_THREADS) {  // row 0 only meets V_0
+        float2 v[QB_NB];
+#pragma unroll
+        for (int i = 0; i < QB_NB; ++i) v[i] = (i < jb) ? Vs[i * ldv + r] : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int b = 1; b < QB_NB; ++b)
+#pragma unroll
+          for (int a = 0; a < b; ++a) {
+            float2& q = sab[b * (b - 1) / 2 + a];
+            q.x = fmaf(v[a].x, v[b].x, fmaf(v[a].y, v[b].y, q.x));
+            q.y = fmaf(v[a].x, v[b].y, fmaf(-v[a].y, v[b].x, q.y));
+          }
+      }
+#pragma unroll
+      for (int q = 0; q < QB_NB * (QB_NB - 1) / 2; ++q) {
+        const float sx = qb_wsum(sab[q].x), sy = qb_wsum(sab[q].y);
+        if (lane == 0) {
+          red[warp * QB_RED + 2 * q] = sx;
+          red[warp * QB_RED + 2 * q + 1] = sy;
+        }
+      }
+      __syncthreads();
+      if (tid < QB_NB * (QB_NB - 1)) {
+        float t = 0.f;
+        for (int w = 0; w < QB_WARPS; ++w) t += red[w * QB_RED + tid];
+        fin[tid] = t;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        float2* Tp = Tall + p * QB_NB * QB_NB;
+        for (int e = 0; e < QB_NB * QB_NB; ++e) Tp[e] = make_float2(0.f, 0.f);
+        for (int i = 0; i < jb; ++i) {
+          const float ti = tau[j0 + i];
+          Tp[i * QB_NB + i] = make_float2(ti, 0.f);
+          for (int a = 0; a < i; ++a) {
+            float2 s = make_float2(0.f, 0.f);
+            for (int b = a; b < i; ++b) {  // T[a][b] S[b][i]
+              const float2 t = Tp[a * QB_NB + b];
+              const int q = i * (i - 1) / 2 + b;
+              const float2 sv = make_float2(fin[2 * q], fin[2 * q + 1]);
+              s.x += t.x * sv.x - t.y * sv.y;
+              s.y += t.x * sv.y + t.y * sv.x;
+            }
+            Tp[a * QB_NB + i] = make_float2(-ti * s.x, -ti * s.y);
+          }
+        }
+      }
+      __syncthreads();
+    }
+    // --- trailing columns: A <- A - V T^H V^H A
+    qb_apply(A, M, j0, jb, j0 + jb, L, Vs, ldv, Tall + p * QB_NB * QB_NB, true, W, W2);
+  }
+
+  // --- Q = H_0 ... H_{L-1} [I; 0], panels backwards
+  for (int64_t e = tid; e < (int64_t)M * L; e += QB_THREADS) {
+    const int c = (int)(e / M), r = (int)(e % M);
+    Qo[e] = make_float2(r == c ? 1.f : 0.f, 0.f);
+  }
+  __syncthreads();
+  for (int p = npan - 1; p >= 0; --p) {
+    const int j0 = p * QB_NB, jb = min(QB_NB, L - j0), Mr = M - j0;
+    for (int e = tid; e < jb * Mr; e += QB_THREADS) {
+      const int i = e / Mr, r = e % Mr;
+      Vs[i * ldv + r] = (r < i) ? make_float2(0.f, 0.f) : A[(size_t)(j0 + i) * M + j0 + r];
+    }
+    __syncthreads();
+    qb_apply(Qo, M, j0, jb, j0, L, Vs, ldv, Tall + p * QB_NB * QB_NB, false, W, W2);
+  }
+}
+
+bool qr_blk_f32_fits(int M, int L) { return M >= L && L >= 1 && qb_smem_bytes(M, L) <= 227 * 1024 - 1024; }
+
+// Raises a kernel's dynamic shared-memory limit to `bytes` (the first time a
+// launch needs more than the last value set for it).
+template <typename K>
+static cudaError_t ensure_smem(K kernel, size_t bytes, size_t* done) {
+  if (bytes <= 48 * 1024 || bytes <= *done) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) *done = bytes;
+  return e;
+}
+
+cudaError_t launch_qr_blk_f32(float2* A, float2* Q, int M, int L, int batch, cudaStream_t st) {
+  const size_t sm = qb_smem_bytes(M, L);
+  static size_t attr = 0;
+  cudaError_t e = ensure_smem(k_qr_blk_f32, sm, &attr);
+  if (e != cudaSuccess) return e;
+  k_qr_blk_f32<<<batch, QB_THREADS, sm, st>>>(A, Q, M, L);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Re-orthonormalisation of an FP32 Q_f (M x L column-major per instance).
+// ---------------------------------------------------------------------------
+// double-float accumulation of exact FP32 products: acc += x * y (TwoSum on
+// the high part, rounding errors gathered in the low part)
+__device__ __forceinline__ void df_acc(float& h, float& lo, float x, float y) {
+  const float ph = x * y;
+  const float pe = fmaf(x, y, -ph);
+  const float t = h + ph;
+  const float zz = t - h;
+  const float e = (h - (t - zz)) + (ph - zz);
+  h = t;
+  lo += e + pe;
+}
+
+// (H, Lo) += (h, lo), renormalised (Dekker's add): keeps the low word below
+// one ulp of the high word, so that the error stays at the u^2 level over
+// long sums instead of growing like K u^2.
+__device__ __forceinline__ void df_merge(float& H, float& Lo, float h, float lo) {
+  const float s = H + h;
+  const float v = s - H;
+  float e = (H - (s - v)) + (h - v);
+  e += Lo + lo;
+  H = s + e;
+  Lo = e - (H - s);
+}
+
+// E = Q_f^H Q_f - I on the tiles on and above the diagonal (32 x 32 tiles,
+// 2 x 2 outputs per thread), written to ptrs[z].R (L x L column-major, FP64).
+// Each 16-deep slice of the sum is accumulated afresh and merged into the
+// running double-float sum.
+__global__ void __launch_bounds__(256) k_gram_df(const float2* __restrict__ Qf, const ProbPtr* __restrict__ ptrs,
+                                                 int M, int L) {
+  constexpr int T = 32, TK = 16;
+  __shared__ float2 As[TK][T + 1];
+  __shared__ float2 Bs[TK][T + 1];
+  const int z = blockIdx.y;
+  const int nt = (L + T - 1) / T;
+  // blockIdx.x enumerates the tile pairs (ti <= tj)
+  int ti = 0, rem = blockIdx.x;
+  while (rem >= nt - ti) { rem -= nt - ti; ++ti; }
+  const int tj = ti + rem;
+  const float2* q = Qf + (size_t)z * M * L;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  float RH[2][2], RL[2][2], IH[2][2], IL[2][2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) RH[i][j] = RL[i][j] = IH[i][j] = IL[i][j] = 0.f;
+  for (int k0 = 0; k0 < M; k0 += TK) {
+    for (int e = tid; e < T * TK; e += 256) {
+      const int kk = e % TK, c = e / TK;
+      const int gk = k0 + kk;
+      const int ca = ti * T + c, cb = tj * T + c;
+      As[kk][c] = (gk < M && ca < L) ? q[(size_t)ca * M + gk] : make_float2(0.f, 0.f);
+      Bs[kk][c] = (gk < M && cb < L) ? q[(size_t)cb * M + gk] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    float rh[2][2], rl[2][2], ih[2][2], il[2][2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) rh[i][j] = rl[i][j] = ih[i][j] = il[i][j] = 0.f;
+#pragma unroll 4
+    for (int kk = 0; kk < TK; ++kk) {
+      float2 a[2], b[2];
+      a[0] = As[kk][ty]; a[1] = As[kk][ty + 16];
+      b[0] = Bs[kk][tx]; b[1] = Bs[kk][tx + 16];
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {  // conj(a) b
+          df_acc(rh[i][j], rl[i][j], a[i].x, b[j].x);
+          df_acc(rh[i][j], rl[i][j], a[i].y, b[j].y);
+          df_acc(ih[i][j], il[i][j], a[i].x, b[j].y);
+          df_acc(ih[i][j], il[i][j], -a[i].y, b[j].x);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        df_merge(RH[i][j], RL[i][j], rh[i][j], rl[i][j]);
+        df_merge(IH[i][j], IL[i][j], ih[i][j], il[i][j]);
+      }
+    __syncthreads();
+  }
+  cplx* E = ptrs[z].R;
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int r = ti * T + ty + 16 * i, c = tj * T + tx + 16 * j;
+      if (r < L && c < L && r <= c)
+        E[(size_t)c * L + r] = cmk(((double)RH[i][j] - (r == c ? 1.0 : 0.0)) + (double)RL[i][j],
+                                   (double)IH[i][j] + (double)IL[i][j]);
+    }
+}
+
+// D = -E/2 + 3 E^2 / 8 (E Hermitian, from its upper triangle), FP32, one CTA
+// per instance; flags the instance when E is not small or not finite.
+__global__ void __launch_bounds__(512) k_lowdin(const ProbPtr* __restrict__ ptrs, float2* Dbase, int L, int* status) {
+  extern __shared__ __align__(16) unsigned char ld_raw[];
+  float2* Ef = reinterpret_cast<float2*>(ld_raw);  // L x L, Ef[a * L + b] = E[a][b]
+  __shared__ float red[32];
+  const int z = blockIdx.x;
+  const cplx* E = ptrs[z].R;
+  float2* D = Dbase + (size_t)z * L * L;
+  const int tid = threadIdx.x;
+  float mx = 0.f;
+  for (int e = tid; e < L * L; e += blockDim.x) {
+    const int a = e / L, b = e % L;
+    cplx v = (a <= b) ? E[(size_t)b * L + a] : cconj(E[(size_t)a * L + b]);
+    const float2 f = make_float2((float)v.x, (float)v.y);
+    Ef[e] = f;
+    const float m = fmaxf(fabsf(f.x), fabsf(f.y));
+    mx = (m > mx || m != m) ? m : mx;  // NaN sticks
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float y = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = (y > mx || y != y) ? y : mx;
+  }
+  if ((tid & 31) == 0) red[tid >> 5] = mx;
+  __syncthreads();
+  if (tid == 0) {
+    float m = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = (red[w] > m || red[w] != red[w]) ? red[w] : m;
+    if (!(m <= 1e-3f)) atomicOr(status, 1);
+  }
+  // D[a][b] = -E[a][b]/2 + 3/8 sum_k E[a][k] E[k][b]; stored column-major (D[b * L + a])
+  for (int e = tid; e < L * L; e += blockDim.x) {
+    const int b = e / L, a = e % L;
+    float sx = 0.f, sy = 0.f;
+    for (int k = 0; k < L; ++k) {
+      const float2 x = Ef[a * L + k], y = Ef[k * L + b];
+      sx = fmaf(x.x, y.x, fmaf(-x.y, y.y, sx));
+      sy = fmaf(x.x, y.y, fmaf(x.y, y.x, sy));
+    }
+    const float2 ea = Ef[a * L + b];
+    D[e] = make_float2(-0.5f * ea.x + 0.375f * sx, -0.5f * ea.y + 0.375f * sy);
+  }
+}
+
+// Out = X + X D with the small correction X D in FP32 (|D| ~ 1e-6, so its
+// relative FP32 error costs ~1e-13 absolute), X M x L column-major per
+// instance: Q = Q_f (I + D) from the FP32 Q_f into ptrs[z].Q, or, in place,
+// B^H = (A^H Q_f)(I + D) on ptrs[z].Yt.  64 rows per CTA, staged column-major
+// in shared memory as FP32; warp w owns the columns c = w (mod 8), lane i the
+// rows 2i and 2i+1 of the tile (one 16-byte shared load per k).
+enum { QF_ROWS = 64, QF_MAXL = 128, QF_MAXCPW = QF_MAXL / 8 };
+
+template <bool FROM_F32>
+__global__ void __launch_bounds__(256) k_fold(const float2* __restrict__ Qf, const float2* __restrict__ Dbase,
+                                              const ProbPtr* __restrict__ ptrs, int M, int L) {
+  extern __shared__ __align__(16) unsigned char qf_raw[];
+  float2* Ds = reinterpret_cast<float2*>(qf_raw);  // L x L column-major
+  float2* Qs = Ds + ((L * L + 1) & ~1);            // QF_ROWS x L column-major (16-byte aligned)
+  const int z = blockIdx.y;
+  const int r0 = blockIdx.x * QF_ROWS;
+  const float2* q = Qf + (size_t)z * M * L;
+  cplx* X = FROM_F32 ? ptrs[z].Q : ptrs[z].Yt;  // output (and FP64 source when !FROM_F32)
+  const float2* D = Dbase + (size_t)z * L * L;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int e = tid; e < L * L; e += 256) Ds[e] = D[e];
+  for (int e = tid; e < QF_ROWS * L; e += 256) {
+    const int c = e / QF_ROWS, r = e % QF_ROWS;
+    float2 v = make_float2(0.f, 0.f);
+    if (r0 + r < M) {
+      if (FROM_F32) {
+        v = q[(size_t)c * M + r0 + r];
+      } else {
+        const cplx x = X[(size_t)c * M + r0 + r];
+        v = make_float2((float)x.x, (float)x.y);
+      }
+    }
+    Qs[e] = v;
+  }
+  __syncthreads();
+  float2 acc[2][QF_MAXCPW];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < QF_MAXCPW; ++j) acc[i][j] = make_float2(0.f, 0.f);
+  for (int k = 0; k < L; ++k) {
+    const float4 x = *reinterpret_cast<const float4*>(&Qs[k * QF_ROWS + 2 * lane]);  // rows 2 lane, 2 lane + 1
+#pragma unroll
+    for (int j = 0; j < QF_MAXCPW; ++j) {
+      const int c = warp + 8 * j;
+      if (c < L) {
+        const float2 d = Ds[c * L + k];
+        acc[0][j].x = fmaf(x.x, d.x, fmaf(-x.y, d.y, acc[0][j].x));
+        acc[0][j].y = fmaf(x.x, d.y, fmaf(x.y, d.x, acc[0][j].y));
+        acc[1][j].x = fmaf(x.z, d.x, fmaf(-x.w, d.y, acc[1][j].x));
+        acc[1][j].y = fmaf(x.z, d.y, fmaf(x.w, d.x, acc[1][j].y));
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const int r = 2 * lane + i;
+    if (r0 + r >= M) continue;
+#pragma unroll
+    for (int j = 0; j < QF_MAXCPW; ++j) {
+      const int c = warp + 8 * j;
+      if (c < L) {
+        cplx b;
+        if (FROM_F32) {
+          const float2 f = Qs[c * QF_ROWS + r];
+          b = cmk((double)f.x, (double)f.y);
+        } else {
+          b = X[(size_t)c * M + r0 + r];
+        }
+        X[(size_t)c * M + r0 + r] = cmk(b.x + (double)acc[i][j].x, b.y + (double)acc[i][j].y);
+      }
+    }
+  }
+}
+
+bool reorth_fits(int M, int L) { return M >= L && L <= QF_MAXL; }
+
+cudaError_t launch_reorth(const float2* Qf, float2* Dbuf, const ProbPtr* ptrs, int M, int L, int batch, int* status,
+                          cudaStream_t st) {
+  static size_t attr_l = 0, attr_f = 0;
+  const size_t sm_l = sizeof(float2) * (size_t)L * L;
+  const size_t sm_f = sizeof(float2) * ((size_t)((L * L + 1) & ~1) + (size_t)QF_ROWS * L);
+  cudaError_t e0 = ensure_smem(k_lowdin, sm_l, &attr_l);
+  if (e0 == cudaSuccess) e0 = ensure_smem(k_fold<true>, sm_f, &attr_f);
+  if (e0 != cudaSuccess) return e0;
+  const int nt = (L + 31) / 32;
+  {
+    ProfScope ps("k_gram_df", st);
+    k_gram_df<<<dim3(nt * (nt + 1) / 2, batch), 256, 0, st>>>(Qf, ptrs, M, L);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  {
+    ProfScope ps("k_lowdin", st);
+    k_lowdin<<<batch, 512, sm_l, st>>>(ptrs, Dbuf, L, status);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  ProfScope ps("k_fold[q]", st);
+  k_fold<true><<<dim3((M + QF_ROWS - 1) / QF_ROWS, batch), 256, sm_f, st>>>(Qf, Dbuf, ptrs, M, L);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Projection B^H = A^H Q with Q = Q_f (I + D) (the re-orthonormalised basis):
+// X = A^H Q_f in double-float arithmetic with the FP32 Q_f used as it is
+// (its entries are exact single floats), then B^H = X + X D.
+// Complex products by Gauss's three multiplications: for alpha = a + ib
+// (from A^H) and beta = c + id (from Q_f),
+//   t1 = a (c + d),  t2 = d (a + b),  t3 = c (b - a),
+//   Re = t1 - t2,  Im = t1 + t3,
+// three double-float products instead of four; a, a + b, b - a are
+// double-float, c, d single floats, c + d a TwoSum pair.  64 x 32 output tile
+// per CTA, 4 x 2 outputs per thread, K in slices of 16 each closed by a
+// renormalising Fast2Sum of the accumulators.
+// ---------------------------------------------------------------------------
+enum { PJ_TM = 64, PJ_TN = 32, PJ_TK = 16 };
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float v = s - a;
+  e = (a - (s - v)) + (b - v);
+}
+// acc += (xh, xl) (yh, yl)
+__device__ __forceinline__ void dfx_dd(float& h, float& lo, float xh, float xl, float yh, float yl) {
+  const float ph = xh * yh;
+  const float pe = fmaf(xh, yh, -ph);
+  const float pc = fmaf(xh, yl, xl * yh);
+  float t, e;
+  two_sum(h, ph, t, e);
+  h = t;
+  lo += (e + pe) + pc;
+}
+// acc += x (yh, yl), x a single float
+__device__ __forceinline__ void dfx_sd(float& h, float& lo, float x, float yh, float yl) {
+  const float ph = x * yh;
+  const float pe = fmaf(x, yh, -ph);
+  float t, e;
+  two_sum(h, ph, t, e);
+  h = t;
+  lo += (e + pe) + x * yl;
+}
+__device__ __forceinline__ void fast2(float& h, float& lo) {
+  const float s = h + lo;
+  lo = lo - (s - h);
+  h = s;
+}
+
+__global__ void __launch_bounds__(256) k_proj_df(const ProbPtr* __restrict__ ptrs, const float2* __restrict__ Qf,
+                                                 int m, int n, int l) {
+  __shared__ float4 Aab[PJ_TK][PJ_TM];  // (a_h, a_l, b_h, b_l)
+  __shared__ float4 Asd[PJ_TK][PJ_TM];  // (a+b)_h, (a+b)_l, (b-a)_h, (b-a)_l
+  __shared__ float4 Bs[PJ_TK][PJ_TN];   // (c, d, (c+d)_h, (c+d)_l)
+  const int z = blockIdx.z;
+  const int tm = blockIdx.y * PJ_TM, tn = blockIdx.x * PJ_TN;
+  const cplx* th = ptrs[z].theta;
+  const float2* q = Qf + (size_t)z * m * l;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  float h1[4][2], l1[4][2], h2[4][2], l2[4][2], h3[4][2], l3[4][2];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) h1[i][j] = l1[i][j] = h2[i][j] = l2[i][j] = h3[i][j] = l3[i][j] = 0.f;
+  for (int k0 = 0; k0 < m; k0 += PJ_TK) {
+    // A^H tile: element (r, k) = conj(theta[k][r]); consecutive threads read consecutive r
+    for (int e = tid; e < PJ_TM * PJ_TK; e += 256) {
+      const int r = e % PJ_TM, kk = e / PJ_TM;
+      const int gr = tm + r, gk = k0 + kk;
+      double a = 0.0, b = 0.0;
+      if (gr < n && gk < m) {
+        const cplx v = th[(size_t)gk * n + gr];
+        a = v.x;
+        b = -v.y;
+      }
+      const float ah = (float)a, al = (float)(a - (double)ah);
+      const float bh = (float)b, bl = (float)(b - (double)bh);
+      float sh, se, dh, de;
+      two_sum(ah, bh, sh, se);
+      two_sum(bh, -ah, dh, de);
+      Aab[kk][r] = make_float4(ah, al, bh, bl);
+      Asd[kk][r] = make_float4(sh, se + (al + bl), dh, de + (bl - al));
+    }
+    // Q_f tile: element (k, c) at q[c * m + k]
+    for (int e = tid; e < PJ_TK * PJ_TN; e += 256) {
+      const int kk = e % PJ_TK, c = e / PJ_TK;
+      const int gk = k0 + kk, gc = tn + c;
+      float2 v = make_float2(0.f, 0.f);
+      if (gk < m && gc < l) v = q[(size_t)gc * m + gk];
+      float sh, se;
+      two_sum(v.x, v.y, sh, se);
+      Bs[kk][c] = make_float4(v.x, v.y, sh, se);
+    }
+    __syncthreads();
+#pragma unroll 2
+    for (int kk = 0; kk < PJ_TK; ++kk) {
+      float4 b[2];
+      b[0] = Bs[kk][tx];
+      b[1] = Bs[kk][tx + 16];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float4 ab = Aab[kk][ty + 16 * i];
+        const float4 sd = Asd[kk][ty + 16 * i];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          dfx_dd(h1[i][j], l1[i][j], ab.x, ab.y, b[j].z, b[j].w);  // a (c + d)
+          dfx_sd(h2[i][j], l2[i][j], b[j].y, sd.x, sd.y);          // d (a + b)
+          dfx_sd(h3[i][j], l3[i][j], b[j].x, sd.z, sd.w);          // c (b - a)
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        fast2(h1[i][j], l1[i][j]);
+        fast2(h2[i][j], l2[i][j]);
+        fast2(h3[i][j], l3[i][j]);
+      }
+    __syncthreads();
+  }
+  cplx* X = ptrs[z].Yt;  // n x l column-major
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int r = tm + ty + 16 * i, c = tn + tx + 16 * j;
+      if (r < n && c < l) {
+        const double t1 = (double)h1[i][j] + (double)l1[i][j];
+        const double t2 = (double)h2[i][j] + (double)l2[i][j];
+        const double t3 = (double)h3[i][j] + (double)l3[i][j];
+        X[(size_t)c * n + r] = cmk(t1 - t2, t1 + t3);
+      }
+    }
+}
+
+cudaError_t launch_proj_df(const ProbPtr* ptrs, const float2* Qf, const float2* Dbuf, int m, int n, int l, int batch,
+                           cudaStream_t st) {
+  {
+    ProfScope ps("k_zgemm_df[project]", st);
+    k_proj_df<<<dim3((l + PJ_TN - 1) / PJ_TN, (n + PJ_TM - 1) / PJ_TM, batch), 256, 0, st>>>(ptrs, Qf, m, n, l);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  static size_t attr = 0;
+  const size_t sm_f = sizeof(float2) * ((size_t)((l * l + 1) & ~1) + (size_t)QF_ROWS * l);
+  cudaError_t e = ensure_smem(k_fold<false>, sm_f, &attr);
+  if (e != cudaSuccess) return e;
+  ProfScope ps("k_fold[bh]", st);
+  k_fold<false><<<dim3((n + QF_ROWS - 1) / QF_ROWS, batch), 256, sm_f, st>>>(Qf, Dbuf, ptrs, n, l);
+  return cudaGetLastError();
+}
+
+}  // namespace tg

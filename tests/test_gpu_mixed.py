@@ -1,6 +1,7 @@
 """The mixed-precision RRSVD form (TEBD_PREC_TF32): TF32 tensor-core sketch
-and power iterations, 3xTF32 refinement of the last power round, FP64 last
-QR / projection / small SVD.
+and power iterations with FP32 Householder QRs, 3xTF32 refinement of the last
+power round, an FP64-accurate re-orthonormalisation of the last Q (FP64
+Householder when l > 128), double-float projection and FP64 small SVD.
 
 Its stated tolerances: with Omega rounded to TF32 and the sketch in TF32 the
 mixed form is a different (equally valid) randomized truncation than the FP64
@@ -10,8 +11,8 @@ oracle, so it is held to the FP64 method's accuracy, not to its rounding
   * excess error (||A - A_k||_F - ||A - A_k(exact)||_F) / ||A||_F no more
     than 1e-8 above the oracle's;
   * where the FP64 method meets the 1e-8 bar, the mixed form meets it too;
-  * the returned factors are orthonormal to 1e-11 (FP64 last QR and Jacobi,
-    double-float U = Q J_k and V = Qb W_k).
+  * the returned factors are orthonormal to 1e-11 (re-orthonormalised last Q,
+    FP64 Jacobi, double-float U = Q J_k and V = Qb W_k).
 """
 import numpy as np
 import pytest
@@ -30,6 +31,8 @@ SEED = 4321
     (300, 200, 40, 10, 1, 8.0),    # ragged: no size is a multiple of 128 / 32
     (130, 70, 20, 6, 0, 4.0),      # q = 0: the sketch itself is the refinement pass
     (96, 96, 24, 8, 2, 5.0),
+    (400, 360, 120, 20, 1, 30.0),  # l = 140 > 128: FP64 last QR
+    (3700, 200, 20, 10, 1, 6.0),   # Y too tall for the blocked FP32 QR: unblocked fallback
 ])
 def test_mixed_form_meets_its_tolerances(lib, m, n, k, p, q, scale):
     from paper_1504_00992_gb300 import binding as B
