@@ -301,31 +301,54 @@ def e2e_measure(B, torch, theta, batch, code, args, rank, world):
             "d2h_bytes_per_step": bo}
 
 
+# Double-float (FP32-pair) arithmetic of the projection kernel: per complex
+# multiply-add three double-float products by Gauss's rule, 37 FP32
+# instructions.  Its ceiling is the FP32 issue rate (152 SMs x 128 lanes x
+# 2.07 GHz) / 37 instructions x 8 FP64-equivalent flop.
+DF_OPS_PER_CMAC = 37
+DF_PEAK_GFLOPS = 152 * 128 * 2.07 / DF_OPS_PER_CMAC * 8
+
+
+def _src_hash(name):
+    import hashlib
+    src = open(os.path.join(ROOT, "paper_1504_00992_gb300", "csrc", name), "rb").read()
+    return hashlib.sha256(src).hexdigest()[:16]
+
+
 def roofline(res, batch):
-    """Roofline object of the dominant kernel class of one measured form."""
+    """Roofline object of the dominant kernel class of one measured form:
+    algorithmic flops of one launch (per instance x batch) over its mean
+    CUDA-event duration, against the derived ceiling of the pipe it runs on;
+    traffic = DRAM bytes per launch from the committed ncu capture of that
+    kernel (scaled by instances), or null when the source has changed since."""
     prof = res["prof"]
     l, k = res["l"], res["k"]
     dom = max(prof, key=lambda kk: prof[kk][0]) if prof else None
     fp64_peak = FP64_PEAK_GFLOPS / 1e3
-    per_launch = {"k_zgemm[sketch]": (8.0 * M * N_ * l * batch, "alu", fp64_peak),
-                  "k_qr": ((16.0 * M * l * l - 16.0 * l ** 3 / 3) * batch, "alu", fp64_peak),
-                  "k_zgemm[uv]": (8.0 * M * l * k * batch, "alu", fp64_peak)}
+    df_peak = DF_PEAK_GFLOPS / 1e3
+    fp64_src = "FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (derived)"
+    df_src = ("FP32 issue rate 152 SMs x 128 lanes x 2.07 GHz / %d FP32 instructions per double-float complex "
+              "multiply-add x 8 flop (derived)" % DF_OPS_PER_CMAC)
+    # kernel -> (algorithmic flops per launch, bound, peak, peak source, file holding the kernel)
+    per_launch = {
+        "k_zgemm[sketch]": (8.0 * M * N_ * l * batch, "alu", fp64_peak, fp64_src, "kernels.cu"),
+        "k_qr": ((16.0 * M * l * l - 16.0 * l ** 3 / 3) * batch, "alu", fp64_peak, fp64_src, "kernels.cu"),
+        "k_zgemm[uv]": (8.0 * M * l * k * batch, "alu", fp64_peak, fp64_src, "kernels.cu"),
+        "k_zgemm_df[project]": (8.0 * M * N_ * l * batch, "alu", df_peak, df_src, "qr_blocked.cu"),
+    }
     if dom not in per_launch:
         return None
-    fl, bound, peak = per_launch[dom]
+    fl, bound, peak, psrc, srcfile = per_launch[dom]
     avg_ms = prof[dom][0] / prof[dom][1]
     achieved = fl / (avg_ms / 1e3) / 1e12
     traffic = None
     tp = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tp):
-        import hashlib
-        rec = json.load(open(tp))
-        src = open(os.path.join(ROOT, "paper_1504_00992_gb300", "csrc", "kernels.cu"), "rb").read()
-        if hashlib.sha256(src).hexdigest()[:16] == rec.get("_kernels_cu_sha256_16") and batch == 152:
-            traffic = rec.get(dom)   # counters taken on this exact kernel source
+        rec = json.load(open(tp)).get(dom)
+        if rec and rec.get("src_sha256_16") == _src_hash(srcfile):
+            traffic = rec["dram_bytes_per_instance"] * batch   # counters taken on this exact kernel source
     return {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": traffic,
-            "peak_source": "FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (derived)"}
+            "frac": achieved / peak, "traffic": traffic, "peak_source": psrc}
 
 
 def run_tebd_many(B, I, torch, n_chains=256, steps=10, warm=2, unbatched_chains=16, unbatched_steps=3):
@@ -487,11 +510,13 @@ def main():
         line = {"metric": METRIC, "value": head["value"], "unit": "bond updates/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms"] / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "tf32+f64" if head["prec"] == "tf32" else "f64", "data": "synthetic",
+                "dtype": "tf32+f32+df64+f64" if head["prec"] == "tf32" else "f64", "data": "synthetic",
                 "config": {"workload": "single-bond stress: RRSVD truncation of given 2000x2000 complex128 theta, "
                                        "sigma_k = exp(-(k-1)/15), k=100, p=20, q=2 (theta given directly)",
-                           "precision": head["prec"] + (" (TF32 sketch, 3xTF32 refinement round, FP64 last QR, "
-                                                        "projection and small SVD)" if head["prec"] == "tf32"
+                           "precision": head["prec"] + (" (TF32 sketch and power round, 3xTF32 refinement round, "
+                                                        "FP32 Householder QRs, FP64-accurate re-orthonormalisation "
+                                                        "of the last Q, double-float projection and U/V, FP64 QR "
+                                                        "of B^H and Jacobi SVD)" if head["prec"] == "tf32"
                                                         else " (plain path)"),
                            "batch_per_gpu": batch, "distinct_theta": POOL, "parallelism": f"replicas x{world}",
                            "l2": "inputs larger than L2: 9.7 GB of theta read per step",

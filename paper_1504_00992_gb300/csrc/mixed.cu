@@ -42,61 +42,142 @@ __device__ __forceinline__ float tf32_rna(float x) {
 }
 
 // ---------------------------------------------------------------------------
-// theta (FP64, m x n row-major, per instance) -> forward copy thf (m x K1)
-// and, when requested, the TF32 remainder thf_lo.
+// theta (FP64, m x n row-major, per instance), read once per 32 x 32 tile:
+//   forward copy thf (m x K1): TF32-rounded (Re, Im) and, when requested,
+//     the TF32 remainder thf_lo;
+//   adjoint copy tha (n x K2), transposed through shared memory:
+//     tha[c][2r] = Re theta[r][c], tha[c][2r+1] = -Im theta[r][c], and its
+//     remainder;
+//   double-float copy of conj(theta) (m x n float4: Re hi, Re lo, -Im hi,
+//     -Im lo), when thd is set, for the projection.
+// The tiles cover the zero padding of both copies.
 // ---------------------------------------------------------------------------
-__global__ void k_conv_fwd(const MixedPtrs mp, const ProbPtr* __restrict__ ptrs, int m, int n, int K1, int want_lo) {
-  const int z = blockIdx.y;
-  const cplx* th = ptrs[z].theta;
-  float* hi = mp.thf_hi + (size_t)z * m * K1;
-  float* lo = mp.thf_lo + (size_t)z * m * K1;
-  const int64_t half = K1 / 2;  // complex columns incl. padding
-  const int64_t total = (int64_t)m * half;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int r = (int)(e / half), c = (int)(e % half);
-    float2 h = make_float2(0.f, 0.f), w = make_float2(0.f, 0.f);
-    if (c < n) {
-      const cplx v = th[(int64_t)r * n + c];
-      const float hr = tf32_rna((float)v.x), hm = tf32_rna((float)v.y);
-      h = make_float2(hr, hm);
-      w = make_float2(tf32_rna((float)(v.x - (double)hr)), tf32_rna((float)(v.y - (double)hm)));
-    }
-    reinterpret_cast<float2*>(hi)[e] = h;
-    if (want_lo) reinterpret_cast<float2*>(lo)[e] = w;
+// x -> hi + lo with integer and FP32 operations only (GB300 runs FP64
+// arithmetic and double<->float conversions on its 1/64-rate FP64 pipe):
+// hi = x truncated to 24 significant bits, lo = the remaining 29 mantissa
+// bits rounded to FP32, so hi + lo = x to 2^-48 relative (lo may be an FP32
+// subnormal).  |x| below 2^-126 flushes to zero; non-finite x gives a
+// non-finite hi.
+__device__ __forceinline__ void split_bits(double x, float& hi, float& lo) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned int sign = (unsigned int)(u >> 32) & 0x80000000u;
+  const int e = (int)((u >> 52) & 0x7FF);
+  const unsigned long long mant = u & 0xFFFFFFFFFFFFFull;
+  const int ef = e - 1023 + 127;  // FP32 biased exponent of hi
+  if (e == 0x7FF || ef >= 255) {   // Inf / NaN / beyond FP32: non-finite hi
+    hi = __uint_as_float(sign | 0x7F800000u | (unsigned int)(mant >> 29) | (mant ? 1u : 0u));
+    lo = 0.f;
+    return;
   }
+  if (ef <= 0) {
+    hi = __uint_as_float(sign);
+    lo = 0.f;
+    return;
+  }
+  hi = __uint_as_float(sign | ((unsigned int)ef << 23) | (unsigned int)(mant >> 29));
+  // weight of mantissa bit 0: 2^(e - 1075) = 2^(e - 1011) * 2^-64, both factors normal FP32 numbers for e >= 897
+  const float r = __uint2float_rn((unsigned int)(mant & 0x1FFFFFFFull));
+  const float l = (r * __uint_as_float((unsigned int)(e - 1011 + 127) << 23)) * 5.421010862427522e-20f;  // 2^-64
+  lo = sign ? -l : l;
 }
 
-// theta -> adjoint copy tha (n x K2): tha[c][2r] = Re theta[r][c],
-// tha[c][2r+1] = -Im theta[r][c]; 32 x 32 complex tiles through shared memory.
-__global__ void __launch_bounds__(256) k_conv_adj(const MixedPtrs mp, const ProbPtr* __restrict__ ptrs, int m, int n,
-                                                  int K2, int want_lo) {
-  __shared__ cplx tile[32][33];
+// Complex standard Gaussian of sketch element `idx` from the same Philox
+// words as the FP64 path, by Box-Muller in FP32 (24-bit uniforms): the
+// mixed form rounds Omega to TF32, and its refinement pass needs it to FP32.
+__device__ __forceinline__ float2 gauss_c_f32(uint64_t idx, uint64_t bond, uint64_t sweep, uint64_t chain,
+                                              uint64_t seed) {
+  const u64x4 w = philox4x64_10(idx, bond, sweep, chain, seed, 0);
+  const float u1 = ((float)(unsigned int)(w.v[0] >> 40) + 0.5f) * 5.9604644775390625e-8f;  // 2^-24
+  const float u2 = ((float)(unsigned int)(w.v[1] >> 40) + 0.5f) * 5.9604644775390625e-8f;
+  const float rho = sqrtf(-2.f * logf(u1));
+  float sn, cs;
+  sincospif(2.f * u2, &sn, &cs);
+  return make_float2(rho * cs, rho * sn);
+}
+
+// double-float pair sum (Knuth's TwoSum on the high words)
+__device__ __forceinline__ void df_add2(float& h, float& l, float oh, float ol) {
+  const float s = h + oh;
+  const float v = s - h;
+  float e = (h - (s - v)) + (oh - v);
+  e += l + ol;
+  h = s + e;
+  l = e - (h - s);
+}
+
+__global__ void __launch_bounds__(256) k_conv_theta(const MixedPtrs mp, const ProbPtr* __restrict__ ptrs, int m, int n,
+                                                    int K1, int K2, int want_lo) {
+  __shared__ float2 tile[32][33];  // TF32 hi and remainder computed once per element
+  __shared__ float2 tlo[32][33];
+  __shared__ float red[16];
   const int z = blockIdx.z;
   const cplx* th = ptrs[z].theta;
-  float2* hi = reinterpret_cast<float2*>(mp.tha_hi + (size_t)z * n * K2);
-  float2* lo = reinterpret_cast<float2*>(mp.tha_lo + (size_t)z * n * K2);
-  const int half = K2 / 2;
-  const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;  // r over theta rows (incl. padding), c over theta columns
+  const int half1 = K1 / 2, half2 = K2 / 2;  // complex columns of thf / tha incl. padding
+  float2* fh = reinterpret_cast<float2*>(mp.thf_hi + (size_t)z * m * K1);
+  float2* fl = reinterpret_cast<float2*>(mp.thf_lo + (size_t)z * m * K1);
+  float2* ah = reinterpret_cast<float2*>(mp.tha_hi + (size_t)z * n * K2);
+  float2* al = reinterpret_cast<float2*>(mp.tha_lo + (size_t)z * n * K2);
+  float4* dd = mp.thd ? mp.thd + (size_t)z * m * n : nullptr;
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  float sh = 0.f, sl = 0.f;  // double-float sum of |theta|^2 over this thread's elements
   for (int i = ty; i < 32; i += 8) {
     const int r = r0 + i, c = c0 + tx;
-    tile[i][tx] = (r < m && c < n) ? th[(int64_t)r * n + c] : cmk(0.0, 0.0);
+    const cplx v = (r < m && c < n) ? th[(int64_t)r * n + c] : cmk(0.0, 0.0);
+    float xh, xl, yh, yl;
+    split_bits(v.x, xh, xl);
+    split_bits(v.y, yh, yl);
+    const float hr = tf32_rna(xh), hm = tf32_rna(yh);
+    const float lr = tf32_rna((xh - hr) + xl), lm = tf32_rna((yh - hm) + yl);
+    tile[i][tx] = make_float2(hr, hm);
+    tlo[i][tx] = make_float2(lr, lm);
+    if (r < m && c < half1) {
+      fh[(int64_t)r * half1 + c] = make_float2(hr, hm);
+      if (want_lo) fl[(int64_t)r * half1 + c] = make_float2(lr, lm);
+    }
+    if (dd && r < m && c < n) dd[(int64_t)r * n + c] = make_float4(xh, xl, -yh, -yl);
+    // |v|^2 = xh^2 + yh^2 + 2 (xh xl + yh yl) + O(2^-48)
+    const float p1 = xh * xh, e1 = fmaf(xh, xh, -p1);
+    const float p2 = yh * yh, e2 = fmaf(yh, yh, -p2);
+    df_add2(sh, sl, p1, e1 + 2.f * xh * xl);
+    df_add2(sh, sl, p2, e2 + 2.f * yh * yl);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, sh, o), ol = __shfl_xor_sync(0xffffffffu, sl, o);
+    df_add2(sh, sl, oh, ol);
+  }
+  if (tx == 0) {
+    red[2 * ty] = sh;
+    red[2 * ty + 1] = sl;
   }
   __syncthreads();
+  if (threadIdx.x == 0) {
+    float h = red[0], l = red[1];
+    for (int w = 1; w < 8; ++w) df_add2(h, l, red[2 * w], red[2 * w + 1]);
+    mp.tpart[(size_t)z * gridDim.x * gridDim.y + blockIdx.y * gridDim.x + blockIdx.x] = (double)h + (double)l;
+  }
   for (int i = ty; i < 32; i += 8) {
-    const int c = c0 + i, r = r0 + tx;  // output row c, complex column r
-    if (c < n && r < half) {
-      const cplx v = tile[tx][i];
-      const float hr = tf32_rna((float)v.x), hm = tf32_rna((float)(-v.y));
-      hi[(int64_t)c * half + r] = make_float2(hr, hm);
-      if (want_lo)
-        lo[(int64_t)c * half + r] =
-            make_float2(tf32_rna((float)(v.x - (double)hr)), tf32_rna((float)(-v.y - (double)hm)));
+    const int c = c0 + i, r = r0 + tx;  // output row c, complex column r: conj of element (r, c)
+    if (c < n && r < half2) {
+      const float2 h = tile[tx][i], l = tlo[tx][i];
+      ah[(int64_t)c * half2 + r] = make_float2(h.x, -h.y);
+      if (want_lo) al[(int64_t)c * half2 + r] = make_float2(l.x, -l.y);
     }
   }
 }
 
-// Omega (Philox, as in the FP64 path) written directly as Bt (Np x K1), and
+// ||theta||_F^2 of each instance: its tile partials summed into the NPART
+// fixed partial sums the epilogue reads (deterministic order).
+__global__ void k_part_reduce(const double* __restrict__ tpart, int ntile, const ProbPtr* __restrict__ ptrs) {
+  const int z = blockIdx.x;
+  const int i = threadIdx.x;  // < NPART
+  double s = 0.0;
+  for (int t = i; t < ntile; t += NPART) s += tpart[(size_t)z * ntile + t];
+  ptrs[z].part[i] = s;
+}
+
+// Omega (the Philox words of the FP64 path, FP32 Box-Muller) written directly as Bt (Np x K1), and
 // its TF32 remainder when the sketch itself is the refinement pass (q = 0).
 __global__ void k_omega_bt(const MixedPtrs mp, const Dims* __restrict__ dims, int n, int l, int Np, int K1,
                            uint64_t seed, uint64_t sweep, int64_t chain0, int chain_stride, int want_lo) {
@@ -111,11 +192,11 @@ __global__ void k_omega_bt(const MixedPtrs mp, const Dims* __restrict__ dims, in
     const int c = (int)(e / half), j = (int)(e % half);
     float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f), al = a, bl = a;
     if (c < l && j < n) {
-      const cplx w = gauss_c((uint64_t)j * l + c, (uint64_t)D.bond, sweep, chain, seed, 0);
-      const float re = tf32_rna((float)w.x), im = tf32_rna((float)w.y);
+      const float2 w = gauss_c_f32((uint64_t)j * l + c, (uint64_t)D.bond, sweep, chain, seed);
+      const float re = tf32_rna(w.x), im = tf32_rna(w.y);
       a = make_float2(re, -im);
       b = make_float2(im, re);
-      const float rl = tf32_rna((float)(w.x - (double)re)), il = tf32_rna((float)(w.y - (double)im));
+      const float rl = tf32_rna(w.x - re), il = tf32_rna(w.y - im);
       al = make_float2(rl, -il);
       bl = make_float2(il, rl);
     }
@@ -305,6 +386,8 @@ MixedSizes mixed_sizes(int m, int n, int k, int l) {
   s.yf = (size_t)m * l * sizeof(float2);
   s.ytf = (size_t)n * l * sizeof(float2);
   s.df = (size_t)l * l * sizeof(float2);
+  s.thd = reorth_fits(m, l) ? (size_t)m * n * sizeof(float4) : 0;
+  s.ntile = ((s.K1 / 2 + 31) / 32) * ((s.K2 / 2 + 31) / 32);
   (void)k;
   return s;
 }
@@ -313,7 +396,8 @@ static size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 size_t mixed_bytes(const MixedSizes& s, int batch) {
   return 2 * up256(s.thf * batch) + 2 * up256(s.tha * batch) + 2 * up256(s.bt * batch) + 2 * up256(s.yf * batch) +
-         2 * up256(s.ytf * batch) + up256(s.df * batch);
+         2 * up256(s.ytf * batch) + up256(s.df * batch) + up256(s.thd * batch) +
+         up256((size_t)s.ntile * sizeof(double) * batch);
 }
 
 MixedPtrs mixed_carve(char* base, const MixedSizes& s, int batch) {
@@ -330,6 +414,10 @@ MixedPtrs mixed_carve(char* base, const MixedSizes& s, int batch) {
   p.Ytf = (float2*)(base + o); o += up256(s.ytf * batch);
   p.Qtf = (float2*)(base + o); o += up256(s.ytf * batch);
   p.Df = (float2*)(base + o); o += up256(s.df * batch);
+  p.thd = s.thd ? (float4*)(base + o) : nullptr;
+  o += up256(s.thd * batch);
+  p.tpart = (double*)(base + o);
+  o += up256((size_t)s.ntile * sizeof(double) * batch);
   return p;
 }
 
@@ -397,9 +485,10 @@ cudaError_t run_rrsvd_mixed(const Dims* dims, const ProbPtr* ptrs, int batch, co
   const MixedSizes s = mixed_sizes(m, n, k, l);
   {
     ProfScope ps("k_conv_theta", st);
-    k_conv_fwd<<<dim3(grid1d((int64_t)m * (s.K1 / 2)), batch), 256, 0, st>>>(mp, ptrs, m, n, s.K1, 1);
+    const int cext = s.K1 / 2, rext = s.K2 / 2;  // padded extents (>= n, >= m)
+    k_conv_theta<<<dim3((cext + 31) / 32, (rext + 31) / 32, batch), 256, 0, st>>>(mp, ptrs, m, n, s.K1, s.K2, 1);
     MX_TRY(cudaGetLastError());
-    k_conv_adj<<<dim3((s.K2 / 2 + 31) / 32, (n + 31) / 32, batch), 256, 0, st>>>(mp, ptrs, m, n, s.K2, 1);
+    k_part_reduce<<<batch, NPART, 0, st>>>(mp.tpart, s.ntile, ptrs);
     MX_TRY(cudaGetLastError());
   }
   {
@@ -425,7 +514,7 @@ cudaError_t run_rrsvd_mixed(const Dims* dims, const ProbPtr* ptrs, int batch, co
     // last QR: FP32 Householder, then the FP64-accurate re-orthonormalisation
     MX_TRY(qr_f32(mp.Yf, mp.Qf, m, l, batch, st));
     MX_TRY(launch_reorth(mp.Qf, mp.Df, ptrs, m, l, batch, status, st));
-    MX_TRY(launch_proj_df(ptrs, mp.Qf, mp.Df, m, n, l, batch, st));  // B^H = A^H Q
+    MX_TRY(launch_proj_df(mp.thd, ptrs, mp.Qf, mp.Df, m, n, l, batch, st));  // B^H = A^H Q
   } else {
     {
       ProfScope ps("k_f32_to_f64", st);
@@ -439,7 +528,6 @@ cudaError_t run_rrsvd_mixed(const Dims* dims, const ProbPtr* ptrs, int batch, co
   MX_TRY(launch_jacobi(dims, ptrs, batch, status, st));
   MX_TRY(launch_zgemm_df(G_U, dims, ptrs, batch, cap, st));
   MX_TRY(launch_zgemm_df(G_V, dims, ptrs, batch, cap, st));
-  MX_TRY(launch_frob2(dims, ptrs, batch, st));
   return cudaSuccess;
 }
 

@@ -13,7 +13,8 @@ struct MixedSizes {
   int K2;        // 2m rounded up to 32: row length of the adjoint copy and of Bt for A^H X
   int Np;        // 2l rounded up to 16: rows of Bt (tensor-core N)
   int BN;        // tensor-core tile width, min(Np, 256)
-  size_t thf, tha, bt, yf, ytf, df;  // bytes per instance
+  size_t thf, tha, bt, yf, ytf, df, thd;  // bytes per instance
+  int ntile;     // 32 x 32 tiles of the theta conversion (partials of ||theta||_F^2)
 };
 
 // Batch-major arrays (instance z at base + z * per-instance size).
@@ -29,6 +30,8 @@ struct MixedPtrs {
   float2* Ytf;    // n x l
   float2* Qtf;
   float2* Df;     // l x l correction of the re-orthonormalisation
+  float4* thd;    // m x n double-float conj(theta) (Re hi, Re lo, -Im hi, -Im lo), or null
+  double* tpart;  // ntile partial sums of |theta|^2 per instance
 };
 
 MixedSizes mixed_sizes(int m, int n, int k, int l);
@@ -46,8 +49,8 @@ cudaError_t launch_reorth(const float2* Qf, float2* Dbuf, const ProbPtr* ptrs, i
                           cudaStream_t st);
 // B^H = A^H Q_f (I + D) into ptrs[z].Yt (n x l column-major): double-float
 // product with the FP32 Q_f, then the correction; after launch_reorth.
-cudaError_t launch_proj_df(const ProbPtr* ptrs, const float2* Qf, const float2* Dbuf, int m, int n, int l, int batch,
-                           cudaStream_t st);
+cudaError_t launch_proj_df(const float4* thd, const ProbPtr* ptrs, const float2* Qf, const float2* Dbuf, int m, int n,
+                           int l, int batch, cudaStream_t st);
 
 // Alg. 1 with tensor-core products and the FP64 projection / small SVD;
 // uniform sizes over the batch (cap holds them).

@@ -66,19 +66,30 @@ __device__ void qb_apply(float2* C, int M, int j0, int jb, int c0, int L, const 
     for (int i = 0; i < QB_NB; ++i)
 #pragma unroll
       for (int w = 0; w < QB_CW; ++w) acc[i][w] = make_float2(0.f, 0.f);
-    for (int r = h * 32 + lane; r < Mr; r += 32 * rs) {
+    // the loads of the next row are issued before the products of this one
+    const int rstep = 32 * rs;
+    int r = h * 32 + lane;
+    float2 an[QB_CW];
+#pragma unroll
+    for (int w = 0; w < QB_CW; ++w)
+      an[w] = (w < nc && r < Mr) ? C[(size_t)(cb + w) * M + j0 + r] : make_float2(0.f, 0.f);
+    for (; r < Mr; r += rstep) {
+      float2 a[QB_CW];
+#pragma unroll
+      for (int w = 0; w < QB_CW; ++w) a[w] = an[w];
+      const int rn = r + rstep;
+#pragma unroll
+      for (int w = 0; w < QB_CW; ++w)
+        if (w < nc && rn < Mr) an[w] = C[(size_t)(cb + w) * M + j0 + rn];
       float2 v[QB_NB];
 #pragma unroll
       for (int i = 0; i < QB_NB; ++i) v[i] = (i < jb) ? Vs[i * ldv + r] : make_float2(0.f, 0.f);
 #pragma unroll
       for (int w = 0; w < QB_CW; ++w) {
-        if (w < nc) {
-          const float2 a = C[(size_t)(cb + w) * M + j0 + r];
 #pragma unroll
-          for (int i = 0; i < QB_NB; ++i) {
-            acc[i][w].x = fmaf(v[i].x, a.x, fmaf(v[i].y, a.y, acc[i][w].x));
-            acc[i][w].y = fmaf(v[i].x, a.y, fmaf(-v[i].y, a.x, acc[i][w].y));
-          }
+        for (int i = 0; i < QB_NB; ++i) {
+          acc[i][w].x = fmaf(v[i].x, a[w].x, fmaf(v[i].y, a[w].y, acc[i][w].x));
+          acc[i][w].y = fmaf(v[i].x, a[w].y, fmaf(-v[i].y, a[w].x, acc[i][w].y));
         }
       }
     }
@@ -125,21 +136,32 @@ __device__ void qb_apply(float2* C, int M, int j0, int jb, int c0, int L, const 
 #pragma unroll
       for (int w = 0; w < QB_CW; ++w)
         w2[i][w] = (i < jb && w < nc) ? W2[i * L + cb + w] : make_float2(0.f, 0.f);
-    for (int r = h * 32 + lane; r < Mr; r += 32 * rs) {
+    const int rstep = 32 * rs;
+    int r = h * 32 + lane;
+    float2 an[QB_CW];
+#pragma unroll
+    for (int w = 0; w < QB_CW; ++w)
+      an[w] = (w < nc && r < Mr) ? C[(size_t)(cb + w) * M + j0 + r] : make_float2(0.f, 0.f);
+    for (; r < Mr; r += rstep) {
+      float2 a[QB_CW];
+#pragma unroll
+      for (int w = 0; w < QB_CW; ++w) a[w] = an[w];
+      const int rn = r + rstep;
+#pragma unroll
+      for (int w = 0; w < QB_CW; ++w)
+        if (w < nc && rn < Mr) an[w] = C[(size_t)(cb + w) * M + j0 + rn];
       float2 v[QB_NB];
 #pragma unroll
       for (int i = 0; i < QB_NB; ++i) v[i] = (i < jb) ? Vs[i * ldv + r] : make_float2(0.f, 0.f);
 #pragma unroll
       for (int w = 0; w < QB_CW; ++w) {
         if (w < nc) {
-          float2* cp = C + (size_t)(cb + w) * M + j0 + r;
-          float2 a = *cp;
 #pragma unroll
           for (int i = 0; i < QB_NB; ++i) {
-            a.x = fmaf(-v[i].x, w2[i][w].x, fmaf(v[i].y, w2[i][w].y, a.x));
-            a.y = fmaf(-v[i].x, w2[i][w].y, fmaf(-v[i].y, w2[i][w].x, a.y));
+            a[w].x = fmaf(-v[i].x, w2[i][w].x, fmaf(v[i].y, w2[i][w].y, a[w].x));
+            a[w].y = fmaf(-v[i].x, w2[i][w].y, fmaf(-v[i].y, w2[i][w].x, a[w].y));
           }
-          *cp = a;
+          C[(size_t)(cb + w) * M + j0 + r] = a[w];
         }
       }
     }
@@ -600,8 +622,9 @@ cudaError_t launch_reorth(const float2* Qf, float2* Dbuf, const ProbPtr* ptrs, i
 
 // ---------------------------------------------------------------------------
 // Projection B^H = A^H Q with Q = Q_f (I + D) (the re-orthonormalised basis):
-// X = A^H Q_f in double-float arithmetic with the FP32 Q_f used as it is
-// (its entries are exact single floats), then B^H = X + X D.
+// X = A^H Q_f in double-float arithmetic, A^H from the double-float copy of
+// conj(A) and the FP32 Q_f used as it is (its entries are exact single
+// floats), then B^H = X + X D.
 // Complex products by Gauss's three multiplications: for alpha = a + ib
 // (from A^H) and beta = c + id (from Q_f),
 //   t1 = a (c + d),  t2 = d (a + b),  t3 = c (b - a),
@@ -643,14 +666,15 @@ __device__ __forceinline__ void fast2(float& h, float& lo) {
   h = s;
 }
 
-__global__ void __launch_bounds__(256) k_proj_df(const ProbPtr* __restrict__ ptrs, const float2* __restrict__ Qf,
-                                                 int m, int n, int l) {
+__global__ void __launch_bounds__(256) k_proj_df(const float4* __restrict__ thd, const float2* __restrict__ Qf,
+                                                 const ProbPtr* __restrict__ ptrs, int m, int n, int l) {
   __shared__ float4 Aab[PJ_TK][PJ_TM];  // (a_h, a_l, b_h, b_l)
   __shared__ float4 Asd[PJ_TK][PJ_TM];  // (a+b)_h, (a+b)_l, (b-a)_h, (b-a)_l
-  __shared__ float4 Bs[PJ_TK][PJ_TN];   // (c, d, (c+d)_h, (c+d)_l)
+  __shared__ float4 Bs[PJ_TK][PJ_TN + 1];  // (c, d, (c+d)_h, (c+d)_l); padded against bank conflicts
+                                          // of the k-fastest stores
   const int z = blockIdx.z;
   const int tm = blockIdx.y * PJ_TM, tn = blockIdx.x * PJ_TN;
-  const cplx* th = ptrs[z].theta;
+  const float4* th = thd + (size_t)z * m * n;
   const float2* q = Qf + (size_t)z * m * l;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   float h1[4][2], l1[4][2], h2[4][2], l2[4][2], h3[4][2], l3[4][2];
@@ -659,23 +683,17 @@ __global__ void __launch_bounds__(256) k_proj_df(const ProbPtr* __restrict__ ptr
 #pragma unroll
     for (int j = 0; j < 2; ++j) h1[i][j] = l1[i][j] = h2[i][j] = l2[i][j] = h3[i][j] = l3[i][j] = 0.f;
   for (int k0 = 0; k0 < m; k0 += PJ_TK) {
-    // A^H tile: element (r, k) = conj(theta[k][r]); consecutive threads read consecutive r
+    // A^H tile: element (r, k) = conj(theta[k][r]), pre-split; consecutive
+    // threads read consecutive r
     for (int e = tid; e < PJ_TM * PJ_TK; e += 256) {
       const int r = e % PJ_TM, kk = e / PJ_TM;
       const int gr = tm + r, gk = k0 + kk;
-      double a = 0.0, b = 0.0;
-      if (gr < n && gk < m) {
-        const cplx v = th[(size_t)gk * n + gr];
-        a = v.x;
-        b = -v.y;
-      }
-      const float ah = (float)a, al = (float)(a - (double)ah);
-      const float bh = (float)b, bl = (float)(b - (double)bh);
+      const float4 f = (gr < n && gk < m) ? th[(size_t)gk * n + gr] : make_float4(0.f, 0.f, 0.f, 0.f);
       float sh, se, dh, de;
-      two_sum(ah, bh, sh, se);
-      two_sum(bh, -ah, dh, de);
-      Aab[kk][r] = make_float4(ah, al, bh, bl);
-      Asd[kk][r] = make_float4(sh, se + (al + bl), dh, de + (bl - al));
+      two_sum(f.x, f.z, sh, se);
+      two_sum(f.z, -f.x, dh, de);
+      Aab[kk][r] = f;
+      Asd[kk][r] = make_float4(sh, se + (f.y + f.w), dh, de + (f.w - f.y));
     }
     // Q_f tile: element (k, c) at q[c * m + k]
     for (int e = tid; e < PJ_TK * PJ_TN; e += 256) {
@@ -730,11 +748,11 @@ __global__ void __launch_bounds__(256) k_proj_df(const ProbPtr* __restrict__ ptr
     }
 }
 
-cudaError_t launch_proj_df(const ProbPtr* ptrs, const float2* Qf, const float2* Dbuf, int m, int n, int l, int batch,
-                           cudaStream_t st) {
+cudaError_t launch_proj_df(const float4* thd, const ProbPtr* ptrs, const float2* Qf, const float2* Dbuf, int m, int n,
+                           int l, int batch, cudaStream_t st) {
   {
     ProfScope ps("k_zgemm_df[project]", st);
-    k_proj_df<<<dim3((l + PJ_TN - 1) / PJ_TN, (n + PJ_TM - 1) / PJ_TM, batch), 256, 0, st>>>(ptrs, Qf, m, n, l);
+    k_proj_df<<<dim3((l + PJ_TN - 1) / PJ_TN, (n + PJ_TM - 1) / PJ_TM, batch), 256, 0, st>>>(thd, Qf, ptrs, m, n, l);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
