@@ -334,7 +334,7 @@ def roofline(res, batch):
         "k_zgemm[sketch]": (8.0 * M * N_ * l * batch, "alu", fp64_peak, fp64_src, "kernels.cu"),
         "k_qr": ((16.0 * M * l * l - 16.0 * l ** 3 / 3) * batch, "alu", fp64_peak, fp64_src, "kernels.cu"),
         "k_zgemm[uv]": (8.0 * M * l * k * batch, "alu", fp64_peak, fp64_src, "kernels.cu"),
-        "k_zgemm_df[project]": (8.0 * M * N_ * l * batch, "alu", df_peak, df_src, "qr_blocked.cu"),
+        "k_zgemm_df[project]": (8.0 * M * N_ * l * batch, "alu", df_peak, df_src, "df_proj.cu"),
     }
     if dom not in per_launch:
         return None
@@ -519,7 +519,7 @@ def main():
                                                         "of B^H and Jacobi SVD)" if head["prec"] == "tf32"
                                                         else " (plain path)"),
                            "batch_per_gpu": batch, "distinct_theta": POOL, "parallelism": f"replicas x{world}",
-                           "l2": "inputs larger than L2: 9.7 GB of theta read per step",
+                           "l2": "inputs larger than L2: %.1f GB of theta read per step" % (batch * M * N_ * 16 / 1e9),
                            "max_abs_sigma_err_vs_exact": head["sig_err"],
                            "excess_frobenius_err": head["excess_err"]},
                 "forms": forms,

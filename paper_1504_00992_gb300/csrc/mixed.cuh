@@ -47,7 +47,9 @@ cudaError_t launch_qr_blk_f32(float2* A, float2* Q, int M, int L, int batch, cud
 bool reorth_fits(int M, int L);
 cudaError_t launch_reorth(const float2* Qf, float2* Dbuf, const ProbPtr* ptrs, int M, int L, int batch, int* status,
                           cudaStream_t st);
-// B^H = A^H Q_f (I + D) into ptrs[z].Yt (n x l column-major): double-float
+// B^H <- B^H (I + D) in place on ptrs[z].Yt (qr_blocked.cu).
+cudaError_t launch_fold_bh(const float2* Dbuf, const ProbPtr* ptrs, int n, int l, int batch, cudaStream_t st);
+// B^H = A^H Q_f (I + D) into ptrs[z].Yt (df_proj.cu) (n x l column-major): double-float
 // product with the FP32 Q_f, then the correction; after launch_reorth.
 cudaError_t launch_proj_df(const float4* thd, const ProbPtr* ptrs, const float2* Qf, const float2* Dbuf, int m, int n,
                            int l, int batch, cudaStream_t st);

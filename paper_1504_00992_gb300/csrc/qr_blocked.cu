@@ -533,7 +533,7 @@ __global__ void __launch_bounds__(256) k_fold(const float2* __restrict__ Qf, con
   float2* Qs = Ds + ((L * L + 1) & ~1);            // QF_ROWS x L column-major (16-byte aligned)
   const int z = blockIdx.y;
   const int r0 = blockIdx.x * QF_ROWS;
-  const float2* q = Qf + (size_t)z * M * L;
+  const float2* q = FROM_F32 ? Qf + (size_t)z * M * L : nullptr;
   cplx* X = FROM_F32 ? ptrs[z].Q : ptrs[z].Yt;  // output (and FP64 source when !FROM_F32)
   const float2* D = Dbase + (size_t)z * L * L;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -620,148 +620,14 @@ cudaError_t launch_reorth(const float2* Qf, float2* Dbuf, const ProbPtr* ptrs, i
   return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------------------
-// Projection B^H = A^H Q with Q = Q_f (I + D) (the re-orthonormalised basis):
-// X = A^H Q_f in double-float arithmetic, A^H from the double-float copy of
-// conj(A) and the FP32 Q_f used as it is (its entries are exact single
-// floats), then B^H = X + X D.
-// Complex products by Gauss's three multiplications: for alpha = a + ib
-// (from A^H) and beta = c + id (from Q_f),
-//   t1 = a (c + d),  t2 = d (a + b),  t3 = c (b - a),
-//   Re = t1 - t2,  Im = t1 + t3,
-// three double-float products instead of four; a, a + b, b - a are
-// double-float, c, d single floats, c + d a TwoSum pair.  64 x 32 output tile
-// per CTA, 4 x 2 outputs per thread, K in slices of 16 each closed by a
-// renormalising Fast2Sum of the accumulators.
-// ---------------------------------------------------------------------------
-enum { PJ_TM = 64, PJ_TN = 32, PJ_TK = 16 };
-
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float v = s - a;
-  e = (a - (s - v)) + (b - v);
-}
-// acc += (xh, xl) (yh, yl)
-__device__ __forceinline__ void dfx_dd(float& h, float& lo, float xh, float xl, float yh, float yl) {
-  const float ph = xh * yh;
-  const float pe = fmaf(xh, yh, -ph);
-  const float pc = fmaf(xh, yl, xl * yh);
-  float t, e;
-  two_sum(h, ph, t, e);
-  h = t;
-  lo += (e + pe) + pc;
-}
-// acc += x (yh, yl), x a single float
-__device__ __forceinline__ void dfx_sd(float& h, float& lo, float x, float yh, float yl) {
-  const float ph = x * yh;
-  const float pe = fmaf(x, yh, -ph);
-  float t, e;
-  two_sum(h, ph, t, e);
-  h = t;
-  lo += (e + pe) + x * yl;
-}
-__device__ __forceinline__ void fast2(float& h, float& lo) {
-  const float s = h + lo;
-  lo = lo - (s - h);
-  h = s;
-}
-
-__global__ void __launch_bounds__(256) k_proj_df(const float4* __restrict__ thd, const float2* __restrict__ Qf,
-                                                 const ProbPtr* __restrict__ ptrs, int m, int n, int l) {
-  __shared__ float4 Aab[PJ_TK][PJ_TM];  // (a_h, a_l, b_h, b_l)
-  __shared__ float4 Asd[PJ_TK][PJ_TM];  // (a+b)_h, (a+b)_l, (b-a)_h, (b-a)_l
-  __shared__ float4 Bs[PJ_TK][PJ_TN + 1];  // (c, d, (c+d)_h, (c+d)_l); padded against bank conflicts
-                                          // of the k-fastest stores
-  const int z = blockIdx.z;
-  const int tm = blockIdx.y * PJ_TM, tn = blockIdx.x * PJ_TN;
-  const float4* th = thd + (size_t)z * m * n;
-  const float2* q = Qf + (size_t)z * m * l;
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  float h1[4][2], l1[4][2], h2[4][2], l2[4][2], h3[4][2], l3[4][2];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 2; ++j) h1[i][j] = l1[i][j] = h2[i][j] = l2[i][j] = h3[i][j] = l3[i][j] = 0.f;
-  for (int k0 = 0; k0 < m; k0 += PJ_TK) {
-    // A^H tile: element (r, k) = conj(theta[k][r]), pre-split; consecutive
-    // threads read consecutive r
-    for (int e = tid; e < PJ_TM * PJ_TK; e += 256) {
-      const int r = e % PJ_TM, kk = e / PJ_TM;
-      const int gr = tm + r, gk = k0 + kk;
-      const float4 f = (gr < n && gk < m) ? th[(size_t)gk * n + gr] : make_float4(0.f, 0.f, 0.f, 0.f);
-      float sh, se, dh, de;
-      two_sum(f.x, f.z, sh, se);
-      two_sum(f.z, -f.x, dh, de);
-      Aab[kk][r] = f;
-      Asd[kk][r] = make_float4(sh, se + (f.y + f.w), dh, de + (f.w - f.y));
-    }
-    // Q_f tile: element (k, c) at q[c * m + k]
-    for (int e = tid; e < PJ_TK * PJ_TN; e += 256) {
-      const int kk = e % PJ_TK, c = e / PJ_TK;
-      const int gk = k0 + kk, gc = tn + c;
-      float2 v = make_float2(0.f, 0.f);
-      if (gk < m && gc < l) v = q[(size_t)gc * m + gk];
-      float sh, se;
-      two_sum(v.x, v.y, sh, se);
-      Bs[kk][c] = make_float4(v.x, v.y, sh, se);
-    }
-    __syncthreads();
-#pragma unroll 2
-    for (int kk = 0; kk < PJ_TK; ++kk) {
-      float4 b[2];
-      b[0] = Bs[kk][tx];
-      b[1] = Bs[kk][tx + 16];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const float4 ab = Aab[kk][ty + 16 * i];
-        const float4 sd = Asd[kk][ty + 16 * i];
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-          dfx_dd(h1[i][j], l1[i][j], ab.x, ab.y, b[j].z, b[j].w);  // a (c + d)
-          dfx_sd(h2[i][j], l2[i][j], b[j].y, sd.x, sd.y);          // d (a + b)
-          dfx_sd(h3[i][j], l3[i][j], b[j].x, sd.z, sd.w);          // c (b - a)
-        }
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        fast2(h1[i][j], l1[i][j]);
-        fast2(h2[i][j], l2[i][j]);
-        fast2(h3[i][j], l3[i][j]);
-      }
-    __syncthreads();
-  }
-  cplx* X = ptrs[z].Yt;  // n x l column-major
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int r = tm + ty + 16 * i, c = tn + tx + 16 * j;
-      if (r < n && c < l) {
-        const double t1 = (double)h1[i][j] + (double)l1[i][j];
-        const double t2 = (double)h2[i][j] + (double)l2[i][j];
-        const double t3 = (double)h3[i][j] + (double)l3[i][j];
-        X[(size_t)c * n + r] = cmk(t1 - t2, t1 + t3);
-      }
-    }
-}
-
-cudaError_t launch_proj_df(const float4* thd, const ProbPtr* ptrs, const float2* Qf, const float2* Dbuf, int m, int n,
-                           int l, int batch, cudaStream_t st) {
-  {
-    ProfScope ps("k_zgemm_df[project]", st);
-    k_proj_df<<<dim3((l + PJ_TN - 1) / PJ_TN, (n + PJ_TM - 1) / PJ_TM, batch), 256, 0, st>>>(thd, Qf, ptrs, m, n, l);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
+// B^H <- B^H (I + D) in place on ptrs[z].Yt (n x l column-major).
+cudaError_t launch_fold_bh(const float2* Dbuf, const ProbPtr* ptrs, int n, int l, int batch, cudaStream_t st) {
   static size_t attr = 0;
   const size_t sm_f = sizeof(float2) * ((size_t)((l * l + 1) & ~1) + (size_t)QF_ROWS * l);
   cudaError_t e = ensure_smem(k_fold<false>, sm_f, &attr);
   if (e != cudaSuccess) return e;
   ProfScope ps("k_fold[bh]", st);
-  k_fold<false><<<dim3((n + QF_ROWS - 1) / QF_ROWS, batch), 256, sm_f, st>>>(Qf, Dbuf, ptrs, n, l);
+  k_fold<false><<<dim3((n + QF_ROWS - 1) / QF_ROWS, batch), 256, sm_f, st>>>(nullptr, Dbuf, ptrs, n, l);
   return cudaGetLastError();
 }
 
