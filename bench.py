@@ -351,11 +351,56 @@ def roofline(res, batch):
             "frac": achieved / peak, "traffic": traffic, "peak_source": psrc}
 
 
+def run_rrsvd_checked(B, torch, dev, theta, sig, batch, steps=2, warm=1):
+    """Fixed-precision RRSVD (Alg. 2 accuracy check) on the single-bond stress
+    matrices: start at k=40, p=10 (l=50), rounds of r=10 probes until the
+    largest probe residual is below eps=1e-3 (the paper's setting; sigma_1=1)
+    or l reaches 200; q=2 power rounds on the grown basis; FP64.  Timed like
+    the headline (device buffers, CUDA events)."""
+    kk, p, q, r, eps, lmax = 40, 10, 2, 10, 1e-3, 200
+    plan = B.rrsvd_plan_create_ex(M, N_, kk, p, q, batch, B.TEBD_PREC_FP64, SEED, r, eps, lmax)
+    kcap, lcap = B.rrsvd_plan_dims(plan)
+    wsb = B.rrsvd_workspace_size(plan)
+    ws = torch.empty(wsb + 256, dtype=torch.uint8, device=dev)
+    wsp = (ws.data_ptr() + 255) // 256 * 256
+    sg = torch.zeros((batch, kcap), dtype=torch.float64, device=dev)
+    rk = torch.zeros(batch, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(s):
+        B.rrsvd_execute(plan, theta.data_ptr(), 7_000_000 + s * batch, sg.data_ptr(), 0, 0, 0, rk.data_ptr(), wsp,
+                        wsb, stream.cuda_stream)
+
+    for s in range(warm):
+        step(s)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for s in range(steps):
+        step(warm + s)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    widths = B.rrsvd_plan_widths(plan, batch)
+    ranks = rk.cpu().numpy()
+    s_h = sg.cpu().numpy()
+    err = max(float(np.abs(s_h[t, :ranks[t]] - sig[:ranks[t]]).max()) for t in range(batch))
+    B.rrsvd_plan_destroy(plan)
+    del ws
+    torch.cuda.empty_cache()
+    return {"value": steps * batch / (ms / 1e3), "unit": "truncations/s", "ms_per_step": ms / steps,
+            "widths_l": {"min": int(min(widths)), "max": int(max(widths)), "mean": float(np.mean(widths))},
+            "kept_rank_mean": float(np.mean(ranks)), "max_abs_sigma_err_vs_exact": err,
+            "workload": "single-bond stress 2000x2000, Alg. 2 accuracy check: k0=40, p=10, r=10 probes per round, "
+                        "eps=1e-3, l_max=200, q=2, FP64, %d instances per step" % batch}
+
+
 def run_tebd_many(B, I, torch, n_chains=256, steps=10, warm=2, unbatched_chains=16, unbatched_steps=3):
     """Many-chain batch: the chains of I.many_chain_specs (seed 0), dt = 0.01,
     p = 10, q = 1, all bonds of a parity of all chains per launch sequence,
-    sweeps replayed from CUDA graphs, tiles autotuned, 16 GB wave budget.
-    Compared with the same chains stepped one handle at a time."""
+    sweeps replayed from CUDA graphs, 16 GB wave budget; in the mixed form
+    (TF32, as the configuration asks) and in the FP64 form (tiles autotuned),
+    the latter also against the same chains stepped one handle at a time."""
     specs = I.many_chain_specs(n_chains, 0)
     dt, p, q = 0.01, 10, 1
 
@@ -370,19 +415,27 @@ def run_tebd_many(B, I, torch, n_chains=256, steps=10, warm=2, unbatched_chains=
         return steps_ * sum(2 * ((N - 1 + 1) // 2) + (N - 1) // 2 for N, _, _, _ in subset)
 
     chains = [(N, [d] * N, [chi] * (N - 1)) for N, d, chi, _ in specs]
-    sim = B.MultiTebd(chains, p, q, 0, use_graph=1, autotune=1, workspace_budget=16 << 30)
-    setup(sim.set_product_state, sim.set_gates, specs)
-    for _ in range(warm):
-        sim.step_even(); sim.step_odd(); sim.step_even()
-    sim.discarded_weight(0)   # synchronises
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        sim.step_even(); sim.step_odd(); sim.step_even()
-    sim.discarded_weight(0)
-    el = time.perf_counter() - t0
-    info = sim.workspace_info()
-    sim.close()
-    batched = updates(specs, steps) / el
+
+    def batched(prec):
+        kw = {"autotune": 1} if prec == B.TEBD_PREC_FP64 else {}
+        sim = B.MultiTebd(chains, p, q, 0, use_graph=1, workspace_budget=16 << 30, precision=prec, **kw)
+        setup(sim.set_product_state, sim.set_gates, specs)
+        for _ in range(warm):
+            sim.step_even(); sim.step_odd(); sim.step_even()
+        sim.discarded_weight(0)   # synchronises
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            sim.step_even(); sim.step_odd(); sim.step_even()
+        sim.discarded_weight(0)
+        el = time.perf_counter() - t0
+        info = sim.workspace_info()
+        _, _, sz = I.spin_ops(specs[0][1])
+        probe = [sim.expect(0, k, sz).real for k in range(specs[0][0])]
+        sim.close()
+        return updates(specs, steps) / el, info, np.array(probe)
+
+    mixed, info_m, probe_m = batched(B.TEBD_PREC_TF32)
+    fp64, info, probe_d = batched(B.TEBD_PREC_FP64)
     # unbatched: the first chains, each in its own handle, stepped in turn
     sub = specs[:unbatched_chains]
     sims = []
@@ -405,12 +458,15 @@ def run_tebd_many(B, I, torch, n_chains=256, steps=10, warm=2, unbatched_chains=
     for s1 in sims:
         s1.close()
     unbatched = updates(sub, unbatched_steps) / el2
-    return {"value": batched, "unit": "bond updates/s", "chains": n_chains, "steps_timed": steps,
-            "unbatched_value": unbatched, "unbatched_chains": unbatched_chains, "speedup_vs_unbatched":
-            batched / unbatched, "arena_bytes": info[0], "waves": [info[1], info[2]],
+    return {"value": mixed, "unit": "bond updates/s", "precision": "tf32 (mixed form)", "chains": n_chains,
+            "steps_timed": steps, "arena_bytes": info_m[0], "waves": [info_m[1], info_m[2]],
+            "fp64_value": fp64, "fp64_arena_bytes": info[0], "fp64_waves": [info[1], info[2]],
+            "speedup_mixed_vs_fp64": mixed / fp64,
+            "chain0_max_abs_sz_diff_mixed_vs_fp64": float(np.abs(probe_m - probe_d).max()),
+            "unbatched_fp64_value": unbatched, "unbatched_chains": unbatched_chains,
+            "speedup_fp64_batched_vs_unbatched": fp64 / unbatched,
             "workload": "256 XXZ chains, N~U{16..128}, d in {2,3,4}, chi_max in {32,64,128}, Delta~U[0,1], "
-                        "dt=0.01, p=10, q=1, Neel; FP64 path, graphs + autotuned tiles + 16 GB wave budget, "
-                        "after 2 warm-up steps"}
+                        "dt=0.01, p=10, q=1, Neel; graphs + 16 GB wave budget, after %d warm-up steps" % warm}
 
 
 def run_tebd_gradient(B, I, torch):
@@ -491,8 +547,9 @@ def main():
     k, l = head["k"], head["l"]
     gemm_f, qr_f, uv_f = flops_rrsvd(M, N_, k, l, Q_PI)
 
-    tebd = many = grad = None
+    tebd = many = grad = checked = None
     if not args.no_tebd:
+        checked = run_rrsvd_checked(B, torch, dev, theta, sig, batch)
         tebd = run_tebd_c1(B, I, torch)
         many = run_tebd_many(B, I, torch, steps=2)
         grad = run_tebd_gradient(B, I, torch)
@@ -527,7 +584,7 @@ def main():
                 "roofline": roof, "kernel_time_ms": shares, "gpu_launches": launches,
                 "flops_per_update": {"gemm": gemm_f, "qr": qr_f, "uv": uv_f},
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": head["clocks"], "tebd_c1": tebd,
-                "tebd_many_chains": many, "tebd_gradient": grad}
+                "tebd_many_chains": many, "tebd_gradient": grad, "rrsvd_accuracy_check": checked}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

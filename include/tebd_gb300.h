@@ -66,8 +66,12 @@ enum {
  *   TEBD_PREC_TF32: Y0 = A Omega and power rounds 1..q-1 on the tensor cores
  *     in TF32 with FP32 accumulation and FP32 QR; power round q (Y0 when
  *     q = 0) as the refinement pass in split 3xTF32 products (FP32-level
- *     accuracy); the last QR, B = Q^H A, the small SVD and lambda in FP64.
- *     Standalone RRSVD plans only. */
+ *     accuracy); the last basis re-orthonormalised FP64-accurately (FP32
+ *     QR and a double-float Loewdin correction; FP64 QR when l > 144);
+ *     B = Q^H A, U and V FP64-accurate in double-float arithmetic; the QR
+ *     of B^H, the Jacobi SVD and lambda in FP64.  Omega comes from the same
+ *     Philox words by an FP32 Box-Muller.  Standalone RRSVD plans and TEBD
+ *     handles (not with tebd_record or autotune). */
 enum { TEBD_PREC_FP64 = 0, TEBD_PREC_TF32 = 2 };
 
 /* ------------------------------------------------------------------------
@@ -84,7 +88,7 @@ typedef struct {
   int p;                /* RRSVD oversampling, >= 0 */
   int q;                /* RRSVD power iterations, >= 0 */
   uint64_t seed;        /* Philox key word 0 */
-  int precision;        /* TEBD_PREC_* */
+  int precision;        /* TEBD_PREC_* (TF32: every bond update in the mixed form) */
   double sv_cutoff;     /* keep s_i > sv_cutoff * s_1 among the first k; <= 0 selects 1e-14 */
   int chain;            /* chain index entering the Philox counter (default 0); with
                            tebd_create_multi, chain c uses chain + c */
@@ -116,10 +120,13 @@ int tebd_create_ex(const tebd_desc_t* desc, tebd_t* out);
  * and precision must agree, use_graph / autotune / workspace_budget are read
  * from descs[0].  tebd_step_even/odd then update the bonds of that parity of
  * every chain in one launch sequence (in waves when a workspace budget is
- * set); the per-chain calls (state, gates, expect, lambda, weights, MPS)
- * act on the chain chosen by tebd_select_chain (default 0).
- * Errors: TEBD_EINVAL (n_chains < 1, inconsistent p/q/seed/precision, as
- * tebd_create_ex), TEBD_ENOMEM, TEBD_ECUDA. */
+ * set; with TEBD_PREC_TF32 the budget also covers the FP32 arrays, laid out
+ * at each wave's largest bond, and the bonds are grouped by shape); the
+ * per-chain calls (state, gates, expect, lambda, weights, MPS) act on the
+ * chain chosen by tebd_select_chain (default 0).
+ * Errors: TEBD_EINVAL (n_chains < 1, inconsistent p/q/seed/precision,
+ * autotune with TEBD_PREC_TF32, as tebd_create_ex), TEBD_ENOMEM,
+ * TEBD_ECUDA. */
 int tebd_create_multi(int n_chains, const tebd_desc_t* descs, tebd_t* out);
 int tebd_num_chains(tebd_t h, int* out);
 int tebd_select_chain(tebd_t h, int chain);
@@ -191,7 +198,8 @@ int tebd_sweep_count(tebd_t h, int64_t* out);
  * tebd_step_* first stores a device checkpoint of the chain's tensors,
  * Schmidt values, gates and bond dimensions (one allocation per sweep,
  * freed by the next tebd_record(h, 1) or tebd_destroy).  Turning it on
- * clears earlier checkpoints.  Errors: TEBD_ENOTIMPL (several chains),
+ * clears earlier checkpoints.  Errors: TEBD_ENOTIMPL (several chains, or a
+ * TEBD_PREC_TF32 handle: the reverse pass differentiates the FP64 form),
  * TEBD_ENOMEM. */
 int tebd_record(tebd_t h, int on);
 

@@ -414,15 +414,15 @@ class Tebd:
     """Owning wrapper of a tebd_t handle (the calls above, bound to one chain)."""
 
     def __init__(self, N, d, chi_max, p, q, seed=0, d_site=None, chi_bond=None, sv_cutoff=0.0, chain=0,
-                 stream=None, use_graph=0, autotune=0):
+                 stream=None, use_graph=0, autotune=0, precision=TEBD_PREC_FP64):
         self.N = N
         self.dims = list(d_site) if d_site is not None else [d] * N
         self.chi_bond = list(chi_bond) if chi_bond is not None else [chi_max] * (N - 1)
         if d_site is None and chi_bond is None and sv_cutoff == 0.0 and chain == 0 and not use_graph \
-                and not autotune:
+                and not autotune and precision == TEBD_PREC_FP64:
             self.h = tebd_create(N, d, chi_max, p, q, seed)
         else:
-            self.h = tebd_create_ex(N, self.dims, self.chi_bond, p, q, seed, TEBD_PREC_FP64, sv_cutoff, chain,
+            self.h = tebd_create_ex(N, self.dims, self.chi_bond, p, q, seed, precision, sv_cutoff, chain,
                                     use_graph, autotune)
         caps = []
         for b in range(N - 1):
@@ -494,10 +494,11 @@ def _caps(dims, chi_bond):
 class MultiTebd:
     """Many chains in one handle; per-chain calls take the chain index."""
 
-    def __init__(self, chains, p, q, seed=0, use_graph=0, autotune=0, workspace_budget=0, stream=None):
+    def __init__(self, chains, p, q, seed=0, use_graph=0, autotune=0, workspace_budget=0, stream=None,
+                 precision=TEBD_PREC_FP64):
         self.chains = [(N, list(ds), list(cb)) for N, ds, cb in chains]
-        self.h = tebd_create_multi(self.chains, p, q, seed, use_graph=use_graph, autotune=autotune,
-                                   workspace_budget=workspace_budget)
+        self.h = tebd_create_multi(self.chains, p, q, seed, precision=precision, use_graph=use_graph,
+                                   autotune=autotune, workspace_budget=workspace_budget)
         self.caps = [_caps(ds, cb) for _, ds, cb in self.chains]
         if stream is not None:
             tebd_set_stream(self.h, stream)

@@ -128,6 +128,7 @@ struct Wave {
   int first = 0, count = 0;
   Caps cap{};
   int tiles[6] = {0, 0, 0, 0, 0, 0};
+  MixedSizes ms{};  // TF32 handles: the wave's FP32 arrays at its capacities
 };
 
 struct ParitySet {
@@ -154,6 +155,8 @@ struct tebd_s {
   double* wacc = nullptr;   // 2 per chain: sum w, prod (1 - w)
   double* wout = nullptr;   // per problem of the larger parity
   uint64_t* sweep_dev = nullptr;
+  int* tcerr = nullptr;        // tensor-core wait timeout flag (TF32 handles)
+  char* mixed = nullptr;       // FP32 arrays of the current wave (TF32 handles)
   cplx* op_dev = nullptr;
   cplx* out_dev = nullptr;
   double* one_lam = nullptr;
@@ -184,10 +187,16 @@ static void free_ckpts(tebd_s* h) {
 }
 
 static int tebd_check_status(tebd_t h) {
-  int st = 0;
+  int st = 0, te = 0;
   CU_OR(h, cudaMemcpyAsync(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  if (h->tcerr) CU_OR(h, cudaMemcpyAsync(&te, h->tcerr, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CU_OR(h, cudaStreamSynchronize(h->stream));
-  if (st & 1) h->err.set(TEBD_ENUMERIC, "a bond update met a zero or non-finite theta");
+  if (te) h->err.set(TEBD_ETIMEOUT, "a tensor-core pipeline wait timed out");
+  else if (st & 4)
+    h->err.set(TEBD_ENUMERIC, "the re-orthonormalisation of an FP32 basis met a non-finite or far from orthonormal "
+                              "basis");
+  else if (st & 1)
+    h->err.set(TEBD_ENUMERIC, "a bond update met a zero or non-finite theta");
   return h->err.code;
 }
 
@@ -264,7 +273,8 @@ extern "C" int tebd_create_multi(int n_chains, const tebd_desc_t* descs, tebd_t*
   if (n_chains < 1 || !descs) return TEBD_EINVAL;
   const tebd_desc_t& d0 = descs[0];
   if (d0.p < 0 || d0.q < 0) return TEBD_EINVAL;
-  if (d0.precision != TEBD_PREC_FP64) return TEBD_ENOTIMPL;
+  if (d0.precision != TEBD_PREC_FP64 && d0.precision != TEBD_PREC_TF32) return TEBD_ENOTIMPL;
+  if (d0.precision == TEBD_PREC_TF32 && d0.autotune) return TEBD_EINVAL;  // the tile autotuner is for FP64 GEMMs
   for (int c = 0; c < n_chains; ++c) {
     const tebd_desc_t& dc = descs[c];
     if (dc.N < 2 || dc.p != d0.p || dc.q != d0.q || dc.seed != d0.seed || dc.precision != d0.precision)
@@ -338,6 +348,7 @@ extern "C" int tebd_create_multi(int n_chains, const tebd_desc_t* descs, tebd_t*
   const size_t st_off = off; off += ALIGN;
   const size_t wacc_off = off; off += align_up(sizeof(double) * 2 * n_chains);
   const size_t sweep_off = off; off += ALIGN;
+  const size_t tcerr_off = off; off += ALIGN;
   const size_t op_off = off; off += align_up(sizeof(cplx) * 64 * 64) + ALIGN;
   // problems of each parity, chain-major, and their waves under the budget
   const size_t budget = d0.workspace_budget;
@@ -345,19 +356,41 @@ extern "C" int tebd_create_multi(int n_chains, const tebd_desc_t* descs, tebd_t*
   std::vector<WsLayout> lay[2];
   std::vector<size_t> pbytes[2];
   int max_batch = 0;
+  const bool tf32 = h->precision == TEBD_PREC_TF32;
+  size_t mixed_max = 0;
+  auto bond_caps = [&](const ChainH& C, int b, int& mc, int& nc, int& kc, int& lc) {
+    mc = C.d[b] * C.cap_ext[b];
+    nc = C.d[b + 1] * C.cap_ext[b + 2];
+    kc = std::min(C.cap_ext[b + 1], std::min(mc, nc));
+    lc = std::min(kc + h->p, std::min(mc, nc));
+  };
   for (int par = 0; par < 2; ++par) {
     ParitySet& ps = h->par[par];
     for (int c = 0; c < n_chains; ++c) {
       const ChainH& C = h->ch[c];
       for (int b = par; b < C.N - 1; b += 2) {
-        const int mc = C.d[b] * C.cap_ext[b], nc = C.d[b + 1] * C.cap_ext[b + 2];
-        const int kc = std::min(C.cap_ext[b + 1], std::min(mc, nc));
-        const int lc = std::min(kc + h->p, std::min(mc, nc));
+        int mc, nc, kc, lc;
+        bond_caps(C, b, mc, nc, kc, lc);
         if (lc > 512) { delete h; return TEBD_ENOTIMPL; }
         ps.bonds.push_back({c, b});
-        lay[par].push_back(ws_layout(mc, nc, kc, lc, true, true));
-        pbytes[par].push_back(align_up(sizeof(cplx) * (size_t)mc * nc) + lay[par].back().total);
       }
+    }
+    if (tf32) {
+      // the FP32 arrays of a wave are laid out at its capacities: group bonds
+      // of similar shape (largest first) so that little of them is padding
+      std::stable_sort(ps.bonds.begin(), ps.bonds.end(), [&](const std::pair<int, int>& x, const std::pair<int, int>& y) {
+        int m1, n1, k1, l1, m2, n2, k2, l2;
+        bond_caps(h->ch[x.first], x.second, m1, n1, k1, l1);
+        bond_caps(h->ch[y.first], y.second, m2, n2, k2, l2);
+        if (l1 != l2) return l1 > l2;
+        return (long long)m1 * n1 > (long long)m2 * n2;
+      });
+    }
+    for (const auto& cb : ps.bonds) {
+      int mc, nc, kc, lc;
+      bond_caps(h->ch[cb.first], cb.second, mc, nc, kc, lc);
+      lay[par].push_back(ws_layout(mc, nc, kc, lc, true, true));
+      pbytes[par].push_back(align_up(sizeof(cplx) * (size_t)mc * nc) + lay[par].back().total);
     }
     ps.batch = (int)ps.bonds.size();
     max_batch = std::max(max_batch, ps.batch);
@@ -365,22 +398,26 @@ extern "C" int tebd_create_multi(int n_chains, const tebd_desc_t* descs, tebd_t*
     Wave w;
     w.first = 0;
     for (int i = 0; i < ps.batch; ++i) {
-      if (w.count > 0 && budget > 0 && acc + pbytes[par][i] > budget) {
+      const int c = ps.bonds[i].first, b = ps.bonds[i].second;
+      const ChainH& C = h->ch[c];
+      int mc, nc, kc, lc;
+      bond_caps(C, b, mc, nc, kc, lc);
+      Caps cp = w.cap;
+      cp.m = std::max(cp.m, mc); cp.n = std::max(cp.n, nc); cp.k = std::max(cp.k, kc); cp.l = std::max(cp.l, lc);
+      cp.cl = std::max(cp.cl, C.cap_ext[b]); cp.cr = std::max(cp.cr, C.cap_ext[b + 2]);
+      cp.dl = std::max(cp.dl, C.d[b]); cp.dr = std::max(cp.dr, C.d[b + 1]);
+      const size_t mix = tf32 ? mixed_bytes(mixed_sizes(cp.m, cp.n, cp.k, cp.l), w.count + 1) : 0;
+      if (w.count > 0 && budget > 0 && acc + pbytes[par][i] + mix > budget) {
         ps.waves.push_back(w);
         ws_max = std::max(ws_max, acc);
         w = Wave();
         w.first = i;
         acc = 0;
+        cp = w.cap;
+        cp.m = mc; cp.n = nc; cp.k = kc; cp.l = lc;
+        cp.cl = C.cap_ext[b]; cp.cr = C.cap_ext[b + 2]; cp.dl = C.d[b]; cp.dr = C.d[b + 1];
       }
-      const int c = ps.bonds[i].first, b = ps.bonds[i].second;
-      const ChainH& C = h->ch[c];
-      const int mc = C.d[b] * C.cap_ext[b], nc = C.d[b + 1] * C.cap_ext[b + 2];
-      const int kc = std::min(C.cap_ext[b + 1], std::min(mc, nc));
-      const int lc = std::min(kc + h->p, std::min(mc, nc));
-      Caps& cp = w.cap;
-      cp.m = std::max(cp.m, mc); cp.n = std::max(cp.n, nc); cp.k = std::max(cp.k, kc); cp.l = std::max(cp.l, lc);
-      cp.cl = std::max(cp.cl, C.cap_ext[b]); cp.cr = std::max(cp.cr, C.cap_ext[b + 2]);
-      cp.dl = std::max(cp.dl, C.d[b]); cp.dr = std::max(cp.dr, C.d[b + 1]);
+      w.cap = cp;
       acc += pbytes[par][i];
       w.count++;
     }
@@ -388,6 +425,11 @@ extern "C" int tebd_create_multi(int n_chains, const tebd_desc_t* descs, tebd_t*
       ps.waves.push_back(w);
       ws_max = std::max(ws_max, acc);
     }
+    if (tf32)
+      for (Wave& wv : ps.waves) {
+        wv.ms = mixed_sizes(wv.cap.m, wv.cap.n, wv.cap.k, wv.cap.l);
+        mixed_max = std::max(mixed_max, mixed_bytes(wv.ms, wv.count));
+      }
   }
   const size_t wout_off = off; off += align_up(sizeof(double) * std::max(1, max_batch));
   const size_t desc_off = off;
@@ -395,6 +437,8 @@ extern "C" int tebd_create_multi(int n_chains, const tebd_desc_t* descs, tebd_t*
   off += 2 * desc_per + align_up(sizeof(Dims) * std::max(1, max_batch));  // + autotuner scratch dims
   const size_t ws_off = off;
   off += ws_max;
+  const size_t mixed_off = off;
+  off += align_up(mixed_max);
   h->arena_bytes = off;
   if (cudaMalloc(&h->arena, h->arena_bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -402,11 +446,18 @@ extern "C" int tebd_create_multi(int n_chains, const tebd_desc_t* descs, tebd_t*
     return TEBD_ENOMEM;
   }
   char* A = h->arena;
-  if (cudaMemset(A, 0, h->arena_bytes - ws_max) != cudaSuccess) { tebd_free(h); return TEBD_ECUDA; }
+  if (cudaMemset(A, 0, ws_off) != cudaSuccess) { tebd_free(h); return TEBD_ECUDA; }
   h->one_lam = (double*)(A + one_off);
   h->status = (int*)(A + st_off);
   h->wacc = (double*)(A + wacc_off);
   h->sweep_dev = (uint64_t*)(A + sweep_off);
+  if (tf32) {
+    h->tcerr = (int*)(A + tcerr_off);
+    h->mixed = A + mixed_off;
+    for (int par = 0; par < 2; ++par)
+      for (const Wave& w : h->par[par].waves)
+        if (mixed_prepare(w.cap) != cudaSuccess) { cudaGetLastError(); tebd_free(h); return TEBD_ECUDA; }
+  }
   h->op_dev = (cplx*)(A + op_off);
   h->out_dev = (cplx*)(A + op_off + align_up(sizeof(cplx) * 64 * 64));
   h->wout = (double*)(A + wout_off);
@@ -701,9 +752,15 @@ static cudaError_t enqueue_sweep(tebd_t h, int parity) {
     cudaError_t e;
     if ((e = launch_plan(ptrs, dims, w.count, h->p, h->stream)) != cudaSuccess) return e;
     if ((e = launch_theta(dims, ptrs, w.count, w.cap, h->stream)) != cudaSuccess) return e;
-    if ((e = run_rrsvd(dims, ptrs, w.count, w.cap, h->q, h->seed, 0, 0, -1, h->status, h->stream, h->sweep_dev,
-                       tuned ? w.tiles : nullptr)) != cudaSuccess)
+    if (h->precision == TEBD_PREC_TF32) {
+      const MixedPtrs mp = mixed_carve(h->mixed, w.ms, w.count);
+      if ((e = run_rrsvd_mixed(dims, ptrs, w.count, w.cap, mp, h->q, h->seed, 0, 0, -1, h->status, h->tcerr,
+                               h->stream, h->sweep_dev)) != cudaSuccess)
+        return e;
+    } else if ((e = run_rrsvd(dims, ptrs, w.count, w.cap, h->q, h->seed, 0, 0, -1, h->status, h->stream,
+                              h->sweep_dev, tuned ? w.tiles : nullptr)) != cudaSuccess) {
       return e;
+    }
     if ((e = launch_rebuild(dims, ptrs, w.count, h->cutoff, h->wout + w.first, h->status, h->stream)) != cudaSuccess)
       return e;
     if ((e = launch_wacc(dims, ptrs, h->wout + w.first, w.count, h->wacc, h->stream)) != cudaSuccess) return e;
@@ -901,6 +958,10 @@ extern "C" int tebd_record(tebd_t h, int on) {
   if (!h) return TEBD_EINVAL;
   if (h->err.code) return h->err.code;
   if (h->ch.size() != 1) { h->err.set(TEBD_ENOTIMPL, "recording needs a single-chain handle"); return h->err.code; }
+  if (h->precision != TEBD_PREC_FP64) {
+    h->err.set(TEBD_ENOTIMPL, "the reverse pass differentiates the FP64 form");
+    return h->err.code;
+  }
   if (on) {
     CU_OR(h, cudaStreamSynchronize(h->stream));
     free_ckpts(h);
@@ -1253,6 +1314,11 @@ extern "C" int rrsvd_execute_host(rrsvd_plan_t P, const double* theta, int64_t c
   CU_OR(P, cudaMemcpyAsync(&tce, P->tcerr, sizeof(int), cudaMemcpyDeviceToHost, st));
   CU_OR(P, cudaStreamSynchronize(st));
   if (tce) { P->err.set(TEBD_ETIMEOUT, "a tensor-core pipeline wait expired"); return P->err.code; }
+  if (stv & 4) {
+    P->err.set(TEBD_ENUMERIC, "the re-orthonormalisation of an FP32 basis met a non-finite or far from orthonormal "
+                              "basis");
+    return P->err.code;
+  }
   if (stv & 1) { P->err.set(TEBD_ENUMERIC, "an instance had a zero or non-finite theta"); return P->err.code; }
   return TEBD_OK;
 }

@@ -55,16 +55,23 @@ __device__ __forceinline__ void fast2(float& h, float& lo) {
   h = s;
 }
 
+// thd and Q_f at capacity mc x nc and mc x lc per instance; the instance's
+// own (m, n, l) from dims bound the sum and the output (D.n x D.l, compact).
 __global__ void __launch_bounds__(256) k_proj_df(const float4* __restrict__ thd, const float2* __restrict__ Qf,
-                                                 const ProbPtr* __restrict__ ptrs, int m, int n, int l) {
+                                                 const Dims* __restrict__ dims, const ProbPtr* __restrict__ ptrs,
+                                                 int mc, int nc, int lc) {
   __shared__ float4 Aab[PJ_TK][PJ_TM];  // (a_h, a_l, b_h, b_l)
   __shared__ float4 Asd[PJ_TK][PJ_TM];  // (a+b)_h, (a+b)_l, (b-a)_h, (b-a)_l
   __shared__ float4 Bs[PJ_TK][PJ_TN + 1];  // (c, d, (c+d)_h, (c+d)_l); padded against bank conflicts
                                           // of the k-fastest stores
   const int z = blockIdx.z;
+  const Dims Dm = dims[z];
+  if (!Dm.active) return;
+  const int m = Dm.m, n = Dm.n, l = Dm.l;
   const int tm = blockIdx.y * PJ_TM, tn = blockIdx.x * PJ_TN;
-  const float4* th = thd + (size_t)z * m * n;
-  const float2* q = Qf + (size_t)z * m * l;
+  if (tm >= n || tn >= l) return;
+  const float4* th = thd + (size_t)z * mc * nc;
+  const float2* q = Qf + (size_t)z * mc * lc;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   float h1[4][2], l1[4][2], h2[4][2], l2[4][2], h3[4][2], l3[4][2];
 #pragma unroll
@@ -77,7 +84,7 @@ __global__ void __launch_bounds__(256) k_proj_df(const float4* __restrict__ thd,
     for (int e = tid; e < PJ_TM * PJ_TK; e += 256) {
       const int r = e % PJ_TM, kk = e / PJ_TM;
       const int gr = tm + r, gk = k0 + kk;
-      const float4 f = (gr < n && gk < m) ? th[(size_t)gk * n + gr] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 f = (gr < n && gk < m) ? th[(size_t)gk * nc + gr] : make_float4(0.f, 0.f, 0.f, 0.f);
       float sh, se, dh, de;
       two_sum(f.x, f.z, sh, se);
       two_sum(f.z, -f.x, dh, de);
@@ -89,7 +96,7 @@ __global__ void __launch_bounds__(256) k_proj_df(const float4* __restrict__ thd,
       const int kk = e % PJ_TK, c = e / PJ_TK;
       const int gk = k0 + kk, gc = tn + c;
       float2 v = make_float2(0.f, 0.f);
-      if (gk < m && gc < l) v = q[(size_t)gc * m + gk];
+      if (gk < m && gc < l) v = q[(size_t)gc * mc + gk];
       float sh, se;
       two_sum(v.x, v.y, sh, se);
       Bs[kk][c] = make_float4(v.x, v.y, sh, se);
@@ -137,15 +144,16 @@ __global__ void __launch_bounds__(256) k_proj_df(const float4* __restrict__ thd,
     }
 }
 
-cudaError_t launch_proj_df(const float4* thd, const ProbPtr* ptrs, const float2* Qf, const float2* Dbuf, int m, int n,
-                           int l, int batch, cudaStream_t st) {
+cudaError_t launch_proj_df(const float4* thd, const Dims* dims, const ProbPtr* ptrs, const float2* Qf,
+                           const float2* Dbuf, int m, int n, int l, int batch, cudaStream_t st) {
   {
     ProfScope ps("k_zgemm_df[project]", st);
-    k_proj_df<<<dim3((l + PJ_TN - 1) / PJ_TN, (n + PJ_TM - 1) / PJ_TM, batch), 256, 0, st>>>(thd, Qf, ptrs, m, n, l);
+    k_proj_df<<<dim3((l + PJ_TN - 1) / PJ_TN, (n + PJ_TM - 1) / PJ_TM, batch), 256, 0, st>>>(thd, Qf, dims, ptrs, m,
+                                                                                             n, l);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  return launch_fold_bh(Dbuf, ptrs, n, l, batch, st);
+  return launch_fold_bh(Dbuf, dims, ptrs, n, l, batch, st);
 }
 
 }  // namespace tg

@@ -408,12 +408,15 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr(const Dims* __restrict__ dims
     s = block_sum(s, red);
     if (tid == 0) {
       const cplx x0 = aj[j];
-      const double ax0 = sqrt(cabs2(x0)), nx = sqrt(s);
-      if (nx == 0.0) {
+      // |x0| by hypot: the phase x0/|x0| must stay on the unit circle for H to be unitary
+      const double ax0 = hypot(x0.x, x0.y);
+      const double nx = sqrt(s);
+      if (!(nx >= 1e-150)) {  // zero column, or one so small that tau would overflow
         tau[j] = 0.0;
         alph[j] = cmk(0.0, 0.0);
       } else {
-        const cplx ph = (ax0 > 0.0) ? cscale(x0, 1.0 / ax0) : cmk(1.0, 0.0);
+        // the phase of a leading entry negligible against ||x|| is not used
+        const cplx ph = (ax0 > 1e-15 * nx) ? cscale(x0, 1.0 / ax0) : cmk(1.0, 0.0);
         alph[j] = cscale(ph, -nx);
         aj[j] = cscale(ph, ax0 + nx);  // v_0 = x_0 - alpha
         tau[j] = 1.0 / (nx * (nx + ax0));
@@ -606,11 +609,13 @@ __global__ void __launch_bounds__(JAC_THREADS) k_jacobi(const Dims* __restrict__
     if (lane == 0) sv[c] = sqrt(s);
   }
   __syncthreads();
+  // rank by descending value, ties by index; a NaN value ranks below every
+  // number, so perm is a permutation of 0..L-1 whatever the input
   for (int c = tid; c < L; c += blockDim.x) {
-    const double s = sv[c];
+    const double s = (sv[c] == sv[c]) ? sv[c] : -1.0;
     int rk = 0;
     for (int j = 0; j < L; ++j) {
-      const double t = sv[j];
+      const double t = (sv[j] == sv[j]) ? sv[j] : -1.0;
       rk += (t > s) || (t == s && j < c);
     }
     perm[rk] = c;

@@ -105,19 +105,23 @@ __device__ __forceinline__ void df_add2(float& h, float& l, float oh, float ol) 
   l = e - (h - s);
 }
 
-__global__ void __launch_bounds__(256) k_conv_theta(const MixedPtrs mp, const ProbPtr* __restrict__ ptrs, int m, int n,
-                                                    int K1, int K2, int want_lo) {
+__global__ void __launch_bounds__(256) k_conv_theta(const MixedPtrs mp, const Dims* __restrict__ dims,
+                                                    const ProbPtr* __restrict__ ptrs, int mc, int nc, int K1, int K2,
+                                                    int want_lo) {
   __shared__ float2 tile[32][33];  // TF32 hi and remainder computed once per element
   __shared__ float2 tlo[32][33];
   __shared__ float red[16];
   const int z = blockIdx.z;
+  const Dims D = dims[z];
+  if (!D.active) return;
+  const int m = D.m, n = D.n;  // this instance (theta is compact m x n); copies at capacity mc x nc
   const cplx* th = ptrs[z].theta;
   const int half1 = K1 / 2, half2 = K2 / 2;  // complex columns of thf / tha incl. padding
-  float2* fh = reinterpret_cast<float2*>(mp.thf_hi + (size_t)z * m * K1);
-  float2* fl = reinterpret_cast<float2*>(mp.thf_lo + (size_t)z * m * K1);
-  float2* ah = reinterpret_cast<float2*>(mp.tha_hi + (size_t)z * n * K2);
-  float2* al = reinterpret_cast<float2*>(mp.tha_lo + (size_t)z * n * K2);
-  float4* dd = mp.thd ? mp.thd + (size_t)z * m * n : nullptr;
+  float2* fh = reinterpret_cast<float2*>(mp.thf_hi + (size_t)z * mc * K1);
+  float2* fl = reinterpret_cast<float2*>(mp.thf_lo + (size_t)z * mc * K1);
+  float2* ah = reinterpret_cast<float2*>(mp.tha_hi + (size_t)z * nc * K2);
+  float2* al = reinterpret_cast<float2*>(mp.tha_lo + (size_t)z * nc * K2);
+  float4* dd = mp.thd ? mp.thd + (size_t)z * mc * nc : nullptr;
   const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   float sh = 0.f, sl = 0.f;  // double-float sum of |theta|^2 over this thread's elements
@@ -131,11 +135,11 @@ __global__ void __launch_bounds__(256) k_conv_theta(const MixedPtrs mp, const Pr
     const float lr = tf32_rna((xh - hr) + xl), lm = tf32_rna((yh - hm) + yl);
     tile[i][tx] = make_float2(hr, hm);
     tlo[i][tx] = make_float2(lr, lm);
-    if (r < m && c < half1) {
+    if (r < mc && c < half1) {
       fh[(int64_t)r * half1 + c] = make_float2(hr, hm);
       if (want_lo) fl[(int64_t)r * half1 + c] = make_float2(lr, lm);
     }
-    if (dd && r < m && c < n) dd[(int64_t)r * n + c] = make_float4(xh, xl, -yh, -yl);
+    if (dd && r < mc && c < nc) dd[(int64_t)r * nc + c] = make_float4(xh, xl, -yh, -yl);
     // |v|^2 = xh^2 + yh^2 + 2 (xh xl + yh yl) + O(2^-48)
     const float p1 = xh * xh, e1 = fmaf(xh, xh, -p1);
     const float p2 = yh * yh, e2 = fmaf(yh, yh, -p2);
@@ -159,7 +163,7 @@ __global__ void __launch_bounds__(256) k_conv_theta(const MixedPtrs mp, const Pr
   }
   for (int i = ty; i < 32; i += 8) {
     const int c = c0 + i, r = r0 + tx;  // output row c, complex column r: conj of element (r, c)
-    if (c < n && r < half2) {
+    if (c < nc && r < half2) {
       const float2 h = tile[tx][i], l = tlo[tx][i];
       ah[(int64_t)c * half2 + r] = make_float2(h.x, -h.y);
       if (want_lo) al[(int64_t)c * half2 + r] = make_float2(l.x, -l.y);
@@ -169,8 +173,10 @@ __global__ void __launch_bounds__(256) k_conv_theta(const MixedPtrs mp, const Pr
 
 // ||theta||_F^2 of each instance: its tile partials summed into the NPART
 // fixed partial sums the epilogue reads (deterministic order).
-__global__ void k_part_reduce(const double* __restrict__ tpart, int ntile, const ProbPtr* __restrict__ ptrs) {
+__global__ void k_part_reduce(const double* __restrict__ tpart, int ntile, const Dims* __restrict__ dims,
+                              const ProbPtr* __restrict__ ptrs) {
   const int z = blockIdx.x;
+  if (!dims[z].active) return;
   const int i = threadIdx.x;  // < NPART
   double s = 0.0;
   for (int t = i; t < ntile; t += NPART) s += tpart[(size_t)z * ntile + t];
@@ -179,15 +185,21 @@ __global__ void k_part_reduce(const double* __restrict__ tpart, int ntile, const
 
 // Omega (the Philox words of the FP64 path, FP32 Box-Muller) written directly as Bt (Np x K1), and
 // its TF32 remainder when the sketch itself is the refinement pass (q = 0).
-__global__ void k_omega_bt(const MixedPtrs mp, const Dims* __restrict__ dims, int n, int l, int Np, int K1,
-                           uint64_t seed, uint64_t sweep, int64_t chain0, int chain_stride, int want_lo) {
+// Instance z: chain chain0 + z chain_stride and the given sweep, or (chain_stride
+// < 0) its own chain index and *sweep_dev, like k_omega.
+__global__ void k_omega_bt(const MixedPtrs mp, const Dims* __restrict__ dims, int Np, int K1, uint64_t seed,
+                           uint64_t sweep, int64_t chain0, int chain_stride, int want_lo,
+                           const uint64_t* __restrict__ sweep_dev) {
   const int z = blockIdx.y;
   const Dims D = dims[z];
+  if (!D.active) return;
+  const int n = D.n, l = D.l;
   float* bt = mp.bt_hi + (size_t)z * Np * K1;
   float* btl = mp.bt_lo + (size_t)z * Np * K1;
   const int half = K1 / 2;
   const int64_t total = (int64_t)(Np / 2) * half;  // (row pair c, complex column j)
-  const uint64_t chain = (uint64_t)(chain0 + (int64_t)z * chain_stride);
+  const uint64_t chain = chain_stride >= 0 ? (uint64_t)(chain0 + (int64_t)z * chain_stride) : (uint64_t)D.chain;
+  if (sweep_dev) sweep = *sweep_dev;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int c = (int)(e / half), j = (int)(e % half);
     float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f), al = a, bl = a;
@@ -211,10 +223,15 @@ __global__ void k_omega_bt(const MixedPtrs mp, const Dims* __restrict__ dims, in
 
 // X (complex FP32, column-major Kc x l, instance stride Kc*l) -> Bt (Np x Kp)
 // and optionally its TF32 remainder.
-__global__ void k_conv_bt(const float2* __restrict__ X, float* bt_hi, float* bt_lo, int Kc, int l, int Np, int Kp,
-                          int want_lo) {
+// Columns past the instance's own l (the junk basis vectors of a padded QR)
+// become zero rows of Bt.
+__global__ void k_conv_bt(const float2* __restrict__ X, const Dims* __restrict__ dims, float* bt_hi, float* bt_lo,
+                          int Kc, int lc, int Np, int Kp, int want_lo) {
   const int z = blockIdx.y;
-  const float2* x = X + (size_t)z * Kc * l;
+  const Dims D = dims[z];
+  if (!D.active) return;
+  const int l = D.l;
+  const float2* x = X + (size_t)z * Kc * lc;
   float* bh = bt_hi + (size_t)z * Np * Kp;
   float* bl = bt_lo + (size_t)z * Np * Kp;
   const int half = Kp / 2;
@@ -241,9 +258,11 @@ __global__ void k_conv_bt(const float2* __restrict__ X, float* bt_hi, float* bt_
 }
 
 // ---------------------------------------------------------------------------
-// Householder QR with explicit Q in FP32 (same algorithm as the FP64 kernel:
-// alpha = -e^{i arg x0} ||x||, v0 = x0 - alpha, tau = 1/(||x|| (||x|| + |x0|))).
-// Input M x L column-major (overwritten), output Q M x L column-major.
+// Householder QR with explicit Q in FP32: alpha = -e^{i arg x0} ||x||,
+// normalised reflector v = x / (x0 - alpha) (v_0 = 1), tau = 1 + |x0| / ||x||
+// (Golub & Van Loan 5.1.2; the unnormalised form of the FP64 kernel would
+// overflow FP32 for columns of norm below ~1e-19).  Input M x L
+// column-major (overwritten), output Q M x L column-major.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float2 fmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 __device__ __forceinline__ void ffma_conj(float2& acc, float2 a, float2 b) {
@@ -260,6 +279,8 @@ __device__ __forceinline__ float fwarp_sum(float v) {
 
 __global__ void __launch_bounds__(1024) k_qr_f32(float2* Abase, float2* Qbase, int M, int L) {
   __shared__ float red[32];
+  __shared__ float2 vscale;
+  __shared__ float vnorm;
   __shared__ float tau[512];
   const int z = blockIdx.x;
   float2* A = Abase + (size_t)z * M * L;
@@ -276,18 +297,65 @@ __global__ void __launch_bounds__(1024) k_qr_f32(float2* Abase, float2* Qbase, i
     if (tid == 0) {
       float t = 0.f;
       for (int w = 0; w < nw; ++w) t += red[w];
+      vnorm = sqrtf(t);
+    }
+    __syncthreads();
+    if (vnorm < 1e-12f) {
+      // squares in the FP32 subnormal range would make the reflector
+      // non-unitary: norm of x / max|x|
+      float mx = 0.f;
+      for (int r = j + tid; r < M; r += blockDim.x) mx = fmaxf(mx, fmaxf(fabsf(aj[r].x), fabsf(aj[r].y)));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if (lane == 0) red[warp] = mx;
+      __syncthreads();
+      float amax = 0.f;
+      for (int w = 0; w < nw; ++w) amax = fmaxf(amax, red[w]);
+      __syncthreads();
+      float s2 = 0.f;
+      if (amax > 0.f) {
+        const float ia = 1.f / amax;
+        for (int r = j + tid; r < M; r += blockDim.x) {
+          const float a = aj[r].x * ia, b = aj[r].y * ia;
+          s2 = fmaf(a, a, fmaf(b, b, s2));
+        }
+      }
+      s2 = fwarp_sum(s2);
+      if (lane == 0) red[warp] = s2;
+      __syncthreads();
+      if (tid == 0) {
+        float t = 0.f;
+        for (int w = 0; w < nw; ++w) t += red[w];
+        vnorm = amax * sqrtf(t);
+      }
+      __syncthreads();
+    }
+    if (tid == 0) {
       const float2 x0 = aj[j];
-      const float ax0 = sqrtf(x0.x * x0.x + x0.y * x0.y), nx = sqrtf(t);
-      if (nx == 0.f) {
+      // |x0| without squaring; see k_qr_blk_f32 for the rules on tiny columns and entries
+      const float ax0 = hypotf(x0.x, x0.y);
+      const float nx = vnorm;
+      if (!(nx >= 1e-30f)) {  // zero column, or one below any meaningful scale: no reflection
         tau[j] = 0.f;
+        vscale = make_float2(1.f, 0.f);
       } else {
-        const float2 ph = (ax0 > 0.f) ? make_float2(x0.x / ax0, x0.y / ax0) : make_float2(1.f, 0.f);
-        aj[j] = make_float2(ph.x * (ax0 + nx), ph.y * (ax0 + nx));
-        tau[j] = 1.f / (nx * (nx + ax0));
+        const float2 ph = (ax0 > 1e-7f * nx) ? make_float2(x0.x / ax0, x0.y / ax0) : make_float2(1.f, 0.f);
+        const float ri = 1.f / (ax0 + nx);
+        vscale = make_float2(ph.x * ri, -ph.y * ri);  // 1 / (x0 - alpha)
+        aj[j] = make_float2(1.f, 0.f);
+        tau[j] = 1.f + ax0 / nx;
       }
     }
     __syncthreads();
     const float t = tau[j];
+    if (t != 0.f) {
+      const float2 sc = vscale;
+      for (int r = j + 1 + tid; r < M; r += blockDim.x) {
+        const float2 v = aj[r];
+        aj[r] = make_float2(v.x * sc.x - v.y * sc.y, v.x * sc.y + v.y * sc.x);
+      }
+      __syncthreads();
+    }
     if (t != 0.f) {
       for (int c = j + 1 + warp; c < L; c += nw) {
         float2* ac = A + (int64_t)c * M;
@@ -327,14 +395,20 @@ __global__ void __launch_bounds__(1024) k_qr_f32(float2* Abase, float2* Qbase, i
   }
 }
 
-// Yf (FP32) -> the FP64 buffer of the final QR.
-__global__ void k_f32_to_f64(const float2* __restrict__ Yf, const ProbPtr* __restrict__ ptrs, int m, int l) {
+// Yf (FP32, capacity mc x lc) -> the compact FP64 buffer Y (m x l) of the final QR.
+__global__ void k_f32_to_f64(const float2* __restrict__ Yf, const Dims* __restrict__ dims,
+                             const ProbPtr* __restrict__ ptrs, int mc, int lc) {
   const int z = blockIdx.y;
-  const float2* y = Yf + (size_t)z * m * l;
+  const Dims D = dims[z];
+  if (!D.active) return;
+  const float2* y = Yf + (size_t)z * mc * lc;
   cplx* Y = ptrs[z].Y;
-  const int64_t total = (int64_t)m * l;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
-    Y[e] = cmk((double)y[e].x, (double)y[e].y);
+  const int64_t total = (int64_t)D.m * D.l;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e / D.m), r = (int)(e % D.m);
+    const float2 v = y[(int64_t)c * mc + r];
+    Y[e] = cmk((double)v.x, (double)v.y);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -452,7 +526,7 @@ static cudaError_t tc_product(const float* A0, const float* A1, const float* B0,
   a.out_stride = (int64_t)rows * l;
   a.err = err;
   const size_t sm = tc_smem_bytes(s.BN);
-  static int attr_done = 0;
+  static int attr_done = 0;  // set once for the largest tile (also by mixed_prepare)
   if (!attr_done) {
     MX_TRY(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes(TC_MAXBN)));
     attr_done = 1;
@@ -470,32 +544,44 @@ static cudaError_t qr_f32(float2* A, float2* Q, int M, int L, int batch, cudaStr
   return cudaGetLastError();
 }
 
-static cudaError_t conv_bt(const float2* X, const MixedPtrs& mp, int Kc, int l, int Kp, const MixedSizes& s, int lo,
-                           int batch, cudaStream_t st) {
+static cudaError_t conv_bt(const float2* X, const Dims* dims, const MixedPtrs& mp, int Kc, int l, int Kp,
+                           const MixedSizes& s, int lo, int batch, cudaStream_t st) {
   ProfScope ps("k_conv_bt", st);
-  k_conv_bt<<<dim3(grid1d((int64_t)(s.Np / 2) * (Kp / 2)), batch), 256, 0, st>>>(X, mp.bt_hi, mp.bt_lo, Kc, l, s.Np,
-                                                                                   Kp, lo);
+  k_conv_bt<<<dim3(grid1d((int64_t)(s.Np / 2) * (Kp / 2)), batch), 256, 0, st>>>(X, dims, mp.bt_hi, mp.bt_lo, Kc, l,
+                                                                                   s.Np, Kp, lo);
   return cudaGetLastError();
+}
+
+cudaError_t mixed_prepare(const Caps& cap) {
+  if (!encode_fn()) return cudaErrorNotSupported;
+  static int attr_done = 0;
+  if (!attr_done) {
+    MX_TRY(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes(TC_MAXBN)));
+    attr_done = 1;
+  }
+  return qr_blocked_prepare(cap.m, cap.n, cap.l);
 }
 
 cudaError_t run_rrsvd_mixed(const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, const MixedPtrs& mp,
                             int q, uint64_t seed, uint64_t sweep, int64_t chain0, int chain_stride, int* status,
-                            int* err, cudaStream_t st) {
+                            int* err, cudaStream_t st, const uint64_t* sweep_dev) {
+  // capacities: every FP32 array is laid out at these sizes, zero-padded past
+  // each instance's own (m, n, l) from dims
   const int m = cap.m, n = cap.n, k = cap.k, l = cap.l;
   const MixedSizes s = mixed_sizes(m, n, k, l);
   {
     ProfScope ps("k_conv_theta", st);
     const int cext = s.K1 / 2, rext = s.K2 / 2;  // padded extents (>= n, >= m)
-    k_conv_theta<<<dim3((cext + 31) / 32, (rext + 31) / 32, batch), 256, 0, st>>>(mp, ptrs, m, n, s.K1, s.K2, 1);
+    k_conv_theta<<<dim3((cext + 31) / 32, (rext + 31) / 32, batch), 256, 0, st>>>(mp, dims, ptrs, m, n, s.K1, s.K2,
+                                                                                   1);
     MX_TRY(cudaGetLastError());
-    k_part_reduce<<<batch, NPART, 0, st>>>(mp.tpart, s.ntile, ptrs);
+    k_part_reduce<<<batch, NPART, 0, st>>>(mp.tpart, s.ntile, dims, ptrs);
     MX_TRY(cudaGetLastError());
   }
   {
     ProfScope ps("k_omega_bt", st);
-    k_omega_bt<<<dim3(grid1d((int64_t)(s.Np / 2) * (s.K1 / 2)), batch), 256, 0, st>>>(mp, dims, n, l, s.Np, s.K1, seed,
-                                                                                      sweep, chain0, chain_stride,
-                                                                                      q == 0 ? 1 : 0);
+    k_omega_bt<<<dim3(grid1d((int64_t)(s.Np / 2) * (s.K1 / 2)), batch), 256, 0, st>>>(
+        mp, dims, s.Np, s.K1, seed, sweep, chain0, chain_stride, q == 0 ? 1 : 0, sweep_dev);
     MX_TRY(cudaGetLastError());
   }
   // Y0 = A Omega: TF32, or the refinement pass when q == 0
@@ -504,21 +590,21 @@ cudaError_t run_rrsvd_mixed(const Dims* dims, const ProbPtr* ptrs, int batch, co
   for (int j = 1; j <= q; ++j) {
     const int np = (j == q) ? 3 : 1;
     MX_TRY(qr_f32(mp.Yf, mp.Qf, m, l, batch, st));                                 // Y = Q R
-    MX_TRY(conv_bt(mp.Qf, mp, m, l, s.K2, s, np == 3, batch, st));
+    MX_TRY(conv_bt(mp.Qf, dims, mp, m, l, s.K2, s, np == 3, batch, st));
     MX_TRY(tc_product(mp.tha_hi, mp.tha_lo, mp.bt_hi, mp.bt_lo, n, s.K2, s, l, np, mp.Ytf, batch, err, st));  // A^H Q
     MX_TRY(qr_f32(mp.Ytf, mp.Qtf, n, l, batch, st));                              // = Q~ R~
-    MX_TRY(conv_bt(mp.Qtf, mp, n, l, s.K1, s, np == 3, batch, st));
+    MX_TRY(conv_bt(mp.Qtf, dims, mp, n, l, s.K1, s, np == 3, batch, st));
     MX_TRY(tc_product(mp.thf_hi, mp.thf_lo, mp.bt_hi, mp.bt_lo, m, s.K1, s, l, np, mp.Yf, batch, err, st));  // A Q~
   }
   if (reorth_fits(m, l)) {
     // last QR: FP32 Householder, then the FP64-accurate re-orthonormalisation
     MX_TRY(qr_f32(mp.Yf, mp.Qf, m, l, batch, st));
-    MX_TRY(launch_reorth(mp.Qf, mp.Df, ptrs, m, l, batch, status, st));
-    MX_TRY(launch_proj_df(mp.thd, ptrs, mp.Qf, mp.Df, m, n, l, batch, st));  // B^H = A^H Q
+    MX_TRY(launch_reorth(mp.Qf, mp.Df, dims, ptrs, m, l, batch, status, st));
+    MX_TRY(launch_proj_df(mp.thd, dims, ptrs, mp.Qf, mp.Df, m, n, l, batch, st));  // B^H = A^H Q
   } else {
     {
       ProfScope ps("k_f32_to_f64", st);
-      k_f32_to_f64<<<dim3(grid1d((int64_t)m * l), batch), 256, 0, st>>>(mp.Yf, ptrs, m, l);
+      k_f32_to_f64<<<dim3(grid1d((int64_t)m * l), batch), 256, 0, st>>>(mp.Yf, dims, ptrs, m, l);
       MX_TRY(cudaGetLastError());
     }
     MX_TRY(launch_qr(QR_Y, dims, ptrs, batch, st));          // last QR in FP64

@@ -45,19 +45,30 @@ cudaError_t launch_qr_blk_f32(float2* A, float2* Q, int M, int L, int batch, cud
 // Q_f (FP32, M x L) -> ptrs[z].Q (FP64) orthonormal to ~1e-13, spanning
 // range(Q_f); uses ptrs[z].R as scratch; usable when reorth_fits(M, L).
 bool reorth_fits(int M, int L);
-cudaError_t launch_reorth(const float2* Qf, float2* Dbuf, const ProbPtr* ptrs, int M, int L, int batch, int* status,
-                          cudaStream_t st);
+cudaError_t launch_reorth(const float2* Qf, float2* Dbuf, const Dims* dims, const ProbPtr* ptrs, int M, int L,
+                          int batch, int* status, cudaStream_t st);
 // B^H <- B^H (I + D) in place on ptrs[z].Yt (qr_blocked.cu).
-cudaError_t launch_fold_bh(const float2* Dbuf, const ProbPtr* ptrs, int n, int l, int batch, cudaStream_t st);
+cudaError_t launch_fold_bh(const float2* Dbuf, const Dims* dims, const ProbPtr* ptrs, int n, int l, int batch,
+                           cudaStream_t st);
 // B^H = A^H Q_f (I + D) into ptrs[z].Yt (df_proj.cu) (n x l column-major): double-float
 // product with the FP32 Q_f, then the correction; after launch_reorth.
-cudaError_t launch_proj_df(const float4* thd, const ProbPtr* ptrs, const float2* Qf, const float2* Dbuf, int m, int n,
-                           int l, int batch, cudaStream_t st);
+cudaError_t launch_proj_df(const float4* thd, const Dims* dims, const ProbPtr* ptrs, const float2* Qf,
+                           const float2* Dbuf, int m, int n, int l, int batch, cudaStream_t st);
 
-// Alg. 1 with tensor-core products and the FP64 projection / small SVD;
-// uniform sizes over the batch (cap holds them).
+// Everything that must happen outside a stream capture before
+// run_rrsvd_mixed runs on capacities `cap` (shared-memory limits, the
+// tensor-map encoder entry point).
+cudaError_t mixed_prepare(const Caps& cap);
+cudaError_t qr_blocked_prepare(int M, int N, int L);
+
+// Alg. 1 with tensor-core products and the FP64-accurate projection / FP64
+// small SVD.  The FP32 arrays are laid out at the capacities `cap` (the
+// maxima over the batch, which size mixed_sizes/mixed_carve); each instance
+// uses its own (m, n, k, l) from dims, zero-padded up to them.  Instance z
+// draws Omega from chain chain0 + z chain_stride at `sweep`, or, with
+// chain_stride < 0, from its own chain index at *sweep_dev.
 cudaError_t run_rrsvd_mixed(const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, const MixedPtrs& mp,
                             int q, uint64_t seed, uint64_t sweep, int64_t chain0, int chain_stride, int* status,
-                            int* err, cudaStream_t st);
+                            int* err, cudaStream_t st, const uint64_t* sweep_dev = nullptr);
 
 }  // namespace tg

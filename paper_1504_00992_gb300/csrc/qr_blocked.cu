@@ -1,9 +1,9 @@
 // Blocked Householder QR in FP32 and the FP64-accurate re-orthonormalisation
 // of its Q (sm_103a), used by the mixed-precision RRSVD.
 //
-// k_qr_blk_f32: the same reflectors as the unblocked kernels (alpha =
-// -e^{i arg x0} ||x||, v0 = x0 - alpha, tau = 1/(||x|| (||x|| + |x0|)),
-// H = I - tau v v^H), grouped in panels of QB_NB columns (compact WY form,
+// k_qr_blk_f32: Householder reflectors H = I - tau v v^H with alpha =
+// -e^{i arg x0} ||x||, normalised v = x / (x0 - alpha) (v_0 = 1) and
+// tau = 1 + |x0| / ||x|| (Golub & Van Loan 5.1.2), grouped in panels of QB_NB columns (compact WY form,
 // Schreiber & Van Loan 1989; Golub & Van Loan 5.2.3):
 //   H_0 ... H_{nb-1} = I - V T V^H,  T upper triangular,
 //   T[i][i] = tau_i,  T[0:i, i] = -tau_i T[0:i, 0:i] (V[:, 0:i]^H v_i).
@@ -174,6 +174,8 @@ __device__ void qb_apply(float2* C, int M, int j0, int jb, int c0, int L, const 
 // dynamic shared memory.
 __global__ void __launch_bounds__(QB_THREADS) k_qr_blk_f32(float2* Abase, float2* Qbase, int M, int L) {
   extern __shared__ __align__(16) unsigned char qb_raw[];
+  __shared__ float2 vscale;
+  __shared__ float vnorm;
   const int ldv = M;
   const int npan = (L + QB_NB - 1) / QB_NB;
   float2* Vs = reinterpret_cast<float2*>(qb_raw);
@@ -209,18 +211,73 @@ __global__ void __launch_bounds__(QB_THREADS) k_qr_blk_f32(float2* Abase, float2
       if (tid == 0) {
         float t = 0.f;
         for (int w = 0; w < QB_WARPS; ++w) t += red[w];
+        vnorm = sqrtf(t);
+      }
+      __syncthreads();
+      if (vnorm < 1e-12f) {
+        // a column this small has squares in the FP32 subnormal range, whose
+        // lost bits would make the reflector non-unitary: norm of x / max|x|
+        float mx = 0.f;
+        for (int r = i + tid; r < Mr; r += QB_THREADS) {
+          const float2 v = Vs[i * ldv + r];
+          mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) red[warp] = mx;
+        __syncthreads();
+        float amax = 0.f;
+        for (int w = 0; w < QB_WARPS; ++w) amax = fmaxf(amax, red[w]);
+        __syncthreads();
+        float s2 = 0.f;
+        if (amax > 0.f) {
+          const float ia = 1.f / amax;
+          for (int r = i + tid; r < Mr; r += QB_THREADS) {
+            const float2 v = Vs[i * ldv + r];
+            const float a = v.x * ia, b = v.y * ia;
+            s2 = fmaf(a, a, fmaf(b, b, s2));
+          }
+        }
+        s2 = qb_wsum(s2);
+        if (lane == 0) red[warp] = s2;
+        __syncthreads();
+        if (tid == 0) {
+          float t = 0.f;
+          for (int w = 0; w < QB_WARPS; ++w) t += red[w];
+          vnorm = amax * sqrtf(t);
+        }
+        __syncthreads();
+      }
+      if (tid == 0) {
         const float2 x0 = Vs[i * ldv + i];
-        const float ax0 = sqrtf(x0.x * x0.x + x0.y * x0.y), nx = sqrtf(t);
-        if (nx == 0.f) {
+        // |x0| without squaring (a square in the subnormal range would leave
+        // the phase x0/|x0| off the unit circle and the reflector non-unitary)
+        const float ax0 = hypotf(x0.x, x0.y);
+        const float nx = vnorm;
+        if (!(nx >= 1e-30f)) {  // zero column, or one below any meaningful scale: no reflection
           tau[j] = 0.f;
+          vscale = make_float2(1.f, 0.f);
         } else {
-          const float2 ph = (ax0 > 0.f) ? make_float2(x0.x / ax0, x0.y / ax0) : make_float2(1.f, 0.f);
-          Vs[i * ldv + i] = make_float2(ph.x * (ax0 + nx), ph.y * (ax0 + nx));
-          tau[j] = 1.f / (nx * (nx + ax0));
+          // normalised reflector: v = x / (x0 - alpha), v_0 = 1, tau = 1 + |x0| / ||x||
+          // (in [1, 2], so columns of tiny norm neither overflow nor lose tau); the
+          // phase of a leading entry negligible against ||x|| is not used
+          const float2 ph = (ax0 > 1e-7f * nx) ? make_float2(x0.x / ax0, x0.y / ax0) : make_float2(1.f, 0.f);
+          const float ri = 1.f / (ax0 + nx);
+          vscale = make_float2(ph.x * ri, -ph.y * ri);  // 1 / (x0 - alpha)
+          Vs[i * ldv + i] = make_float2(1.f, 0.f);
+          tau[j] = 1.f + ax0 / nx;
         }
       }
       __syncthreads();
       const float tj = tau[j];
+      if (tj != 0.f) {
+        const float2 sc = vscale;
+        for (int r = i + 1 + tid; r < Mr; r += QB_THREADS) {
+          const float2 v = Vs[i * ldv + r];
+          Vs[i * ldv + r] = make_float2(v.x * sc.x - v.y * sc.y, v.x * sc.y + v.y * sc.x);
+        }
+        __syncthreads();
+      }
       const int nc = jb - 1 - i;
       if (tj != 0.f && nc > 0) {
         float2 acc[QB_NB - 1];
@@ -352,7 +409,7 @@ __global__ void __launch_bounds__(QB_THREADS) k_qr_blk_f32(float2* Abase, float2
   }
 }
 
-bool qr_blk_f32_fits(int M, int L) { return M >= L && L >= 1 && qb_smem_bytes(M, L) <= 227 * 1024 - 1024; }
+bool qr_blk_f32_fits(int M, int L) { return M >= L && L >= 1 && qb_smem_bytes(M, L) <= 227 * 1024 - 2048; }
 
 // Raises a kernel's dynamic shared-memory limit to `bytes` (the first time a
 // launch needs more than the last value set for it).
@@ -364,10 +421,13 @@ static cudaError_t ensure_smem(K kernel, size_t bytes, size_t* done) {
   return e;
 }
 
+// Shared-memory limits set so far, per kernel (one record each, shared by the
+// launchers and qr_blocked_prepare so that a limit is never lowered).
+static size_t g_attr_qr = 0, g_attr_ld = 0, g_attr_fold[2][2] = {{0, 0}, {0, 0}};
+
 cudaError_t launch_qr_blk_f32(float2* A, float2* Q, int M, int L, int batch, cudaStream_t st) {
   const size_t sm = qb_smem_bytes(M, L);
-  static size_t attr = 0;
-  cudaError_t e = ensure_smem(k_qr_blk_f32, sm, &attr);
+  cudaError_t e = ensure_smem(k_qr_blk_f32, sm, &g_attr_qr);
   if (e != cudaSuccess) return e;
   k_qr_blk_f32<<<batch, QB_THREADS, sm, st>>>(A, Q, M, L);
   return cudaGetLastError();
@@ -404,18 +464,24 @@ __device__ __forceinline__ void df_merge(float& H, float& Lo, float h, float lo)
 // 2 x 2 outputs per thread), written to ptrs[z].R (L x L column-major, FP64).
 // Each 16-deep slice of the sum is accumulated afresh and merged into the
 // running double-float sum.
-__global__ void __launch_bounds__(256) k_gram_df(const float2* __restrict__ Qf, const ProbPtr* __restrict__ ptrs,
-                                                 int M, int L) {
+// Q_f at capacity Mc x Lc per instance; the instance's own sizes come from
+// dims (rows past D.m are zero, columns past D.l are not part of its basis).
+__global__ void __launch_bounds__(256) k_gram_df(const float2* __restrict__ Qf, const Dims* __restrict__ dims,
+                                                 const ProbPtr* __restrict__ ptrs, int Mc, int Lc) {
   constexpr int T = 32, TK = 16;
   __shared__ float2 As[TK][T + 1];
   __shared__ float2 Bs[TK][T + 1];
   const int z = blockIdx.y;
-  const int nt = (L + T - 1) / T;
-  // blockIdx.x enumerates the tile pairs (ti <= tj)
+  const Dims D = dims[z];
+  if (!D.active) return;
+  const int ntc = (Lc + T - 1) / T;
+  // blockIdx.x enumerates the tile pairs (ti <= tj) of the capacity
   int ti = 0, rem = blockIdx.x;
-  while (rem >= nt - ti) { rem -= nt - ti; ++ti; }
+  while (rem >= ntc - ti) { rem -= ntc - ti; ++ti; }
   const int tj = ti + rem;
-  const float2* q = Qf + (size_t)z * M * L;
+  const int L = D.l, M = D.m;
+  if (ti * T >= L || tj * T >= L) return;
+  const float2* q = Qf + (size_t)z * Mc * Lc;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   float RH[2][2], RL[2][2], IH[2][2], IL[2][2];
 #pragma unroll
@@ -427,8 +493,8 @@ __global__ void __launch_bounds__(256) k_gram_df(const float2* __restrict__ Qf, 
       const int kk = e % TK, c = e / TK;
       const int gk = k0 + kk;
       const int ca = ti * T + c, cb = tj * T + c;
-      As[kk][c] = (gk < M && ca < L) ? q[(size_t)ca * M + gk] : make_float2(0.f, 0.f);
-      Bs[kk][c] = (gk < M && cb < L) ? q[(size_t)cb * M + gk] : make_float2(0.f, 0.f);
+      As[kk][c] = (gk < M && ca < L) ? q[(size_t)ca * Mc + gk] : make_float2(0.f, 0.f);
+      Bs[kk][c] = (gk < M && cb < L) ? q[(size_t)cb * Mc + gk] : make_float2(0.f, 0.f);
     }
     __syncthreads();
     float rh[2][2], rl[2][2], ih[2][2], il[2][2];
@@ -473,14 +539,17 @@ __global__ void __launch_bounds__(256) k_gram_df(const float2* __restrict__ Qf, 
 }
 
 // D = -E/2 + 3 E^2 / 8 (E Hermitian, from its upper triangle), FP32, one CTA
-// per instance; flags the instance when E is not small or not finite.
-__global__ void __launch_bounds__(512) k_lowdin(const ProbPtr* __restrict__ ptrs, float2* Dbase, int L, int* status) {
+// per instance; raises status bit 4 when E is not small or not finite.
+__global__ void __launch_bounds__(512) k_lowdin(const Dims* __restrict__ dims, const ProbPtr* __restrict__ ptrs,
+                                                float2* Dbase, int Lc, int* status) {
   extern __shared__ __align__(16) unsigned char ld_raw[];
   float2* Ef = reinterpret_cast<float2*>(ld_raw);  // L x L, Ef[a * L + b] = E[a][b]
   __shared__ float red[32];
   const int z = blockIdx.x;
+  if (!dims[z].active) return;
+  const int L = dims[z].l;
   const cplx* E = ptrs[z].R;
-  float2* D = Dbase + (size_t)z * L * L;
+  float2* D = Dbase + (size_t)z * Lc * Lc;
   const int tid = threadIdx.x;
   float mx = 0.f;
   for (int e = tid; e < L * L; e += blockDim.x) {
@@ -501,7 +570,7 @@ __global__ void __launch_bounds__(512) k_lowdin(const ProbPtr* __restrict__ ptrs
   if (tid == 0) {
     float m = 0.f;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = (red[w] > m || red[w] != red[w]) ? red[w] : m;
-    if (!(m <= 1e-3f)) atomicOr(status, 1);
+    if (!(m <= 1e-3f)) atomicOr(status, 4);
   }
   // D[a][b] = -E[a][b]/2 + 3/8 sum_k E[a][k] E[k][b]; stored column-major (D[b * L + a])
   for (int e = tid; e < L * L; e += blockDim.x) {
@@ -518,32 +587,38 @@ __global__ void __launch_bounds__(512) k_lowdin(const ProbPtr* __restrict__ ptrs
 }
 
 // Out = X + X D with the small correction X D in FP32 (|D| ~ 1e-6, so its
-// relative FP32 error costs ~1e-13 absolute), X M x L column-major per
-// instance: Q = Q_f (I + D) from the FP32 Q_f into ptrs[z].Q, or, in place,
-// B^H = (A^H Q_f)(I + D) on ptrs[z].Yt.  64 rows per CTA, staged column-major
-// in shared memory as FP32; warp w owns the columns c = w (mod 8), lane i the
-// rows 2i and 2i+1 of the tile (one 16-byte shared load per k).
-enum { QF_ROWS = 64, QF_MAXL = 128, QF_MAXCPW = QF_MAXL / 8 };
+// relative FP32 error costs ~1e-13 absolute): Q = Q_f (I + D) from the FP32
+// Q_f (capacity Mc x Lc per instance) into ptrs[z].Q (D.m x D.l, compact), or,
+// in place, B^H = (A^H Q_f)(I + D) on ptrs[z].Yt (D.n x D.l, compact).  RPL
+// rows per lane (32 RPL rows per CTA), staged column-major in shared memory
+// as FP32; warp w owns the columns c = w (mod 8).
+enum { QF_MAXL = 144, QF_MAXCPW = QF_MAXL / 8 };
 
-template <bool FROM_F32>
+template <bool FROM_F32, int RPL>
 __global__ void __launch_bounds__(256) k_fold(const float2* __restrict__ Qf, const float2* __restrict__ Dbase,
-                                              const ProbPtr* __restrict__ ptrs, int M, int L) {
+                                              const Dims* __restrict__ dims, const ProbPtr* __restrict__ ptrs, int Mc,
+                                              int Lc) {
+  constexpr int ROWS = 32 * RPL;
   extern __shared__ __align__(16) unsigned char qf_raw[];
-  float2* Ds = reinterpret_cast<float2*>(qf_raw);  // L x L column-major
-  float2* Qs = Ds + ((L * L + 1) & ~1);            // QF_ROWS x L column-major (16-byte aligned)
   const int z = blockIdx.y;
-  const int r0 = blockIdx.x * QF_ROWS;
-  const float2* q = FROM_F32 ? Qf + (size_t)z * M * L : nullptr;
-  cplx* X = FROM_F32 ? ptrs[z].Q : ptrs[z].Yt;  // output (and FP64 source when !FROM_F32)
-  const float2* D = Dbase + (size_t)z * L * L;
+  const Dims Dm = dims[z];
+  if (!Dm.active) return;
+  const int M = FROM_F32 ? Dm.m : Dm.n, L = Dm.l;
+  const int r0 = blockIdx.x * ROWS;
+  if (r0 >= M) return;
+  float2* Ds = reinterpret_cast<float2*>(qf_raw);  // L x L column-major
+  float2* Qs = Ds + ((L * L + 1) & ~1);            // ROWS x L column-major (16-byte aligned)
+  const float2* q = FROM_F32 ? Qf + (size_t)z * Mc * Lc : nullptr;
+  cplx* X = FROM_F32 ? ptrs[z].Q : ptrs[z].Yt;  // output (and FP64 source when !FROM_F32), ld M
+  const float2* D = Dbase + (size_t)z * Lc * Lc;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int e = tid; e < L * L; e += 256) Ds[e] = D[e];
-  for (int e = tid; e < QF_ROWS * L; e += 256) {
-    const int c = e / QF_ROWS, r = e % QF_ROWS;
+  for (int e = tid; e < ROWS * L; e += 256) {
+    const int c = e / ROWS, r = e % ROWS;
     float2 v = make_float2(0.f, 0.f);
     if (r0 + r < M) {
       if (FROM_F32) {
-        v = q[(size_t)c * M + r0 + r];
+        v = q[(size_t)c * Mc + r0 + r];
       } else {
         const cplx x = X[(size_t)c * M + r0 + r];
         v = make_float2((float)x.x, (float)x.y);
@@ -552,28 +627,36 @@ __global__ void __launch_bounds__(256) k_fold(const float2* __restrict__ Qf, con
     Qs[e] = v;
   }
   __syncthreads();
-  float2 acc[2][QF_MAXCPW];
+  float2 acc[RPL][QF_MAXCPW];
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < RPL; ++i)
 #pragma unroll
     for (int j = 0; j < QF_MAXCPW; ++j) acc[i][j] = make_float2(0.f, 0.f);
   for (int k = 0; k < L; ++k) {
-    const float4 x = *reinterpret_cast<const float4*>(&Qs[k * QF_ROWS + 2 * lane]);  // rows 2 lane, 2 lane + 1
+    float2 x[RPL];
+    if (RPL == 2) {
+      const float4 x4 = *reinterpret_cast<const float4*>(&Qs[k * ROWS + 2 * lane]);  // rows 2 lane, 2 lane + 1
+      x[0] = make_float2(x4.x, x4.y);
+      x[RPL - 1] = make_float2(x4.z, x4.w);
+    } else {
+      x[0] = Qs[k * ROWS + lane];
+    }
 #pragma unroll
     for (int j = 0; j < QF_MAXCPW; ++j) {
       const int c = warp + 8 * j;
       if (c < L) {
         const float2 d = Ds[c * L + k];
-        acc[0][j].x = fmaf(x.x, d.x, fmaf(-x.y, d.y, acc[0][j].x));
-        acc[0][j].y = fmaf(x.x, d.y, fmaf(x.y, d.x, acc[0][j].y));
-        acc[1][j].x = fmaf(x.z, d.x, fmaf(-x.w, d.y, acc[1][j].x));
-        acc[1][j].y = fmaf(x.z, d.y, fmaf(x.w, d.x, acc[1][j].y));
+#pragma unroll
+        for (int i = 0; i < RPL; ++i) {
+          acc[i][j].x = fmaf(x[i].x, d.x, fmaf(-x[i].y, d.y, acc[i][j].x));
+          acc[i][j].y = fmaf(x[i].x, d.y, fmaf(x[i].y, d.x, acc[i][j].y));
+        }
       }
     }
   }
 #pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    const int r = 2 * lane + i;
+  for (int i = 0; i < RPL; ++i) {
+    const int r = RPL * lane + i;
     if (r0 + r >= M) continue;
 #pragma unroll
     for (int j = 0; j < QF_MAXCPW; ++j) {
@@ -581,7 +664,7 @@ __global__ void __launch_bounds__(256) k_fold(const float2* __restrict__ Qf, con
       if (c < L) {
         cplx b;
         if (FROM_F32) {
-          const float2 f = Qs[c * QF_ROWS + r];
+          const float2 f = Qs[c * ROWS + r];
           b = cmk((double)f.x, (double)f.y);
         } else {
           b = X[(size_t)c * M + r0 + r];
@@ -592,43 +675,67 @@ __global__ void __launch_bounds__(256) k_fold(const float2* __restrict__ Qf, con
   }
 }
 
-bool reorth_fits(int M, int L) { return M >= L && L <= QF_MAXL; }
+// batch == 0 only raises the shared-memory limit.
+template <bool FROM_F32>
+static cudaError_t launch_fold(const float2* Qf, const float2* Dbuf, const Dims* dims, const ProbPtr* ptrs, int Mc,
+                               int Lc, int batch, cudaStream_t st) {
+  if (Lc <= 128) {
+    const size_t sm = sizeof(float2) * ((size_t)((Lc * Lc + 1) & ~1) + 64 * (size_t)Lc);
+    cudaError_t e = ensure_smem(k_fold<FROM_F32, 2>, sm, &g_attr_fold[FROM_F32][1]);
+    if (e != cudaSuccess || batch == 0) return e;
+    k_fold<FROM_F32, 2><<<dim3((Mc + 63) / 64, batch), 256, sm, st>>>(Qf, Dbuf, dims, ptrs, Mc, Lc);
+  } else {
+    const size_t sm = sizeof(float2) * ((size_t)((Lc * Lc + 1) & ~1) + 32 * (size_t)Lc);
+    cudaError_t e = ensure_smem(k_fold<FROM_F32, 1>, sm, &g_attr_fold[FROM_F32][0]);
+    if (e != cudaSuccess || batch == 0) return e;
+    k_fold<FROM_F32, 1><<<dim3((Mc + 31) / 32, batch), 256, sm, st>>>(Qf, Dbuf, dims, ptrs, Mc, Lc);
+  }
+  return cudaGetLastError();
+}
 
-cudaError_t launch_reorth(const float2* Qf, float2* Dbuf, const ProbPtr* ptrs, int M, int L, int batch, int* status,
-                          cudaStream_t st) {
-  static size_t attr_l = 0, attr_f = 0;
+// Raises the dynamic shared-memory limits the blocked QR, the Loewdin step
+// and the folds need for capacities (M, N, L), outside any stream capture.
+cudaError_t qr_blocked_prepare(int M, int N, int L) {
+  cudaError_t e = cudaSuccess;
+  const size_t qr = qb_smem_bytes(M > N ? M : N, L);
+  if (qr <= 227 * 1024 - 1024) e = ensure_smem(k_qr_blk_f32, qr, &g_attr_qr);
+  if (e == cudaSuccess && L <= QF_MAXL) {
+    e = ensure_smem(k_lowdin, sizeof(float2) * (size_t)L * L, &g_attr_ld);
+    if (e == cudaSuccess) e = launch_fold<true>(nullptr, nullptr, nullptr, nullptr, M, L, 0, nullptr);
+    if (e == cudaSuccess) e = launch_fold<false>(nullptr, nullptr, nullptr, nullptr, N, L, 0, nullptr);
+  }
+  return e;
+}
+
+bool reorth_fits(int M, int L) { return M >= L && L <= QF_MAXL; }  // shared memory of k_lowdin and k_fold
+
+cudaError_t launch_reorth(const float2* Qf, float2* Dbuf, const Dims* dims, const ProbPtr* ptrs, int M, int L,
+                          int batch, int* status, cudaStream_t st) {
   const size_t sm_l = sizeof(float2) * (size_t)L * L;
-  const size_t sm_f = sizeof(float2) * ((size_t)((L * L + 1) & ~1) + (size_t)QF_ROWS * L);
-  cudaError_t e0 = ensure_smem(k_lowdin, sm_l, &attr_l);
-  if (e0 == cudaSuccess) e0 = ensure_smem(k_fold<true>, sm_f, &attr_f);
+  cudaError_t e0 = ensure_smem(k_lowdin, sm_l, &g_attr_ld);
   if (e0 != cudaSuccess) return e0;
   const int nt = (L + 31) / 32;
   {
     ProfScope ps("k_gram_df", st);
-    k_gram_df<<<dim3(nt * (nt + 1) / 2, batch), 256, 0, st>>>(Qf, ptrs, M, L);
+    k_gram_df<<<dim3(nt * (nt + 1) / 2, batch), 256, 0, st>>>(Qf, dims, ptrs, M, L);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   {
     ProfScope ps("k_lowdin", st);
-    k_lowdin<<<batch, 512, sm_l, st>>>(ptrs, Dbuf, L, status);
+    k_lowdin<<<batch, 512, sm_l, st>>>(dims, ptrs, Dbuf, L, status);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   ProfScope ps("k_fold[q]", st);
-  k_fold<true><<<dim3((M + QF_ROWS - 1) / QF_ROWS, batch), 256, sm_f, st>>>(Qf, Dbuf, ptrs, M, L);
-  return cudaGetLastError();
+  return launch_fold<true>(Qf, Dbuf, dims, ptrs, M, L, batch, st);
 }
 
-// B^H <- B^H (I + D) in place on ptrs[z].Yt (n x l column-major).
-cudaError_t launch_fold_bh(const float2* Dbuf, const ProbPtr* ptrs, int n, int l, int batch, cudaStream_t st) {
-  static size_t attr = 0;
-  const size_t sm_f = sizeof(float2) * ((size_t)((l * l + 1) & ~1) + (size_t)QF_ROWS * l);
-  cudaError_t e = ensure_smem(k_fold<false>, sm_f, &attr);
-  if (e != cudaSuccess) return e;
+// B^H <- B^H (I + D) in place on ptrs[z].Yt (D.n x D.l column-major).
+cudaError_t launch_fold_bh(const float2* Dbuf, const Dims* dims, const ProbPtr* ptrs, int n, int l, int batch,
+                           cudaStream_t st) {
   ProfScope ps("k_fold[bh]", st);
-  k_fold<false><<<dim3((n + QF_ROWS - 1) / QF_ROWS, batch), 256, sm_f, st>>>(nullptr, Dbuf, ptrs, n, l);
-  return cudaGetLastError();
+  return launch_fold<false>(nullptr, Dbuf, dims, ptrs, n, l, batch, st);
 }
 
 }  // namespace tg
