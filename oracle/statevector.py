@@ -35,3 +35,26 @@ def sweep(psi, N, d, parity, gates):
     for b in range(parity, N - 1, 2):
         psi = apply_two_site(psi, N, d, b, gates[b])
     return psi
+
+
+def apply_two_site_dims(psi, dims, b, G):
+    """apply_two_site for per-site local dimensions dims."""
+    N = len(dims)
+    t = psi.reshape(tuple(dims))
+    G4 = np.asarray(G).reshape(dims[b], dims[b + 1], dims[b], dims[b + 1])
+    t = np.tensordot(G4, t, axes=([2, 3], [b, b + 1]))
+    t = np.moveaxis(t, [0, 1], [b, b + 1])
+    return t.reshape(-1)
+
+
+def expect_onesite_dims(psi, dims, site, op):
+    t = psi.reshape(tuple(dims))
+    ot = np.tensordot(np.asarray(op), t, axes=([1], [site]))
+    ot = np.moveaxis(ot, 0, site)
+    return complex(np.vdot(t.reshape(-1), ot.reshape(-1)))
+
+
+def sweep_dims(psi, dims, parity, gates):
+    for b in range(parity, len(dims) - 1, 2):
+        psi = apply_two_site_dims(psi, dims, b, gates[b])
+    return psi

@@ -130,10 +130,12 @@ def bond_update(mps, b, G, chi_max, p, q, seed, sweep, chain=0, method="rrsvd", 
 
 def sweep(mps, parity, gates, chi_max, p, q, seed, sweep_index, chain=0, method="rrsvd", cutoff=1e-14):
     """All bonds b with b % 2 == parity, left to right (they commute).
-    gates[b] is the gate of bond b.  Returns the list of discarded weights."""
+    gates[b] is the gate of bond b; chi_max is one cap for every bond or a
+    sequence of per-bond caps.  Returns the list of discarded weights."""
     ws = []
     for b in range(parity, mps.N - 1, 2):
-        info = bond_update(mps, b, gates[b], chi_max, p, q, seed, sweep_index, chain, method, cutoff)
+        cap = chi_max[b] if hasattr(chi_max, "__len__") else chi_max
+        info = bond_update(mps, b, gates[b], cap, p, q, seed, sweep_index, chain, method, cutoff)
         ws.append(info["w"])
     return ws
 

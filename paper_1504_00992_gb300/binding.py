@@ -414,16 +414,16 @@ class Tebd:
     """Owning wrapper of a tebd_t handle (the calls above, bound to one chain)."""
 
     def __init__(self, N, d, chi_max, p, q, seed=0, d_site=None, chi_bond=None, sv_cutoff=0.0, chain=0,
-                 stream=None, use_graph=0, autotune=0, precision=TEBD_PREC_FP64):
+                 stream=None, use_graph=0, autotune=0, precision=TEBD_PREC_FP64, workspace_budget=0):
         self.N = N
         self.dims = list(d_site) if d_site is not None else [d] * N
         self.chi_bond = list(chi_bond) if chi_bond is not None else [chi_max] * (N - 1)
         if d_site is None and chi_bond is None and sv_cutoff == 0.0 and chain == 0 and not use_graph \
-                and not autotune and precision == TEBD_PREC_FP64:
+                and not autotune and precision == TEBD_PREC_FP64 and not workspace_budget:
             self.h = tebd_create(N, d, chi_max, p, q, seed)
         else:
             self.h = tebd_create_ex(N, self.dims, self.chi_bond, p, q, seed, precision, sv_cutoff, chain,
-                                    use_graph, autotune)
+                                    use_graph, autotune, workspace_budget)
         caps = []
         for b in range(N - 1):
             left = int(np.prod([float(x) for x in self.dims[: b + 1]]))

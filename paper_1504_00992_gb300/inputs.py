@@ -175,3 +175,118 @@ def gate_derivative(h, tau, dh):
     same = np.abs(de) < 1e-12 * max(1.0, np.abs(e).max())
     Phi = np.where(same, -1j * tau * f[:, None] * np.ones_like(de), (f[:, None] - f[None, :]) / np.where(same, 1.0, de))
     return W @ ((W.conj().T @ dh @ W) * Phi) @ W.conj().T
+
+
+# ---------------------------------------------------------------------------
+# Spin-boson chain (star-to-chain form; Section II.C applications, SURVEY
+# reading A9): a spin coupled through sigma^z to the first of n bosonic sites,
+#   H = (Delta_s/2) sx + t0 sz (a_1 + a_1^+) + sum_n omega n_n
+#       + sum_n t_n (a_n^+ a_{n+1} + a_n a_{n+1}^+),   t_n = t0 / (1 + n),
+# bosons truncated to d_n levels falling linearly from d_first to d_last.
+# ---------------------------------------------------------------------------
+def boson_ops(d):
+    """(a, a^+, n) on a boson truncated to d levels |0>..|d-1>."""
+    a = np.diag(np.sqrt(np.arange(1, d)), 1).astype(np.complex128)
+    return a, a.conj().T, np.diag(np.arange(d)).astype(np.complex128)
+
+
+def spin_boson_sizes(n_bosons, d_first, d_last, chi_first, chi_last):
+    """Local dimensions [2, d_1 .. d_n] and per-bond caps chi_b, both falling
+    linearly (rounded) along the chain."""
+    nb = n_bosons
+    ds = [2] + [int(round(d_first - (d_first - d_last) * (k - 1) / max(1, nb - 1))) for k in range(1, nb + 1)]
+    chis = [int(round(chi_first - (chi_first - chi_last) * b / max(1, nb - 1))) for b in range(nb)]
+    return ds, chis
+
+
+def spin_boson_bond_terms(dims, omega=1.0, t0=0.5, delta_s=1.0):
+    """Bond Hamiltonians h_b on sites (b, b+1) of the spin-boson chain with
+    local dimensions dims = [2, d_1, ...]; on-site terms split half and half
+    between the two bonds of a site, with full weight at the chain ends."""
+    N = len(dims)
+    sx, _, sz = pauli()
+    out = []
+    for b in range(N - 1):
+        dl, dr = dims[b], dims[b + 1]
+        il, ir = np.eye(dl), np.eye(dr)
+        wl = 1.0 if b == 0 else 0.5
+        wr = 1.0 if b + 1 == N - 1 else 0.5
+        ar, adr, nr = boson_ops(dr)
+        if b == 0:
+            h = t0 * np.kron(sz, ar + adr) + wl * 0.5 * delta_s * np.kron(sx, ir)
+        else:
+            al, adl, nl = boson_ops(dl)
+            tb = t0 / (1.0 + b)
+            h = tb * (np.kron(adl, ar) + np.kron(al, adr)) + wl * omega * np.kron(nl, ir)
+        h = h + wr * omega * np.kron(il, nr)
+        out.append(h)
+    return out
+
+
+def spin_boson_product_state(dims):
+    """|up> (x) |0 ... 0>."""
+    out = []
+    for d in dims:
+        v = np.zeros(d, dtype=np.complex128)
+        v[0] = 1.0
+        out.append(v)
+    return out
+
+
+def random_canonical_mps(dims, chi_caps, seed, return_raw=False):
+    """Seeded random MPS brought into Vidal form: bond b carries
+    chi_b = min(cap_b, prod_{s<=b} d_s, prod_{s>b} d_s); column j of each
+    random tensor is weighted by exp(-j / (chi/8)) so the Schmidt values decay;
+    a right QR sweep then a left SVD sweep give Gamma[s] (d, chi_{s-1}, chi_s)
+    and Schmidt vectors lambda[b] (sum lambda^2 = 1).  A caller-side fixture:
+    it makes every bond start at its cap.  return_raw also returns the random
+    tensors (the same state, unnormalised and not canonical)."""
+    rng = np.random.default_rng(seed)
+    N = len(dims)
+    chi = [1]
+    for b in range(N - 1):
+        left = float(np.prod([float(x) for x in dims[: b + 1]]))
+        right = float(np.prod([float(x) for x in dims[b + 1:]]))
+        chi.append(int(min(chi_caps[b], left, right)))
+    chi.append(1)
+    A = []
+    for s in range(N):
+        t = rng.standard_normal((dims[s], chi[s], chi[s + 1])) + 1j * rng.standard_normal((dims[s], chi[s], chi[s + 1]))
+        w = np.exp(-np.arange(chi[s + 1]) / max(1.0, chi[s + 1] / 8.0))
+        A.append(t * w[None, None, :])
+    # right sweep: A[s] -> right-orthonormal B[s] (rows a of the chi_{s-1} x (d chi_s) matrix orthonormal)
+    B = [None] * N
+    carry = None
+    for s in range(N - 1, -1, -1):
+        t = A[s] if carry is None else np.einsum("iag,gh->iah", A[s], carry)
+        d, cl, cr = t.shape
+        M = t.transpose(1, 0, 2).reshape(cl, d * cr)          # rows alpha, columns (i, gamma)
+        if s == 0:
+            B[s] = t / np.linalg.norm(M)
+            break
+        Qt, Rt = np.linalg.qr(M.conj().T)                      # M = Rt^H Qt^H, Qt^H with orthonormal rows
+        k = Qt.shape[1]
+        B[s] = Qt.conj().T.reshape(k, d, cr).transpose(1, 0, 2)
+        carry = Rt.conj().T                                    # cl x k, absorbed into A[s-1]
+        if k != cl:
+            raise ValueError("bond %d lost rank in the QR sweep" % s)
+    # left sweep: SVDs give the Schmidt values and Gamma
+    gam, lam = [], []
+    psi = B[0]
+    lam_prev = np.ones(1)
+    for s in range(N - 1):
+        d, cl, cr = psi.shape
+        M = psi.reshape(d * cl, cr)                            # rows (i, alpha), i-major
+        U, S, Vh = np.linalg.svd(M, full_matrices=False)
+        nrm = np.linalg.norm(S)
+        U, S, Vh = U[:, :cr], S[:cr] / nrm, Vh[:cr]
+        inv = np.where(lam_prev > 0, 1.0 / np.where(lam_prev > 0, lam_prev, 1.0), 0.0)
+        gam.append(U.reshape(d, cl, cr) * inv[None, :, None])
+        lam.append(S)
+        psi = np.einsum("g,gh,jhc->jgc", S, Vh, B[s + 1])
+        lam_prev = S
+    inv = np.where(lam_prev > 0, 1.0 / np.where(lam_prev > 0, lam_prev, 1.0), 0.0)
+    gam.append(psi * inv[None, :, None])
+    if return_raw:
+        return gam, lam, A
+    return gam, lam
