@@ -390,7 +390,9 @@ extern "C" int tebd_create_multi(int n_chains, const tebd_desc_t* descs, tebd_t*
       int mc, nc, kc, lc;
       bond_caps(h->ch[cb.first], cb.second, mc, nc, kc, lc);
       lay[par].push_back(ws_layout(mc, nc, kc, lc, true, true));
-      pbytes[par].push_back(align_up(sizeof(cplx) * (size_t)mc * nc) + lay[par].back().total);
+      const ChainH& Cb = h->ch[cb.first];
+      const bool gemm_gate = Cb.d[cb.second] * Cb.d[cb.second + 1] >= GATE_GEMM_MIN;  // pre-gate theta buffer
+      pbytes[par].push_back(align_up(sizeof(cplx) * (size_t)mc * nc) * (gemm_gate ? 2 : 1) + lay[par].back().total);
     }
     ps.batch = (int)ps.bonds.size();
     max_batch = std::max(max_batch, ps.batch);
@@ -523,6 +525,10 @@ extern "C" int tebd_create_multi(int n_chains, const tebd_desc_t* descs, tebd_t*
         P.slot = c;
         P.theta = (const cplx*)(ws + o);
         o += align_up(sizeof(cplx) * (size_t)C.d[b] * C.cap_ext[b] * C.d[b + 1] * C.cap_ext[b + 2]);
+        if (C.d[b] * C.d[b + 1] >= GATE_GEMM_MIN) {
+          P.Cpre = (cplx*)(ws + o);
+          o += align_up(sizeof(cplx) * (size_t)C.d[b] * C.cap_ext[b] * C.d[b + 1] * C.cap_ext[b + 2]);
+        }
         fill_ptrs(P, ws + o, lay[par][i]);
         o += lay[par][i].total;
       }
@@ -752,6 +758,7 @@ static cudaError_t enqueue_sweep(tebd_t h, int parity) {
     cudaError_t e;
     if ((e = launch_plan(ptrs, dims, w.count, h->p, h->stream)) != cudaSuccess) return e;
     if ((e = launch_theta(dims, ptrs, w.count, w.cap, h->stream)) != cudaSuccess) return e;
+    if ((e = launch_gate_gemm(dims, ptrs, w.count, w.cap, h->stream)) != cudaSuccess) return e;
     if (h->precision == TEBD_PREC_TF32) {
       const MixedPtrs mp = mixed_carve(h->mixed, w.ms, w.count);
       if ((e = run_rrsvd_mixed(dims, ptrs, w.count, w.cap, mp, h->q, h->seed, 0, 0, -1, h->status, h->tcerr,
@@ -1045,6 +1052,7 @@ extern "C" int tebd_backward(tebd_t h, int site, const double* op, double* dgate
             launch_theta(dims, ptrs, w.count, w.cap, st, 1) != cudaSuccess ||
             launch_adj_keep_theta(dims, ptrs, adj, w.count, st) != cudaSuccess ||
             launch_theta(dims, ptrs, w.count, w.cap, st) != cudaSuccess ||
+            launch_gate_gemm(dims, ptrs, w.count, w.cap, st) != cudaSuccess ||
             run_rrsvd(dims, ptrs, w.count, w.cap, h->q, h->seed, 0, 0, -1, h->status, st, h->sweep_dev,
                       tuned ? w.tiles : nullptr) != cudaSuccess ||
             launch_rebuild(dims, ptrs, w.count, h->cutoff, h->wout + w.first, h->status, st) != cudaSuccess ||

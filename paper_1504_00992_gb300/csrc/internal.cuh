@@ -63,6 +63,7 @@ struct ProbPtr {
   double* part;       // NPART partial sums of |theta|^2
   double* scal;       // per-problem scalars: [0] ||theta||_F^2, [1] w, [2] kept rank
   cplx* Dr;           // m x r: Q Q^H A Omega_r of the accuracy check
+  cplx* Cpre;         // m x n pre-gate theta of a bond whose gate is applied as a GEMM (large d_l d_r), or null
 };
 
 enum { NPART = 64 };
@@ -93,9 +94,15 @@ cudaError_t launch_qr(int stage, const Dims* dims, const ProbPtr* ptrs, int batc
                       int only_flagged = 0);
 cudaError_t launch_jacobi(const Dims* dims, const ProbPtr* ptrs, int batch, int* status, cudaStream_t st);
 cudaError_t launch_frob2(const Dims* dims, const ProbPtr* ptrs, int batch, cudaStream_t st);
-// identity_gate = 1 writes the pre-gate theta (reverse pass)
+// identity_gate = 1 writes the pre-gate theta (reverse pass).  Otherwise a
+// bond with ptrs[p].Cpre set gets its pre-gate theta written there, and
+// launch_gate_gemm applies its gate.
 cudaError_t launch_theta(const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, cudaStream_t st,
                          int identity_gate = 0);
+// theta~ = G C for the bonds with Cpre set (a complex GEMM over the physical
+// indices, FP64): local dimensions with d_l d_r >= GATE_GEMM_MIN take this path.
+enum { GATE_GEMM_MIN = 32 };
+cudaError_t launch_gate_gemm(const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, cudaStream_t st);
 
 // standalone RRSVD epilogue: sigma/U/Vh/w/rank into caller buffers
 cudaError_t launch_rrsvd_finalize(const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, double cutoff,

@@ -122,21 +122,101 @@ __global__ void __launch_bounds__(256) k_theta(const Dims* __restrict__ dims, co
     if (o < nout) Cs[o] = acc[s];
   }
   __syncthreads();
-  // gate: rows of Cs are (i', a) = i'*ta + a, columns (j', c) = j'*tb + c
+  // gate: rows of Cs are (i', a) = i'*ta + a, columns (j', c) = j'*tb + c.
+  // A bond whose gate is applied as a GEMM gets its pre-gate theta in Cpre.
   const int dd = dl * dr;
-  cplx* th = const_cast<cplx*>(P.theta);
+  const bool pre = !identity_gate && P.Cpre != nullptr;
+  cplx* th = pre ? P.Cpre : const_cast<cplx*>(P.theta);
   for (int o = tid; o < nout; o += 256) {
     const int ri = o / cols, ci = o % cols;
     const int i = ri / ta, a = ri % ta, j = ci / tb, c = ci % tb;
     const cplx* grow = P.gate + (int64_t)(i * dr + j) * dd;
     cplx v = cmk(0.0, 0.0);
-    if (identity_gate)
+    if (identity_gate || pre)
       v = Cs[(i * ta + a) * cols + j * tb + c];
     else
       for (int ip = 0; ip < dl; ++ip)
         for (int jp = 0; jp < dr; ++jp) cfma(v, grow[ip * dr + jp], Cs[(ip * ta + a) * cols + jp * tb + c]);
     th[(int64_t)(i * cl + a0 + a) * D.n + j * cr + b0 + c] = v;
   }
+}
+
+// ---------------------------------------------------------------------------
+// Gate as a GEMM (Eq. defupdatetheta for large local dimensions):
+//   theta~[(i cl + a), (j cr + c)] = sum_{i'j'} G[(i dr + j), (i' dr + j')] C[(i' cl + a), (j' cr + c)],
+// rows (i, j) of G times the (d_l d_r) x (cl cr) matrix whose column (a, c)
+// gathers C over the physical indices.  32 x 32 output tiles (rows (i, j),
+// columns (a, c) with c fastest), 2 x 2 outputs per thread, K = d_l d_r in
+// slices of 16, FP64 (the layout of k_zgemm).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_gate_gemm(const Dims* __restrict__ dims, const ProbPtr* __restrict__ ptrs) {
+  constexpr int T = 32, TK = 16;
+  __shared__ cplx As[TK][T + 1];  // G[row][k]
+  __shared__ cplx Bs[TK][T + 1];  // C-gather[k][col]
+  const int p = blockIdx.z;
+  const Dims D = dims[p];
+  if (!D.active) return;
+  const ProbPtr P = ptrs[p];
+  if (!P.Cpre) return;
+  const int dl = D.dl, dr = D.dr, cl = D.cl, cr = D.cr;
+  const int M = dl * dr, N = cl * cr, K = M;
+  const int tm = blockIdx.y * T, tn = blockIdx.x * T;
+  if (tm >= M || tn >= N) return;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int n_ = D.n;
+  cplx acc[2][2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) acc[i][j] = cmk(0.0, 0.0);
+  for (int k0 = 0; k0 < K; k0 += TK) {
+    for (int e = tid; e < T * TK; e += 256) {  // G tile: consecutive threads along k (contiguous)
+      const int kk = e % TK, r = e / TK;
+      const int gr = tm + r, gk = k0 + kk;
+      As[kk][r] = (gr < M && gk < K) ? P.gate[(int64_t)gr * K + gk] : cmk(0.0, 0.0);
+    }
+    for (int e = tid; e < T * TK; e += 256) {  // C tile: consecutive threads along (a, c), c fastest
+      const int c = e % T, kk = e / T;
+      const int gn = tn + c, gk = k0 + kk;
+      cplx v = cmk(0.0, 0.0);
+      if (gn < N && gk < K) {
+        const int ip = gk / dr, jp = gk % dr, a = gn / cr, cc = gn % cr;
+        v = P.Cpre[(int64_t)(ip * cl + a) * n_ + jp * cr + cc];
+      }
+      Bs[kk][c] = v;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < TK; ++kk) {
+      const cplx a0 = As[kk][ty], a1 = As[kk][ty + 16];
+      const cplx b0 = Bs[kk][tx], b1 = Bs[kk][tx + 16];
+      cfma(acc[0][0], a0, b0);
+      cfma(acc[0][1], a0, b1);
+      cfma(acc[1][0], a1, b0);
+      cfma(acc[1][1], a1, b1);
+    }
+    __syncthreads();
+  }
+  cplx* th = const_cast<cplx*>(P.theta);
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int r = tm + ty + 16 * i, c = tn + tx + 16 * j;
+      if (r < M && c < N) {
+        const int ii = r / dr, jj = r % dr, a = c / cr, cc = c % cr;
+        th[(int64_t)(ii * cl + a) * n_ + jj * cr + cc] = acc[i][j];
+      }
+    }
+}
+
+cudaError_t launch_gate_gemm(const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, cudaStream_t st) {
+  const int M = cap.dl * cap.dr, N = cap.cl * cap.cr;
+  if (M < GATE_GEMM_MIN) return cudaSuccess;  // no bond of this wave takes the GEMM path
+  ProfScope ps("k_gate_gemm", st);
+  dim3 grid((N + 31) / 32, (M + 31) / 32, batch);
+  k_gate_gemm<<<grid, 256, 0, st>>>(dims, ptrs);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_theta(const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, cudaStream_t st,
