@@ -117,17 +117,17 @@ cudaError_t run_rrsvd_checked(Dims* dims, const ProbPtr* ptrs, int batch, const 
   cudaError_t e;
   if ((e = launch_omega(dims, ptrs, batch, cap, seed, 0, chain0, 1, st)) != cudaSuccess) return e;
   if ((e = launch_zgemm(G_Y0, dims, ptrs, batch, cap, st)) != cudaSuccess) return e;
-  if ((e = launch_qr(QR_Y, dims, ptrs, batch, st)) != cudaSuccess) return e;
+  if ((e = launch_qr_sized(QR_Y, dims, ptrs, batch, cap, st)) != cudaSuccess) return e;
   if ((e = run_accuracy_check(dims, ptrs, batch, cap, rounds, eps, l_max, p, seed, 0, chain0, 1, st)) != cudaSuccess)
     return e;
   for (int j = 0; j < q; ++j) {
     if ((e = launch_zgemm(G_YT, dims, ptrs, batch, cap, st)) != cudaSuccess) return e;
-    if ((e = launch_qr(QR_YT, dims, ptrs, batch, st)) != cudaSuccess) return e;
+    if ((e = launch_qr_sized(QR_YT, dims, ptrs, batch, cap, st)) != cudaSuccess) return e;
     if ((e = launch_zgemm(G_Y, dims, ptrs, batch, cap, st)) != cudaSuccess) return e;
-    if ((e = launch_qr(QR_Y, dims, ptrs, batch, st)) != cudaSuccess) return e;
+    if ((e = launch_qr_sized(QR_Y, dims, ptrs, batch, cap, st)) != cudaSuccess) return e;
   }
   if ((e = launch_zgemm(G_BH, dims, ptrs, batch, cap, st)) != cudaSuccess) return e;
-  if ((e = launch_qr(QR_BH, dims, ptrs, batch, st)) != cudaSuccess) return e;
+  if ((e = launch_qr_sized(QR_BH, dims, ptrs, batch, cap, st)) != cudaSuccess) return e;
   if ((e = launch_jacobi(dims, ptrs, batch, status, st)) != cudaSuccess) return e;
   if ((e = launch_zgemm(G_U, dims, ptrs, batch, cap, st)) != cudaSuccess) return e;
   if ((e = launch_zgemm(G_V, dims, ptrs, batch, cap, st)) != cudaSuccess) return e;

@@ -1,0 +1,38 @@
+// Double -> double-float split without FP64 arithmetic (sm_103a), shared by
+// the mixed-precision kernels and the double-float GEMMs.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tg {
+
+// x -> hi + lo with integer and FP32 operations only (GB300 runs FP64
+// arithmetic and double<->float conversions on its 1/64-rate FP64 pipe):
+// hi = x truncated to 24 significant bits, lo = the remaining 29 mantissa
+// bits rounded to FP32, so hi + lo = x to 2^-48 relative (lo may be an FP32
+// subnormal).  |x| below 2^-126 flushes to zero; non-finite x gives a
+// non-finite hi.
+__device__ __forceinline__ void split_bits(double x, float& hi, float& lo) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned int sign = (unsigned int)(u >> 32) & 0x80000000u;
+  const int e = (int)((u >> 52) & 0x7FF);
+  const unsigned long long mant = u & 0xFFFFFFFFFFFFFull;
+  const int ef = e - 1023 + 127;  // FP32 biased exponent of hi
+  if (e == 0x7FF || ef >= 255) {   // Inf / NaN / beyond FP32: non-finite hi
+    hi = __uint_as_float(sign | 0x7F800000u | (unsigned int)(mant >> 29) | (mant ? 1u : 0u));
+    lo = 0.f;
+    return;
+  }
+  if (ef <= 0) {
+    hi = __uint_as_float(sign);
+    lo = 0.f;
+    return;
+  }
+  hi = __uint_as_float(sign | ((unsigned int)ef << 23) | (unsigned int)(mant >> 29));
+  // weight of mantissa bit 0: 2^(e - 1075) = 2^(e - 1011) * 2^-64, both factors normal FP32 numbers for e >= 897
+  const float r = __uint2float_rn((unsigned int)(mant & 0x1FFFFFFFull));
+  const float l = (r * __uint_as_float((unsigned int)(e - 1011 + 127) << 23)) * 5.421010862427522e-20f;  // 2^-64
+  lo = sign ? -l : l;
+}
+
+}  // namespace tg

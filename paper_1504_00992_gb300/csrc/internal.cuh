@@ -92,6 +92,10 @@ cudaError_t launch_zgemm(int stage, const Dims* dims, const ProbPtr* ptrs, int b
                          cudaStream_t st);
 cudaError_t launch_qr(int stage, const Dims* dims, const ProbPtr* ptrs, int batch, cudaStream_t st,
                       int only_flagged = 0);
+// the same, spread over many CTAs per instance (qr_multi.cu) when the batch
+// is a few tall matrices (cap.m or cap.n rows, cap.l columns)
+cudaError_t launch_qr_sized(int stage, const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap,
+                           cudaStream_t st);
 cudaError_t launch_jacobi(const Dims* dims, const ProbPtr* ptrs, int batch, int* status, cudaStream_t st);
 cudaError_t launch_frob2(const Dims* dims, const ProbPtr* ptrs, int batch, cudaStream_t st);
 // identity_gate = 1 writes the pre-gate theta (reverse pass).  Otherwise a
@@ -103,6 +107,8 @@ cudaError_t launch_theta(const Dims* dims, const ProbPtr* ptrs, int batch, const
 // indices, FP64): local dimensions with d_l d_r >= GATE_GEMM_MIN take this path.
 enum { GATE_GEMM_MIN = 32 };
 cudaError_t launch_gate_gemm(const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, cudaStream_t st);
+// the same in double-float arithmetic on the FP32 pipes (FP64-accurate; df_proj.cu)
+cudaError_t launch_gate_gemm_df(const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, cudaStream_t st);
 
 // standalone RRSVD epilogue: sigma/U/Vh/w/rank into caller buffers
 cudaError_t launch_rrsvd_finalize(const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, double cutoff,

@@ -15,6 +15,7 @@
 
 #include "internal.cuh"
 #include "profiler.cuh"
+#include "dfsplit.cuh"
 
 namespace tg {
 
@@ -200,7 +201,7 @@ static cudaError_t launch_zgemm_stage(int rows, int cols, const Dims* dims, cons
 // ---------------------------------------------------------------------------
 // Double-float ("FP64-accurate on FP32 pipes") batched complex GEMM, same
 // stages and layouts as k_zgemm.  Every FP64 input x is split at staging into
-// hi = fl32(x), lo = fl32(x - hi) (48 significant bits); each real product
+// a pair hi + lo of FP32 numbers (48 significant bits); each real product
 // x y is formed error-free up to the cross terms, p = xh yh exactly split by
 // FMA into (ph, pe), plus xh yl + xl yh; sums use Knuth's TwoSum on the high
 // parts with the error terms gathered in a low accumulator (Dekker 1971;
@@ -211,10 +212,9 @@ static cudaError_t launch_zgemm_stage(int rows, int cols, const Dims* dims, cons
 // ---------------------------------------------------------------------------
 struct df2 { float h, l; };
 
-__device__ __forceinline__ void df_split(double x, float& h, float& l) {
-  h = (float)x;
-  l = (float)(x - (double)h);
-}
+// hi = x truncated to 24 bits, lo = the rest (integer and FP32 operations
+// only: conversions through the FP64 pipe would cost half its throughput)
+__device__ __forceinline__ void df_split(double x, float& h, float& l) { split_bits(x, h, l); }
 
 // acc += x * y   (x, y double-float, acc double-float)
 __device__ __forceinline__ void df_fma(df2& acc, float xh, float xl, float yh, float yl) {
@@ -736,15 +736,15 @@ cudaError_t run_rrsvd(const Dims* dims, const ProbPtr* ptrs, int batch, const Ca
   auto T = [&](int stage) { return tiles ? tiles[stage] : 0; };
   TG_TRY(launch_omega(dims, ptrs, batch, cap, seed, sweep, chain0, chain_stride, st, sweep_dev));
   TG_TRY(launch_zgemm_tile(G_Y0, T(G_Y0), dims, ptrs, batch, cap, st));  // Y0 = A Omega
-  TG_TRY(launch_qr(QR_Y, dims, ptrs, batch, st));                          // Y0 = Q0 R0
+  TG_TRY(launch_qr_sized(QR_Y, dims, ptrs, batch, cap, st));                    // Y0 = Q0 R0
   for (int j = 0; j < q; ++j) {
     TG_TRY(launch_zgemm_tile(G_YT, T(G_YT), dims, ptrs, batch, cap, st)); // Y~ = A^H Q
-    TG_TRY(launch_qr(QR_YT, dims, ptrs, batch, st));                       // Y~ = Q~ R~
+    TG_TRY(launch_qr_sized(QR_YT, dims, ptrs, batch, cap, st));                 // Y~ = Q~ R~
     TG_TRY(launch_zgemm_tile(G_Y, T(G_Y), dims, ptrs, batch, cap, st));   // Y = A Q~
-    TG_TRY(launch_qr(QR_Y, dims, ptrs, batch, st));                        // Y = Q R
+    TG_TRY(launch_qr_sized(QR_Y, dims, ptrs, batch, cap, st));                  // Y = Q R
   }
   TG_TRY(launch_zgemm_tile(G_BH, T(G_BH), dims, ptrs, batch, cap, st));   // B^H = A^H Q
-  TG_TRY(launch_qr(QR_BH, dims, ptrs, batch, st));                         // B^H = Qb Rb
+  TG_TRY(launch_qr_sized(QR_BH, dims, ptrs, batch, cap, st));                   // B^H = Qb Rb
   TG_TRY(launch_jacobi(dims, ptrs, batch, status, st));                    // Rb^H J = W S
   TG_TRY(launch_zgemm_tile(G_U, T(G_U), dims, ptrs, batch, cap, st));     // U = Q J_k
   TG_TRY(launch_zgemm_tile(G_V, T(G_V), dims, ptrs, batch, cap, st));     // V = Qb W_k  (stored as V^H)

@@ -30,6 +30,7 @@
 
 #include "internal.cuh"
 #include "mixed.cuh"
+#include "dfsplit.cuh"
 #include "profiler.cuh"
 #include "tc_gemm.cuh"
 
@@ -52,35 +53,6 @@ __device__ __forceinline__ float tf32_rna(float x) {
 //     -Im lo), when thd is set, for the projection.
 // The tiles cover the zero padding of both copies.
 // ---------------------------------------------------------------------------
-// x -> hi + lo with integer and FP32 operations only (GB300 runs FP64
-// arithmetic and double<->float conversions on its 1/64-rate FP64 pipe):
-// hi = x truncated to 24 significant bits, lo = the remaining 29 mantissa
-// bits rounded to FP32, so hi + lo = x to 2^-48 relative (lo may be an FP32
-// subnormal).  |x| below 2^-126 flushes to zero; non-finite x gives a
-// non-finite hi.
-__device__ __forceinline__ void split_bits(double x, float& hi, float& lo) {
-  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
-  const unsigned int sign = (unsigned int)(u >> 32) & 0x80000000u;
-  const int e = (int)((u >> 52) & 0x7FF);
-  const unsigned long long mant = u & 0xFFFFFFFFFFFFFull;
-  const int ef = e - 1023 + 127;  // FP32 biased exponent of hi
-  if (e == 0x7FF || ef >= 255) {   // Inf / NaN / beyond FP32: non-finite hi
-    hi = __uint_as_float(sign | 0x7F800000u | (unsigned int)(mant >> 29) | (mant ? 1u : 0u));
-    lo = 0.f;
-    return;
-  }
-  if (ef <= 0) {
-    hi = __uint_as_float(sign);
-    lo = 0.f;
-    return;
-  }
-  hi = __uint_as_float(sign | ((unsigned int)ef << 23) | (unsigned int)(mant >> 29));
-  // weight of mantissa bit 0: 2^(e - 1075) = 2^(e - 1011) * 2^-64, both factors normal FP32 numbers for e >= 897
-  const float r = __uint2float_rn((unsigned int)(mant & 0x1FFFFFFFull));
-  const float l = (r * __uint_as_float((unsigned int)(e - 1011 + 127) << 23)) * 5.421010862427522e-20f;  // 2^-64
-  lo = sign ? -l : l;
-}
-
 // Complex standard Gaussian of sketch element `idx` from the same Philox
 // words as the FP64 path, by Box-Muller in FP32 (24-bit uniforms): the
 // mixed form rounds Omega to TF32, and its refinement pass needs it to FP32.
@@ -607,10 +579,10 @@ cudaError_t run_rrsvd_mixed(const Dims* dims, const ProbPtr* ptrs, int batch, co
       k_f32_to_f64<<<dim3(grid1d((int64_t)m * l), batch), 256, 0, st>>>(mp.Yf, dims, ptrs, m, l);
       MX_TRY(cudaGetLastError());
     }
-    MX_TRY(launch_qr(QR_Y, dims, ptrs, batch, st));          // last QR in FP64
+    MX_TRY(launch_qr_sized(QR_Y, dims, ptrs, batch, cap, st));  // last QR in FP64
     MX_TRY(launch_zgemm_df(G_BH, dims, ptrs, batch, cap, st));  // B^H = A^H Q (double-float)
   }
-  MX_TRY(launch_qr(QR_BH, dims, ptrs, batch, st));
+  MX_TRY(launch_qr_sized(QR_BH, dims, ptrs, batch, cap, st));
   MX_TRY(launch_jacobi(dims, ptrs, batch, status, st));
   MX_TRY(launch_zgemm_df(G_U, dims, ptrs, batch, cap, st));
   MX_TRY(launch_zgemm_df(G_V, dims, ptrs, batch, cap, st));

@@ -47,6 +47,10 @@ def _compare(theta, res, t, k, p, q, chain):
     (50, 120, 16, 4, 3),      # wide
     (40, 30, 30, 10, 2),      # l reaches min(m, n): exact
     (7, 5, 8, 3, 1),          # k above min(m, n)
+    # few tall instances: Householder QRs spread over many CTAs per instance
+    (1100, 300, 40, 8, 2),    # Y (1100 x 48) only
+    (300, 1300, 30, 10, 1),   # A^H Q and B^H (1300 x 40) only
+    (1500, 1200, 60, 9, 1),   # all three, l = 69: ragged last panel
 ])
 def test_rrsvd_matches_oracle(lib, m, n, k, p, q):
     from paper_1504_00992_gb300 import binding as B
@@ -129,21 +133,25 @@ def test_rrsvd_argument_errors(lib):
         B.rrsvd_plan_destroy(plan)
 
 
-def test_single_bond_stress_full_size_sampled(lib):
+@pytest.mark.parametrize("batch", [2, 50])
+def test_single_bond_stress_full_size_sampled(lib, batch):
     """The single-bond stress workload at full size (2000 x 2000, k=100, p=20,
-    q=2, spectrum exp(-(k-1)/15)) in the bench's launch configuration, two
-    sampled instances checked against the oracle; the method meets the 1e-8
-    accuracy bar against the exact spectrum."""
+    q=2, spectrum exp(-(k-1)/15)), two sampled instances checked against the
+    oracle; the method meets the 1e-8 accuracy bar against the exact
+    spectrum.  Two instances take the Householder QRs spread over many CTAs
+    per instance; a batch of 50 (two distinct matrices repeated) takes the
+    one-CTA-per-instance QRs of the bench's batch."""
     from paper_1504_00992_gb300 import binding as B
     m = n = 2000
-    k, p, q, batch = 100, 20, 2, 2
+    k, p, q = 100, 20, 2
     sig = I.exp_spectrum(n)
-    theta = np.stack([I.synthetic_theta(m, n, sig, seed=t) for t in range(batch)])
+    base = [I.synthetic_theta(m, n, sig, seed=t) for t in range(2)]
+    theta = np.stack([base[t % 2] for t in range(batch)])
     plan = B.rrsvd_plan_create(m, n, k, p, q, batch, B.TEBD_PREC_FP64, SEED)
     try:
         res = rrsvd_device(B, plan, theta)
     finally:
         B.rrsvd_plan_destroy(plan)
-    for t in range(batch):
+    for t in (0, batch - 1):
         _compare(theta[t], res, t, k, p, q, t)
         assert np.abs(res["sigma"][t] - sig[:k]).max() <= 1e-8
