@@ -433,6 +433,10 @@ MixedSizes mixed_sizes(int m, int n, int k, int l) {
   s.ytf = (size_t)n * l * sizeof(float2);
   s.df = (size_t)l * l * sizeof(float2);
   s.thd = reorth_fits(m, l) ? (size_t)m * n * sizeof(float4) : 0;
+  const int mx = m > n ? m : n;
+  s.qs = ((!qr_blk_f32_fits(m, l) && qr_multi_f32_fits(m, l)) || (!qr_blk_f32_fits(n, l) && qr_multi_f32_fits(n, l)))
+             ? qr_multi_f32_scratch(mx, l) * sizeof(float2)
+             : 0;
   s.ntile = ((s.K1 / 2 + 31) / 32) * ((s.K2 / 2 + 31) / 32);
   (void)k;
   return s;
@@ -443,7 +447,7 @@ static size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 size_t mixed_bytes(const MixedSizes& s, int batch) {
   return 2 * up256(s.thf * batch) + 2 * up256(s.tha * batch) + 2 * up256(s.bt * batch) + 2 * up256(s.yf * batch) +
          2 * up256(s.ytf * batch) + up256(s.df * batch) + up256(s.thd * batch) +
-         up256((size_t)s.ntile * sizeof(double) * batch);
+         up256((size_t)s.ntile * sizeof(double) * batch) + up256(s.qs * batch);
 }
 
 MixedPtrs mixed_carve(char* base, const MixedSizes& s, int batch) {
@@ -464,6 +468,8 @@ MixedPtrs mixed_carve(char* base, const MixedSizes& s, int batch) {
   o += up256(s.thd * batch);
   p.tpart = (double*)(base + o);
   o += up256((size_t)s.ntile * sizeof(double) * batch);
+  p.qscr = s.qs ? (float2*)(base + o) : nullptr;
+  o += up256(s.qs * batch);
   return p;
 }
 
@@ -509,7 +515,10 @@ static cudaError_t tc_product(const float* A0, const float* A1, const float* B0,
   return cudaGetLastError();
 }
 
-static cudaError_t qr_f32(float2* A, float2* Q, int M, int L, int batch, cudaStream_t st) {
+static cudaError_t qr_f32(float2* A, float2* Q, int M, int L, int batch, const MixedPtrs& mp, const MixedSizes& s,
+                          cudaStream_t st) {
+  if (!qr_blk_f32_fits(M, L) && mp.qscr && qr_multi_f32_fits(M, L))
+    return launch_qr_multi_f32(A, Q, mp.qscr, s.qs / sizeof(float2), M, L, batch, st);
   ProfScope ps("k_qr_f32", st);
   if (qr_blk_f32_fits(M, L)) return launch_qr_blk_f32(A, Q, M, L, batch, st);
   k_qr_f32<<<batch, 1024, 0, st>>>(A, Q, M, L);
@@ -561,16 +570,16 @@ cudaError_t run_rrsvd_mixed(const Dims* dims, const ProbPtr* ptrs, int batch, co
   MX_TRY(tc_product(mp.thf_hi, mp.thf_lo, mp.bt_hi, mp.bt_lo, m, s.K1, s, l, p0, mp.Yf, batch, err, st));
   for (int j = 1; j <= q; ++j) {
     const int np = (j == q) ? 3 : 1;
-    MX_TRY(qr_f32(mp.Yf, mp.Qf, m, l, batch, st));                                 // Y = Q R
+    MX_TRY(qr_f32(mp.Yf, mp.Qf, m, l, batch, mp, s, st));    // Y = Q R
     MX_TRY(conv_bt(mp.Qf, dims, mp, m, l, s.K2, s, np == 3, batch, st));
     MX_TRY(tc_product(mp.tha_hi, mp.tha_lo, mp.bt_hi, mp.bt_lo, n, s.K2, s, l, np, mp.Ytf, batch, err, st));  // A^H Q
-    MX_TRY(qr_f32(mp.Ytf, mp.Qtf, n, l, batch, st));                              // = Q~ R~
+    MX_TRY(qr_f32(mp.Ytf, mp.Qtf, n, l, batch, mp, s, st));  // = Q~ R~
     MX_TRY(conv_bt(mp.Qtf, dims, mp, n, l, s.K1, s, np == 3, batch, st));
     MX_TRY(tc_product(mp.thf_hi, mp.thf_lo, mp.bt_hi, mp.bt_lo, m, s.K1, s, l, np, mp.Yf, batch, err, st));  // A Q~
   }
   if (reorth_fits(m, l)) {
     // last QR: FP32 Householder, then the FP64-accurate re-orthonormalisation
-    MX_TRY(qr_f32(mp.Yf, mp.Qf, m, l, batch, st));
+    MX_TRY(qr_f32(mp.Yf, mp.Qf, m, l, batch, mp, s, st));
     MX_TRY(launch_reorth(mp.Qf, mp.Df, dims, ptrs, m, l, batch, status, st));
     MX_TRY(launch_proj_df(mp.thd, dims, ptrs, mp.Qf, mp.Df, m, n, l, batch, st));  // B^H = A^H Q
   } else {

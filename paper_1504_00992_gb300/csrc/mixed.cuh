@@ -14,6 +14,7 @@ struct MixedSizes {
   int Np;        // 2l rounded up to 16: rows of Bt (tensor-core N)
   int BN;        // tensor-core tile width, min(Np, 256)
   size_t thf, tha, bt, yf, ytf, df, thd;  // bytes per instance
+  size_t qs;     // bytes per instance of the many-CTA FP32 QR's scratch (0: not used)
   int ntile;     // 32 x 32 tiles of the theta conversion (partials of ||theta||_F^2)
 };
 
@@ -32,6 +33,7 @@ struct MixedPtrs {
   float2* Df;     // l x l correction of the re-orthonormalisation
   float4* thd;    // m x n double-float conj(theta) (Re hi, Re lo, -Im hi, -Im lo), or null
   double* tpart;  // ntile partial sums of |theta|^2 per instance
+  float2* qscr;   // scratch of the many-CTA FP32 QR (qs bytes per instance), or null
 };
 
 MixedSizes mixed_sizes(int m, int n, int k, int l);
@@ -42,6 +44,13 @@ MixedPtrs mixed_carve(char* base, const MixedSizes& s, int batch);
 // instance, overwritten) -> Q; usable when qr_blk_f32_fits(M, L).
 bool qr_blk_f32_fits(int M, int L);
 cudaError_t launch_qr_blk_f32(float2* A, float2* Q, int M, int L, int batch, cudaStream_t st);
+// The same QR spread over many CTAs per instance (qr_multi.cu), for matrices
+// too tall for the blocked kernel's shared memory; scr holds
+// qr_multi_f32_scratch(M, L) float2 per instance at the given stride.
+bool qr_multi_f32_fits(int M, int L);
+size_t qr_multi_f32_scratch(int M, int L);
+cudaError_t launch_qr_multi_f32(float2* A, float2* Q, float2* scr, size_t stride, int M, int L, int batch,
+                                cudaStream_t st);
 // Q_f (FP32, M x L) -> ptrs[z].Q (FP64) orthonormal to ~1e-13, spanning
 // range(Q_f); uses ptrs[z].R as scratch; usable when reorth_fits(M, L).
 bool reorth_fits(int M, int L);

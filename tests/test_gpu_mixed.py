@@ -34,6 +34,7 @@ SEED = 4321
     (400, 360, 120, 20, 1, 30.0),  # l = 140 > 128: FP64 last QR
     (3700, 200, 20, 10, 1, 6.0),   # Y too tall for the blocked FP32 QR: unblocked fallback
     (1200, 400, 140, 20, 1, 12.0), # l = 160: FP64 last QR spread over many CTAs per instance
+    (3700, 300, 30, 10, 1, 6.0),   # Y too tall for the blocked FP32 QR, l = 40: FP32 QR over many CTAs
 ])
 def test_mixed_form_meets_its_tolerances(lib, m, n, k, p, q, scale):
     from paper_1504_00992_gb300 import binding as B
