@@ -52,6 +52,7 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tebd", action="store_true")
+    ap.add_argument("--no-spin-boson", action="store_true")
     return ap.parse_args()
 
 
@@ -469,6 +470,42 @@ def run_tebd_many(B, I, torch, n_chains=256, steps=10, warm=2, unbatched_chains=
                         "dt=0.01, p=10, q=1, Neel; graphs + 16 GB wave budget, after %d warm-up steps" % warm}
 
 
+def run_tebd_spin_boson(B, I, torch, steps=1, warm=1):
+    """Spin-boson chain in star-to-chain form: a spin and 100 bosonic sites
+    whose local dimension falls from 32 to 4, couplings 1/(1+n), per-bond
+    caps falling from 256 to 64, from a canonical random MPS at the caps
+    (seed 0), dt = 0.05, p = 10, q = 2; the TF32 form (TF32 sketches with FP32
+    QRs, FP64-accurate projection, FP64 small SVD), all bonds of a parity per
+    launch sequence replayed from CUDA graphs, 40 GB wave budget.  One
+    second-order step = even, odd, even sweep."""
+    dims, caps = I.spin_boson_sizes(100, 32, 4, 256, 64)
+    g0, lam0 = I.random_canonical_mps(dims, caps, 0)
+    hs = I.spin_boson_bond_terms(dims)
+    dt, p, q = 0.05, 10, 2
+    sim = B.Tebd(len(dims), 2, 0, p, q, 3, d_site=dims, chi_bond=caps, precision=B.TEBD_PREC_TF32, use_graph=1,
+                 workspace_budget=40 << 30)
+    sim.set_mps(g0, lam0)
+    sim.set_gates(0, I.trotter_gates(hs, dt / 2))
+    sim.set_gates(1, I.trotter_gates(hs, dt))
+    for _ in range(warm):
+        sim.step_even(); sim.step_odd(); sim.step_even()
+    sim.discarded_weight()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        sim.step_even(); sim.step_odd(); sim.step_even()
+    w = sim.discarded_weight()
+    el = time.perf_counter() - t0
+    nb = len(dims) - 1
+    upd = steps * (2 * ((nb + 1) // 2) + nb // 2)
+    info = sim.workspace_info() if hasattr(sim, "workspace_info") else None
+    sim.close()
+    return {"value": upd / el, "unit": "bond updates/s", "seconds_per_step": el / steps, "steps_timed": steps,
+            "precision": "tf32 (mixed form)", "discarded_weight": float(w[0]), "workspace": info,
+            "workload": "spin-boson chain: spin + 100 bosons, d 32 -> 4, chi caps 256 -> 64, dt=0.05, p=10, q=2, "
+                        "canonical random MPS at the caps (seed 0); graphs, 40 GB wave budget, after %d warm-up "
+                        "step(s)" % warm}
+
+
 def run_tebd_gradient(B, I, torch):
     """Differentiable form: gradient of <sigma^z_19>(t=1) of the transverse-field
     Ising chain N=40, chi=64, dt=0.02, 50 steps with respect to its 39
@@ -547,12 +584,16 @@ def main():
     k, l = head["k"], head["l"]
     gemm_f, qr_f, uv_f = flops_rrsvd(M, N_, k, l, Q_PI)
 
-    tebd = many = grad = checked = None
+    tebd = many = grad = checked = sb = None
     if not args.no_tebd:
         checked = run_rrsvd_checked(B, torch, dev, theta, sig, batch)
         tebd = run_tebd_c1(B, I, torch)
         many = run_tebd_many(B, I, torch, steps=2)
         grad = run_tebd_gradient(B, I, torch)
+        if not args.no_spin_boson:
+            del theta
+            torch.cuda.empty_cache()
+            sb = run_tebd_spin_boson(B, I, torch)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -584,7 +625,8 @@ def main():
                 "roofline": roof, "kernel_time_ms": shares, "gpu_launches": launches,
                 "flops_per_update": {"gemm": gemm_f, "qr": qr_f, "uv": uv_f},
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": head["clocks"], "tebd_c1": tebd,
-                "tebd_many_chains": many, "tebd_gradient": grad, "rrsvd_accuracy_check": checked}
+                "tebd_many_chains": many, "tebd_gradient": grad, "rrsvd_accuracy_check": checked,
+                "tebd_spin_boson": sb}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

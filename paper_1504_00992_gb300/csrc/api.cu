@@ -757,10 +757,15 @@ static cudaError_t enqueue_sweep(tebd_t h, int parity) {
     const bool tuned = w.tiles[0] != 0;
     cudaError_t e;
     if ((e = launch_plan(ptrs, dims, w.count, h->p, h->stream)) != cudaSuccess) return e;
-    if ((e = launch_theta(dims, ptrs, w.count, w.cap, h->stream)) != cudaSuccess) return e;
-    if ((e = (h->precision == TEBD_PREC_TF32 ? launch_gate_gemm_df : launch_gate_gemm)(dims, ptrs, w.count, w.cap,
-                                                                                      h->stream)) != cudaSuccess)
-      return e;
+    if (h->precision == TEBD_PREC_TF32) {
+      // bonds of large local dimensions: contraction and gate as double-float GEMMs
+      if ((e = launch_theta(dims, ptrs, w.count, w.cap, h->stream, 0, 1)) != cudaSuccess) return e;
+      if ((e = launch_theta_df(dims, ptrs, w.count, w.cap, h->stream)) != cudaSuccess) return e;
+      if ((e = launch_gate_gemm_df(dims, ptrs, w.count, w.cap, h->stream)) != cudaSuccess) return e;
+    } else {
+      if ((e = launch_theta(dims, ptrs, w.count, w.cap, h->stream)) != cudaSuccess) return e;
+      if ((e = launch_gate_gemm(dims, ptrs, w.count, w.cap, h->stream)) != cudaSuccess) return e;
+    }
     if (h->precision == TEBD_PREC_TF32) {
       const MixedPtrs mp = mixed_carve(h->mixed, w.ms, w.count);
       if ((e = run_rrsvd_mixed(dims, ptrs, w.count, w.cap, mp, h->q, h->seed, 0, 0, -1, h->status, h->tcerr,

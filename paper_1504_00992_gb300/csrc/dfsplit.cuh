@@ -1,5 +1,6 @@
-// Double -> double-float split without FP64 arithmetic (sm_103a), shared by
-// the mixed-precision kernels and the double-float GEMMs.
+// Double-float (FP32 pair) arithmetic of the mixed-precision kernels and the
+// double-float GEMMs (sm_103a): the split of a double without FP64
+// arithmetic, TwoSum, products accumulated into a pair, renormalisation.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -33,6 +34,37 @@ __device__ __forceinline__ void split_bits(double x, float& hi, float& lo) {
   const float r = __uint2float_rn((unsigned int)(mant & 0x1FFFFFFFull));
   const float l = (r * __uint_as_float((unsigned int)(e - 1011 + 127) << 23)) * 5.421010862427522e-20f;  // 2^-64
   lo = sign ? -l : l;
+}
+
+// (s, e) with s + e = a + b exactly (Knuth's TwoSum)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float v = s - a;
+  e = (a - (s - v)) + (b - v);
+}
+// acc += (xh, xl) (yh, yl)
+__device__ __forceinline__ void dfx_dd(float& h, float& lo, float xh, float xl, float yh, float yl) {
+  const float ph = xh * yh;
+  const float pe = fmaf(xh, yh, -ph);
+  const float pc = fmaf(xh, yl, xl * yh);
+  float t, e;
+  two_sum(h, ph, t, e);
+  h = t;
+  lo += (e + pe) + pc;
+}
+// acc += x (yh, yl), x a single float
+__device__ __forceinline__ void dfx_sd(float& h, float& lo, float x, float yh, float yl) {
+  const float ph = x * yh;
+  const float pe = fmaf(x, yh, -ph);
+  float t, e;
+  two_sum(h, ph, t, e);
+  h = t;
+  lo += (e + pe) + x * yl;
+}
+__device__ __forceinline__ void fast2(float& h, float& lo) {
+  const float s = h + lo;
+  lo = lo - (s - h);
+  h = s;
 }
 
 }  // namespace tg

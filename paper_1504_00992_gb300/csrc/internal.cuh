@@ -97,18 +97,25 @@ cudaError_t launch_qr(int stage, const Dims* dims, const ProbPtr* ptrs, int batc
 cudaError_t launch_qr_sized(int stage, const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap,
                            cudaStream_t st);
 cudaError_t launch_jacobi(const Dims* dims, const ProbPtr* ptrs, int batch, int* status, cudaStream_t st);
+// the same, each instance on a cluster of CTAs (jacobi_cluster.cu) when the
+// batch is a few instances with cap.l >= 64
+cudaError_t launch_jacobi_sized(const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, int* status,
+                                cudaStream_t st);
 cudaError_t launch_frob2(const Dims* dims, const ProbPtr* ptrs, int batch, cudaStream_t st);
 // identity_gate = 1 writes the pre-gate theta (reverse pass).  Otherwise a
 // bond with ptrs[p].Cpre set gets its pre-gate theta written there, and
-// launch_gate_gemm applies its gate.
+// launch_gate_gemm applies its gate; skip_pre = 1 leaves those bonds to
+// launch_theta_df.
 cudaError_t launch_theta(const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, cudaStream_t st,
-                         int identity_gate = 0);
+                         int identity_gate = 0, int skip_pre = 0);
 // theta~ = G C for the bonds with Cpre set (a complex GEMM over the physical
 // indices, FP64): local dimensions with d_l d_r >= GATE_GEMM_MIN take this path.
 enum { GATE_GEMM_MIN = 32 };
 cudaError_t launch_gate_gemm(const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, cudaStream_t st);
-// the same in double-float arithmetic on the FP32 pipes (FP64-accurate; df_proj.cu)
+// the same in double-float arithmetic on the FP32 pipes (FP64-accurate; df_gemm.cu)
 cudaError_t launch_gate_gemm_df(const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, cudaStream_t st);
+// the pre-gate theta of the bonds with Cpre set, in double-float arithmetic (df_gemm.cu)
+cudaError_t launch_theta_df(const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, cudaStream_t st);
 
 // standalone RRSVD epilogue: sigma/U/Vh/w/rank into caller buffers
 cudaError_t launch_rrsvd_finalize(const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, double cutoff,

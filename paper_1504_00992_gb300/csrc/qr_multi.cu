@@ -35,7 +35,7 @@
 namespace tg {
 
 enum { QM_NB = 16, QM_PT = 512, QM_AT = 256, QM_CW = QM_AT / 32, QM_MIN_RC = 512 };
-enum { QM_MIN_M = 1024, QM_MIN_L = 32, QM_MAX_BATCH = 48 };
+enum { QM_MIN_M = 1024, QM_MIN_L = 32, QM_MAX_BATCH = 96 };
 
 // number of row chunks of the apply kernels: rows of at least QM_MIN_RC, and
 // at most L / QM_NB chunks (the partial products of the FP64 form live in the

@@ -56,12 +56,13 @@ cudaError_t launch_plan(const ProbPtr* ptrs, Dims* dims, int batch, int p, cudaS
 enum { TH_TK = 16, TH_MAXR = 64 };
 
 __global__ void __launch_bounds__(256) k_theta(const Dims* __restrict__ dims, const ProbPtr* __restrict__ ptrs,
-                                               int identity_gate) {
+                                               int identity_gate, int skip_pre) {
   extern __shared__ cplx th_sm[];
   const int p = blockIdx.z;
   const Dims D = dims[p];
   if (!D.active) return;
   const ProbPtr P = ptrs[p];
+  if (skip_pre && !identity_gate && P.Cpre) return;  // contracted by launch_theta_df
   const int dl = D.dl, dr = D.dr, cl = D.cl, cm = D.cm, cr = D.cr;
   const int TA = max(1, 32 / dl), TB = max(1, 32 / dr);
   const int a0 = blockIdx.y * TA, b0 = blockIdx.x * TB;
@@ -220,7 +221,7 @@ cudaError_t launch_gate_gemm(const Dims* dims, const ProbPtr* ptrs, int batch, c
 }
 
 cudaError_t launch_theta(const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, cudaStream_t st,
-                         int identity_gate) {
+                         int identity_gate, int skip_pre) {
   const int TA = (cap.dl >= 32) ? 1 : 32 / cap.dl;
   const int TB = (cap.dr >= 32) ? 1 : 32 / cap.dr;
   dim3 grid((cap.cr + TB - 1) / TB, (cap.cl + TA - 1) / TA, batch);
@@ -231,7 +232,7 @@ cudaError_t launch_theta(const Dims* dims, const ProbPtr* ptrs, int batch, const
     attr_set = true;
   }
   ProfScope ps("k_theta", st);
-  k_theta<<<grid, 256, smem, st>>>(dims, ptrs, identity_gate);
+  k_theta<<<grid, 256, smem, st>>>(dims, ptrs, identity_gate, skip_pre);
   return cudaGetLastError();
 }
 
