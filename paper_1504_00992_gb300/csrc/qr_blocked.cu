@@ -45,9 +45,13 @@ __host__ __device__ inline size_t qb_smem_bytes(int M, int L) {
 
 // C[j0:M, c0:L) <- C - V op(T) (V^H C), op(T) = T^H (trans) or T.  V holds jb
 // reflectors in shared memory (local row r = global row j0 + r, zero above
-// each reflector's first row).  All threads of the CTA call it.
+// each reflector's first row).  When a column group's rows are split over
+// several warps, their partial products go to the scratch `part`
+// (QB_WARPS * QB_NB * QB_CW real and imaginary parts) and are summed in a
+// fixed order, so the result does not depend on scheduling.  All threads of
+// the CTA call it.
 __device__ void qb_apply(float2* C, int M, int j0, int jb, int c0, int L, const float2* Vs, int ldv,
-                         const float2* Tp, bool trans, float2* W, float2* W2) {
+                         const float2* Tp, bool trans, float2* W, float2* W2, float* part) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int Mr = M - j0, ncol = L - c0;
   if (ncol <= 0) return;
@@ -98,13 +102,31 @@ __device__ void qb_apply(float2* C, int M, int j0, int jb, int c0, int L, const 
 #pragma unroll
       for (int w = 0; w < QB_CW; ++w) {
         const float sx = qb_wsum(acc[i][w].x), sy = qb_wsum(acc[i][w].y);
-        if (lane == ((i * QB_CW + w) & 31) && i < jb && w < nc) {
-          atomicAdd(&W[i * L + cb + w].x, sx);
-          atomicAdd(&W[i * L + cb + w].y, sy);
+        if (lane == ((i * QB_CW + w) & 31)) {
+          if (rs > 1) {  // one task per warp (ntask <= QB_WARPS): a slot per warp
+            part[(warp * QB_NB + i) * QB_CW + w] = sx;
+            part[QB_WARPS * QB_NB * QB_CW + (warp * QB_NB + i) * QB_CW + w] = sy;
+          } else if (i < jb && w < nc) {  // the column group's only contributor
+            W[i * L + cb + w] = make_float2(sx, sy);
+          }
         }
       }
   }
   __syncthreads();
+  if (rs > 1) {
+    // task t = h ncg + cg ran on warp t: sum the row slices h in order
+    for (int e = tid; e < jb * ncol; e += QB_THREADS) {
+      const int i = e / ncol, cl = e % ncol, cg = cl / QB_CW, w = cl % QB_CW;
+      float sx = 0.f, sy = 0.f;
+      for (int h = 0; h < rs; ++h) {
+        const int slot = ((h * ncg + cg) * QB_NB + i) * QB_CW + w;
+        sx += part[slot];
+        sy += part[QB_WARPS * QB_NB * QB_CW + slot];
+      }
+      W[i * L + c0 + cl] = make_float2(sx, sy);
+    }
+    __syncthreads();
+  }
   // W2 = op(T) W
   for (int e = tid; e < jb * ncol; e += QB_THREADS) {
     const int i = e / ncol, c = c0 + e % ncol;
@@ -389,7 +411,7 @@ __global__ void __launch_bounds__(QB_THREADS) k_qr_blk_f32(float2* Abase, float2
       __syncthreads();
     }
     // --- trailing columns: A <- A - V T^H V^H A
-    qb_apply(A, M, j0, jb, j0 + jb, L, Vs, ldv, Tall + p * QB_NB * QB_NB, true, W, W2);
+    qb_apply(A, M, j0, jb, j0 + jb, L, Vs, ldv, Tall + p * QB_NB * QB_NB, true, W, W2, red);
   }
 
   // --- Q = H_0 ... H_{L-1} [I; 0], panels backwards
@@ -405,7 +427,7 @@ __global__ void __launch_bounds__(QB_THREADS) k_qr_blk_f32(float2* Abase, float2
       Vs[i * ldv + r] = (r < i) ? make_float2(0.f, 0.f) : A[(size_t)(j0 + i) * M + j0 + r];
     }
     __syncthreads();
-    qb_apply(Qo, M, j0, jb, j0, L, Vs, ldv, Tall + p * QB_NB * QB_NB, false, W, W2);
+    qb_apply(Qo, M, j0, jb, j0, L, Vs, ldv, Tall + p * QB_NB * QB_NB, false, W, W2, red);
   }
 }
 
