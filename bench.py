@@ -53,6 +53,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tebd", action="store_true")
     ap.add_argument("--no-spin-boson", action="store_true")
+    ap.add_argument("--spin-boson-only", action="store_true",
+                    help="run only the spin-boson chain measurement (for kernel launch lists)")
     return ap.parse_args()
 
 
@@ -563,6 +565,10 @@ def main():
     __graft_entry__.build()
     from paper_1504_00992_gb300 import binding as B
     from paper_1504_00992_gb300 import inputs as I
+    if args.spin_boson_only:
+        if rank == 0:
+            print(json.dumps({"tebd_spin_boson": run_tebd_spin_boson(B, I, torch)}), flush=True)
+        return
 
     batch = args.batch
     pool, sig = synthetic_pool(POOL)

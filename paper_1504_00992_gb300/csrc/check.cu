@@ -128,7 +128,7 @@ cudaError_t run_rrsvd_checked(Dims* dims, const ProbPtr* ptrs, int batch, const 
   }
   if ((e = launch_zgemm(G_BH, dims, ptrs, batch, cap, st)) != cudaSuccess) return e;
   if ((e = launch_qr_sized(QR_BH, dims, ptrs, batch, cap, st)) != cudaSuccess) return e;
-  if ((e = launch_jacobi(dims, ptrs, batch, status, st)) != cudaSuccess) return e;
+  if ((e = launch_jacobi_sized(dims, ptrs, batch, cap, status, st)) != cudaSuccess) return e;
   if ((e = launch_zgemm(G_U, dims, ptrs, batch, cap, st)) != cudaSuccess) return e;
   if ((e = launch_zgemm(G_V, dims, ptrs, batch, cap, st)) != cudaSuccess) return e;
   return launch_frob2(dims, ptrs, batch, st);

@@ -736,16 +736,16 @@ cudaError_t run_rrsvd(const Dims* dims, const ProbPtr* ptrs, int batch, const Ca
   auto T = [&](int stage) { return tiles ? tiles[stage] : 0; };
   TG_TRY(launch_omega(dims, ptrs, batch, cap, seed, sweep, chain0, chain_stride, st, sweep_dev));
   TG_TRY(launch_zgemm_tile(G_Y0, T(G_Y0), dims, ptrs, batch, cap, st));  // Y0 = A Omega
-  TG_TRY(launch_qr_sized(QR_Y, dims, ptrs, batch, cap, st));                    // Y0 = Q0 R0
+  TG_TRY(launch_qr_sized(QR_Y, dims, ptrs, batch, cap, st));              // Y0 = Q0 R0
   for (int j = 0; j < q; ++j) {
     TG_TRY(launch_zgemm_tile(G_YT, T(G_YT), dims, ptrs, batch, cap, st)); // Y~ = A^H Q
-    TG_TRY(launch_qr_sized(QR_YT, dims, ptrs, batch, cap, st));                 // Y~ = Q~ R~
+    TG_TRY(launch_qr_sized(QR_YT, dims, ptrs, batch, cap, st));           // Y~ = Q~ R~
     TG_TRY(launch_zgemm_tile(G_Y, T(G_Y), dims, ptrs, batch, cap, st));   // Y = A Q~
-    TG_TRY(launch_qr_sized(QR_Y, dims, ptrs, batch, cap, st));                  // Y = Q R
+    TG_TRY(launch_qr_sized(QR_Y, dims, ptrs, batch, cap, st));            // Y = Q R
   }
   TG_TRY(launch_zgemm_tile(G_BH, T(G_BH), dims, ptrs, batch, cap, st));   // B^H = A^H Q
-  TG_TRY(launch_qr_sized(QR_BH, dims, ptrs, batch, cap, st));                   // B^H = Qb Rb
-  TG_TRY(launch_jacobi(dims, ptrs, batch, status, st));                    // Rb^H J = W S
+  TG_TRY(launch_qr_sized(QR_BH, dims, ptrs, batch, cap, st));             // B^H = Qb Rb
+  TG_TRY(launch_jacobi_sized(dims, ptrs, batch, cap, status, st));        // Rb^H J = W S
   TG_TRY(launch_zgemm_tile(G_U, T(G_U), dims, ptrs, batch, cap, st));     // U = Q J_k
   TG_TRY(launch_zgemm_tile(G_V, T(G_V), dims, ptrs, batch, cap, st));     // V = Qb W_k  (stored as V^H)
   TG_TRY(launch_frob2(dims, ptrs, batch, st));

@@ -592,7 +592,7 @@ cudaError_t run_rrsvd_mixed(const Dims* dims, const ProbPtr* ptrs, int batch, co
     MX_TRY(launch_zgemm_df(G_BH, dims, ptrs, batch, cap, st));  // B^H = A^H Q (double-float)
   }
   MX_TRY(launch_qr_sized(QR_BH, dims, ptrs, batch, cap, st));
-  MX_TRY(launch_jacobi(dims, ptrs, batch, status, st));
+  MX_TRY(launch_jacobi_sized(dims, ptrs, batch, cap, status, st));
   MX_TRY(launch_zgemm_df(G_U, dims, ptrs, batch, cap, st));
   MX_TRY(launch_zgemm_df(G_V, dims, ptrs, batch, cap, st));
   return cudaSuccess;
