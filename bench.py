@@ -55,6 +55,8 @@ def parse_args():
     ap.add_argument("--no-spin-boson", action="store_true")
     ap.add_argument("--spin-boson-only", action="store_true",
                     help="run only the spin-boson chain measurement (for kernel launch lists)")
+    ap.add_argument("--sb-size", default="100,32,4,256,64",
+                    help="spin-boson chain: bosons, first and last local dimension, first and last bond cap")
     return ap.parse_args()
 
 
@@ -273,17 +275,27 @@ def measure(B, torch, dev, theta, sig, batch, prec, args, rank, world, local):
             "clocks": clocks, "sig_err": sig_err, "excess_err": float(excess), "k": k, "l": l}
 
 
-def e2e_measure(B, torch, theta, batch, code, args, rank, world):
-    """Through the host-buffer entry point: pinned host theta in, results out,
-    copies inside the timed region."""
+def e2e_host_buffers(torch, batch, pool):
+    """Pinned host buffers of the end-to-end measurement, allocated before any
+    device memory (as a serving process would set up its staging once); the
+    host theta is written by the CPU from the pool of distinct matrices."""
     k = min(K_MAX, M, N_)
     th_h = torch.empty((batch, M, N_), dtype=torch.complex128, pin_memory=True)
-    th_h.copy_(theta)
-    sg_h = torch.empty((batch, k), dtype=torch.float64, pin_memory=True)
-    U_h = torch.empty((batch, M, k), dtype=torch.complex128, pin_memory=True)
-    Vh_h = torch.empty((batch, k, N_), dtype=torch.complex128, pin_memory=True)
-    w_h = torch.empty(batch, dtype=torch.float64, pin_memory=True)
-    rk_h = torch.empty(batch, dtype=torch.int32, pin_memory=True)
+    th_np = th_h.numpy()
+    for t in range(batch):
+        th_np[t] = pool[t % len(pool)]
+    return {"theta": th_h,
+            "sigma": torch.empty((batch, k), dtype=torch.float64, pin_memory=True),
+            "U": torch.empty((batch, M, k), dtype=torch.complex128, pin_memory=True),
+            "Vh": torch.empty((batch, k, N_), dtype=torch.complex128, pin_memory=True),
+            "w": torch.empty(batch, dtype=torch.float64, pin_memory=True),
+            "rank": torch.empty(batch, dtype=torch.int32, pin_memory=True)}
+
+
+def e2e_measure(B, torch, theta, batch, code, args, rank, world, host):
+    """Through the host-buffer entry point: pinned host theta in, results out,
+    copies inside the timed region."""
+    th_h, sg_h, U_h, Vh_h, w_h, rk_h = (host[x] for x in ("theta", "sigma", "U", "Vh", "w", "rank"))
     sp = torch.cuda.current_stream().cuda_stream
     inst0 = replica_offset(rank) + 5_000_000
     hp = B.rrsvd_plan_create(M, N_, K_MAX, P_OS, Q_PI, batch, code, SEED)
@@ -472,7 +484,7 @@ def run_tebd_many(B, I, torch, n_chains=256, steps=10, warm=2, unbatched_chains=
                         "dt=0.01, p=10, q=1, Neel; graphs + 16 GB wave budget, after %d warm-up steps" % warm}
 
 
-def run_tebd_spin_boson(B, I, torch, steps=1, warm=1):
+def run_tebd_spin_boson(B, I, torch, steps=1, warm=1, size=(100, 32, 4, 256, 64)):
     """Spin-boson chain in star-to-chain form: a spin and 100 bosonic sites
     whose local dimension falls from 32 to 4, couplings 1/(1+n), per-bond
     caps falling from 256 to 64, from a canonical random MPS at the caps
@@ -480,7 +492,7 @@ def run_tebd_spin_boson(B, I, torch, steps=1, warm=1):
     QRs, FP64-accurate projection, FP64 small SVD), all bonds of a parity per
     launch sequence replayed from CUDA graphs, 40 GB wave budget.  One
     second-order step = even, odd, even sweep."""
-    dims, caps = I.spin_boson_sizes(100, 32, 4, 256, 64)
+    dims, caps = I.spin_boson_sizes(*size)
     g0, lam0 = I.random_canonical_mps(dims, caps, 0)
     hs = I.spin_boson_bond_terms(dims)
     dt, p, q = 0.05, 10, 2
@@ -503,9 +515,9 @@ def run_tebd_spin_boson(B, I, torch, steps=1, warm=1):
     sim.close()
     return {"value": upd / el, "unit": "bond updates/s", "seconds_per_step": el / steps, "steps_timed": steps,
             "precision": "tf32 (mixed form)", "discarded_weight": float(w[0]), "workspace": info,
-            "workload": "spin-boson chain: spin + 100 bosons, d 32 -> 4, chi caps 256 -> 64, dt=0.05, p=10, q=2, "
+            "workload": "spin-boson chain: spin + %d bosons, d %d -> %d, chi caps %d -> %d, dt=0.05, p=10, q=2, "
                         "canonical random MPS at the caps (seed 0); graphs, 40 GB wave budget, after %d warm-up "
-                        "step(s)" % warm}
+                        "step(s)" % (tuple(size) + (warm,))}
 
 
 def run_tebd_gradient(B, I, torch):
@@ -567,11 +579,13 @@ def main():
     from paper_1504_00992_gb300 import inputs as I
     if args.spin_boson_only:
         if rank == 0:
-            print(json.dumps({"tebd_spin_boson": run_tebd_spin_boson(B, I, torch)}), flush=True)
+            size = tuple(int(x) for x in args.sb_size.split(","))
+            print(json.dumps({"tebd_spin_boson": run_tebd_spin_boson(B, I, torch, size=size)}), flush=True)
         return
 
     batch = args.batch
     pool, sig = synthetic_pool(POOL)
+    host = e2e_host_buffers(torch, batch, pool) if args.e2e_steps > 0 else None
     theta = torch.empty((batch, M, N_), dtype=torch.complex128, device=dev)
     pool_dev = torch.from_numpy(pool).to(dev)
     for t in range(batch):
@@ -582,7 +596,7 @@ def main():
     # headline: the fastest form that meets the 1e-8 truncation-accuracy bar
     ok = [r for r in results.values() if r["sig_err"] <= 1e-8 and r["excess_err"] <= 1e-8]
     head = max(ok or list(results.values()), key=lambda r: r["value"])
-    e2e = e2e_measure(B, torch, theta, batch, head["code"], args, rank, world) if args.e2e_steps > 0 else None
+    e2e = e2e_measure(B, torch, theta, batch, head["code"], args, rank, world, host) if args.e2e_steps > 0 else None
     roof = roofline(head, batch)
     prof = head["prof"]
     shares = {kk: {"ms": v[0], "launches": v[1]} for kk, v in sorted(prof.items(), key=lambda x: -x[1][0])}

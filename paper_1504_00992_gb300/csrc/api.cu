@@ -1315,15 +1315,21 @@ extern "C" int rrsvd_execute_host(rrsvd_plan_t P, const double* theta, int64_t c
   int* d_r = (int*)(s + th + sg + uu + vv + ww);
   void* d_ws = s + th + sg + uu + vv + ww + rr;
   cudaStream_t st = (cudaStream_t)stream;
-  CU_OR(P, cudaMemcpyAsync(d_th, theta, c * (size_t)P->m * P->n * B, cudaMemcpyHostToDevice, st));
+  {
+    ProfScope ps("copy[h2d]", st);
+    CU_OR(P, cudaMemcpyAsync(d_th, theta, c * (size_t)P->m * P->n * B, cudaMemcpyHostToDevice, st));
+  }
   int rc = rrsvd_execute(P, d_th, chain0, d_sg, U ? d_u : nullptr, Vh ? d_v : nullptr, w ? d_w : nullptr,
                          rank ? d_r : nullptr, d_ws, P->ws_bytes, stream);
   if (rc) return rc;
-  CU_OR(P, cudaMemcpyAsync(sigma, d_sg, sizeof(double) * P->k * B, cudaMemcpyDeviceToHost, st));
-  if (U) CU_OR(P, cudaMemcpyAsync(U, d_u, c * (size_t)P->m * P->k * B, cudaMemcpyDeviceToHost, st));
-  if (Vh) CU_OR(P, cudaMemcpyAsync(Vh, d_v, c * (size_t)P->k * P->n * B, cudaMemcpyDeviceToHost, st));
-  if (w) CU_OR(P, cudaMemcpyAsync(w, d_w, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
-  if (rank) CU_OR(P, cudaMemcpyAsync(rank, d_r, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
+  {
+    ProfScope ps("copy[d2h]", st);
+    CU_OR(P, cudaMemcpyAsync(sigma, d_sg, sizeof(double) * P->k * B, cudaMemcpyDeviceToHost, st));
+    if (U) CU_OR(P, cudaMemcpyAsync(U, d_u, c * (size_t)P->m * P->k * B, cudaMemcpyDeviceToHost, st));
+    if (Vh) CU_OR(P, cudaMemcpyAsync(Vh, d_v, c * (size_t)P->k * P->n * B, cudaMemcpyDeviceToHost, st));
+    if (w) CU_OR(P, cudaMemcpyAsync(w, d_w, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
+    if (rank) CU_OR(P, cudaMemcpyAsync(rank, d_r, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
+  }
   int stv = 0, tce = 0;
   CU_OR(P, cudaMemcpyAsync(&stv, P->status, sizeof(int), cudaMemcpyDeviceToHost, st));
   CU_OR(P, cudaMemcpyAsync(&tce, P->tcerr, sizeof(int), cudaMemcpyDeviceToHost, st));

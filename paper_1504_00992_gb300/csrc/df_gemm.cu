@@ -10,7 +10,8 @@
 //       sum_{i'j'} G[(i dr + j), (i' dr + j')] C[(i' cl + a), (j' cr + c)],
 //     rows (i, j) of G times the (d_l d_r) x (cl cr) gather of C.
 // Both: operands split at staging into FP32 pairs (integer bit operations;
-// the lambda weights multiply in FP64 first), complex products by Gauss's
+// lam_m multiplies Gamma_r in FP64 first, lam_l lam_r scale the FP64 result
+// in the epilogue), complex products by Gauss's
 // rule with three double-float products (for alpha = a + ib, beta = c + id:
 // t1 = a (c + d), t2 = d (a + b), t3 = c (b - a), Re = t1 - t2,
 // Im = t1 + t3), 64 x 32 output tiles, 4 x 2 outputs per thread, K in slices
@@ -26,17 +27,25 @@ namespace tg {
 
 enum { DG_TM = 64, DG_TN = 32, DG_TK = 16 };
 
+// Operand access.  Each thread stages the same rows of A and the same column
+// of B in every K slice, so the index arithmetic of a row or column is done
+// once: A rows are contiguous in k (a_row), B columns are addressed from a
+// per-column base (b_col) plus a per-k offset (b_at).
+
 // Operands of the gate GEMM (bonds with Cpre set).
 struct DgGate {
   __device__ static int rows(const Dims& D) { return D.dl * D.dr; }
   __device__ static int cols(const Dims& D) { return D.cl * D.cr; }
   __device__ static int depth(const Dims& D) { return D.dl * D.dr; }
-  __device__ static cplx a(const Dims& D, const ProbPtr& P, int r, int k) {
-    return P.gate[(int64_t)r * (D.dl * D.dr) + k];
+  __device__ static const cplx* a_row(const Dims& D, const ProbPtr& P, int r) {
+    return P.gate + (int64_t)r * (D.dl * D.dr);
   }
-  __device__ static cplx b(const Dims& D, const ProbPtr& P, int k, int c) {
-    const int ip = k / D.dr, jp = k % D.dr, al = c / D.cr, be = c % D.cr;
-    return P.Cpre[(int64_t)(ip * D.cl + al) * D.n + jp * D.cr + be];
+  __device__ static int64_t b_col(const Dims& D, const ProbPtr& P, int c) {
+    return (int64_t)(c / D.cr) * D.n + c % D.cr;  // (alpha, beta) -> alpha n + beta
+  }
+  __device__ static cplx b_at(const Dims& D, const ProbPtr& P, int64_t cb, int k) {
+    const int ip = k / D.dr, jp = k - ip * D.dr;  // k = (i', j')
+    return P.Cpre[cb + (int64_t)ip * D.cl * D.n + jp * D.cr];
   }
   __device__ static void store(const Dims& D, const ProbPtr& P, int r, int c, cplx v) {
     const int i = r / D.dr, j = r % D.dr, al = c / D.cr, be = c % D.cr;
@@ -44,21 +53,26 @@ struct DgGate {
   }
 };
 
-// Operands of the theta contraction into Cpre.
+// Operands of the theta contraction into Cpre: A = Gamma_l (rows (i, alpha)),
+// B = lam_m Gamma_r (columns (j, beta)); lam_l[alpha] lam_r[beta] scale the
+// result in the epilogue.
 struct DgTheta {
   __device__ static int rows(const Dims& D) { return D.dl * D.cl; }
   __device__ static int cols(const Dims& D) { return D.dr * D.cr; }
   __device__ static int depth(const Dims& D) { return D.cm; }
-  __device__ static cplx a(const Dims& D, const ProbPtr& P, int r, int g) {
-    const int i = r / D.cl, al = r % D.cl;
-    return cscale(P.gl[((int64_t)i * P.cap_l + al) * P.cap_m + g], P.laml[al] * P.lamm[g]);
+  __device__ static const cplx* a_row(const Dims& D, const ProbPtr& P, int r) {
+    const int i = r / D.cl, al = r - i * D.cl;
+    return P.gl + ((int64_t)i * P.cap_l + al) * P.cap_m;
   }
-  __device__ static cplx b(const Dims& D, const ProbPtr& P, int g, int c) {
-    const int j = c / D.cr, be = c % D.cr;
-    return cscale(P.gr[((int64_t)j * P.cap_m + g) * P.cap_r + be], P.lamr[be]);
+  __device__ static int64_t b_col(const Dims& D, const ProbPtr& P, int c) {
+    const int j = c / D.cr, be = c - j * D.cr;
+    return (int64_t)j * P.cap_m * P.cap_r + be;
+  }
+  __device__ static cplx b_at(const Dims& D, const ProbPtr& P, int64_t cb, int g) {
+    return cscale(P.gr[cb + (int64_t)g * P.cap_r], P.lamm[g]);
   }
   __device__ static void store(const Dims& D, const ProbPtr& P, int r, int c, cplx v) {
-    P.Cpre[(int64_t)r * D.n + c] = v;
+    P.Cpre[(int64_t)r * D.n + c] = cscale(v, P.laml[r % D.cl] * P.lamr[c % D.cr]);
   }
 };
 
@@ -77,38 +91,50 @@ __global__ void __launch_bounds__(256) k_cgemm_df(const Dims* __restrict__ dims,
   const int tm = blockIdx.y * DG_TM, tn = blockIdx.x * DG_TN;
   if (tm >= M || tn >= N) return;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  // staging assignment: A elements (kk = tid % 16, rows tid / 16 + 16 t),
+  // B elements (column tid % 32, kk = tid / 32 + 8 t)
+  constexpr int AT = DG_TM * DG_TK / 256, BT = DG_TK * DG_TN / 256;
+  const int akk = tid % DG_TK, bc = tid % DG_TN;
+  const cplx* arow[AT];
+#pragma unroll
+  for (int t = 0; t < AT; ++t) {
+    const int gr = tm + tid / DG_TK + (256 / DG_TK) * t;
+    arow[t] = (gr < M) ? Op::a_row(D, P, gr) : nullptr;
+  }
+  const int gn = tn + bc;
+  const int64_t bcol = (gn < N) ? Op::b_col(D, P, gn) : 0;
   float h1[4][2], l1[4][2], h2[4][2], l2[4][2], h3[4][2], l3[4][2];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 2; ++j) h1[i][j] = l1[i][j] = h2[i][j] = l2[i][j] = h3[i][j] = l3[i][j] = 0.f;
   for (int k0 = 0; k0 < K; k0 += DG_TK) {
-    for (int e = tid; e < DG_TM * DG_TK; e += 256) {  // A tile: consecutive threads along k
-      const int kk = e % DG_TK, r = e / DG_TK;
-      const int gr = tm + r, gk = k0 + kk;
+#pragma unroll
+    for (int t = 0; t < AT; ++t) {  // A tile: consecutive threads along k
+      const int r = tid / DG_TK + (256 / DG_TK) * t, gk = k0 + akk;
       cplx v = cmk(0.0, 0.0);
-      if (gr < M && gk < K) v = Op::a(D, P, gr, gk);
+      if (arow[t] && gk < K) v = arow[t][gk];
       float ah, al, bh, bl;
       split_bits(v.x, ah, al);
       split_bits(v.y, bh, bl);
       float sh, se, dh, de;
       two_sum(ah, bh, sh, se);
       two_sum(bh, -ah, dh, de);
-      Aab[kk][r] = make_float4(ah, al, bh, bl);
-      Asd[kk][r] = make_float4(sh, se + (al + bl), dh, de + (bl - al));
+      Aab[akk][r] = make_float4(ah, al, bh, bl);
+      Asd[akk][r] = make_float4(sh, se + (al + bl), dh, de + (bl - al));
     }
-    for (int e = tid; e < DG_TK * DG_TN; e += 256) {  // B tile: consecutive threads along the columns
-      const int c = e % DG_TN, kk = e / DG_TN;
-      const int gn = tn + c, gk = k0 + kk;
+#pragma unroll
+    for (int t = 0; t < BT; ++t) {  // B tile: consecutive threads along the columns
+      const int kk = tid / DG_TN + (256 / DG_TN) * t, gk = k0 + kk;
       cplx v = cmk(0.0, 0.0);
-      if (gn < N && gk < K) v = Op::b(D, P, gk, gn);
+      if (gn < N && gk < K) v = Op::b_at(D, P, bcol, gk);
       float ch, clo, dh, dlo;
       split_bits(v.x, ch, clo);
       split_bits(v.y, dh, dlo);
       float sh, se;
       two_sum(ch, dh, sh, se);
-      Bcd[kk][c] = make_float4(ch, clo, dh, dlo);
-      Bsum[kk][c] = make_float2(sh, se + (clo + dlo));
+      Bcd[kk][bc] = make_float4(ch, clo, dh, dlo);
+      Bsum[kk][bc] = make_float2(sh, se + (clo + dlo));
     }
     __syncthreads();
 #pragma unroll 2

@@ -9,7 +9,7 @@
 //   last QR                                : FP32 blocked Householder and an
 //                                           FP64-accurate re-orthonormalisation
 //                                           (qr_blocked.cu), or FP64 Householder
-//                                           when l > 128;
+//                                           when l > 512 or m < l;
 //   B^H = A^H Q, U = Q J_k, V = Qb W_k      : double-float GEMM on the FP32 pipes
 //                                           (FP32 pairs, ~1e-14 relative);
 //   QR of B^H, Jacobi SVD                   : FP64 (the existing kernels).

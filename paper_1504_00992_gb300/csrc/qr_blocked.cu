@@ -715,6 +715,168 @@ static cudaError_t launch_fold(const float2* Qf, const float2* Dbuf, const Dims*
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// The same steps for bases wider than QF_MAXL (D no longer fits in shared
+// memory next to the rows), up to QF_MAXL_BIG columns.
+// k_lowdin_big: D = -E/2 + 3 E^2 / 8 in 32 x 32 tiles over a grid (E read from
+// its upper triangle in FP64 and staged as FP32, 32-deep K slices).
+// k_fold_big: one CTA per 32 rows holding its rows of X (all L columns, FP32)
+// in shared memory; each warp computes 16 output columns at a time with D
+// read through L1 (every lane of a warp reads the same D element).  Out of
+// place for Q; for B^H the rows are staged before any is overwritten, and a
+// CTA owns whole rows, so the in-place update is safe.
+// ---------------------------------------------------------------------------
+enum { QF_MAXL_BIG = 512, QFB_ROWS = 32, QFB_CW = 16 };
+
+__device__ __forceinline__ cplx herm_get(const cplx* E, int L, int a, int b) {
+  return (a <= b) ? E[(size_t)b * L + a] : cconj(E[(size_t)a * L + b]);
+}
+
+__global__ void __launch_bounds__(256) k_lowdin_big(const Dims* __restrict__ dims, const ProbPtr* __restrict__ ptrs,
+                                                    float2* Dbase, int Lc, int* status) {
+  constexpr int T = 32;
+  __shared__ float2 Ea[T][T + 1];  // E[a0 + i][k0 + kk] at [kk][i]
+  __shared__ float2 Eb[T][T + 1];  // E[k0 + kk][b0 + j] at [kk][j]
+  const int z = blockIdx.y;
+  const Dims Dm = dims[z];
+  if (!Dm.active) return;
+  const int L = Dm.l;
+  const int nt = (Lc + T - 1) / T;
+  const int a0 = (blockIdx.x / nt) * T, b0 = (blockIdx.x % nt) * T;
+  if (a0 >= L || b0 >= L) return;
+  const cplx* E = ptrs[z].R;
+  float2* D = Dbase + (size_t)z * Lc * Lc;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  float2 acc[2][2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) acc[i][j] = make_float2(0.f, 0.f);
+  int bad = 0;
+  for (int k0 = 0; k0 < L; k0 += T) {
+    for (int e = tid; e < T * T; e += 256) {
+      const int kk = e % T, i = e / T;
+      float2 va = make_float2(0.f, 0.f), vb = make_float2(0.f, 0.f);
+      if (a0 + i < L && k0 + kk < L) {
+        const cplx x = herm_get(E, L, a0 + i, k0 + kk);
+        va = make_float2((float)x.x, (float)x.y);
+        bad |= !(fmaxf(fabsf(va.x), fabsf(va.y)) <= 1e-3f);
+      }
+      if (k0 + kk < L && b0 + i < L) {
+        const cplx x = herm_get(E, L, k0 + kk, b0 + i);
+        vb = make_float2((float)x.x, (float)x.y);
+      }
+      Ea[kk][i] = va;
+      Eb[kk][i] = vb;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < T; ++kk) {
+      const float2 x0 = Ea[kk][ty], x1 = Ea[kk][ty + 16];
+      const float2 y0 = Eb[kk][tx], y1 = Eb[kk][tx + 16];
+      const float2 xs[2] = {x0, x1}, ys[2] = {y0, y1};
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          acc[i][j].x = fmaf(xs[i].x, ys[j].x, fmaf(-xs[i].y, ys[j].y, acc[i][j].x));
+          acc[i][j].y = fmaf(xs[i].x, ys[j].y, fmaf(xs[i].y, ys[j].x, acc[i][j].y));
+        }
+    }
+    __syncthreads();
+  }
+  if (__syncthreads_or(bad) && tid == 0) atomicOr(status, 4);  // E not small, or not finite
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int a = a0 + ty + 16 * i, b = b0 + tx + 16 * j;
+      if (a < L && b < L) {
+        const cplx ex = herm_get(E, L, a, b);
+        D[(size_t)b * L + a] = make_float2(-0.5f * (float)ex.x + 0.375f * acc[i][j].x,
+                                           -0.5f * (float)ex.y + 0.375f * acc[i][j].y);
+      }
+    }
+}
+
+template <bool FROM_F32>
+__global__ void __launch_bounds__(256) k_fold_big(const float2* __restrict__ Qf, const float2* __restrict__ Dbase,
+                                                  const Dims* __restrict__ dims, const ProbPtr* __restrict__ ptrs,
+                                                  int Mc, int Lc) {
+  extern __shared__ __align__(16) unsigned char qfb_raw[];
+  const int z = blockIdx.y;
+  const Dims Dm = dims[z];
+  if (!Dm.active) return;
+  const int M = FROM_F32 ? Dm.m : Dm.n, L = Dm.l;
+  const int r0 = blockIdx.x * QFB_ROWS;
+  if (r0 >= M) return;
+  float2* Xs = reinterpret_cast<float2*>(qfb_raw);  // QFB_ROWS x L column-major
+  const float2* q = FROM_F32 ? Qf + (size_t)z * Mc * Lc : nullptr;
+  cplx* X = FROM_F32 ? ptrs[z].Q : ptrs[z].Yt;  // output (and FP64 source when !FROM_F32), ld M
+  const float2* D = Dbase + (size_t)z * Lc * Lc;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int e = tid; e < QFB_ROWS * L; e += 256) {
+    const int c = e / QFB_ROWS, r = e % QFB_ROWS;
+    float2 v = make_float2(0.f, 0.f);
+    if (r0 + r < M) {
+      if (FROM_F32) {
+        v = q[(size_t)c * Mc + r0 + r];
+      } else {
+        const cplx x = X[(size_t)c * M + r0 + r];
+        v = make_float2((float)x.x, (float)x.y);
+      }
+    }
+    Xs[e] = v;
+  }
+  __syncthreads();
+  const int r = r0 + lane;
+  for (int cb = warp * QFB_CW; cb < L; cb += 8 * QFB_CW) {
+    float2 acc[QFB_CW];
+#pragma unroll
+    for (int j = 0; j < QFB_CW; ++j) acc[j] = make_float2(0.f, 0.f);
+    for (int k = 0; k < L; ++k) {
+      const float2 x = Xs[k * QFB_ROWS + lane];
+#pragma unroll
+      for (int j = 0; j < QFB_CW; ++j) {
+        if (cb + j < L) {
+          const float2 d = __ldg(&D[(size_t)(cb + j) * L + k]);
+          acc[j].x = fmaf(x.x, d.x, fmaf(-x.y, d.y, acc[j].x));
+          acc[j].y = fmaf(x.x, d.y, fmaf(x.y, d.x, acc[j].y));
+        }
+      }
+    }
+    if (r < M) {
+#pragma unroll
+      for (int j = 0; j < QFB_CW; ++j) {
+        const int c = cb + j;
+        if (c < L) {
+          cplx b;
+          if (FROM_F32) {
+            const float2 f = Xs[c * QFB_ROWS + lane];
+            b = cmk((double)f.x, (double)f.y);
+          } else {
+            b = X[(size_t)c * M + r];
+          }
+          X[(size_t)c * M + r] = cmk(b.x + (double)acc[j].x, b.y + (double)acc[j].y);
+        }
+      }
+    }
+  }
+}
+
+static size_t g_attr_foldbig[2] = {0, 0};
+
+// batch == 0 only raises the shared-memory limit.
+template <bool FROM_F32>
+static cudaError_t launch_fold_big(const float2* Qf, const float2* Dbuf, const Dims* dims, const ProbPtr* ptrs, int Mc,
+                                   int Lc, int batch, cudaStream_t st) {
+  const size_t sm = sizeof(float2) * (size_t)QFB_ROWS * Lc;
+  cudaError_t e = ensure_smem(k_fold_big<FROM_F32>, sm, &g_attr_foldbig[FROM_F32]);
+  if (e != cudaSuccess || batch == 0) return e;
+  k_fold_big<FROM_F32><<<dim3((Mc + QFB_ROWS - 1) / QFB_ROWS, batch), 256, sm, st>>>(Qf, Dbuf, dims, ptrs, Mc, Lc);
+  return cudaGetLastError();
+}
+
 // Raises the dynamic shared-memory limits the blocked QR, the Loewdin step
 // and the folds need for capacities (M, N, L), outside any stream capture.
 cudaError_t qr_blocked_prepare(int M, int N, int L) {
@@ -725,17 +887,17 @@ cudaError_t qr_blocked_prepare(int M, int N, int L) {
     e = ensure_smem(k_lowdin, sizeof(float2) * (size_t)L * L, &g_attr_ld);
     if (e == cudaSuccess) e = launch_fold<true>(nullptr, nullptr, nullptr, nullptr, M, L, 0, nullptr);
     if (e == cudaSuccess) e = launch_fold<false>(nullptr, nullptr, nullptr, nullptr, N, L, 0, nullptr);
+  } else if (e == cudaSuccess && L <= QF_MAXL_BIG) {
+    e = launch_fold_big<true>(nullptr, nullptr, nullptr, nullptr, M, L, 0, nullptr);
+    if (e == cudaSuccess) e = launch_fold_big<false>(nullptr, nullptr, nullptr, nullptr, N, L, 0, nullptr);
   }
   return e;
 }
 
-bool reorth_fits(int M, int L) { return M >= L && L <= QF_MAXL; }  // shared memory of k_lowdin and k_fold
+bool reorth_fits(int M, int L) { return M >= L && L <= QF_MAXL_BIG; }
 
 cudaError_t launch_reorth(const float2* Qf, float2* Dbuf, const Dims* dims, const ProbPtr* ptrs, int M, int L,
                           int batch, int* status, cudaStream_t st) {
-  const size_t sm_l = sizeof(float2) * (size_t)L * L;
-  cudaError_t e0 = ensure_smem(k_lowdin, sm_l, &g_attr_ld);
-  if (e0 != cudaSuccess) return e0;
   const int nt = (L + 31) / 32;
   {
     ProfScope ps("k_gram_df", st);
@@ -743,6 +905,19 @@ cudaError_t launch_reorth(const float2* Qf, float2* Dbuf, const Dims* dims, cons
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
+  if (L > QF_MAXL) {
+    {
+      ProfScope ps("k_lowdin", st);
+      k_lowdin_big<<<dim3(nt * nt, batch), 256, 0, st>>>(dims, ptrs, Dbuf, L, status);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+    ProfScope ps("k_fold[q]", st);
+    return launch_fold_big<true>(Qf, Dbuf, dims, ptrs, M, L, batch, st);
+  }
+  const size_t sm_l = sizeof(float2) * (size_t)L * L;
+  cudaError_t e0 = ensure_smem(k_lowdin, sm_l, &g_attr_ld);
+  if (e0 != cudaSuccess) return e0;
   {
     ProfScope ps("k_lowdin", st);
     k_lowdin<<<batch, 512, sm_l, st>>>(dims, ptrs, Dbuf, L, status);
@@ -757,6 +932,7 @@ cudaError_t launch_reorth(const float2* Qf, float2* Dbuf, const Dims* dims, cons
 cudaError_t launch_fold_bh(const float2* Dbuf, const Dims* dims, const ProbPtr* ptrs, int n, int l, int batch,
                            cudaStream_t st) {
   ProfScope ps("k_fold[bh]", st);
+  if (l > QF_MAXL) return launch_fold_big<false>(nullptr, Dbuf, dims, ptrs, n, l, batch, st);
   return launch_fold<false>(nullptr, Dbuf, dims, ptrs, n, l, batch, st);
 }
 

@@ -199,6 +199,8 @@ __global__ void __launch_bounds__(QM_PT) qm_panel(Src src, int j0) {
   __shared__ R red[32];
   __shared__ R tau_s;
   __shared__ Tc vsc;
+  __shared__ R pred[QM_PT / 32][2 * (QM_NB - 1)];
+  __shared__ R sdv[2 * (QM_NB - 1)];
   QmView<Tc> v;
   if (!src.get(blockIdx.x, v)) return;
   const int M = v.M, L = v.L;
@@ -259,7 +261,9 @@ __global__ void __launch_bounds__(QM_PT) qm_panel(Src src, int j0) {
       for (int r = j + 1 + tid; r < M; r += blockDim.x) aj[r] = qm_mul(aj[r], sc);
       __syncthreads();
     }
-    if (t != 0) {
+    const int nc = j0 + jb - j - 1;  // panel columns right of j (uniform)
+    if (!F32 && t != 0) {
+      // FP64: the FP64 pipe bounds the panel; one warp per column
       for (int c = j + 1 + warp; c < j0 + jb; c += nw) {
         Tc* ac = v.A + (int64_t)c * M;
         Tc sd = qm_c<Tc>(0, 0);
@@ -267,6 +271,47 @@ __global__ void __launch_bounds__(QM_PT) qm_panel(Src src, int j0) {
         sd.x = qm_wsum(sd.x) * t;
         sd.y = qm_wsum(sd.y) * t;
         for (int r = j + lane; r < M; r += 32) qm_fms(ac[r], aj[r], sd);
+      }
+    }
+    if (F32 && t != 0 && nc > 0) {
+      // FP32: latency bounds the panel; all threads over the rows: partial
+      // v_j^H a_c for the nc columns, reduced over the block, then
+      // a_c -= tau v_j (v_j^H a_c)
+      Tc* a1 = aj + M;  // column j + 1
+      Tc dp[QM_NB - 1];
+#pragma unroll
+      for (int q = 0; q < QM_NB - 1; ++q) dp[q] = qm_c<Tc>(0, 0);
+      for (int r = j + tid; r < M; r += blockDim.x) {
+        const Tc x = aj[r];
+#pragma unroll
+        for (int q = 0; q < QM_NB - 1; ++q)
+          if (q < nc) qm_fmac(dp[q], x, a1[(int64_t)q * M + r]);
+      }
+#pragma unroll
+      for (int q = 0; q < QM_NB - 1; ++q) {
+        if (q < nc) {  // uniform
+          const R sx = qm_wsum(dp[q].x), sy = qm_wsum(dp[q].y);
+          if (lane == 0) {
+            pred[warp][2 * q] = sx;
+            pred[warp][2 * q + 1] = sy;
+          }
+        }
+      }
+      __syncthreads();
+      if (tid < 2 * nc) {
+        R acc = 0;
+        for (int w = 0; w < nw; ++w) acc += pred[w][tid];
+        sdv[tid] = acc * t;
+      }
+      __syncthreads();
+      Tc sd[QM_NB - 1];
+#pragma unroll
+      for (int q = 0; q < QM_NB - 1; ++q) sd[q] = (q < nc) ? qm_c<Tc>(sdv[2 * q], sdv[2 * q + 1]) : qm_c<Tc>(0, 0);
+      for (int r = j + tid; r < M; r += blockDim.x) {
+        const Tc x = aj[r];
+#pragma unroll
+        for (int q = 0; q < QM_NB - 1; ++q)
+          if (q < nc) qm_fms(a1[(int64_t)q * M + r], x, sd[q]);
       }
     }
     __syncthreads();

@@ -1,7 +1,7 @@
 """The mixed-precision RRSVD form (TEBD_PREC_TF32): TF32 tensor-core sketch
 and power iterations with FP32 Householder QRs, 3xTF32 refinement of the last
 power round, an FP64-accurate re-orthonormalisation of the last Q (FP64
-Householder when l > 128), double-float projection and FP64 small SVD.
+Householder when l > 512), double-float projection and FP64 small SVD.
 
 Its stated tolerances: with Omega rounded to TF32 and the sketch in TF32 the
 mixed form is a different (equally valid) randomized truncation than the FP64
@@ -31,9 +31,9 @@ SEED = 4321
     (300, 200, 40, 10, 1, 8.0),    # ragged: no size is a multiple of 128 / 32
     (130, 70, 20, 6, 0, 4.0),      # q = 0: the sketch itself is the refinement pass
     (96, 96, 24, 8, 2, 5.0),
-    (400, 360, 120, 20, 1, 30.0),  # l = 140 > 128: FP64 last QR
+    (400, 360, 120, 20, 1, 30.0),  # l = 140: the widest correction held in shared memory
     (3700, 200, 20, 10, 1, 6.0),   # Y too tall for the blocked FP32 QR: unblocked fallback
-    (1200, 400, 140, 20, 1, 12.0), # l = 160: FP64 last QR spread over many CTAs per instance
+    (1200, 400, 140, 20, 1, 12.0), # l = 160: correction read through L1 (tiled Loewdin and fold)
     (3700, 300, 30, 10, 1, 6.0),   # Y too tall for the blocked FP32 QR, l = 40: FP32 QR over many CTAs
 ])
 def test_mixed_form_meets_its_tolerances(lib, m, n, k, p, q, scale):
