@@ -57,6 +57,8 @@ def parse_args():
                     help="run only the spin-boson chain measurement (for kernel launch lists)")
     ap.add_argument("--sb-size", default="100,32,4,256,64",
                     help="spin-boson chain: bosons, first and last local dimension, first and last bond cap")
+    ap.add_argument("--sb-precision", default="tf32", choices=["tf32", "fp64"],
+                    help="form of the spin-boson chain measurement")
     return ap.parse_args()
 
 
@@ -484,19 +486,21 @@ def run_tebd_many(B, I, torch, n_chains=256, steps=10, warm=2, unbatched_chains=
                         "dt=0.01, p=10, q=1, Neel; graphs + 16 GB wave budget, after %d warm-up steps" % warm}
 
 
-def run_tebd_spin_boson(B, I, torch, steps=1, warm=1, size=(100, 32, 4, 256, 64)):
+def run_tebd_spin_boson(B, I, torch, steps=1, warm=1, size=(100, 32, 4, 256, 64), precision="tf32"):
     """Spin-boson chain in star-to-chain form: a spin and 100 bosonic sites
     whose local dimension falls from 32 to 4, couplings 1/(1+n), per-bond
     caps falling from 256 to 64, from a canonical random MPS at the caps
     (seed 0), dt = 0.05, p = 10, q = 2; the TF32 form (TF32 sketches with FP32
-    QRs, FP64-accurate projection, FP64 small SVD), all bonds of a parity per
-    launch sequence replayed from CUDA graphs, 40 GB wave budget.  One
-    second-order step = even, odd, even sweep."""
+    QRs, FP64-accurate projection, FP64 small SVD; the configuration's
+    precision) or the plain FP64 form, all bonds of a parity per launch
+    sequence replayed from CUDA graphs, 40 GB wave budget.  One second-order
+    step = even, odd, even sweep."""
     dims, caps = I.spin_boson_sizes(*size)
     g0, lam0 = I.random_canonical_mps(dims, caps, 0)
     hs = I.spin_boson_bond_terms(dims)
     dt, p, q = 0.05, 10, 2
-    sim = B.Tebd(len(dims), 2, 0, p, q, 3, d_site=dims, chi_bond=caps, precision=B.TEBD_PREC_TF32, use_graph=1,
+    code = B.TEBD_PREC_TF32 if precision == "tf32" else B.TEBD_PREC_FP64
+    sim = B.Tebd(len(dims), 2, 0, p, q, 3, d_site=dims, chi_bond=caps, precision=code, use_graph=1,
                  workspace_budget=40 << 30)
     sim.set_mps(g0, lam0)
     sim.set_gates(0, I.trotter_gates(hs, dt / 2))
@@ -514,7 +518,8 @@ def run_tebd_spin_boson(B, I, torch, steps=1, warm=1, size=(100, 32, 4, 256, 64)
     info = sim.workspace_info() if hasattr(sim, "workspace_info") else None
     sim.close()
     return {"value": upd / el, "unit": "bond updates/s", "seconds_per_step": el / steps, "steps_timed": steps,
-            "precision": "tf32 (mixed form)", "discarded_weight": float(w[0]), "workspace": info,
+            "precision": "tf32 (mixed form)" if precision == "tf32" else "fp64 (plain)",
+            "discarded_weight": float(w[0]), "workspace": info,
             "workload": "spin-boson chain: spin + %d bosons, d %d -> %d, chi caps %d -> %d, dt=0.05, p=10, q=2, "
                         "canonical random MPS at the caps (seed 0); graphs, 40 GB wave budget, after %d warm-up "
                         "step(s)" % (tuple(size) + (warm,))}
@@ -580,7 +585,8 @@ def main():
     if args.spin_boson_only:
         if rank == 0:
             size = tuple(int(x) for x in args.sb_size.split(","))
-            print(json.dumps({"tebd_spin_boson": run_tebd_spin_boson(B, I, torch, size=size)}), flush=True)
+            print(json.dumps({"tebd_spin_boson": run_tebd_spin_boson(B, I, torch, size=size,
+                                                                     precision=args.sb_precision)}), flush=True)
         return
 
     batch = args.batch
