@@ -63,8 +63,11 @@ WsLayout ws_layout(int m, int n, int k, int l, bool own_U, bool own_V, int r = 0
   w.Q = o; o += align_up(c * (size_t)m * l);
   w.Yt = o; o += align_up(c * (size_t)n * l);
   w.Qt = o; o += align_up(c * (size_t)n * l);
-  w.R = o; o += align_up(c * (size_t)l * l);
-  w.J = o; o += align_up(c * (size_t)l * l);
+  // R and J also hold the scratch of the many-CTA QR (partial products in R,
+  // alpha, tau and the panels' T in J), which a bond batched with larger
+  // ones may run even when its own l is small
+  w.R = o; o += align_up(c * std::max((size_t)l * l, qr_multi_scratch_r(l)));
+  w.J = o; o += align_up(c * std::max((size_t)l * l, qr_multi_scratch_j(l)));
   w.Jk = o; o += align_up(c * (size_t)l * k);
   w.Wk = o; o += align_up(c * (size_t)l * k);
   w.U = o; if (own_U) o += align_up(c * (size_t)m * k);

@@ -93,9 +93,13 @@ cudaError_t launch_zgemm(int stage, const Dims* dims, const ProbPtr* ptrs, int b
 cudaError_t launch_qr(int stage, const Dims* dims, const ProbPtr* ptrs, int batch, cudaStream_t st,
                       int only_flagged = 0);
 // the same, spread over many CTAs per instance (qr_multi.cu) when the batch
-// is a few tall matrices (cap.m or cap.n rows, cap.l columns)
+// is a few tall matrices (cap.m or cap.n rows, cap.l columns); every
+// instance's R and J buffers must hold at least qr_multi_scratch_r(l) and
+// qr_multi_scratch_j(l) complex words for its own l
 cudaError_t launch_qr_sized(int stage, const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap,
                            cudaStream_t st);
+size_t qr_multi_scratch_r(int l);
+size_t qr_multi_scratch_j(int l);
 cudaError_t launch_jacobi(const Dims* dims, const ProbPtr* ptrs, int batch, int* status, cudaStream_t st);
 // the same, each instance on a cluster of CTAs (jacobi_cluster.cu) when the
 // batch is a few instances with cap.l >= 64

@@ -28,6 +28,7 @@
 #include <cuda_runtime.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "../../include/tebd_gb300.h"
@@ -57,8 +58,8 @@ NaLayout na_layout(int m, int n, int k, int l) {
   w.Q = o; o += na_up(c * (size_t)m * l);
   w.Yt = o; o += na_up(c * (size_t)n * l);
   w.Qt = o; o += na_up(c * (size_t)n * l);
-  w.R = o; o += na_up(c * (size_t)l * l);
-  w.J = o; o += na_up(c * (size_t)l * l);
+  w.R = o; o += na_up(c * std::max((size_t)l * l, qr_multi_scratch_r(l)));  // many-CTA QR scratch
+  w.J = o; o += na_up(c * std::max((size_t)l * l, qr_multi_scratch_j(l)));
   w.Jk = o; o += na_up(c * (size_t)l * k);
   w.Wk = o; o += na_up(c * (size_t)l * k);
   w.U = o; o += na_up(c * (size_t)m * k);

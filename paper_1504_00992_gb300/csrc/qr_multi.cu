@@ -509,9 +509,9 @@ static cudaError_t qm_run(const Src& src, int batch, int M, int L, cudaStream_t 
   return cudaGetLastError();
 }
 
-// Few tall instances: the one-CTA kernel would leave most SMs idle.  L >= 32
-// also leaves room for the panel scratch (L + L/2 + 256 ceil(L/16) complex
-// words) in the instance's L x L buffer J.
+// Few tall instances: the one-CTA kernel would leave most SMs idle.  The
+// scratch lives in each instance's R and J, sized by qr_multi_scratch_r/j of
+// its own l (an l x l buffer holds it from l = 24 on).
 static bool qr_multi_fits(int M, int L, int batch) {
   return M >= QM_MIN_M && L >= QM_MIN_L && batch <= QM_MAX_BATCH;
 }
@@ -535,6 +535,14 @@ cudaError_t launch_qr_sized(int stage, const Dims* dims, const ProbPtr* ptrs, in
     default: return cudaErrorInvalidValue;
   }
   return e;
+}
+
+// Scratch of an FP64 instance with l columns (complex words): the partial
+// products of at most max(1, l / QM_NB) row chunks in R; alpha, tau and one
+// QM_NB x QM_NB T per panel in J.
+size_t qr_multi_scratch_r(int l) { return (size_t)(l / QM_NB > 1 ? l / QM_NB : 1) * QM_NB * l; }
+size_t qr_multi_scratch_j(int l) {
+  return (size_t)l + (l + 1) / 2 + (size_t)((l + QM_NB - 1) / QM_NB) * QM_NB * QM_NB;
 }
 
 bool qr_multi_f32_fits(int M, int L) { return M >= QM_MIN_M && L >= QM_MIN_L; }
