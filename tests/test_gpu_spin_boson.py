@@ -61,8 +61,9 @@ def test_spin_boson_chain_matches_oracle(lib, prec, tol_obs, tol_lam):
     assert abs(w - w_o) <= 1e-10
 
 
+@pytest.mark.parametrize("size", [(6, 16, 16, 64, 64), (6, 7, 7, 200, 200)])
 @pytest.mark.parametrize("prec,tol_spin", [(0, 1e-8), (2, 2e-7)])
-def test_spin_boson_wave_mixes_tiny_and_tall_bonds(lib, prec, tol_spin):
+def test_spin_boson_wave_mixes_tiny_and_tall_bonds(lib, prec, tol_spin, size):
     """Head of a chain with d = 16: one parity's wave holds the spin bond
     (theta 2 x 512, l = 2, no truncation) next to bonds of 1024 rows whose QRs
     run over many CTAs per instance, so every instance's scratch must fit its
@@ -71,9 +72,11 @@ def test_spin_boson_wave_mixes_tiny_and_tall_bonds(lib, prec, tol_spin):
     weight to 1e-8.  The other bonds start from a random MPS whose spectra
     have no gap at the cap, so the smallest kept values of any randomized
     truncation move with the rounding order (up to ~5e-6 between two FP64
-    codes on the same Omega); they are held to 1e-5."""
+    codes on the same Omega); they are held to 1e-5.  The second chain (d = 7,
+    caps 200) has bases of l = 210: the TF32 form re-orthonormalises them with
+    the correction read through L1."""
     from paper_1504_00992_gb300 import binding as B
-    dims, caps = I.spin_boson_sizes(6, 16, 16, 64, 64)
+    dims, caps = I.spin_boson_sizes(*size)
     g0, lam0 = I.random_canonical_mps(dims, caps, 0)
     _, lam, w = _run(B, prec, dims, caps, g0, lam0, 1, 0.05, 10, 2, 3)
     _, lam_o, w_o = _oracle(dims, caps, g0, lam0, 1, 0.05, 10, 2, 3)
