@@ -3,15 +3,15 @@
 //
 // The same method as k_jacobi (round-robin pairs, the same rotation,
 // convergence test, treatment of negligible columns and ranking), with the
-// L/2 disjoint pairs of each round spread over the JC_CL CTAs of a cluster
-// instead of one CTA, one group of JC_G lanes per pair, each lane loading
-// JC_U rows at a time (the columns come from L2, so the loads are batched): the columns of X and J stay
-// in global memory, the squared column norms move there too (the instance's
-// sigma buffer until the final values are written), and the cluster barrier
-// (release/acquire at cluster scope) separates the rounds; columns and norms
-// written by other CTAs are read through L2 (ld.global.cg).  A round's pairs
-// are disjoint, so no two groups touch the same column within a round; the
-// arithmetic of every pair is that of k_jacobi.
+// L/2 disjoint pairs of each round interleaved over the JC_CL CTAs of a
+// cluster instead of one CTA, one group of JC_G lanes per pair.  The columns
+// of X and J stay in global memory and the squared column norms move there
+// too (the instance's sigma buffer until the final values are written); the
+// cluster barrier (release/acquire at cluster scope) separates the rounds,
+// and columns and norms written by other CTAs are read through L2
+// (ld.global.cg), JC_U rows per lane at a time so that the loads overlap.  A
+// round's pairs are disjoint, so no two groups touch the same column within a
+// round; the arithmetic of every pair is that of k_jacobi.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <math.h>

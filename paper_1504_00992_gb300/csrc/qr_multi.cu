@@ -7,8 +7,9 @@
 // GPU idles.  Here the reflectors are grouped in panels of QM_NB columns
 // (compact WY form: H_j0 ... H_j0+nb-1 = I - V T V^H, T upper triangular;
 // Golub & Van Loan 5.2.3) and each panel is three launches:
-//   qm_panel  one CTA per instance factors the panel's columns (the same
-//             column steps as the one-CTA kernels, restricted to the panel);
+//   qm_panel_cl  a cluster of CTAs per instance factors the panel's columns
+//             (the same column steps as the one-CTA kernels, restricted to
+//             the panel, with the rows split over the cluster);
 //   qm_w      W = V^H C over row chunks x column blocks x instances, each
 //             chunk's partial sums written to its own slot (no atomics: the
 //             result does not depend on scheduling);
@@ -17,7 +18,8 @@
 //             C <- C - V op(T) W to its rows.
 // op(T) = T^H for the trailing columns of A; Q = H_0 ... H_{L-1} [I; 0] is
 // formed backwards with op(T) = T (qm_w, qm_upd per panel).  Kernel
-// boundaries order the steps: no CTA waits on another.
+// boundaries order the steps; within a panel the CTAs of a cluster meet at
+// cluster barriers (hardware barriers of co-scheduled CTAs, no spinning).
 //
 // Reflector rules.  FP64 (as k_qr): alpha = -e^{i arg x0} ||x||,
 // v = x - alpha e_1, tau = 1 / (||x|| (||x|| + |x0|)); columns below 1e-150
@@ -25,12 +27,15 @@
 // k_qr_f32): normalised reflectors v0 = 1, tau = 1 + |x0| / ||x||, the norm of
 // a column below 1e-12 taken from x / max|x|, columns below 1e-30 are zero,
 // the phase of x0 dropped when |x0| <= 1e-7 ||x||.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <math.h>
 
 #include "internal.cuh"
 #include "mixed.cuh"
 #include "profiler.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace tg {
 
@@ -193,96 +198,136 @@ struct QmSrc32 {
   }
 };
 
+// The panel over a cluster of QM_PC CTAs per instance: the panel's rows
+// [j0, M) are split into QM_PC contiguous blocks, one per CTA, and every
+// column step's reductions (the norm, the scaled norm of tiny FP32 columns,
+// the products v_j^H a_c for the panel's later columns) combine the CTAs'
+// partial sums read from each other's shared memory after a cluster barrier
+// (release/acquire at cluster scope), in rank order, so every CTA derives the
+// same reflector.  A CTA updates only its own rows; the one element another
+// CTA reads, the leading entry x0 = a_j[j] of a column, is written before the
+// barrier that precedes its read (and read through L2), and its owner stores
+// the reflector's v_0 there only after the next barrier, when every CTA has
+// read x0.
+enum { QM_PC = 8 };
+
 template <typename Tc, class Src, bool F32>
-__global__ void __launch_bounds__(QM_PT) qm_panel(Src src, int j0) {
+__global__ void __cluster_dims__(QM_PC, 1, 1) __launch_bounds__(QM_PT) qm_panel_cl(Src src, int j0) {
   typedef typename QmReal<Tc>::R R;
+  constexpr int NS = 3 + 2 * (QM_NB - 1);  // partial slots: norm, max, scaled norm, dot products
   __shared__ R red[32];
-  __shared__ R tau_s;
-  __shared__ Tc vsc;
+  __shared__ R part[NS];
+  __shared__ R comb[NS];
   __shared__ R pred[QM_PT / 32][2 * (QM_NB - 1)];
-  __shared__ R sdv[2 * (QM_NB - 1)];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int crank = (int)cluster.block_rank();
   QmView<Tc> v;
-  if (!src.get(blockIdx.x, v)) return;
+  if (!src.get(blockIdx.x / QM_PC, v)) return;  // uniform over the cluster
   const int M = v.M, L = v.L;
   if (j0 >= L) return;
   const int jb = min((int)QM_NB, L - j0);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int per = (M - j0 + QM_PC - 1) / QM_PC;
+  const int rlo = j0 + crank * per, rhi = min(M, rlo + per);
   const R ztol = F32 ? (R)1e-30f : (R)1e-150;
   const R ptol = F32 ? (R)1e-7f : (R)1e-15;
+  // sums slot s over the cluster's CTAs (in rank order) into comb[s] for s in [s0, s1)
+  auto combine = [&](int s0, int s1) {
+    if (tid >= s0 && tid < s1) {
+      R a = 0;
+      for (int c = 0; c < QM_PC; ++c) a += *cluster.map_shared_rank(&part[tid], c);
+      comb[tid] = a;
+    }
+    __syncthreads();
+  };
+  Tc* pend = nullptr;  // (tid 0 of the owner) where v_0 of the previous column goes
+  Tc pend_v = qm_c<Tc>(0, 0);
   for (int i = 0; i < jb; ++i) {
     const int j = j0 + i;
     Tc* aj = v.A + (int64_t)j * M;
+    const int r0 = max(j, rlo);
     R s = 0;
-    for (int r = j + tid; r < M; r += blockDim.x) s = qm_fma(aj[r].x, aj[r].x, qm_fma(aj[r].y, aj[r].y, s));
-    R nx = qm_sqrt(qm_bsum(s, red));
-    if (F32 && nx < (R)1e-12f) {
+    for (int r = r0 + tid; r < rhi; r += blockDim.x) {
+      const Tc x = aj[r];
+      s = qm_fma(x.x, x.x, qm_fma(x.y, x.y, s));
+    }
+    s = qm_bsum(s, red);
+    if (tid == 0) part[0] = s;
+    cluster.sync();
+    if (pend) {  // every CTA has read the previous column's x0
+      *pend = pend_v;
+      pend = nullptr;
+    }
+    combine(0, 1);
+    R nx = qm_sqrt(comb[0]);
+    if (F32 && nx < (R)1e-12f) {  // uniform over the cluster
       // squares in the FP32 subnormal range: the norm of x / max|x|
       R mx = 0;
-      for (int r = j + tid; r < M; r += blockDim.x) mx = fmax(mx, fmax(fabs(aj[r].x), fabs(aj[r].y)));
+      for (int r = r0 + tid; r < rhi; r += blockDim.x) mx = fmax(mx, fmax(fabs(aj[r].x), fabs(aj[r].y)));
       mx = qm_bmax(mx, red);
+      if (tid == 0) part[1] = mx;
+      cluster.sync();
+      if (tid == 0) {
+        R m2 = 0;
+        for (int c = 0; c < QM_PC; ++c) m2 = fmax(m2, *cluster.map_shared_rank(&part[1], c));
+        comb[1] = m2;
+      }
+      __syncthreads();
+      const R amax = comb[1];
       R s2 = 0;
-      if (mx > 0) {
-        const R ia = (R)1 / mx;
-        for (int r = j + tid; r < M; r += blockDim.x) {
+      if (amax > 0) {
+        const R ia = (R)1 / amax;
+        for (int r = r0 + tid; r < rhi; r += blockDim.x) {
           const R a = aj[r].x * ia, b = aj[r].y * ia;
           s2 = qm_fma(a, a, qm_fma(b, b, s2));
         }
       }
-      nx = mx * qm_sqrt(qm_bsum(s2, red));
+      s2 = qm_bsum(s2, red);
+      if (tid == 0) part[2] = s2;
+      cluster.sync();
+      combine(2, 3);
+      nx = amax * qm_sqrt(comb[2]);
     }
-    if (tid == 0) {
-      const Tc x0 = aj[j];
-      const R ax0 = qm_hypot(x0.x, x0.y);
-      R t = 0;
-      Tc sc = qm_c<Tc>(1, 0);
-      if (!(nx >= ztol)) {
-        if (!F32) v.alph[j] = qm_c<Tc>(0, 0);
+    // the reflector, derived identically in every CTA from x0 = a_j[j]
+    const Tc x0 = __ldcg(aj + j);
+    const R ax0 = qm_hypot(x0.x, x0.y);
+    R t = 0;
+    Tc sc = qm_c<Tc>(1, 0), v0 = x0;
+    if (nx >= ztol) {
+      const Tc ph = (ax0 > ptol * nx) ? qm_c<Tc>(x0.x / ax0, x0.y / ax0) : qm_c<Tc>(1, 0);
+      if (F32) {
+        const R ri = (R)1 / (ax0 + nx);
+        sc = qm_c<Tc>(ph.x * ri, -ph.y * ri);  // 1 / (x0 - alpha)
+        v0 = qm_c<Tc>(1, 0);
+        t = (R)1 + ax0 / nx;
       } else {
-        const Tc ph = (ax0 > ptol * nx) ? qm_c<Tc>(x0.x / ax0, x0.y / ax0) : qm_c<Tc>(1, 0);
-        if (F32) {
-          const R ri = (R)1 / (ax0 + nx);
-          sc = qm_c<Tc>(ph.x * ri, -ph.y * ri);  // 1 / (x0 - alpha)
-          aj[j] = qm_c<Tc>(1, 0);
-          t = (R)1 + ax0 / nx;
-        } else {
-          v.alph[j] = qm_c<Tc>(-ph.x * nx, -ph.y * nx);
-          aj[j] = qm_c<Tc>(ph.x * (ax0 + nx), ph.y * (ax0 + nx));
-          t = (R)1 / (nx * (nx + ax0));
-        }
+        v0 = qm_c<Tc>(ph.x * (ax0 + nx), ph.y * (ax0 + nx));
+        t = (R)1 / (nx * (nx + ax0));
       }
-      tau_s = t;
-      vsc = sc;
-      v.tau[j] = t;
+      if (crank == 0 && tid == 0 && !F32) v.alph[j] = qm_c<Tc>(-ph.x * nx, -ph.y * nx);
+    } else if (crank == 0 && tid == 0 && !F32) {
+      v.alph[j] = qm_c<Tc>(0, 0);
     }
-    __syncthreads();
-    const R t = tau_s;
-    if (F32 && t != 0) {
-      const Tc sc = vsc;
-      for (int r = j + 1 + tid; r < M; r += blockDim.x) aj[r] = qm_mul(aj[r], sc);
-      __syncthreads();
-    }
+    if (crank == 0 && tid == 0) v.tau[j] = t;
     const int nc = j0 + jb - j - 1;  // panel columns right of j (uniform)
-    if (!F32 && t != 0) {
-      // FP64: the FP64 pipe bounds the panel; one warp per column
-      for (int c = j + 1 + warp; c < j0 + jb; c += nw) {
-        Tc* ac = v.A + (int64_t)c * M;
-        Tc sd = qm_c<Tc>(0, 0);
-        for (int r = j + lane; r < M; r += 32) qm_fmac(sd, aj[r], ac[r]);
-        sd.x = qm_wsum(sd.x) * t;
-        sd.y = qm_wsum(sd.y) * t;
-        for (int r = j + lane; r < M; r += 32) qm_fms(ac[r], aj[r], sd);
+    const bool owner = j >= rlo && j < rhi;
+    if (t != 0) {
+      if (tid == 0 && owner) {
+        pend = aj + j;
+        pend_v = v0;
+      }
+      if (F32) {
+        for (int r = max(j + 1, rlo) + tid; r < rhi; r += blockDim.x) aj[r] = qm_mul(aj[r], sc);
+        __syncthreads();
       }
     }
-    if (F32 && t != 0 && nc > 0) {
-      // FP32: latency bounds the panel; all threads over the rows: partial
-      // v_j^H a_c for the nc columns, reduced over the block, then
-      // a_c -= tau v_j (v_j^H a_c)
+    if (t != 0 && nc > 0) {
       Tc* a1 = aj + M;  // column j + 1
       Tc dp[QM_NB - 1];
 #pragma unroll
       for (int q = 0; q < QM_NB - 1; ++q) dp[q] = qm_c<Tc>(0, 0);
-      for (int r = j + tid; r < M; r += blockDim.x) {
-        const Tc x = aj[r];
+      for (int r = r0 + tid; r < rhi; r += blockDim.x) {
+        const Tc x = (r == j) ? v0 : aj[r];
 #pragma unroll
         for (int q = 0; q < QM_NB - 1; ++q)
           if (q < nc) qm_fmac(dp[q], x, a1[(int64_t)q * M + r]);
@@ -301,21 +346,25 @@ __global__ void __launch_bounds__(QM_PT) qm_panel(Src src, int j0) {
       if (tid < 2 * nc) {
         R acc = 0;
         for (int w = 0; w < nw; ++w) acc += pred[w][tid];
-        sdv[tid] = acc * t;
+        part[3 + tid] = acc;
       }
-      __syncthreads();
+      cluster.sync();
+      combine(3, 3 + 2 * nc);
       Tc sd[QM_NB - 1];
 #pragma unroll
-      for (int q = 0; q < QM_NB - 1; ++q) sd[q] = (q < nc) ? qm_c<Tc>(sdv[2 * q], sdv[2 * q + 1]) : qm_c<Tc>(0, 0);
-      for (int r = j + tid; r < M; r += blockDim.x) {
-        const Tc x = aj[r];
+      for (int q = 0; q < QM_NB - 1; ++q)
+        sd[q] = (q < nc) ? qm_c<Tc>(t * comb[3 + 2 * q], t * comb[4 + 2 * q]) : qm_c<Tc>(0, 0);
+      for (int r = r0 + tid; r < rhi; r += blockDim.x) {
+        const Tc x = (r == j) ? v0 : aj[r];
 #pragma unroll
         for (int q = 0; q < QM_NB - 1; ++q)
           if (q < nc) qm_fms(a1[(int64_t)q * M + r], x, sd[q]);
       }
     }
-    __syncthreads();
+    __syncthreads();  // the next column's loops read rows this column's loops gave other threads
   }
+  cluster.sync();  // every CTA has read the last x0, and no CTA still reads another's partial sums
+  if (pend) *pend = pend_v;
 }
 
 // W = V^H C over one row chunk (blockIdx.y) for QM_CW columns from j0 (one
@@ -493,7 +542,7 @@ static cudaError_t qm_run(const Src& src, int batch, int M, int L, cudaStream_t 
   auto blocks = [](int cols) { return cols <= 0 ? 1 : (cols + QM_CW - 1) / QM_CW; };
   for (int pn = 0; pn < npan; ++pn) {
     const int j0 = pn * QM_NB, jb = (L - j0 < QM_NB) ? L - j0 : QM_NB;
-    qm_panel<Tc, Src, F32><<<batch, QM_PT, 0, st>>>(src, j0);
+    qm_panel_cl<Tc, Src, F32><<<batch * QM_PC, QM_PT, 0, st>>>(src, j0);
     qm_w<Tc, Src, false><<<dim3(blocks(L - j0), nch, batch), QM_AT, 0, st>>>(src, j0);
     qm_upd<Tc, Src, false><<<dim3(blocks(L - j0 - jb), nch, batch), QM_AT, 0, st>>>(src, j0);
   }
