@@ -86,3 +86,40 @@ def test_mixed_form_full_size_sampled(lib):
         opt = np.sqrt(np.sum(sig[100:] ** 2))
         err = np.linalg.norm(theta[t] - truncated(res["U"][t], res["sigma"][t], res["Vh"][t]))
         assert (err - opt) / np.linalg.norm(theta[t]) <= 1e-8
+
+
+@pytest.mark.parametrize("m,n,k,p,rank", [
+    (3700, 300, 30, 10, 12),   # FP32 QR of Y over a cluster panel: columns 13..40 collapse to rounding noise
+    (2000, 160, 24, 8, 5),     # blocked FP32 QR in shared memory
+])
+def test_mixed_form_rank_deficient(lib, m, n, k, p, rank):
+    """Exact rank below the sketch width: the FP32 QRs meet columns at the
+    rounding level (the tiny-column rules keep every reflector unitary), the
+    basis stays orthonormal, the singular values are the exact ones to
+    1e-8 s_1 and the rest fall to the noise level.  The rank-r reconstruction
+    carries the form's first-order range error (the refinement pass resolves
+    the sketched range to FP32 level, ~1e-7 relative; singular values feel it
+    only to second order): it is held to 3e-6 relative."""
+    from paper_1504_00992_gb300 import binding as B
+    rng = np.random.default_rng(17)
+    batch = 2
+    theta = np.stack([(rng.standard_normal((m, rank)) + 1j * rng.standard_normal((m, rank))) @
+                      (rng.standard_normal((rank, n)) + 1j * rng.standard_normal((rank, n))) for _ in range(batch)])
+    plan = B.rrsvd_plan_create(m, n, k, p, 1, batch, B.TEBD_PREC_TF32, SEED)
+    try:
+        res = rrsvd_device(B, plan, theta)
+    finally:
+        B.rrsvd_plan_destroy(plan)
+    for t in range(batch):
+        s_ref = np.linalg.svd(theta[t], compute_uv=False)
+        s = res["sigma"][t]
+        assert np.all(np.isfinite(s)) and res["rank"][t] >= rank
+        assert np.abs(s[:rank] - s_ref[:rank]).max() <= 1e-8 * s_ref[0]
+        assert np.all(s[rank:] <= 1e-6 * s_ref[0])
+        r = rank
+        rec = truncated(res["U"][t][:, :r], s[:r], res["Vh"][t][:r])
+        assert np.linalg.norm(rec - theta[t]) <= 3e-6 * np.linalg.norm(theta[t])
+        U = res["U"][t][:, :r]
+        assert np.abs(U.conj().T @ U - np.eye(r)).max() < 1e-11
+        V = res["Vh"][t][:r]
+        assert np.abs(V @ V.conj().T - np.eye(r)).max() < 1e-11
