@@ -19,6 +19,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -53,6 +54,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tebd", action="store_true")
     ap.add_argument("--no-spin-boson", action="store_true")
+    ap.add_argument("--clocks-dir", default=None,
+                    help="directory for the nvidia-smi clock samples of the timed regions (default: a temp dir)")
     ap.add_argument("--spin-boson-only", action="store_true",
                     help="run only the spin-boson chain measurement (for kernel launch lists)")
     ap.add_argument("--sb-size", default="100,32,4,256,64",
@@ -246,13 +249,14 @@ def measure(B, torch, dev, theta, sig, batch, prec, args, rank, world, local):
         step(s)
     torch.cuda.synchronize()
     # accuracy of this launch configuration against the exact spectrum, and
-    # the excess Frobenius error of one instance (A14 reading of the metric)
+    # the excess Frobenius error of one instance: (||theta - theta_k||_F -
+    # ||theta - theta_k(exact)||_F) / ||theta||_F
     sig_err = float(np.abs(sg.cpu().numpy() - sig[:k][None, :]).max())
     u0, s0, v0 = U[0].cpu().numpy(), sg[0].cpu().numpy(), Vh[0].cpu().numpy()
     th0 = theta[0].cpu().numpy()
     excess = (np.linalg.norm(th0 - (u0 * s0) @ v0) - np.sqrt(np.sum(sig[k:] ** 2))) / np.linalg.norm(th0)
-    sampler = ClockSampler(local, os.path.join(ROOT, "gpurun_out", f"clocks_{prec}_rank{rank}.csv")) \
-        if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ClockSampler(local, f"/tmp/clocks_rank{rank}.csv")
+    sampler = ClockSampler(local, os.path.join(args.clocks_dir or tempfile.gettempdir(),
+                                               f"clocks_{prec}_rank{rank}.csv"))
     B.tebd_profiler_reset()
     B.tebd_profiler_enable(True)
     barrier()

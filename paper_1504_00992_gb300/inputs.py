@@ -178,8 +178,9 @@ def gate_derivative(h, tau, dh):
 
 
 # ---------------------------------------------------------------------------
-# Spin-boson chain (star-to-chain form; Section II.C applications, SURVEY
-# reading A9): a spin coupled through sigma^z to the first of n bosonic sites,
+# Spin-boson chain (star-to-chain form of the paper's TEDOPA applications; the
+# chain coefficients are simple stand-ins): a spin coupled through sigma^z to
+# the first of n bosonic sites,
 #   H = (Delta_s/2) sx + t0 sz (a_1 + a_1^+) + sum_n omega n_n
 #       + sum_n t_n (a_n^+ a_{n+1} + a_n a_{n+1}^+),   t_n = t0 / (1 + n),
 # bosons truncated to d_n levels falling linearly from d_first to d_last.
