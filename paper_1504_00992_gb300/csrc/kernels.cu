@@ -474,10 +474,13 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr(const Dims* __restrict__ dims
 cudaError_t launch_qr(int stage, const Dims* dims, const ProbPtr* ptrs, int batch, cudaStream_t st,
                       int only_flagged) {
   ProfScope ps("k_qr", st);
+  // batches of four matrices per SM or more: 256-thread CTAs, four per SM,
+  // so that one matrix's per-column barriers overlap with the others' work
+  const int nt = batch >= 4 * 152 ? 256 : QR_THREADS;
   switch (stage) {
-    case QR_Y: k_qr<QR_Y><<<batch, QR_THREADS, 0, st>>>(dims, ptrs, only_flagged); break;
-    case QR_YT: k_qr<QR_YT><<<batch, QR_THREADS, 0, st>>>(dims, ptrs, only_flagged); break;
-    case QR_BH: k_qr<QR_BH><<<batch, QR_THREADS, 0, st>>>(dims, ptrs, only_flagged); break;
+    case QR_Y: k_qr<QR_Y><<<batch, nt, 0, st>>>(dims, ptrs, only_flagged); break;
+    case QR_YT: k_qr<QR_YT><<<batch, nt, 0, st>>>(dims, ptrs, only_flagged); break;
+    case QR_BH: k_qr<QR_BH><<<batch, nt, 0, st>>>(dims, ptrs, only_flagged); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -633,7 +636,8 @@ __global__ void __launch_bounds__(JAC_THREADS) k_jacobi(const Dims* __restrict__
 
 cudaError_t launch_jacobi(const Dims* dims, const ProbPtr* ptrs, int batch, int* status, cudaStream_t st) {
   ProfScope ps("k_jacobi", st);
-  k_jacobi<<<batch, JAC_THREADS, 0, st>>>(dims, ptrs, status);
+  // two matrices per SM or more: 256-thread CTAs, two per SM
+  k_jacobi<<<batch, batch >= 2 * 152 ? 256 : JAC_THREADS, 0, st>>>(dims, ptrs, status);
   return cudaGetLastError();
 }
 

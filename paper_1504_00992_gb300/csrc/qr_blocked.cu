@@ -37,31 +37,33 @@ __device__ __forceinline__ float qb_wsum(float v) {
 }
 
 // Shared-memory layout of k_qr_blk_f32 (bytes), shared with the host check.
-__host__ __device__ inline size_t qb_smem_bytes(int M, int L) {
+__host__ __device__ inline size_t qb_smem_bytes(int M, int L, int nw = QB_WARPS) {
   const int npan = (L + QB_NB - 1) / QB_NB;
   return sizeof(float2) * ((size_t)QB_NB * M + 2 * (size_t)QB_NB * L + (size_t)npan * QB_NB * QB_NB) +
-         sizeof(float) * ((size_t)L + QB_WARPS * QB_RED + QB_RED);
+         sizeof(float) * ((size_t)L + (size_t)nw * QB_RED + QB_RED);
 }
 
 // C[j0:M, c0:L) <- C - V op(T) (V^H C), op(T) = T^H (trans) or T.  V holds jb
 // reflectors in shared memory (local row r = global row j0 + r, zero above
 // each reflector's first row).  When a column group's rows are split over
 // several warps, their partial products go to the scratch `part`
-// (QB_WARPS * QB_NB * QB_CW real and imaginary parts) and are summed in a
+// (warps x QB_NB x QB_CW real and imaginary parts) and are summed in a
 // fixed order, so the result does not depend on scheduling.  All threads of
 // the CTA call it.
+template <int NT>
 __device__ void qb_apply(float2* C, int M, int j0, int jb, int c0, int L, const float2* Vs, int ldv,
                          const float2* Tp, bool trans, float2* W, float2* W2, float* part) {
+  constexpr int NW = NT / 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int Mr = M - j0, ncol = L - c0;
   if (ncol <= 0) return;
-  for (int e = tid; e < QB_NB * ncol; e += QB_THREADS) W[(e / ncol) * L + c0 + e % ncol] = make_float2(0.f, 0.f);
+  for (int e = tid; e < QB_NB * ncol; e += NT) W[(e / ncol) * L + c0 + e % ncol] = make_float2(0.f, 0.f);
   __syncthreads();
   const int ncg = (ncol + QB_CW - 1) / QB_CW;
-  const int rs = ncg >= QB_WARPS ? 1 : QB_WARPS / ncg;
+  const int rs = ncg >= NW ? 1 : NW / ncg;
   const int ntask = ncg * rs;
   // pass 1: W = V^H C
-  for (int t = warp; t < ntask; t += QB_WARPS) {
+  for (int t = warp; t < ntask; t += NW) {
     const int cg = t % ncg, h = t / ncg;
     const int cb = c0 + cg * QB_CW;
     const int nc = min(QB_CW, L - cb);
@@ -103,9 +105,9 @@ __device__ void qb_apply(float2* C, int M, int j0, int jb, int c0, int L, const 
       for (int w = 0; w < QB_CW; ++w) {
         const float sx = qb_wsum(acc[i][w].x), sy = qb_wsum(acc[i][w].y);
         if (lane == ((i * QB_CW + w) & 31)) {
-          if (rs > 1) {  // one task per warp (ntask <= QB_WARPS): a slot per warp
+          if (rs > 1) {  // one task per warp (ntask <= NW): a slot per warp
             part[(warp * QB_NB + i) * QB_CW + w] = sx;
-            part[QB_WARPS * QB_NB * QB_CW + (warp * QB_NB + i) * QB_CW + w] = sy;
+            part[NW * QB_NB * QB_CW + (warp * QB_NB + i) * QB_CW + w] = sy;
           } else if (i < jb && w < nc) {  // the column group's only contributor
             W[i * L + cb + w] = make_float2(sx, sy);
           }
@@ -115,20 +117,20 @@ __device__ void qb_apply(float2* C, int M, int j0, int jb, int c0, int L, const 
   __syncthreads();
   if (rs > 1) {
     // task t = h ncg + cg ran on warp t: sum the row slices h in order
-    for (int e = tid; e < jb * ncol; e += QB_THREADS) {
+    for (int e = tid; e < jb * ncol; e += NT) {
       const int i = e / ncol, cl = e % ncol, cg = cl / QB_CW, w = cl % QB_CW;
       float sx = 0.f, sy = 0.f;
       for (int h = 0; h < rs; ++h) {
         const int slot = ((h * ncg + cg) * QB_NB + i) * QB_CW + w;
         sx += part[slot];
-        sy += part[QB_WARPS * QB_NB * QB_CW + slot];
+        sy += part[NW * QB_NB * QB_CW + slot];
       }
       W[i * L + c0 + cl] = make_float2(sx, sy);
     }
     __syncthreads();
   }
   // W2 = op(T) W
-  for (int e = tid; e < jb * ncol; e += QB_THREADS) {
+  for (int e = tid; e < jb * ncol; e += NT) {
     const int i = e / ncol, c = c0 + e % ncol;
     float2 s = make_float2(0.f, 0.f);
     if (trans) {
@@ -148,7 +150,7 @@ __device__ void qb_apply(float2* C, int M, int j0, int jb, int c0, int L, const 
   }
   __syncthreads();
   // pass 2: C -= V W2
-  for (int t = warp; t < ntask; t += QB_WARPS) {
+  for (int t = warp; t < ntask; t += NW) {
     const int cg = t % ncg, h = t / ncg;
     const int cb = c0 + cg * QB_CW;
     const int nc = min(QB_CW, L - cb);
@@ -194,7 +196,9 @@ __device__ void qb_apply(float2* C, int M, int j0, int jb, int c0, int L, const 
 // A: M x L column-major per instance (overwritten by R and the reflectors);
 // Q: M x L column-major output.  Requires M >= L and qb_smem_bytes(M, L) of
 // dynamic shared memory.
-__global__ void __launch_bounds__(QB_THREADS) k_qr_blk_f32(float2* Abase, float2* Qbase, int M, int L) {
+template <int NT>
+__global__ void __launch_bounds__(NT) k_qr_blk_f32(float2* Abase, float2* Qbase, int M, int L) {
+  constexpr int NW = NT / 32;
   extern __shared__ __align__(16) unsigned char qb_raw[];
   __shared__ float2 vscale;
   __shared__ float vnorm;
@@ -206,7 +210,7 @@ __global__ void __launch_bounds__(QB_THREADS) k_qr_blk_f32(float2* Abase, float2
   float2* Tall = W2 + QB_NB * L;
   float* tau = reinterpret_cast<float*>(Tall + npan * QB_NB * QB_NB);
   float* red = tau + L;
-  float* fin = red + QB_WARPS * QB_RED;
+  float* fin = red + NW * QB_RED;
   const int z = blockIdx.x;
   float2* A = Abase + (size_t)z * M * L;
   float2* Qo = Qbase + (size_t)z * M * L;
@@ -214,7 +218,7 @@ __global__ void __launch_bounds__(QB_THREADS) k_qr_blk_f32(float2* Abase, float2
 
   for (int p = 0; p < npan; ++p) {
     const int j0 = p * QB_NB, jb = min(QB_NB, L - j0), Mr = M - j0;
-    for (int e = tid; e < jb * Mr; e += QB_THREADS) {
+    for (int e = tid; e < jb * Mr; e += NT) {
       const int i = e / Mr, r = e % Mr;
       Vs[i * ldv + r] = A[(size_t)(j0 + i) * M + j0 + r];
     }
@@ -223,7 +227,7 @@ __global__ void __launch_bounds__(QB_THREADS) k_qr_blk_f32(float2* Abase, float2
     for (int i = 0; i < jb; ++i) {
       const int j = j0 + i;
       float s = 0.f;
-      for (int r = i + tid; r < Mr; r += QB_THREADS) {
+      for (int r = i + tid; r < Mr; r += NT) {
         const float2 v = Vs[i * ldv + r];
         s = fmaf(v.x, v.x, fmaf(v.y, v.y, s));
       }
@@ -232,7 +236,7 @@ __global__ void __launch_bounds__(QB_THREADS) k_qr_blk_f32(float2* Abase, float2
       __syncthreads();
       if (tid == 0) {
         float t = 0.f;
-        for (int w = 0; w < QB_WARPS; ++w) t += red[w];
+        for (int w = 0; w < NW; ++w) t += red[w];
         vnorm = sqrtf(t);
       }
       __syncthreads();
@@ -240,7 +244,7 @@ __global__ void __launch_bounds__(QB_THREADS) k_qr_blk_f32(float2* Abase, float2
         // a column this small has squares in the FP32 subnormal range, whose
         // lost bits would make the reflector non-unitary: norm of x / max|x|
         float mx = 0.f;
-        for (int r = i + tid; r < Mr; r += QB_THREADS) {
+        for (int r = i + tid; r < Mr; r += NT) {
           const float2 v = Vs[i * ldv + r];
           mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
         }
@@ -249,12 +253,12 @@ __global__ void __launch_bounds__(QB_THREADS) k_qr_blk_f32(float2* Abase, float2
         if (lane == 0) red[warp] = mx;
         __syncthreads();
         float amax = 0.f;
-        for (int w = 0; w < QB_WARPS; ++w) amax = fmaxf(amax, red[w]);
+        for (int w = 0; w < NW; ++w) amax = fmaxf(amax, red[w]);
         __syncthreads();
         float s2 = 0.f;
         if (amax > 0.f) {
           const float ia = 1.f / amax;
-          for (int r = i + tid; r < Mr; r += QB_THREADS) {
+          for (int r = i + tid; r < Mr; r += NT) {
             const float2 v = Vs[i * ldv + r];
             const float a = v.x * ia, b = v.y * ia;
             s2 = fmaf(a, a, fmaf(b, b, s2));
@@ -265,7 +269,7 @@ __global__ void __launch_bounds__(QB_THREADS) k_qr_blk_f32(float2* Abase, float2
         __syncthreads();
         if (tid == 0) {
           float t = 0.f;
-          for (int w = 0; w < QB_WARPS; ++w) t += red[w];
+          for (int w = 0; w < NW; ++w) t += red[w];
           vnorm = amax * sqrtf(t);
         }
         __syncthreads();
@@ -294,7 +298,7 @@ __global__ void __launch_bounds__(QB_THREADS) k_qr_blk_f32(float2* Abase, float2
       const float tj = tau[j];
       if (tj != 0.f) {
         const float2 sc = vscale;
-        for (int r = i + 1 + tid; r < Mr; r += QB_THREADS) {
+        for (int r = i + 1 + tid; r < Mr; r += NT) {
           const float2 v = Vs[i * ldv + r];
           Vs[i * ldv + r] = make_float2(v.x * sc.x - v.y * sc.y, v.x * sc.y + v.y * sc.x);
         }
@@ -305,7 +309,7 @@ __global__ void __launch_bounds__(QB_THREADS) k_qr_blk_f32(float2* Abase, float2
         float2 acc[QB_NB - 1];
 #pragma unroll
         for (int c = 0; c < QB_NB - 1; ++c) acc[c] = make_float2(0.f, 0.f);
-        for (int r = i + tid; r < Mr; r += QB_THREADS) {
+        for (int r = i + tid; r < Mr; r += NT) {
           const float2 v = Vs[i * ldv + r];
 #pragma unroll
           for (int c = 0; c < QB_NB - 1; ++c)
@@ -326,11 +330,11 @@ __global__ void __launch_bounds__(QB_THREADS) k_qr_blk_f32(float2* Abase, float2
         __syncthreads();
         if (tid < 2 * nc) {
           float t = 0.f;
-          for (int w = 0; w < QB_WARPS; ++w) t += red[w * QB_RED + tid];
+          for (int w = 0; w < NW; ++w) t += red[w * QB_RED + tid];
           fin[tid] = t * tj;
         }
         __syncthreads();
-        for (int r = i + tid; r < Mr; r += QB_THREADS) {
+        for (int r = i + tid; r < Mr; r += NT) {
           const float2 v = Vs[i * ldv + r];
 #pragma unroll
           for (int c = 0; c < QB_NB - 1; ++c)
@@ -346,12 +350,12 @@ __global__ void __launch_bounds__(QB_THREADS) k_qr_blk_f32(float2* Abase, float2
     }
     // --- panel (R part and reflectors) back to global memory, then clear
     // the R part so that Vs holds V with its zeros
-    for (int e = tid; e < jb * Mr; e += QB_THREADS) {
+    for (int e = tid; e < jb * Mr; e += NT) {
       const int i = e / Mr, r = e % Mr;
       A[(size_t)(j0 + i) * M + j0 + r] = Vs[i * ldv + r];
     }
     __syncthreads();
-    for (int e = tid; e < jb * jb; e += QB_THREADS) {
+    for (int e = tid; e < jb * jb; e += NT) {
       const int i = e / jb, r = e % jb;
       if (r < i) Vs[i * ldv + r] = make_float2(0.f, 0.f);
     }
@@ -361,7 +365,7 @@ __global__ void __launch_bounds__(QB_THREADS) k_qr_blk_f32(float2* Abase, float2
       float2 sab[QB_NB * (QB_NB - 1) / 2];
 #pragma unroll
       for (int q = 0; q < QB_NB * (QB_NB - 1) / 2; ++q) sab[q] = make_float2(0.f, 0.f);
-      for (int r = 1 + tid; r < Mr; r += QB_THREADS) {  // row 0 only meets V_0
+      for (int r = 1 + tid; r < Mr; r += NT) {  // row 0 only meets V_0
         float2 v[QB_NB];
 #pragma unroll
         for (int i = 0; i < QB_NB; ++i) v[i] = (i < jb) ? Vs[i * ldv + r] : make_float2(0.f, 0.f);
@@ -385,7 +389,7 @@ __global__ void __launch_bounds__(QB_THREADS) k_qr_blk_f32(float2* Abase, float2
       __syncthreads();
       if (tid < QB_NB * (QB_NB - 1)) {
         float t = 0.f;
-        for (int w = 0; w < QB_WARPS; ++w) t += red[w * QB_RED + tid];
+        for (int w = 0; w < NW; ++w) t += red[w * QB_RED + tid];
         fin[tid] = t;
       }
       __syncthreads();
@@ -411,23 +415,23 @@ __global__ void __launch_bounds__(QB_THREADS) k_qr_blk_f32(float2* Abase, float2
       __syncthreads();
     }
     // --- trailing columns: A <- A - V T^H V^H A
-    qb_apply(A, M, j0, jb, j0 + jb, L, Vs, ldv, Tall + p * QB_NB * QB_NB, true, W, W2, red);
+    qb_apply<NT>(A, M, j0, jb, j0 + jb, L, Vs, ldv, Tall + p * QB_NB * QB_NB, true, W, W2, red);
   }
 
   // --- Q = H_0 ... H_{L-1} [I; 0], panels backwards
-  for (int64_t e = tid; e < (int64_t)M * L; e += QB_THREADS) {
+  for (int64_t e = tid; e < (int64_t)M * L; e += NT) {
     const int c = (int)(e / M), r = (int)(e % M);
     Qo[e] = make_float2(r == c ? 1.f : 0.f, 0.f);
   }
   __syncthreads();
   for (int p = npan - 1; p >= 0; --p) {
     const int j0 = p * QB_NB, jb = min(QB_NB, L - j0), Mr = M - j0;
-    for (int e = tid; e < jb * Mr; e += QB_THREADS) {
+    for (int e = tid; e < jb * Mr; e += NT) {
       const int i = e / Mr, r = e % Mr;
       Vs[i * ldv + r] = (r < i) ? make_float2(0.f, 0.f) : A[(size_t)(j0 + i) * M + j0 + r];
     }
     __syncthreads();
-    qb_apply(Qo, M, j0, jb, j0, L, Vs, ldv, Tall + p * QB_NB * QB_NB, false, W, W2, red);
+    qb_apply<NT>(Qo, M, j0, jb, j0, L, Vs, ldv, Tall + p * QB_NB * QB_NB, false, W, W2, red);
   }
 }
 
@@ -445,13 +449,33 @@ static cudaError_t ensure_smem(K kernel, size_t bytes, size_t* done) {
 
 // Shared-memory limits set so far, per kernel (one record each, shared by the
 // launchers and qr_blocked_prepare so that a limit is never lowered).
-static size_t g_attr_qr = 0, g_attr_ld = 0, g_attr_fold[2][2] = {{0, 0}, {0, 0}};
+static size_t g_attr_qr = 0, g_attr_qr256 = 0, g_attr_ld = 0, g_attr_fold[2][2] = {{0, 0}, {0, 0}};
+
+// Batches of many small matrices take smaller CTAs when several fit an SM
+// (registers: 128 per thread; shared memory): the per-column barriers of one
+// matrix then overlap with the others' work.  Four 128-thread CTAs per SM
+// from four matrices per SM, two 256-thread CTAs from two.
+static size_t g_attr_qr128 = 0;
 
 cudaError_t launch_qr_blk_f32(float2* A, float2* Q, int M, int L, int batch, cudaStream_t st) {
+  if (batch >= 4 * 152 && qb_smem_bytes(M, L, 4) <= 56 * 1024) {
+    const size_t sm = qb_smem_bytes(M, L, 4);
+    cudaError_t e = ensure_smem(k_qr_blk_f32<128>, sm, &g_attr_qr128);
+    if (e != cudaSuccess) return e;
+    k_qr_blk_f32<128><<<batch, 128, sm, st>>>(A, Q, M, L);
+    return cudaGetLastError();
+  }
+  if (batch >= 2 * 152 && qb_smem_bytes(M, L, 8) <= 112 * 1024) {
+    const size_t sm = qb_smem_bytes(M, L, 8);
+    cudaError_t e = ensure_smem(k_qr_blk_f32<256>, sm, &g_attr_qr256);
+    if (e != cudaSuccess) return e;
+    k_qr_blk_f32<256><<<batch, 256, sm, st>>>(A, Q, M, L);
+    return cudaGetLastError();
+  }
   const size_t sm = qb_smem_bytes(M, L);
-  cudaError_t e = ensure_smem(k_qr_blk_f32, sm, &g_attr_qr);
+  cudaError_t e = ensure_smem(k_qr_blk_f32<QB_THREADS>, sm, &g_attr_qr);
   if (e != cudaSuccess) return e;
-  k_qr_blk_f32<<<batch, QB_THREADS, sm, st>>>(A, Q, M, L);
+  k_qr_blk_f32<QB_THREADS><<<batch, QB_THREADS, sm, st>>>(A, Q, M, L);
   return cudaGetLastError();
 }
 
@@ -882,7 +906,10 @@ static cudaError_t launch_fold_big(const float2* Qf, const float2* Dbuf, const D
 cudaError_t qr_blocked_prepare(int M, int N, int L) {
   cudaError_t e = cudaSuccess;
   const size_t qr = qb_smem_bytes(M > N ? M : N, L);
-  if (qr <= 227 * 1024 - 1024) e = ensure_smem(k_qr_blk_f32, qr, &g_attr_qr);
+  if (qr <= 227 * 1024 - 1024) e = ensure_smem(k_qr_blk_f32<QB_THREADS>, qr, &g_attr_qr);
+  const size_t qr256 = qb_smem_bytes(M > N ? M : N, L, 8), qr128 = qb_smem_bytes(M > N ? M : N, L, 4);
+  if (e == cudaSuccess && qr256 <= 112 * 1024) e = ensure_smem(k_qr_blk_f32<256>, qr256, &g_attr_qr256);
+  if (e == cudaSuccess && qr128 <= 56 * 1024) e = ensure_smem(k_qr_blk_f32<128>, qr128, &g_attr_qr128);
   if (e == cudaSuccess && L <= QF_MAXL) {
     e = ensure_smem(k_lowdin, sizeof(float2) * (size_t)L * L, &g_attr_ld);
     if (e == cudaSuccess) e = launch_fold<true>(nullptr, nullptr, nullptr, nullptr, M, L, 0, nullptr);
