@@ -516,11 +516,11 @@ static cudaError_t tc_product(const float* A0, const float* A1, const float* B0,
 }
 
 static cudaError_t qr_f32(float2* A, float2* Q, int M, int L, int batch, const MixedPtrs& mp, const MixedSizes& s,
-                          cudaStream_t st) {
+                          const Dims* dims, int use_n, cudaStream_t st) {
   if (!qr_blk_f32_fits(M, L) && mp.qscr && qr_multi_f32_fits(M, L))
     return launch_qr_multi_f32(A, Q, mp.qscr, s.qs / sizeof(float2), M, L, batch, st);
   ProfScope ps("k_qr_f32", st);
-  if (qr_blk_f32_fits(M, L)) return launch_qr_blk_f32(A, Q, M, L, batch, st);
+  if (qr_blk_f32_fits(M, L)) return launch_qr_blk_f32(A, Q, M, L, batch, st, dims, use_n);
   k_qr_f32<<<batch, 1024, 0, st>>>(A, Q, M, L);
   return cudaGetLastError();
 }
@@ -570,16 +570,16 @@ cudaError_t run_rrsvd_mixed(const Dims* dims, const ProbPtr* ptrs, int batch, co
   MX_TRY(tc_product(mp.thf_hi, mp.thf_lo, mp.bt_hi, mp.bt_lo, m, s.K1, s, l, p0, mp.Yf, batch, err, st));
   for (int j = 1; j <= q; ++j) {
     const int np = (j == q) ? 3 : 1;
-    MX_TRY(qr_f32(mp.Yf, mp.Qf, m, l, batch, mp, s, st));    // Y = Q R
+    MX_TRY(qr_f32(mp.Yf, mp.Qf, m, l, batch, mp, s, dims, 0, st));    // Y = Q R
     MX_TRY(conv_bt(mp.Qf, dims, mp, m, l, s.K2, s, np == 3, batch, st));
     MX_TRY(tc_product(mp.tha_hi, mp.tha_lo, mp.bt_hi, mp.bt_lo, n, s.K2, s, l, np, mp.Ytf, batch, err, st));  // A^H Q
-    MX_TRY(qr_f32(mp.Ytf, mp.Qtf, n, l, batch, mp, s, st));  // = Q~ R~
+    MX_TRY(qr_f32(mp.Ytf, mp.Qtf, n, l, batch, mp, s, dims, 1, st));  // = Q~ R~
     MX_TRY(conv_bt(mp.Qtf, dims, mp, n, l, s.K1, s, np == 3, batch, st));
     MX_TRY(tc_product(mp.thf_hi, mp.thf_lo, mp.bt_hi, mp.bt_lo, m, s.K1, s, l, np, mp.Yf, batch, err, st));  // A Q~
   }
   if (reorth_fits(m, l)) {
     // last QR: FP32 Householder, then the FP64-accurate re-orthonormalisation
-    MX_TRY(qr_f32(mp.Yf, mp.Qf, m, l, batch, mp, s, st));
+    MX_TRY(qr_f32(mp.Yf, mp.Qf, m, l, batch, mp, s, dims, 0, st));
     MX_TRY(launch_reorth(mp.Qf, mp.Df, dims, ptrs, m, l, batch, status, st));
     MX_TRY(launch_proj_df(mp.thd, dims, ptrs, mp.Qf, mp.Df, m, n, l, batch, st));  // B^H = A^H Q
   } else {

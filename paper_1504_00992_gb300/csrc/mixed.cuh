@@ -41,9 +41,12 @@ size_t mixed_bytes(const MixedSizes& s, int batch);
 MixedPtrs mixed_carve(char* base, const MixedSizes& s, int batch);
 
 // Blocked FP32 Householder QR (qr_blocked.cu): A (M x L column-major per
-// instance, overwritten) -> Q; usable when qr_blk_f32_fits(M, L).
+// instance, overwritten) -> Q; usable when qr_blk_f32_fits(M, L).  With
+// dims, each instance factors only its own rows (D.n if use_n, else D.m) and
+// D.l columns of the zero-padded M x L layout.
 bool qr_blk_f32_fits(int M, int L);
-cudaError_t launch_qr_blk_f32(float2* A, float2* Q, int M, int L, int batch, cudaStream_t st);
+cudaError_t launch_qr_blk_f32(float2* A, float2* Q, int M, int L, int batch, cudaStream_t st,
+                              const Dims* dims = nullptr, int use_n = 0);
 // The same QR spread over many CTAs per instance (qr_multi.cu), for matrices
 // too tall for the blocked kernel's shared memory; scr holds
 // qr_multi_f32_scratch(M, L) float2 per instance at the given stride.

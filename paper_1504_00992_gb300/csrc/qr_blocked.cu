@@ -51,7 +51,7 @@ __host__ __device__ inline size_t qb_smem_bytes(int M, int L, int nw = QB_WARPS)
 // fixed order, so the result does not depend on scheduling.  All threads of
 // the CTA call it.
 template <int NT>
-__device__ void qb_apply(float2* C, int M, int j0, int jb, int c0, int L, const float2* Vs, int ldv,
+__device__ void qb_apply(float2* C, int ldc, int M, int j0, int jb, int c0, int L, const float2* Vs, int ldv,
                          const float2* Tp, bool trans, float2* W, float2* W2, float* part) {
   constexpr int NW = NT / 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -78,7 +78,7 @@ __device__ void qb_apply(float2* C, int M, int j0, int jb, int c0, int L, const 
     float2 an[QB_CW];
 #pragma unroll
     for (int w = 0; w < QB_CW; ++w)
-      an[w] = (w < nc && r < Mr) ? C[(size_t)(cb + w) * M + j0 + r] : make_float2(0.f, 0.f);
+      an[w] = (w < nc && r < Mr) ? C[(size_t)(cb + w) * ldc + j0 + r] : make_float2(0.f, 0.f);
     for (; r < Mr; r += rstep) {
       float2 a[QB_CW];
 #pragma unroll
@@ -86,7 +86,7 @@ __device__ void qb_apply(float2* C, int M, int j0, int jb, int c0, int L, const 
       const int rn = r + rstep;
 #pragma unroll
       for (int w = 0; w < QB_CW; ++w)
-        if (w < nc && rn < Mr) an[w] = C[(size_t)(cb + w) * M + j0 + rn];
+        if (w < nc && rn < Mr) an[w] = C[(size_t)(cb + w) * ldc + j0 + rn];
       float2 v[QB_NB];
 #pragma unroll
       for (int i = 0; i < QB_NB; ++i) v[i] = (i < jb) ? Vs[i * ldv + r] : make_float2(0.f, 0.f);
@@ -165,7 +165,7 @@ __device__ void qb_apply(float2* C, int M, int j0, int jb, int c0, int L, const 
     float2 an[QB_CW];
 #pragma unroll
     for (int w = 0; w < QB_CW; ++w)
-      an[w] = (w < nc && r < Mr) ? C[(size_t)(cb + w) * M + j0 + r] : make_float2(0.f, 0.f);
+      an[w] = (w < nc && r < Mr) ? C[(size_t)(cb + w) * ldc + j0 + r] : make_float2(0.f, 0.f);
     for (; r < Mr; r += rstep) {
       float2 a[QB_CW];
 #pragma unroll
@@ -173,7 +173,7 @@ __device__ void qb_apply(float2* C, int M, int j0, int jb, int c0, int L, const 
       const int rn = r + rstep;
 #pragma unroll
       for (int w = 0; w < QB_CW; ++w)
-        if (w < nc && rn < Mr) an[w] = C[(size_t)(cb + w) * M + j0 + rn];
+        if (w < nc && rn < Mr) an[w] = C[(size_t)(cb + w) * ldc + j0 + rn];
       float2 v[QB_NB];
 #pragma unroll
       for (int i = 0; i < QB_NB; ++i) v[i] = (i < jb) ? Vs[i * ldv + r] : make_float2(0.f, 0.f);
@@ -185,7 +185,7 @@ __device__ void qb_apply(float2* C, int M, int j0, int jb, int c0, int L, const 
             a[w].x = fmaf(-v[i].x, w2[i][w].x, fmaf(v[i].y, w2[i][w].y, a[w].x));
             a[w].y = fmaf(-v[i].x, w2[i][w].y, fmaf(-v[i].y, w2[i][w].x, a[w].y));
           }
-          C[(size_t)(cb + w) * M + j0 + r] = a[w];
+          C[(size_t)(cb + w) * ldc + j0 + r] = a[w];
         }
       }
     }
@@ -193,34 +193,45 @@ __device__ void qb_apply(float2* C, int M, int j0, int jb, int c0, int L, const 
   __syncthreads();
 }
 
-// A: M x L column-major per instance (overwritten by R and the reflectors);
-// Q: M x L column-major output.  Requires M >= L and qb_smem_bytes(M, L) of
-// dynamic shared memory.
+// A: Mc x Lc column-major per instance (overwritten by R and the reflectors);
+// Q: Mc x Lc column-major output.  With dims, instance z factors only its own
+// rows (D.n when use_n, else D.m) and D.l columns of the zero-padded capacity
+// layout, and Q is [I; 0] outside them.  Requires Mc >= Lc and
+// qb_smem_bytes(Mc, Lc) of dynamic shared memory.
 template <int NT>
-__global__ void __launch_bounds__(NT) k_qr_blk_f32(float2* Abase, float2* Qbase, int M, int L) {
+__global__ void __launch_bounds__(NT) k_qr_blk_f32(float2* Abase, float2* Qbase, int Mc, int Lc,
+                                                  const Dims* __restrict__ dims, int use_n) {
   constexpr int NW = NT / 32;
   extern __shared__ __align__(16) unsigned char qb_raw[];
   __shared__ float2 vscale;
   __shared__ float vnorm;
-  const int ldv = M;
-  const int npan = (L + QB_NB - 1) / QB_NB;
+  const int ldv = Mc;  // shared memory is laid out for the capacity (Mc, Lc)
+  const int npan_c = (Lc + QB_NB - 1) / QB_NB;
   float2* Vs = reinterpret_cast<float2*>(qb_raw);
   float2* W = Vs + (size_t)QB_NB * ldv;
-  float2* W2 = W + QB_NB * L;
-  float2* Tall = W2 + QB_NB * L;
-  float* tau = reinterpret_cast<float*>(Tall + npan * QB_NB * QB_NB);
-  float* red = tau + L;
+  float2* W2 = W + QB_NB * Lc;
+  float2* Tall = W2 + QB_NB * Lc;
+  float* tau = reinterpret_cast<float*>(Tall + npan_c * QB_NB * QB_NB);
+  float* red = tau + Lc;
   float* fin = red + NW * QB_RED;
   const int z = blockIdx.x;
-  float2* A = Abase + (size_t)z * M * L;
-  float2* Qo = Qbase + (size_t)z * M * L;
+  int M = Mc, L = Lc;  // this instance's rows and columns
+  if (dims) {
+    const Dims D = dims[z];
+    if (!D.active) return;  // uniform over the block
+    M = use_n ? D.n : D.m;
+    L = D.l;
+  }
+  const int npan = (L + QB_NB - 1) / QB_NB;
+  float2* A = Abase + (size_t)z * Mc * Lc;
+  float2* Qo = Qbase + (size_t)z * Mc * Lc;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   for (int p = 0; p < npan; ++p) {
     const int j0 = p * QB_NB, jb = min(QB_NB, L - j0), Mr = M - j0;
     for (int e = tid; e < jb * Mr; e += NT) {
       const int i = e / Mr, r = e % Mr;
-      Vs[i * ldv + r] = A[(size_t)(j0 + i) * M + j0 + r];
+      Vs[i * ldv + r] = A[(size_t)(j0 + i) * Mc + j0 + r];
     }
     __syncthreads();
     // --- panel factorisation in shared memory
@@ -352,7 +363,7 @@ __global__ void __launch_bounds__(NT) k_qr_blk_f32(float2* Abase, float2* Qbase,
     // the R part so that Vs holds V with its zeros
     for (int e = tid; e < jb * Mr; e += NT) {
       const int i = e / Mr, r = e % Mr;
-      A[(size_t)(j0 + i) * M + j0 + r] = Vs[i * ldv + r];
+      A[(size_t)(j0 + i) * Mc + j0 + r] = Vs[i * ldv + r];
     }
     __syncthreads();
     for (int e = tid; e < jb * jb; e += NT) {
@@ -415,23 +426,23 @@ __global__ void __launch_bounds__(NT) k_qr_blk_f32(float2* Abase, float2* Qbase,
       __syncthreads();
     }
     // --- trailing columns: A <- A - V T^H V^H A
-    qb_apply<NT>(A, M, j0, jb, j0 + jb, L, Vs, ldv, Tall + p * QB_NB * QB_NB, true, W, W2, red);
+    qb_apply<NT>(A, Mc, M, j0, jb, j0 + jb, L, Vs, ldv, Tall + p * QB_NB * QB_NB, true, W, W2, red);
   }
 
   // --- Q = H_0 ... H_{L-1} [I; 0], panels backwards
-  for (int64_t e = tid; e < (int64_t)M * L; e += NT) {
-    const int c = (int)(e / M), r = (int)(e % M);
-    Qo[e] = make_float2(r == c ? 1.f : 0.f, 0.f);
+  for (int64_t e = tid; e < (int64_t)Mc * Lc; e += NT) {  // [I; 0] over the whole capacity
+    const int c = (int)(e / Mc), r = (int)(e % Mc);
+    Qo[e] = make_float2(r == c && c < L ? 1.f : 0.f, 0.f);
   }
   __syncthreads();
   for (int p = npan - 1; p >= 0; --p) {
     const int j0 = p * QB_NB, jb = min(QB_NB, L - j0), Mr = M - j0;
     for (int e = tid; e < jb * Mr; e += NT) {
       const int i = e / Mr, r = e % Mr;
-      Vs[i * ldv + r] = (r < i) ? make_float2(0.f, 0.f) : A[(size_t)(j0 + i) * M + j0 + r];
+      Vs[i * ldv + r] = (r < i) ? make_float2(0.f, 0.f) : A[(size_t)(j0 + i) * Mc + j0 + r];
     }
     __syncthreads();
-    qb_apply<NT>(Qo, M, j0, jb, j0, L, Vs, ldv, Tall + p * QB_NB * QB_NB, false, W, W2, red);
+    qb_apply<NT>(Qo, Mc, M, j0, jb, j0, L, Vs, ldv, Tall + p * QB_NB * QB_NB, false, W, W2, red);
   }
 }
 
@@ -457,25 +468,26 @@ static size_t g_attr_qr = 0, g_attr_qr256 = 0, g_attr_ld = 0, g_attr_fold[2][2] 
 // from four matrices per SM, two 256-thread CTAs from two.
 static size_t g_attr_qr128 = 0;
 
-cudaError_t launch_qr_blk_f32(float2* A, float2* Q, int M, int L, int batch, cudaStream_t st) {
+cudaError_t launch_qr_blk_f32(float2* A, float2* Q, int M, int L, int batch, cudaStream_t st, const Dims* dims,
+                              int use_n) {
   if (batch >= 4 * 152 && qb_smem_bytes(M, L, 4) <= 56 * 1024) {
     const size_t sm = qb_smem_bytes(M, L, 4);
     cudaError_t e = ensure_smem(k_qr_blk_f32<128>, sm, &g_attr_qr128);
     if (e != cudaSuccess) return e;
-    k_qr_blk_f32<128><<<batch, 128, sm, st>>>(A, Q, M, L);
+    k_qr_blk_f32<128><<<batch, 128, sm, st>>>(A, Q, M, L, dims, use_n);
     return cudaGetLastError();
   }
   if (batch >= 2 * 152 && qb_smem_bytes(M, L, 8) <= 112 * 1024) {
     const size_t sm = qb_smem_bytes(M, L, 8);
     cudaError_t e = ensure_smem(k_qr_blk_f32<256>, sm, &g_attr_qr256);
     if (e != cudaSuccess) return e;
-    k_qr_blk_f32<256><<<batch, 256, sm, st>>>(A, Q, M, L);
+    k_qr_blk_f32<256><<<batch, 256, sm, st>>>(A, Q, M, L, dims, use_n);
     return cudaGetLastError();
   }
   const size_t sm = qb_smem_bytes(M, L);
   cudaError_t e = ensure_smem(k_qr_blk_f32<QB_THREADS>, sm, &g_attr_qr);
   if (e != cudaSuccess) return e;
-  k_qr_blk_f32<QB_THREADS><<<batch, QB_THREADS, sm, st>>>(A, Q, M, L);
+  k_qr_blk_f32<QB_THREADS><<<batch, QB_THREADS, sm, st>>>(A, Q, M, L, dims, use_n);
   return cudaGetLastError();
 }
 
