@@ -518,7 +518,7 @@ static cudaError_t tc_product(const float* A0, const float* A1, const float* B0,
 static cudaError_t qr_f32(float2* A, float2* Q, int M, int L, int batch, const MixedPtrs& mp, const MixedSizes& s,
                           const Dims* dims, int use_n, cudaStream_t st) {
   if (!qr_blk_f32_fits(M, L) && mp.qscr && qr_multi_f32_fits(M, L))
-    return launch_qr_multi_f32(A, Q, mp.qscr, s.qs / sizeof(float2), M, L, batch, st);
+    return launch_qr_multi_f32(A, Q, mp.qscr, s.qs / sizeof(float2), M, L, batch, st, dims, use_n);
   ProfScope ps("k_qr_f32", st);
   if (qr_blk_f32_fits(M, L)) return launch_qr_blk_f32(A, Q, M, L, batch, st, dims, use_n);
   k_qr_f32<<<batch, 1024, 0, st>>>(A, Q, M, L);

@@ -49,11 +49,12 @@ cudaError_t launch_qr_blk_f32(float2* A, float2* Q, int M, int L, int batch, cud
                               const Dims* dims = nullptr, int use_n = 0);
 // The same QR spread over many CTAs per instance (qr_multi.cu), for matrices
 // too tall for the blocked kernel's shared memory; scr holds
-// qr_multi_f32_scratch(M, L) float2 per instance at the given stride.
+// qr_multi_f32_scratch(M, L) float2 per instance at the given stride; with
+// dims each instance is factored at its own size, as above.
 bool qr_multi_f32_fits(int M, int L);
 size_t qr_multi_f32_scratch(int M, int L);
 cudaError_t launch_qr_multi_f32(float2* A, float2* Q, float2* scr, size_t stride, int M, int L, int batch,
-                                cudaStream_t st);
+                                cudaStream_t st, const Dims* dims = nullptr, int use_n = 0);
 // Q_f (FP32, M x L) -> ptrs[z].Q (FP64) orthonormal to ~1e-13, spanning
 // range(Q_f); uses ptrs[z].R as scratch; usable when reorth_fits(M, L).
 bool reorth_fits(int M, int L);

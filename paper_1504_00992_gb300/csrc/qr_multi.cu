@@ -145,9 +145,10 @@ __device__ __forceinline__ R qm_bmax(R v, R* red) {
 // One instance as the kernels see it.
 template <typename Tc>
 struct QmView {
-  int M, L;
-  Tc* A;                         // M x L column-major, overwritten by the reflectors
-  Tc* Q;                         // M x L
+  int M, L;                      // rows and columns of this instance
+  int ld, Lq;                    // column stride of A and Q, and Q's stored columns (zero past L)
+  Tc* A;                         // M x L column-major (stride ld), overwritten by the reflectors
+  Tc* Q;                         // M x L (stride ld)
   typename QmReal<Tc>::R* tau;   // L
   Tc* T;                         // one QM_NB x QM_NB matrix per panel, T[a][b] at a * QM_NB + b
   Tc* Wp;                        // nch x QM_NB x L partial products
@@ -166,6 +167,8 @@ struct QmSrc64 {
     const ProbPtr P = ptrs[p];
     v.M = (QS == QR_Y) ? D.m : D.n;
     v.L = D.l;
+    v.ld = v.M;
+    v.Lq = v.L;
     v.A = (QS == QR_Y) ? P.Y : P.Yt;
     v.Q = (QS == QR_Y) ? P.Q : P.Qt;
     v.alph = P.J;
@@ -176,17 +179,29 @@ struct QmSrc64 {
   }
 };
 
-// FP32 instances of the TF32 form: every instance at (M, L), scratch in its
-// own slot of a separate array.
+// FP32 instances of the TF32 form: arrays laid out at the batch's capacity
+// (M, L) with each instance zero-padded past its own rows (D.n when use_n,
+// else D.m) and D.l columns, which it factors alone when dims is given;
+// scratch in its own slot of a separate array.
 struct QmSrc32 {
   float2* A;
   float2* Q;
   float2* scr;
   size_t stride;  // float2 elements of scratch per instance
   int M, L;
+  const Dims* dims;
+  int use_n;
   __device__ __forceinline__ bool get(int p, QmView<float2>& v) const {
     v.M = M;
     v.L = L;
+    if (dims) {
+      const Dims D = dims[p];
+      if (!D.active) return false;
+      v.M = use_n ? D.n : D.m;
+      v.L = D.l;
+    }
+    v.ld = M;
+    v.Lq = L;
     v.A = A + (size_t)p * M * L;
     v.Q = Q + (size_t)p * M * L;
     float2* s = scr + (size_t)p * stride;
@@ -244,7 +259,7 @@ __global__ void __cluster_dims__(QM_PC, 1, 1) __launch_bounds__(QM_PT) qm_panel_
   Tc pend_v = qm_c<Tc>(0, 0);
   for (int i = 0; i < jb; ++i) {
     const int j = j0 + i;
-    Tc* aj = v.A + (int64_t)j * M;
+    Tc* aj = v.A + (int64_t)j * v.ld;
     const int r0 = max(j, rlo);
     R s = 0;
     for (int r = r0 + tid; r < rhi; r += blockDim.x) {
@@ -322,7 +337,7 @@ __global__ void __cluster_dims__(QM_PC, 1, 1) __launch_bounds__(QM_PT) qm_panel_
       }
     }
     if (t != 0 && nc > 0) {
-      Tc* a1 = aj + M;  // column j + 1
+      Tc* a1 = aj + v.ld;  // column j + 1
       Tc dp[QM_NB - 1];
 #pragma unroll
       for (int q = 0; q < QM_NB - 1; ++q) dp[q] = qm_c<Tc>(0, 0);
@@ -330,7 +345,7 @@ __global__ void __cluster_dims__(QM_PC, 1, 1) __launch_bounds__(QM_PT) qm_panel_
         const Tc x = (r == j) ? v0 : aj[r];
 #pragma unroll
         for (int q = 0; q < QM_NB - 1; ++q)
-          if (q < nc) qm_fmac(dp[q], x, a1[(int64_t)q * M + r]);
+          if (q < nc) qm_fmac(dp[q], x, a1[(int64_t)q * v.ld + r]);
       }
 #pragma unroll
       for (int q = 0; q < QM_NB - 1; ++q) {
@@ -358,7 +373,7 @@ __global__ void __cluster_dims__(QM_PC, 1, 1) __launch_bounds__(QM_PT) qm_panel_
         const Tc x = (r == j) ? v0 : aj[r];
 #pragma unroll
         for (int q = 0; q < QM_NB - 1; ++q)
-          if (q < nc) qm_fms(a1[(int64_t)q * M + r], x, sd[q]);
+          if (q < nc) qm_fms(a1[(int64_t)q * v.ld + r], x, sd[q]);
       }
     }
     __syncthreads();  // the next column's loops read rows this column's loops gave other threads
@@ -384,10 +399,10 @@ __global__ void __launch_bounds__(QM_AT) qm_w(Src src, int j0) {
   if (c >= L) return;  // no block-wide synchronisation below
   const int rc = qm_rc(M, j0, nch);
   const int rlo = j0 + y * rc, rhi = min(M, rlo + rc);
-  const Tc* cc = (FORQ ? v.Q : v.A) + (int64_t)c * M;
+  const Tc* cc = (FORQ ? v.Q : v.A) + (int64_t)c * v.ld;
   const bool pcol = !FORQ && c < j0 + jb;
   const int rstart = max(rlo, pcol ? c : j0);
-  const Tc* V = v.A + (int64_t)j0 * M;
+  const Tc* V = v.A + (int64_t)j0 * v.ld;
   Tc acc[QM_NB];
 #pragma unroll
   for (int i = 0; i < QM_NB; ++i) acc[i] = qm_c<Tc>(0, 0);
@@ -395,7 +410,7 @@ __global__ void __launch_bounds__(QM_AT) qm_w(Src src, int j0) {
     const Tc x = cc[r];
 #pragma unroll
     for (int i = 0; i < QM_NB; ++i)
-      if (i < jb && r >= j0 + i) qm_fmac(acc[i], V[(int64_t)i * M + r], x);
+      if (i < jb && r >= j0 + i) qm_fmac(acc[i], V[(int64_t)i * v.ld + r], x);
   }
   Tc mine = qm_c<Tc>(0, 0);
 #pragma unroll
@@ -496,13 +511,13 @@ __global__ void __launch_bounds__(QM_AT) qm_upd(Src src, int j0) {
   for (int i = 0; i < QM_NB; ++i) w2r[i] = Wsh[i][warp];
   const int rc = qm_rc(M, j0, nch);
   const int rlo = j0 + y * rc, rhi = min(M, rlo + rc);
-  Tc* cc = (FORQ ? v.Q : v.A) + (int64_t)c * M;
-  const Tc* V = v.A + (int64_t)j0 * M;
+  Tc* cc = (FORQ ? v.Q : v.A) + (int64_t)c * v.ld;
+  const Tc* V = v.A + (int64_t)j0 * v.ld;
   for (int r = rlo + lane; r < rhi; r += 32) {
     Tc x = cc[r];
 #pragma unroll
     for (int i = 0; i < QM_NB; ++i)
-      if (i < jb && r >= j0 + i) qm_fms(x, V[(int64_t)i * M + r], w2r[i]);
+      if (i < jb && r >= j0 + i) qm_fms(x, V[(int64_t)i * v.ld + r], w2r[i]);
     cc[r] = x;
   }
 }
@@ -511,10 +526,10 @@ template <typename Tc, class Src>
 __global__ void qm_qinit(Src src) {
   QmView<Tc> v;
   if (!src.get(blockIdx.y, v)) return;
-  const int64_t total = (int64_t)v.M * v.L;
+  const int64_t total = (int64_t)v.ld * v.Lq;  // [I; 0] over the stored layout
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(e / v.M), r = (int)(e % v.M);
-    v.Q[e] = qm_c<Tc>(r == c ? 1 : 0, 0);
+    const int c = (int)(e / v.ld), r = (int)(e % v.ld);
+    v.Q[e] = qm_c<Tc>(r == c && c < v.L ? 1 : 0, 0);
   }
 }
 
@@ -602,10 +617,10 @@ size_t qr_multi_f32_scratch(int M, int L) {
 }
 
 cudaError_t launch_qr_multi_f32(float2* A, float2* Q, float2* scr, size_t stride, int M, int L, int batch,
-                                cudaStream_t st) {
+                                cudaStream_t st, const Dims* dims, int use_n) {
   if (stride < qr_multi_f32_scratch(M, L)) return cudaErrorInvalidValue;
   ProfScope ps("k_qr_f32[multi]", st);
-  return qm_run<float2, QmSrc32, true>(QmSrc32{A, Q, scr, stride, M, L}, batch, M, L, st);
+  return qm_run<float2, QmSrc32, true>(QmSrc32{A, Q, scr, stride, M, L, dims, use_n}, batch, M, L, st);
 }
 
 }  // namespace tg
