@@ -280,7 +280,8 @@ int rrsvd_execute(rrsvd_plan_t plan, const double* theta, int64_t chain0, double
 /* Same truncation from and to HOST buffers (same shapes): copies theta to
  * the device, runs, and copies the results back, all on `stream`, and
  * synchronises.  Device staging buffers and workspace are allocated on the
- * first call and kept by the plan. */
+ * first call and kept by the plan.  Page-locked host buffers let the copies
+ * run at the link's rate; pageable ones are staged by the CUDA runtime. */
 int rrsvd_execute_host(rrsvd_plan_t plan, const double* theta, int64_t chain0, double* sigma, double* U,
                        double* Vh, double* w, int* rank, void* stream);
 
@@ -290,8 +291,9 @@ const char* rrsvd_last_error(rrsvd_plan_t plan);
 /* ------------------------------------------------------------------------
  * Kernel timing (tracing aid).  When enabled, every kernel launch of the
  * library is bracketed by CUDA events on its stream, grouped by kernel class
- * (e.g. "k_zgemm[sketch]", "k_qr", "k_jacobi").  Process-wide; not to be
- * enabled while a stream is being captured into a CUDA graph.
+ * (e.g. "k_zgemm[sketch]", "k_qr", "k_jacobi"; the copies of
+ * rrsvd_execute_host as "copy[h2d]" and "copy[d2h]").  Process-wide; not to
+ * be enabled while a stream is being captured into a CUDA graph.
  * ---------------------------------------------------------------------- */
 int tebd_profiler_enable(int enable);
 /* Drops all accumulated timings. */
