@@ -307,13 +307,13 @@ extern "C" int tebd_create_multi(int n_chains, const tebd_desc_t* descs, tebd_t*
     C.d.resize(N);
     for (int s = 0; s < N; ++s) {
       const int ds = dc.d_site ? dc.d_site[s] : dc.d;
-      if (ds < 2 || ds > 64) { delete h; return TEBD_EINVAL; }
+      if (ds < 2 || ds > 64) { tebd_free(h); return TEBD_EINVAL; }
       C.d[s] = ds;
     }
     C.chi_cap.resize(N - 1);
     for (int b = 0; b < N - 1; ++b) {
       const int cc = dc.chi_bond ? dc.chi_bond[b] : dc.chi_max;
-      if (cc < 1) { delete h; return TEBD_EINVAL; }
+      if (cc < 1) { tebd_free(h); return TEBD_EINVAL; }
       C.chi_cap[b] = cc;
     }
     // chi_b <= min(cap_b, prod_{s<=b} d_s, prod_{s>b} d_s)
@@ -374,7 +374,7 @@ extern "C" int tebd_create_multi(int n_chains, const tebd_desc_t* descs, tebd_t*
       for (int b = par; b < C.N - 1; b += 2) {
         int mc, nc, kc, lc;
         bond_caps(C, b, mc, nc, kc, lc);
-        if (lc > 512) { delete h; return TEBD_ENOTIMPL; }
+        if (lc > 512) { tebd_free(h); return TEBD_ENOTIMPL; }
         ps.bonds.push_back({c, b});
       }
     }
@@ -447,7 +447,8 @@ extern "C" int tebd_create_multi(int n_chains, const tebd_desc_t* descs, tebd_t*
   h->arena_bytes = off;
   if (cudaMalloc(&h->arena, h->arena_bytes) != cudaSuccess) {
     cudaGetLastError();
-    delete h;
+    h->arena = nullptr;
+    tebd_free(h);  // also the stream of our own
     return TEBD_ENOMEM;
   }
   char* A = h->arena;
