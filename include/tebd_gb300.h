@@ -134,6 +134,16 @@ int tebd_select_chain(tebd_t h, int chain);
 /* Device bytes held by the handle and the number of waves per parity. */
 int tebd_workspace_info(tebd_t h, size_t* arena_bytes, int* waves_even, int* waves_odd);
 
+/* The plan tebd_create_multi(n_chains, descs, ...) would make, without
+ * creating a handle: the device bytes it would allocate and its waves per
+ * parity (what tebd_workspace_info reports for that handle).  Host only: no
+ * CUDA call and no GPU needed, so a caller can size workspace_budget before
+ * creating.  Any output pointer may be NULL.
+ * Errors: as tebd_create_multi's argument checks (TEBD_EINVAL, TEBD_ENOTIMPL);
+ * on error the outputs are left unchanged. */
+int tebd_plan_query(int n_chains, const tebd_desc_t* descs, size_t* arena_bytes, int* waves_even,
+                    int* waves_odd);
+
 /* Frees all device and host memory of the handle (NULL is accepted). */
 int tebd_destroy(tebd_t h);
 

@@ -59,6 +59,7 @@ _SIGS = {
     "tebd_num_chains": (_i, [_vp, _pi]),
     "tebd_select_chain": (_i, [_vp, _i]),
     "tebd_workspace_info": (_i, [_vp, ctypes.POINTER(ctypes.c_size_t), _pi, _pi]),
+    "tebd_plan_query": (_i, [_i, ctypes.POINTER(TebdDesc), ctypes.POINTER(ctypes.c_size_t), _pi, _pi]),
     "tebd_destroy": (_i, [_vp]),
     "tebd_set_stream": (_i, [_vp, _vp]),
     "tebd_set_product_state": (_i, [_vp, _pd]),
@@ -176,6 +177,20 @@ def tebd_create_multi(chains, p, q, seed, precision=TEBD_PREC_FP64, sv_cutoff=0.
     if rc != TEBD_OK:
         raise TebdError(rc, "tebd_create_multi")
     return h
+
+
+def tebd_plan_query(chains, p, q, seed, precision=TEBD_PREC_FP64, autotune=0, workspace_budget=0):
+    """The (arena bytes, waves even, waves odd) that tebd_create_multi would
+    plan for these chains, computed on the host without a GPU."""
+    arr = (TebdDesc * max(1, len(chains)))()
+    for c, (N, d_site, chi_bond) in enumerate(chains):
+        arr[c] = _desc(N, d_site, chi_bond, p, q, seed, precision, 0.0, 0, 0, autotune, workspace_budget)
+    b, we, wo = ctypes.c_size_t(), ctypes.c_int(), ctypes.c_int()
+    rc = load().tebd_plan_query(len(chains), arr, ctypes.byref(b), ctypes.byref(we), ctypes.byref(wo))
+    _KEEP.clear()
+    if rc != TEBD_OK:
+        raise TebdError(rc, "tebd_plan_query")
+    return b.value, we.value, wo.value
 
 
 def tebd_num_chains(h):

@@ -270,9 +270,19 @@ static int tune_wave(const ParitySet& ps, Wave& w, cudaStream_t st, Dims* scratc
 
 static int tebd_reset_state(tebd_t h, int slot, const double* psi);
 
-extern "C" int tebd_create_multi(int n_chains, const tebd_desc_t* descs, tebd_t* out) {
-  if (!out) return TEBD_EINVAL;
-  *out = nullptr;
+// Byte offsets of the handle's arena, from the plan of tebd_create_multi.
+struct HandlePlan {
+  size_t one_off = 0, st_off = 0, wacc_off = 0, sweep_off = 0, tcerr_off = 0, op_off = 0, wout_off = 0;
+  size_t desc_off = 0, desc_per = 0, ws_off = 0, mixed_off = 0, total = 0;
+  std::vector<WsLayout> lay[2];
+  int max_batch = 0;
+};
+
+// Validates the chain descriptors and plans the handle on the host: the
+// chains' capacities and Gamma/lambda/gate regions, the bonds of each parity
+// (grouped by shape in the mixed form), their waves under the workspace
+// budget and the arena's offsets.  Makes no CUDA call.
+static int plan_handle(tebd_s* h, int n_chains, const tebd_desc_t* descs, HandlePlan& lay_plan) {
   if (n_chains < 1 || !descs) return TEBD_EINVAL;
   const tebd_desc_t& d0 = descs[0];
   if (d0.p < 0 || d0.q < 0) return TEBD_EINVAL;
@@ -283,19 +293,12 @@ extern "C" int tebd_create_multi(int n_chains, const tebd_desc_t* descs, tebd_t*
     if (dc.N < 2 || dc.p != d0.p || dc.q != d0.q || dc.seed != d0.seed || dc.precision != d0.precision)
       return TEBD_EINVAL;
   }
-  tebd_s* h = new tebd_s();
   h->p = d0.p;
   h->q = d0.q;
   h->seed = d0.seed;
   h->precision = d0.precision;
   h->cutoff = d0.sv_cutoff > 0 ? d0.sv_cutoff : 1e-14;
   h->use_graph = d0.use_graph != 0;
-  if (h->use_graph) {
-    // the legacy default stream cannot be captured: run on a blocking stream
-    // of our own (it still orders with stream 0)
-    if (cudaStreamCreate(&h->own_stream) != cudaSuccess) { cudaGetLastError(); delete h; return TEBD_ECUDA; }
-    h->stream = h->own_stream;
-  }
   h->ch.resize(n_chains);
   size_t off = 0;
   for (int c = 0; c < n_chains; ++c) {
@@ -307,13 +310,13 @@ extern "C" int tebd_create_multi(int n_chains, const tebd_desc_t* descs, tebd_t*
     C.d.resize(N);
     for (int s = 0; s < N; ++s) {
       const int ds = dc.d_site ? dc.d_site[s] : dc.d;
-      if (ds < 2 || ds > 64) { tebd_free(h); return TEBD_EINVAL; }
+      if (ds < 2 || ds > 64) { return TEBD_EINVAL; }
       C.d[s] = ds;
     }
     C.chi_cap.resize(N - 1);
     for (int b = 0; b < N - 1; ++b) {
       const int cc = dc.chi_bond ? dc.chi_bond[b] : dc.chi_max;
-      if (cc < 1) { tebd_free(h); return TEBD_EINVAL; }
+      if (cc < 1) { return TEBD_EINVAL; }
       C.chi_cap[b] = cc;
     }
     // chi_b <= min(cap_b, prod_{s<=b} d_s, prod_{s>b} d_s)
@@ -347,16 +350,16 @@ extern "C" int tebd_create_multi(int n_chains, const tebd_desc_t* descs, tebd_t*
     C.int_off = off;
     off += 3 * align_up(sizeof(int) * (N + 1));
   }
-  const size_t one_off = off; off += ALIGN;
-  const size_t st_off = off; off += ALIGN;
-  const size_t wacc_off = off; off += align_up(sizeof(double) * 2 * n_chains);
-  const size_t sweep_off = off; off += ALIGN;
-  const size_t tcerr_off = off; off += ALIGN;
-  const size_t op_off = off; off += align_up(sizeof(cplx) * 64 * 64) + ALIGN;
+  lay_plan.one_off = off; off += ALIGN;
+  lay_plan.st_off = off; off += ALIGN;
+  lay_plan.wacc_off = off; off += align_up(sizeof(double) * 2 * n_chains);
+  lay_plan.sweep_off = off; off += ALIGN;
+  lay_plan.tcerr_off = off; off += ALIGN;
+  lay_plan.op_off = off; off += align_up(sizeof(cplx) * 64 * 64) + ALIGN;
   // problems of each parity, chain-major, and their waves under the budget
   const size_t budget = d0.workspace_budget;
   size_t ws_max = 0;
-  std::vector<WsLayout> lay[2];
+  std::vector<WsLayout>* lay = lay_plan.lay;
   std::vector<size_t> pbytes[2];
   int max_batch = 0;
   const bool tf32 = h->precision == TEBD_PREC_TF32;
@@ -374,7 +377,7 @@ extern "C" int tebd_create_multi(int n_chains, const tebd_desc_t* descs, tebd_t*
       for (int b = par; b < C.N - 1; b += 2) {
         int mc, nc, kc, lc;
         bond_caps(C, b, mc, nc, kc, lc);
-        if (lc > 512) { tebd_free(h); return TEBD_ENOTIMPL; }
+        if (lc > 512) { return TEBD_ENOTIMPL; }
         ps.bonds.push_back({c, b});
       }
     }
@@ -436,15 +439,56 @@ extern "C" int tebd_create_multi(int n_chains, const tebd_desc_t* descs, tebd_t*
         mixed_max = std::max(mixed_max, mixed_bytes(wv.ms, wv.count));
       }
   }
-  const size_t wout_off = off; off += align_up(sizeof(double) * std::max(1, max_batch));
-  const size_t desc_off = off;
-  const size_t desc_per = align_up(sizeof(Dims) * std::max(1, max_batch)) + align_up(sizeof(ProbPtr) * std::max(1, max_batch));
-  off += 2 * desc_per + align_up(sizeof(Dims) * std::max(1, max_batch));  // + autotuner scratch dims
-  const size_t ws_off = off;
+  lay_plan.wout_off = off; off += align_up(sizeof(double) * std::max(1, max_batch));
+  lay_plan.desc_off = off;
+  lay_plan.desc_per = align_up(sizeof(Dims) * std::max(1, max_batch)) + align_up(sizeof(ProbPtr) * std::max(1, max_batch));
+  off += 2 * lay_plan.desc_per + align_up(sizeof(Dims) * std::max(1, max_batch));  // + autotuner scratch dims
+  lay_plan.ws_off = off;
   off += ws_max;
-  const size_t mixed_off = off;
+  lay_plan.mixed_off = off;
   off += align_up(mixed_max);
+  lay_plan.total = off;
+  lay_plan.max_batch = max_batch;
   h->arena_bytes = off;
+  return TEBD_OK;
+}
+
+extern "C" int tebd_plan_query(int n_chains, const tebd_desc_t* descs, size_t* arena_bytes, int* waves_even,
+                               int* waves_odd) {
+  tebd_s* h = new tebd_s();
+  HandlePlan lay_plan;
+  const int rc = plan_handle(h, n_chains, descs, lay_plan);
+  if (rc == TEBD_OK) {
+    if (arena_bytes) *arena_bytes = lay_plan.total;
+    if (waves_even) *waves_even = (int)h->par[0].waves.size();
+    if (waves_odd) *waves_odd = (int)h->par[1].waves.size();
+  }
+  delete h;
+  return rc;
+}
+
+extern "C" int tebd_create_multi(int n_chains, const tebd_desc_t* descs, tebd_t* out) {
+  if (!out) return TEBD_EINVAL;
+  *out = nullptr;
+  tebd_s* h = new tebd_s();
+  HandlePlan lay_plan;
+  {
+    const int rc = plan_handle(h, n_chains, descs, lay_plan);
+    if (rc != TEBD_OK) { delete h; return rc; }
+  }
+  const tebd_desc_t& d0 = descs[0];
+  const bool tf32 = h->precision == TEBD_PREC_TF32;
+  const std::vector<WsLayout>* lay = lay_plan.lay;
+  const int max_batch = lay_plan.max_batch;
+  const size_t one_off = lay_plan.one_off, st_off = lay_plan.st_off, wacc_off = lay_plan.wacc_off, sweep_off = lay_plan.sweep_off,
+               tcerr_off = lay_plan.tcerr_off, op_off = lay_plan.op_off, wout_off = lay_plan.wout_off, desc_off = lay_plan.desc_off,
+               desc_per = lay_plan.desc_per, ws_off = lay_plan.ws_off, mixed_off = lay_plan.mixed_off;
+  if (h->use_graph) {
+    // the legacy default stream cannot be captured: run on a blocking stream
+    // of our own (it still orders with stream 0)
+    if (cudaStreamCreate(&h->own_stream) != cudaSuccess) { cudaGetLastError(); delete h; return TEBD_ECUDA; }
+    h->stream = h->own_stream;
+  }
   if (cudaMalloc(&h->arena, h->arena_bytes) != cudaSuccess) {
     cudaGetLastError();
     h->arena = nullptr;

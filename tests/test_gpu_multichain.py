@@ -80,6 +80,10 @@ def test_graph_waves_and_autotune_change_nothing(lib):
         got, info = _run_multi(B, *args, **kw)
         if "workspace_budget" in kw:
             assert info[1] > 1 and info[2] > 1       # the budget split the sweeps into waves
+        # the host-only plan is the plan the handle was created with
+        chains = [(N, [d] * N, [chi] * (N - 1)) for N, d, chi, _ in specs]
+        assert B.tebd_plan_query(chains, 3, 2, 4, autotune=kw.get("autotune", 0),
+                                 workspace_budget=kw.get("workspace_budget", 0)) == info
         for (e0, l0, w0), (e1, l1, w1) in zip(base, got):
             assert np.array_equal(e0, e1)
             assert all(np.array_equal(a, b) for a, b in zip(l0, l1))
