@@ -32,7 +32,7 @@
  *     returns; the caller keeps its buffers.  Outputs go to caller buffers.
  *     Device pointers passed to rrsvd_execute stay owned by the caller.
  *
- * The sketch matrix Omega (Alg. 1 step 1) is drawn from Philox4x64-10
+ * The sketch matrix Omega of Alg. 1 is drawn from Philox4x64-10
  * (Salmon et al., SC'11): element (r, c) of the n x l matrix uses counter
  * (r*l + c, bond, sweep, chain) and key (seed, 0); the 64-bit words w0, w1
  * become u = ((w >> 12) + 0.5) 2^-52 and Box-Muller gives

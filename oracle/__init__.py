@@ -8,7 +8,7 @@ method's arithmetic.
 
 Modules
   philox   Philox4x64-10 counter-based generator and the complex Gaussian
-           sketch matrix Omega drawn from it (Section IV, Alg. 1 step 1).
+           sketch matrix Omega drawn from it (Section IV, Alg. 1).
   rrsvd    Randomized SVD with power iterations (Alg. 1) followed by the
            projection B = Q^H A, the SVD of B and U = Q U~ (Section IV, steps
            i-iii); exact dense-SVD truncation (Eckart-Young, Section IV).

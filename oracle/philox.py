@@ -3,7 +3,7 @@
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 
 The paper draws the columns of Omega with independent standard Gaussian
-entries (Section IV, Alg. 1 step 1) and notes that the method does not depend
+entries (Section IV, Alg. 1) and notes that the method does not depend
 on the quality of the generator.  To make the CPU oracle and the GPU path use
 the identical Omega, both implement the same counter-based generator from its
 published definition: Philox4x64 with 10 rounds (Salmon, Moraes, Dror, Shaw,
@@ -85,7 +85,7 @@ def uniform53(w):
 
 
 def gaussian_omega(n, l, seed, bond=0, sweep=0, chain=0, stream=0):
-    """The n x l complex Gaussian sketch matrix of Alg. 1 step 1.
+    """The n x l complex Gaussian sketch matrix of Alg. 1.
 
     Real and imaginary parts are iid N(0, 1) (the paper's "standard Gaussian",
     read per component for complex A).

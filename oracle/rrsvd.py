@@ -149,7 +149,7 @@ def accuracy_check(A, Q, r, eps, l_max, seed, bond=0, sweep=0, chain=0):
 
 
 def rrsvd_fixed_precision(A, Omega, q, r, eps, l_max, p, seed, bond=0, sweep=0, chain=0):
-    """Alg. 1 steps 1-3, the accuracy check of Alg. 2 on Q0, the q power
+    """Alg. 1's sketch and first basis, the accuracy check of Alg. 2 on Q0, the q power
     iterations of Alg. 1 on the (possibly enlarged) basis, then steps i-iii.
     The kept rank follows the basis: k = l - p.  Returns (U, s, Vh, l, k,
     exact Frobenius residual of the final Q)."""

@@ -1,6 +1,6 @@
 // Accuracy check (Alg. 2) and the fixed-precision RRSVD built on it, FP64.
 //
-// After Alg. 1 step 3 (Q0 = orth(A Omega)), every round draws r Gaussian
+// After the first basis of Alg. 1 (Q0 = orth(A Omega)), every round draws r Gaussian
 // probes Omega_r (Philox stream 1, element (j, c) of round t at counter
 // (t n + j) r + c), forms Br = A Omega_r and D = (I - Q Q^H) Br, and takes
 // MAX = max_i ||d_i||.  If MAX > eps the probes' images join the basis

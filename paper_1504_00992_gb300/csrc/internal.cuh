@@ -130,7 +130,7 @@ cudaError_t run_rrsvd(const Dims* dims, const ProbPtr* ptrs, int batch, const Ca
                       uint64_t sweep, int64_t chain0, int chain_stride, int* status, cudaStream_t st,
                       const uint64_t* sweep_dev = nullptr, const int* tiles = nullptr);
 
-// Accuracy check (Alg. 2) rounds between Alg. 1 step 3 and the power
+// Accuracy check (Alg. 2) rounds between the first basis of Alg. 1 and the power
 // iterations: rounds = host bound on the number of rounds; l grows on the
 // device; eps the threshold; stream-1 Philox probes.
 cudaError_t run_accuracy_check(const Dims* dims_mut, const ProbPtr* ptrs, int batch, const Caps& cap, int rounds,

@@ -1,4 +1,4 @@
-"""Pins of the oracle's counter-based generator (Alg. 1 step 1 draws Omega).
+"""Pins of the oracle's counter-based generator (Alg. 1 draws Omega from it).
 
 The oracle's Philox4x64-10 is checked against NumPy's Philox bit generator, an
 independent implementation of the same published definition (NumPy advances
