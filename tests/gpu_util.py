@@ -9,12 +9,17 @@ def torch_cuda():
 
 
 def rrsvd_device(B, plan, theta, chain0=0, want_uv=True):
-    """Runs rrsvd_execute on device buffers; returns numpy results."""
+    """Runs rrsvd_execute on device buffers; returns numpy results.  theta is
+    a host array, or a contiguous complex128 tensor already on the device."""
     torch = torch_cuda()
     batch, m, n = theta.shape
     k, l = B.rrsvd_plan_dims(plan)
     dev = torch.device("cuda:0")
-    th = torch.from_numpy(np.ascontiguousarray(theta)).to(dev)
+    if isinstance(theta, torch.Tensor):
+        assert theta.is_cuda and theta.is_contiguous() and theta.dtype == torch.complex128
+        th = theta
+    else:
+        th = torch.from_numpy(np.ascontiguousarray(theta)).to(dev)
     sg = torch.zeros((batch, k), dtype=torch.float64, device=dev)
     U = torch.zeros((batch, m, k), dtype=torch.complex128, device=dev) if want_uv else None
     Vh = torch.zeros((batch, k, n), dtype=torch.complex128, device=dev) if want_uv else None
@@ -37,3 +42,12 @@ def rrsvd_device(B, plan, theta, chain0=0, want_uv=True):
 
 def truncated(U, s, Vh):
     return (U * s[None, :]) @ Vh
+
+
+def repeat_on_device(base, batch):
+    """A batch of `batch` matrices on the device, instance t = base[t % len(base)]
+    (full-size batches without holding every copy in host memory)."""
+    torch = torch_cuda()
+    b = torch.from_numpy(np.ascontiguousarray(np.stack(base))).to("cuda:0")
+    idx = torch.arange(batch, device=b.device) % len(base)
+    return b[idx].contiguous()
