@@ -39,3 +39,34 @@ def test_traffic_only_from_a_matching_capture():
 
 def test_unknown_dominant_kernel_has_no_roofline():
     assert bench.roofline(_res({"k_jacobi": (40.0, 1)}), 152) is None
+
+
+def _bench(args, env_extra=None):
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, **(env_extra or {}))
+    return subprocess.run([sys.executable, os.path.join(root, "bench.py"), *args], capture_output=True, text=True,
+                          cwd=root, env=env, timeout=600)
+
+
+def test_reference_arm_prints_its_line_on_the_host():
+    """bench.py --impl reference: the oracle timed on the host cores on a
+    bounded sample of the single-bond stress workload, one JSON line with the
+    contract's keys; no GPU involved."""
+    r = _bench(["--impl", "reference", "--steps", "1", "--warmup", "1"])
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == "bond updates/s"
+    assert d["higher_is_better"] is True and d["steps"] == 1 and d["warmup"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert "2000x2000" in d["config"]["workload"]
+
+
+def test_reference_arm_other_ranks_exit_without_work():
+    r = _bench(["--impl", "reference", "--steps", "1", "--warmup", "1"], {"RANK": "1", "WORLD_SIZE": "2"})
+    assert r.returncode == 0 and r.stdout.strip() == ""
