@@ -67,7 +67,7 @@ enum {
  *     in TF32 with FP32 accumulation and FP32 QR; power round q (Y0 when
  *     q = 0) as the refinement pass in split 3xTF32 products (FP32-level
  *     accuracy); the last basis re-orthonormalised FP64-accurately (FP32
- *     QR and a double-float Loewdin correction; FP64 QR when l > 512);
+ *     QR and a double-float Loewdin correction);
  *     B = Q^H A, U and V FP64-accurate in double-float arithmetic; the QR
  *     of B^H, the Jacobi SVD and lambda in FP64.  Omega comes from the same
  *     Philox words by an FP32 Box-Muller.  Standalone RRSVD plans and TEBD

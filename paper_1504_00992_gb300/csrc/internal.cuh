@@ -146,7 +146,8 @@ cudaError_t launch_finalize_checked(const Dims* dims, const ProbPtr* ptrs, int b
                                     cudaStream_t st);
 cudaError_t launch_checked_init(Dims* dims, int batch, const Dims& tmpl, cudaStream_t st);
 
-// Double-float (FP32-pair) variant of the FP64 GEMM for G_BH, G_U, G_V.
+// Double-float (FP32-pair) variant of the FP64 GEMM for G_U and G_V (U = Q J_k,
+// V = Qb W_k of the mixed form); other stages return cudaErrorInvalidValue.
 cudaError_t launch_zgemm_df(int stage, const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap,
                             cudaStream_t st);
 

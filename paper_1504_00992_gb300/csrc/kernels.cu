@@ -341,9 +341,8 @@ static cudaError_t launch_zgemm_df_stage(int rows, int cols, const Dims* dims, c
 
 cudaError_t launch_zgemm_df(int stage, const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap,
                             cudaStream_t st) {
-  ProfScope ps((stage == G_U || stage == G_V) ? "k_zgemm_df[uv]" : "k_zgemm_df[project]", st);
+  ProfScope ps("k_zgemm_df[uv]", st);
   switch (stage) {
-    case G_BH: return launch_zgemm_df_stage<G_BH>(cap.n, cap.l, dims, ptrs, batch, st);
     case G_U: return launch_zgemm_df_stage<G_U>(cap.m, cap.k, dims, ptrs, batch, st);
     case G_V: return launch_zgemm_df_stage<G_V>(cap.n, cap.k, dims, ptrs, batch, st);
   }

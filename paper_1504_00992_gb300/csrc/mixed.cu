@@ -8,10 +8,10 @@
 //                                           products (FP32-level accuracy);
 //   last QR                                : FP32 blocked Householder and an
 //                                           FP64-accurate re-orthonormalisation
-//                                           (qr_blocked.cu), or FP64 Householder
-//                                           when l > 512 or m < l;
-//   B^H = A^H Q, U = Q J_k, V = Qb W_k      : double-float GEMM on the FP32 pipes
-//                                           (FP32 pairs, ~1e-14 relative);
+//                                           (qr_blocked.cu; l <= 512);
+//   B^H = A^H Q, U = Q J_k, V = Qb W_k      : double-float products on the FP32
+//                                           pipes (df_proj.cu for B^H, k_zgemm_df
+//                                           for U and V; ~1e-14 relative);
 //   QR of B^H, Jacobi SVD                   : FP64 (the existing kernels).
 //
 // Complex products use the real embedding: A (M x K complex) becomes the
@@ -367,22 +367,6 @@ __global__ void __launch_bounds__(1024) k_qr_f32(float2* Abase, float2* Qbase, i
   }
 }
 
-// Yf (FP32, capacity mc x lc) -> the compact FP64 buffer Y (m x l) of the final QR.
-__global__ void k_f32_to_f64(const float2* __restrict__ Yf, const Dims* __restrict__ dims,
-                             const ProbPtr* __restrict__ ptrs, int mc, int lc) {
-  const int z = blockIdx.y;
-  const Dims D = dims[z];
-  if (!D.active) return;
-  const float2* y = Yf + (size_t)z * mc * lc;
-  cplx* Y = ptrs[z].Y;
-  const int64_t total = (int64_t)D.m * D.l;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(e / D.m), r = (int)(e % D.m);
-    const float2 v = y[(int64_t)c * mc + r];
-    Y[e] = cmk((double)v.x, (double)v.y);
-  }
-}
-
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -577,20 +561,13 @@ cudaError_t run_rrsvd_mixed(const Dims* dims, const ProbPtr* ptrs, int batch, co
     MX_TRY(conv_bt(mp.Qtf, dims, mp, n, l, s.K1, s, np == 3, batch, st));
     MX_TRY(tc_product(mp.thf_hi, mp.thf_lo, mp.bt_hi, mp.bt_lo, m, s.K1, s, l, np, mp.Yf, batch, err, st));  // A Q~
   }
-  if (reorth_fits(m, l)) {
-    // last QR: FP32 Householder, then the FP64-accurate re-orthonormalisation
-    MX_TRY(qr_f32(mp.Yf, mp.Qf, m, l, batch, mp, s, dims, 0, st));
-    MX_TRY(launch_reorth(mp.Qf, mp.Df, dims, ptrs, m, l, batch, status, st));
-    MX_TRY(launch_proj_df(mp.thd, dims, ptrs, mp.Qf, mp.Df, m, n, l, batch, st));  // B^H = A^H Q
-  } else {
-    {
-      ProfScope ps("k_f32_to_f64", st);
-      k_f32_to_f64<<<dim3(grid1d((int64_t)m * l), batch), 256, 0, st>>>(mp.Yf, dims, ptrs, m, l);
-      MX_TRY(cudaGetLastError());
-    }
-    MX_TRY(launch_qr_sized(QR_Y, dims, ptrs, batch, cap, st));  // last QR in FP64
-    MX_TRY(launch_zgemm_df(G_BH, dims, ptrs, batch, cap, st));  // B^H = A^H Q (double-float)
-  }
+  // last QR: FP32 Householder, then the FP64-accurate re-orthonormalisation.
+  // Plans and handles refuse sketches wider than 512 columns, and l <= m, so
+  // every basis they pass fits it.
+  if (!reorth_fits(m, l)) return cudaErrorInvalidValue;
+  MX_TRY(qr_f32(mp.Yf, mp.Qf, m, l, batch, mp, s, dims, 0, st));
+  MX_TRY(launch_reorth(mp.Qf, mp.Df, dims, ptrs, m, l, batch, status, st));
+  MX_TRY(launch_proj_df(mp.thd, dims, ptrs, mp.Qf, mp.Df, m, n, l, batch, st));  // B^H = A^H Q
   MX_TRY(launch_qr_sized(QR_BH, dims, ptrs, batch, cap, st));
   MX_TRY(launch_jacobi_sized(dims, ptrs, batch, cap, status, st));
   MX_TRY(launch_zgemm_df(G_U, dims, ptrs, batch, cap, st));
