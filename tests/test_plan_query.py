@@ -105,3 +105,16 @@ def test_argument_errors():
     assert nb.value == 7  # outputs untouched on error
     assert L.tebd_plan_query(0, arr, None, None, None) == B.TEBD_EINVAL
     assert L.tebd_plan_query(1, None, None, None, None) == B.TEBD_EINVAL
+
+
+def test_a_handle_larger_than_any_device_reports_enomem():
+    """Allocation failure reported as a status, not a crash: 20 chains of 60 sites with d = 64 and caps of 500 plan a 20 TB
+    arena, more than any device holds, so creation fails with TEBD_ENOMEM and
+    returns no handle.  Without a device the allocation fails the same way,
+    so this runs on the host too."""
+    chains = [_chain(60, 64, 500)] * 20
+    arena, _, _ = B.tebd_plan_query(chains, 10, 2, 0)
+    assert arena > 10 * (1 << 40)
+    with pytest.raises(B.TebdError) as e:
+        B.tebd_create_multi(chains, 10, 2, 0)
+    assert e.value.code == B.TEBD_ENOMEM
