@@ -108,10 +108,11 @@ def test_argument_errors():
 
 
 def test_a_handle_larger_than_any_device_reports_enomem():
-    """Allocation failure reported as a status, not a crash: 20 chains of 60 sites with d = 64 and caps of 500 plan a 20 TB
-    arena, more than any device holds, so creation fails with TEBD_ENOMEM and
-    returns no handle.  Without a device the allocation fails the same way,
-    so this runs on the host too."""
+    """Allocation failure is reported as a status, not a crash: 20 chains of
+    60 sites with d = 64 and caps of 500 plan a 20 TB arena, more than any
+    device holds, so creation fails with TEBD_ENOMEM and returns no handle.
+    Without a device the allocation fails the same way, so this runs on the
+    host too."""
     chains = [_chain(60, 64, 500)] * 20
     arena, _, _ = B.tebd_plan_query(chains, 10, 2, 0)
     assert arena > 10 * (1 << 40)
