@@ -314,6 +314,36 @@ int tebd_profiler_reset(void);
 int tebd_profiler_read(int max_entries, char* names, double* total_ms, int64_t* launches, int* count);
 
 /* ------------------------------------------------------------------------
+ * The sketch generator (Section IV, Alg. 1: Omega "drawn from the Gaussian
+ * distribution"), exported so that its output can be checked against an
+ * independent implementation of the same published generator.  Both calls
+ * run the device functions the sketch kernels call, on device buffers owned
+ * by the caller, asynchronously on `stream`; they allocate nothing.
+ * ---------------------------------------------------------------------- */
+
+/* Philox4x64-10 blocks: for i < count, counter (counters[4i], ..., [4i+3])
+ * and key (key0, key1) give words[4i .. 4i+3].  counters and words are
+ * device arrays of 4 * count uint64_t.
+ * Errors: TEBD_EINVAL (count < 0, NULL buffer with count > 0), TEBD_ECUDA. */
+int tebd_philox4x64_10(const uint64_t* counters, int64_t count, uint64_t key0, uint64_t key1, uint64_t* words,
+                       void* stream);
+
+/* The n x l sketch matrix of a truncation, row-major into `out` (device):
+ * element (r, c) from counter (r*l + c, bond, sweep, chain), key (seed, 0),
+ * as described at the top of this header.
+ *   TEBD_PREC_FP64: complex128 (2 doubles per element), the Omega of the
+ *     FP64 form: u = ((w >> 12) + 0.5) 2^-52, Box-Muller in FP64.
+ *   TEBD_PREC_TF32: complex64 (2 floats per element), the Omega of the mixed
+ *     form before its TF32 rounding: u = ((w >> 40) + 0.5) 2^-24, Box-Muller
+ *     in FP32.
+ * Standalone plans use bond 0, sweep 0 and chain chain0 + instance; TEBD
+ * handles use the bond index, the handle's sweep count at the step and the
+ * chain index.  Errors: TEBD_EINVAL (negative size or index, NULL out with
+ * n l > 0), TEBD_ENOTIMPL (precision), TEBD_ECUDA. */
+int rrsvd_sketch_omega(int n, int l, uint64_t seed, int64_t bond, int64_t sweep, int64_t chain, int precision,
+                       void* out, void* stream);
+
+/* ------------------------------------------------------------------------
  * No-allocation variant of rrsvd_execute.  The paper has no counterpart:
  * this entry point exists for callers that cannot call cudaMalloc -- code
  * running inside another library's scheduling loop or a host callback that

@@ -85,6 +85,8 @@ _SIGS = {
     "rrsvd_execute_host": (_i, [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp]),
     "rrsvd_last_error": (ctypes.c_char_p, [_vp]),
     "rrsvd_execute_noalloc": (_i, [_i, _i, _i, _i, _i, _i, _u64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "tebd_philox4x64_10": (_i, [_vp, _i64, _u64, _u64, _vp, _vp]),
+    "rrsvd_sketch_omega": (_i, [_i, _i, _u64, _i64, _i64, _i64, _i, _vp, _vp]),
     "tebd_profiler_enable": (_i, [_i]),
     "tebd_profiler_reset": (_i, []),
     "tebd_profiler_read": (_i, [_i, ctypes.c_char_p, _pd, ctypes.POINTER(_i64), _pi]),
@@ -390,6 +392,26 @@ def rrsvd_execute_noalloc(m, n, k_max, p, q, batch, seed, chain0, theta_ptr, sig
                                       vp(U_ptr), vp(Vh_ptr), vp(w_ptr), vp(rank_ptr), vp(stream_ptr))
     if rc != TEBD_OK:
         raise TebdError(rc, "rrsvd_execute_noalloc")
+
+
+def tebd_philox4x64_10(counters_ptr, count, key0, key1, words_ptr, stream_ptr=0):
+    """Philox4x64-10 blocks of the library's sketch generator on device
+    buffers (integer addresses of 4 * count uint64 each)."""
+    rc = load().tebd_philox4x64_10(_vp(int(counters_ptr)) if counters_ptr else None, count, key0 & (2**64 - 1),
+                                   key1 & (2**64 - 1), _vp(int(words_ptr)) if words_ptr else None,
+                                   _vp(int(stream_ptr)) if stream_ptr else None)
+    if rc != TEBD_OK:
+        raise TebdError(rc, "tebd_philox4x64_10")
+
+
+def rrsvd_sketch_omega(n, l, seed, bond, sweep, chain, precision, out_ptr, stream_ptr=0):
+    """The n x l sketch matrix (row-major, device buffer: complex128 for the
+    FP64 form, complex64 for the mixed form) exactly as the sketch draws it."""
+    rc = load().rrsvd_sketch_omega(n, l, seed & (2**64 - 1), bond, sweep, chain, precision,
+                                   _vp(int(out_ptr)) if out_ptr else None,
+                                   _vp(int(stream_ptr)) if stream_ptr else None)
+    if rc != TEBD_OK:
+        raise TebdError(rc, "rrsvd_sketch_omega")
 
 
 def rrsvd_last_error(plan):

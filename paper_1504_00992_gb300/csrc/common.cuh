@@ -104,4 +104,18 @@ __device__ __forceinline__ cplx gauss_c(uint64_t idx, uint64_t bond, uint64_t sw
   return cmk(rho * c, rho * s);
 }
 
+// Complex standard Gaussian of sketch element `idx` from the same Philox
+// words as the FP64 path, by Box-Muller in FP32 (24-bit uniforms): the
+// mixed form rounds Omega to TF32, and its refinement pass needs it to FP32.
+__device__ __forceinline__ float2 gauss_c_f32(uint64_t idx, uint64_t bond, uint64_t sweep, uint64_t chain,
+                                              uint64_t seed) {
+  const u64x4 w = philox4x64_10(idx, bond, sweep, chain, seed, 0);
+  const float u1 = ((float)(unsigned int)(w.v[0] >> 40) + 0.5f) * 5.9604644775390625e-8f;  // 2^-24
+  const float u2 = ((float)(unsigned int)(w.v[1] >> 40) + 0.5f) * 5.9604644775390625e-8f;
+  const float rho = sqrtf(-2.f * logf(u1));
+  float sn, cs;
+  sincospif(2.f * u2, &sn, &cs);
+  return make_float2(rho * cs, rho * sn);
+}
+
 }  // namespace tg
