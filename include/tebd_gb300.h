@@ -79,6 +79,15 @@ enum { TEBD_PREC_FP64 = 0, TEBD_PREC_TF32 = 2 };
  * ---------------------------------------------------------------------- */
 typedef struct tebd_s* tebd_t;
 
+/* Device allocator of a handle (e.g. a framework's caching allocator, so that
+ * the handle's memory comes from the same pool as the caller's tensors).
+ * alloc(bytes, ctx) returns device memory of the current device, at least
+ * 256-byte aligned, or NULL when out of memory; release(ptr, ctx) returns a
+ * block.  Blocks are used on the handle's stream and released only after
+ * that stream has been synchronised.  Both NULL: cudaMalloc / cudaFree. */
+typedef void* (*tebd_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*tebd_release_fn)(void* ptr, void* ctx);
+
 typedef struct {
   int N;                /* sites, >= 2 */
   int d;                /* local dimension of every site (used if d_site == NULL), 2..64 */
@@ -100,6 +109,10 @@ typedef struct {
                            every stage at the capacity sizes and keep the faster */
   size_t workspace_budget; /* bytes of per-bond workspace one wave may use (0 = all bonds
                               of a parity in one wave); larger batches run in waves */
+  tebd_alloc_fn alloc;     /* optional: allocator of every device block of the handle
+                              (read from descs[0]); with release, or both NULL */
+  tebd_release_fn release;
+  void* alloc_ctx;         /* passed to alloc and release */
 } tebd_desc_t;
 
 /* Section II (Eq. defmps, deftheta, defupdatetheta) with the RRSVD of
@@ -109,7 +122,9 @@ typedef struct {
  * the caps (the bond dimension of bond b never exceeds
  * min(chi_max, prod_{s<=b} d_s, prod_{s>b} d_s)).
  * Errors: TEBD_EINVAL (N < 2, d < 2 or > 64, chi_max < 1, p < 0, q < 0,
- * out == NULL), TEBD_ENOMEM, TEBD_ECUDA.  On error *out is NULL. */
+ * out == NULL; only one of desc alloc / release given, or a block from alloc
+ * that is not 256-byte aligned), TEBD_ENOMEM, TEBD_ECUDA.  On error *out is
+ * NULL. */
 int tebd_create(int N, int d, int chi_max, int p, int q, uint64_t seed, tebd_t* out);
 
 /* As tebd_create, with per-site d, per-bond caps, precision and cutoff. */
@@ -150,6 +165,18 @@ int tebd_destroy(tebd_t h);
 /* Device work of later calls goes to `cuda_stream` (a cudaStream_t). */
 int tebd_set_stream(tebd_t h, void* cuda_stream);
 
+/* Moves every device block of the handle to `alloc` / `release` (both NULL:
+ * cudaMalloc / cudaFree): the arena is allocated anew, the state (MPS, gates,
+ * sweep counter, weights) and any recorded checkpoints are copied into the
+ * new blocks, and the old blocks go back to the allocator they came from.
+ * Later blocks (checkpoints, reverse-pass buffers) come from `alloc` too.
+ * Captured sweep graphs are dropped and captured again at the next step.
+ * Synchronises the handle's stream.  On error the handle keeps its old
+ * blocks and allocator.
+ * Errors: TEBD_EINVAL (only one of alloc / release NULL, a block that is not
+ * 256-byte aligned), TEBD_ENOMEM (alloc returned NULL), TEBD_ECUDA. */
+int tebd_set_allocator(tebd_t h, tebd_alloc_fn alloc, tebd_release_fn release, void* ctx);
+
 /* Product state of the selected chain: psi is N blocks of d_s complex
  * amplitudes (host), each normalised by the library.  Resets the chain's bond
  * dimensions to 1 and its discarded-weight accumulators, and the handle's
@@ -160,6 +187,8 @@ int tebd_set_product_state(tebd_t h, const double* psi);
 /* Arbitrary Vidal-form state (host arrays, copied): gamma[s] points at a
  * [d_s][chi[s-1]][chi[s]] complex array (chi[-1] = chi[N-1] = 1 implied),
  * lambda[b] at chi[b] doubles, chi has N-1 entries each within the bond's cap.
+ * Resets the chain's discarded-weight accumulators and the handle's sweep
+ * counter to 0 (tebd_set_sweep_count restores a checkpointed counter).
  * Errors: TEBD_EINVAL. */
 int tebd_set_mps(tebd_t h, const double* const* gamma, const double* const* lambda, const int* chi);
 
@@ -203,6 +232,19 @@ int tebd_discarded_weight(tebd_t h, double* out);
 
 /* Number of tebd_step_* calls made (the Philox sweep counter). */
 int tebd_sweep_count(tebd_t h, int64_t* out);
+
+/* Sets the sweep counter (count >= 0): Omega of the next step is drawn at
+ * sweep `count`.  A run checkpointed with tebd_get_mps + tebd_sweep_count and
+ * resumed with tebd_set_mps + tebd_set_sweep_count then draws the same sketch
+ * matrices as the uninterrupted run and gives bit-identical states.
+ * Errors: TEBD_EINVAL (count < 0), TEBD_ECUDA. */
+int tebd_set_sweep_count(tebd_t h, int64_t count);
+
+/* Discarded weight w_b = 1 - sum_kept s^2 / ||theta||_F^2 (Eq. defdiscweigt)
+ * of the latest update of every bond b of the selected chain: out holds N-1
+ * doubles (host); 0 for bonds not updated since the state was set.
+ * Synchronises. */
+int tebd_bond_weights(tebd_t h, double* out);
 
 /* Recording for the reverse pass (single-chain handles): while on, every
  * tebd_step_* first stores a device checkpoint of the chain's tensors,
@@ -297,6 +339,13 @@ int rrsvd_execute_host(rrsvd_plan_t plan, const double* theta, int64_t chain0, d
 
 const char* rrsvd_last_error(rrsvd_plan_t plan);
 
+/* Clears the plan's recorded error and its device status flags (a zero or
+ * non-finite theta, an expired tensor-core wait): an execute that failed
+ * that way leaves nothing behind that the next execute reads, since every
+ * buffer of the workspace is written before it is read.  Synchronises the
+ * legacy default stream. */
+int rrsvd_clear_error(rrsvd_plan_t plan);
+
 
 /* ------------------------------------------------------------------------
  * Kernel timing (tracing aid).  When enabled, every kernel launch of the
@@ -312,6 +361,25 @@ int tebd_profiler_reset(void);
  * names (64 chars each, NUL-terminated), total milliseconds and launch
  * counts; *count receives the number of classes (may exceed max_entries). */
 int tebd_profiler_read(int max_entries, char* names, double* total_ms, int64_t* launches, int* count);
+
+/* ------------------------------------------------------------------------
+ * Failure injection (test hook; the paper has no counterpart).  Faults are
+ * made on the host, never by faulting the GPU:
+ *   TEBD_FAULT_ALLOC:    the next device allocation of a handle or plan
+ *                        (arena, checkpoint, reverse-pass or staging buffer,
+ *                        plan descriptors) fails as if out of memory, so the
+ *                        call returns TEBD_ENOMEM;
+ *   TEBD_FAULT_TC_STALL: the next tensor-core product launched (mixed form)
+ *                        outside a stream capture issues none of its operand
+ *                        copies and polls its pipeline waits at most 2^12
+ *                        times, so its bounded waits expire: the kernel
+ *                        raises the timeout flag, writes zeros, frees its
+ *                        tensor memory and returns, and the next
+ *                        synchronising call reports TEBD_ETIMEOUT.
+ * Each armed fault fires once; TEBD_FAULT_NONE disarms all.  Process-wide.
+ * Errors: TEBD_EINVAL (unknown kind). */
+enum { TEBD_FAULT_NONE = 0, TEBD_FAULT_ALLOC = 1, TEBD_FAULT_TC_STALL = 2 };
+int tebd_fault_inject(int kind);
 
 /* ------------------------------------------------------------------------
  * The sketch generator (Section IV, Alg. 1: Omega "drawn from the Gaussian

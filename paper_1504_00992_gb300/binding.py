@@ -36,12 +36,52 @@ class TebdError(RuntimeError):
         super().__init__(f"{_CODES.get(code, code)}: {msg}")
 
 
+# tebd_alloc_fn / tebd_release_fn
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+RELEASE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+TEBD_FAULT_NONE = 0
+TEBD_FAULT_ALLOC = 1
+TEBD_FAULT_TC_STALL = 2
+
+
 class TebdDesc(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int), ("d", ctypes.c_int), ("d_site", ctypes.POINTER(ctypes.c_int)),
                 ("chi_max", ctypes.c_int), ("chi_bond", ctypes.POINTER(ctypes.c_int)),
                 ("p", ctypes.c_int), ("q", ctypes.c_int), ("seed", ctypes.c_uint64),
                 ("precision", ctypes.c_int), ("sv_cutoff", ctypes.c_double), ("chain", ctypes.c_int),
-                ("use_graph", ctypes.c_int), ("autotune", ctypes.c_int), ("workspace_budget", ctypes.c_size_t)]
+                ("use_graph", ctypes.c_int), ("autotune", ctypes.c_int), ("workspace_budget", ctypes.c_size_t),
+                ("alloc", ALLOC_FN), ("release", RELEASE_FN), ("alloc_ctx", ctypes.c_void_p)]
+
+
+class TorchAllocator:
+    """Device blocks of a TEBD handle from PyTorch's CUDA caching allocator
+    (torch.cuda.caching_allocator_alloc / _delete), so that the handle's
+    arena, checkpoints and reverse-pass buffers share the caller's memory
+    pool.  Keep the object alive as long as a handle uses it; `live` maps the
+    blocks it has handed out to their sizes."""
+
+    def __init__(self, device=None, stream=None):
+        import torch
+        self.device = torch.cuda.current_device() if device is None else device
+        self.stream = stream
+        self.live = {}
+
+        def _alloc(nbytes, ctx):
+            try:
+                ptr = int(torch.cuda.caching_allocator_alloc(int(nbytes), self.device, self.stream))
+            except Exception:   # out of memory: the library sees NULL
+                return None
+            self.live[ptr] = int(nbytes)
+            return ptr
+
+        def _release(ptr, ctx):
+            if ptr:
+                self.live.pop(int(ptr), None)
+                torch.cuda.caching_allocator_delete(int(ptr))
+
+        self.alloc = ALLOC_FN(_alloc)
+        self.release = RELEASE_FN(_release)
 
 
 _LIB = None
@@ -62,6 +102,11 @@ _SIGS = {
     "tebd_plan_query": (_i, [_i, ctypes.POINTER(TebdDesc), ctypes.POINTER(ctypes.c_size_t), _pi, _pi]),
     "tebd_destroy": (_i, [_vp]),
     "tebd_set_stream": (_i, [_vp, _vp]),
+    "tebd_set_allocator": (_i, [_vp, ALLOC_FN, RELEASE_FN, _vp]),
+    "tebd_set_sweep_count": (_i, [_vp, _i64]),
+    "tebd_bond_weights": (_i, [_vp, _pd]),
+    "tebd_fault_inject": (_i, [_i]),
+    "rrsvd_clear_error": (_i, [_vp]),
     "tebd_set_product_state": (_i, [_vp, _pd]),
     "tebd_set_mps": (_i, [_vp, ctypes.POINTER(_pd), ctypes.POINTER(_pd), _pi]),
     "tebd_get_mps": (_i, [_vp, ctypes.POINTER(_pd), ctypes.POINTER(_pd), _pi]),
@@ -146,18 +191,22 @@ _KEEP = []
 
 
 def _desc(N, d_site, chi_bond, p, q, seed, precision=TEBD_PREC_FP64, sv_cutoff=0.0, chain=0, use_graph=0,
-          autotune=0, workspace_budget=0):
+          autotune=0, workspace_budget=0, allocator=None):
     ds = (ctypes.c_int * N)(*[int(x) for x in d_site])
     cb = (ctypes.c_int * (N - 1))(*[int(x) for x in chi_bond])
     _KEEP.append((ds, cb))
-    return TebdDesc(N, int(d_site[0]), ds, int(max(chi_bond)), cb, p, q, seed, precision, sv_cutoff, chain,
-                    use_graph, autotune, workspace_budget)
+    d = TebdDesc(N, int(d_site[0]), ds, int(max(chi_bond)), cb, p, q, seed, precision, sv_cutoff, chain,
+                 use_graph, autotune, workspace_budget)
+    if allocator is not None:
+        d.alloc = allocator.alloc
+        d.release = allocator.release
+    return d
 
 
 def tebd_create_ex(N, d_site, chi_bond, p, q, seed, precision=TEBD_PREC_FP64, sv_cutoff=0.0, chain=0, use_graph=0,
-                   autotune=0, workspace_budget=0):
+                   autotune=0, workspace_budget=0, allocator=None):
     desc = _desc(N, d_site, chi_bond, p, q, seed, precision, sv_cutoff, chain, use_graph, autotune,
-                 workspace_budget)
+                 workspace_budget, allocator)
     h = _vp()
     rc = load().tebd_create_ex(ctypes.byref(desc), ctypes.byref(h))
     _KEEP.clear()
@@ -167,12 +216,12 @@ def tebd_create_ex(N, d_site, chi_bond, p, q, seed, precision=TEBD_PREC_FP64, sv
 
 
 def tebd_create_multi(chains, p, q, seed, precision=TEBD_PREC_FP64, sv_cutoff=0.0, chain=0, use_graph=0,
-                      autotune=0, workspace_budget=0):
+                      autotune=0, workspace_budget=0, allocator=None):
     """chains: list of (N, d_site list, chi_bond list)."""
     arr = (TebdDesc * len(chains))()
     for c, (N, d_site, chi_bond) in enumerate(chains):
         arr[c] = _desc(N, d_site, chi_bond, p, q, seed, precision, sv_cutoff, chain, use_graph, autotune,
-                       workspace_budget)
+                       workspace_budget, allocator if c == 0 else None)
     h = _vp()
     rc = load().tebd_create_multi(len(chains), arr, ctypes.byref(h))
     _KEEP.clear()
@@ -217,6 +266,32 @@ def tebd_destroy(h):
 
 def tebd_set_stream(h, stream_ptr):
     _check(h, load().tebd_set_stream(h, _vp(int(stream_ptr))))
+
+
+def tebd_set_allocator(h, allocator=None):
+    """Moves the handle's device memory to `allocator` (an object with ctypes
+    callbacks .alloc / .release, e.g. TorchAllocator), or back to cudaMalloc
+    when None.  The caller keeps `allocator` alive while the handle uses it."""
+    if allocator is None:
+        _check(h, load().tebd_set_allocator(h, ALLOC_FN(), RELEASE_FN(), None))
+    else:
+        _check(h, load().tebd_set_allocator(h, allocator.alloc, allocator.release, None))
+
+
+def tebd_set_sweep_count(h, count):
+    _check(h, load().tebd_set_sweep_count(h, int(count)))
+
+
+def tebd_bond_weights(h, n_bonds):
+    out = np.zeros(n_bonds, dtype=np.float64)
+    _check(h, load().tebd_bond_weights(h, _dp(out)))
+    return out
+
+
+def tebd_fault_inject(kind):
+    rc = load().tebd_fault_inject(kind)
+    if rc != TEBD_OK:
+        raise TebdError(rc, "tebd_fault_inject")
 
 
 def tebd_set_product_state(h, psis):
@@ -418,6 +493,10 @@ def rrsvd_last_error(plan):
     return (load().rrsvd_last_error(plan) or b"").decode()
 
 
+def rrsvd_clear_error(plan):
+    _pcheck(plan, load().rrsvd_clear_error(plan))
+
+
 # ------------------------------------------------------------------ kernel timing
 def tebd_profiler_enable(on=True):
     load().tebd_profiler_enable(1 if on else 0)
@@ -451,16 +530,18 @@ class Tebd:
     """Owning wrapper of a tebd_t handle (the calls above, bound to one chain)."""
 
     def __init__(self, N, d, chi_max, p, q, seed=0, d_site=None, chi_bond=None, sv_cutoff=0.0, chain=0,
-                 stream=None, use_graph=0, autotune=0, precision=TEBD_PREC_FP64, workspace_budget=0):
+                 stream=None, use_graph=0, autotune=0, precision=TEBD_PREC_FP64, workspace_budget=0,
+                 allocator=None):
         self.N = N
         self.dims = list(d_site) if d_site is not None else [d] * N
         self.chi_bond = list(chi_bond) if chi_bond is not None else [chi_max] * (N - 1)
+        self.allocator = allocator
         if d_site is None and chi_bond is None and sv_cutoff == 0.0 and chain == 0 and not use_graph \
-                and not autotune and precision == TEBD_PREC_FP64 and not workspace_budget:
+                and not autotune and precision == TEBD_PREC_FP64 and not workspace_budget and allocator is None:
             self.h = tebd_create(N, d, chi_max, p, q, seed)
         else:
             self.h = tebd_create_ex(N, self.dims, self.chi_bond, p, q, seed, precision, sv_cutoff, chain,
-                                    use_graph, autotune, workspace_budget)
+                                    use_graph, autotune, workspace_budget, allocator)
         caps = []
         for b in range(N - 1):
             left = int(np.prod([float(x) for x in self.dims[: b + 1]]))
@@ -511,6 +592,16 @@ class Tebd:
     def sweeps(self):
         return tebd_sweep_count(self.h)
 
+    def set_sweep_count(self, count):
+        tebd_set_sweep_count(self.h, count)
+
+    def bond_weights(self):
+        return tebd_bond_weights(self.h, self.N - 1)
+
+    def set_allocator(self, allocator):
+        tebd_set_allocator(self.h, allocator)
+        self.allocator = allocator
+
     def record(self, on=True):
         tebd_record(self.h, on)
 
@@ -532,10 +623,11 @@ class MultiTebd:
     """Many chains in one handle; per-chain calls take the chain index."""
 
     def __init__(self, chains, p, q, seed=0, use_graph=0, autotune=0, workspace_budget=0, stream=None,
-                 precision=TEBD_PREC_FP64):
+                 precision=TEBD_PREC_FP64, allocator=None):
         self.chains = [(N, list(ds), list(cb)) for N, ds, cb in chains]
+        self.allocator = allocator
         self.h = tebd_create_multi(self.chains, p, q, seed, precision=precision, use_graph=use_graph,
-                                   autotune=autotune, workspace_budget=workspace_budget)
+                                   autotune=autotune, workspace_budget=workspace_budget, allocator=allocator)
         self.caps = [_caps(ds, cb) for _, ds, cb in self.chains]
         if stream is not None:
             tebd_set_stream(self.h, stream)
@@ -579,6 +671,14 @@ class MultiTebd:
     def discarded_weight(self, c):
         self._sel(c)
         return tebd_discarded_weight(self.h)
+
+    def bond_weights(self, c):
+        self._sel(c)
+        return tebd_bond_weights(self.h, self.chains[c][0] - 1)
+
+    def set_mps(self, c, gammas, lambdas):
+        self._sel(c)
+        tebd_set_mps(self.h, gammas, lambdas)
 
     def workspace_info(self):
         return tebd_workspace_info(self.h)

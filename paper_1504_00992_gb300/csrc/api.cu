@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <string>
@@ -17,6 +18,7 @@
 #include "internal.cuh"
 #include "mixed.cuh"
 #include "profiler.cuh"
+#include "workspace.cuh"
 
 using namespace tg;
 
@@ -49,12 +51,16 @@ struct ErrState {
     }                                                                                     \
   } while (0)
 
-// Per-problem RRSVD workspace layout (byte offsets from a base).
-struct WsLayout {
-  size_t omega, Y, Q, Yt, Qt, R, J, Jk, Wk, U, V, sigma, part, scal, Dr, total;
-};
+bool all_finite(const double* x, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!isfinite(x[i])) return false;
+  return true;
+}
 
-WsLayout ws_layout(int m, int n, int k, int l, bool own_U, bool own_V, int r = 0) {
+}  // namespace
+
+namespace tg {
+WsLayout ws_layout(int m, int n, int k, int l, bool own_U, bool own_V, int r) {
   WsLayout w;
   size_t o = 0;
   const size_t c = sizeof(cplx);
@@ -80,30 +86,58 @@ WsLayout ws_layout(int m, int n, int k, int l, bool own_U, bool own_V, int r = 0
   return w;
 }
 
-void fill_ptrs(ProbPtr& P, char* base, const WsLayout& w) {
-  P.omega = (cplx*)(base + w.omega);
-  P.Y = (cplx*)(base + w.Y);
-  P.Q = (cplx*)(base + w.Q);
-  P.Yt = (cplx*)(base + w.Yt);
-  P.Qt = (cplx*)(base + w.Qt);
-  P.R = (cplx*)(base + w.R);
-  P.J = (cplx*)(base + w.J);
-  P.Jk = (cplx*)(base + w.Jk);
-  P.Wk = (cplx*)(base + w.Wk);
-  P.U = (cplx*)(base + w.U);
-  P.V = (cplx*)(base + w.V);
-  P.sigma = (double*)(base + w.sigma);
-  P.part = (double*)(base + w.part);
-  P.scal = (double*)(base + w.scal);
-  P.Dr = (cplx*)(base + w.Dr);
+static std::atomic<int> g_fault_alloc{0}, g_fault_tc{0};
+
+bool fault_take(int kind) {
+  std::atomic<int>& f = (kind == TEBD_FAULT_ALLOC) ? g_fault_alloc : g_fault_tc;
+  int armed = 1;
+  return f.compare_exchange_strong(armed, 0);
+}
+}  // namespace tg
+
+extern "C" int tebd_fault_inject(int kind) {
+  switch (kind) {
+    case TEBD_FAULT_NONE: g_fault_alloc = 0; g_fault_tc = 0; return TEBD_OK;
+    case TEBD_FAULT_ALLOC: g_fault_alloc = 1; return TEBD_OK;
+    case TEBD_FAULT_TC_STALL: g_fault_tc = 1; return TEBD_OK;
+    default: return TEBD_EINVAL;
+  }
 }
 
-bool all_finite(const double* x, size_t n) {
-  for (size_t i = 0; i < n; ++i)
-    if (!isfinite(x[i])) return false;
-  return true;
-}
-
+namespace {
+// Device blocks of a handle: the caller's allocator, or cudaMalloc / cudaFree.
+struct DevAlloc {
+  tebd_alloc_fn fn = nullptr;
+  tebd_release_fn rel = nullptr;
+  void* ctx = nullptr;
+  // TEBD_OK, TEBD_ENOMEM (no memory, or an injected allocation fault) or
+  // TEBD_EINVAL (a block that is not 256-byte aligned; returned at once)
+  int get(size_t bytes, void** out) const {
+    *out = nullptr;
+    if (fault_take(TEBD_FAULT_ALLOC)) return TEBD_ENOMEM;
+    if (fn) {
+      void* q = fn(bytes, ctx);
+      if (!q) return TEBD_ENOMEM;
+      if ((uintptr_t)q % ALIGN) {
+        rel(q, ctx);
+        return TEBD_EINVAL;
+      }
+      *out = q;
+      return TEBD_OK;
+    }
+    if (cudaMalloc(out, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      *out = nullptr;
+      return TEBD_ENOMEM;
+    }
+    return TEBD_OK;
+  }
+  void put(void* q) const {
+    if (!q) return;
+    if (fn) rel(q, ctx);
+    else cudaFree(q);
+  }
+};
 }  // namespace
 
 // ===========================================================================
@@ -115,7 +149,7 @@ struct ChainH {
   std::vector<int> d, chi_cap, cap_ext;
   std::vector<size_t> gamma_off, lam_off, gate_off;
   size_t gamma_lo = 0, gamma_hi = 0;  // the chain's Gamma block in the arena
-  size_t tab_off = 0, int_off = 0;
+  size_t tab_off = 0, int_off = 0, wb_off = 0;
   std::vector<cplx*> gamma_ptr;       // N
   std::vector<double*> lam_ptr;       // N+1, outer ones -> the constant 1.0
   int* chi_ext = nullptr;             // device, N+1
@@ -123,6 +157,7 @@ struct ChainH {
   int* cap_ext_dev = nullptr;
   cplx** gamma_tab = nullptr;
   double** lam_tab = nullptr;
+  double* wbond = nullptr;            // device, N-1: w of each bond's latest update
   bool gates_set[2] = {false, false};
   ChainDev dev{};
 };
@@ -142,8 +177,18 @@ struct ParitySet {
   std::vector<Wave> waves;
 };
 
+// Byte offsets of the handle's arena, from the plan of tebd_create_multi.
+struct HandlePlan {
+  size_t one_off = 0, st_off = 0, wacc_off = 0, sweep_off = 0, tcerr_off = 0, op_off = 0, wout_off = 0;
+  size_t desc_off = 0, desc_per = 0, ws_off = 0, mixed_off = 0, total = 0;
+  std::vector<WsLayout> lay[2];
+  int max_batch = 0;
+};
+
 struct tebd_s {
   ErrState err;
+  DevAlloc alloc;
+  HandlePlan plan;
   int p = 0, q = 0, precision = 0;
   uint64_t seed = 0;
   double cutoff = 1e-14;
@@ -185,7 +230,7 @@ static size_t chain_region_end(const ChainH& C) {
 }
 
 static void free_ckpts(tebd_s* h) {
-  for (auto& c : h->ckpts) cudaFree(c.buf);
+  for (auto& c : h->ckpts) h->alloc.put(c.buf);
   h->ckpts.clear();
 }
 
@@ -204,11 +249,13 @@ static int tebd_check_status(tebd_t h) {
 }
 
 static void tebd_free(tebd_s* h) {
+  // a caller's allocator may hand the blocks out again at once
+  if (h->alloc.fn) cudaStreamSynchronize(h->stream);
   free_ckpts(h);
-  if (h->adj_arena) cudaFree(h->adj_arena);
+  h->alloc.put(h->adj_arena);
   for (int i = 0; i < 2; ++i)
     if (h->gexec[i]) cudaGraphExecDestroy(h->gexec[i]);
-  if (h->arena) cudaFree(h->arena);
+  h->alloc.put(h->arena);
   if (h->own_stream) cudaStreamDestroy(h->own_stream);
   delete h;
 }
@@ -270,13 +317,6 @@ static int tune_wave(const ParitySet& ps, Wave& w, cudaStream_t st, Dims* scratc
 
 static int tebd_reset_state(tebd_t h, int slot, const double* psi);
 
-// Byte offsets of the handle's arena, from the plan of tebd_create_multi.
-struct HandlePlan {
-  size_t one_off = 0, st_off = 0, wacc_off = 0, sweep_off = 0, tcerr_off = 0, op_off = 0, wout_off = 0;
-  size_t desc_off = 0, desc_per = 0, ws_off = 0, mixed_off = 0, total = 0;
-  std::vector<WsLayout> lay[2];
-  int max_batch = 0;
-};
 
 // Validates the chain descriptors and plans the handle on the host: the
 // chains' capacities and Gamma/lambda/gate regions, the bonds of each parity
@@ -288,6 +328,7 @@ static int plan_handle(tebd_s* h, int n_chains, const tebd_desc_t* descs, Handle
   if (d0.p < 0 || d0.q < 0) return TEBD_EINVAL;
   if (d0.precision != TEBD_PREC_FP64 && d0.precision != TEBD_PREC_TF32) return TEBD_ENOTIMPL;
   if (d0.precision == TEBD_PREC_TF32 && d0.autotune) return TEBD_EINVAL;  // the tile autotuner is for FP64 GEMMs
+  if ((d0.alloc == nullptr) != (d0.release == nullptr)) return TEBD_EINVAL;
   for (int c = 0; c < n_chains; ++c) {
     const tebd_desc_t& dc = descs[c];
     if (dc.N < 2 || dc.p != d0.p || dc.q != d0.q || dc.seed != d0.seed || dc.precision != d0.precision)
@@ -349,6 +390,8 @@ static int plan_handle(tebd_s* h, int n_chains, const tebd_desc_t* descs, Handle
     off += align_up(sizeof(cplx*) * N) + align_up(sizeof(double*) * (N + 1));
     C.int_off = off;
     off += 3 * align_up(sizeof(int) * (N + 1));
+    C.wb_off = off;
+    off += align_up(sizeof(double) * (N - 1));
   }
   lay_plan.one_off = off; off += ALIGN;
   lay_plan.st_off = off; off += ALIGN;
@@ -467,52 +510,26 @@ extern "C" int tebd_plan_query(int n_chains, const tebd_desc_t* descs, size_t* a
   return rc;
 }
 
-extern "C" int tebd_create_multi(int n_chains, const tebd_desc_t* descs, tebd_t* out) {
-  if (!out) return TEBD_EINVAL;
-  *out = nullptr;
-  tebd_s* h = new tebd_s();
-  HandlePlan lay_plan;
-  {
-    const int rc = plan_handle(h, n_chains, descs, lay_plan);
-    if (rc != TEBD_OK) { delete h; return rc; }
-  }
-  const tebd_desc_t& d0 = descs[0];
-  const bool tf32 = h->precision == TEBD_PREC_TF32;
-  const std::vector<WsLayout>* lay = lay_plan.lay;
-  const int max_batch = lay_plan.max_batch;
-  const size_t one_off = lay_plan.one_off, st_off = lay_plan.st_off, wacc_off = lay_plan.wacc_off, sweep_off = lay_plan.sweep_off,
-               tcerr_off = lay_plan.tcerr_off, op_off = lay_plan.op_off, wout_off = lay_plan.wout_off, desc_off = lay_plan.desc_off,
-               desc_per = lay_plan.desc_per, ws_off = lay_plan.ws_off, mixed_off = lay_plan.mixed_off;
-  if (h->use_graph) {
-    // the legacy default stream cannot be captured: run on a blocking stream
-    // of our own (it still orders with stream 0)
-    if (cudaStreamCreate(&h->own_stream) != cudaSuccess) { cudaGetLastError(); delete h; return TEBD_ECUDA; }
-    h->stream = h->own_stream;
-  }
-  if (cudaMalloc(&h->arena, h->arena_bytes) != cudaSuccess) {
-    cudaGetLastError();
-    h->arena = nullptr;
-    tebd_free(h);  // also the stream of our own
-    return TEBD_ENOMEM;
-  }
+// Points every pointer of the handle (host copies and device tables) into
+// its arena h->arena from the offsets of h->plan, and uploads the pointer
+// tables and the constant lambda = 1 of the outer bonds; the arena's other
+// contents are left as they are.  Runs at creation and after
+// tebd_set_allocator moved the arena.  Synchronous.
+static bool bind_arena(tebd_s* h) {
+  const HandlePlan& L = h->plan;
   char* A = h->arena;
-  if (cudaMemset(A, 0, ws_off) != cudaSuccess) { tebd_free(h); return TEBD_ECUDA; }
-  h->one_lam = (double*)(A + one_off);
-  h->status = (int*)(A + st_off);
-  h->wacc = (double*)(A + wacc_off);
-  h->sweep_dev = (uint64_t*)(A + sweep_off);
-  if (tf32) {
-    h->tcerr = (int*)(A + tcerr_off);
-    h->mixed = A + mixed_off;
-    for (int par = 0; par < 2; ++par)
-      for (const Wave& w : h->par[par].waves)
-        if (mixed_prepare(w.cap) != cudaSuccess) { cudaGetLastError(); tebd_free(h); return TEBD_ECUDA; }
-  }
-  h->op_dev = (cplx*)(A + op_off);
-  h->out_dev = (cplx*)(A + op_off + align_up(sizeof(cplx) * 64 * 64));
-  h->wout = (double*)(A + wout_off);
+  const bool tf32 = h->precision == TEBD_PREC_TF32;
+  h->one_lam = (double*)(A + L.one_off);
+  h->status = (int*)(A + L.st_off);
+  h->wacc = (double*)(A + L.wacc_off);
+  h->sweep_dev = (uint64_t*)(A + L.sweep_off);
+  h->tcerr = tf32 ? (int*)(A + L.tcerr_off) : nullptr;
+  h->mixed = tf32 ? A + L.mixed_off : nullptr;
+  h->op_dev = (cplx*)(A + L.op_off);
+  h->out_dev = (cplx*)(A + L.op_off + align_up(sizeof(cplx) * 64 * 64));
+  h->wout = (double*)(A + L.wout_off);
   bool ok = true;
-  for (int c = 0; c < n_chains && ok; ++c) {
+  for (size_t c = 0; c < h->ch.size() && ok; ++c) {
     ChainH& C = h->ch[c];
     const int N = C.N;
     C.gamma_ptr.resize(N);
@@ -526,6 +543,7 @@ extern "C" int tebd_create_multi(int n_chains, const tebd_desc_t* descs, tebd_t*
     C.chi_ext = (int*)(A + C.int_off);
     C.dsite_dev = (int*)(A + C.int_off + align_up(sizeof(int) * (N + 1)));
     C.cap_ext_dev = (int*)(A + C.int_off + 2 * align_up(sizeof(int) * (N + 1)));
+    C.wbond = (double*)(A + C.wb_off);
     ok = cudaMemcpy(C.gamma_tab, C.gamma_ptr.data(), sizeof(cplx*) * N, cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(C.lam_tab, C.lam_ptr.data(), sizeof(double*) * (N + 1), cudaMemcpyHostToDevice) ==
              cudaSuccess &&
@@ -540,10 +558,11 @@ extern "C" int tebd_create_multi(int n_chains, const tebd_desc_t* descs, tebd_t*
   }
   const double one = 1.0;
   ok = ok && cudaMemcpy(h->one_lam, &one, sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess;
-  char* ws = A + ws_off;
+  char* ws = A + L.ws_off;
+  const int max_batch = L.max_batch;
   for (int par = 0; par < 2 && ok; ++par) {
     ParitySet& ps = h->par[par];
-    ps.dims = (Dims*)(A + desc_off + par * desc_per);
+    ps.dims = (Dims*)(A + L.desc_off + par * L.desc_per);
     ps.ptrs = (ProbPtr*)((char*)ps.dims + align_up(sizeof(Dims) * std::max(1, max_batch)));
     std::vector<ProbPtr> hp(ps.batch);
     for (const Wave& w : ps.waves) {
@@ -571,20 +590,56 @@ extern "C" int tebd_create_multi(int n_chains, const tebd_desc_t* descs, tebd_t*
         P.bond_s = b;
         P.chain_s = (int)C.chain_index;
         P.slot = c;
+        P.wbond = C.wbond + b;
         P.theta = (const cplx*)(ws + o);
         o += align_up(sizeof(cplx) * (size_t)C.d[b] * C.cap_ext[b] * C.d[b + 1] * C.cap_ext[b + 2]);
         if (C.d[b] * C.d[b + 1] >= GATE_GEMM_MIN) {
           P.Cpre = (cplx*)(ws + o);
           o += align_up(sizeof(cplx) * (size_t)C.d[b] * C.cap_ext[b] * C.d[b + 1] * C.cap_ext[b + 2]);
         }
-        fill_ptrs(P, ws + o, lay[par][i]);
-        o += lay[par][i].total;
+        fill_ptrs(P, ws + o, L.lay[par][i]);
+        o += L.lay[par][i].total;
       }
     }
     if (ps.batch > 0)
       ok = cudaMemcpy(ps.ptrs, hp.data(), sizeof(ProbPtr) * ps.batch, cudaMemcpyHostToDevice) == cudaSuccess;
   }
-  if (!ok) { tebd_free(h); return TEBD_ECUDA; }
+  return ok;
+}
+
+extern "C" int tebd_create_multi(int n_chains, const tebd_desc_t* descs, tebd_t* out) {
+  if (!out) return TEBD_EINVAL;
+  *out = nullptr;
+  tebd_s* h = new tebd_s();
+  {
+    const int rc = plan_handle(h, n_chains, descs, h->plan);
+    if (rc != TEBD_OK) { delete h; return rc; }
+  }
+  const tebd_desc_t& d0 = descs[0];
+  h->alloc.fn = d0.alloc;
+  h->alloc.rel = d0.release;
+  h->alloc.ctx = d0.alloc_ctx;
+  if (h->use_graph) {
+    // the legacy default stream cannot be captured: run on a blocking stream
+    // of our own (it still orders with stream 0)
+    if (cudaStreamCreate(&h->own_stream) != cudaSuccess) { cudaGetLastError(); delete h; return TEBD_ECUDA; }
+    h->stream = h->own_stream;
+  }
+  {
+    void* blk = nullptr;
+    const int rc = h->alloc.get(h->arena_bytes, &blk);
+    if (rc != TEBD_OK) {
+      tebd_free(h);  // also the stream of our own
+      return rc;
+    }
+    h->arena = (char*)blk;
+  }
+  if (cudaMemset(h->arena, 0, h->plan.ws_off) != cudaSuccess) { tebd_free(h); return TEBD_ECUDA; }
+  if (h->precision == TEBD_PREC_TF32)
+    for (int par = 0; par < 2; ++par)
+      for (const Wave& w : h->par[par].waves)
+        if (mixed_prepare(w.cap) != cudaSuccess) { cudaGetLastError(); tebd_free(h); return TEBD_ECUDA; }
+  if (!bind_arena(h)) { tebd_free(h); return TEBD_ECUDA; }
   // every chain starts in |0...0>
   for (int c = 0; c < n_chains; ++c) {
     std::vector<double> psi;
@@ -597,7 +652,7 @@ extern "C" int tebd_create_multi(int n_chains, const tebd_desc_t* descs, tebd_t*
     if (rc != TEBD_OK) { tebd_free(h); return rc; }
   }
   if (d0.autotune) {
-    Dims* scratch = (Dims*)(A + desc_off + 2 * desc_per);
+    Dims* scratch = (Dims*)(h->arena + h->plan.desc_off + 2 * h->plan.desc_per);
     for (int par = 0; par < 2; ++par)
       for (Wave& w : h->par[par].waves)
         if (tune_wave(h->par[par], w, h->stream, scratch, h->p) != 0) { tebd_free(h); return TEBD_ECUDA; }
@@ -635,6 +690,79 @@ extern "C" int tebd_set_stream(tebd_t h, void* s) {
     for (int i = 0; i < 2; ++i)
       if (h->gexec[i]) { cudaGraphExecDestroy(h->gexec[i]); h->gexec[i] = nullptr; }
   h->stream = (cudaStream_t)s;
+  return TEBD_OK;
+}
+
+extern "C" int tebd_set_allocator(tebd_t h, tebd_alloc_fn fn, tebd_release_fn rel, void* ctx) {
+  if (!h) return TEBD_EINVAL;
+  if (h->err.code) return h->err.code;
+  if ((fn == nullptr) != (rel == nullptr)) {
+    h->err.set(TEBD_EINVAL, "allocator: give both alloc and release, or neither");
+    return h->err.code;
+  }
+  DevAlloc na;
+  na.fn = fn;
+  na.rel = rel;
+  na.ctx = ctx;
+  CU_OR(h, cudaStreamSynchronize(h->stream));
+  // new blocks first: on failure the handle keeps its old ones
+  void* nb = nullptr;
+  int rc = na.get(h->arena_bytes, &nb);
+  if (rc != TEBD_OK) {
+    h->err.set(rc, "allocator: arena of %zu bytes %s", h->arena_bytes,
+               rc == TEBD_ENOMEM ? "not available" : "not 256-byte aligned");
+    return h->err.code;
+  }
+  const size_t cbytes = h->ch.empty() ? 0 : chain_region_end(h->ch[0]) - h->ch[0].gamma_lo;
+  std::vector<char*> nck(h->ckpts.size(), nullptr);
+  for (size_t i = 0; i < nck.size(); ++i) {
+    void* q = nullptr;
+    rc = na.get(cbytes, &q);
+    if (rc != TEBD_OK) {
+      for (size_t j = 0; j < i; ++j) na.put(nck[j]);
+      na.put(nb);
+      h->err.set(rc, "allocator: checkpoint of %zu bytes %s", cbytes,
+                 rc == TEBD_ENOMEM ? "not available" : "not 256-byte aligned");
+      return h->err.code;
+    }
+    nck[i] = (char*)q;
+  }
+  bool ok = cudaMemcpyAsync(nb, h->arena, h->arena_bytes, cudaMemcpyDeviceToDevice, h->stream) == cudaSuccess;
+  for (size_t i = 0; i < nck.size() && ok; ++i)
+    ok = cudaMemcpyAsync(nck[i], h->ckpts[i].buf, cbytes, cudaMemcpyDeviceToDevice, h->stream) == cudaSuccess;
+  ok = ok && cudaStreamSynchronize(h->stream) == cudaSuccess;
+  if (!ok) {
+    for (char* q : nck) na.put(q);
+    na.put(nb);
+    h->err.set(TEBD_ECUDA, "allocator: copy into the new blocks failed");
+    return h->err.code;
+  }
+  const DevAlloc old = h->alloc;
+  char* old_arena = h->arena;
+  h->arena = (char*)nb;
+  ok = bind_arena(h);
+  // the checkpoints carry copies of the chain's pointer tables, which a
+  // restore writes back: point them at the new arena too
+  for (size_t i = 0; i < nck.size() && ok; ++i) {
+    const ChainH& C = h->ch[0];
+    char* t = nck[i] + (C.tab_off - C.gamma_lo);
+    ok = cudaMemcpy(t, C.gamma_ptr.data(), sizeof(cplx*) * C.N, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(t + align_up(sizeof(cplx*) * C.N), C.lam_ptr.data(), sizeof(double*) * (C.N + 1),
+                    cudaMemcpyHostToDevice) == cudaSuccess;
+  }
+  for (size_t i = 0; i < nck.size(); ++i) {
+    old.put(h->ckpts[i].buf);
+    h->ckpts[i].buf = nck[i];
+  }
+  old.put(h->adj_arena);  // made again from the new allocator when needed
+  h->adj_arena = nullptr;
+  h->gbar0 = nullptr;
+  h->adj_dev[0] = h->adj_dev[1] = nullptr;
+  old.put(old_arena);
+  h->alloc = na;
+  for (int i = 0; i < 2; ++i)
+    if (h->gexec[i]) { cudaGraphExecDestroy(h->gexec[i]); h->gexec[i] = nullptr; }
+  if (!ok) { h->err.set(TEBD_ECUDA, "allocator: rebinding the arena failed"); return h->err.code; }
   return TEBD_OK;
 }
 
@@ -681,6 +809,7 @@ static int tebd_reset_state(tebd_t h, int slot, const double* psi) {
   CU_OR(h, cudaMemcpyAsync(C.chi_ext, chi.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice, h->stream));
   const double w0[2] = {0.0, 1.0};
   CU_OR(h, cudaMemcpyAsync(h->wacc + 2 * slot, w0, sizeof w0, cudaMemcpyHostToDevice, h->stream));
+  CU_OR(h, cudaMemsetAsync(C.wbond, 0, sizeof(double) * (N - 1), h->stream));
   CU_OR(h, cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
   CU_OR(h, cudaMemsetAsync(h->sweep_dev, 0, sizeof(uint64_t), h->stream));
   CU_OR(h, cudaStreamSynchronize(h->stream));
@@ -732,6 +861,7 @@ extern "C" int tebd_set_mps(tebd_t h, const double* const* gamma, const double* 
   CU_OR(h, cudaMemcpyAsync(C.chi_ext, ce.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice, h->stream));
   const double w0[2] = {0.0, 1.0};
   CU_OR(h, cudaMemcpyAsync(h->wacc + 2 * h->cur, w0, sizeof w0, cudaMemcpyHostToDevice, h->stream));
+  CU_OR(h, cudaMemsetAsync(C.wbond, 0, sizeof(double) * (N - 1), h->stream));
   CU_OR(h, cudaMemsetAsync(h->sweep_dev, 0, sizeof(uint64_t), h->stream));
   CU_OR(h, cudaStreamSynchronize(h->stream));
   h->sweeps = 0;
@@ -841,12 +971,13 @@ static int tebd_step(tebd_t h, int parity) {
   if (h->recording) {
     const ChainH& C = h->ch[0];
     const size_t bytes = chain_region_end(C) - C.gamma_lo;
-    char* buf = nullptr;
-    if (cudaMalloc(&buf, bytes) != cudaSuccess) {
-      cudaGetLastError();
-      h->err.set(TEBD_ENOMEM, "checkpoint of %zu bytes failed", bytes);
+    void* blk = nullptr;
+    const int rc = h->alloc.get(bytes, &blk);
+    if (rc != TEBD_OK) {
+      h->err.set(rc, "checkpoint of %zu bytes failed", bytes);
       return h->err.code;
     }
+    char* buf = (char*)blk;
     h->ckpts.push_back({parity, h->sweeps, buf});
     CU_OR(h, cudaMemcpyAsync(buf, h->arena + C.gamma_lo, bytes, cudaMemcpyDeviceToDevice, h->stream));
   }
@@ -920,6 +1051,26 @@ extern "C" int tebd_sweep_count(tebd_t h, int64_t* out) {
   return TEBD_OK;
 }
 
+extern "C" int tebd_set_sweep_count(tebd_t h, int64_t count) {
+  if (!h) return TEBD_EINVAL;
+  if (h->err.code) return h->err.code;
+  if (count < 0) { h->err.set(TEBD_EINVAL, "sweep count %lld < 0", (long long)count); return h->err.code; }
+  const uint64_t c = (uint64_t)count;
+  CU_OR(h, cudaMemcpyAsync(h->sweep_dev, &c, sizeof c, cudaMemcpyHostToDevice, h->stream));
+  CU_OR(h, cudaStreamSynchronize(h->stream));
+  h->sweeps = count;
+  return TEBD_OK;
+}
+
+extern "C" int tebd_bond_weights(tebd_t h, double* out) {
+  if (!h) return TEBD_EINVAL;
+  if (h->err.code) return h->err.code;
+  if (!out) { h->err.set(TEBD_EINVAL, "NULL pointer"); return h->err.code; }
+  const ChainH& C = h->ch[h->cur];
+  CU_OR(h, cudaMemcpyAsync(out, C.wbond, sizeof(double) * (C.N - 1), cudaMemcpyDeviceToHost, h->stream));
+  return tebd_check_status(h);
+}
+
 extern "C" int tebd_workspace_info(tebd_t h, size_t* arena_bytes, int* waves_even, int* waves_odd) {
   if (!h) return TEBD_EINVAL;
   if (arena_bytes) *arena_bytes = h->arena_bytes;
@@ -964,11 +1115,15 @@ static int tebd_adj_alloc(tebd_t h) {
     }
   const size_t desc_off = off;
   for (int par = 0; par < 2; ++par) off += align_up(sizeof(AdjPtr) * std::max<size_t>(1, h->par[par].bonds.size()));
-  if (cudaMalloc(&h->adj_arena, off) != cudaSuccess) {
-    cudaGetLastError();
-    h->adj_arena = nullptr;
-    h->err.set(TEBD_ENOMEM, "reverse-pass buffers of %zu bytes failed", off);
-    return h->err.code;
+  {
+    void* blk = nullptr;
+    const int rc = h->alloc.get(off, &blk);
+    if (rc != TEBD_OK) {
+      h->adj_arena = nullptr;
+      h->err.set(rc, "reverse-pass buffers of %zu bytes failed", off);
+      return h->err.code;
+    }
+    h->adj_arena = (char*)blk;
   }
   char* A = h->adj_arena;
   h->gbar0 = (cplx*)A;
@@ -1048,10 +1203,14 @@ extern "C" int tebd_backward(tebd_t h, int site, const double* op, double* dgate
   char* region = h->arena + C.gamma_lo;
   // keep the final state, sweep counter and weights to restore them afterwards
   char* save = nullptr;
-  if (cudaMalloc(&save, rbytes + 2 * ALIGN + align_up(sizeof(double) * 2 * h->ch.size())) != cudaSuccess) {
-    cudaGetLastError();
-    h->err.set(TEBD_ENOMEM, "reverse-pass save buffer failed");
-    return h->err.code;
+  {
+    void* blk = nullptr;
+    const int arc = h->alloc.get(rbytes + 2 * ALIGN + align_up(sizeof(double) * 2 * h->ch.size()), &blk);
+    if (arc != TEBD_OK) {
+      h->err.set(arc, "reverse-pass save buffer failed");
+      return h->err.code;
+    }
+    save = (char*)blk;
   }
   int rc = TEBD_OK;
   do {
@@ -1139,7 +1298,7 @@ extern "C" int tebd_backward(tebd_t h, int site, const double* op, double* dgate
   cudaMemcpyAsync(h->sweep_dev, save + rbytes, sizeof(uint64_t), cudaMemcpyDeviceToDevice, st);
   cudaMemcpyAsync(h->wacc, save + rbytes + ALIGN, sizeof(double) * 2 * h->ch.size(), cudaMemcpyDeviceToDevice, st);
   const cudaError_t e = cudaStreamSynchronize(st);
-  cudaFree(save);
+  h->alloc.put(save);
   if (rc == TEBD_OK && e != cudaSuccess) rc = TEBD_ECUDA;
   if (rc != TEBD_OK) {
     h->err.set(rc, "reverse pass failed: %s", cudaGetErrorString(cudaGetLastError()));
@@ -1176,31 +1335,25 @@ struct rrsvd_plan_s {
 };
 
 namespace tg {
-// Fills the per-instance pointers from the call's buffers.
 __global__ void k_rrsvd_bind(ProbPtr* ptrs, int batch, char* ws, size_t per, WsLayout lay, const cplx* theta,
-                             size_t theta_stride, cplx* U, size_t U_stride, cplx* Vh, size_t V_stride) {
+                             size_t theta_stride, cplx* U, size_t U_stride, cplx* Vh, size_t V_stride, Dims* dims,
+                             int dims_m, int dims_n, int dims_k, int dims_l, int* status) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (dims_m > 0 && p == 0) *status = 0;
   if (p >= batch) return;
   ProbPtr P;
   memset(&P, 0, sizeof P);
-  char* base = ws + per * (size_t)p;
+  fill_ptrs(P, ws + per * (size_t)p, lay);
   P.theta = theta + theta_stride * p;
-  P.omega = (cplx*)(base + lay.omega);
-  P.Y = (cplx*)(base + lay.Y);
-  P.Q = (cplx*)(base + lay.Q);
-  P.Yt = (cplx*)(base + lay.Yt);
-  P.Qt = (cplx*)(base + lay.Qt);
-  P.R = (cplx*)(base + lay.R);
-  P.J = (cplx*)(base + lay.J);
-  P.Jk = (cplx*)(base + lay.Jk);
-  P.Wk = (cplx*)(base + lay.Wk);
-  P.U = U ? U + U_stride * p : (cplx*)(base + lay.U);
-  P.V = Vh ? Vh + V_stride * p : (cplx*)(base + lay.V);
-  P.sigma = (double*)(base + lay.sigma);
-  P.part = (double*)(base + lay.part);
-  P.scal = (double*)(base + lay.scal);
-  P.Dr = (cplx*)(base + lay.Dr);
+  if (U) P.U = U + U_stride * p;
+  if (Vh) P.V = Vh + V_stride * p;
   ptrs[p] = P;
+  if (dims_m > 0) {
+    Dims D;
+    memset(&D, 0, sizeof D);
+    D.m = dims_m; D.n = dims_n; D.k = dims_k; D.l = dims_l; D.bond = 0; D.active = 1;
+    dims[p] = D;
+  }
 }
 }  // namespace tg
 
@@ -1238,7 +1391,11 @@ extern "C" int rrsvd_plan_create_ex(int m, int n, int k_max, int p, int q, int b
     P->ws_bytes += mixed_bytes(P->ms, batch);
   }
   const size_t meta = align_up(sizeof(Dims) * batch) + align_up(sizeof(ProbPtr) * batch) + 2 * ALIGN;
-  if (cudaMalloc(&P->meta, meta) != cudaSuccess) { cudaGetLastError(); delete P; return TEBD_ENOMEM; }
+  if (fault_take(TEBD_FAULT_ALLOC) || cudaMalloc(&P->meta, meta) != cudaSuccess) {
+    cudaGetLastError();
+    delete P;
+    return TEBD_ENOMEM;
+  }
   P->dims = (Dims*)P->meta;
   P->ptrs = (ProbPtr*)(P->meta + align_up(sizeof(Dims) * batch));
   P->status = (int*)(P->meta + align_up(sizeof(Dims) * batch) + align_up(sizeof(ProbPtr) * batch));
@@ -1310,7 +1467,7 @@ extern "C" int rrsvd_execute(rrsvd_plan_t P, const double* theta, int64_t chain0
   k_rrsvd_bind<<<(P->batch + 127) / 128, 128, 0, st>>>(P->ptrs, P->batch, (char*)workspace, P->per, P->lay,
                                                      (const cplx*)theta, (size_t)P->m * P->n,
                                                      checked ? nullptr : (cplx*)U, (size_t)P->m * P->k, (cplx*)Vh,
-                                                     (size_t)P->k * P->n);
+                                                     (size_t)P->k * P->n, nullptr, 0, 0, 0, 0, nullptr);
   }
   CU_OR(P, cudaGetLastError());
   if (checked) {
@@ -1347,8 +1504,9 @@ extern "C" int rrsvd_execute_host(rrsvd_plan_t P, const double* theta, int64_t c
                ww = align_up(sizeof(double) * B), rr = align_up(sizeof(int) * B);
   const size_t need = th + sg + uu + vv + ww + rr + P->ws_bytes;
   if (!P->stage) {
-    if (cudaMalloc(&P->stage, need) != cudaSuccess) {
+    if (fault_take(TEBD_FAULT_ALLOC) || cudaMalloc(&P->stage, need) != cudaSuccess) {
       cudaGetLastError();
+      P->stage = nullptr;
       P->err.set(TEBD_ENOMEM, "staging allocation of %zu bytes failed", need);
       return P->err.code;
     }
@@ -1393,3 +1551,16 @@ extern "C" int rrsvd_execute_host(rrsvd_plan_t P, const double* theta, int64_t c
 }
 
 extern "C" const char* rrsvd_last_error(rrsvd_plan_t P) { return P ? P->err.msg.c_str() : "NULL plan"; }
+
+extern "C" int rrsvd_clear_error(rrsvd_plan_t P) {
+  if (!P) return TEBD_EINVAL;
+  P->err.code = TEBD_OK;
+  P->err.msg.clear();
+  // status and the tensor-core flag sit in the two ALIGN-sized slots after
+  // the descriptors
+  if (cudaMemset(P->status, 0, 2 * ALIGN) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+    P->err.set(TEBD_ECUDA, "clearing the device flags failed");
+    return P->err.code;
+  }
+  return TEBD_OK;
+}

@@ -46,6 +46,7 @@ struct ProbPtr {
   int bond_s;         // bond index within its chain
   int chain_s;        // Philox chain index of the chain
   int slot;           // chain slot in the handle (discarded-weight accumulators)
+  double* wbond;      // where the bond's latest discarded weight goes (TEBD only), or null
   // RRSVD buffers
   const cplx* theta;  // m x n (read only for the sketches)
   cplx* omega;        // n x l

@@ -33,6 +33,8 @@
 #include "dfsplit.cuh"
 #include "profiler.cuh"
 #include "tc_gemm.cuh"
+#include "workspace.cuh"
+#include "../../include/tebd_gb300.h"
 
 namespace tg {
 
@@ -473,6 +475,13 @@ static cudaError_t tc_product(const float* A0, const float* A1, const float* B0,
   a.out = out;
   a.out_stride = (int64_t)rows * l;
   a.err = err;
+  // an injected pipeline stall (test hook): no operand copies, short waits
+  // (never inside a stream capture, where it would stall every replay)
+  cudaStreamCaptureStatus cap_st = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap_st) != cudaSuccess) cap_st = cudaStreamCaptureStatusActive;
+  const bool stall = cap_st == cudaStreamCaptureStatusNone && fault_take(TEBD_FAULT_TC_STALL);
+  a.poll_limit = stall ? (1u << 12) : (1u << 24);
+  a.stall = stall ? 1 : 0;
   const size_t sm = tc_smem_bytes(s.BN);
   static int attr_done = 0;  // set once for the largest tile (also by mixed_prepare)
   if (!attr_done) {

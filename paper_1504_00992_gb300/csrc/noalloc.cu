@@ -33,6 +33,8 @@
 
 #include "../../include/tebd_gb300.h"
 #include "internal.cuh"
+#include "profiler.cuh"
+#include "workspace.cuh"
 
 namespace tg {
 
@@ -44,70 +46,11 @@ namespace {
 const size_t NA_ALIGN = 256;
 inline size_t na_up(size_t x) { return (x + NA_ALIGN - 1) & ~(NA_ALIGN - 1); }
 
-// byte offsets of one instance's buffers inside its slice of the array
-struct NaLayout {
-  size_t omega, Y, Q, Yt, Qt, R, J, Jk, Wk, U, V, sigma, part, scal, total;
-};
-
-NaLayout na_layout(int m, int n, int k, int l) {
-  NaLayout w;
-  const size_t c = sizeof(cplx);
-  size_t o = 0;
-  w.omega = o; o += na_up(c * (size_t)n * l);
-  w.Y = o; o += na_up(c * (size_t)m * l);
-  w.Q = o; o += na_up(c * (size_t)m * l);
-  w.Yt = o; o += na_up(c * (size_t)n * l);
-  w.Qt = o; o += na_up(c * (size_t)n * l);
-  w.R = o; o += na_up(c * std::max((size_t)l * l, qr_multi_scratch_r(l)));  // many-CTA QR scratch
-  w.J = o; o += na_up(c * std::max((size_t)l * l, qr_multi_scratch_j(l)));
-  w.Jk = o; o += na_up(c * (size_t)l * k);
-  w.Wk = o; o += na_up(c * (size_t)l * k);
-  w.U = o; o += na_up(c * (size_t)m * k);
-  w.V = o; o += na_up(c * (size_t)k * n);
-  w.sigma = o; o += na_up(sizeof(double) * (size_t)l);
-  w.part = o; o += na_up(sizeof(double) * NPART);
-  w.scal = o; o += na_up(sizeof(double) * 4);
-  w.total = o;
-  return w;
-}
-
 std::mutex na_mu;
 const int NA_MAXDEV = 64;
 void* na_addr[NA_MAXDEV] = {nullptr};
 
 }  // namespace
-
-// Writes the descriptors of every instance into the array and clears the
-// status word (the one value that must start at zero).
-__global__ void k_noalloc_bind(Dims* dims, ProbPtr* ptrs, int* status, int batch, int m, int n, int k, int l,
-                               char* ws, size_t per, NaLayout lay, const cplx* theta, cplx* U, cplx* Vh) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p == 0) *status = 0;
-  if (p >= batch) return;
-  Dims D;
-  memset(&D, 0, sizeof D);
-  D.m = m; D.n = n; D.k = k; D.l = l; D.bond = 0; D.active = 1;
-  dims[p] = D;
-  ProbPtr P;
-  memset(&P, 0, sizeof P);
-  char* base = ws + per * (size_t)p;
-  P.theta = theta + (size_t)m * n * p;
-  P.omega = (cplx*)(base + lay.omega);
-  P.Y = (cplx*)(base + lay.Y);
-  P.Q = (cplx*)(base + lay.Q);
-  P.Yt = (cplx*)(base + lay.Yt);
-  P.Qt = (cplx*)(base + lay.Qt);
-  P.R = (cplx*)(base + lay.R);
-  P.J = (cplx*)(base + lay.J);
-  P.Jk = (cplx*)(base + lay.Jk);
-  P.Wk = (cplx*)(base + lay.Wk);
-  P.U = U ? U + (size_t)m * k * p : (cplx*)(base + lay.U);
-  P.V = Vh ? Vh + (size_t)k * n * p : (cplx*)(base + lay.V);
-  P.sigma = (double*)(base + lay.sigma);
-  P.part = (double*)(base + lay.part);
-  P.scal = (double*)(base + lay.scal);
-  ptrs[p] = P;
-}
 
 }  // namespace tg
 
@@ -122,7 +65,9 @@ extern "C" int rrsvd_execute_noalloc(int m, int n, int k_max, int p, int q, int 
   const int mn = m < n ? m : n;
   const int l = (k + p < mn) ? k + p : mn;
   if (l > 512) return TEBD_EINVAL;
-  const NaLayout lay = na_layout(m, n, k, l);
+  // the workspace layout of an rrsvd plan of the same sizes (U and V^H have
+  // room in it, for calls that pass NULL for them)
+  const WsLayout lay = ws_layout(m, n, k, l, true, true, 0);
   const size_t head = na_up(sizeof(Dims) * (size_t)batch) + na_up(sizeof(ProbPtr) * (size_t)batch) + NA_ALIGN;
   const size_t need = head + lay.total * (size_t)batch;
   if (need > NOALLOC_SCRATCH_BYTES) return TEBD_EINVAL;  // beyond the fixed 16 MiB scratch
@@ -144,8 +89,14 @@ extern "C" int rrsvd_execute_noalloc(int m, int n, int k_max, int p, int q, int 
   int* status = (int*)(base + na_up(sizeof(Dims) * (size_t)batch) + na_up(sizeof(ProbPtr) * (size_t)batch));
   char* ws = base + head;
   cudaStream_t st = (cudaStream_t)stream;
-  k_noalloc_bind<<<(batch + 127) / 128, 128, 0, st>>>(dims, ptrs, status, batch, m, n, k, l, ws, lay.total, lay,
-                                                     (const cplx*)theta, (cplx*)U, (cplx*)Vh);
+  {
+    // descriptors of every instance, and the status word cleared (the one
+    // value of the array that must start at zero)
+    ProfScope ps("k_rrsvd_bind", st);
+    k_rrsvd_bind<<<(batch + 127) / 128, 128, 0, st>>>(ptrs, batch, ws, lay.total, lay, (const cplx*)theta,
+                                                       (size_t)m * n, (cplx*)U, (size_t)m * k, (cplx*)Vh,
+                                                       (size_t)k * n, dims, m, n, k, l, status);
+  }
   if (cudaGetLastError() != cudaSuccess) return TEBD_ECUDA;
   Caps cap;
   memset(&cap, 0, sizeof cap);

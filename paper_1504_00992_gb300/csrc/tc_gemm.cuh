@@ -19,8 +19,9 @@
 //                       tcgen05.commit -> mbarrier,
 //   all 4 warps       : epilogue, tcgen05.ld 32x32b from the accumulator
 //                       (warp w owns TMEM lanes 32w..32w+31 = tile rows).
-// Every mbarrier wait is bounded; on expiry the kernel raises *err, skips
-// the remaining work, waits (bounded) for its own copies and frees TMEM.
+// Every mbarrier wait is bounded (poll_limit polls); on expiry the kernel
+// raises *err, skips the remaining work, waits (bounded) for its own copies
+// and for the MMAs it already issued, and frees TMEM.
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -39,6 +40,8 @@ struct TcArgs {
   float2* out;    // complex output, column-major M x l, instance stride out_stride
   int64_t out_stride;
   int* err;       // error flag (timeouts)
+  uint32_t poll_limit;  // polls of a pipeline wait before it gives up (1 << 24)
+  int stall;      // test hook: the producer issues no copies, so the waits expire
 };
 
 __device__ __forceinline__ uint32_t tc_smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -63,8 +66,9 @@ __device__ __forceinline__ bool tc_mbar_try_wait(uint64_t* bar, uint32_t parity)
 }
 // Bounded wait on a phase of an mbarrier; returns false (and raises *err /
 // the CTA abort flag) when the limit expires or another thread gave up.
-__device__ __forceinline__ bool tc_mbar_wait(uint64_t* bar, uint32_t parity, int* err, volatile int* abort_flag) {
-  for (uint32_t i = 0; i < (1u << 24); ++i) {
+__device__ __forceinline__ bool tc_mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit, int* err,
+                                             volatile int* abort_flag) {
+  for (uint32_t i = 0; i < limit; ++i) {
     if (tc_mbar_try_wait(bar, parity)) return true;
     if ((i & 1023u) == 1023u && *abort_flag) return false;
   }
@@ -110,7 +114,8 @@ __global__ void __launch_bounds__(128, 1)
   uint64_t* full = (uint64_t*)(sB + TC_STAGES * bytesB);
   uint64_t* empty = full + TC_STAGES;
   uint64_t* accf = empty + TC_STAGES;
-  uint32_t* tmem_holder = (uint32_t*)(accf + 1);
+  uint64_t* drain = accf + 1;  // completion of the MMAs issued before an abort
+  uint32_t* tmem_holder = (uint32_t*)(drain + 1);
   volatile int* abort_flag = (volatile int*)(tmem_holder + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -130,6 +135,7 @@ __global__ void __launch_bounds__(128, 1)
       tc_mbar_init(&empty[s], 1);
     }
     tc_mbar_init(accf, 1);
+    tc_mbar_init(drain, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -141,10 +147,10 @@ __global__ void __launch_bounds__(128, 1)
   if (warp == 0 && lane == 0) {
     // ---- producer
     int issued = 0;
-    for (int it = 0; it < iters; ++it) {
+    for (int it = 0; it < (a.stall ? 0 : iters); ++it) {
       const int s = it % TC_STAGES;
       const uint32_t r = (uint32_t)(it / TC_STAGES);
-      if (it >= TC_STAGES && !tc_mbar_wait(&empty[s], (r & 1u) ^ 1u, a.err, abort_flag)) break;
+      if (it >= TC_STAGES && !tc_mbar_wait(&empty[s], (r & 1u) ^ 1u, a.poll_limit, a.err, abort_flag)) break;
       const int pass = it / KB, kb = it % KB;
       const CUtensorMap* ta = (pass == 2) ? &tmA1 : &tmA0;
       const CUtensorMap* tb = (pass == 1) ? &tmB1 : &tmB0;
@@ -163,10 +169,11 @@ __global__ void __launch_bounds__(128, 1)
     // ---- MMA issuer
     const uint32_t idesc = tc_idesc_tf32(TC_BM, a.BN);
     bool ok = true;
+    int issued_mma = 0;
     for (int it = 0; it < iters; ++it) {
       const int s = it % TC_STAGES;
       const uint32_t r = (uint32_t)(it / TC_STAGES);
-      if (!tc_mbar_wait(&full[s], r & 1u, a.err, abort_flag)) { ok = false; break; }
+      if (!tc_mbar_wait(&full[s], r & 1u, a.poll_limit, a.err, abort_flag)) { ok = false; break; }
       tc_fence_after();
       const uint32_t aa = tc_smem_u32(sA + s * bytesA), bb = tc_smem_u32(sB + s * bytesB);
 #pragma unroll
@@ -183,19 +190,37 @@ __global__ void __launch_bounds__(128, 1)
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                        tc_smem_u32(&empty[s]))
                    : "memory");
+      issued_mma = it + 1;
     }
-    if (ok)
+    if (ok) {
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                        tc_smem_u32(accf))
                    : "memory");
-    else
+    } else {
       *abort_flag = 1;
+      if (issued_mma > 0) {
+        // the MMAs already issued read shared memory and write the tensor
+        // memory freed below: wait (bounded) until they have completed
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         tc_smem_u32(drain))
+                     : "memory");
+        for (uint32_t i = 0; i < a.poll_limit; ++i)
+          if (tc_mbar_try_wait(drain, 0)) break;
+      }
+    }
   }
   __syncwarp();
   // ---- epilogue: every thread owns one row of the tile
-  const bool have = tc_mbar_wait(accf, 0, a.err, abort_flag);
+  const bool have = tc_mbar_wait(accf, 0, a.poll_limit, a.err, abort_flag);
   tc_fence_after();
-  if (have) {
+  if (!have) {
+    // aborted: defined (zero) output for the kernels that read it next; the
+    // timeout flag already marks the result as invalid
+    const int row = m0 + warp * 32 + lane;
+    float2* out = a.out + a.out_stride * z;
+    if (row < a.M)
+      for (int cc = n0 / 2; cc < (n0 + a.BN) / 2 && cc < a.l; ++cc) out[(int64_t)cc * a.M + row] = make_float2(0.f, 0.f);
+  } else {
     const int row = m0 + warp * 32 + lane;
     float2* out = a.out + a.out_stride * z;
     for (int c0 = 0; c0 < a.BN; c0 += 16) {
@@ -227,7 +252,7 @@ __global__ void __launch_bounds__(128, 1)
 }
 
 inline size_t tc_smem_bytes(int BN) {
-  return 1024 + (size_t)TC_STAGES * (TC_BM * TC_BK * 4 + (size_t)BN * TC_BK * 4) + (2 * TC_STAGES + 1) * 8 + 16;
+  return 1024 + (size_t)TC_STAGES * (TC_BM * TC_BK * 4 + (size_t)BN * TC_BK * 4) + (2 * TC_STAGES + 2) * 8 + 16;
 }
 
 }  // namespace tg

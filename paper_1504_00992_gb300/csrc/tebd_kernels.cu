@@ -318,6 +318,7 @@ __global__ void k_wacc(const Dims* dims, const ProbPtr* ptrs, const double* wout
     const int s = ptrs[p].slot;
     wacc[2 * s] += wout[p];
     wacc[2 * s + 1] *= (1.0 - wout[p]);
+    if (ptrs[p].wbond) *ptrs[p].wbond = wout[p];
   }
 }
 
