@@ -4,23 +4,29 @@ benchmark times, on sampled outputs the oracle computes one by one.
 Spin-boson chain (spin + 100 bosons, d 32 -> 4, caps 256 -> 64; graphs,
 40 GB wave budget): one even sweep from a full-size state on the device, then
 sampled even bonds -- the spin bond, the largest theta of the sweep
-(~7800 x 7500), a middle and the last one -- against the oracle's update of
-the same bond from the same state and the same Omega (Section II.B with the
-RRSVD of Section IV).  Even bonds touch disjoint sites, so each sampled
-bond's result depends on the pre-sweep state alone.  The state is a seeded
-random Vidal form at the caps, not brought into canonical form: the update's
-arithmetic does not need it, and it keeps the generation cheap at this size.
-Its spectra have no gap at the caps, so the smallest kept Schmidt values of
-any randomized truncation move with the rounding order (up to ~5e-6 between
-two FP64 codes on the same Omega): they are held to 1e-5, the spin bond (no
-truncation) to the form's tolerance.
+(~7800 x 7500, many-CTA QRs and the cluster Jacobi at l = 266), a middle and
+the last one -- against the oracle's update of the same bond from the same
+state and the same Omega (Section II.B with the RRSVD of Section IV).  Even
+bonds touch disjoint sites, so each sampled bond's result depends on the
+pre-sweep state alone.  The states are seeded random Vidal forms at the caps
+(not canonicalised: the update's arithmetic does not need it), in two kinds:
+  * gapped: Schmidt values e^{-j/4}, so theta's spectrum falls far below the
+    1e-14 cutoff well before the cap and every kept value is resolved by the
+    sketch: held to the FP64 bar -- kept values 1e-10 s_1 (normwise), the
+    truncated theta 1e-10 in Frobenius norm, the discarded weight 1e-12;
+  * gapless: Schmidt values e^{-j/(chi/8)}, with no gap at the cap: the
+    smallest kept values of any randomized truncation then move with the
+    rounding order of its QRs.  The oracle against itself with its
+    hand-written Householder QR in place of LAPACK's measures that spread on
+    the largest bond, and the GPU is held to a few times it.
 
 Many-chain batch (256 uneven XXZ chains, p = 10, q = 1, dt = 0.01; graphs,
-16 GB wave budget, waves on both parities): two second-order steps, then
-sampled chains against their own oracle runs at the form's tolerances.  Their
-Schmidt spectra reach the 1e-14 cutoff (a value of 1.00006e-14 relative is
-kept by the FP64 oracle and rounds below the cutoff in the TF32 form), so the
-kept ranks may differ by such values and the lists are compared zero-padded."""
+16 GB wave budget, waves on both parities): ten second-order steps, then
+sampled chains against their own oracle runs at the form's tolerances (FP64:
+Schmidt values and observables 1e-10).  Their Schmidt spectra reach the
+1e-14 cutoff (a value of 1.00006e-14 relative is kept by the FP64 oracle and
+rounds below the cutoff in the TF32 form), so the kept ranks may differ by
+such values and the lists are compared zero-padded."""
 import numpy as np
 import pytest
 
@@ -33,10 +39,11 @@ SB_SIZE = (100, 32, 4, 256, 64)
 SB_DT, SB_P, SB_Q, SB_SEED = 0.05, 10, 2, 3
 
 
-def _random_vidal_state(dims, caps, seed):
+def _random_vidal_state(dims, caps, seed, decay=None):
     """Gamma[s] complex Gaussian (d, chi_{s-1}, chi_s) scaled to O(1) bond
-    norms; lambda[b] decaying as exp(-j / (chi/8)), unit 2-norm; every bond at
-    its cap min(chi_b, prod_{s<=b} d_s, prod_{s>b} d_s)."""
+    norms; lambda[b] decaying as exp(-j / decay) (decay = chi/8 when None),
+    unit 2-norm; every bond at its cap min(chi_b, prod_{s<=b} d_s,
+    prod_{s>b} d_s)."""
     rng = np.random.default_rng(seed)
     N = len(dims)
     chi = [1]
@@ -50,51 +57,132 @@ def _random_vidal_state(dims, caps, seed):
         gam.append((rng.standard_normal(shape) + 1j * rng.standard_normal(shape)) / np.sqrt(2.0 * dims[s] * chi[s]))
     lam = []
     for b in range(N - 1):
-        x = np.exp(-np.arange(chi[b + 1]) / max(1.0, chi[b + 1] / 8.0))
+        dc = decay if decay is not None else max(1.0, chi[b + 1] / 8.0)
+        x = np.exp(-np.arange(chi[b + 1]) / dc)
         lam.append(x / np.linalg.norm(x))
     return gam, lam, chi
 
 
-@pytest.fixture(scope="module")
-def spin_boson_case():
-    dims, caps = I.spin_boson_sizes(*SB_SIZE)
-    g0, lam0, chi = _random_vidal_state(dims, caps, 5)
-    gates = I.trotter_gates(I.spin_boson_bond_terms(dims), SB_DT / 2)
-    N = len(dims)
-    even = list(range(0, N - 1, 2))
+def _sampled_bonds(dims, chi):
+    even = list(range(0, len(dims) - 1, 2))
     size = {b: dims[b] * chi[b] * dims[b + 1] * chi[b + 2] for b in even}
     largest = max(even, key=lambda b: size[b])
-    sample = sorted({0, 2, largest, 50, even[-1]})
+    return sorted({0, 2, largest, 50, even[-1]}), largest
+
+
+def _oracle_refs(dims, caps, g0, lam0, gates, sample, keep_theta):
+    """The oracle's update of each sampled bond from the same state: its
+    Schmidt values, the boson number of site b+1, its discarded weight and,
+    with keep_theta, its truncated theta normalised like lambda (unit
+    Frobenius norm)."""
     ref = {}
     for b in sample:
         mps = T.VidalMPS(g0, lam0)
         info = T.bond_update(mps, b, gates[b], caps[b], SB_P, SB_Q, SB_SEED, 0)
         nb = I.boson_ops(dims[b + 1])[2]
-        ref[b] = (mps.lam[b].copy(), T.expect_onesite(mps, b + 1, nb).real, info["theta"].shape)
+        ref[b] = {"lam": mps.lam[b].copy(), "n": T.expect_onesite(mps, b + 1, nb).real,
+                  "shape": info["theta"].shape, "w": info["w"]}
+        if keep_theta:
+            ref[b]["theta_k"] = info["theta_k"] / np.sqrt(np.sum(info["s"] ** 2))
+    return ref
+
+
+def _padded_diff(x, y):
+    r = max(len(x), len(y))
+    a, b = np.zeros(r), np.zeros(r)
+    a[:len(x)], b[:len(y)] = x, y
+    return float(np.abs(a - b).max())
+
+
+@pytest.fixture(scope="module")
+def spin_boson_gapless():
+    dims, caps = I.spin_boson_sizes(*SB_SIZE)
+    g0, lam0, chi = _random_vidal_state(dims, caps, 5)
+    gates = I.trotter_gates(I.spin_boson_bond_terms(dims), SB_DT / 2)
+    sample, largest = _sampled_bonds(dims, chi)
+    ref = _oracle_refs(dims, caps, g0, lam0, gates, sample, False)
+    # the oracle against itself on the largest bond: LAPACK's QR replaced by
+    # the hand-written Householder QR, everything else identical
+    from oracle import linalg as OL
+    from oracle import rrsvd as OR
+    saved = OR._qr_q
+    try:
+        OR._qr_q = lambda Y: OL.householder_qr(Y)[0]
+        mps = T.VidalMPS(g0, lam0)
+        T.bond_update(mps, largest, gates[largest], caps[largest], SB_P, SB_Q, SB_SEED, 0)
+        lam_hw = mps.lam[largest].copy()
+    finally:
+        OR._qr_q = saved
+    spread = _padded_diff(ref[largest]["lam"], lam_hw)
+    return dims, caps, g0, lam0, gates, sample, ref, spread
+
+
+@pytest.fixture(scope="module")
+def spin_boson_gapped():
+    dims, caps = I.spin_boson_sizes(*SB_SIZE)
+    g0, lam0, chi = _random_vidal_state(dims, caps, 6, decay=4.0)
+    gates = I.trotter_gates(I.spin_boson_bond_terms(dims), SB_DT / 2)
+    sample, _ = _sampled_bonds(dims, chi)
+    ref = _oracle_refs(dims, caps, g0, lam0, gates, sample, True)
     return dims, caps, g0, lam0, gates, sample, ref
 
 
-@pytest.mark.parametrize("prec,tol_spin", [(0, 1e-8), (2, 2e-7)])
-def test_spin_boson_full_size_sampled_bonds(lib, spin_boson_case, prec, tol_spin):
-    from paper_1504_00992_gb300 import binding as B
-    dims, caps, g0, lam0, gates, sample, ref = spin_boson_case
-    assert max(np.prod(ref[b][2]) for b in sample) > 7000 * 7000   # the largest theta is in the sample
+def _run_even_sweep(B, dims, caps, g0, lam0, gates, prec):
     sim = B.Tebd(len(dims), 2, 0, SB_P, SB_Q, SB_SEED, d_site=dims, chi_bond=caps, precision=prec,
                  use_graph=1, workspace_budget=40 << 30)
+    sim.set_mps(g0, lam0)
+    sim.set_gates(0, gates)
+    sim.set_gates(1, gates)
+    sim.step_even()
+    return sim
+
+
+@pytest.mark.parametrize("prec,tol_lam,tol_theta,tol_w", [(0, 1e-10, 1e-10, 1e-12), (2, 2e-7, 1e-6, 1e-10)])
+def test_spin_boson_full_size_gapped(lib, spin_boson_gapped, prec, tol_lam, tol_theta, tol_w):
+    from paper_1504_00992_gb300 import binding as B
+    dims, caps, g0, lam0, gates, sample, ref = spin_boson_gapped
+    assert max(np.prod(ref[b]["shape"]) for b in sample) > 7000 * 7000   # the largest theta is in the sample
+    sim = _run_even_sweep(B, dims, caps, g0, lam0, gates, prec)
     try:
-        sim.set_mps(g0, lam0)
-        sim.set_gates(0, gates)
-        sim.set_gates(1, gates)
-        sim.step_even()
+        gam, lam = sim.get_mps()
+        wb = sim.bond_weights()
         for b in sample:
-            lam_o, n_o, _ = ref[b]
+            r = ref[b]
+            dl = _padded_diff(lam[b], r["lam"])
+            # the truncated theta from the rebuilt tensors (gauge invariant):
+            # lambda_l Gamma'[b] lambda' Gamma'[b+1] lambda_r in i-major blocks
+            ll = lam[b - 1] if b > 0 else np.ones(1)
+            lr = lam[b + 1] if b + 1 < len(lam) else np.ones(1)
+            X = (ll[None, :, None] * gam[b] * lam[b][None, None, :]).reshape(-1, len(lam[b]))
+            Y = (gam[b + 1] * lr[None, None, :]).transpose(1, 0, 2).reshape(len(lam[b]), -1)
+            dth = float(np.linalg.norm(X @ Y - r["theta_k"]))
+            dw = abs(wb[b] - r["w"])
+            assert dl <= tol_lam, (b, dl, dth, dw)
+            assert dth <= tol_theta, (b, dl, dth, dw)
+            assert dw <= tol_w, (b, dl, dth, dw)
+    finally:
+        sim.close()
+
+
+@pytest.mark.parametrize("prec,tol_spin", [(0, 1e-8), (2, 2e-7)])
+def test_spin_boson_full_size_gapless(lib, spin_boson_gapless, prec, tol_spin):
+    from paper_1504_00992_gb300 import binding as B
+    dims, caps, g0, lam0, gates, sample, ref, spread = spin_boson_gapless
+    # two correct FP64 codes on this input disagree by `spread` on the
+    # smallest kept values: they are not determined more finely than that
+    assert 1e-9 < spread < 1e-4, spread
+    tol = max(4.0 * spread, 1e-8)
+    sim = _run_even_sweep(B, dims, caps, g0, lam0, gates, prec)
+    try:
+        for b in sample:
+            lam_o, n_o = ref[b]["lam"], ref[b]["n"]
             lg = sim.get_lambda(b)
             assert len(lg) == len(lam_o), b
-            assert np.abs(lg - lam_o).max() <= (tol_spin if b == 0 else 1e-5), b
+            assert np.abs(lg - lam_o).max() <= (tol_spin if b == 0 else tol), (b, spread)
             # the rebuilt Gamma of site b+1 (V^H / lambda_r): its boson number,
             # a gauge-invariant function of the new tensors
             n_g = sim.expect(b + 1, I.boson_ops(dims[b + 1])[2]).real
-            assert abs(n_g - n_o) <= (tol_spin if b == 0 else 1e-5) * (dims[b + 1] - 1), b
+            assert abs(n_g - n_o) <= (tol_spin if b == 0 else tol) * (dims[b + 1] - 1), b
     finally:
         sim.close()
 
@@ -111,13 +199,13 @@ def _xxz_oracle(N, d, chi, delta, steps, dt, p, q, seed, chain):
 
 
 @pytest.mark.parametrize("prec,tol_obs,tol_lam,extra", [
-    (0, 1e-8, 1e-8, {"autotune": 1}),
+    (0, 1e-10, 1e-10, {"autotune": 1}),
     (2, 1e-7, 2e-7, {}),
 ])
 def test_many_chain_batch_full_size_sampled(lib, prec, tol_obs, tol_lam, extra):
     from paper_1504_00992_gb300 import binding as B
     specs = I.many_chain_specs(256, 0)
-    steps, dt, p, q, seed = 2, 0.01, 10, 1, 0
+    steps, dt, p, q, seed = 10, 0.01, 10, 1, 0
     chains = [(N, [d] * N, [chi] * (N - 1)) for N, d, chi, _ in specs]
     sim = B.MultiTebd(chains, p, q, seed, use_graph=1, workspace_budget=16 << 30, precision=prec, **extra)
     try:
@@ -141,10 +229,7 @@ def test_many_chain_batch_full_size_sampled(lib, prec, tol_obs, tol_lam, extra):
                 # a Schmidt value within rounding of the 1e-14 cutoff may be
                 # kept on one side only: the shorter list is padded with zeros,
                 # and the values only one side kept must lie at the cutoff
-                r = max(len(lg), len(lo))
-                pg, po = np.zeros(r), np.zeros(r)
-                pg[:len(lg)], po[:len(lo)] = lg, lo
-                assert np.abs(pg - po).max() <= tol_lam, (c, b)
+                assert _padded_diff(lg, lo) <= tol_lam, (c, b)
                 tail = min(len(lg), len(lo))
                 assert np.all(np.concatenate([lg[tail:], lo[tail:]]) <= 2e-14 * lo[0]), (c, b)
             assert abs(sim.discarded_weight(c)[0] - w_o) <= 1e-10, c

@@ -1,18 +1,27 @@
-"""The no-allocation truncation entry point (for callers that cannot call
-cudaMalloc, e.g. code inside another library's scheduling loop or a host
-callback, or a process whose device memory is reserved up front) gives the
-same results as the workspace-based rrsvd_execute, on two calls in a row
-that reuse its static scratch.  Collected last on purpose."""
+"""The no-allocation truncation entry point, for callers that cannot call
+cudaMalloc (code inside another library's scheduling loop or a host callback
+that must not block, or a process whose device memory is reserved up front):
+it gives the oracle's truncation (Alg. 1 and the projection steps of
+Section IV, same Omega) and the same results as the workspace-based
+rrsvd_execute, on calls in a row that reuse its static scratch, and the
+device's free memory does not move across a call.
+
+The file name sorts last so that a run stopping at the first failure has run
+every other test first: the entry point's one-time set-up (the lookup of its
+static array's device address) then also happens after the rest of the suite
+has used the device, as well as in a fresh process when run alone."""
 import numpy as np
 import pytest
 
+from oracle import rrsvd as R
+from oracle.philox import gaussian_omega
 from paper_1504_00992_gb300 import inputs as I
 from tests.gpu_util import rrsvd_device, torch_cuda, truncated
 
 pytestmark = pytest.mark.gpu
 
 
-def _noalloc(B, theta, k, p, q, seed, chain0):
+def _noalloc(B, theta, k, p, q, seed, chain0, outputs=True):
     torch = torch_cuda()
     batch, m, n = theta.shape
     kk = min(k, m, n)
@@ -24,11 +33,17 @@ def _noalloc(B, theta, k, p, q, seed, chain0):
     w = torch.zeros(batch, dtype=torch.float64, device=dev)
     rk = torch.zeros(batch, dtype=torch.int32, device=dev)
     st = torch.cuda.current_stream().cuda_stream
-    B.rrsvd_execute_noalloc(m, n, k, p, q, batch, seed, chain0, th.data_ptr(), sg.data_ptr(), U.data_ptr(),
-                            Vh.data_ptr(), w.data_ptr(), rk.data_ptr(), st)
     torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    if outputs:
+        B.rrsvd_execute_noalloc(m, n, k, p, q, batch, seed, chain0, th.data_ptr(), sg.data_ptr(), U.data_ptr(),
+                                Vh.data_ptr(), w.data_ptr(), rk.data_ptr(), st)
+    else:   # sigma only: U and V^H stay in the static array, w and rank are not written
+        B.rrsvd_execute_noalloc(m, n, k, p, q, batch, seed, chain0, th.data_ptr(), sg.data_ptr(), 0, 0, 0, 0, st)
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
     return {"sigma": sg.cpu().numpy(), "U": U.cpu().numpy(), "Vh": Vh.cpu().numpy(), "w": w.cpu().numpy(),
-            "rank": rk.cpu().numpy()}
+            "rank": rk.cpu().numpy(), "free_delta": free0 - free1}
 
 
 def _reference(B, theta, k, p, q, seed, chain0):
@@ -50,18 +65,53 @@ def _same(a, b, theta):
         assert abs(a["w"][t] - b["w"][t]) <= 1e-12
 
 
-def test_noalloc_matches_workspace_entry_point_twice(lib):
+def _matches_oracle(a, theta, k, p, q, seed, chain0):
+    """Element-wise parity with the oracle on the same Omega: kept values to
+    1e-10 s_1, the truncated theta to 1e-10 in Frobenius norm, w to 1e-12."""
+    batch, m, n = theta.shape
+    kk, l = R.sketch_sizes(m, n, k, p)
+    for t in range(batch):
+        Uk, sk, Vhk, w = R.rrsvd_truncate(theta[t], gaussian_omega(n, l, seed, chain=chain0 + t), kk, q)
+        r = len(sk)
+        assert a["rank"][t] == r
+        assert np.abs(a["sigma"][t][:r] - sk).max() <= 1e-10 * sk[0]
+        assert np.all(a["sigma"][t][r:] == 0.0)
+        d = truncated(a["U"][t], a["sigma"][t], a["Vh"][t]) - (Uk * sk) @ Vhk
+        assert np.linalg.norm(d) <= 1e-10 * np.linalg.norm(theta[t])
+        assert abs(a["w"][t] - w) <= 1e-12
+
+
+def test_noalloc_matches_oracle_and_workspace_entry_point_twice(lib):
     from paper_1504_00992_gb300 import binding as B
-    # first call: two 96 x 80 instances
+    # a first call does the one-time set-up: the static array's module is
+    # loaded (on first use) and its address looked up; after it, calls move
+    # no device memory
+    sig0 = I.exp_spectrum(16, 4.0)
+    _noalloc(B, np.stack([I.synthetic_theta(16, 16, sig0, seed=1)]), 4, 2, 1, 0, 0)
+    # two 96 x 80 instances
     sig = I.exp_spectrum(80, 6.0)
     th1 = np.stack([I.synthetic_theta(96, 80, sig, seed=40 + t) for t in range(2)])
     a1 = _noalloc(B, th1, 20, 7, 2, 99, 3)
+    _matches_oracle(a1, th1, 20, 7, 2, 99, 3)
     _same(a1, _reference(B, th1, 20, 7, 2, 99, 3), th1)
     # second call right after, other sizes and chains, same static scratch
     sig2 = I.exp_spectrum(64, 5.0)
     th2 = np.stack([I.synthetic_theta(64, 64, sig2, seed=77)])
     a2 = _noalloc(B, th2, 32, 10, 2, 5, 11)
+    _matches_oracle(a2, th2, 32, 10, 2, 5, 11)
     _same(a2, _reference(B, th2, 32, 10, 2, 5, 11), th2)
+    # the device's free memory did not move across either call
+    assert a1["free_delta"] == 0 and a2["free_delta"] == 0
+
+
+def test_noalloc_without_optional_outputs(lib):
+    from paper_1504_00992_gb300 import binding as B
+    sig = I.exp_spectrum(100, 8.0)
+    th = np.stack([I.synthetic_theta(120, 100, sig, seed=90 + t) for t in range(3)])
+    full = _noalloc(B, th, 24, 8, 1, 7, 0)
+    bare = _noalloc(B, th, 24, 8, 1, 7, 0, outputs=False)
+    assert np.array_equal(bare["sigma"], full["sigma"])   # same kernels, same Omega: bit for bit
+    assert bare["free_delta"] == 0
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch(lib):
