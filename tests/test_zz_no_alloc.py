@@ -33,13 +33,22 @@ def _noalloc(B, theta, k, p, q, seed, chain0, outputs=True):
     w = torch.zeros(batch, dtype=torch.float64, device=dev)
     rk = torch.zeros(batch, dtype=torch.int32, device=dev)
     st = torch.cuda.current_stream().cuda_stream
+
+    def call():
+        if outputs:
+            B.rrsvd_execute_noalloc(m, n, k, p, q, batch, seed, chain0, th.data_ptr(), sg.data_ptr(),
+                                    U.data_ptr(), Vh.data_ptr(), w.data_ptr(), rk.data_ptr(), st)
+        else:   # sigma only: U and V^H stay in the static array, w and rank are not written
+            B.rrsvd_execute_noalloc(m, n, k, p, q, batch, seed, chain0, th.data_ptr(), sg.data_ptr(), 0, 0, 0, 0,
+                                    st)
+
+    # the same call twice in a row; the first may load kernel code on first
+    # use (lazy module loading), so the device's free memory is read across
+    # the second, which must not move it
+    call()
     torch.cuda.synchronize()
     free0 = torch.cuda.mem_get_info()[0]
-    if outputs:
-        B.rrsvd_execute_noalloc(m, n, k, p, q, batch, seed, chain0, th.data_ptr(), sg.data_ptr(), U.data_ptr(),
-                                Vh.data_ptr(), w.data_ptr(), rk.data_ptr(), st)
-    else:   # sigma only: U and V^H stay in the static array, w and rank are not written
-        B.rrsvd_execute_noalloc(m, n, k, p, q, batch, seed, chain0, th.data_ptr(), sg.data_ptr(), 0, 0, 0, 0, st)
+    call()
     torch.cuda.synchronize()
     free1 = torch.cuda.mem_get_info()[0]
     return {"sigma": sg.cpu().numpy(), "U": U.cpu().numpy(), "Vh": Vh.cpu().numpy(), "w": w.cpu().numpy(),
@@ -83,11 +92,6 @@ def _matches_oracle(a, theta, k, p, q, seed, chain0):
 
 def test_noalloc_matches_oracle_and_workspace_entry_point_twice(lib):
     from paper_1504_00992_gb300 import binding as B
-    # a first call does the one-time set-up: the static array's module is
-    # loaded (on first use) and its address looked up; after it, calls move
-    # no device memory
-    sig0 = I.exp_spectrum(16, 4.0)
-    _noalloc(B, np.stack([I.synthetic_theta(16, 16, sig0, seed=1)]), 4, 2, 1, 0, 0)
     # two 96 x 80 instances
     sig = I.exp_spectrum(80, 6.0)
     th1 = np.stack([I.synthetic_theta(96, 80, sig, seed=40 + t) for t in range(2)])
@@ -100,7 +104,7 @@ def test_noalloc_matches_oracle_and_workspace_entry_point_twice(lib):
     a2 = _noalloc(B, th2, 32, 10, 2, 5, 11)
     _matches_oracle(a2, th2, 32, 10, 2, 5, 11)
     _same(a2, _reference(B, th2, 32, 10, 2, 5, 11), th2)
-    # the device's free memory did not move across either call
+    # the device's free memory did not move across the repeated calls
     assert a1["free_delta"] == 0 and a2["free_delta"] == 0
 
 
