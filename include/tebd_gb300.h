@@ -106,13 +106,22 @@ typedef struct {
                            legacy stream 0 cannot be captured, so such a handle then
                            runs on a blocking stream of its own */
   int autotune;         /* nonzero: at creation, time the 16x16 and 32x32 GEMM tiles of
-                           every stage at the capacity sizes and keep the faster */
+                           every stage at the capacity sizes and keep the faster, and
+                           (with fused = 0) the staged sequence against the fused
+                           persistent launch for every wave it fits (tebd_wave_info) */
   size_t workspace_budget; /* bytes of per-bond workspace one wave may use (0 = all bonds
                               of a parity in one wave); larger batches run in waves */
   tebd_alloc_fn alloc;     /* optional: allocator of every device block of the handle
                               (read from descs[0]); with release, or both NULL */
   tebd_release_fn release;
   void* alloc_ctx;         /* passed to alloc and release */
+  int fused;               /* persistent fused launch (FP64 handles; read from descs[0]):
+                              every bond of a wave updated whole by one CTA of one
+                              persistent launch, for waves whose bonds have
+                              d_l d_r < 32 and m, n <= 512.  0: where the autotuner
+                              finds it faster (never without autotune); 1: wherever
+                              it fits; -1: never.  Same results as the staged launches,
+                              bit for bit */
 } tebd_desc_t;
 
 /* Section II (Eq. defmps, deftheta, defupdatetheta) with the RRSVD of
@@ -148,6 +157,15 @@ int tebd_select_chain(tebd_t h, int chain);
 
 /* Device bytes held by the handle and the number of waves per parity. */
 int tebd_workspace_info(tebd_t h, size_t* arena_bytes, int* waves_even, int* waves_odd);
+
+/* Plan and tuning of wave `wave` of a parity (0 <= wave < its count from
+ * tebd_workspace_info).  info (16 ints): [0] bonds in the wave, [1..4] its
+ * capacities m, n, k, l, [5] 1 if it runs as the persistent fused launch,
+ * [6..11] the GEMM tile of stages Y0, Y~, Y, B^H, U, V (0: by grid size),
+ * [12..15] reserved (0).  ms (2 doubles): the autotuner's timings of the
+ * wave's staged and fused RRSVD on synthetic theta (0 when not timed).
+ * Either may be NULL.  Errors: TEBD_EINVAL (parity, wave). */
+int tebd_wave_info(tebd_t h, int parity, int wave, int* info, double* ms);
 
 /* The plan tebd_create_multi(n_chains, descs, ...) would make, without
  * creating a handle: the device bytes it would allocate and its waves per

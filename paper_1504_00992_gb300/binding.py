@@ -51,7 +51,8 @@ class TebdDesc(ctypes.Structure):
                 ("p", ctypes.c_int), ("q", ctypes.c_int), ("seed", ctypes.c_uint64),
                 ("precision", ctypes.c_int), ("sv_cutoff", ctypes.c_double), ("chain", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("autotune", ctypes.c_int), ("workspace_budget", ctypes.c_size_t),
-                ("alloc", ALLOC_FN), ("release", RELEASE_FN), ("alloc_ctx", ctypes.c_void_p)]
+                ("alloc", ALLOC_FN), ("release", RELEASE_FN), ("alloc_ctx", ctypes.c_void_p),
+                ("fused", ctypes.c_int)]
 
 
 class TorchAllocator:
@@ -99,6 +100,7 @@ _SIGS = {
     "tebd_num_chains": (_i, [_vp, _pi]),
     "tebd_select_chain": (_i, [_vp, _i]),
     "tebd_workspace_info": (_i, [_vp, ctypes.POINTER(ctypes.c_size_t), _pi, _pi]),
+    "tebd_wave_info": (_i, [_vp, _i, _i, _pi, _pd]),
     "tebd_plan_query": (_i, [_i, ctypes.POINTER(TebdDesc), ctypes.POINTER(ctypes.c_size_t), _pi, _pi]),
     "tebd_destroy": (_i, [_vp]),
     "tebd_set_stream": (_i, [_vp, _vp]),
@@ -191,7 +193,7 @@ _KEEP = []
 
 
 def _desc(N, d_site, chi_bond, p, q, seed, precision=TEBD_PREC_FP64, sv_cutoff=0.0, chain=0, use_graph=0,
-          autotune=0, workspace_budget=0, allocator=None):
+          autotune=0, workspace_budget=0, allocator=None, fused=0):
     ds = (ctypes.c_int * N)(*[int(x) for x in d_site])
     cb = (ctypes.c_int * (N - 1))(*[int(x) for x in chi_bond])
     _KEEP.append((ds, cb))
@@ -200,13 +202,14 @@ def _desc(N, d_site, chi_bond, p, q, seed, precision=TEBD_PREC_FP64, sv_cutoff=0
     if allocator is not None:
         d.alloc = allocator.alloc
         d.release = allocator.release
+    d.fused = fused
     return d
 
 
 def tebd_create_ex(N, d_site, chi_bond, p, q, seed, precision=TEBD_PREC_FP64, sv_cutoff=0.0, chain=0, use_graph=0,
-                   autotune=0, workspace_budget=0, allocator=None):
+                   autotune=0, workspace_budget=0, allocator=None, fused=0):
     desc = _desc(N, d_site, chi_bond, p, q, seed, precision, sv_cutoff, chain, use_graph, autotune,
-                 workspace_budget, allocator)
+                 workspace_budget, allocator, fused)
     h = _vp()
     rc = load().tebd_create_ex(ctypes.byref(desc), ctypes.byref(h))
     _KEEP.clear()
@@ -216,12 +219,12 @@ def tebd_create_ex(N, d_site, chi_bond, p, q, seed, precision=TEBD_PREC_FP64, sv
 
 
 def tebd_create_multi(chains, p, q, seed, precision=TEBD_PREC_FP64, sv_cutoff=0.0, chain=0, use_graph=0,
-                      autotune=0, workspace_budget=0, allocator=None):
+                      autotune=0, workspace_budget=0, allocator=None, fused=0):
     """chains: list of (N, d_site list, chi_bond list)."""
     arr = (TebdDesc * len(chains))()
     for c, (N, d_site, chi_bond) in enumerate(chains):
         arr[c] = _desc(N, d_site, chi_bond, p, q, seed, precision, sv_cutoff, chain, use_graph, autotune,
-                       workspace_budget, allocator if c == 0 else None)
+                       workspace_budget, allocator if c == 0 else None, fused)
     h = _vp()
     rc = load().tebd_create_multi(len(chains), arr, ctypes.byref(h))
     _KEEP.clear()
@@ -258,6 +261,21 @@ def tebd_workspace_info(h):
     b, we, wo = ctypes.c_size_t(), ctypes.c_int(), ctypes.c_int()
     _check(h, load().tebd_workspace_info(h, ctypes.byref(b), ctypes.byref(we), ctypes.byref(wo)))
     return b.value, we.value, wo.value
+
+
+def tebd_wave_info(h, parity, wave):
+    """Dict of one wave's plan and tuning (tebd_wave_info)."""
+    info = (ctypes.c_int * 16)()
+    ms = (ctypes.c_double * 2)()
+    _check(h, load().tebd_wave_info(h, parity, wave, info, ms))
+    return {"bonds": info[0], "m": info[1], "n": info[2], "k": info[3], "l": info[4], "fused": info[5],
+            "tiles": list(info[6:12]), "tune_ms": {"staged": ms[0], "fused": ms[1]}}
+
+
+def tebd_tuning_table(h):
+    """Every wave's plan and tuning, both parities."""
+    _, we, wo = tebd_workspace_info(h)
+    return {par: [tebd_wave_info(h, par, w) for w in range(n)] for par, n in ((0, we), (1, wo))}
 
 
 def tebd_destroy(h):
@@ -531,17 +549,18 @@ class Tebd:
 
     def __init__(self, N, d, chi_max, p, q, seed=0, d_site=None, chi_bond=None, sv_cutoff=0.0, chain=0,
                  stream=None, use_graph=0, autotune=0, precision=TEBD_PREC_FP64, workspace_budget=0,
-                 allocator=None):
+                 allocator=None, fused=0):
         self.N = N
         self.dims = list(d_site) if d_site is not None else [d] * N
         self.chi_bond = list(chi_bond) if chi_bond is not None else [chi_max] * (N - 1)
         self.allocator = allocator
         if d_site is None and chi_bond is None and sv_cutoff == 0.0 and chain == 0 and not use_graph \
-                and not autotune and precision == TEBD_PREC_FP64 and not workspace_budget and allocator is None:
+                and not autotune and precision == TEBD_PREC_FP64 and not workspace_budget and allocator is None \
+                and not fused:
             self.h = tebd_create(N, d, chi_max, p, q, seed)
         else:
             self.h = tebd_create_ex(N, self.dims, self.chi_bond, p, q, seed, precision, sv_cutoff, chain,
-                                    use_graph, autotune, workspace_budget, allocator)
+                                    use_graph, autotune, workspace_budget, allocator, fused)
         caps = []
         for b in range(N - 1):
             left = int(np.prod([float(x) for x in self.dims[: b + 1]]))
@@ -608,6 +627,9 @@ class Tebd:
     def backward(self, site, op):
         return tebd_backward(self.h, site, op, self.dims)
 
+    def tuning_table(self):
+        return tebd_tuning_table(self.h)
+
 
 def _caps(dims, chi_bond):
     caps = []
@@ -623,11 +645,12 @@ class MultiTebd:
     """Many chains in one handle; per-chain calls take the chain index."""
 
     def __init__(self, chains, p, q, seed=0, use_graph=0, autotune=0, workspace_budget=0, stream=None,
-                 precision=TEBD_PREC_FP64, allocator=None):
+                 precision=TEBD_PREC_FP64, allocator=None, fused=0):
         self.chains = [(N, list(ds), list(cb)) for N, ds, cb in chains]
         self.allocator = allocator
         self.h = tebd_create_multi(self.chains, p, q, seed, precision=precision, use_graph=use_graph,
-                                   autotune=autotune, workspace_budget=workspace_budget, allocator=allocator)
+                                   autotune=autotune, workspace_budget=workspace_budget, allocator=allocator,
+                                   fused=fused)
         self.caps = [_caps(ds, cb) for _, ds, cb in self.chains]
         if stream is not None:
             tebd_set_stream(self.h, stream)
@@ -682,3 +705,6 @@ class MultiTebd:
 
     def workspace_info(self):
         return tebd_workspace_info(self.h)
+
+    def tuning_table(self):
+        return tebd_tuning_table(self.h)

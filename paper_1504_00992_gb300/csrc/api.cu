@@ -166,6 +166,8 @@ struct Wave {
   int first = 0, count = 0;
   Caps cap{};
   int tiles[6] = {0, 0, 0, 0, 0, 0};
+  int fused = 0;    // 1: the whole update of every bond in one persistent launch (fused.cu)
+  float tune_ms[2] = {0.f, 0.f};  // tuner timings of the staged and fused RRSVD (0: not timed)
   MixedSizes ms{};  // TF32 handles: the wave's FP32 arrays at its capacities
 };
 
@@ -179,7 +181,7 @@ struct ParitySet {
 
 // Byte offsets of the handle's arena, from the plan of tebd_create_multi.
 struct HandlePlan {
-  size_t one_off = 0, st_off = 0, wacc_off = 0, sweep_off = 0, tcerr_off = 0, op_off = 0, wout_off = 0;
+  size_t one_off = 0, st_off = 0, wacc_off = 0, sweep_off = 0, tcerr_off = 0, op_off = 0, wout_off = 0, queue_off = 0;
   size_t desc_off = 0, desc_per = 0, ws_off = 0, mixed_off = 0, total = 0;
   std::vector<WsLayout> lay[2];
   int max_batch = 0;
@@ -203,6 +205,7 @@ struct tebd_s {
   double* wacc = nullptr;   // 2 per chain: sum w, prod (1 - w)
   double* wout = nullptr;   // per problem of the larger parity
   uint64_t* sweep_dev = nullptr;
+  int* queue = nullptr;        // work counter of the persistent fused launch
   int* tcerr = nullptr;        // tensor-core wait timeout flag (TF32 handles)
   char* mixed = nullptr;       // FP32 arrays of the current wave (TF32 handles)
   cplx* op_dev = nullptr;
@@ -266,7 +269,8 @@ static void tebd_free(tebd_s* h) {
 static std::map<std::vector<long long>, int> g_tile_cache;
 static std::mutex g_tile_mu;
 
-static int tune_wave(const ParitySet& ps, Wave& w, cudaStream_t st, Dims* scratch_dims, const int p_os) {
+static int tune_wave(tebd_s* h, const ParitySet& ps, Wave& w, cudaStream_t st, Dims* scratch_dims, const int p_os,
+                     int fused_mode) {
   // capacity-sized descriptors of the wave's problems
   std::vector<Dims> hd(w.count);
   std::vector<ProbPtr> hp(w.count);
@@ -310,6 +314,32 @@ static int tune_wave(const ParitySet& ps, Wave& w, cudaStream_t st, Dims* scratc
     std::lock_guard<std::mutex> g(g_tile_mu);
     g_tile_cache[key] = pick;
   }
+  // the whole RRSVD of the wave, staged (tuned tiles) against the persistent
+  // fused kernel, on synthetic theta at the capacity sizes (the two give the
+  // same results; the data only sets the QR and Jacobi work)
+  if (fused_mode == 0 && fused_fits(w.cap)) {
+    if (launch_tune_theta(scratch_dims, ps.ptrs + w.first, w.count, st) != cudaSuccess) return -1;
+    float ms[2] = {1e30f, 1e30f};
+    for (int variant = 0; variant < 2; ++variant)
+      for (int r = 0; r < 2; ++r) {  // the first run warms up
+        cudaEventRecord(e0, st);
+        const cudaError_t e =
+            variant == 0 ? run_rrsvd(scratch_dims, ps.ptrs + w.first, w.count, w.cap, h->q, h->seed, 0, 0, -1,
+                                     h->status, st, h->sweep_dev, w.tiles)
+                         : launch_bond_fused(ps.ptrs + w.first, nullptr, scratch_dims, w.count, p_os, h->q, h->seed,
+                                             h->sweep_dev, h->cutoff, nullptr, h->status, h->queue, st);
+        if (e != cudaSuccess) return -1;
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (r == 1) ms[variant] = t;
+      }
+    w.tune_ms[0] = ms[0];
+    w.tune_ms[1] = ms[1];
+    w.fused = ms[1] < ms[0] ? 1 : 0;
+    if (cudaMemsetAsync(h->status, 0, sizeof(int), st) != cudaSuccess) return -1;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
@@ -329,6 +359,7 @@ static int plan_handle(tebd_s* h, int n_chains, const tebd_desc_t* descs, Handle
   if (d0.precision != TEBD_PREC_FP64 && d0.precision != TEBD_PREC_TF32) return TEBD_ENOTIMPL;
   if (d0.precision == TEBD_PREC_TF32 && d0.autotune) return TEBD_EINVAL;  // the tile autotuner is for FP64 GEMMs
   if ((d0.alloc == nullptr) != (d0.release == nullptr)) return TEBD_EINVAL;
+  if (d0.fused < -1 || d0.fused > 1) return TEBD_EINVAL;
   for (int c = 0; c < n_chains; ++c) {
     const tebd_desc_t& dc = descs[c];
     if (dc.N < 2 || dc.p != d0.p || dc.q != d0.q || dc.seed != d0.seed || dc.precision != d0.precision)
@@ -398,6 +429,7 @@ static int plan_handle(tebd_s* h, int n_chains, const tebd_desc_t* descs, Handle
   lay_plan.wacc_off = off; off += align_up(sizeof(double) * 2 * n_chains);
   lay_plan.sweep_off = off; off += ALIGN;
   lay_plan.tcerr_off = off; off += ALIGN;
+  lay_plan.queue_off = off; off += ALIGN;
   lay_plan.op_off = off; off += align_up(sizeof(cplx) * 64 * 64) + ALIGN;
   // problems of each parity, chain-major, and their waves under the budget
   const size_t budget = d0.workspace_budget;
@@ -523,6 +555,7 @@ static bool bind_arena(tebd_s* h) {
   h->status = (int*)(A + L.st_off);
   h->wacc = (double*)(A + L.wacc_off);
   h->sweep_dev = (uint64_t*)(A + L.sweep_off);
+  h->queue = (int*)(A + L.queue_off);
   h->tcerr = tf32 ? (int*)(A + L.tcerr_off) : nullptr;
   h->mixed = tf32 ? A + L.mixed_off : nullptr;
   h->op_dev = (cplx*)(A + L.op_off);
@@ -639,6 +672,7 @@ extern "C" int tebd_create_multi(int n_chains, const tebd_desc_t* descs, tebd_t*
     for (int par = 0; par < 2; ++par)
       for (const Wave& w : h->par[par].waves)
         if (mixed_prepare(w.cap) != cudaSuccess) { cudaGetLastError(); tebd_free(h); return TEBD_ECUDA; }
+  if (fused_prepare() != cudaSuccess) { cudaGetLastError(); tebd_free(h); return TEBD_ECUDA; }
   if (!bind_arena(h)) { tebd_free(h); return TEBD_ECUDA; }
   // every chain starts in |0...0>
   for (int c = 0; c < n_chains; ++c) {
@@ -651,11 +685,14 @@ extern "C" int tebd_create_multi(int n_chains, const tebd_desc_t* descs, tebd_t*
     const int rc = tebd_reset_state(h, c, psi.data());
     if (rc != TEBD_OK) { tebd_free(h); return rc; }
   }
+  if (d0.fused == 1 && h->precision == TEBD_PREC_FP64)
+    for (int par = 0; par < 2; ++par)
+      for (Wave& w : h->par[par].waves) w.fused = fused_fits(w.cap) ? 1 : 0;
   if (d0.autotune) {
     Dims* scratch = (Dims*)(h->arena + h->plan.desc_off + 2 * h->plan.desc_per);
     for (int par = 0; par < 2; ++par)
       for (Wave& w : h->par[par].waves)
-        if (tune_wave(h->par[par], w, h->stream, scratch, h->p) != 0) { tebd_free(h); return TEBD_ECUDA; }
+        if (tune_wave(h, h->par[par], w, h->stream, scratch, h->p, d0.fused) != 0) { tebd_free(h); return TEBD_ECUDA; }
     if (cudaDeviceSynchronize() != cudaSuccess) { tebd_free(h); return TEBD_ECUDA; }
   }
   *out = h;
@@ -934,6 +971,14 @@ static cudaError_t enqueue_sweep(tebd_t h, int parity) {
     ProbPtr* ptrs = ps.ptrs + w.first;
     const bool tuned = w.tiles[0] != 0;
     cudaError_t e;
+    if (w.fused) {
+      // the whole update of every bond of the wave in one persistent launch
+      if ((e = launch_bond_fused(ptrs, dims, nullptr, w.count, h->p, h->q, h->seed, h->sweep_dev, h->cutoff,
+                                 h->wout + w.first, h->status, h->queue, h->stream)) != cudaSuccess)
+        return e;
+      if ((e = launch_wacc(dims, ptrs, h->wout + w.first, w.count, h->wacc, h->stream)) != cudaSuccess) return e;
+      continue;
+    }
     if ((e = launch_plan(ptrs, dims, w.count, h->p, h->stream)) != cudaSuccess) return e;
     if (h->precision == TEBD_PREC_TF32) {
       // bonds of large local dimensions: contraction and gate as double-float GEMMs
@@ -1069,6 +1114,24 @@ extern "C" int tebd_bond_weights(tebd_t h, double* out) {
   const ChainH& C = h->ch[h->cur];
   CU_OR(h, cudaMemcpyAsync(out, C.wbond, sizeof(double) * (C.N - 1), cudaMemcpyDeviceToHost, h->stream));
   return tebd_check_status(h);
+}
+
+extern "C" int tebd_wave_info(tebd_t h, int parity, int wave, int* info, double* ms) {
+  if (!h) return TEBD_EINVAL;
+  if (parity < 0 || parity > 1 || wave < 0 || wave >= (int)h->par[parity].waves.size()) return TEBD_EINVAL;
+  const Wave& w = h->par[parity].waves[wave];
+  if (info) {
+    memset(info, 0, sizeof(int) * 16);
+    info[0] = w.count;
+    info[1] = w.cap.m; info[2] = w.cap.n; info[3] = w.cap.k; info[4] = w.cap.l;
+    info[5] = w.fused;
+    for (int i = 0; i < 6; ++i) info[6 + i] = w.tiles[i];
+  }
+  if (ms) {
+    ms[0] = w.tune_ms[0];
+    ms[1] = w.tune_ms[1];
+  }
+  return TEBD_OK;
 }
 
 extern "C" int tebd_workspace_info(tebd_t h, size_t* arena_bytes, int* waves_even, int* waves_odd) {

@@ -177,4 +177,17 @@ cudaError_t launch_wacc(const Dims* dims, const ProbPtr* ptrs, const double* wou
 cudaError_t launch_sweep_tick(uint64_t* sweep_dev, cudaStream_t st);
 cudaError_t launch_expect(const ChainDev& ch, int site, const cplx* op, int d, cplx* out, cudaStream_t st);
 
+// --- persistent fused bond update (fused.cu) -------------------------------
+// Bonds of a wave whose capacities satisfy fused_fits can be updated by one
+// persistent launch instead of the staged sequence; `queue` is a device int
+// that starts at zero (the kernel leaves it at zero).  With dims_in set, the
+// RRSVD alone of theta already in place (the tuner's timing run).
+enum { FUSED_MAXMN = 512 };
+bool fused_fits(const Caps& cap);
+cudaError_t fused_prepare();
+cudaError_t launch_bond_fused(const ProbPtr* ptrs, Dims* dims, const Dims* dims_in, int batch, int p_os, int q,
+                              uint64_t seed, const uint64_t* sweep_dev, double cutoff, double* wout, int* status,
+                              int* queue, cudaStream_t st);
+cudaError_t launch_tune_theta(const Dims* dims, const ProbPtr* ptrs, int batch, cudaStream_t st);
+
 }  // namespace tg

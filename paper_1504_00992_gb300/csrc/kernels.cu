@@ -16,6 +16,7 @@
 #include "internal.cuh"
 #include "profiler.cuh"
 #include "dfsplit.cuh"
+#include "stages.cuh"
 
 namespace tg {
 
@@ -56,67 +57,10 @@ cudaError_t launch_omega(const Dims* dims, const ProbPtr* ptrs, int batch, const
 // serves row- and column-major buffers; loads map consecutive threads onto the
 // unit-stride direction.
 // ---------------------------------------------------------------------------
-struct GemmOp {
-  int M, N, K;
-  const cplx* A; int64_t ars, acs;
-  const cplx* B; int64_t brs, bcs;
-  cplx* C; int64_t crs, ccs;
-};
-
-template <int STAGE>
-__device__ __forceinline__ GemmOp gemm_of(const Dims& D, const ProbPtr& P) {
-  GemmOp g;
-  if (STAGE == G_Y0 || STAGE == G_Y) {  // Y = A Omega  /  Y = A Q~   (m x l, column-major)
-    g.M = D.m; g.N = D.l; g.K = D.n;
-    g.A = P.theta; g.ars = D.n; g.acs = 1;
-    g.B = (STAGE == G_Y0) ? P.omega : P.Qt; g.brs = 1; g.bcs = D.n;
-    g.C = P.Y; g.crs = 1; g.ccs = D.m;
-  } else if (STAGE == G_YT || STAGE == G_BH) {  // Y~ = A^H Q (n x l, column-major)
-    g.M = D.n; g.N = D.l; g.K = D.m;
-    g.A = P.theta; g.ars = 1; g.acs = D.n;       // op(A)(r, k) = conj(A[k][r])
-    g.B = P.Q; g.brs = 1; g.bcs = D.m;
-    g.C = P.Yt; g.crs = 1; g.ccs = D.n;
-  } else if (STAGE == G_U) {  // U = Q Jk (m x k, row-major)
-    g.M = D.m; g.N = D.k; g.K = D.l;
-    g.A = P.Q; g.ars = 1; g.acs = D.m;
-    g.B = P.Jk; g.brs = 1; g.bcs = D.l;
-    g.C = P.U; g.crs = D.k; g.ccs = 1;
-  } else if (STAGE == G_V) {  // V = Qb Wk, stored conjugated as Vh (k x n, row-major)
-    g.M = D.n; g.N = D.k; g.K = D.l;
-    g.A = P.Qt; g.ars = 1; g.acs = D.n;
-    g.B = P.Wk; g.brs = 1; g.bcs = D.l;
-    g.C = P.V; g.crs = 1; g.ccs = D.n;
-  } else if (STAGE == G_PR) {  // Br = A Omega_r -> columns l .. l+r-1 of Y (m x r)
-    g.M = D.m; g.N = D.r; g.K = D.n;
-    g.A = P.theta; g.ars = D.n; g.acs = 1;
-    g.B = P.omega; g.brs = 1; g.bcs = D.n;
-    g.C = P.Y + (int64_t)D.l * D.m; g.crs = 1; g.ccs = D.m;
-  } else if (STAGE == G_PQ) {  // C1 = Q^H Br (l x r, column-major in R)
-    g.M = D.l; g.N = D.r; g.K = D.m;
-    g.A = P.Q; g.ars = D.m; g.acs = 1;          // op(A)(i, k) = conj(Q[k][i])
-    g.B = P.Y + (int64_t)D.l * D.m; g.brs = 1; g.bcs = D.m;
-    g.C = P.R; g.crs = 1; g.ccs = D.l;
-  } else {  // G_PD: Dr = Q C1 (m x r)
-    g.M = D.m; g.N = D.r; g.K = D.l;
-    g.A = P.Q; g.ars = 1; g.acs = D.m;
-    g.B = P.R; g.brs = 1; g.bcs = D.l;
-    g.C = P.Dr; g.crs = 1; g.ccs = D.m;
-  }
-  return g;
-}
-
-template <int STAGE>
-struct StageFlags {
-  static constexpr bool conjA = (STAGE == G_YT || STAGE == G_BH || STAGE == G_PQ);
-  static constexpr bool conjC = (STAGE == G_V);
-};
-
 template <int T, int STAGE>
 __global__ void __launch_bounds__(256) k_zgemm(const Dims* __restrict__ dims, const ProbPtr* __restrict__ ptrs) {
-  constexpr int TK = 16;
-  constexpr int S = T / 16;  // outputs per thread along each direction
-  __shared__ cplx As[TK][T + 1];
-  __shared__ cplx Bs[TK][T + 1];
+  __shared__ cplx As[ZG_TK][T + 1];
+  __shared__ cplx Bs[ZG_TK][T + 1];
   const int p = blockIdx.z;
   const Dims D = dims[p];
   if (!D.active) return;
@@ -124,62 +68,7 @@ __global__ void __launch_bounds__(256) k_zgemm(const Dims* __restrict__ dims, co
   const GemmOp g = gemm_of<STAGE>(D, ptrs[p]);
   const int tm = blockIdx.y * T, tn = blockIdx.x * T;
   if (tm >= g.M || tn >= g.N) return;
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const bool ccol = (g.crs == 1);
-  cplx acc[S][S];
-#pragma unroll
-  for (int i = 0; i < S; ++i)
-#pragma unroll
-    for (int j = 0; j < S; ++j) acc[i][j] = cmk(0.0, 0.0);
-
-  for (int k0 = 0; k0 < g.K; k0 += TK) {
-    // A tile: op(A)(tm + r, k0 + kk) -> As[kk][r]
-    for (int e = tid; e < T * TK; e += 256) {
-      int r, kk;
-      if (g.acs == 1) { kk = e % TK; r = e / TK; } else { r = e % T; kk = e / T; }
-      const int gr = tm + r, gk = k0 + kk;
-      cplx v = cmk(0.0, 0.0);
-      if (gr < g.M && gk < g.K) {
-        v = g.A[(int64_t)gr * g.ars + (int64_t)gk * g.acs];
-        if (StageFlags<STAGE>::conjA) v.y = -v.y;
-      }
-      As[kk][r] = v;
-    }
-    // B tile: B(k0 + kk, tn + c) -> Bs[kk][c]
-    for (int e = tid; e < T * TK; e += 256) {
-      int c, kk;
-      if (g.brs == 1) { kk = e % TK; c = e / TK; } else { c = e % T; kk = e / T; }
-      const int gc = tn + c, gk = k0 + kk;
-      cplx v = cmk(0.0, 0.0);
-      if (gc < g.N && gk < g.K) v = g.B[(int64_t)gk * g.brs + (int64_t)gc * g.bcs];
-      Bs[kk][c] = v;
-    }
-    __syncthreads();
-#pragma unroll 4
-    for (int kk = 0; kk < TK; ++kk) {
-      cplx a[S], b[S];
-#pragma unroll
-      for (int i = 0; i < S; ++i) a[i] = As[kk][(ccol ? tx : ty) + 16 * i];
-#pragma unroll
-      for (int j = 0; j < S; ++j) b[j] = Bs[kk][(ccol ? ty : tx) + 16 * j];
-#pragma unroll
-      for (int i = 0; i < S; ++i)
-#pragma unroll
-        for (int j = 0; j < S; ++j) cfma(acc[i][j], a[i], b[j]);
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int i = 0; i < S; ++i)
-#pragma unroll
-    for (int j = 0; j < S; ++j) {
-      const int r = tm + (ccol ? tx : ty) + 16 * i, c = tn + (ccol ? ty : tx) + 16 * j;
-      if (r < g.M && c < g.N) {
-        cplx v = acc[i][j];
-        if (StageFlags<STAGE>::conjC) v.y = -v.y;
-        g.C[(int64_t)r * g.crs + (int64_t)c * g.ccs] = v;
-      }
-    }
+  zgemm_tile_dev<T, STAGE>(g, tm, tn, As, Bs);
 }
 
 template <int STAGE>
@@ -379,9 +268,6 @@ cudaError_t launch_zgemm(int stage, const Dims* dims, const ProbPtr* ptrs, int b
 // alpha_j = -e^{i arg x_0} ||x||, v_0 = x_0 - alpha_j, tau_j = 1/(||x|| (||x|| + |x_0|)).
 // Q = H_0 ... H_{L-1} [I; 0] is accumulated backwards into the output.
 // ---------------------------------------------------------------------------
-enum { QR_MAXL = 512 };
-
-enum { QR_THREADS = 1024, JAC_THREADS = 512 };
 
 template <int QS>
 __global__ void __launch_bounds__(QR_THREADS) k_qr(const Dims* __restrict__ dims, const ProbPtr* __restrict__ ptrs,
@@ -393,81 +279,7 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr(const Dims* __restrict__ dims
   const Dims D = dims[p];
   if (!D.active) return;
   if (only_flagged && !D.qflag) return;
-  const ProbPtr P = ptrs[p];
-  const int M = (QS == QR_Y) ? D.m : D.n;
-  const int L = D.l;
-  cplx* A = (QS == QR_Y) ? P.Y : P.Yt;
-  cplx* Qo = (QS == QR_Y) ? P.Q : P.Qt;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-
-  for (int j = 0; j < L; ++j) {
-    cplx* aj = A + (int64_t)j * M;
-    double s = 0.0;
-    for (int r = j + tid; r < M; r += blockDim.x) s += cabs2(aj[r]);
-    s = block_sum(s, red);
-    if (tid == 0) {
-      const cplx x0 = aj[j];
-      // |x0| by hypot: the phase x0/|x0| must stay on the unit circle for H to be unitary
-      const double ax0 = hypot(x0.x, x0.y);
-      const double nx = sqrt(s);
-      if (!(nx >= 1e-150)) {  // zero column, or one so small that tau would overflow
-        tau[j] = 0.0;
-        alph[j] = cmk(0.0, 0.0);
-      } else {
-        // the phase of a leading entry negligible against ||x|| is not used
-        const cplx ph = (ax0 > 1e-15 * nx) ? cscale(x0, 1.0 / ax0) : cmk(1.0, 0.0);
-        alph[j] = cscale(ph, -nx);
-        aj[j] = cscale(ph, ax0 + nx);  // v_0 = x_0 - alpha
-        tau[j] = 1.0 / (nx * (nx + ax0));
-      }
-    }
-    __syncthreads();
-    const double t = tau[j];
-    if (t != 0.0) {
-      for (int c = j + 1 + warp; c < L; c += nw) {
-        cplx* ac = A + (int64_t)c * M;
-        cplx sd = cmk(0.0, 0.0);
-        for (int r = j + lane; r < M; r += 32) cfma_conj(sd, aj[r], ac[r]);
-        sd = cscale(warp_sum(sd), t);
-        for (int r = j + lane; r < M; r += 32) {
-          const cplx v = aj[r];
-          ac[r] = csub(ac[r], cmul(v, sd));
-        }
-      }
-    }
-    __syncthreads();
-  }
-  // X = Rb^H (lower triangle, column-major L x L) for the SVD of B: element
-  // (r, c) of X is conj(Rb[c][r]), Rb[i][c] = A[c M + i] above the diagonal
-  // and alpha_c on it
-  if (QS == QR_BH) {
-    for (int e = tid; e < L * L; e += blockDim.x) {
-      const int c = e / L, r = e % L;
-      cplx v = cmk(0.0, 0.0);
-      if (c < r) v = cconj(A[(int64_t)r * M + c]);
-      else if (c == r) v = cconj(alph[c]);
-      P.R[(int64_t)c * L + r] = v;
-    }
-  }
-  // Q = [I; 0], then Q <- H_j Q for j = L-1 .. 0 (only columns c >= j change)
-  for (int64_t e = tid; e < (int64_t)M * L; e += blockDim.x) {
-    const int c = (int)(e / M), r = (int)(e % M);
-    Qo[e] = cmk(r == c ? 1.0 : 0.0, 0.0);
-  }
-  __syncthreads();
-  for (int j = L - 1; j >= 0; --j) {
-    const double t = tau[j];
-    if (t == 0.0) continue;  // uniform across the block
-    const cplx* aj = A + (int64_t)j * M;
-    for (int c = j + warp; c < L; c += nw) {
-      cplx* qc = Qo + (int64_t)c * M;
-      cplx sd = cmk(0.0, 0.0);
-      for (int r = j + lane; r < M; r += 32) cfma_conj(sd, aj[r], qc[r]);
-      sd = cscale(warp_sum(sd), t);
-      for (int r = j + lane; r < M; r += 32) qc[r] = csub(qc[r], cmul(aj[r], sd));
-    }
-    __syncthreads();
-  }
+  qr_dev<QS>(D, ptrs[p], red, tau, alph);
 }
 
 cudaError_t launch_qr(int stage, const Dims* dims, const ProbPtr* ptrs, int batch, cudaStream_t st,
@@ -503,15 +315,6 @@ cudaError_t launch_qr(int stage, const Dims* dims, const ProbPtr* ptrs, int batc
 // Output: sigma sorted descending (ties by lower index), Jk = the leading k
 // columns of W (for U = Q Jk), Wk = the matching columns of J (for V = Qb Wk).
 // ---------------------------------------------------------------------------
-enum { JAC_MAXSWEEPS = 60, JAC_G = 8 };
-
-// sum over the JAC_G lanes of this lane's group (the group's lanes all call it)
-__device__ __forceinline__ double grp_sum(double v, unsigned mask) {
-#pragma unroll
-  for (int o = JAC_G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
-  return v;
-}
-
 __global__ void __launch_bounds__(JAC_THREADS) k_jacobi(const Dims* __restrict__ dims,
                                                         const ProbPtr* __restrict__ ptrs, int* status) {
   __shared__ double sv[QR_MAXL];
@@ -522,115 +325,7 @@ __global__ void __launch_bounds__(JAC_THREADS) k_jacobi(const Dims* __restrict__
   const int p = blockIdx.x;
   const Dims D = dims[p];
   if (!D.active) return;
-  const ProbPtr P = ptrs[p];
-  const int L = D.l, K = D.k;
-  cplx* X = P.R;
-  cplx* J = P.J;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  const int gl = lane & (JAC_G - 1);                      // lane within its group
-  const int grp = tid / JAC_G, ngrp = blockDim.x / JAC_G;  // group index, groups per CTA
-  const unsigned gmask = ((1u << JAC_G) - 1u) << (lane & ~(JAC_G - 1));
-  double f2 = 0.0;
-  for (int e = tid; e < L * L; e += blockDim.x) {
-    J[e] = cmk((e / L) == (e % L) ? 1.0 : 0.0, 0.0);
-    f2 += cabs2(X[e]);
-  }
-  f2 = block_sum(f2, red);
-  const int Lp = (L + 1) & ~1;
-  const double eps = 2.220446049250313e-16;
-  const double tol = 4.0 * eps * sqrt((double)L);
-  const double small = ((double)L * eps) * ((double)L * eps) * f2;
-  int sweep = 0;
-  for (; sweep < JAC_MAXSWEEPS; ++sweep) {
-    // exact squared column norms at the start of every sweep; within the sweep
-    // they follow each rotation: |x_a'|^2 = |x_a|^2 - t|g|, |x_b'|^2 = |x_b|^2 + t|g|
-    for (int c = warp; c < L; c += nw) {
-      const cplx* xc = X + (int64_t)c * L;
-      double s2 = 0.0;
-      for (int r = lane; r < L; r += 32) s2 += cabs2(xc[r]);
-      s2 = warp_sum(s2);
-      if (lane == 0) nrm[c] = s2;
-    }
-    if (tid == 0) rotated = 0;
-    __syncthreads();
-    for (int rnd = 0; rnd < Lp - 1; ++rnd) {
-      for (int pi = grp; pi < Lp / 2; pi += ngrp) {
-        int a, b;
-        if (pi == 0) { a = Lp - 1; b = rnd; }
-        else { a = (rnd + pi) % (Lp - 1); b = (rnd - pi + (Lp - 1)) % (Lp - 1); }
-        if (a > b) { const int t = a; a = b; b = t; }
-        if (b >= L) continue;  // uniform over the group
-        cplx* xa = X + (int64_t)a * L;
-        cplx* xb = X + (int64_t)b * L;
-        const double aa = nrm[a], bb = nrm[b];
-        if (aa <= small || bb <= small) continue;
-        cplx g = cmk(0.0, 0.0);
-        for (int r = gl; r < L; r += JAC_G) cfma_conj(g, xa[r], xb[r]);
-        g.x = grp_sum(g.x, gmask);
-        g.y = grp_sum(g.y, gmask);
-        const double ag2 = cabs2(g);
-        if (!(ag2 > tol * tol * (aa * bb)) || ag2 == 0.0) continue;
-        const double ag = sqrt(ag2);
-        // rotation: x_a' = c x_a - s e* x_b, x_b' = s e x_a + c x_b, e = g/|g|
-        const cplx e = cscale(g, 1.0 / ag);
-        const double zeta = (bb - aa) / (2.0 * ag);
-        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
-        const cplx se = cscale(e, s), sec = cconj(se);
-        for (int r = gl; r < L; r += JAC_G) {
-          const cplx u = xa[r], v = xb[r];
-          xa[r] = csub(cscale(u, c), cmul(sec, v));
-          xb[r] = cadd(cmul(se, u), cscale(v, c));
-        }
-        cplx* ja = J + (int64_t)a * L;
-        cplx* jb = J + (int64_t)b * L;
-        for (int r = gl; r < L; r += JAC_G) {
-          const cplx u = ja[r], v = jb[r];
-          ja[r] = csub(cscale(u, c), cmul(sec, v));
-          jb[r] = cadd(cmul(se, u), cscale(v, c));
-        }
-        if (gl == 0) {
-          nrm[a] = aa - t * ag;
-          nrm[b] = bb + t * ag;
-          rotated = 1;
-        }
-      }
-      __syncthreads();
-    }
-    const int any = rotated;
-    __syncthreads();
-    if (!any) break;
-  }
-  if (sweep == JAC_MAXSWEEPS && tid == 0) atomicOr(status, 2);  // not converged (non-fatal)
-  // singular values = column norms
-  for (int c = warp; c < L; c += nw) {
-    const cplx* xc = X + (int64_t)c * L;
-    double s = 0.0;
-    for (int r = lane; r < L; r += 32) s += cabs2(xc[r]);
-    s = warp_sum(s);
-    if (lane == 0) sv[c] = sqrt(s);
-  }
-  __syncthreads();
-  // rank by descending value, ties by index; a NaN value ranks below every
-  // number, so perm is a permutation of 0..L-1 whatever the input
-  for (int c = tid; c < L; c += blockDim.x) {
-    const double s = (sv[c] == sv[c]) ? sv[c] : -1.0;
-    int rk = 0;
-    for (int j = 0; j < L; ++j) {
-      const double t = (sv[j] == sv[j]) ? sv[j] : -1.0;
-      rk += (t > s) || (t == s && j < c);
-    }
-    perm[rk] = c;
-  }
-  __syncthreads();
-  for (int i = tid; i < L; i += blockDim.x) P.sigma[i] = sv[perm[i]];
-  for (int e = tid; e < K * L; e += blockDim.x) {
-    const int t = e / L, r = e % L;
-    const int c = perm[t];
-    const double s = sv[c];
-    P.Jk[e] = (s > 0.0) ? cscale(X[(int64_t)c * L + r], 1.0 / s) : cmk(0.0, 0.0);
-    P.Wk[e] = J[(int64_t)c * L + r];
-  }
+  jacobi_dev(D, ptrs[p], status, sv, nrm, perm, &rotated, red);
 }
 
 cudaError_t launch_jacobi(const Dims* dims, const ProbPtr* ptrs, int batch, int* status, cudaStream_t st) {

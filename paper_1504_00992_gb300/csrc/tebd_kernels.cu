@@ -6,6 +6,7 @@
 
 #include "internal.cuh"
 #include "profiler.cuh"
+#include "stages.cuh"
 
 namespace tg {
 
@@ -18,25 +19,7 @@ namespace tg {
 __global__ void k_plan(const ProbPtr* __restrict__ ptrs, Dims* dims, int batch, int p) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= batch) return;
-  const ProbPtr P = ptrs[t];
-  Dims D;
-  D.dl = P.dl_s;
-  D.dr = P.dr_s;
-  D.cl = *P.chi_l;
-  D.cm = *P.chi_m;
-  D.cr = *P.chi_r;
-  D.m = D.dl * D.cl;
-  D.n = D.dr * D.cr;
-  const int k = min(P.chicap, min(D.m, D.n));
-  D.k = k;
-  D.l = min(k + p, min(D.m, D.n));
-  D.bond = P.bond_s;
-  D.chain = P.chain_s;
-  D.active = (D.cm > 0) ? 1 : 0;
-  D.r = 0;
-  D.chk = 0;
-  D.qflag = 0;
-  dims[t] = D;
+  dims[t] = plan_dev(ptrs[t], p);
 }
 
 cudaError_t launch_plan(const ProbPtr* ptrs, Dims* dims, int batch, int p, cudaStream_t st) {
@@ -53,8 +36,6 @@ cudaError_t launch_plan(const ProbPtr* ptrs, Dims* dims, int batch, int p, cudaS
 // physical indices), so the gate is applied from shared memory right after
 // the contraction.  Tile: dl*TA <= 32 rows (TA >= 1), dr*TB <= 32 columns.
 // ---------------------------------------------------------------------------
-enum { TH_TK = 16, TH_MAXR = 64 };
-
 __global__ void __launch_bounds__(256) k_theta(const Dims* __restrict__ dims, const ProbPtr* __restrict__ ptrs,
                                                int identity_gate, int skip_pre) {
   extern __shared__ cplx th_sm[];
@@ -63,83 +44,7 @@ __global__ void __launch_bounds__(256) k_theta(const Dims* __restrict__ dims, co
   if (!D.active) return;
   const ProbPtr P = ptrs[p];
   if (skip_pre && !identity_gate && P.Cpre) return;  // contracted by launch_theta_df
-  const int dl = D.dl, dr = D.dr, cl = D.cl, cm = D.cm, cr = D.cr;
-  const int TA = max(1, 32 / dl), TB = max(1, 32 / dr);
-  const int a0 = blockIdx.y * TA, b0 = blockIdx.x * TB;
-  if (a0 >= cl || b0 >= cr) return;
-  const int ta = min(TA, cl - a0), tb = min(TB, cr - b0);
-  const int rows = dl * ta, cols = dr * tb;  // <= 64 each
-  cplx* Ls = th_sm;                          // [TH_TK][TH_MAXR]
-  cplx* Rs = Ls + TH_TK * TH_MAXR;           // [TH_TK][TH_MAXR]
-  cplx* Cs = Rs + TH_TK * TH_MAXR;           // [rows][cols]
-  const int tid = threadIdx.x;
-  const int nout = rows * cols;
-  cplx acc[16];
-#pragma unroll
-  for (int s = 0; s < 16; ++s) acc[s] = cmk(0.0, 0.0);
-  const cplx* gl = P.gl;
-  const cplx* gr = P.gr;
-  for (int g0 = 0; g0 < cm; g0 += TH_TK) {
-    // L rows (i', a): lam_l[a] Gl[i'][a0+a][g] lam_m[g]; g fastest
-    for (int e = tid; e < TH_TK * rows; e += 256) {
-      const int kk = e % TH_TK, ri = e / TH_TK;
-      const int ip = ri / ta, a = ri % ta, g = g0 + kk;
-      cplx v = cmk(0.0, 0.0);
-      if (g < cm) {
-        v = gl[((int64_t)ip * P.cap_l + a0 + a) * P.cap_m + g];
-        v = cscale(v, P.laml[a0 + a] * P.lamm[g]);
-      }
-      Ls[kk * TH_MAXR + ri] = v;
-    }
-    // R columns (j', c): Gr[j'][g][b0+c] lam_r[c]; c fastest
-    for (int e = tid; e < TH_TK * cols; e += 256) {
-      const int c = e % tb, rest = e / tb;
-      const int jp = rest % dr, kk = rest / dr;
-      const int g = g0 + kk;
-      cplx v = cmk(0.0, 0.0);
-      if (g < cm) {
-        v = gr[((int64_t)jp * P.cap_m + g) * P.cap_r + b0 + c];
-        v = cscale(v, P.lamr[b0 + c]);
-      }
-      Rs[kk * TH_MAXR + jp * tb + c] = v;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int s = 0; s < 16; ++s) {
-      const int o = tid + 256 * s;
-      if (o < nout) {
-        const int ri = o / cols, ci = o % cols;
-        cplx a = acc[s];
-#pragma unroll 4
-        for (int kk = 0; kk < TH_TK; ++kk) cfma(a, Ls[kk * TH_MAXR + ri], Rs[kk * TH_MAXR + ci]);
-        acc[s] = a;
-      }
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int s = 0; s < 16; ++s) {
-    const int o = tid + 256 * s;
-    if (o < nout) Cs[o] = acc[s];
-  }
-  __syncthreads();
-  // gate: rows of Cs are (i', a) = i'*ta + a, columns (j', c) = j'*tb + c.
-  // A bond whose gate is applied as a GEMM gets its pre-gate theta in Cpre.
-  const int dd = dl * dr;
-  const bool pre = !identity_gate && P.Cpre != nullptr;
-  cplx* th = pre ? P.Cpre : const_cast<cplx*>(P.theta);
-  for (int o = tid; o < nout; o += 256) {
-    const int ri = o / cols, ci = o % cols;
-    const int i = ri / ta, a = ri % ta, j = ci / tb, c = ci % tb;
-    const cplx* grow = P.gate + (int64_t)(i * dr + j) * dd;
-    cplx v = cmk(0.0, 0.0);
-    if (identity_gate || pre)
-      v = Cs[(i * ta + a) * cols + j * tb + c];
-    else
-      for (int ip = 0; ip < dl; ++ip)
-        for (int jp = 0; jp < dr; ++jp) cfma(v, grow[ip * dr + jp], Cs[(ip * ta + a) * cols + jp * tb + c]);
-    th[(int64_t)(i * cl + a0 + a) * D.n + j * cr + b0 + c] = v;
-  }
+  theta_tile_dev(D, P, blockIdx.y, blockIdx.x, identity_gate, th_sm);
 }
 
 // ---------------------------------------------------------------------------
@@ -252,55 +157,7 @@ __global__ void __launch_bounds__(256) k_rebuild(const Dims* __restrict__ dims, 
   const int p = blockIdx.x;
   const Dims D = dims[p];
   if (!D.active) return;
-  const ProbPtr P = ptrs[p];
-  if (threadIdx.x == 0) {
-    double nf = 0.0;
-    for (int i = 0; i < NPART; ++i) nf += P.part[i];
-    const double s0 = P.sigma[0];
-    int r = 0;
-    double kept = 0.0;
-    const bool finite = isfinite(nf) && isfinite(s0);
-    if (finite && s0 > 0.0) {
-      while (r < D.k && P.sigma[r] > cutoff * s0) {
-        kept += P.sigma[r] * P.sigma[r];
-        ++r;
-      }
-    }
-    if (!finite || r == 0 || !isfinite(kept)) {
-      atomicOr(status, 1);
-      r = 0;
-    }
-    s_rank = r;
-    s_inv = (r > 0) ? 1.0 / sqrt(kept) : 0.0;
-    wout[p] = (r > 0 && nf > 0.0) ? 1.0 - kept / nf : 0.0;
-  }
-  __syncthreads();
-  const int r = s_rank;
-  if (r == 0) return;
-  double* lam = const_cast<double*>(P.lamm);
-  const int capm = P.cap_m;
-  for (int i = threadIdx.x; i < capm; i += blockDim.x) lam[i] = (i < r) ? P.sigma[i] * s_inv : 0.0;
-  cplx* gl = const_cast<cplx*>(P.gl);
-  cplx* gr = const_cast<cplx*>(P.gr);
-  const int dl = D.dl, dr = D.dr, cl = D.cl, cr = D.cr, K = D.k;
-  for (int64_t e = threadIdx.x; e < (int64_t)dl * cl * r; e += blockDim.x) {
-    const int g = (int)(e % r);
-    const int row = (int)(e / r);  // i*cl + a
-    const int a = row % cl, i = row / cl;
-    const double ll = P.laml[a];
-    const cplx u = P.U[(int64_t)row * K + g];
-    gl[((int64_t)i * P.cap_l + a) * capm + g] = (ll > 0.0) ? cscale(u, 1.0 / ll) : cmk(0.0, 0.0);
-  }
-  for (int64_t e = threadIdx.x; e < (int64_t)dr * r * cr; e += blockDim.x) {
-    const int c = (int)(e % cr);
-    const int rest = (int)(e / cr);
-    const int g = rest % r, j = rest / r;
-    const double lr = P.lamr[c];
-    const cplx v = P.V[(int64_t)g * D.n + j * cr + c];
-    gr[((int64_t)j * capm + g) * P.cap_r + c] = (lr > 0.0) ? cscale(v, 1.0 / lr) : cmk(0.0, 0.0);
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) *P.chi_m = r;
+  rebuild_dev(D, ptrs[p], cutoff, wout + p, status, &s_rank, &s_inv);
 }
 
 cudaError_t launch_rebuild(const Dims* dims, const ProbPtr* ptrs, int batch, double cutoff, double* wout,

@@ -164,25 +164,28 @@ def test_spin_boson_full_size_gapped(lib, spin_boson_gapped, prec, tol_lam, tol_
         sim.close()
 
 
-@pytest.mark.parametrize("prec,tol_spin", [(0, 1e-8), (2, 2e-7)])
+@pytest.mark.parametrize("prec,tol_spin", [(0, 1e-10), (2, 2e-7)])
 def test_spin_boson_full_size_gapless(lib, spin_boson_gapless, prec, tol_spin):
     from paper_1504_00992_gb300 import binding as B
     dims, caps, g0, lam0, gates, sample, ref, spread = spin_boson_gapless
-    # two correct FP64 codes on this input disagree by `spread` on the
-    # smallest kept values: they are not determined more finely than that
-    assert 1e-9 < spread < 1e-4, spread
-    tol = max(4.0 * spread, 1e-8)
+    # two correct FP64 codes on this input (LAPACK's QR and a hand-written
+    # Householder QR in the oracle) disagree by `spread` on the largest bond:
+    # the GPU's FP64 form is held to a few times that, and never looser than
+    # the FP64 bar; the mixed form to its stated tolerance
+    tol = max(4.0 * spread, 1e-10) if prec == 0 else tol_spin
     sim = _run_even_sweep(B, dims, caps, g0, lam0, gates, prec)
     try:
+        dev = {}
         for b in sample:
             lam_o, n_o = ref[b]["lam"], ref[b]["n"]
             lg = sim.get_lambda(b)
-            assert len(lg) == len(lam_o), b
-            assert np.abs(lg - lam_o).max() <= (tol_spin if b == 0 else tol), (b, spread)
             # the rebuilt Gamma of site b+1 (V^H / lambda_r): its boson number,
             # a gauge-invariant function of the new tensors
             n_g = sim.expect(b + 1, I.boson_ops(dims[b + 1])[2]).real
-            assert abs(n_g - n_o) <= (tol_spin if b == 0 else tol) * (dims[b + 1] - 1), b
+            dev[b] = (len(lg), len(lam_o), _padded_diff(lg, lam_o), abs(n_g - n_o) / (dims[b + 1] - 1))
+        for b in sample:
+            t = tol_spin if b == 0 else tol
+            assert dev[b][0] == dev[b][1] and dev[b][2] <= t and dev[b][3] <= t, (b, spread, dev)
     finally:
         sim.close()
 
