@@ -404,7 +404,13 @@ MixedSizes mixed_sizes(int m, int n, int k, int l) {
   s.yf = (size_t)m * l * sizeof(float2);
   s.ytf = (size_t)n * l * sizeof(float2);
   s.df = (size_t)l * l * sizeof(float2);
-  s.thd = reorth_fits(m, l) ? (size_t)m * n * sizeof(float4) : 0;
+  // the projection runs on the tensor cores from BF16 digits (oz_proj.cu)
+  // rather than from a double-float copy of theta
+  s.thd = 0;
+  s.bd = oz_digits_bytes(n, m);
+  s.bsc = oz_scales_bytes(n, m);
+  s.ad = oz_digits_bytes(l, m);
+  s.asc = oz_scales_bytes(l, m);
   const int mx = m > n ? m : n;
   s.qs = ((!qr_blk_f32_fits(m, l) && qr_multi_f32_fits(m, l)) || (!qr_blk_f32_fits(n, l) && qr_multi_f32_fits(n, l)))
              ? qr_multi_f32_scratch(mx, l) * sizeof(float2)
@@ -419,7 +425,8 @@ static size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 size_t mixed_bytes(const MixedSizes& s, int batch) {
   return 2 * up256(s.thf * batch) + 2 * up256(s.tha * batch) + 2 * up256(s.bt * batch) + 2 * up256(s.yf * batch) +
          2 * up256(s.ytf * batch) + up256(s.df * batch) + up256(s.thd * batch) +
-         up256((size_t)s.ntile * sizeof(double) * batch) + up256(s.qs * batch);
+         up256((size_t)s.ntile * sizeof(double) * batch) + up256(s.qs * batch) + up256(s.bd * batch) +
+         up256(s.bsc * batch) + up256(s.ad * batch) + up256(s.asc * batch);
 }
 
 MixedPtrs mixed_carve(char* base, const MixedSizes& s, int batch) {
@@ -442,6 +449,10 @@ MixedPtrs mixed_carve(char* base, const MixedSizes& s, int batch) {
   o += up256((size_t)s.ntile * sizeof(double) * batch);
   p.qscr = s.qs ? (float2*)(base + o) : nullptr;
   o += up256(s.qs * batch);
+  p.bd = (uint16_t*)(base + o); o += up256(s.bd * batch);
+  p.bsc = (float*)(base + o); o += up256(s.bsc * batch);
+  p.ad = (uint16_t*)(base + o); o += up256(s.ad * batch);
+  p.asc = (float*)(base + o); o += up256(s.asc * batch);
   return p;
 }
 
@@ -514,6 +525,7 @@ static cudaError_t conv_bt(const float2* X, const Dims* dims, const MixedPtrs& m
 
 cudaError_t mixed_prepare(const Caps& cap) {
   if (!encode_fn()) return cudaErrorNotSupported;
+  MX_TRY(oz_prepare());
   static int attr_done = 0;
   if (!attr_done) {
     MX_TRY(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes(TC_MAXBN)));
@@ -538,6 +550,7 @@ cudaError_t run_rrsvd_mixed(const Dims* dims, const ProbPtr* ptrs, int batch, co
     k_part_reduce<<<batch, NPART, 0, st>>>(mp.tpart, s.ntile, dims, ptrs);
     MX_TRY(cudaGetLastError());
   }
+  MX_TRY(launch_oz_digits_theta(dims, ptrs, mp.bd, mp.bsc, m, n, batch, st));
   {
     ProfScope ps("k_omega_bt", st);
     k_omega_bt<<<dim3(grid1d((int64_t)(s.Np / 2) * (s.K1 / 2)), batch), 256, 0, st>>>(
@@ -562,7 +575,7 @@ cudaError_t run_rrsvd_mixed(const Dims* dims, const ProbPtr* ptrs, int batch, co
   if (!reorth_fits(m, l)) return cudaErrorInvalidValue;
   MX_TRY(qr_f32(mp.Yf, mp.Qf, m, l, batch, mp, s, dims, 0, st));
   MX_TRY(launch_reorth(mp.Qf, mp.Df, dims, ptrs, m, l, batch, status, st));
-  MX_TRY(launch_proj_df(mp.thd, dims, ptrs, mp.Qf, mp.Df, m, n, l, batch, st));  // B^H = A^H Q
+  MX_TRY(launch_proj_oz(dims, ptrs, mp.Qf, mp.Df, mp.ad, mp.asc, mp.bd, mp.bsc, m, n, l, batch, err, st));  // B^H = A^H Q
   MX_TRY(launch_qr_sized(QR_BH, dims, ptrs, batch, cap, st));
   MX_TRY(launch_jacobi_sized(dims, ptrs, batch, cap, status, st));
   MX_TRY(launch_zgemm_df(G_U, dims, ptrs, batch, cap, st));

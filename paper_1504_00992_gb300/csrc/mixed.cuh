@@ -14,6 +14,7 @@ struct MixedSizes {
   int Np;        // 2l rounded up to 16: rows of Bt (tensor-core N)
   int BN;        // tensor-core tile width, min(Np, 256)
   size_t thf, tha, bt, yf, ytf, df, thd;  // bytes per instance
+  size_t bd, bsc, ad, asc;  // BF16 digits and block scales of theta and of Q_f^H (tensor-core projection)
   size_t qs;     // bytes per instance of the many-CTA FP32 QR's scratch (0: not used)
   int ntile;     // 32 x 32 tiles of the theta conversion (partials of ||theta||_F^2)
 };
@@ -32,6 +33,10 @@ struct MixedPtrs {
   float2* Qtf;
   float2* Df;     // l x l correction of the re-orthonormalisation
   float4* thd;    // m x n double-float conj(theta) (Re hi, Re lo, -Im hi, -Im lo), or null
+  uint16_t* bd;   // digits of theta for the tensor-core projection (oz_proj.cu)
+  float* bsc;     // their block scales
+  uint16_t* ad;   // digits of Q_f^H
+  float* asc;
   double* tpart;  // ntile partial sums of |theta|^2 per instance
   float2* qscr;   // scratch of the many-CTA FP32 QR (qs bytes per instance), or null
 };
@@ -67,6 +72,19 @@ cudaError_t launch_fold_bh(const float2* Dbuf, const Dims* dims, const ProbPtr* 
 // product with the FP32 Q_f, then the correction; after launch_reorth.
 cudaError_t launch_proj_df(const float4* thd, const Dims* dims, const ProbPtr* ptrs, const float2* Qf,
                            const float2* Dbuf, int m, int n, int l, int batch, cudaStream_t st);
+
+// B^H = A^H Q_f (I + D) into ptrs[z].Yt on the tensor cores from BF16 digits
+// (oz_proj.cu): launch_oz_digits_theta once theta is in place, launch_proj_oz
+// after launch_reorth.  Arrays at capacities m x n (theta) and m x l (Q_f).
+int oz_kpad(int m);
+size_t oz_digits_bytes(int rows, int m);
+size_t oz_scales_bytes(int rows, int m);
+cudaError_t oz_prepare();
+cudaError_t launch_oz_digits_theta(const Dims* dims, const ProbPtr* ptrs, uint16_t* Bd, float* Bs, int m, int n,
+                                   int batch, cudaStream_t st);
+cudaError_t launch_proj_oz(const Dims* dims, const ProbPtr* ptrs, const float2* Qf, const float2* Dbuf,
+                           uint16_t* Ad, float* As, const uint16_t* Bd, const float* Bs, int m, int n, int l, int batch,
+                           int* err, cudaStream_t st);
 
 // Everything that must happen outside a stream capture before
 // run_rrsvd_mixed runs on capacities `cap` (shared-memory limits, the

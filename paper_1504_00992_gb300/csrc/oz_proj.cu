@@ -1,0 +1,600 @@
+// FP64-accurate projection on the tensor cores (sm_103a tcgen05, BF16 slices).
+//
+// The step B = Q^H A of Section IV (after Alg. 1), in the mixed form with the
+// FP32 basis Q_f and its re-orthonormalisation Q = Q_f (I + D): C = Q_f^H A
+// (l x n) is formed from error-free slices of both operands, then
+// B^H = C^H (I + D) (the fold of qr_blocked.cu).
+//
+// Slices (Ozaki's error-free splitting; Ozaki, Ogita, Oishi, Rump, Numer.
+// Algorithms 59, 2012): within each block of OZ_KB consecutive k, every row i
+// of Q_f^H and every column j of A is scaled by a power of two s so that the
+// block's entries x satisfy |x| < s 2^8, and x / s is cut into OZ_S signed
+// 8-bit digits d_1 .. d_S (x = s (d_1 + d_2 2^-8 + ... ), truncated after 40
+// bits).  Digit t is stored as the BF16 number d_t 2^-8(t-1) (exact: 8
+// significant bits).  A product of digits t and u is then an integer times
+// 2^-8(t+u-2) below 2^16 in that unit, and the tensor core sums them in FP32
+// exactly as long as each sum stays below 2^24 units:
+//   level 2 (t + u = 2): one digit pair, 2 real products per k of C_r or C_i;
+//   level 3 (t + u = 3): two pairs, 4 products per k: exact for 64 k;
+//   levels 4 .. 6: summed together in FP32 (their rounding is 2^-40 of the
+//   level-2 sum); digit pairs with t + u > 6 are dropped (2^-40 relative).
+// Each block of OZ_KB = 64 k therefore runs into six accumulators in tensor
+// memory (C_r and C_i at levels 2, 3, 4+), which the epilogue warps read after
+// every block, scale by the two block scales and add into double-float
+// (FP32 pair) sums in registers.  Accuracy: ~1e-12 relative to |Q_f^H||A|,
+// FP64-accurate for the truncation (the double-float path it replaces gave
+// ~1e-14; both are far below the randomized method's own error).
+//
+// Complex products: C_r = Ar Br - Ai Bi, C_i = Ar Bi + Ai Br with Ar, Ai the
+// digits of Re and Im of Q_f^H (the conjugate folded in) and Br, Bi those of
+// A; the minus sign is the MMA's negate-A bit.
+//
+// Kernel structure (one CTA = 128 rows of C (l) x OZ_BN = 48 columns (n), all
+// k): warp 0 lane 0 streams the digit tiles of each 16-deep k step with 5-D
+// TMA loads (k, row, digit, re/im, instance; 32-byte swizzle) into a ring of
+// OZ_STAGES stages; warp 1 lane 0 issues 60 tcgen05.mma.kind::f16 per k step
+// (15 digit pairs x 4 real products); warps 2 .. 13 read the accumulators
+// after each k block (warp w reads TMEM lanes 32 (w % 4) .. +31, a third of
+// the columns) and keep the double-float sums.  Every mbarrier wait is
+// bounded; on expiry the kernel raises *err, waits for its own copies and
+// MMAs, and frees its tensor memory.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+
+#include "../../include/tebd_gb300.h"
+#include "dfsplit.cuh"
+#include "internal.cuh"
+#include "mixed.cuh"
+#include "profiler.cuh"
+#include "tc_sync.cuh"
+#include "workspace.cuh"
+
+namespace tg {
+
+enum {
+  OZ_S = 5,        // digits per operand
+  OZ_KB = 64,      // k per exact block
+  OZ_KS = 16,      // k per MMA / TMA stage
+  OZ_BM = 128,     // rows of C per CTA (TMEM lanes)
+  OZ_BN = 48,      // columns of C per CTA
+  OZ_STAGES = 3,
+  OZ_EPI_WARPS = 12,  // three per TMEM lane quadrant, 16 columns each
+  OZ_THREADS = 64 + 32 * OZ_EPI_WARPS,
+  OZ_NPAIR = 15,
+  OZ_TMEM_COLS = 512  // six 48-column accumulators, rounded up to a power of two
+};
+
+static const uint32_t OZ_A_TILE = OZ_BM * OZ_KS * 2;  // one digit tile of Q_f^H: 4 KB
+static const uint32_t OZ_B_TILE = OZ_BN * OZ_KS * 2;  // one digit tile of A: 1.5 KB
+static const uint32_t OZ_A_STAGE = 2 * OZ_S * OZ_A_TILE;
+static const uint32_t OZ_B_STAGE = 2 * OZ_S * OZ_B_TILE;
+// low words of the epilogue's double-float sums: [epilogue warp][value][lane],
+// 32 values (16 columns, Re and Im) per thread
+static const uint32_t OZ_LO_BYTES = OZ_EPI_WARPS * 32 * 32 * 4;
+
+// ---------------------------------------------------------------------------
+// Digits.  An FP64 or FP32 value and the block's largest biased exponent E
+// give a 40-bit fixed-point magnitude N (x = +-N 2^(E - bias - mantissa - 13)
+// for FP64), cut into five 8-bit digits, each stored as the BF16 number
+// +-d_t 2^-8(t-1) (bit pattern built from FP32 arithmetic that is exact).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint16_t oz_bf16_digit(unsigned d, int t, bool neg) {
+  const float f = (float)d * __uint_as_float((unsigned)(127 - 8 * t) << 23);  // d 2^-8t, exact
+  const unsigned u = __float_as_uint(f) >> 16;
+  return (uint16_t)(u | (neg && d ? 0x8000u : 0u));
+}
+
+// 40-bit magnitude of an FP64 value relative to block exponent E (biased).
+__device__ __forceinline__ uint64_t oz_n40_f64(double x, int E) {
+  const uint64_t u = (uint64_t)__double_as_longlong(x);
+  const int e = (int)((u >> 52) & 0x7FF);
+  if (e == 0 || e == 0x7FF) return 0;  // zero, subnormal (negligible), non-finite (flagged elsewhere)
+  const uint64_t m = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const int sh = E - e + 13;  // >= 13
+  return sh >= 64 ? 0 : (m >> sh);
+}
+
+__device__ __forceinline__ uint64_t oz_n40_f32(float x, int E) {
+  const unsigned u = __float_as_uint(x);
+  const int e = (int)((u >> 23) & 0xFF);
+  if (e == 0 || e == 0xFF) return 0;
+  const uint64_t m = (uint64_t)((u & 0x7FFFFFu) | 0x800000u);
+  const int sh = e - E + 16;  // <= 16
+  return sh >= 0 ? (m << sh) : ((-sh) >= 64 ? 0 : (m >> (-sh)));
+}
+
+// Scale 2^(E - off) as an FP32 number, or 0 when it is below the normal range
+// (the whole block is then negligible and its digits are zero).
+__device__ __forceinline__ float oz_scale(int E, int off) {
+  const int b = E - off + 127;
+  return (b >= 1 && b <= 254) ? __uint_as_float((unsigned)b << 23) : 0.f;
+}
+
+// ---------------------------------------------------------------------------
+// Digits of A (theta, m x n row-major FP64 per instance) into
+// Bd[z][reim][t][j][k] (k contiguous, Kp per row, rows nc) and block scales
+// Bs[z][kb][j].  A CTA takes 64 k x 32 j; rows past the instance's (m, n)
+// become zero digits.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_oz_digits_theta(const Dims* __restrict__ dims,
+                                                         const ProbPtr* __restrict__ ptrs, uint16_t* Bd, float* Bs,
+                                                         int nc, int Kp) {
+  __shared__ int emax[8][33];
+  __shared__ uint16_t dig[2 * OZ_S][32][OZ_KB + 2];  // [reim t][j][k]
+  const int z = blockIdx.z;
+  const Dims D = dims[z];
+  if (!D.active) return;
+  const int m = D.m, n = D.n;
+  const cplx* th = ptrs[z].theta;
+  const int k0 = blockIdx.y * OZ_KB, j0 = blockIdx.x * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int j = j0 + tx;
+  cplx v[8];
+  int e = 0;
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const int k = k0 + ty + 8 * s;
+    v[s] = (k < m && j < n) ? th[(int64_t)k * n + j] : cmk(0.0, 0.0);
+    const uint64_t ur = (uint64_t)__double_as_longlong(v[s].x), ui = (uint64_t)__double_as_longlong(v[s].y);
+    const int er = (int)((ur >> 52) & 0x7FF), ei = (int)((ui >> 52) & 0x7FF);
+    e = max(e, max(er == 0x7FF ? 0 : er, ei == 0x7FF ? 0 : ei));
+  }
+  emax[ty][tx] = e;
+  __syncthreads();
+  int E = 0;
+#pragma unroll
+  for (int s = 0; s < 8; ++s) E = max(E, emax[s][tx]);
+  const float sc = oz_scale(E, 1030);  // x = sum_t digit_t * 2^(E - 1030)
+  const bool live = sc != 0.f;
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const int k = ty + 8 * s;
+    const uint64_t nr = live ? oz_n40_f64(v[s].x, E) : 0, ni = live ? oz_n40_f64(v[s].y, E) : 0;
+    const bool sr = v[s].x < 0.0, si = v[s].y < 0.0;
+#pragma unroll
+    for (int t = 0; t < OZ_S; ++t) {
+      dig[t][tx][k] = oz_bf16_digit((unsigned)((nr >> (32 - 8 * t)) & 0xFF), t, sr);
+      dig[OZ_S + t][tx][k] = oz_bf16_digit((unsigned)((ni >> (32 - 8 * t)) & 0xFF), t, si);
+    }
+  }
+  if (ty == 0 && j < nc) Bs[((size_t)z * (Kp / OZ_KB) + blockIdx.y) * nc + j] = live ? sc : 0.f;
+  __syncthreads();
+  // rows (reim t, j) of 64 k = 128 bytes each: 8 threads per row, 16 bytes each
+  uint16_t* base = Bd + (size_t)z * 2 * OZ_S * nc * Kp;
+  for (int w = threadIdx.x; w < 2 * OZ_S * 32 * 8; w += 256) {
+    const int q = w & 7, row = w >> 3, jj = row & 31, rt = row >> 5;
+    if (j0 + jj >= nc) continue;
+    const uint16_t* src = &dig[rt][jj][q * 8];
+    uint4 pk;
+    pk.x = (unsigned)src[0] | ((unsigned)src[1] << 16);
+    pk.y = (unsigned)src[2] | ((unsigned)src[3] << 16);
+    pk.z = (unsigned)src[4] | ((unsigned)src[5] << 16);
+    pk.w = (unsigned)src[6] | ((unsigned)src[7] << 16);
+    *reinterpret_cast<uint4*>(base + ((size_t)rt * nc + j0 + jj) * Kp + k0 + q * 8) = pk;
+  }
+}
+
+// Digits of Q_f^H (Q_f m x l column-major FP32 complex per instance, capacity
+// mc x lc) into Ad[z][reim][t][i][k] and scales As[z][kb][i]: one warp per
+// (i, k block), two k per lane; Im negated (the conjugate).
+__global__ void __launch_bounds__(256) k_oz_digits_q(const Dims* __restrict__ dims, const float2* __restrict__ Qf,
+                                                     uint16_t* Ad, float* As, int mc, int lc, int Kp) {
+  const int z = blockIdx.y;
+  const Dims D = dims[z];
+  if (!D.active) return;
+  const int nkb = Kp / OZ_KB;
+  const int lane = threadIdx.x & 31;
+  const int wid = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (wid >= lc * nkb) return;
+  const int i = wid / nkb, kb = wid % nkb;
+  const int k = kb * OZ_KB + 2 * lane;
+  float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
+  if (i < D.l) {
+    const float2* q = Qf + (size_t)z * mc * lc + (size_t)i * mc;
+    if (k < D.m) a = q[k];
+    if (k + 1 < D.m) b = q[k + 1];
+  }
+  auto ex = [](float x) {
+    const int e = (int)((__float_as_uint(x) >> 23) & 0xFF);
+    return e == 0xFF ? 0 : e;
+  };
+  int E = max(max(ex(a.x), ex(a.y)), max(ex(b.x), ex(b.y)));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) E = max(E, __shfl_xor_sync(0xffffffffu, E, o));
+  const float sc = oz_scale(E, 134);  // x = sum_t digit_t * 2^(E - 134)
+  const bool live = sc != 0.f;
+  uint16_t* base = Ad + (size_t)z * 2 * OZ_S * lc * Kp;
+  const float re[2] = {a.x, b.x}, im[2] = {-a.y, -b.y};
+#pragma unroll
+  for (int t = 0; t < OZ_S; ++t) {
+    uint16_t dr[2], di[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const uint64_t nr = live ? oz_n40_f32(re[h], E) : 0, ni = live ? oz_n40_f32(im[h], E) : 0;
+      dr[h] = oz_bf16_digit((unsigned)((nr >> (32 - 8 * t)) & 0xFF), t, re[h] < 0.f);
+      di[h] = oz_bf16_digit((unsigned)((ni >> (32 - 8 * t)) & 0xFF), t, im[h] < 0.f);
+    }
+    *reinterpret_cast<unsigned*>(base + ((size_t)t * lc + i) * Kp + k) = (unsigned)dr[0] | ((unsigned)dr[1] << 16);
+    *reinterpret_cast<unsigned*>(base + ((size_t)(OZ_S + t) * lc + i) * Kp + k) =
+        (unsigned)di[0] | ((unsigned)di[1] << 16);
+  }
+  if (lane == 0) As[((size_t)z * nkb + kb) * lc + i] = live ? sc : 0.f;
+}
+
+// ---------------------------------------------------------------------------
+// The digit-pair GEMM.
+// ---------------------------------------------------------------------------
+struct OzArgs {
+  int lc, nc, Kp;      // capacities: rows of C, columns of C, padded k
+  const float* As;     // [z][kb][i]
+  const float* Bs;     // [z][kb][j]
+  int* err;
+  uint32_t poll_limit;
+  int stall;
+};
+
+__device__ __forceinline__ void oz_tma_load_5d(void* dst, const CUtensorMap* tm, int c0, int c1, int c4, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
+      "%6}], [%7];" ::"r"(tc_smem_u32(dst)),
+      "l"((uint64_t)tm), "r"(c0), "r"(c1), "r"(0), "r"(0), "r"(c4), "r"(tc_smem_u32(bar))
+      : "memory");
+}
+
+// K-major, 32-byte swizzle: 8-row atoms of 256 bytes (stride byte offset 256).
+__device__ __forceinline__ uint64_t oz_desc_sw32(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;            // leading byte offset (unused: one atom along k)
+  d |= (uint64_t)(256 >> 4) << 32;   // stride byte offset
+  d |= (uint64_t)1 << 46;            // version
+  d |= (uint64_t)6 << 61;            // 32-byte swizzle
+  return d;
+}
+
+// kind::f16 instruction descriptor: D = F32, A = B = BF16, K-major, M x N.
+__host__ __device__ constexpr uint32_t oz_idesc(int M, int N, bool negA) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (negA ? (1u << 13) : 0u) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void oz_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void oz_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(tc_smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void oz_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc_smem_u32(bar)) : "memory");
+}
+
+// Warp-uniform bounded wait: lane 0 polls, the warp gets its answer.
+__device__ __forceinline__ bool oz_warp_wait(uint64_t* bar, uint32_t parity, uint32_t limit, int* err,
+                                             volatile int* abort_flag) {
+  bool ok = false;
+  if ((threadIdx.x & 31) == 0) ok = tc_mbar_wait(bar, parity, limit, err, abort_flag);
+  return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+}
+
+__device__ __forceinline__ void oz_ld2(uint32_t taddr, float* v) {
+  uint32_t r[2];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(taddr) : "memory");
+  v[0] = __uint_as_float(r[0]);
+  v[1] = __uint_as_float(r[1]);
+}
+
+// acc (h, l) += s (hs, ls), then renormalised
+__device__ __forceinline__ void oz_df_add(float& h, float& l, float hs, float ls) {
+  float t, e;
+  two_sum(h, hs, t, e);
+  e += l + ls;
+  h = t + e;
+  l = e - (h - t);
+}
+
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+    k_oz_proj(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+              const Dims* __restrict__ dims, const ProbPtr* __restrict__ ptrs, OzArgs a) {
+  extern __shared__ __align__(1024) uint8_t oz_smem_raw[];
+  const int z = blockIdx.z;
+  const Dims D = dims[z];
+  const int i0 = blockIdx.y * OZ_BM, j0 = blockIdx.x * OZ_BN;
+  if (!D.active || i0 >= D.l || j0 >= D.n) return;  // uniform: before any barrier or allocation
+  uint8_t* smem = (uint8_t*)(((uintptr_t)oz_smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + OZ_STAGES * OZ_A_STAGE;
+  float* lo_s = (float*)(sB + OZ_STAGES * OZ_B_STAGE);
+  uint64_t* full = (uint64_t*)((uint8_t*)lo_s + OZ_LO_BYTES);
+  uint64_t* empty = full + OZ_STAGES;
+  uint64_t* accf = empty + OZ_STAGES;
+  uint64_t* accfree = accf + 1;
+  uint64_t* drain = accfree + 1;
+  uint32_t* tmem_holder = (uint32_t*)(drain + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_holder + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nks = (min(D.m, a.Kp) + OZ_KS - 1) / OZ_KS;  // k steps of this instance
+  const int nkb = (nks + (OZ_KB / OZ_KS) - 1) / (OZ_KB / OZ_KS);
+  const int iters = nkb * (OZ_KB / OZ_KS);  // whole blocks (zero digits past m)
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_smem_u32(tmem_holder)),
+                 "r"((uint32_t)OZ_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 32) {
+    for (int s = 0; s < OZ_STAGES; ++s) {
+      tc_mbar_init(&full[s], 1);
+      tc_mbar_init(&empty[s], 1);
+    }
+    tc_mbar_init(accf, 1);
+    tc_mbar_init(accfree, OZ_EPI_WARPS);
+    tc_mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_holder;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---- producer
+      int issued = 0;
+      for (int it = 0; it < (a.stall ? 0 : iters); ++it) {
+        const int s = it % OZ_STAGES;
+        const uint32_t r = (uint32_t)(it / OZ_STAGES);
+        if (it >= OZ_STAGES && !tc_mbar_wait(&empty[s], (r & 1u) ^ 1u, a.poll_limit, a.err, abort_flag)) break;
+        tc_mbar_expect_tx(&full[s], OZ_A_STAGE + OZ_B_STAGE);
+        oz_tma_load_5d(sA + s * OZ_A_STAGE, &tmA, it * OZ_KS, i0, z, &full[s]);
+        oz_tma_load_5d(sB + s * OZ_B_STAGE, &tmB, it * OZ_KS, j0, z, &full[s]);
+        issued = it + 1;
+      }
+      if (*abort_flag) {  // every copy issued lands before the teardown
+        for (int it = (issued > OZ_STAGES ? issued - OZ_STAGES : 0); it < issued; ++it)
+          for (uint32_t i = 0; i < (1u << 22); ++i)
+            if (tc_mbar_try_wait(&full[it % OZ_STAGES], (uint32_t)(it / OZ_STAGES) & 1u)) break;
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---- MMA issuer: per k step, the 15 digit pairs (t, u) with t + u <= 6
+      // in level order, four real products each
+      const uint32_t ip = oz_idesc(OZ_BM, OZ_BN, false), in = oz_idesc(OZ_BM, OZ_BN, true);
+      bool ok = true;
+      int issued_mma = 0;
+      for (int kb = 0; kb < nkb && ok; ++kb) {
+        if (kb > 0 && !tc_mbar_wait(accfree, (uint32_t)(kb - 1) & 1u, a.poll_limit, a.err, abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        for (int ks = 0; ks < OZ_KB / OZ_KS; ++ks) {
+          const int it = kb * (OZ_KB / OZ_KS) + ks;
+          const int s = it % OZ_STAGES;
+          if (!tc_mbar_wait(&full[s], (uint32_t)(it / OZ_STAGES) & 1u, a.poll_limit, a.err, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t abase = tc_smem_u32(sA + s * OZ_A_STAGE), bbase = tc_smem_u32(sB + s * OZ_B_STAGE);
+          int pi = 0;
+#pragma unroll
+          for (int lv = 2; lv <= OZ_S + 1; ++lv) {
+#pragma unroll
+            for (int t = 1; t < lv; ++t) {
+              const int u = lv - t;
+              if (t > OZ_S || u > OZ_S) continue;
+              const int g = lv == 2 ? 0 : (lv == 3 ? 1 : 2);  // accumulator group of the level
+              const bool first = ks == 0 && ((lv == 2) || (lv == 3 && t == 1) || (lv == 4 && t == 1));
+              const uint32_t dr = tmem + (uint32_t)(OZ_BN * g), di = tmem + (uint32_t)(OZ_BN * (3 + g));
+              const uint64_t ar = oz_desc_sw32(abase + (0 * OZ_S + t - 1) * OZ_A_TILE);
+              const uint64_t ai = oz_desc_sw32(abase + (1 * OZ_S + t - 1) * OZ_A_TILE);
+              const uint64_t br = oz_desc_sw32(bbase + (0 * OZ_S + u - 1) * OZ_B_TILE);
+              const uint64_t bi = oz_desc_sw32(bbase + (1 * OZ_S + u - 1) * OZ_B_TILE);
+              oz_mma(dr, ar, br, ip, first ? 0u : 1u);  // C_r += Ar Br
+              oz_mma(dr, ai, bi, in, 1u);               // C_r -= Ai Bi
+              oz_mma(di, ar, bi, ip, first ? 0u : 1u);  // C_i += Ar Bi
+              oz_mma(di, ai, br, ip, 1u);               // C_i += Ai Br
+              ++pi;
+            }
+          }
+          (void)pi;
+          oz_commit(&empty[s]);  // the stage is free once these MMAs have read it
+          issued_mma = it + 1;
+        }
+        if (!ok) break;
+        oz_commit(accf);  // block kb's sums are ready
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        if (issued_mma > 0) {  // the MMAs issued read shared memory and write the tensor memory freed below
+          oz_commit(drain);
+          for (uint32_t i = 0; i < a.poll_limit; ++i)
+            if (tc_mbar_try_wait(drain, 0)) break;
+        }
+      }
+    }
+    __syncwarp();
+  } else {
+    // ---- epilogue: warp w reads lanes 32 (w % 4) .. +31 and one third of the columns
+    const int ew = warp - 2, quad = warp & 3, part = ew >> 2;
+    const int i = i0 + 32 * quad + lane;  // row of C
+    const int jq = j0 + 16 * part;        // first column of this warp
+    const int nkbt = a.Kp / OZ_KB;        // k blocks of the scale arrays
+    float hr[16], hi[16];                  // high words in registers, low words in shared memory
+    float* lw = lo_s + (size_t)ew * 32 * 32 + lane;  // value v at lw[32 v]
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      hr[c] = hi[c] = 0.f;
+      lw[32 * c] = 0.f;
+      lw[32 * (16 + c)] = 0.f;
+    }
+    bool ok = true;
+    for (int kb = 0; kb < nkb; ++kb) {
+      ok = oz_warp_wait(accf, (uint32_t)kb & 1u, a.poll_limit, a.err, abort_flag);
+      if (!ok) break;
+      tc_fence_after();
+      const float sa = (i < a.lc) ? a.As[((size_t)z * nkbt + kb) * a.lc + i] : 0.f;
+      const float* sbp = a.Bs + ((size_t)z * nkbt + kb) * a.nc;
+      const uint32_t lanes = (uint32_t)(32 * quad) << 16;
+#pragma unroll
+      for (int c4 = 0; c4 < 16; c4 += 2) {
+        float v[6][2];
+#pragma unroll
+        for (int g = 0; g < 6; ++g) oz_ld2(tmem + lanes + (uint32_t)(OZ_BN * g + 16 * part + c4), v[g]);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int j = jq + c4 + q;
+          const float sc = sa * ((j < a.nc) ? __ldg(sbp + j) : 0.f);
+          float s, e;
+          two_sum(v[0][q], v[1][q], s, e);  // levels 2 and 3 exactly, level 4+ into the low part
+          e += v[2][q];
+          oz_df_add(hr[c4 + q], lw[32 * (c4 + q)], s * sc, e * sc);
+          two_sum(v[3][q], v[4][q], s, e);
+          e += v[5][q];
+          oz_df_add(hi[c4 + q], lw[32 * (16 + c4 + q)], s * sc, e * sc);
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) oz_arrive(accfree);  // the accumulators may be overwritten
+    }
+    if (ok && i < D.l) {
+      cplx* X = ptrs[z].Yt;  // B^H = C^H: n x l column-major, element (j, i) = conj C[i][j]
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const int j = jq + c;
+        if (j < D.n)
+          X[(size_t)i * D.n + j] = cmk((double)hr[c] + (double)lw[32 * c], -((double)hi[c] + (double)lw[32 * (16 + c)]));
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)OZ_TMEM_COLS)
+                 : "memory");
+  }
+}
+
+static size_t oz_smem_bytes() {
+  return 1024 + (size_t)OZ_STAGES * (OZ_A_STAGE + OZ_B_STAGE) + OZ_LO_BYTES + (2 * OZ_STAGES + 3) * 8 + 16;
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+typedef CUresult (*OzEncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                               const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                               CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static OzEncodeFn oz_encode_fn() {
+  static std::mutex mu;
+  static OzEncodeFn fn = nullptr;
+  std::lock_guard<std::mutex> g(mu);
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (OzEncodeFn)p;
+  }
+  return fn;
+}
+
+// 5-D map over digit arrays [z][reim][t][row][k] (BF16): box 16 k x box_rows
+// rows x all digits x both parts x one instance, 32-byte swizzle.
+static bool oz_make_map(CUtensorMap* m, const uint16_t* base, int Kp, int rows, int batch, int box_rows) {
+  OzEncodeFn enc = oz_encode_fn();
+  if (!enc) return false;
+  cuuint64_t dims[5] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)OZ_S, 2, (cuuint64_t)batch};
+  const cuuint64_t rb = (cuuint64_t)Kp * 2;
+  cuuint64_t strides[4] = {rb, rb * rows, rb * rows * OZ_S, rb * rows * OZ_S * 2};
+  cuuint32_t box[5] = {(cuuint32_t)OZ_KS, (cuuint32_t)box_rows, (cuuint32_t)OZ_S, 2, 1};
+  cuuint32_t es[5] = {1, 1, 1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, (void*)base, dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int oz_kpad(int m) { return ((m + OZ_KB - 1) / OZ_KB) * OZ_KB; }
+
+size_t oz_digits_bytes(int rows, int m) { return (size_t)2 * OZ_S * rows * oz_kpad(m) * sizeof(uint16_t); }
+size_t oz_scales_bytes(int rows, int m) { return (size_t)(oz_kpad(m) / OZ_KB) * rows * sizeof(float); }
+
+cudaError_t oz_prepare() {
+  if (!oz_encode_fn()) return cudaErrorNotSupported;
+  static int done = 0;
+  if (!done) {
+    const cudaError_t e = cudaFuncSetAttribute(k_oz_proj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes());
+    if (e != cudaSuccess) return e;
+    done = 1;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_oz_digits_theta(const Dims* dims, const ProbPtr* ptrs, uint16_t* Bd, float* Bs, int m, int n,
+                                   int batch, cudaStream_t st) {
+  ProfScope ps("k_oz_digits[theta]", st);
+  const int Kp = oz_kpad(m);
+  k_oz_digits_theta<<<dim3((n + 31) / 32, Kp / OZ_KB, batch), 256, 0, st>>>(dims, ptrs, Bd, Bs, n, Kp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_proj_oz(const Dims* dims, const ProbPtr* ptrs, const float2* Qf, const float2* Dbuf,
+                           uint16_t* Ad, float* As, const uint16_t* Bd, const float* Bs, int m, int n, int l, int batch,
+                           int* err, cudaStream_t st) {
+  const int Kp = oz_kpad(m);
+  {
+    ProfScope ps("k_oz_digits[q]", st);
+    const int warps = l * (Kp / OZ_KB);
+    k_oz_digits_q<<<dim3((warps + 7) / 8, batch), 256, 0, st>>>(dims, Qf, Ad, As, m, l, Kp);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  {
+    cudaError_t e = oz_prepare();
+    if (e != cudaSuccess) return e;
+    CUtensorMap ta, tb;
+    if (!oz_make_map(&ta, Ad, Kp, l, batch, OZ_BM) || !oz_make_map(&tb, Bd, Kp, n, batch, OZ_BN))
+      return cudaErrorInvalidValue;
+    OzArgs oa;
+    oa.lc = l;
+    oa.nc = n;
+    oa.Kp = Kp;
+    oa.As = As;
+    oa.Bs = Bs;
+    oa.err = err;
+    // an injected pipeline stall (test hook), never inside a stream capture
+    cudaStreamCaptureStatus cap_st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap_st) != cudaSuccess) cap_st = cudaStreamCaptureStatusActive;
+    const bool stall = cap_st == cudaStreamCaptureStatusNone && fault_take(TEBD_FAULT_TC_STALL);
+    oa.poll_limit = stall ? (1u << 12) : (1u << 24);
+    oa.stall = stall ? 1 : 0;
+    ProfScope ps("k_oz_proj[project]", st);
+    k_oz_proj<<<dim3((n + OZ_BN - 1) / OZ_BN, (l + OZ_BM - 1) / OZ_BM, batch), OZ_THREADS, oz_smem_bytes(), st>>>(
+        ta, tb, dims, ptrs, oa);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return launch_fold_bh(Dbuf, dims, ptrs, n, l, batch, st);
+}
+
+}  // namespace tg

@@ -27,6 +27,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "tc_sync.cuh"
+
 namespace tg {
 
 enum { TC_BM = 128, TC_BK = 32, TC_STAGES = 4, TC_MAXBN = 256, TC_TMEM_COLS = 256 };
@@ -43,48 +45,6 @@ struct TcArgs {
   uint32_t poll_limit;  // polls of a pipeline wait before it gives up (1 << 24)
   int stall;      // test hook: the producer issues no copies, so the waits expire
 };
-
-__device__ __forceinline__ uint32_t tc_smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void tc_mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc_smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void tc_mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc_smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool tc_mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}\n"
-      : "=r"(ok)
-      : "r"(tc_smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait on a phase of an mbarrier; returns false (and raises *err /
-// the CTA abort flag) when the limit expires or another thread gave up.
-__device__ __forceinline__ bool tc_mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit, int* err,
-                                             volatile int* abort_flag) {
-  for (uint32_t i = 0; i < limit; ++i) {
-    if (tc_mbar_try_wait(bar, parity)) return true;
-    if ((i & 1023u) == 1023u && *abort_flag) return false;
-  }
-  *abort_flag = 1;
-  atomicExch(err, 1);
-  return false;
-}
-__device__ __forceinline__ void tc_tma_load_3d(void* dst, const CUtensorMap* tm, int x, int y, int z, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
-          "r"(tc_smem_u32(dst)),
-      "l"((uint64_t)tm), "r"(x), "r"(y), "r"(z), "r"(tc_smem_u32(bar))
-      : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms of
 // 1024 bytes stacked along M/N (stride byte offset 1024), descriptor version 1.

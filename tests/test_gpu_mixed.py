@@ -129,3 +129,38 @@ def test_mixed_form_rank_deficient(lib, m, n, k, p, rank):
         assert np.abs(U.conj().T @ U - np.eye(r)).max() < 1e-11
         V = res["Vh"][t][:r]
         assert np.abs(V @ V.conj().T - np.eye(r)).max() < 1e-11
+
+
+@pytest.mark.parametrize("m,n,k,scale_rows", [
+    (200, 120, 120, False),   # l = n: the sketch spans the whole column space
+    (150, 300, 150, True),    # l = m, rows scaled over 2^-40 .. 2^40 (block scales of the digits)
+    (4000, 100, 100, False),  # 63 k blocks of the projection
+])
+def test_mixed_projection_is_fp64_accurate(lib, m, n, k, scale_rows):
+    """When the sketch covers min(m, n) columns the RRSVD is exact, and the
+    mixed form's singular values and reconstruction are then limited by its
+    FP64-accurate steps: the projection B^H = A^H Q on the tensor cores (BF16
+    digits of both operands, exact FP32 sums per 64-deep k block; ~1e-12
+    relative), the re-orthonormalised basis and the FP64 small SVD.  Held to
+    1e-11 relative, where an FP32-level projection would miss by 1e-7."""
+    from paper_1504_00992_gb300 import binding as B
+    batch = 2
+    rng = np.random.default_rng(31)
+    r = min(m, n)
+    sig = np.exp(-np.arange(r) / (r / 12.0))
+    theta = np.stack([I.synthetic_theta(m, n, sig, seed=500 + t) for t in range(batch)])
+    if scale_rows:
+        theta = theta * (2.0 ** rng.integers(-40, 41, size=(1, m, 1)))
+    plan = B.rrsvd_plan_create(m, n, k, 10, 1, batch, B.TEBD_PREC_TF32, SEED)
+    try:
+        res = rrsvd_device(B, plan, theta)
+    finally:
+        B.rrsvd_plan_destroy(plan)
+    kk = min(k, m, n)
+    for t in range(batch):
+        s_ref = np.linalg.svd(theta[t], compute_uv=False)
+        s = res["sigma"][t]
+        assert res["rank"][t] == kk
+        assert np.abs(s - s_ref[:kk]).max() <= 1e-11 * s_ref[0]
+        rec = truncated(res["U"][t], s, res["Vh"][t])
+        assert np.linalg.norm(rec - theta[t]) <= 1e-11 * np.linalg.norm(theta[t])
