@@ -105,10 +105,12 @@ typedef struct {
                            replayed (not while the kernel profiler is enabled); the
                            legacy stream 0 cannot be captured, so such a handle then
                            runs on a blocking stream of its own */
-  int autotune;         /* nonzero: at creation, time the 16x16 and 32x32 GEMM tiles of
-                           every stage at the capacity sizes and keep the faster, and
-                           (with fused = 0) the staged sequence against the fused
-                           persistent launch for every wave it fits (tebd_wave_info) */
+  int autotune;         /* nonzero: at creation, time each wave's launch choices at its
+                           capacity sizes and keep the fastest (tebd_wave_info): FP64 --
+                           the 16x16 or 32x32 GEMM tiles of every stage and (with
+                           fused = 0) the staged sequence against the fused persistent
+                           launch; TF32 -- the mixed form's choices as for
+                           rrsvd_plan_autotune */
   size_t workspace_budget; /* bytes of per-bond workspace one wave may use (0 = all bonds
                               of a parity in one wave); larger batches run in waves */
   tebd_alloc_fn alloc;     /* optional: allocator of every device block of the handle
@@ -162,8 +164,10 @@ int tebd_workspace_info(tebd_t h, size_t* arena_bytes, int* waves_even, int* wav
  * tebd_workspace_info).  info (16 ints): [0] bonds in the wave, [1..4] its
  * capacities m, n, k, l, [5] 1 if it runs as the persistent fused launch,
  * [6..11] the GEMM tile of stages Y0, Y~, Y, B^H, U, V (0: by grid size),
- * [12..15] reserved (0).  ms (2 doubles): the autotuner's timings of the
- * wave's staged and fused RRSVD on synthetic theta (0 when not timed).
+ * [12..15] the mixed form's launch choices of TF32 handles (as
+ * rrsvd_plan_tuning's [6..9]).  ms (2 doubles): the autotuner's timings on
+ * synthetic theta -- FP64: the wave's staged and fused RRSVD; TF32: the RRSVD
+ * with the size rules and with the choices kept (0 when not timed).
  * Either may be NULL.  Errors: TEBD_EINVAL (parity, wave). */
 int tebd_wave_info(tebd_t h, int parity, int wave, int* info, double* ms);
 
@@ -356,6 +360,24 @@ int rrsvd_execute_host(rrsvd_plan_t plan, const double* theta, int64_t chain0, d
                        double* Vh, double* w, int* rank, void* stream);
 
 const char* rrsvd_last_error(rrsvd_plan_t plan);
+
+/* Autotuner of a plan (the batched launches of Section IV's steps): times
+ * the launch choices on the caller's theta (device, as for rrsvd_execute) and
+ * keeps the fastest for later executes.  FP64 plans: the GEMM tile of every
+ * stage; TF32 plans: the mixed form's choices (tensor-core tile width, CTA
+ * size of the FP32 QRs, one-CTA or many-CTA QR of B^H, one-CTA or cluster
+ * Jacobi), one at a time, each kept only for a clear gain.  Results of a
+ * tuned plan agree with an untuned one to rounding.  Synchronises `stream`.
+ * Errors: as rrsvd_execute. */
+int rrsvd_plan_autotune(rrsvd_plan_t plan, const double* theta, void* workspace, size_t workspace_bytes,
+                        void* stream);
+
+/* What the autotuner chose: info (16 ints): [0..5] the FP64 GEMM tile of
+ * stages Y0, Y~, Y, B^H, U, V (0: by grid size), [6..9] the mixed form's
+ * choices (tile split, FP32 QR threads, QR of B^H, Jacobi; 0: the size rule),
+ * [10] 1 once tuned; ms (2 doubles, TF32 plans): the step with the size
+ * rules and with the choices kept.  Either may be NULL. */
+int rrsvd_plan_tuning(rrsvd_plan_t plan, int* info, double* ms);
 
 /* Clears the plan's recorded error and its device status flags (a zero or
  * non-finite theta, an expired tensor-core wait): an execute that failed

@@ -109,6 +109,8 @@ _SIGS = {
     "tebd_bond_weights": (_i, [_vp, _pd]),
     "tebd_fault_inject": (_i, [_i]),
     "rrsvd_clear_error": (_i, [_vp]),
+    "rrsvd_plan_autotune": (_i, [_vp, _vp, _vp, ctypes.c_size_t, _vp]),
+    "rrsvd_plan_tuning": (_i, [_vp, _pi, _pd]),
     "tebd_set_product_state": (_i, [_vp, _pd]),
     "tebd_set_mps": (_i, [_vp, ctypes.POINTER(_pd), ctypes.POINTER(_pd), _pi]),
     "tebd_get_mps": (_i, [_vp, ctypes.POINTER(_pd), ctypes.POINTER(_pd), _pi]),
@@ -269,7 +271,9 @@ def tebd_wave_info(h, parity, wave):
     ms = (ctypes.c_double * 2)()
     _check(h, load().tebd_wave_info(h, parity, wave, info, ms))
     return {"bonds": info[0], "m": info[1], "n": info[2], "k": info[3], "l": info[4], "fused": info[5],
-            "tiles": list(info[6:12]), "tune_ms": {"staged": ms[0], "fused": ms[1]}}
+            "tiles": list(info[6:12]), "mixed": {"tc_half": info[12], "qr_threads": info[13], "qrbh": info[14],
+                                                 "jacobi": info[15]},
+            "tune_ms": [ms[0], ms[1]]}
 
 
 def tebd_tuning_table(h):
@@ -513,6 +517,21 @@ def rrsvd_last_error(plan):
 
 def rrsvd_clear_error(plan):
     _pcheck(plan, load().rrsvd_clear_error(plan))
+
+
+def rrsvd_plan_autotune(plan, theta_ptr, ws_ptr, ws_bytes, stream_ptr=0):
+    """Time the plan's launch choices on device theta and keep the fastest."""
+    def vp(x):
+        return _vp(int(x)) if x else None
+    _pcheck(plan, load().rrsvd_plan_autotune(plan, vp(theta_ptr), vp(ws_ptr), ws_bytes, vp(stream_ptr)))
+
+
+def rrsvd_plan_tuning(plan):
+    info = (ctypes.c_int * 16)()
+    ms = (ctypes.c_double * 2)()
+    _pcheck(plan, load().rrsvd_plan_tuning(plan, info, ms))
+    return {"tiles": list(info[0:6]), "tc_half": info[6], "qr_threads": info[7], "qrbh": info[8], "jacobi": info[9],
+            "tuned": info[10], "ms_rules": ms[0], "ms_kept": ms[1]}
 
 
 # ------------------------------------------------------------------ kernel timing

@@ -167,6 +167,7 @@ struct Wave {
   Caps cap{};
   int tiles[6] = {0, 0, 0, 0, 0, 0};
   int fused = 0;    // 1: the whole update of every bond in one persistent launch (fused.cu)
+  MixedKnobs mk{0, 0, 0, 0};  // launch choices of the mixed form (TF32 handles)
   float tune_ms[2] = {0.f, 0.f};  // tuner timings of the staged and fused RRSVD (0: not timed)
   MixedSizes ms{};  // TF32 handles: the wave's FP32 arrays at its capacities
 };
@@ -267,6 +268,7 @@ static void tebd_free(tebd_s* h) {
 // on the wave's capacity sizes (the saturated regime) and keeps the faster.
 // Results are cached per (stage, rows, cols, inner, batch) for the process.
 static std::map<std::vector<long long>, int> g_tile_cache;
+static std::map<std::vector<long long>, std::pair<MixedKnobs, std::vector<float>>> g_knob_cache;
 static std::mutex g_tile_mu;
 
 static int tune_wave(tebd_s* h, const ParitySet& ps, Wave& w, cudaStream_t st, Dims* scratch_dims, const int p_os,
@@ -345,6 +347,48 @@ static int tune_wave(tebd_s* h, const ParitySet& ps, Wave& w, cudaStream_t st, D
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
+// Coordinate search over the mixed form's launch choices (MixedKnobs): one
+// knob at a time, each candidate timed once on the current best of the
+// others; `run` launches the whole RRSVD with the given knobs on `st`.
+// Returns the timings of the size rules and of the choice kept.
+template <class Run>
+static int tune_knobs(Run run, cudaStream_t st, const Caps& cap, int batch, MixedKnobs& best, float ms_out[2]) {
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  auto time_of = [&](const MixedKnobs& k, float& ms) -> bool {
+    cudaEventRecord(e0, st);
+    if (run(k) != cudaSuccess) return false;
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess) return false;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return true;
+  };
+  best = MixedKnobs{0, 0, 0, 0};
+  float t_best = 0.f, t_rule = 0.f;
+  bool ok = run(best) == cudaSuccess && time_of(best, t_best);  // warm-up, then the size rules
+  t_rule = t_best;
+  const bool multi_ok = cap.n >= 1024 && cap.l >= 16;  // the many-CTA QR's structure (its own rule adds the batch)
+  const bool cl_ok = cap.l >= 64 && cap.l <= 512;
+  std::vector<std::vector<int>> cand = {{0, 1}, {0, 512, 256, 128}, {0, 1, 2}, {0, 1, 2}};
+  for (int knob = 0; knob < 4 && ok; ++knob)
+    for (int v : cand[knob]) {
+      MixedKnobs k = best;
+      int* f = knob == 0 ? &k.tc_half : knob == 1 ? &k.qr_threads : knob == 2 ? &k.qrbh : &k.jac;
+      if (*f == v || (knob == 2 && v == 2 && !multi_ok) || (knob == 3 && v == 2 && !cl_ok)) continue;
+      *f = v;
+      float t = 0.f;
+      if (!time_of(k, t)) { ok = false; break; }
+      if (t < 0.97f * t_best) { best = k; t_best = t; }  // a clear gain only
+    }
+  (void)batch;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ms_out[0] = t_rule;
+  ms_out[1] = t_best;
+  return ok && cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 static int tebd_reset_state(tebd_t h, int slot, const double* psi);
 
 
@@ -357,7 +401,6 @@ static int plan_handle(tebd_s* h, int n_chains, const tebd_desc_t* descs, Handle
   const tebd_desc_t& d0 = descs[0];
   if (d0.p < 0 || d0.q < 0) return TEBD_EINVAL;
   if (d0.precision != TEBD_PREC_FP64 && d0.precision != TEBD_PREC_TF32) return TEBD_ENOTIMPL;
-  if (d0.precision == TEBD_PREC_TF32 && d0.autotune) return TEBD_EINVAL;  // the tile autotuner is for FP64 GEMMs
   if ((d0.alloc == nullptr) != (d0.release == nullptr)) return TEBD_EINVAL;
   if (d0.fused < -1 || d0.fused > 1) return TEBD_EINVAL;
   for (int c = 0; c < n_chains; ++c) {
@@ -688,12 +731,55 @@ extern "C" int tebd_create_multi(int n_chains, const tebd_desc_t* descs, tebd_t*
   if (d0.fused == 1 && h->precision == TEBD_PREC_FP64)
     for (int par = 0; par < 2; ++par)
       for (Wave& w : h->par[par].waves) w.fused = fused_fits(w.cap) ? 1 : 0;
-  if (d0.autotune) {
+  if (d0.autotune && h->precision == TEBD_PREC_FP64) {
     Dims* scratch = (Dims*)(h->arena + h->plan.desc_off + 2 * h->plan.desc_per);
     for (int par = 0; par < 2; ++par)
       for (Wave& w : h->par[par].waves)
         if (tune_wave(h, h->par[par], w, h->stream, scratch, h->p, d0.fused) != 0) { tebd_free(h); return TEBD_ECUDA; }
     if (cudaDeviceSynchronize() != cudaSuccess) { tebd_free(h); return TEBD_ECUDA; }
+  }
+  if (d0.autotune && h->precision == TEBD_PREC_TF32) {
+    // the mixed form's launch choices, timed on synthetic theta at each
+    // wave's capacity sizes (cached per wave shape for the process)
+    Dims* scratch = (Dims*)(h->arena + h->plan.desc_off + 2 * h->plan.desc_per);
+    for (int par = 0; par < 2; ++par)
+      for (Wave& w : h->par[par].waves) {
+        const ParitySet& ps = h->par[par];
+        std::vector<long long> key = {100, w.cap.m, w.cap.n, w.cap.l, w.cap.k, w.count, h->q};
+        {
+          std::lock_guard<std::mutex> g(g_tile_mu);
+          auto it = g_knob_cache.find(key);
+          if (it != g_knob_cache.end()) { w.mk = it->second.first; w.tune_ms[0] = it->second.second[0]; w.tune_ms[1] = it->second.second[1]; continue; }
+        }
+        std::vector<Dims> hd(w.count);
+        std::vector<ProbPtr> hp(w.count);
+        bool ok = cudaMemcpy(hp.data(), ps.ptrs + w.first, sizeof(ProbPtr) * w.count, cudaMemcpyDeviceToHost) == cudaSuccess;
+        for (int i = 0; i < w.count && ok; ++i) {
+          Dims& D = hd[i];
+          memset(&D, 0, sizeof D);
+          D.dl = hp[i].dl_s; D.dr = hp[i].dr_s;
+          D.cl = hp[i].cap_l; D.cm = hp[i].cap_m; D.cr = hp[i].cap_r;
+          D.m = D.dl * D.cl; D.n = D.dr * D.cr;
+          D.k = std::min(hp[i].chicap, std::min(D.m, D.n));
+          D.l = std::min(D.k + h->p, std::min(D.m, D.n));
+          D.active = 1;
+        }
+        ok = ok && cudaMemcpy(scratch, hd.data(), sizeof(Dims) * w.count, cudaMemcpyHostToDevice) == cudaSuccess &&
+             launch_tune_theta(scratch, ps.ptrs + w.first, w.count, h->stream) == cudaSuccess;
+        const MixedPtrs mp = mixed_carve(h->mixed, w.ms, w.count);
+        auto run = [&](const MixedKnobs& k) {
+          return run_rrsvd_mixed(scratch, ps.ptrs + w.first, w.count, w.cap, mp, h->q, h->seed, 0, 0, -1, h->status,
+                                 h->tcerr, h->stream, h->sweep_dev, &k);
+        };
+        float ms[2] = {0.f, 0.f};
+        if (!ok || tune_knobs(run, h->stream, w.cap, w.count, w.mk, ms) != 0) { tebd_free(h); return TEBD_ECUDA; }
+        w.tune_ms[0] = ms[0];
+        w.tune_ms[1] = ms[1];
+        std::lock_guard<std::mutex> g(g_tile_mu);
+        g_knob_cache[key] = {w.mk, {ms[0], ms[1]}};
+      }
+    if (cudaMemset(h->status, 0, sizeof(int)) != cudaSuccess || cudaMemset(h->tcerr, 0, sizeof(int)) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess) { tebd_free(h); return TEBD_ECUDA; }
   }
   *out = h;
   return TEBD_OK;
@@ -992,7 +1078,7 @@ static cudaError_t enqueue_sweep(tebd_t h, int parity) {
     if (h->precision == TEBD_PREC_TF32) {
       const MixedPtrs mp = mixed_carve(h->mixed, w.ms, w.count);
       if ((e = run_rrsvd_mixed(dims, ptrs, w.count, w.cap, mp, h->q, h->seed, 0, 0, -1, h->status, h->tcerr,
-                               h->stream, h->sweep_dev)) != cudaSuccess)
+                               h->stream, h->sweep_dev, &w.mk)) != cudaSuccess)
         return e;
     } else if ((e = run_rrsvd(dims, ptrs, w.count, w.cap, h->q, h->seed, 0, 0, -1, h->status, h->stream,
                               h->sweep_dev, tuned ? w.tiles : nullptr)) != cudaSuccess) {
@@ -1126,6 +1212,7 @@ extern "C" int tebd_wave_info(tebd_t h, int parity, int wave, int* info, double*
     info[1] = w.cap.m; info[2] = w.cap.n; info[3] = w.cap.k; info[4] = w.cap.l;
     info[5] = w.fused;
     for (int i = 0; i < 6; ++i) info[6 + i] = w.tiles[i];
+    info[12] = w.mk.tc_half; info[13] = w.mk.qr_threads; info[14] = w.mk.qrbh; info[15] = w.mk.jac;
   }
   if (ms) {
     ms[0] = w.tune_ms[0];
@@ -1395,6 +1482,11 @@ struct rrsvd_plan_s {
   // host-path staging (allocated on first use)
   char* stage = nullptr;
   size_t stage_bytes = 0;
+  // autotuner choices (rrsvd_plan_autotune): FP64 GEMM tiles, mixed-form knobs
+  int tiles[6] = {0, 0, 0, 0, 0, 0};
+  MixedKnobs mk{0, 0, 0, 0};
+  float tune_ms[2] = {0.f, 0.f};
+  int tuned = 0;
 };
 
 namespace tg {
@@ -1548,9 +1640,10 @@ extern "C" int rrsvd_execute(rrsvd_plan_t P, const double* theta, int64_t chain0
   if (P->precision == TEBD_PREC_TF32) {
     const MixedPtrs mp = mixed_carve((char*)workspace + P->mixed_off, P->ms, P->batch);
     CU_OR(P, run_rrsvd_mixed(P->dims, P->ptrs, P->batch, P->cap, mp, P->q, P->seed, 0, chain0, 1, P->status,
-                             P->tcerr, st));
+                             P->tcerr, st, nullptr, &P->mk));
   } else {
-    CU_OR(P, run_rrsvd(P->dims, P->ptrs, P->batch, P->cap, P->q, P->seed, 0, chain0, 1, P->status, st));
+    CU_OR(P, run_rrsvd(P->dims, P->ptrs, P->batch, P->cap, P->q, P->seed, 0, chain0, 1, P->status, st, nullptr,
+                       P->tuned ? P->tiles : nullptr));
   }
   CU_OR(P, launch_rrsvd_finalize(P->dims, P->ptrs, P->batch, P->cap, 1e-14, sigma, Vh, w, rank, P->status, st));
   return TEBD_OK;
@@ -1614,6 +1707,79 @@ extern "C" int rrsvd_execute_host(rrsvd_plan_t P, const double* theta, int64_t c
 }
 
 extern "C" const char* rrsvd_last_error(rrsvd_plan_t P) { return P ? P->err.msg.c_str() : "NULL plan"; }
+
+extern "C" int rrsvd_plan_autotune(rrsvd_plan_t P, const double* theta, void* workspace, size_t workspace_bytes,
+                                   void* stream) {
+  if (!P) return TEBD_EINVAL;
+  if (P->err.code) return P->err.code;
+  if (!theta || !workspace) { P->err.set(TEBD_EINVAL, "NULL theta or workspace"); return P->err.code; }
+  if (workspace_bytes < P->ws_bytes || ((uintptr_t)workspace) % ALIGN) {
+    P->err.set(TEBD_EINVAL, "workspace too small or not 256-byte aligned");
+    return P->err.code;
+  }
+  if (P->check_r > 0) return TEBD_OK;  // the accuracy-check sequence has no launch choices to tune
+  cudaStream_t st = (cudaStream_t)stream;
+  k_rrsvd_bind<<<(P->batch + 127) / 128, 128, 0, st>>>(P->ptrs, P->batch, (char*)workspace, P->per, P->lay,
+                                                     (const cplx*)theta, (size_t)P->m * P->n, nullptr, 0, nullptr, 0,
+                                                     nullptr, 0, 0, 0, 0, nullptr);
+  CU_OR(P, cudaGetLastError());
+  if (P->precision == TEBD_PREC_TF32) {
+    const MixedPtrs mp = mixed_carve((char*)workspace + P->mixed_off, P->ms, P->batch);
+    auto run = [&](const MixedKnobs& k) {
+      return run_rrsvd_mixed(P->dims, P->ptrs, P->batch, P->cap, mp, P->q, P->seed, 0, 0, 1, P->status, P->tcerr, st,
+                             nullptr, &k);
+    };
+    float ms[2] = {0.f, 0.f};
+    if (tune_knobs(run, st, P->cap, P->batch, P->mk, ms) != 0) {
+      P->err.set(TEBD_ECUDA, "autotuning failed: %s", cudaGetErrorString(cudaGetLastError()));
+      return P->err.code;
+    }
+    P->tune_ms[0] = ms[0];
+    P->tune_ms[1] = ms[1];
+  } else {
+    // GEMM tiles of every stage: the kernels alone (their time does not depend
+    // on the data), after one whole RRSVD that fills every operand
+    CU_OR(P, run_rrsvd(P->dims, P->ptrs, P->batch, P->cap, P->q, P->seed, 0, 0, 1, P->status, st));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int stage = 0; stage < 6; ++stage) {
+      float best = 1e30f;
+      for (int tile : {16, 32}) {
+        launch_zgemm_tile(stage, tile, P->dims, P->ptrs, P->batch, P->cap, st);
+        cudaEventRecord(e0, st);
+        launch_zgemm_tile(stage, tile, P->dims, P->ptrs, P->batch, P->cap, st);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (t < best) { best = t; P->tiles[stage] = tile; }
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  P->tuned = 1;
+  // the timing runs raise no flag the next execute should see
+  CU_OR(P, cudaMemsetAsync(P->status, 0, 2 * ALIGN, st));
+  CU_OR(P, cudaStreamSynchronize(st));
+  return TEBD_OK;
+}
+
+extern "C" int rrsvd_plan_tuning(rrsvd_plan_t P, int* info, double* ms) {
+  if (!P) return TEBD_EINVAL;
+  if (info) {
+    memset(info, 0, sizeof(int) * 16);
+    for (int i = 0; i < 6; ++i) info[i] = P->tiles[i];
+    info[6] = P->mk.tc_half; info[7] = P->mk.qr_threads; info[8] = P->mk.qrbh; info[9] = P->mk.jac;
+    info[10] = P->tuned;
+  }
+  if (ms) {
+    ms[0] = P->tune_ms[0];
+    ms[1] = P->tune_ms[1];
+  }
+  return TEBD_OK;
+}
 
 extern "C" int rrsvd_clear_error(rrsvd_plan_t P) {
   if (!P) return TEBD_EINVAL;

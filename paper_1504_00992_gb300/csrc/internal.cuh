@@ -97,15 +97,18 @@ cudaError_t launch_qr(int stage, const Dims* dims, const ProbPtr* ptrs, int batc
 // is a few tall matrices (cap.m or cap.n rows, cap.l columns); every
 // instance's R and J buffers must hold at least qr_multi_scratch_r(l) and
 // qr_multi_scratch_j(l) complex words for its own l
+// force: 0 the size rule, 1 the one-CTA kernel, 2 the many-CTA form wherever
+// its structure allows (the autotuner's choices)
 cudaError_t launch_qr_sized(int stage, const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap,
-                           cudaStream_t st);
+                           cudaStream_t st, int force = 0);
 size_t qr_multi_scratch_r(int l);
 size_t qr_multi_scratch_j(int l);
 cudaError_t launch_jacobi(const Dims* dims, const ProbPtr* ptrs, int batch, int* status, cudaStream_t st);
 // the same, each instance on a cluster of CTAs (jacobi_cluster.cu) when the
 // batch is a few instances with cap.l >= 64
+// force: 0 the size rule, 1 one CTA per matrix, 2 the cluster form wherever l allows
 cudaError_t launch_jacobi_sized(const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, int* status,
-                                cudaStream_t st);
+                                cudaStream_t st, int force = 0);
 cudaError_t launch_frob2(const Dims* dims, const ProbPtr* ptrs, int batch, cudaStream_t st);
 // identity_gate = 1 writes the pre-gate theta (reverse pass).  Otherwise a
 // bond with ptrs[p].Cpre set gets its pre-gate theta written there, and

@@ -188,8 +188,10 @@ __global__ void __cluster_dims__(JC_CL, 1, 1) __launch_bounds__(JC_THREADS)
 }
 
 cudaError_t launch_jacobi_sized(const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, int* status,
-                                cudaStream_t st) {
-  if (cap.l < JC_MIN_L || cap.l > JC_MAXL || batch > JC_MAX_BATCH) return launch_jacobi(dims, ptrs, batch, status, st);
+                                cudaStream_t st, int force) {
+  const bool fits = cap.l >= JC_MIN_L && cap.l <= JC_MAXL;
+  const bool cl = force == 2 ? fits : (force == 0 && fits && batch <= JC_MAX_BATCH);
+  if (!cl) return launch_jacobi(dims, ptrs, batch, status, st);
   ProfScope ps("k_jacobi[cluster]", st);
   k_jacobi_cl<<<batch * JC_CL, JC_THREADS, 0, st>>>(dims, ptrs, status);
   return cudaGetLastError();

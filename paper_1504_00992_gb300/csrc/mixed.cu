@@ -471,8 +471,11 @@ static int grid1d(int64_t total) {
 // One tensor-core product: out (rows x l complex, per instance) from
 // A (rows x Kp) and Bt (Np x Kp); npass 1 or 3.
 static cudaError_t tc_product(const float* A0, const float* A1, const float* B0, const float* B1, int rows, int Kp,
-                              const MixedSizes& s, int l, int npass, float2* out, int batch, int* err,
-                              cudaStream_t st) {
+                              const MixedSizes& s0, int l, int npass, float2* out, int batch, int* err,
+                              cudaStream_t st, int half) {
+  // half: the columns of the product split over two CTAs (tile width rounded to 16)
+  MixedSizes s = s0;
+  if (half && s.BN > 16) s.BN = ((s.BN / 2 + 15) / 16) * 16;
   CUtensorMap ma0, ma1, mb0, mb1;
   if (!make_map(&ma0, A0, Kp, rows, batch, TC_BM) || !make_map(&ma1, A1, Kp, rows, batch, TC_BM) ||
       !make_map(&mb0, B0, Kp, s.Np, batch, s.BN) || !make_map(&mb1, B1, Kp, s.Np, batch, s.BN))
@@ -506,11 +509,11 @@ static cudaError_t tc_product(const float* A0, const float* A1, const float* B0,
 }
 
 static cudaError_t qr_f32(float2* A, float2* Q, int M, int L, int batch, const MixedPtrs& mp, const MixedSizes& s,
-                          const Dims* dims, int use_n, cudaStream_t st) {
+                          const Dims* dims, int use_n, cudaStream_t st, int threads) {
   if (!qr_blk_f32_fits(M, L) && mp.qscr && qr_multi_f32_fits(M, L))
     return launch_qr_multi_f32(A, Q, mp.qscr, s.qs / sizeof(float2), M, L, batch, st, dims, use_n);
   ProfScope ps("k_qr_f32", st);
-  if (qr_blk_f32_fits(M, L)) return launch_qr_blk_f32(A, Q, M, L, batch, st, dims, use_n);
+  if (qr_blk_f32_fits(M, L)) return launch_qr_blk_f32(A, Q, M, L, batch, st, dims, use_n, threads);
   k_qr_f32<<<batch, 1024, 0, st>>>(A, Q, M, L);
   return cudaGetLastError();
 }
@@ -536,7 +539,8 @@ cudaError_t mixed_prepare(const Caps& cap) {
 
 cudaError_t run_rrsvd_mixed(const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, const MixedPtrs& mp,
                             int q, uint64_t seed, uint64_t sweep, int64_t chain0, int chain_stride, int* status,
-                            int* err, cudaStream_t st, const uint64_t* sweep_dev) {
+                            int* err, cudaStream_t st, const uint64_t* sweep_dev, const MixedKnobs* knobs) {
+  const MixedKnobs kn = knobs ? *knobs : MixedKnobs{0, 0, 0, 0};
   // capacities: every FP32 array is laid out at these sizes, zero-padded past
   // each instance's own (m, n, l) from dims
   const int m = cap.m, n = cap.n, k = cap.k, l = cap.l;
@@ -559,25 +563,27 @@ cudaError_t run_rrsvd_mixed(const Dims* dims, const ProbPtr* ptrs, int batch, co
   }
   // Y0 = A Omega: TF32, or the refinement pass when q == 0
   const int p0 = (q == 0) ? 3 : 1;
-  MX_TRY(tc_product(mp.thf_hi, mp.thf_lo, mp.bt_hi, mp.bt_lo, m, s.K1, s, l, p0, mp.Yf, batch, err, st));
+  MX_TRY(tc_product(mp.thf_hi, mp.thf_lo, mp.bt_hi, mp.bt_lo, m, s.K1, s, l, p0, mp.Yf, batch, err, st, kn.tc_half));
   for (int j = 1; j <= q; ++j) {
     const int np = (j == q) ? 3 : 1;
-    MX_TRY(qr_f32(mp.Yf, mp.Qf, m, l, batch, mp, s, dims, 0, st));    // Y = Q R
+    MX_TRY(qr_f32(mp.Yf, mp.Qf, m, l, batch, mp, s, dims, 0, st, kn.qr_threads));    // Y = Q R
     MX_TRY(conv_bt(mp.Qf, dims, mp, m, l, s.K2, s, np == 3, batch, st));
-    MX_TRY(tc_product(mp.tha_hi, mp.tha_lo, mp.bt_hi, mp.bt_lo, n, s.K2, s, l, np, mp.Ytf, batch, err, st));  // A^H Q
-    MX_TRY(qr_f32(mp.Ytf, mp.Qtf, n, l, batch, mp, s, dims, 1, st));  // = Q~ R~
+    MX_TRY(tc_product(mp.tha_hi, mp.tha_lo, mp.bt_hi, mp.bt_lo, n, s.K2, s, l, np, mp.Ytf, batch, err, st,
+                      kn.tc_half));  // A^H Q
+    MX_TRY(qr_f32(mp.Ytf, mp.Qtf, n, l, batch, mp, s, dims, 1, st, kn.qr_threads));  // = Q~ R~
     MX_TRY(conv_bt(mp.Qtf, dims, mp, n, l, s.K1, s, np == 3, batch, st));
-    MX_TRY(tc_product(mp.thf_hi, mp.thf_lo, mp.bt_hi, mp.bt_lo, m, s.K1, s, l, np, mp.Yf, batch, err, st));  // A Q~
+    MX_TRY(tc_product(mp.thf_hi, mp.thf_lo, mp.bt_hi, mp.bt_lo, m, s.K1, s, l, np, mp.Yf, batch, err, st,
+                      kn.tc_half));  // A Q~
   }
   // last QR: FP32 Householder, then the FP64-accurate re-orthonormalisation.
   // Plans and handles refuse sketches wider than 512 columns, and l <= m, so
   // every basis they pass fits it.
   if (!reorth_fits(m, l)) return cudaErrorInvalidValue;
-  MX_TRY(qr_f32(mp.Yf, mp.Qf, m, l, batch, mp, s, dims, 0, st));
+  MX_TRY(qr_f32(mp.Yf, mp.Qf, m, l, batch, mp, s, dims, 0, st, kn.qr_threads));
   MX_TRY(launch_reorth(mp.Qf, mp.Df, dims, ptrs, m, l, batch, status, st));
   MX_TRY(launch_proj_oz(dims, ptrs, mp.Qf, mp.Df, mp.ad, mp.asc, mp.bd, mp.bsc, m, n, l, batch, err, st));  // B^H = A^H Q
-  MX_TRY(launch_qr_sized(QR_BH, dims, ptrs, batch, cap, st));
-  MX_TRY(launch_jacobi_sized(dims, ptrs, batch, cap, status, st));
+  MX_TRY(launch_qr_sized(QR_BH, dims, ptrs, batch, cap, st, kn.qrbh));
+  MX_TRY(launch_jacobi_sized(dims, ptrs, batch, cap, status, st, kn.jac));
   MX_TRY(launch_zgemm_df(G_U, dims, ptrs, batch, cap, st));
   MX_TRY(launch_zgemm_df(G_V, dims, ptrs, batch, cap, st));
   return cudaSuccess;

@@ -50,8 +50,10 @@ MixedPtrs mixed_carve(char* base, const MixedSizes& s, int batch);
 // dims, each instance factors only its own rows (D.n if use_n, else D.m) and
 // D.l columns of the zero-padded M x L layout.
 bool qr_blk_f32_fits(int M, int L);
+// threads: 0 picks the CTA size by batch; 128, 256 or 512 force it (when its
+// shared memory fits)
 cudaError_t launch_qr_blk_f32(float2* A, float2* Q, int M, int L, int batch, cudaStream_t st,
-                              const Dims* dims = nullptr, int use_n = 0);
+                              const Dims* dims = nullptr, int use_n = 0, int threads = 0);
 // The same QR spread over many CTAs per instance (qr_multi.cu), for matrices
 // too tall for the blocked kernel's shared memory; scr holds
 // qr_multi_f32_scratch(M, L) float2 per instance at the given stride; with
@@ -86,6 +88,15 @@ cudaError_t launch_proj_oz(const Dims* dims, const ProbPtr* ptrs, const float2* 
                            uint16_t* Ad, float* As, const uint16_t* Bd, const float* Bs, int m, int n, int l, int batch,
                            int* err, cudaStream_t st);
 
+// Launch choices of the mixed form that the autotuner may override (0 keeps
+// each size rule): tc_half = 1 splits the tensor-core products' columns over
+// two CTAs; qr_threads sets the CTA size of the blocked FP32 QRs (128, 256,
+// 512); qrbh and jac force the QR of B^H and the Jacobi SVD as in
+// launch_qr_sized / launch_jacobi_sized.
+struct MixedKnobs {
+  int tc_half, qr_threads, qrbh, jac;
+};
+
 // Everything that must happen outside a stream capture before
 // run_rrsvd_mixed runs on capacities `cap` (shared-memory limits, the
 // tensor-map encoder entry point).
@@ -100,6 +111,7 @@ cudaError_t qr_blocked_prepare(int M, int N, int L);
 // chain_stride < 0, from its own chain index at *sweep_dev.
 cudaError_t run_rrsvd_mixed(const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, const MixedPtrs& mp,
                             int q, uint64_t seed, uint64_t sweep, int64_t chain0, int chain_stride, int* status,
-                            int* err, cudaStream_t st, const uint64_t* sweep_dev = nullptr);
+                            int* err, cudaStream_t st, const uint64_t* sweep_dev = nullptr,
+                            const MixedKnobs* knobs = nullptr);
 
 }  // namespace tg

@@ -469,15 +469,17 @@ static size_t g_attr_qr = 0, g_attr_qr256 = 0, g_attr_ld = 0, g_attr_fold[2][2] 
 static size_t g_attr_qr128 = 0;
 
 cudaError_t launch_qr_blk_f32(float2* A, float2* Q, int M, int L, int batch, cudaStream_t st, const Dims* dims,
-                              int use_n) {
-  if (batch >= 4 * 152 && qb_smem_bytes(M, L, 4) <= 56 * 1024) {
+                              int use_n, int threads) {
+  const bool t128 = threads == 128 || (threads == 0 && batch >= 4 * 152);
+  const bool t256 = threads == 256 || (threads == 0 && batch >= 2 * 152);
+  if (t128 && qb_smem_bytes(M, L, 4) <= 56 * 1024) {
     const size_t sm = qb_smem_bytes(M, L, 4);
     cudaError_t e = ensure_smem(k_qr_blk_f32<128>, sm, &g_attr_qr128);
     if (e != cudaSuccess) return e;
     k_qr_blk_f32<128><<<batch, 128, sm, st>>>(A, Q, M, L, dims, use_n);
     return cudaGetLastError();
   }
-  if (batch >= 2 * 152 && qb_smem_bytes(M, L, 8) <= 112 * 1024) {
+  if ((t128 || t256) && qb_smem_bytes(M, L, 8) <= 112 * 1024) {
     const size_t sm = qb_smem_bytes(M, L, 8);
     cudaError_t e = ensure_smem(k_qr_blk_f32<256>, sm, &g_attr_qr256);
     if (e != cudaSuccess) return e;

@@ -581,9 +581,10 @@ static bool qr_multi_fits(int M, int L, int batch) {
 }
 
 cudaError_t launch_qr_sized(int stage, const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap,
-                            cudaStream_t st) {
+                            cudaStream_t st, int force) {
   const int M = (stage == QR_Y) ? cap.m : cap.n;
-  if (!qr_multi_fits(M, cap.l, batch)) return launch_qr(stage, dims, ptrs, batch, st);
+  const bool multi = force == 2 ? qr_multi_fits(M, cap.l, 1) : (force == 0 && qr_multi_fits(M, cap.l, batch));
+  if (!multi) return launch_qr(stage, dims, ptrs, batch, st);
   ProfScope ps("k_qr[multi]", st);
   cudaError_t e;
   switch (stage) {

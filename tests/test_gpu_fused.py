@@ -106,8 +106,9 @@ def test_autotuner_times_both_launches(lib):
     table = sim.tuning_table()
     for par in (0, 1):
         for w in table[par]:
-            assert w["tune_ms"]["staged"] > 0 and w["tune_ms"]["fused"] > 0
-            assert w["fused"] == (1 if w["tune_ms"]["fused"] < w["tune_ms"]["staged"] else 0)
+            staged, fused = w["tune_ms"]
+            assert staged > 0 and fused > 0
+            assert w["fused"] == (1 if fused < staged else 0)
             assert all(t in (16, 32) for t in w["tiles"])
     sim.set_product_state(I.neel_state(20, 2))
     sim.set_gates(0, I.trotter_gates(hs, 0.005))
