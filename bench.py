@@ -209,8 +209,12 @@ def run_tebd_c1(B, I, torch):
     N, d = 20, 2
     hs = I.xxz_bond_terms(N, d, 1.0, 0.5)
 
+    tuning = []
+
     def run(use_graph):
-        sim = B.Tebd(N, d, 32, 10, 2, 0, stream=torch.cuda.current_stream().cuda_stream, use_graph=use_graph)
+        sim = B.Tebd(N, d, 32, 10, 2, 0, stream=torch.cuda.current_stream().cuda_stream, use_graph=use_graph,
+                     autotune=1)
+        tuning.append(sim.tuning_table())
         sim.set_product_state(I.neel_state(N, d))
         sim.set_gates(0, I.trotter_gates(hs, 0.005))
         sim.set_gates(1, I.trotter_gates(hs, 0.01))
@@ -231,7 +235,9 @@ def run_tebd_c1(B, I, torch):
             "workload": "XXZ chain N=20 d=2 J=1 Delta=0.5 dt=0.01, 100 second-order steps, chi_max=32 "
                         "(theta 64x64), p=10, q=2, Neel, seed 0; whole update theta+gate+RRSVD+rebuild; "
                         "the first sweeps capture the graphs inside the timed region",
-            "discarded_weight": ws_g, "discarded_weight_no_graph": ws}
+            "discarded_weight": ws_g, "discarded_weight_no_graph": ws,
+            "tuning": [{"parity": par, "bonds": w["bonds"], "m": w["m"], "l": w["l"], "fused": w["fused"],
+                        "tiles": w["tiles"], "tune_ms": w["tune_ms"]} for par in (0, 1) for w in tuning[0][par]]}
 
 
 def measure(B, torch, dev, theta, sig, batch, prec, args, rank, world, local):
@@ -254,6 +260,10 @@ def measure(B, torch, dev, theta, sig, batch, prec, args, rank, world, local):
     def step(s):
         B.rrsvd_execute(plan, theta.data_ptr(), inst0 + s * batch, sg.data_ptr(), U.data_ptr(), Vh.data_ptr(),
                         w.data_ptr(), rk.data_ptr(), wsp, wsb, sp)
+
+    # the plan's launch choices, timed on this workload before the warm-up
+    B.rrsvd_plan_autotune(plan, theta.data_ptr(), wsp, wsb, sp)
+    tuning = B.rrsvd_plan_tuning(plan)
 
     def barrier():
         if world > 1:
@@ -291,7 +301,7 @@ def measure(B, torch, dev, theta, sig, batch, prec, args, rank, world, local):
     del ws, U, Vh
     torch.cuda.empty_cache()
     return {"prec": prec, "code": code, "value": whole_job_rate(args.steps * batch, world, ms / 1e3), "ms": ms,
-            "prof": prof,
+            "prof": prof, "tuning": tuning,
             "clocks": clocks, "sig_err": sig_err, "excess_err": float(excess), "k": k, "l": l}
 
 
@@ -350,6 +360,21 @@ def _src_hash(name):
     return hashlib.sha256(src).hexdigest()[:16]
 
 
+# The tensor-core projection forms each complex multiply-add of C = Q_f^H A
+# from 15 pairs of BF16 digits x 4 real products: 120 BF16 flop per 8
+# FP64-equivalent flop, so its FP64-equivalent ceiling is the measured BF16
+# rate x 8 / 120.
+OZ_BF16_FLOP_PER_CMAC = 15 * 4 * 2
+
+
+def measured_peaks():
+    """The driver's measured GB300 peaks (HBM GB/s, dense BF16 TFLOP/s)."""
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
 def roofline(res, batch):
     """Roofline object of the dominant kernel class of one measured form:
     algorithmic flops of one launch (per instance x batch) over its mean
@@ -365,11 +390,22 @@ def roofline(res, batch):
     df_src = ("FP32 issue rate 152 SMs x 128 lanes x 2.07 GHz / %d FP32 instructions per double-float complex "
               "multiply-add x 8 flop (derived)" % DF_OPS_PER_CMAC)
     # kernel -> (algorithmic flops per launch, bound, peak, peak source, file holding the kernel)
+    pk = measured_peaks()
+    bf16 = pk.get("bf16_tflops_sustained") or 1700.0
+    oz_peak = bf16 * 8.0 / OZ_BF16_FLOP_PER_CMAC
+    oz_src = ("measured sustained BF16 %.0f TFLOP/s (MEASURED_PEAKS.json) x 8 FP64-equivalent flop / %d BF16 flop "
+              "per complex multiply-add of the digit products" % (bf16, OZ_BF16_FLOP_PER_CMAC))
+    # per launch: (algorithmic flops, bound, peak, peak source, file, flops
+    # counted in the kernel's own unit when it differs from the algorithmic
+    # FP64-equivalent figure)
     per_launch = {
         "k_zgemm[sketch]": (8.0 * M * N_ * l * batch, "alu", fp64_peak, fp64_src, "kernels.cu"),
-        "k_qr": ((16.0 * M * l * l - 16.0 * l ** 3 / 3) * batch, "alu", fp64_peak, fp64_src, "kernels.cu"),
+        # the QR of B^H (n x l) of the mixed form, R and Q
+        "k_qr": ((16.0 * N_ * l * l - 16.0 * l ** 3 / 3) * batch, "alu", fp64_peak, fp64_src, "stages.cuh"),
+        "k_jacobi": (60.0 * l ** 3 * batch, "alu", fp64_peak, fp64_src, "stages.cuh"),
         "k_zgemm[uv]": (8.0 * M * l * k * batch, "alu", fp64_peak, fp64_src, "kernels.cu"),
         "k_zgemm_df[project]": (8.0 * M * N_ * l * batch, "alu", df_peak, df_src, "df_proj.cu"),
+        "k_oz_proj[project]": (8.0 * M * N_ * l * batch, "tensor", oz_peak, oz_src, "oz_proj.cu"),
     }
     if dom not in per_launch:
         return None
@@ -382,8 +418,16 @@ def roofline(res, batch):
         rec = json.load(open(tp)).get(dom)
         if rec and rec.get("src_sha256_16") == _src_hash(srcfile):
             traffic = rec["dram_bytes_per_instance"] * batch   # counters taken on this exact kernel source
-    return {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": traffic, "peak_source": psrc}
+    out = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+           "frac": achieved / peak, "traffic": traffic, "peak_source": psrc}
+    # every kernel class of the step against its own ceiling (same units)
+    out["by_kernel"] = {}
+    for kk, (flk, bd, pkk, _, _) in per_launch.items():
+        if kk in prof and prof[kk][1] > 0:
+            a = flk / (prof[kk][0] / prof[kk][1] / 1e3) / 1e12
+            out["by_kernel"][kk] = {"bound": bd, "achieved": a, "peak": pkk, "frac": a / pkk,
+                                    "ms_per_step": prof[kk][0] / max(1, prof[kk][1]) * prof[kk][1]}
+    return out
 
 
 def run_rrsvd_checked(B, torch, dev, theta, sig, batch, steps=2, warm=1):
@@ -450,10 +494,11 @@ def run_tebd_many(B, I, torch, n_chains=256, steps=10, warm=2, unbatched_chains=
         return steps_ * sum(2 * ((N - 1 + 1) // 2) + (N - 1) // 2 for N, _, _, _ in subset)
 
     chains = [(N, [d] * N, [chi] * (N - 1)) for N, d, chi, _ in specs]
+    tables = {}
 
     def batched(prec):
-        kw = {"autotune": 1} if prec == B.TEBD_PREC_FP64 else {}
-        sim = B.MultiTebd(chains, p, q, 0, use_graph=1, workspace_budget=16 << 30, precision=prec, **kw)
+        sim = B.MultiTebd(chains, p, q, 0, use_graph=1, workspace_budget=16 << 30, precision=prec, autotune=1)
+        tables[prec] = sim.tuning_table()
         setup(sim.set_product_state, sim.set_gates, specs)
         for _ in range(warm):
             sim.step_even(); sim.step_odd(); sim.step_even()
@@ -500,6 +545,12 @@ def run_tebd_many(B, I, torch, n_chains=256, steps=10, warm=2, unbatched_chains=
             "chain0_max_abs_sz_diff_mixed_vs_fp64": float(np.abs(probe_m - probe_d).max()),
             "unbatched_fp64_value": unbatched, "unbatched_chains": unbatched_chains,
             "speedup_fp64_batched_vs_unbatched": fp64 / unbatched,
+            "tuning": {"tf32": [{"parity": par, "bonds": w["bonds"], "m": w["m"], "n": w["n"], "l": w["l"],
+                                 "mixed": w["mixed"], "tune_ms": w["tune_ms"]}
+                                for par in (0, 1) for w in tables[B.TEBD_PREC_TF32][par]],
+                       "fp64": [{"parity": par, "bonds": w["bonds"], "m": w["m"], "n": w["n"], "l": w["l"],
+                                 "fused": w["fused"], "tiles": w["tiles"], "tune_ms": w["tune_ms"]}
+                                for par in (0, 1) for w in tables[B.TEBD_PREC_FP64][par]]},
             "workload": "256 XXZ chains, N~U{16..128}, d in {2,3,4}, chi_max in {32,64,128}, Delta~U[0,1], "
                         "dt=0.01, p=10, q=1, Neel; graphs + 16 GB wave budget, after %d warm-up steps" % warm}
 
@@ -647,7 +698,8 @@ def main():
                          f"OPENBLAS_NUM_THREADS={os.environ['OPENBLAS_NUM_THREADS']}, nproc={os.cpu_count()})"}
     if rank == 0:
         forms = {p: {"value": r["value"], "ms_per_step": r["ms"] / args.steps,
-                     "max_abs_sigma_err_vs_exact": r["sig_err"], "excess_frobenius_err": r["excess_err"]}
+                     "max_abs_sigma_err_vs_exact": r["sig_err"], "excess_frobenius_err": r["excess_err"],
+                     "tuning": r["tuning"]}
                  for p, r in results.items()}
         line = {"metric": METRIC, "value": head["value"], "unit": "bond updates/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms"] / args.steps,
