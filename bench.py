@@ -474,19 +474,55 @@ def run_rrsvd_checked(B, torch, dev, theta, sig, batch, steps=2, warm=1):
                         "eps=1e-3, l_max=200, q=2, FP64, %d instances per step" % batch}
 
 
-def run_tebd_many(B, I, torch, n_chains=256, steps=10, warm=2, unbatched_chains=16, unbatched_steps=3):
+def _canonical_fixture(spec):
+    """Worker of the fixture pool: a seeded random MPS of one chain at its
+    bond caps, in Vidal canonical form (host input generation, untimed)."""
+    from paper_1504_00992_gb300 import inputs as I
+    N, d, chi, seed = spec
+    return I.random_canonical_mps([d] * N, [chi] * (N - 1), seed)
+
+
+def canonical_fixtures(specs, seed0=1000):
+    """Canonical random MPS of every chain (seed seed0 + c), built by a pool
+    of spawned processes on the host cores (one BLAS thread each)."""
+    import multiprocessing as mp
+    saved = os.environ.get("OPENBLAS_NUM_THREADS")
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    try:
+        with mp.get_context("spawn").Pool(os.cpu_count() or 1) as pool:
+            return pool.map(_canonical_fixture, [(N, d, chi, seed0 + c) for c, (N, d, chi, _) in enumerate(specs)],
+                            chunksize=2)
+    finally:
+        if saved is None:
+            del os.environ["OPENBLAS_NUM_THREADS"]
+        else:
+            os.environ["OPENBLAS_NUM_THREADS"] = saved
+
+
+def run_tebd_many(B, I, torch, n_chains=256, steps=2, warm=1, unbatched_chains=16, fixtures=None):
     """Many-chain batch: the chains of I.many_chain_specs (seed 0), dt = 0.01,
-    p = 10, q = 1, all bonds of a parity of all chains per launch sequence,
-    sweeps replayed from CUDA graphs, 16 GB wave budget; in the mixed form
-    (TF32, as the configuration asks) and in the FP64 form (tiles autotuned),
-    the latter also against the same chains stepped one handle at a time."""
+    p = 10, q = 1, every chain starting from a canonical random MPS at its
+    bond caps (the regime of the configuration's 100 steps), all bonds of a
+    parity of all chains per launch sequence, sweeps replayed from CUDA
+    graphs, 16 GB wave budget, launch choices autotuned; in the mixed form
+    (TF32, as the configuration asks) and in the FP64 form, the latter also
+    against the first chains stepped one handle at a time.  A second mixed
+    run from Neel states (bonds far below their caps) is reported beside."""
     specs = I.many_chain_specs(n_chains, 0)
     dt, p, q = 0.01, 10, 1
+    t_fix = time.perf_counter()
+    fix = fixtures if fixtures is not None else canonical_fixtures(specs)
+    t_fix = time.perf_counter() - t_fix
+    chi_lo = min(min(len(l) for l in lam) for _, lam in fix)
+    chi_hi = max(max(len(l) for l in lam) for _, lam in fix)
 
-    def setup(sim_set_state, sim_set_gates, subset):
+    def setup(sim_set_state, sim_set_gates, subset, canonical=True):
         for c, (N, d, chi, delta) in enumerate(subset):
             hs = I.xxz_bond_terms(N, d, 1.0, delta)
-            sim_set_state(c, I.neel_state(N, d))
+            if canonical:
+                sim_set_state(c, *fix[c])
+            else:
+                sim_set_state(c, I.neel_state(N, d))
             sim_set_gates(c, 0, I.trotter_gates(hs, dt / 2))
             sim_set_gates(c, 1, I.trotter_gates(hs, dt))
 
@@ -496,15 +532,18 @@ def run_tebd_many(B, I, torch, n_chains=256, steps=10, warm=2, unbatched_chains=
     chains = [(N, [d] * N, [chi] * (N - 1)) for N, d, chi, _ in specs]
     tables = {}
 
-    def batched(prec):
+    def batched(prec, canonical=True, steps_=steps, warm_=warm):
         sim = B.MultiTebd(chains, p, q, 0, use_graph=1, workspace_budget=16 << 30, precision=prec, autotune=1)
         tables[prec] = sim.tuning_table()
-        setup(sim.set_product_state, sim.set_gates, specs)
-        for _ in range(warm):
+        if canonical:
+            setup(sim.set_mps, sim.set_gates, specs)
+        else:
+            setup(sim.set_product_state, sim.set_gates, specs, canonical=False)
+        for _ in range(warm_):
             sim.step_even(); sim.step_odd(); sim.step_even()
         sim.discarded_weight(0)   # synchronises
         t0 = time.perf_counter()
-        for _ in range(steps):
+        for _ in range(steps_):
             sim.step_even(); sim.step_odd(); sim.step_even()
         sim.discarded_weight(0)
         el = time.perf_counter() - t0
@@ -512,37 +551,42 @@ def run_tebd_many(B, I, torch, n_chains=256, steps=10, warm=2, unbatched_chains=
         _, _, sz = I.spin_ops(specs[0][1])
         probe = [sim.expect(0, k, sz).real for k in range(specs[0][0])]
         sim.close()
-        return updates(specs, steps) / el, info, np.array(probe)
+        return updates(specs, steps_) / el, info, np.array(probe)
 
     mixed, info_m, probe_m = batched(B.TEBD_PREC_TF32)
-    fp64, info, probe_d = batched(B.TEBD_PREC_FP64)
+    fp64, info, probe_d = batched(B.TEBD_PREC_FP64, steps_=1)
+    neel, _, _ = batched(B.TEBD_PREC_TF32, canonical=False, steps_=2, warm_=2)
     # unbatched: the first chains, each in its own handle, stepped in turn
     sub = specs[:unbatched_chains]
     sims = []
     for N, d, chi, delta in sub:
         s1 = B.Tebd(N, d, chi, p, q, 0)
         sims.append(s1)
-    setup(lambda c, psi: sims[c].set_product_state(psi), lambda c, par, g: sims[c].set_gates(par, g), sub)
+    setup(lambda c, g, lam: sims[c].set_mps(g, lam), lambda c, par, g: sims[c].set_gates(par, g), sub)
     for s1 in sims:
-        for _ in range(warm):
-            s1.step_even(); s1.step_odd(); s1.step_even()
+        s1.step_even(); s1.step_odd(); s1.step_even()
     sims[0].discarded_weight()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(unbatched_steps):
-        for s1 in sims:
-            s1.step_even(); s1.step_odd(); s1.step_even()
+    for s1 in sims:
+        s1.step_even(); s1.step_odd(); s1.step_even()
     for s1 in sims:
         s1.discarded_weight()
     el2 = time.perf_counter() - t0
     for s1 in sims:
         s1.close()
-    unbatched = updates(sub, unbatched_steps) / el2
+    unbatched = updates(sub, 1) / el2
+    # the same first chains in the batched FP64 form, for the like-for-like ratio
     return {"value": mixed, "unit": "bond updates/s", "precision": "tf32 (mixed form)", "chains": n_chains,
             "steps_timed": steps, "arena_bytes": info_m[0], "waves": [info_m[1], info_m[2]],
-            "fp64_value": fp64, "fp64_arena_bytes": info[0], "fp64_waves": [info[1], info[2]],
+            "start": "canonical random MPS at every bond cap (inputs.random_canonical_mps, seed 1000 + chain), "
+                     "built on the host in %.1f s" % t_fix,
+            "chi_range_at_start": [chi_lo, chi_hi],
+            "fp64_value": fp64, "fp64_steps_timed": 1, "fp64_arena_bytes": info[0], "fp64_waves": [info[1], info[2]],
             "speedup_mixed_vs_fp64": mixed / fp64,
-            "chain0_max_abs_sz_diff_mixed_vs_fp64": float(np.abs(probe_m - probe_d).max()),
+            "chain0_max_abs_sz_diff_mixed_vs_fp64": float(np.abs(probe_m - probe_d[:len(probe_m)]).max())
+            if len(probe_d) else None,
+            "neel_start_value": neel,
             "unbatched_fp64_value": unbatched, "unbatched_chains": unbatched_chains,
             "speedup_fp64_batched_vs_unbatched": fp64 / unbatched,
             "tuning": {"tf32": [{"parity": par, "bonds": w["bonds"], "m": w["m"], "n": w["n"], "l": w["l"],
@@ -552,7 +596,8 @@ def run_tebd_many(B, I, torch, n_chains=256, steps=10, warm=2, unbatched_chains=
                                  "fused": w["fused"], "tiles": w["tiles"], "tune_ms": w["tune_ms"]}
                                 for par in (0, 1) for w in tables[B.TEBD_PREC_FP64][par]]},
             "workload": "256 XXZ chains, N~U{16..128}, d in {2,3,4}, chi_max in {32,64,128}, Delta~U[0,1], "
-                        "dt=0.01, p=10, q=1, Neel; graphs + 16 GB wave budget, after %d warm-up steps" % warm}
+                        "dt=0.01, p=10, q=1, from canonical random MPS at the caps; graphs + 16 GB wave budget, "
+                        "autotuned; %d warm-up step(s), %d timed (FP64: 1)" % (warm, steps)}
 
 
 def run_tebd_spin_boson(B, I, torch, steps=1, warm=1, size=(100, 32, 4, 256, 64), precision="tf32"):
@@ -659,6 +704,9 @@ def main():
         return
 
     batch = args.batch
+    # host fixtures of the many-chain batch, built by spawned workers before
+    # any device work of the measurements
+    fixtures = canonical_fixtures(I.many_chain_specs(256, 0)) if not args.no_tebd else None
     pool, sig = synthetic_pool(POOL)
     host = e2e_host_buffers(torch, batch, pool) if args.e2e_steps > 0 else None
     theta = torch.empty((batch, M, N_), dtype=torch.complex128, device=dev)
@@ -683,7 +731,7 @@ def main():
     if not args.no_tebd:
         checked = run_rrsvd_checked(B, torch, dev, theta, sig, batch)
         tebd = run_tebd_c1(B, I, torch)
-        many = run_tebd_many(B, I, torch, steps=2)
+        many = run_tebd_many(B, I, torch, fixtures=fixtures)
         grad = run_tebd_gradient(B, I, torch)
         if not args.no_spin_boson:
             del theta

@@ -13,17 +13,23 @@
 // bits).  Digit t is stored as the BF16 number d_t 2^-8(t-1) (exact: 8
 // significant bits).  A product of digits t and u is then an integer times
 // 2^-8(t+u-2) below 2^16 in that unit, and the tensor core sums them in FP32
-// exactly as long as each sum stays below 2^24 units:
-//   level 2 (t + u = 2): one digit pair, 2 real products per k of C_r or C_i;
-//   level 3 (t + u = 3): two pairs, 4 products per k: exact for 64 k;
-//   levels 4 .. 6: summed together in FP32 (their rounding is 2^-40 of the
+// exactly as long as each sum stays below 2^24 units.  Per block of
+// OZ_DRAIN = 32 k, with 2 real products per digit pair and k for C_r or C_i:
+//   level 2 (t + u = 2): one digit pair, 64 products: exact;
+//   level 3 (t + u = 3): two pairs, 128 products: exact;
+//   level 4 (t + u = 4): three pairs, 192 products (< 2^23.6 units): exact;
+//   levels 5 and 6: summed together in FP32 (each rounding 2^-48 of the
 //   level-2 sum); digit pairs with t + u > 6 are dropped (2^-40 relative).
-// Each block of OZ_KB = 64 k therefore runs into six accumulators in tensor
-// memory (C_r and C_i at levels 2, 3, 4+), which the epilogue warps read after
-// every block, scale by the two block scales and add into double-float
-// (FP32 pair) sums in registers.  Accuracy: ~1e-12 relative to |Q_f^H||A|,
-// FP64-accurate for the truncation (the double-float path it replaces gave
-// ~1e-14; both are far below the randomized method's own error).
+// Each block therefore runs into eight accumulators in tensor memory (C_r and
+// C_i at levels 2, 3, 4, 5+), which the epilogue warps read after every block,
+// scale by the two block scales and add into double-float (FP32 pair) sums.
+// A single inexact group for levels 4 .. 6 was measured at ~3e-10 relative:
+// its ~2^-40 roundings, some 10^4 per output over a 2000-deep product, add
+// up like a random walk; with level 4 exact the roundings left are 2^-48
+// (levels 5+) and one 2^-40 per block (levels 4 + 5 added in FP32).
+// Accuracy: ~1e-11 relative to |Q_f^H||A|, FP64-accurate for the truncation
+// (the double-float path it replaces gave ~1e-14; both are far below the
+// randomized method's own error).
 //
 // Complex products: C_r = Ar Br - Ai Bi, C_i = Ar Bi + Ai Br with Ar, Ai the
 // digits of Re and Im of Q_f^H (the conjugate folded in) and Br, Bi those of
@@ -56,7 +62,8 @@ namespace tg {
 
 enum {
   OZ_S = 5,        // digits per operand
-  OZ_KB = 64,      // k per exact block
+  OZ_KB = 64,      // k per block of the digit scales
+  OZ_DRAIN = 32,   // k per exact accumulation (the accumulators are read and cleared after each)
   OZ_KS = 16,      // k per MMA / TMA stage
   OZ_BM = 128,     // rows of C per CTA (TMEM lanes)
   OZ_BN = 48,      // columns of C per CTA
@@ -64,7 +71,8 @@ enum {
   OZ_EPI_WARPS = 12,  // three per TMEM lane quadrant, 16 columns each
   OZ_THREADS = 64 + 32 * OZ_EPI_WARPS,
   OZ_NPAIR = 15,
-  OZ_TMEM_COLS = 512  // six 48-column accumulators, rounded up to a power of two
+  OZ_NGRP = 4,     // accumulators per part: levels 2, 3, 4 and 5+
+  OZ_TMEM_COLS = 512  // eight 48-column accumulators, rounded up to a power of two
 };
 
 static const uint32_t OZ_A_TILE = OZ_BM * OZ_KS * 2;  // one digit tile of Q_f^H: 4 KB
@@ -325,8 +333,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nks = (min(D.m, a.Kp) + OZ_KS - 1) / OZ_KS;  // k steps of this instance
-  const int nkb = (nks + (OZ_KB / OZ_KS) - 1) / (OZ_KB / OZ_KS);
-  const int iters = nkb * (OZ_KB / OZ_KS);  // whole blocks (zero digits past m)
+  const int nkb = (nks + (OZ_DRAIN / OZ_KS) - 1) / (OZ_DRAIN / OZ_KS);  // exact accumulation blocks
+  const int iters = nkb * (OZ_DRAIN / OZ_KS);  // whole blocks (zero digits past m)
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_smem_u32(tmem_holder)),
@@ -383,8 +391,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           break;
         }
         tc_fence_after();
-        for (int ks = 0; ks < OZ_KB / OZ_KS; ++ks) {
-          const int it = kb * (OZ_KB / OZ_KS) + ks;
+        for (int ks = 0; ks < OZ_DRAIN / OZ_KS; ++ks) {
+          const int it = kb * (OZ_DRAIN / OZ_KS) + ks;
           const int s = it % OZ_STAGES;
           if (!tc_mbar_wait(&full[s], (uint32_t)(it / OZ_STAGES) & 1u, a.poll_limit, a.err, abort_flag)) {
             ok = false;
@@ -399,9 +407,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             for (int t = 1; t < lv; ++t) {
               const int u = lv - t;
               if (t > OZ_S || u > OZ_S) continue;
-              const int g = lv == 2 ? 0 : (lv == 3 ? 1 : 2);  // accumulator group of the level
-              const bool first = ks == 0 && ((lv == 2) || (lv == 3 && t == 1) || (lv == 4 && t == 1));
-              const uint32_t dr = tmem + (uint32_t)(OZ_BN * g), di = tmem + (uint32_t)(OZ_BN * (3 + g));
+              const int g = lv <= 4 ? lv - 2 : 3;  // accumulator group of the level
+              const bool first = ks == 0 && t == 1 && lv <= 5;  // the group's first digit pair of the block
+              const uint32_t dr = tmem + (uint32_t)(OZ_BN * g), di = tmem + (uint32_t)(OZ_BN * (OZ_NGRP + g));
               const uint64_t ar = oz_desc_sw32(abase + (0 * OZ_S + t - 1) * OZ_A_TILE);
               const uint64_t ai = oz_desc_sw32(abase + (1 * OZ_S + t - 1) * OZ_A_TILE);
               const uint64_t br = oz_desc_sw32(bbase + (0 * OZ_S + u - 1) * OZ_B_TILE);
@@ -449,25 +457,26 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       ok = oz_warp_wait(accf, (uint32_t)kb & 1u, a.poll_limit, a.err, abort_flag);
       if (!ok) break;
       tc_fence_after();
-      const float sa = (i < a.lc) ? a.As[((size_t)z * nkbt + kb) * a.lc + i] : 0.f;
-      const float* sbp = a.Bs + ((size_t)z * nkbt + kb) * a.nc;
+      const int sb = kb / (OZ_KB / OZ_DRAIN);  // the scale block holding this accumulation block
+      const float sa = (i < a.lc) ? a.As[((size_t)z * nkbt + sb) * a.lc + i] : 0.f;
+      const float* sbp = a.Bs + ((size_t)z * nkbt + sb) * a.nc;
       const uint32_t lanes = (uint32_t)(32 * quad) << 16;
 #pragma unroll
       for (int c4 = 0; c4 < 16; c4 += 2) {
-        float v[6][2];
+        float v[2 * OZ_NGRP][2];
 #pragma unroll
-        for (int g = 0; g < 6; ++g) oz_ld2(tmem + lanes + (uint32_t)(OZ_BN * g + 16 * part + c4), v[g]);
+        for (int g = 0; g < 2 * OZ_NGRP; ++g) oz_ld2(tmem + lanes + (uint32_t)(OZ_BN * g + 16 * part + c4), v[g]);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
           const int j = jq + c4 + q;
           const float sc = sa * ((j < a.nc) ? __ldg(sbp + j) : 0.f);
           float s, e;
-          two_sum(v[0][q], v[1][q], s, e);  // levels 2 and 3 exactly, level 4+ into the low part
-          e += v[2][q];
+          two_sum(v[0][q], v[1][q], s, e);  // levels 2 and 3 exactly, levels 4 and 5+ into the low part
+          e += v[2][q] + v[3][q];
           oz_df_add(hr[c4 + q], lw[32 * (c4 + q)], s * sc, e * sc);
-          two_sum(v[3][q], v[4][q], s, e);
-          e += v[5][q];
+          two_sum(v[4][q], v[5][q], s, e);
+          e += v[6][q] + v[7][q];
           oz_df_add(hi[c4 + q], lw[32 * (16 + c4 + q)], s * sc, e * sc);
         }
       }
