@@ -8,28 +8,28 @@
 // Slices (Ozaki's error-free splitting; Ozaki, Ogita, Oishi, Rump, Numer.
 // Algorithms 59, 2012): within each block of OZ_KB consecutive k, every row i
 // of Q_f^H and every column j of A is scaled by a power of two s so that the
-// block's entries x satisfy |x| < s 2^8, and x / s is cut into OZ_S signed
-// 8-bit digits d_1 .. d_S (x = s (d_1 + d_2 2^-8 + ... ), truncated after 40
-// bits).  Digit t is stored as the BF16 number d_t 2^-8(t-1) (exact: 8
-// significant bits).  A product of digits t and u is then an integer times
+// block's entries x satisfy |x| < s 2^8, and x / s is cut into OZ_S = 6
+// signed 8-bit digits d_1 .. d_6 (x = s (d_1 + d_2 2^-8 + ... ), truncated
+// after 48 bits).  Digit t is stored as the BF16 number d_t 2^-8(t-1) (exact:
+// 8 significant bits).  A product of digits t and u is then an integer times
 // 2^-8(t+u-2) below 2^16 in that unit, and the tensor core sums them in FP32
 // exactly as long as each sum stays below 2^24 units.  Per block of
 // OZ_DRAIN = 32 k, with 2 real products per digit pair and k for C_r or C_i:
 //   level 2 (t + u = 2): one digit pair, 64 products: exact;
-//   level 3 (t + u = 3): two pairs, 128 products: exact;
-//   level 4 (t + u = 4): three pairs, 192 products (< 2^23.6 units): exact;
-//   levels 5 and 6: summed together in FP32 (each rounding 2^-48 of the
-//   level-2 sum); digit pairs with t + u > 6 are dropped (2^-40 relative).
-// Each block therefore runs into eight accumulators in tensor memory (C_r and
-// C_i at levels 2, 3, 4, 5+), which the epilogue warps read after every block,
-// scale by the two block scales and add into double-float (FP32 pair) sums.
-// A single inexact group for levels 4 .. 6 was measured at ~3e-10 relative:
-// its ~2^-40 roundings, some 10^4 per output over a 2000-deep product, add
-// up like a random walk; with level 4 exact the roundings left are 2^-48
-// (levels 5+) and one 2^-40 per block (levels 4 + 5 added in FP32).
-// Accuracy: ~1e-11 relative to |Q_f^H||A|, FP64-accurate for the truncation
-// (the double-float path it replaces gave ~1e-14; both are far below the
-// randomized method's own error).
+//   level 3: two pairs, 128 products; level 4: three pairs, 192 products;
+//   level 5: four pairs, 256 products (< 2^23.99 units): all exact;
+//   levels 6 and 7: summed together in FP32 (each rounding 2^-56 of the
+//   level-2 sum); digit pairs with t + u > 7 are dropped (2^-48 relative).
+// Each block therefore runs into ten accumulators in tensor memory (C_r and
+// C_i at levels 2, 3, 4, 5, 6+), which the epilogue warps read after every
+// block, scale by the two block scales and add into double-float (FP32 pair)
+// sums in registers.  Measured on 40-bit digits with levels 4 .. 6 in one
+// inexact group: ~3e-10 relative (some 10^4 roundings of 2^-40 per output of
+// a 2000-deep product add up like a random walk); with level 4 exact, 1.4e-11
+// (the 40-bit truncation of the digits).  With 48-bit digits and levels 2 .. 5
+// exact the roundings left are 2^-56 (levels 6+) and 2^-48 (combining the
+// levels once per block): FP64-accurate, like the double-float path it
+// replaces (~1e-14).
 //
 // Complex products: C_r = Ar Br - Ai Bi, C_i = Ar Bi + Ai Br with Ar, Ai the
 // digits of Re and Im of Q_f^H (the conjugate folded in) and Br, Bi those of
@@ -38,9 +38,9 @@
 // Kernel structure (one CTA = 128 rows of C (l) x OZ_BN = 48 columns (n), all
 // k): warp 0 lane 0 streams the digit tiles of each 16-deep k step with 5-D
 // TMA loads (k, row, digit, re/im, instance; 32-byte swizzle) into a ring of
-// OZ_STAGES stages; warp 1 lane 0 issues 60 tcgen05.mma.kind::f16 per k step
-// (15 digit pairs x 4 real products); warps 2 .. 13 read the accumulators
-// after each k block (warp w reads TMEM lanes 32 (w % 4) .. +31, a third of
+// OZ_STAGES stages; warp 1 lane 0 issues 84 tcgen05.mma.kind::f16 per k step
+// (21 digit pairs x 4 real products); warps 2 .. 25 read the accumulators
+// after each k block (warp w reads TMEM lanes 32 (w % 4) .. +31, a sixth of
 // the columns) and keep the double-float sums.  Every mbarrier wait is
 // bounded; on expiry the kernel raises *err, waits for its own copies and
 // MMAs, and frees its tensor memory.
@@ -61,32 +61,30 @@
 namespace tg {
 
 enum {
-  OZ_S = 5,        // digits per operand
+  OZ_S = 6,        // digits per operand
   OZ_KB = 64,      // k per block of the digit scales
   OZ_DRAIN = 32,   // k per exact accumulation (the accumulators are read and cleared after each)
   OZ_KS = 16,      // k per MMA / TMA stage
   OZ_BM = 128,     // rows of C per CTA (TMEM lanes)
   OZ_BN = 48,      // columns of C per CTA
   OZ_STAGES = 3,
-  OZ_EPI_WARPS = 12,  // three per TMEM lane quadrant, 16 columns each
+  OZ_EPI_WARPS = 24,  // six per TMEM lane quadrant, 8 columns each
   OZ_THREADS = 64 + 32 * OZ_EPI_WARPS,
-  OZ_NPAIR = 15,
-  OZ_NGRP = 4,     // accumulators per part: levels 2, 3, 4 and 5+
-  OZ_TMEM_COLS = 512  // eight 48-column accumulators, rounded up to a power of two
+  OZ_NPAIR = 21,
+  OZ_NGRP = 5,     // accumulators per part: levels 2, 3, 4, 5 and 6+
+  OZ_TMEM_COLS = 512  // ten 48-column accumulators, rounded up to a power of two
 };
 
 static const uint32_t OZ_A_TILE = OZ_BM * OZ_KS * 2;  // one digit tile of Q_f^H: 4 KB
 static const uint32_t OZ_B_TILE = OZ_BN * OZ_KS * 2;  // one digit tile of A: 1.5 KB
 static const uint32_t OZ_A_STAGE = 2 * OZ_S * OZ_A_TILE;
 static const uint32_t OZ_B_STAGE = 2 * OZ_S * OZ_B_TILE;
-// low words of the epilogue's double-float sums: [epilogue warp][value][lane],
-// 32 values (16 columns, Re and Im) per thread
-static const uint32_t OZ_LO_BYTES = OZ_EPI_WARPS * 32 * 32 * 4;
+
 
 // ---------------------------------------------------------------------------
 // Digits.  An FP64 or FP32 value and the block's largest biased exponent E
-// give a 40-bit fixed-point magnitude N (x = +-N 2^(E - bias - mantissa - 13)
-// for FP64), cut into five 8-bit digits, each stored as the BF16 number
+// give a 48-bit fixed-point magnitude N (x = +-N 2^(E - bias - mantissa - 5)
+// for FP64), cut into six 8-bit digits, each stored as the BF16 number
 // +-d_t 2^-8(t-1) (bit pattern built from FP32 arithmetic that is exact).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint16_t oz_bf16_digit(unsigned d, int t, bool neg) {
@@ -95,22 +93,22 @@ __device__ __forceinline__ uint16_t oz_bf16_digit(unsigned d, int t, bool neg) {
   return (uint16_t)(u | (neg && d ? 0x8000u : 0u));
 }
 
-// 40-bit magnitude of an FP64 value relative to block exponent E (biased).
-__device__ __forceinline__ uint64_t oz_n40_f64(double x, int E) {
+// 48-bit magnitude of an FP64 value relative to block exponent E (biased).
+__device__ __forceinline__ uint64_t oz_n48_f64(double x, int E) {
   const uint64_t u = (uint64_t)__double_as_longlong(x);
   const int e = (int)((u >> 52) & 0x7FF);
   if (e == 0 || e == 0x7FF) return 0;  // zero, subnormal (negligible), non-finite (flagged elsewhere)
   const uint64_t m = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-  const int sh = E - e + 13;  // >= 13
+  const int sh = E - e + 5;  // >= 5
   return sh >= 64 ? 0 : (m >> sh);
 }
 
-__device__ __forceinline__ uint64_t oz_n40_f32(float x, int E) {
+__device__ __forceinline__ uint64_t oz_n48_f32(float x, int E) {
   const unsigned u = __float_as_uint(x);
   const int e = (int)((u >> 23) & 0xFF);
   if (e == 0 || e == 0xFF) return 0;
   const uint64_t m = (uint64_t)((u & 0x7FFFFFu) | 0x800000u);
-  const int sh = e - E + 16;  // <= 16
+  const int sh = e - E + 24;  // <= 24
   return sh >= 0 ? (m << sh) : ((-sh) >= 64 ? 0 : (m >> (-sh)));
 }
 
@@ -124,27 +122,27 @@ __device__ __forceinline__ float oz_scale(int E, int off) {
 // ---------------------------------------------------------------------------
 // Digits of A (theta, m x n row-major FP64 per instance) into
 // Bd[z][reim][t][j][k] (k contiguous, Kp per row, rows nc) and block scales
-// Bs[z][kb][j].  A CTA takes 64 k x 32 j; rows past the instance's (m, n)
+// Bs[z][kb][j].  A CTA takes 64 k x 16 j; rows past the instance's (m, n)
 // become zero digits.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_oz_digits_theta(const Dims* __restrict__ dims,
                                                          const ProbPtr* __restrict__ ptrs, uint16_t* Bd, float* Bs,
                                                          int nc, int Kp) {
-  __shared__ int emax[8][33];
-  __shared__ uint16_t dig[2 * OZ_S][32][OZ_KB + 2];  // [reim t][j][k]
+  __shared__ int emax[16][17];
+  __shared__ uint16_t dig[2 * OZ_S][16][OZ_KB + 2];  // [reim t][j][k]
   const int z = blockIdx.z;
   const Dims D = dims[z];
   if (!D.active) return;
   const int m = D.m, n = D.n;
   const cplx* th = ptrs[z].theta;
-  const int k0 = blockIdx.y * OZ_KB, j0 = blockIdx.x * 32;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int k0 = blockIdx.y * OZ_KB, j0 = blockIdx.x * 16;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int j = j0 + tx;
-  cplx v[8];
+  cplx v[4];
   int e = 0;
 #pragma unroll
-  for (int s = 0; s < 8; ++s) {
-    const int k = k0 + ty + 8 * s;
+  for (int s = 0; s < 4; ++s) {
+    const int k = k0 + ty + 16 * s;
     v[s] = (k < m && j < n) ? th[(int64_t)k * n + j] : cmk(0.0, 0.0);
     const uint64_t ur = (uint64_t)__double_as_longlong(v[s].x), ui = (uint64_t)__double_as_longlong(v[s].y);
     const int er = (int)((ur >> 52) & 0x7FF), ei = (int)((ui >> 52) & 0x7FF);
@@ -154,26 +152,26 @@ __global__ void __launch_bounds__(256) k_oz_digits_theta(const Dims* __restrict_
   __syncthreads();
   int E = 0;
 #pragma unroll
-  for (int s = 0; s < 8; ++s) E = max(E, emax[s][tx]);
+  for (int s = 0; s < 16; ++s) E = max(E, emax[s][tx]);
   const float sc = oz_scale(E, 1030);  // x = sum_t digit_t * 2^(E - 1030)
   const bool live = sc != 0.f;
 #pragma unroll
-  for (int s = 0; s < 8; ++s) {
-    const int k = ty + 8 * s;
-    const uint64_t nr = live ? oz_n40_f64(v[s].x, E) : 0, ni = live ? oz_n40_f64(v[s].y, E) : 0;
+  for (int s = 0; s < 4; ++s) {
+    const int k = ty + 16 * s;
+    const uint64_t nr = live ? oz_n48_f64(v[s].x, E) : 0, ni = live ? oz_n48_f64(v[s].y, E) : 0;
     const bool sr = v[s].x < 0.0, si = v[s].y < 0.0;
 #pragma unroll
     for (int t = 0; t < OZ_S; ++t) {
-      dig[t][tx][k] = oz_bf16_digit((unsigned)((nr >> (32 - 8 * t)) & 0xFF), t, sr);
-      dig[OZ_S + t][tx][k] = oz_bf16_digit((unsigned)((ni >> (32 - 8 * t)) & 0xFF), t, si);
+      dig[t][tx][k] = oz_bf16_digit((unsigned)((nr >> (40 - 8 * t)) & 0xFF), t, sr);
+      dig[OZ_S + t][tx][k] = oz_bf16_digit((unsigned)((ni >> (40 - 8 * t)) & 0xFF), t, si);
     }
   }
   if (ty == 0 && j < nc) Bs[((size_t)z * (Kp / OZ_KB) + blockIdx.y) * nc + j] = live ? sc : 0.f;
   __syncthreads();
   // rows (reim t, j) of 64 k = 128 bytes each: 8 threads per row, 16 bytes each
   uint16_t* base = Bd + (size_t)z * 2 * OZ_S * nc * Kp;
-  for (int w = threadIdx.x; w < 2 * OZ_S * 32 * 8; w += 256) {
-    const int q = w & 7, row = w >> 3, jj = row & 31, rt = row >> 5;
+  for (int w = threadIdx.x; w < 2 * OZ_S * 16 * 8; w += 256) {
+    const int q = w & 7, row = w >> 3, jj = row & 15, rt = row >> 4;
     if (j0 + jj >= nc) continue;
     const uint16_t* src = &dig[rt][jj][q * 8];
     uint4 pk;
@@ -221,9 +219,9 @@ __global__ void __launch_bounds__(256) k_oz_digits_q(const Dims* __restrict__ di
     uint16_t dr[2], di[2];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const uint64_t nr = live ? oz_n40_f32(re[h], E) : 0, ni = live ? oz_n40_f32(im[h], E) : 0;
-      dr[h] = oz_bf16_digit((unsigned)((nr >> (32 - 8 * t)) & 0xFF), t, re[h] < 0.f);
-      di[h] = oz_bf16_digit((unsigned)((ni >> (32 - 8 * t)) & 0xFF), t, im[h] < 0.f);
+      const uint64_t nr = live ? oz_n48_f32(re[h], E) : 0, ni = live ? oz_n48_f32(im[h], E) : 0;
+      dr[h] = oz_bf16_digit((unsigned)((nr >> (40 - 8 * t)) & 0xFF), t, re[h] < 0.f);
+      di[h] = oz_bf16_digit((unsigned)((ni >> (40 - 8 * t)) & 0xFF), t, im[h] < 0.f);
     }
     *reinterpret_cast<unsigned*>(base + ((size_t)t * lc + i) * Kp + k) = (unsigned)dr[0] | ((unsigned)dr[1] << 16);
     *reinterpret_cast<unsigned*>(base + ((size_t)(OZ_S + t) * lc + i) * Kp + k) =
@@ -295,11 +293,10 @@ __device__ __forceinline__ bool oz_warp_wait(uint64_t* bar, uint32_t parity, uin
   return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
 }
 
-__device__ __forceinline__ void oz_ld2(uint32_t taddr, float* v) {
-  uint32_t r[2];
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(taddr) : "memory");
-  v[0] = __uint_as_float(r[0]);
-  v[1] = __uint_as_float(r[1]);
+__device__ __forceinline__ float oz_ld1(uint32_t taddr) {
+  uint32_t r;
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr) : "memory");
+  return __uint_as_float(r);
 }
 
 // acc (h, l) += s (hs, ls), then renormalised
@@ -322,8 +319,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   uint8_t* smem = (uint8_t*)(((uintptr_t)oz_smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;
   uint8_t* sB = smem + OZ_STAGES * OZ_A_STAGE;
-  float* lo_s = (float*)(sB + OZ_STAGES * OZ_B_STAGE);
-  uint64_t* full = (uint64_t*)((uint8_t*)lo_s + OZ_LO_BYTES);
+  uint64_t* full = (uint64_t*)(sB + OZ_STAGES * OZ_B_STAGE);
   uint64_t* empty = full + OZ_STAGES;
   uint64_t* accf = empty + OZ_STAGES;
   uint64_t* accfree = accf + 1;
@@ -380,7 +376,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     __syncwarp();
   } else if (warp == 1) {
     if (lane == 0) {
-      // ---- MMA issuer: per k step, the 15 digit pairs (t, u) with t + u <= 6
+      // ---- MMA issuer: per k step, the 21 digit pairs (t, u) with t + u <= 7
       // in level order, four real products each
       const uint32_t ip = oz_idesc(OZ_BM, OZ_BN, false), in = oz_idesc(OZ_BM, OZ_BN, true);
       bool ok = true;
@@ -401,14 +397,14 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           tc_fence_after();
           const uint32_t abase = tc_smem_u32(sA + s * OZ_A_STAGE), bbase = tc_smem_u32(sB + s * OZ_B_STAGE);
           int pi = 0;
-#pragma unroll
+#pragma unroll 1
           for (int lv = 2; lv <= OZ_S + 1; ++lv) {
-#pragma unroll
+#pragma unroll 1
             for (int t = 1; t < lv; ++t) {
               const int u = lv - t;
               if (t > OZ_S || u > OZ_S) continue;
-              const int g = lv <= 4 ? lv - 2 : 3;  // accumulator group of the level
-              const bool first = ks == 0 && t == 1 && lv <= 5;  // the group's first digit pair of the block
+              const int g = lv <= 5 ? lv - 2 : 4;  // accumulator group of the level
+              const bool first = ks == 0 && t == 1 && lv <= 6;  // the group's first digit pair of the block
               const uint32_t dr = tmem + (uint32_t)(OZ_BN * g), di = tmem + (uint32_t)(OZ_BN * (OZ_NGRP + g));
               const uint64_t ar = oz_desc_sw32(abase + (0 * OZ_S + t - 1) * OZ_A_TILE);
               const uint64_t ai = oz_desc_sw32(abase + (1 * OZ_S + t - 1) * OZ_A_TILE);
@@ -439,19 +435,14 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     }
     __syncwarp();
   } else {
-    // ---- epilogue: warp w reads lanes 32 (w % 4) .. +31 and one third of the columns
+    // ---- epilogue: warp w reads lanes 32 (w % 4) .. +31 and one sixth of the columns
     const int ew = warp - 2, quad = warp & 3, part = ew >> 2;
     const int i = i0 + 32 * quad + lane;  // row of C
-    const int jq = j0 + 16 * part;        // first column of this warp
+    const int jq = j0 + 8 * part;         // first column of this warp
     const int nkbt = a.Kp / OZ_KB;        // k blocks of the scale arrays
-    float hr[16], hi[16];                  // high words in registers, low words in shared memory
-    float* lw = lo_s + (size_t)ew * 32 * 32 + lane;  // value v at lw[32 v]
+    float hr[8], lr[8], hi[8], li[8];      // double-float sums (Re, Im) of 8 columns
 #pragma unroll
-    for (int c = 0; c < 16; ++c) {
-      hr[c] = hi[c] = 0.f;
-      lw[32 * c] = 0.f;
-      lw[32 * (16 + c)] = 0.f;
-    }
+    for (int c = 0; c < 8; ++c) hr[c] = lr[c] = hi[c] = li[c] = 0.f;
     bool ok = true;
     for (int kb = 0; kb < nkb; ++kb) {
       ok = oz_warp_wait(accf, (uint32_t)kb & 1u, a.poll_limit, a.err, abort_flag);
@@ -462,22 +453,25 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       const float* sbp = a.Bs + ((size_t)z * nkbt + sb) * a.nc;
       const uint32_t lanes = (uint32_t)(32 * quad) << 16;
 #pragma unroll
-      for (int c4 = 0; c4 < 16; c4 += 2) {
-        float v[2 * OZ_NGRP][2];
+      for (int c4 = 0; c4 < 8; ++c4) {
+        float v[2 * OZ_NGRP][1];
 #pragma unroll
-        for (int g = 0; g < 2 * OZ_NGRP; ++g) oz_ld2(tmem + lanes + (uint32_t)(OZ_BN * g + 16 * part + c4), v[g]);
+        for (int g = 0; g < 2 * OZ_NGRP; ++g) v[g][0] = oz_ld1(tmem + lanes + (uint32_t)(OZ_BN * g + 8 * part + c4));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
+        for (int q = 0; q < 1; ++q) {
           const int j = jq + c4 + q;
           const float sc = sa * ((j < a.nc) ? __ldg(sbp + j) : 0.f);
-          float s, e;
-          two_sum(v[0][q], v[1][q], s, e);  // levels 2 and 3 exactly, levels 4 and 5+ into the low part
-          e += v[2][q] + v[3][q];
-          oz_df_add(hr[c4 + q], lw[32 * (c4 + q)], s * sc, e * sc);
-          two_sum(v[4][q], v[5][q], s, e);
-          e += v[6][q] + v[7][q];
-          oz_df_add(hi[c4 + q], lw[32 * (16 + c4 + q)], s * sc, e * sc);
+          // levels 2, 3, 4 exactly into (s, e + e2), levels 5 and 6+ into the low part
+          float s, e, s2, e2;
+          two_sum(v[0][q], v[1][q], s, e);
+          two_sum(s, v[2][q], s2, e2);
+          float lo = (e + e2) + (v[3][q] + v[4][q]);
+          oz_df_add(hr[c4 + q], lr[c4 + q], s2 * sc, lo * sc);
+          two_sum(v[5][q], v[6][q], s, e);
+          two_sum(s, v[7][q], s2, e2);
+          lo = (e + e2) + (v[8][q] + v[9][q]);
+          oz_df_add(hi[c4 + q], li[c4 + q], s2 * sc, lo * sc);
         }
       }
       tc_fence_before();
@@ -487,10 +481,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     if (ok && i < D.l) {
       cplx* X = ptrs[z].Yt;  // B^H = C^H: n x l column-major, element (j, i) = conj C[i][j]
 #pragma unroll
-      for (int c = 0; c < 16; ++c) {
+      for (int c = 0; c < 8; ++c) {
         const int j = jq + c;
-        if (j < D.n)
-          X[(size_t)i * D.n + j] = cmk((double)hr[c] + (double)lw[32 * c], -((double)hi[c] + (double)lw[32 * (16 + c)]));
+        if (j < D.n) X[(size_t)i * D.n + j] = cmk((double)hr[c] + (double)lr[c], -((double)hi[c] + (double)li[c]));
       }
     }
   }
@@ -503,9 +496,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   }
 }
 
-static size_t oz_smem_bytes() {
-  return 1024 + (size_t)OZ_STAGES * (OZ_A_STAGE + OZ_B_STAGE) + OZ_LO_BYTES + (2 * OZ_STAGES + 3) * 8 + 16;
-}
+static size_t oz_smem_bytes() { return 1024 + (size_t)OZ_STAGES * (OZ_A_STAGE + OZ_B_STAGE) + (2 * OZ_STAGES + 3) * 8 + 16; }
 
 // ---------------------------------------------------------------------------
 // host side
@@ -563,7 +554,7 @@ cudaError_t launch_oz_digits_theta(const Dims* dims, const ProbPtr* ptrs, uint16
                                    int batch, cudaStream_t st) {
   ProfScope ps("k_oz_digits[theta]", st);
   const int Kp = oz_kpad(m);
-  k_oz_digits_theta<<<dim3((n + 31) / 32, Kp / OZ_KB, batch), 256, 0, st>>>(dims, ptrs, Bd, Bs, n, Kp);
+  k_oz_digits_theta<<<dim3((n + 15) / 16, Kp / OZ_KB, batch), 256, 0, st>>>(dims, ptrs, Bd, Bs, n, Kp);
   return cudaGetLastError();
 }
 
