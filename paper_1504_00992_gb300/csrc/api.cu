@@ -370,7 +370,7 @@ static int tune_knobs(Run run, cudaStream_t st, const Caps& cap, int batch, Mixe
   t_rule = t_best;
   const bool multi_ok = cap.n >= 1024 && cap.l >= 16;  // the many-CTA QR's structure (its own rule adds the batch)
   const bool cl_ok = cap.l >= 64 && cap.l <= 512;
-  std::vector<std::vector<int>> cand = {{0, 1}, {0, 512, 256, 128}, {0, 1, 2}, {0, 1, 2}};
+  std::vector<std::vector<int>> cand = {{0, 1}, {0, 512, 256, 128}, {0, 1, 2, 3}, {0, 1, 2}};
   for (int knob = 0; knob < 4 && ok; ++knob)
     for (int v : cand[knob]) {
       MixedKnobs k = best;

@@ -1,0 +1,138 @@
+// Cholesky QR of B^H for the mixed form (sm_103a): the QR factorisation the
+// small-B SVD of Section IV's step ii starts from (B^H = Qb Rb, then the
+// one-sided Jacobi SVD of Rb^H), for well-conditioned B.
+//
+// CholeskyQR2 (Yamamoto, Nakatsukasa, Yanagisawa, Fukaya, ETNA 44, 2015):
+//   G1 = B B^H = R1^H R1,  Q1 = B^H R1^-1,
+//   G2 = Q1^H Q1 = R2^H R2, Qb = Q1 R2^-1,
+// with the Gram matrices and the triangular products in FP64-accurate
+// double-float arithmetic (k_zgemm_df stages G_G1 .. G_X) and the Cholesky
+// factorisations and triangular inverses in FP64 here.  For kappa(B) below
+// ~1e8 the two passes give an orthonormal Qb and a backward-stable
+// factorisation (residual and orthogonality at the unit-roundoff level), so
+// the singular values of Rb are those of B to ~eps ||B||.  Rb^H is formed as
+// X = B Qb.  An instance whose first Gram matrix is too ill-conditioned for
+// that (a Cholesky pivot below CQ_PIVOT times the largest diagonal entry,
+// i.e. kappa(B) above ~1e5) is flagged (Dims::qflag) and factored by the
+// Householder QR instead; its Cholesky output is replaced by the identity so
+// that the products in between stay finite.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "internal.cuh"
+#include "profiler.cuh"
+
+namespace tg {
+
+static const double CQ_PIVOT = 1e-10;
+
+// Cholesky G = R^H R of the l x l Hermitian matrix in P.R (upper triangle,
+// column-major, in place), then J = R^-1 (upper triangular, zero below).  One
+// CTA per instance.  pass 0 sets dims[p].qflag to 0 or 1; pass 1 skips the
+// instances already flagged and flags those whose second Gram fails.
+__global__ void __launch_bounds__(256) k_chol_inv(Dims* dims, const ProbPtr* __restrict__ ptrs, int pass) {
+  __shared__ double red[32];
+  __shared__ double s_inv;
+  __shared__ int s_fail;
+  const int p = blockIdx.x;
+  const Dims D = dims[p];
+  if (!D.active) return;
+  if (pass == 1 && D.qflag) return;
+  const ProbPtr P = ptrs[p];
+  const int L = D.l, tid = threadIdx.x;
+  cplx* G = P.R;
+  cplx* J = P.J;
+  double dm = 0.0;
+  for (int j = tid; j < L; j += blockDim.x) dm = fmax(dm, G[(size_t)j * L + j].x);
+  // block maximum through the sum helper's pattern
+  {
+    const int lane = tid & 31, warp = tid >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+    if (lane == 0) red[warp] = dm;
+    __syncthreads();
+    if (tid == 0) {
+      double m = 0.0;
+      for (int w = 0; w < nw; ++w) m = fmax(m, red[w]);
+      red[0] = m;
+      s_fail = !(m > 0.0) || !isfinite(m);
+    }
+    __syncthreads();
+    dm = red[0];
+  }
+  for (int j = 0; j < L && !s_fail; ++j) {
+    if (tid == 0) {
+      const double d = G[(size_t)j * L + j].x;
+      if (!(d > CQ_PIVOT * dm) || !isfinite(d)) {
+        s_fail = 1;
+      } else {
+        const double r = sqrt(d);
+        G[(size_t)j * L + j] = cmk(r, 0.0);
+        s_inv = 1.0 / r;
+      }
+    }
+    __syncthreads();
+    if (s_fail) break;
+    const double inv = s_inv;
+    for (int c = j + 1 + tid; c < L; c += blockDim.x) G[(size_t)c * L + j] = cscale(G[(size_t)c * L + j], inv);
+    __syncthreads();
+    // trailing update of the upper triangle: G[c1][c2] -= conj(R[j][c1]) R[j][c2], j < c1 <= c2
+    const int w = L - j - 1;
+    for (int e = tid; e < w * w; e += blockDim.x) {
+      const int c1 = j + 1 + e % w, c2 = j + 1 + e / w;
+      if (c1 > c2) continue;
+      const cplx a = G[(size_t)c1 * L + j], b = G[(size_t)c2 * L + j];
+      cplx& g = G[(size_t)c2 * L + c1];
+      g.x -= a.x * b.x + a.y * b.y;
+      g.y -= a.x * b.y - a.y * b.x;
+    }
+    __syncthreads();
+  }
+  const int fail = s_fail;
+  if (tid == 0) dims[p].qflag = fail ? 1 : (pass == 0 ? 0 : D.qflag);
+  if (fail) {  // identity factor: the products in between stay finite
+    for (int e = tid; e < L * L; e += blockDim.x) J[e] = cmk((e / L) == (e % L) ? 1.0 : 0.0, 0.0);
+    return;
+  }
+  // J = R^-1 by back substitution, one column per thread: R x = e_c
+  for (int c = tid; c < L; c += blockDim.x) {
+    cplx* x = J + (size_t)c * L;
+    for (int i = c + 1; i < L; ++i) x[i] = cmk(0.0, 0.0);
+    for (int i = c; i >= 0; --i) {
+      cplx s = cmk(i == c ? 1.0 : 0.0, 0.0);
+      for (int k = i + 1; k <= c; ++k) {
+        const cplx r = G[(size_t)k * L + i], v = x[k];
+        s.x -= r.x * v.x - r.y * v.y;
+        s.y -= r.x * v.y + r.y * v.x;
+      }
+      const double rii = G[(size_t)i * L + i].x;  // real and positive
+      x[i] = cscale(s, 1.0 / rii);
+    }
+  }
+}
+
+static cudaError_t chol_inv(Dims* dims, const ProbPtr* ptrs, int batch, int pass, cudaStream_t st) {
+  ProfScope ps("k_chol_inv", st);
+  k_chol_inv<<<batch, 256, 0, st>>>(dims, ptrs, pass);
+  return cudaGetLastError();
+}
+
+#define CQ_TRY(x)                     \
+  do {                                \
+    cudaError_t e_ = (x);             \
+    if (e_ != cudaSuccess) return e_; \
+  } while (0)
+
+cudaError_t run_cholqr_bh(Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, cudaStream_t st) {
+  CQ_TRY(launch_zgemm_df(G_G1, dims, ptrs, batch, cap, st));  // G1 = B B^H
+  CQ_TRY(chol_inv(dims, ptrs, batch, 0, st));                 // R1, J = R1^-1
+  CQ_TRY(launch_zgemm_df(G_Q1, dims, ptrs, batch, cap, st));  // Q1 = B^H R1^-1
+  CQ_TRY(launch_zgemm_df(G_G2, dims, ptrs, batch, cap, st));  // G2 = Q1^H Q1
+  CQ_TRY(chol_inv(dims, ptrs, batch, 1, st));                 // R2, J = R2^-1
+  CQ_TRY(launch_zgemm_df(G_QB, dims, ptrs, batch, cap, st));  // Qb = Q1 R2^-1
+  CQ_TRY(launch_zgemm_df(G_X, dims, ptrs, batch, cap, st));   // X = B Qb = Rb^H
+  // ill-conditioned instances: Householder QR of B^H (overwrites X and Qb)
+  return launch_qr(QR_BH, dims, ptrs, batch, st, 1);
+}
+
+}  // namespace tg

@@ -72,7 +72,11 @@ enum { NPART = 64 };
 // GEMM stages of the pipeline (op(A) op(B) -> C).
 enum GemmStage { G_Y0 = 0, G_YT = 1, G_Y = 2, G_BH = 3, G_U = 4, G_V = 5,
                  // accuracy check: Br = A Omega_r (into Y after the basis), C1 = Q^H Br, Dr = Q C1
-                 G_PR = 6, G_PQ = 7, G_PD = 8 };
+                 G_PR = 6, G_PQ = 7, G_PD = 8,
+                 // Cholesky QR of B^H (the mixed form, cholqr.cu): G1 = B B^H into R,
+                 // Q1 = B^H R1^-1 into omega, G2 = Q1^H Q1 into R, Qb = Q1 R2^-1 into Qt,
+                 // X = B Qb (= Rb^H) into R; the inverse factors come in J
+                 G_G1 = 9, G_Q1 = 10, G_G2 = 11, G_QB = 12, G_X = 13 };
 // QR stages: which buffer is factored and where Q goes.
 enum QrStage { QR_Y = 0, QR_YT = 1, QR_BH = 2 };
 
@@ -101,6 +105,11 @@ cudaError_t launch_qr(int stage, const Dims* dims, const ProbPtr* ptrs, int batc
 // its structure allows (the autotuner's choices)
 cudaError_t launch_qr_sized(int stage, const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap,
                            cudaStream_t st, int force = 0);
+// true when launch_qr_sized(stage, ..., force) runs the many-CTA form
+bool qr_multi_chosen(int stage, const Caps& cap, int batch, int force);
+// Cholesky QR (two passes) of B^H for well-conditioned instances, Householder
+// for the others (cholqr.cu); writes dims[p].qflag
+cudaError_t run_cholqr_bh(Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, cudaStream_t st);
 size_t qr_multi_scratch_r(int l);
 size_t qr_multi_scratch_j(int l);
 cudaError_t launch_jacobi(const Dims* dims, const ProbPtr* ptrs, int batch, int* status, cudaStream_t st);

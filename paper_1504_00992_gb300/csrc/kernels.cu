@@ -230,10 +230,15 @@ static cudaError_t launch_zgemm_df_stage(int rows, int cols, const Dims* dims, c
 
 cudaError_t launch_zgemm_df(int stage, const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap,
                             cudaStream_t st) {
-  ProfScope ps("k_zgemm_df[uv]", st);
+  ProfScope ps(stage == G_U || stage == G_V ? "k_zgemm_df[uv]" : "k_zgemm_df[cholqr]", st);
   switch (stage) {
     case G_U: return launch_zgemm_df_stage<G_U>(cap.m, cap.k, dims, ptrs, batch, st);
     case G_V: return launch_zgemm_df_stage<G_V>(cap.n, cap.k, dims, ptrs, batch, st);
+    case G_G1: return launch_zgemm_df_stage<G_G1>(cap.l, cap.l, dims, ptrs, batch, st);
+    case G_Q1: return launch_zgemm_df_stage<G_Q1>(cap.n, cap.l, dims, ptrs, batch, st);
+    case G_G2: return launch_zgemm_df_stage<G_G2>(cap.l, cap.l, dims, ptrs, batch, st);
+    case G_QB: return launch_zgemm_df_stage<G_QB>(cap.n, cap.l, dims, ptrs, batch, st);
+    case G_X: return launch_zgemm_df_stage<G_X>(cap.l, cap.l, dims, ptrs, batch, st);
   }
   return cudaErrorInvalidValue;
 }

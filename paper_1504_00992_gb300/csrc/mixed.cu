@@ -582,7 +582,12 @@ cudaError_t run_rrsvd_mixed(const Dims* dims, const ProbPtr* ptrs, int batch, co
   MX_TRY(qr_f32(mp.Yf, mp.Qf, m, l, batch, mp, s, dims, 0, st, kn.qr_threads));
   MX_TRY(launch_reorth(mp.Qf, mp.Df, dims, ptrs, m, l, batch, status, st));
   MX_TRY(launch_proj_oz(dims, ptrs, mp.Qf, mp.Df, mp.ad, mp.asc, mp.bd, mp.bsc, m, n, l, batch, err, st));  // B^H = A^H Q
-  MX_TRY(launch_qr_sized(QR_BH, dims, ptrs, batch, cap, st, kn.qrbh));
+  // QR of B^H: Cholesky QR where the one-CTA Householder would run (it falls
+  // back to Householder per ill-conditioned instance), else the size rule
+  if (kn.qrbh == 3 || (kn.qrbh == 0 && !qr_multi_chosen(QR_BH, cap, batch, 0)))
+    MX_TRY(run_cholqr_bh(const_cast<Dims*>(dims), ptrs, batch, cap, st));
+  else
+    MX_TRY(launch_qr_sized(QR_BH, dims, ptrs, batch, cap, st, kn.qrbh));
   MX_TRY(launch_jacobi_sized(dims, ptrs, batch, cap, status, st, kn.jac));
   MX_TRY(launch_zgemm_df(G_U, dims, ptrs, batch, cap, st));
   MX_TRY(launch_zgemm_df(G_V, dims, ptrs, batch, cap, st));

@@ -91,8 +91,10 @@ cudaError_t launch_proj_oz(const Dims* dims, const ProbPtr* ptrs, const float2* 
 // Launch choices of the mixed form that the autotuner may override (0 keeps
 // each size rule): tc_half = 1 splits the tensor-core products' columns over
 // two CTAs; qr_threads sets the CTA size of the blocked FP32 QRs (128, 256,
-// 512); qrbh and jac force the QR of B^H and the Jacobi SVD as in
-// launch_qr_sized / launch_jacobi_sized.
+// 512); qrbh forces the QR of B^H (1 one-CTA Householder, 2 many-CTA
+// Householder, 3 Cholesky QR with Householder for ill-conditioned instances;
+// the size rule takes the Cholesky QR wherever it would run the one-CTA
+// kernel); jac forces the Jacobi SVD as in launch_jacobi_sized.
 struct MixedKnobs {
   int tc_half, qr_threads, qrbh, jac;
 };

@@ -580,6 +580,11 @@ static bool qr_multi_fits(int M, int L, int batch) {
   return M >= QM_MIN_M && L >= QM_MIN_L && batch <= QM_MAX_BATCH;
 }
 
+bool qr_multi_chosen(int stage, const Caps& cap, int batch, int force) {
+  const int M = (stage == QR_Y) ? cap.m : cap.n;
+  return force == 2 ? qr_multi_fits(M, cap.l, 1) : (force == 0 && qr_multi_fits(M, cap.l, batch));
+}
+
 cudaError_t launch_qr_sized(int stage, const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap,
                             cudaStream_t st, int force) {
   const int M = (stage == QR_Y) ? cap.m : cap.n;

@@ -55,18 +55,33 @@ __device__ __forceinline__ GemmOp gemm_of(const Dims& D, const ProbPtr& P) {
     g.A = P.Q; g.ars = D.m; g.acs = 1;          // op(A)(i, k) = conj(Q[k][i])
     g.B = P.Y + (int64_t)D.l * D.m; g.brs = 1; g.bcs = D.m;
     g.C = P.R; g.crs = 1; g.ccs = D.l;
-  } else {  // G_PD: Dr = Q C1 (m x r)
+  } else if (STAGE == G_PD) {  // Dr = Q C1 (m x r)
     g.M = D.m; g.N = D.r; g.K = D.l;
     g.A = P.Q; g.ars = 1; g.acs = D.m;
     g.B = P.R; g.brs = 1; g.bcs = D.l;
     g.C = P.Dr; g.crs = 1; g.ccs = D.m;
+  } else if (STAGE == G_G1 || STAGE == G_G2 || STAGE == G_X) {
+    // l x l Gram-type products with the n x l column-major B^H (Yt), Q1
+    // (omega) or Qb (Qt): G1 = Yt^H Yt, G2 = omega^H omega, X = Yt^H Qt
+    const cplx* L = (STAGE == G_G2) ? P.omega : P.Yt;
+    const cplx* Rt = (STAGE == G_G1) ? P.Yt : (STAGE == G_G2 ? P.omega : P.Qt);
+    g.M = D.l; g.N = D.l; g.K = D.n;
+    g.A = L; g.ars = D.n; g.acs = 1;             // op(A)(i, k) = conj(L[k][i])
+    g.B = Rt; g.brs = 1; g.bcs = D.n;
+    g.C = P.R; g.crs = 1; g.ccs = D.l;
+  } else {  // G_Q1 = Yt J, G_QB = omega J: n x l times the l x l inverse factor
+    g.M = D.n; g.N = D.l; g.K = D.l;
+    g.A = (STAGE == G_Q1) ? P.Yt : P.omega; g.ars = 1; g.acs = D.n;
+    g.B = P.J; g.brs = 1; g.bcs = D.l;
+    g.C = (STAGE == G_Q1) ? P.omega : P.Qt; g.crs = 1; g.ccs = D.n;
   }
   return g;
 }
 
 template <int STAGE>
 struct StageFlags {
-  static constexpr bool conjA = (STAGE == G_YT || STAGE == G_BH || STAGE == G_PQ);
+  static constexpr bool conjA =
+      (STAGE == G_YT || STAGE == G_BH || STAGE == G_PQ || STAGE == G_G1 || STAGE == G_G2 || STAGE == G_X);
   static constexpr bool conjC = (STAGE == G_V);
 };
 
