@@ -45,6 +45,16 @@ CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.ac
                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
 
+# arithmetic of each form of the single-bond measurement
+DTYPES = {"fp64": "f64", "tf32": "tf32+f32+bf16x6+df64+f64", "bf16": "bf16+tf32+f32+bf16x6+df64+f64"}
+_MIXED_TAIL = ("3xTF32 refinement round, FP32 Householder QRs, FP64-accurate re-orthonormalisation of the last "
+               "Q, projection B = Q^H theta on the tensor cores from exact BF16 digit splits (FP64-accurate), "
+               "two double-float Cholesky QR passes of B^H, FP64 Jacobi SVD, double-float U and V")
+FORMS = {"fp64": "plain path, every step in FP64",
+         "tf32": "TF32 sketch and power rounds before the last, " + _MIXED_TAIL,
+         "bf16": "BF16 sketch and power rounds before the last, " + _MIXED_TAIL}
+
+
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -52,7 +62,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--batch", type=int, default=152)
-    ap.add_argument("--precision", default="both", choices=["both", "tf32", "fp64"])
+    ap.add_argument("--precision", default="all", choices=["all", "both", "tf32", "bf16", "fp64"],
+                    help="forms of the single-bond measurement (all: fp64, tf32 and bf16; both: fp64 and tf32)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -242,7 +253,7 @@ def run_tebd_c1(B, I, torch):
 
 def measure(B, torch, dev, theta, sig, batch, prec, args, rank, world, local):
     """Device-timed steps of one precision form; inputs resident in HBM."""
-    code = B.TEBD_PREC_TF32 if prec == "tf32" else B.TEBD_PREC_FP64
+    code = {"tf32": B.TEBD_PREC_TF32, "bf16": B.TEBD_PREC_BF16}.get(prec, B.TEBD_PREC_FP64)
     plan = B.rrsvd_plan_create(M, N_, K_MAX, P_OS, Q_PI, batch, code, SEED)
     k, l = B.rrsvd_plan_dims(plan)
     wsb = B.rrsvd_workspace_size(plan)
@@ -395,6 +406,9 @@ def roofline(res, batch):
     oz_peak = bf16 * 8.0 / OZ_BF16_FLOP_PER_CMAC
     oz_src = ("measured sustained BF16 %.0f TFLOP/s (MEASURED_PEAKS.json) x 8 FP64-equivalent flop / %d BF16 flop "
               "per complex multiply-add of the digit products" % (bf16, OZ_BF16_FLOP_PER_CMAC))
+    tf32 = bf16 * 1.1 / 2.25
+    tf32_src = "measured sustained BF16 %.0f TFLOP/s (MEASURED_PEAKS.json) x nominal TF32:BF16 ratio 1.1:2.25" % bf16
+    bf16_src = "measured sustained BF16 %.0f TFLOP/s (MEASURED_PEAKS.json)" % bf16
     # per launch: (algorithmic flops, bound, peak, peak source, file, flops
     # counted in the kernel's own unit when it differs from the algorithmic
     # FP64-equivalent figure)
@@ -406,6 +420,11 @@ def roofline(res, batch):
         "k_zgemm[uv]": (8.0 * M * l * k * batch, "alu", fp64_peak, fp64_src, "kernels.cu"),
         "k_zgemm_df[project]": (8.0 * M * N_ * l * batch, "alu", df_peak, df_src, "df_proj.cu"),
         "k_oz_proj[project]": (8.0 * M * N_ * l * batch, "tensor", oz_peak, oz_src, "oz_proj.cu"),
+        # the sketch products (one complex m x n x l product per launch; the
+        # 3xTF32 launch does three TF32 products for the same algorithmic flops)
+        "k_tc_gemm[tf32]": (8.0 * M * N_ * l * batch, "tensor", tf32, tf32_src, "tc_gemm.cuh"),
+        "k_tc_gemm[3xtf32]": (8.0 * M * N_ * l * batch, "tensor", tf32, tf32_src, "tc_gemm.cuh"),
+        "k_tc_gemm[bf16]": (8.0 * M * N_ * l * batch, "tensor", bf16, bf16_src, "tc_gemm.cuh"),
     }
     if dom not in per_launch:
         return None
@@ -714,7 +733,7 @@ def main():
     for t in range(batch):
         theta[t].copy_(pool_dev[t % POOL])
     del pool_dev
-    precs = ["fp64", "tf32"] if args.precision == "both" else [args.precision]
+    precs = {"all": ["fp64", "tf32", "bf16"], "both": ["fp64", "tf32"]}.get(args.precision, [args.precision])
     results = {p: measure(B, torch, dev, theta, sig, batch, p, args, rank, world, local) for p in precs}
     # headline: the fastest form that meets the 1e-8 truncation-accuracy bar
     ok = [r for r in results.values() if r["sig_err"] <= 1e-8 and r["excess_err"] <= 1e-8]
@@ -752,14 +771,10 @@ def main():
         line = {"metric": METRIC, "value": head["value"], "unit": "bond updates/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms"] / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "tf32+f32+df64+f64" if head["prec"] == "tf32" else "f64", "data": "synthetic",
+                "dtype": DTYPES[head["prec"]], "data": "synthetic",
                 "config": {"workload": "single-bond stress: RRSVD truncation of given 2000x2000 complex128 theta, "
                                        "sigma_k = exp(-(k-1)/15), k=100, p=20, q=2 (theta given directly)",
-                           "precision": head["prec"] + (" (TF32 sketch and power round, 3xTF32 refinement round, "
-                                                        "FP32 Householder QRs, FP64-accurate re-orthonormalisation "
-                                                        "of the last Q, double-float projection and U/V, FP64 QR "
-                                                        "of B^H and Jacobi SVD)" if head["prec"] == "tf32"
-                                                        else " (plain path)"),
+                           "precision": head["prec"] + " (" + FORMS[head["prec"]] + ")",
                            "batch_per_gpu": batch, "distinct_theta": POOL, "parallelism": f"replicas x{world}",
                            "l2": "inputs larger than L2: %.1f GB of theta read per step" % (batch * M * N_ * 16 / 1e9),
                            "max_abs_sigma_err_vs_exact": head["sig_err"],

@@ -61,18 +61,30 @@ enum {
   TEBD_ESTATE = -7     /* call out of order (e.g. a step before its gates) */
 };
 
-/* Arithmetic of the RRSVD sketch (Alg. 1 GEMMs).
+/* Arithmetic of the RRSVD (Alg. 1 and the steps after it).
  *   TEBD_PREC_FP64: the plain path, every step in FP64.
- *   TEBD_PREC_TF32: Y0 = A Omega and power rounds 1..q-1 on the tensor cores
- *     in TF32 with FP32 accumulation and FP32 QR; power round q (Y0 when
- *     q = 0) as the refinement pass in split 3xTF32 products (FP32-level
- *     accuracy); the last basis re-orthonormalised FP64-accurately (FP32
- *     QR and a double-float Loewdin correction);
- *     B = Q^H A, U and V FP64-accurate in double-float arithmetic; the QR
- *     of B^H, the Jacobi SVD and lambda in FP64.  Omega comes from the same
- *     Philox words by an FP32 Box-Muller.  Standalone RRSVD plans and TEBD
- *     handles (not with tebd_record or autotune). */
-enum { TEBD_PREC_FP64 = 0, TEBD_PREC_TF32 = 2 };
+ *   TEBD_PREC_TF32: the mixed form.  Y0 = A Omega and power rounds 1..q-1
+ *     on the tensor cores in TF32 with FP32 accumulation and FP32 QR;
+ *     power round q (Y0 when q = 0) as the refinement pass in split 3xTF32
+ *     products (FP32-level accuracy); the last basis re-orthonormalised
+ *     FP64-accurately (FP32 QR and a double-float Loewdin correction);
+ *     B = Q^H A on the tensor cores from exact BF16 digit splits of Q and
+ *     A (products exact in FP32, digit levels summed in double-float:
+ *     FP64-level accuracy); the QR of B^H by two Cholesky QR passes in
+ *     double-float arithmetic (Householder QR in FP64 for an instance whose
+ *     Gram matrix is too ill-conditioned); the Jacobi SVD, U, V and lambda
+ *     FP64-accurate.  Omega comes from the same Philox words by an FP32
+ *     Box-Muller.
+ *   TEBD_PREC_BF16: the mixed form with the products before the refinement
+ *     round (Y0 and power rounds 1..q-1) in BF16 with FP32 accumulation,
+ *     from BF16 roundings of theta and of the FP32 Omega / bases; the
+ *     refinement round and everything after it as TEBD_PREC_TF32.  With
+ *     q = 0 it is TEBD_PREC_TF32.  The subspace the refinement round starts
+ *     from is perturbed at the BF16 level (2^-9 relative), which the power
+ *     iteration damps like any other sketch error.
+ * Both mixed forms: standalone RRSVD plans and TEBD handles, autotune
+ * allowed, not tebd_record. */
+enum { TEBD_PREC_FP64 = 0, TEBD_PREC_TF32 = 2, TEBD_PREC_BF16 = 3 };
 
 /* ------------------------------------------------------------------------
  * TEBD handle: an N-site chain in Vidal form resident on the device.
@@ -97,7 +109,7 @@ typedef struct {
   int p;                /* RRSVD oversampling, >= 0 */
   int q;                /* RRSVD power iterations, >= 0 */
   uint64_t seed;        /* Philox key word 0 */
-  int precision;        /* TEBD_PREC_* (TF32: every bond update in the mixed form) */
+  int precision;        /* TEBD_PREC_* (TF32, BF16: every bond update in a mixed form) */
   double sv_cutoff;     /* keep s_i > sv_cutoff * s_1 among the first k; <= 0 selects 1e-14 */
   int chain;            /* chain index entering the Philox counter (default 0); with
                            tebd_create_multi, chain c uses chain + c */
@@ -146,13 +158,12 @@ int tebd_create_ex(const tebd_desc_t* desc, tebd_t* out);
  * and precision must agree, use_graph / autotune / workspace_budget are read
  * from descs[0].  tebd_step_even/odd then update the bonds of that parity of
  * every chain in one launch sequence (in waves when a workspace budget is
- * set; with TEBD_PREC_TF32 the budget also covers the FP32 arrays, laid out
+ * set; with a mixed form the budget also covers the FP32 arrays, laid out
  * at each wave's largest bond, and the bonds are grouped by shape); the
  * per-chain calls (state, gates, expect, lambda, weights, MPS) act on the
  * chain chosen by tebd_select_chain (default 0).
- * Errors: TEBD_EINVAL (n_chains < 1, inconsistent p/q/seed/precision,
- * autotune with TEBD_PREC_TF32, as tebd_create_ex), TEBD_ENOMEM,
- * TEBD_ECUDA. */
+ * Errors: TEBD_EINVAL (n_chains < 1, inconsistent p/q/seed/precision, as
+ * tebd_create_ex), TEBD_ENOMEM, TEBD_ECUDA. */
 int tebd_create_multi(int n_chains, const tebd_desc_t* descs, tebd_t* out);
 int tebd_num_chains(tebd_t h, int* out);
 int tebd_select_chain(tebd_t h, int chain);
@@ -273,7 +284,7 @@ int tebd_bond_weights(tebd_t h, double* out);
  * Schmidt values, gates and bond dimensions (one allocation per sweep,
  * freed by the next tebd_record(h, 1) or tebd_destroy).  Turning it on
  * clears earlier checkpoints.  Errors: TEBD_ENOTIMPL (several chains, or a
- * TEBD_PREC_TF32 handle: the reverse pass differentiates the FP64 form),
+ * mixed-form handle: the reverse pass differentiates the FP64 form),
  * TEBD_ENOMEM. */
 int tebd_record(tebd_t h, int on);
 
@@ -306,9 +317,9 @@ typedef struct rrsvd_plan_s* rrsvd_plan_t;
 /* Plan for `batch` complex m x n matrices truncated to k = min(k_max, m, n)
  * singular triplets with sketch width l = min(k + p, m, n) and q power
  * iterations.  Instance t of a call uses Philox counter chain = chain0 + t,
- * bond 0, sweep 0.  precision: TEBD_PREC_FP64 or TEBD_PREC_TF32 (the
- * workspace then also holds TF32 copies of theta, about 4 m n 8 bytes per
- * instance).  Errors: TEBD_EINVAL (m, n, batch < 1, k_max < 1, p < 0,
+ * bond 0, sweep 0.  precision: TEBD_PREC_FP64, TEBD_PREC_TF32 or
+ * TEBD_PREC_BF16 (the workspace then also holds FP32 copies of theta, about
+ * 4 m n 8 bytes per instance, and with BF16 half as much again).  Errors: TEBD_EINVAL (m, n, batch < 1, k_max < 1, p < 0,
  * q < 0), TEBD_ENOTIMPL (precision, or l > 512). */
 int rrsvd_plan_create(int m, int n, int k_max, int p, int q, int batch, int precision, uint64_t seed,
                       rrsvd_plan_t* out);
@@ -441,9 +452,9 @@ int tebd_philox4x64_10(const uint64_t* counters, int64_t count, uint64_t key0, u
  * as described at the top of this header.
  *   TEBD_PREC_FP64: complex128 (2 doubles per element), the Omega of the
  *     FP64 form: u = ((w >> 12) + 0.5) 2^-52, Box-Muller in FP64.
- *   TEBD_PREC_TF32: complex64 (2 floats per element), the Omega of the mixed
- *     form before its TF32 rounding: u = ((w >> 40) + 0.5) 2^-24, Box-Muller
- *     in FP32.
+ *   TEBD_PREC_TF32, TEBD_PREC_BF16: complex64 (2 floats per element), the
+ *     Omega of the mixed forms before their TF32 or BF16 rounding:
+ *     u = ((w >> 40) + 0.5) 2^-24, Box-Muller in FP32.
  * Standalone plans use bond 0, sweep 0 and chain chain0 + instance; TEBD
  * handles use the bond index, the handle's sweep count at the step and the
  * chain index.  Errors: TEBD_EINVAL (negative size or index, NULL out with

@@ -25,6 +25,7 @@ TEBD_ENOTIMPL = -6
 TEBD_ESTATE = -7
 TEBD_PREC_FP64 = 0
 TEBD_PREC_TF32 = 2
+TEBD_PREC_BF16 = 3
 
 _CODES = {0: "TEBD_OK", -1: "TEBD_EINVAL", -2: "TEBD_ENOMEM", -3: "TEBD_ECUDA", -4: "TEBD_ENUMERIC",
           -5: "TEBD_ETIMEOUT", -6: "TEBD_ENOTIMPL", -7: "TEBD_ESTATE"}

@@ -25,6 +25,8 @@ using namespace tg;
 namespace {
 
 const size_t ALIGN = 256;
+// the precisions that run the mixed form (mixed.cu)
+inline bool prec_mixed(int p) { return p == TEBD_PREC_TF32 || p == TEBD_PREC_BF16; }
 inline size_t align_up(size_t x) { return (x + ALIGN - 1) & ~(ALIGN - 1); }
 
 struct ErrState {
@@ -400,7 +402,7 @@ static int plan_handle(tebd_s* h, int n_chains, const tebd_desc_t* descs, Handle
   if (n_chains < 1 || !descs) return TEBD_EINVAL;
   const tebd_desc_t& d0 = descs[0];
   if (d0.p < 0 || d0.q < 0) return TEBD_EINVAL;
-  if (d0.precision != TEBD_PREC_FP64 && d0.precision != TEBD_PREC_TF32) return TEBD_ENOTIMPL;
+  if (d0.precision != TEBD_PREC_FP64 && !prec_mixed(d0.precision)) return TEBD_ENOTIMPL;
   if ((d0.alloc == nullptr) != (d0.release == nullptr)) return TEBD_EINVAL;
   if (d0.fused < -1 || d0.fused > 1) return TEBD_EINVAL;
   for (int c = 0; c < n_chains; ++c) {
@@ -480,7 +482,8 @@ static int plan_handle(tebd_s* h, int n_chains, const tebd_desc_t* descs, Handle
   std::vector<WsLayout>* lay = lay_plan.lay;
   std::vector<size_t> pbytes[2];
   int max_batch = 0;
-  const bool tf32 = h->precision == TEBD_PREC_TF32;
+  const bool tf32 = prec_mixed(h->precision);
+  const int bf16 = h->precision == TEBD_PREC_BF16;
   size_t mixed_max = 0;
   auto bond_caps = [&](const ChainH& C, int b, int& mc, int& nc, int& kc, int& lc) {
     mc = C.d[b] * C.cap_ext[b];
@@ -532,7 +535,7 @@ static int plan_handle(tebd_s* h, int n_chains, const tebd_desc_t* descs, Handle
       cp.m = std::max(cp.m, mc); cp.n = std::max(cp.n, nc); cp.k = std::max(cp.k, kc); cp.l = std::max(cp.l, lc);
       cp.cl = std::max(cp.cl, C.cap_ext[b]); cp.cr = std::max(cp.cr, C.cap_ext[b + 2]);
       cp.dl = std::max(cp.dl, C.d[b]); cp.dr = std::max(cp.dr, C.d[b + 1]);
-      const size_t mix = tf32 ? mixed_bytes(mixed_sizes(cp.m, cp.n, cp.k, cp.l), w.count + 1) : 0;
+      const size_t mix = tf32 ? mixed_bytes(mixed_sizes(cp.m, cp.n, cp.k, cp.l, bf16), w.count + 1) : 0;
       if (w.count > 0 && budget > 0 && acc + pbytes[par][i] + mix > budget) {
         ps.waves.push_back(w);
         ws_max = std::max(ws_max, acc);
@@ -553,7 +556,7 @@ static int plan_handle(tebd_s* h, int n_chains, const tebd_desc_t* descs, Handle
     }
     if (tf32)
       for (Wave& wv : ps.waves) {
-        wv.ms = mixed_sizes(wv.cap.m, wv.cap.n, wv.cap.k, wv.cap.l);
+        wv.ms = mixed_sizes(wv.cap.m, wv.cap.n, wv.cap.k, wv.cap.l, bf16);
         mixed_max = std::max(mixed_max, mixed_bytes(wv.ms, wv.count));
       }
   }
@@ -593,7 +596,7 @@ extern "C" int tebd_plan_query(int n_chains, const tebd_desc_t* descs, size_t* a
 static bool bind_arena(tebd_s* h) {
   const HandlePlan& L = h->plan;
   char* A = h->arena;
-  const bool tf32 = h->precision == TEBD_PREC_TF32;
+  const bool tf32 = prec_mixed(h->precision);
   h->one_lam = (double*)(A + L.one_off);
   h->status = (int*)(A + L.st_off);
   h->wacc = (double*)(A + L.wacc_off);
@@ -711,7 +714,7 @@ extern "C" int tebd_create_multi(int n_chains, const tebd_desc_t* descs, tebd_t*
     h->arena = (char*)blk;
   }
   if (cudaMemset(h->arena, 0, h->plan.ws_off) != cudaSuccess) { tebd_free(h); return TEBD_ECUDA; }
-  if (h->precision == TEBD_PREC_TF32)
+  if (prec_mixed(h->precision))
     for (int par = 0; par < 2; ++par)
       for (const Wave& w : h->par[par].waves)
         if (mixed_prepare(w.cap) != cudaSuccess) { cudaGetLastError(); tebd_free(h); return TEBD_ECUDA; }
@@ -738,7 +741,7 @@ extern "C" int tebd_create_multi(int n_chains, const tebd_desc_t* descs, tebd_t*
         if (tune_wave(h, h->par[par], w, h->stream, scratch, h->p, d0.fused) != 0) { tebd_free(h); return TEBD_ECUDA; }
     if (cudaDeviceSynchronize() != cudaSuccess) { tebd_free(h); return TEBD_ECUDA; }
   }
-  if (d0.autotune && h->precision == TEBD_PREC_TF32) {
+  if (d0.autotune && prec_mixed(h->precision)) {
     // the mixed form's launch choices, timed on synthetic theta at each
     // wave's capacity sizes (cached per wave shape for the process)
     Dims* scratch = (Dims*)(h->arena + h->plan.desc_off + 2 * h->plan.desc_per);
@@ -769,7 +772,7 @@ extern "C" int tebd_create_multi(int n_chains, const tebd_desc_t* descs, tebd_t*
         const MixedPtrs mp = mixed_carve(h->mixed, w.ms, w.count);
         auto run = [&](const MixedKnobs& k) {
           return run_rrsvd_mixed(scratch, ps.ptrs + w.first, w.count, w.cap, mp, h->q, h->seed, 0, 0, -1, h->status,
-                                 h->tcerr, h->stream, h->sweep_dev, &k);
+                                 h->tcerr, h->stream, h->sweep_dev, &k, h->precision == TEBD_PREC_BF16);
         };
         float ms[2] = {0.f, 0.f};
         if (!ok || tune_knobs(run, h->stream, w.cap, w.count, w.mk, ms) != 0) { tebd_free(h); return TEBD_ECUDA; }
@@ -1066,7 +1069,7 @@ static cudaError_t enqueue_sweep(tebd_t h, int parity) {
       continue;
     }
     if ((e = launch_plan(ptrs, dims, w.count, h->p, h->stream)) != cudaSuccess) return e;
-    if (h->precision == TEBD_PREC_TF32) {
+    if (prec_mixed(h->precision)) {
       // bonds of large local dimensions: contraction and gate as double-float GEMMs
       if ((e = launch_theta(dims, ptrs, w.count, w.cap, h->stream, 0, 1)) != cudaSuccess) return e;
       if ((e = launch_theta_df(dims, ptrs, w.count, w.cap, h->stream)) != cudaSuccess) return e;
@@ -1075,10 +1078,10 @@ static cudaError_t enqueue_sweep(tebd_t h, int parity) {
       if ((e = launch_theta(dims, ptrs, w.count, w.cap, h->stream)) != cudaSuccess) return e;
       if ((e = launch_gate_gemm(dims, ptrs, w.count, w.cap, h->stream)) != cudaSuccess) return e;
     }
-    if (h->precision == TEBD_PREC_TF32) {
+    if (prec_mixed(h->precision)) {
       const MixedPtrs mp = mixed_carve(h->mixed, w.ms, w.count);
       if ((e = run_rrsvd_mixed(dims, ptrs, w.count, w.cap, mp, h->q, h->seed, 0, 0, -1, h->status, h->tcerr,
-                               h->stream, h->sweep_dev, &w.mk)) != cudaSuccess)
+                               h->stream, h->sweep_dev, &w.mk, h->precision == TEBD_PREC_BF16)) != cudaSuccess)
         return e;
     } else if ((e = run_rrsvd(dims, ptrs, w.count, w.cap, h->q, h->seed, 0, 0, -1, h->status, h->stream,
                               h->sweep_dev, tuned ? w.tiles : nullptr)) != cudaSuccess) {
@@ -1517,7 +1520,7 @@ extern "C" int rrsvd_plan_create_ex(int m, int n, int k_max, int p, int q, int b
   if (!out) return TEBD_EINVAL;
   *out = nullptr;
   if (m < 1 || n < 1 || k_max < 1 || p < 0 || q < 0 || batch < 1 || check_r < 0) return TEBD_EINVAL;
-  if (precision != TEBD_PREC_FP64 && precision != TEBD_PREC_TF32) return TEBD_ENOTIMPL;
+  if (precision != TEBD_PREC_FP64 && !prec_mixed(precision)) return TEBD_ENOTIMPL;
   if (check_r > 0 && (precision != TEBD_PREC_FP64 || !(check_eps > 0.0))) return check_eps > 0.0 ? TEBD_ENOTIMPL : TEBD_EINVAL;
   rrsvd_plan_s* P = new rrsvd_plan_s();
   P->m = m; P->n = n; P->p = p; P->q = q; P->batch = batch; P->precision = precision; P->seed = seed;
@@ -1540,8 +1543,8 @@ extern "C" int rrsvd_plan_create_ex(int m, int n, int k_max, int p, int q, int b
   P->lay = ws_layout(m, n, P->k, P->l, true, true, check_r);
   P->per = P->lay.total;
   P->ws_bytes = P->per * (size_t)batch;
-  if (precision == TEBD_PREC_TF32) {
-    P->ms = mixed_sizes(m, n, P->k, P->l);
+  if (prec_mixed(precision)) {
+    P->ms = mixed_sizes(m, n, P->k, P->l, precision == TEBD_PREC_BF16);
     P->mixed_off = P->ws_bytes;
     P->ws_bytes += mixed_bytes(P->ms, batch);
   }
@@ -1637,10 +1640,10 @@ extern "C" int rrsvd_execute(rrsvd_plan_t P, const double* theta, int64_t chain0
                                      st));
     return TEBD_OK;
   }
-  if (P->precision == TEBD_PREC_TF32) {
+  if (prec_mixed(P->precision)) {
     const MixedPtrs mp = mixed_carve((char*)workspace + P->mixed_off, P->ms, P->batch);
     CU_OR(P, run_rrsvd_mixed(P->dims, P->ptrs, P->batch, P->cap, mp, P->q, P->seed, 0, chain0, 1, P->status,
-                             P->tcerr, st, nullptr, &P->mk));
+                             P->tcerr, st, nullptr, &P->mk, P->precision == TEBD_PREC_BF16));
   } else {
     CU_OR(P, run_rrsvd(P->dims, P->ptrs, P->batch, P->cap, P->q, P->seed, 0, chain0, 1, P->status, st, nullptr,
                        P->tuned ? P->tiles : nullptr));
@@ -1723,11 +1726,11 @@ extern "C" int rrsvd_plan_autotune(rrsvd_plan_t P, const double* theta, void* wo
                                                      (const cplx*)theta, (size_t)P->m * P->n, nullptr, 0, nullptr, 0,
                                                      nullptr, 0, 0, 0, 0, nullptr);
   CU_OR(P, cudaGetLastError());
-  if (P->precision == TEBD_PREC_TF32) {
+  if (prec_mixed(P->precision)) {
     const MixedPtrs mp = mixed_carve((char*)workspace + P->mixed_off, P->ms, P->batch);
     auto run = [&](const MixedKnobs& k) {
       return run_rrsvd_mixed(P->dims, P->ptrs, P->batch, P->cap, mp, P->q, P->seed, 0, 0, 1, P->status, P->tcerr, st,
-                             nullptr, &k);
+                             nullptr, &k, P->precision == TEBD_PREC_BF16);
     };
     float ms[2] = {0.f, 0.f};
     if (tune_knobs(run, st, P->cap, P->batch, P->mk, ms) != 0) {

@@ -38,6 +38,12 @@
 
 namespace tg {
 
+// FP32 -> BF16 bits, round to nearest even (finite inputs)
+__device__ __forceinline__ unsigned bf16_rn(float x) {
+  const unsigned u = __float_as_uint(x);
+  return (u + 0x7FFFu + ((u >> 16) & 1u)) >> 16;
+}
+
 __device__ __forceinline__ float tf32_rna(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
@@ -67,9 +73,10 @@ __device__ __forceinline__ void df_add2(float& h, float& l, float oh, float ol) 
 
 __global__ void __launch_bounds__(256) k_conv_theta(const MixedPtrs mp, const Dims* __restrict__ dims,
                                                     const ProbPtr* __restrict__ ptrs, int mc, int nc, int K1, int K2,
-                                                    int want_lo) {
+                                                    int want_lo, int K1b, int K2b) {
   __shared__ float2 tile[32][33];  // TF32 hi and remainder computed once per element
   __shared__ float2 tlo[32][33];
+  __shared__ unsigned tb16[32][33];  // BF16 (Re, Im) pairs of the BF16 copies
   __shared__ float red[16];
   const int z = blockIdx.z;
   const Dims D = dims[z];
@@ -82,6 +89,8 @@ __global__ void __launch_bounds__(256) k_conv_theta(const MixedPtrs mp, const Di
   float2* ah = reinterpret_cast<float2*>(mp.tha_hi + (size_t)z * nc * K2);
   float2* al = reinterpret_cast<float2*>(mp.tha_lo + (size_t)z * nc * K2);
   float4* dd = mp.thd ? mp.thd + (size_t)z * mc * nc : nullptr;
+  unsigned* fb = mp.thf_b ? reinterpret_cast<unsigned*>(mp.thf_b + (size_t)z * mc * K1b) : nullptr;
+  unsigned* ab = mp.tha_b ? reinterpret_cast<unsigned*>(mp.tha_b + (size_t)z * nc * K2b) : nullptr;
   const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   float sh = 0.f, sl = 0.f;  // double-float sum of |theta|^2 over this thread's elements
@@ -95,6 +104,10 @@ __global__ void __launch_bounds__(256) k_conv_theta(const MixedPtrs mp, const Di
     const float lr = tf32_rna((xh - hr) + xl), lm = tf32_rna((yh - hm) + yl);
     tile[i][tx] = make_float2(hr, hm);
     tlo[i][tx] = make_float2(lr, lm);
+    if (fb) {
+      tb16[i][tx] = bf16_rn(xh) | (bf16_rn(-yh) << 16);  // adjoint entry conj(theta), read transposed below
+      if (r < mc && c < K1b / 2) fb[(int64_t)r * (K1b / 2) + c] = bf16_rn(xh) | (bf16_rn(yh) << 16);
+    }
     if (r < mc && c < half1) {
       fh[(int64_t)r * half1 + c] = make_float2(hr, hm);
       if (want_lo) fl[(int64_t)r * half1 + c] = make_float2(lr, lm);
@@ -128,6 +141,7 @@ __global__ void __launch_bounds__(256) k_conv_theta(const MixedPtrs mp, const Di
       ah[(int64_t)c * half2 + r] = make_float2(h.x, -h.y);
       if (want_lo) al[(int64_t)c * half2 + r] = make_float2(l.x, -l.y);
     }
+    if (ab && c < nc && r < K2b / 2) ab[(int64_t)c * (K2b / 2) + r] = tb16[tx][i];
   }
 }
 
@@ -214,6 +228,55 @@ __global__ void k_conv_bt(const float2* __restrict__ X, const Dims* __restrict__
       reinterpret_cast<float2*>(bl + (size_t)(2 * c) * Kp)[j] = al;
       reinterpret_cast<float2*>(bl + (size_t)(2 * c + 1) * Kp)[j] = bl2;
     }
+  }
+}
+
+// BF16 forms of k_omega_bt and k_conv_bt (the products before the refinement
+// round of TEBD_PREC_BF16): Bt (Np x Kp BF16) from Omega or from X.
+__global__ void k_omega_bt_bf16(uint16_t* bt_b, const Dims* __restrict__ dims, int Np, int Kp, uint64_t seed,
+                                uint64_t sweep, int64_t chain0, int chain_stride, const uint64_t* __restrict__ sweep_dev) {
+  const int z = blockIdx.y;
+  const Dims D = dims[z];
+  if (!D.active) return;
+  const int n = D.n, l = D.l;
+  unsigned* bt = reinterpret_cast<unsigned*>(bt_b + (size_t)z * Np * Kp);
+  const int half = Kp / 2;
+  const int64_t total = (int64_t)(Np / 2) * half;
+  const uint64_t chain = chain_stride >= 0 ? (uint64_t)(chain0 + (int64_t)z * chain_stride) : (uint64_t)D.chain;
+  if (sweep_dev) sweep = *sweep_dev;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e / half), j = (int)(e % half);
+    unsigned a = 0, b = 0;
+    if (c < l && j < n) {
+      const float2 w = gauss_c_f32((uint64_t)j * l + c, (uint64_t)D.bond, sweep, chain, seed);
+      a = bf16_rn(w.x) | (bf16_rn(-w.y) << 16);
+      b = bf16_rn(w.y) | (bf16_rn(w.x) << 16);
+    }
+    bt[(size_t)(2 * c) * half + j] = a;
+    bt[(size_t)(2 * c + 1) * half + j] = b;
+  }
+}
+
+__global__ void k_conv_bt_bf16(const float2* __restrict__ X, const Dims* __restrict__ dims, uint16_t* bt_b, int Kc,
+                               int lc, int Np, int Kp) {
+  const int z = blockIdx.y;
+  const Dims D = dims[z];
+  if (!D.active) return;
+  const int l = D.l;
+  const float2* x = X + (size_t)z * Kc * lc;
+  unsigned* bt = reinterpret_cast<unsigned*>(bt_b + (size_t)z * Np * Kp);
+  const int half = Kp / 2;
+  const int64_t total = (int64_t)(Np / 2) * half;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e / half), j = (int)(e % half);
+    unsigned a = 0, b = 0;
+    if (c < l && j < Kc) {
+      const float2 v = x[(int64_t)c * Kc + j];
+      a = bf16_rn(v.x) | (bf16_rn(-v.y) << 16);
+      b = bf16_rn(v.y) | (bf16_rn(v.x) << 16);
+    }
+    bt[(size_t)(2 * c) * half + j] = a;
+    bt[(size_t)(2 * c + 1) * half + j] = b;
   }
 }
 
@@ -376,24 +439,29 @@ static EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// 3-D map over (K-padded row, row, instance) of FP32 data with a box of
-// 32 x box_rows x 1 and 128-byte swizzle.
-static bool make_map(CUtensorMap* m, const float* base, int Kp, int rows, int batch, int box_rows) {
+// 3-D map over (K-padded row, row, instance) of FP32 (or BF16) data with a
+// box of one 128-byte row segment x box_rows x 1 and 128-byte swizzle.
+static bool make_map(CUtensorMap* m, const void* base, int Kp, int rows, int batch, int box_rows, bool bf16 = false) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return false;
+  const cuuint64_t es_b = bf16 ? 2 : 4;
   cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)batch};
-  cuuint64_t strides[2] = {(cuuint64_t)Kp * 4, (cuuint64_t)rows * Kp * 4};
-  cuuint32_t box[3] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows, 1};
+  cuuint64_t strides[2] = {(cuuint64_t)Kp * es_b, (cuuint64_t)rows * Kp * es_b};
+  cuuint32_t box[3] = {(cuuint32_t)(128 / es_b), (cuuint32_t)box_rows, 1};
   cuuint32_t es[3] = {1, 1, 1};
-  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)base, dims, strides, box, es,
+  return enc(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)base, dims,
+             strides, box, es,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-MixedSizes mixed_sizes(int m, int n, int k, int l) {
+MixedSizes mixed_sizes(int m, int n, int k, int l, int bf16) {
   MixedSizes s;
+  s.bf16 = bf16 ? 1 : 0;
   s.K1 = ((2 * n + TC_BK - 1) / TC_BK) * TC_BK;
   s.K2 = ((2 * m + TC_BK - 1) / TC_BK) * TC_BK;
+  s.K1b = ((2 * n + 63) / 64) * 64;
+  s.K2b = ((2 * m + 63) / 64) * 64;
   s.Np = ((2 * l + 15) / 16) * 16;
   s.BN = s.Np <= TC_MAXBN ? s.Np : TC_MAXBN;
   const int Kmax = s.K1 > s.K2 ? s.K1 : s.K2;
@@ -411,11 +479,17 @@ MixedSizes mixed_sizes(int m, int n, int k, int l) {
   s.bsc = oz_scales_bytes(n, m);
   s.ad = oz_digits_bytes(l, m);
   s.asc = oz_scales_bytes(l, m);
+  s.thfb = s.bf16 ? (size_t)m * s.K1b * 2 : 0;
+  s.thab = s.bf16 ? (size_t)n * s.K2b * 2 : 0;
+  s.btb = s.bf16 ? (size_t)s.Np * (s.K1b > s.K2b ? s.K1b : s.K2b) * 2 : 0;
   const int mx = m > n ? m : n;
   s.qs = ((!qr_blk_f32_fits(m, l) && qr_multi_f32_fits(m, l)) || (!qr_blk_f32_fits(n, l) && qr_multi_f32_fits(n, l)))
              ? qr_multi_f32_scratch(mx, l) * sizeof(float2)
              : 0;
-  s.ntile = ((s.K1 / 2 + 31) / 32) * ((s.K2 / 2 + 31) / 32);
+  {
+    const int c1 = s.bf16 && s.K1b > s.K1 ? s.K1b : s.K1, c2 = s.bf16 && s.K2b > s.K2 ? s.K2b : s.K2;
+    s.ntile = ((c1 / 2 + 31) / 32) * ((c2 / 2 + 31) / 32);
+  }
   (void)k;
   return s;
 }
@@ -426,7 +500,8 @@ size_t mixed_bytes(const MixedSizes& s, int batch) {
   return 2 * up256(s.thf * batch) + 2 * up256(s.tha * batch) + 2 * up256(s.bt * batch) + 2 * up256(s.yf * batch) +
          2 * up256(s.ytf * batch) + up256(s.df * batch) + up256(s.thd * batch) +
          up256((size_t)s.ntile * sizeof(double) * batch) + up256(s.qs * batch) + up256(s.bd * batch) +
-         up256(s.bsc * batch) + up256(s.ad * batch) + up256(s.asc * batch);
+         up256(s.bsc * batch) + up256(s.ad * batch) + up256(s.asc * batch) + up256(s.thfb * batch) +
+         up256(s.thab * batch) + up256(s.btb * batch);
 }
 
 MixedPtrs mixed_carve(char* base, const MixedSizes& s, int batch) {
@@ -453,6 +528,9 @@ MixedPtrs mixed_carve(char* base, const MixedSizes& s, int batch) {
   p.bsc = (float*)(base + o); o += up256(s.bsc * batch);
   p.ad = (uint16_t*)(base + o); o += up256(s.ad * batch);
   p.asc = (float*)(base + o); o += up256(s.asc * batch);
+  p.thf_b = s.bf16 ? (uint16_t*)(base + o) : nullptr; o += up256(s.thfb * batch);
+  p.tha_b = s.bf16 ? (uint16_t*)(base + o) : nullptr; o += up256(s.thab * batch);
+  p.bt_b = s.bf16 ? (uint16_t*)(base + o) : nullptr; o += up256(s.btb * batch);
   return p;
 }
 
@@ -462,6 +540,19 @@ MixedPtrs mixed_carve(char* base, const MixedSizes& s, int batch) {
     if (e_ != cudaSuccess) return e_; \
   } while (0)
 
+// the tensor-core kernels' shared memory limit, set once for the largest tile
+static cudaError_t tc_attrs() {
+  static int done = 0;
+  if (!done) {
+    MX_TRY(cudaFuncSetAttribute(k_tc_gemm<TC_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)tc_smem_bytes(TC_MAXBN)));
+    MX_TRY(cudaFuncSetAttribute(k_tc_gemm<TC_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)tc_smem_bytes(TC_MAXBN)));
+    done = 1;
+  }
+  return cudaSuccess;
+}
+
 static int grid1d(int64_t total) {
   int64_t b = (total + 255) / 256;
   if (b > 1024) b = 1024;
@@ -470,15 +561,17 @@ static int grid1d(int64_t total) {
 
 // One tensor-core product: out (rows x l complex, per instance) from
 // A (rows x Kp) and Bt (Np x Kp); npass 1 or 3.
-static cudaError_t tc_product(const float* A0, const float* A1, const float* B0, const float* B1, int rows, int Kp,
+// bf16: A0, B0 hold BF16 copies (one pass; A1, B1 unused) and Kp counts BF16
+// values; otherwise FP32 arrays of TF32-rounded values.
+static cudaError_t tc_product(const void* A0, const void* A1, const void* B0, const void* B1, int rows, int Kp,
                               const MixedSizes& s0, int l, int npass, float2* out, int batch, int* err,
-                              cudaStream_t st, int half) {
+                              cudaStream_t st, int half, bool bf16 = false) {
   // half: the columns of the product split over two CTAs (tile width rounded to 16)
   MixedSizes s = s0;
   if (half && s.BN > 16) s.BN = ((s.BN / 2 + 15) / 16) * 16;
   CUtensorMap ma0, ma1, mb0, mb1;
-  if (!make_map(&ma0, A0, Kp, rows, batch, TC_BM) || !make_map(&ma1, A1, Kp, rows, batch, TC_BM) ||
-      !make_map(&mb0, B0, Kp, s.Np, batch, s.BN) || !make_map(&mb1, B1, Kp, s.Np, batch, s.BN))
+  if (!make_map(&ma0, A0, Kp, rows, batch, TC_BM, bf16) || !make_map(&ma1, bf16 ? A0 : A1, Kp, rows, batch, TC_BM, bf16) ||
+      !make_map(&mb0, B0, Kp, s.Np, batch, s.BN, bf16) || !make_map(&mb1, bf16 ? B0 : B1, Kp, s.Np, batch, s.BN, bf16))
     return cudaErrorInvalidValue;
   TcArgs a;
   a.M = rows;
@@ -497,14 +590,15 @@ static cudaError_t tc_product(const float* A0, const float* A1, const float* B0,
   a.poll_limit = stall ? (1u << 12) : (1u << 24);
   a.stall = stall ? 1 : 0;
   const size_t sm = tc_smem_bytes(s.BN);
-  static int attr_done = 0;  // set once for the largest tile (also by mixed_prepare)
-  if (!attr_done) {
-    MX_TRY(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes(TC_MAXBN)));
-    attr_done = 1;
-  }
+  MX_TRY(tc_attrs());
   dim3 grid((rows + TC_BM - 1) / TC_BM, (s.Np + s.BN - 1) / s.BN, batch);
-  ProfScope ps(npass == 1 ? "k_tc_gemm[tf32]" : "k_tc_gemm[3xtf32]", st);
-  k_tc_gemm<<<grid, 128, sm, st>>>(ma0, ma1, mb0, mb1, a);
+  if (bf16) {
+    ProfScope ps("k_tc_gemm[bf16]", st);
+    k_tc_gemm<TC_BF16><<<grid, 128, sm, st>>>(ma0, ma1, mb0, mb1, a);
+  } else {
+    ProfScope ps(npass == 1 ? "k_tc_gemm[tf32]" : "k_tc_gemm[3xtf32]", st);
+    k_tc_gemm<TC_TF32><<<grid, 128, sm, st>>>(ma0, ma1, mb0, mb1, a);
+  }
   return cudaGetLastError();
 }
 
@@ -526,54 +620,86 @@ static cudaError_t conv_bt(const float2* X, const Dims* dims, const MixedPtrs& m
   return cudaGetLastError();
 }
 
+static cudaError_t conv_bt_bf16(const float2* X, const Dims* dims, const MixedPtrs& mp, int Kc, int l, int Kp,
+                                const MixedSizes& s, int batch, cudaStream_t st) {
+  ProfScope ps("k_conv_bt", st);
+  k_conv_bt_bf16<<<dim3(grid1d((int64_t)(s.Np / 2) * (Kp / 2)), batch), 256, 0, st>>>(X, dims, mp.bt_b, Kc, l, s.Np,
+                                                                                      Kp);
+  return cudaGetLastError();
+}
+
 cudaError_t mixed_prepare(const Caps& cap) {
   if (!encode_fn()) return cudaErrorNotSupported;
   MX_TRY(oz_prepare());
-  static int attr_done = 0;
-  if (!attr_done) {
-    MX_TRY(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes(TC_MAXBN)));
-    attr_done = 1;
-  }
+  MX_TRY(tc_attrs());
   return qr_blocked_prepare(cap.m, cap.n, cap.l);
 }
 
 cudaError_t run_rrsvd_mixed(const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, const MixedPtrs& mp,
                             int q, uint64_t seed, uint64_t sweep, int64_t chain0, int chain_stride, int* status,
-                            int* err, cudaStream_t st, const uint64_t* sweep_dev, const MixedKnobs* knobs) {
+                            int* err, cudaStream_t st, const uint64_t* sweep_dev, const MixedKnobs* knobs,
+                            int bf16_form) {
   const MixedKnobs kn = knobs ? *knobs : MixedKnobs{0, 0, 0, 0};
   // capacities: every FP32 array is laid out at these sizes, zero-padded past
   // each instance's own (m, n, l) from dims
   const int m = cap.m, n = cap.n, k = cap.k, l = cap.l;
-  const MixedSizes s = mixed_sizes(m, n, k, l);
+  const MixedSizes s = mixed_sizes(m, n, k, l, bf16_form);
+  // BF16 products: every one before the refinement round (the last power
+  // round; Y0 itself when q = 0, which then stays 3xTF32)
+  const bool bf = bf16_form && mp.thf_b && q > 0;
   {
     ProfScope ps("k_conv_theta", st);
-    const int cext = s.K1 / 2, rext = s.K2 / 2;  // padded extents (>= n, >= m)
-    k_conv_theta<<<dim3((cext + 31) / 32, (rext + 31) / 32, batch), 256, 0, st>>>(mp, dims, ptrs, m, n, s.K1, s.K2,
-                                                                                   1);
+    // padded extents (>= n, >= m) of every copy written
+    const int cext = (bf && s.K1b > s.K1 ? s.K1b : s.K1) / 2, rext = (bf && s.K2b > s.K2 ? s.K2b : s.K2) / 2;
+    MixedPtrs mq = mp;
+    if (!bf) mq.thf_b = mq.tha_b = nullptr;
+    const dim3 grid((cext + 31) / 32, (rext + 31) / 32, batch);  // grid.x * grid.y <= s.ntile
+    k_conv_theta<<<grid, 256, 0, st>>>(mq, dims, ptrs, m, n, s.K1, s.K2, 1, s.K1b, s.K2b);
     MX_TRY(cudaGetLastError());
-    k_part_reduce<<<batch, NPART, 0, st>>>(mp.tpart, s.ntile, dims, ptrs);
+    k_part_reduce<<<batch, NPART, 0, st>>>(mp.tpart, (int)(grid.x * grid.y), dims, ptrs);
     MX_TRY(cudaGetLastError());
   }
   MX_TRY(launch_oz_digits_theta(dims, ptrs, mp.bd, mp.bsc, m, n, batch, st));
   {
     ProfScope ps("k_omega_bt", st);
-    k_omega_bt<<<dim3(grid1d((int64_t)(s.Np / 2) * (s.K1 / 2)), batch), 256, 0, st>>>(
-        mp, dims, s.Np, s.K1, seed, sweep, chain0, chain_stride, q == 0 ? 1 : 0, sweep_dev);
+    if (bf)
+      k_omega_bt_bf16<<<dim3(grid1d((int64_t)(s.Np / 2) * (s.K1b / 2)), batch), 256, 0, st>>>(
+          mp.bt_b, dims, s.Np, s.K1b, seed, sweep, chain0, chain_stride, sweep_dev);
+    else
+      k_omega_bt<<<dim3(grid1d((int64_t)(s.Np / 2) * (s.K1 / 2)), batch), 256, 0, st>>>(
+          mp, dims, s.Np, s.K1, seed, sweep, chain0, chain_stride, q == 0 ? 1 : 0, sweep_dev);
     MX_TRY(cudaGetLastError());
   }
   // Y0 = A Omega: TF32, or the refinement pass when q == 0
   const int p0 = (q == 0) ? 3 : 1;
-  MX_TRY(tc_product(mp.thf_hi, mp.thf_lo, mp.bt_hi, mp.bt_lo, m, s.K1, s, l, p0, mp.Yf, batch, err, st, kn.tc_half));
+  if (bf)
+    MX_TRY(tc_product(mp.thf_b, nullptr, mp.bt_b, nullptr, m, s.K1b, s, l, 1, mp.Yf, batch, err, st, kn.tc_half, true));
+  else
+    MX_TRY(tc_product(mp.thf_hi, mp.thf_lo, mp.bt_hi, mp.bt_lo, m, s.K1, s, l, p0, mp.Yf, batch, err, st,
+                      kn.tc_half));
   for (int j = 1; j <= q; ++j) {
     const int np = (j == q) ? 3 : 1;
+    const bool b16 = bf && np == 1;  // BF16 for the rounds before the refinement round
     MX_TRY(qr_f32(mp.Yf, mp.Qf, m, l, batch, mp, s, dims, 0, st, kn.qr_threads));    // Y = Q R
-    MX_TRY(conv_bt(mp.Qf, dims, mp, m, l, s.K2, s, np == 3, batch, st));
-    MX_TRY(tc_product(mp.tha_hi, mp.tha_lo, mp.bt_hi, mp.bt_lo, n, s.K2, s, l, np, mp.Ytf, batch, err, st,
-                      kn.tc_half));  // A^H Q
+    if (b16) {
+      MX_TRY(conv_bt_bf16(mp.Qf, dims, mp, m, l, s.K2b, s, batch, st));
+      MX_TRY(tc_product(mp.tha_b, nullptr, mp.bt_b, nullptr, n, s.K2b, s, l, 1, mp.Ytf, batch, err, st, kn.tc_half,
+                        true));  // A^H Q
+    } else {
+      MX_TRY(conv_bt(mp.Qf, dims, mp, m, l, s.K2, s, np == 3, batch, st));
+      MX_TRY(tc_product(mp.tha_hi, mp.tha_lo, mp.bt_hi, mp.bt_lo, n, s.K2, s, l, np, mp.Ytf, batch, err, st,
+                        kn.tc_half));  // A^H Q
+    }
     MX_TRY(qr_f32(mp.Ytf, mp.Qtf, n, l, batch, mp, s, dims, 1, st, kn.qr_threads));  // = Q~ R~
-    MX_TRY(conv_bt(mp.Qtf, dims, mp, n, l, s.K1, s, np == 3, batch, st));
-    MX_TRY(tc_product(mp.thf_hi, mp.thf_lo, mp.bt_hi, mp.bt_lo, m, s.K1, s, l, np, mp.Yf, batch, err, st,
-                      kn.tc_half));  // A Q~
+    if (b16) {
+      MX_TRY(conv_bt_bf16(mp.Qtf, dims, mp, n, l, s.K1b, s, batch, st));
+      MX_TRY(tc_product(mp.thf_b, nullptr, mp.bt_b, nullptr, m, s.K1b, s, l, 1, mp.Yf, batch, err, st, kn.tc_half,
+                        true));  // A Q~
+    } else {
+      MX_TRY(conv_bt(mp.Qtf, dims, mp, n, l, s.K1, s, np == 3, batch, st));
+      MX_TRY(tc_product(mp.thf_hi, mp.thf_lo, mp.bt_hi, mp.bt_lo, m, s.K1, s, l, np, mp.Yf, batch, err, st,
+                        kn.tc_half));  // A Q~
+    }
   }
   // last QR: FP32 Householder, then the FP64-accurate re-orthonormalisation.
   // Plans and handles refuse sketches wider than 512 columns, and l <= m, so

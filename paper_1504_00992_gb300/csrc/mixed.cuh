@@ -9,12 +9,15 @@ namespace tg {
 
 // Padded sizes of the real-embedded operands of one instance.
 struct MixedSizes {
+  int bf16;      // 1: the products before the refinement round in BF16 (TEBD_PREC_BF16)
   int K1;        // 2n rounded up to 32: row length of theta's forward copy and of Bt for A X
   int K2;        // 2m rounded up to 32: row length of the adjoint copy and of Bt for A^H X
+  int K1b, K2b;  // the same rounded up to 64 for the BF16 copies (128-byte rows)
   int Np;        // 2l rounded up to 16: rows of Bt (tensor-core N)
   int BN;        // tensor-core tile width, min(Np, 256)
   size_t thf, tha, bt, yf, ytf, df, thd;  // bytes per instance
   size_t bd, bsc, ad, asc;  // BF16 digits and block scales of theta and of Q_f^H (tensor-core projection)
+  size_t thfb, thab, btb;   // BF16 copies of theta, theta^H and Bt (bf16 only)
   size_t qs;     // bytes per instance of the many-CTA FP32 QR's scratch (0: not used)
   int ntile;     // 32 x 32 tiles of the theta conversion (partials of ||theta||_F^2)
 };
@@ -37,11 +40,14 @@ struct MixedPtrs {
   float* bsc;     // their block scales
   uint16_t* ad;   // digits of Q_f^H
   float* asc;
+  uint16_t* thf_b;  // m x K1b BF16 theta (bf16 form), or null
+  uint16_t* tha_b;  // n x K2b BF16 theta^H
+  uint16_t* bt_b;   // Np x max(K1b, K2b) BF16 right operand
   double* tpart;  // ntile partial sums of |theta|^2 per instance
   float2* qscr;   // scratch of the many-CTA FP32 QR (qs bytes per instance), or null
 };
 
-MixedSizes mixed_sizes(int m, int n, int k, int l);
+MixedSizes mixed_sizes(int m, int n, int k, int l, int bf16 = 0);
 size_t mixed_bytes(const MixedSizes& s, int batch);
 MixedPtrs mixed_carve(char* base, const MixedSizes& s, int batch);
 
@@ -114,6 +120,6 @@ cudaError_t qr_blocked_prepare(int M, int N, int L);
 cudaError_t run_rrsvd_mixed(const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, const MixedPtrs& mp,
                             int q, uint64_t seed, uint64_t sweep, int64_t chain0, int chain_stride, int* status,
                             int* err, cudaStream_t st, const uint64_t* sweep_dev = nullptr,
-                            const MixedKnobs* knobs = nullptr);
+                            const MixedKnobs* knobs = nullptr, int bf16 = 0);
 
 }  // namespace tg

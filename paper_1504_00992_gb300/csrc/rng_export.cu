@@ -57,7 +57,8 @@ extern "C" int tebd_philox4x64_10(const uint64_t* counters, int64_t count, uint6
 extern "C" int rrsvd_sketch_omega(int n, int l, uint64_t seed, int64_t bond, int64_t sweep, int64_t chain,
                                   int precision, void* out, void* stream) {
   if (n < 0 || l < 0 || bond < 0 || sweep < 0 || chain < 0) return TEBD_EINVAL;
-  if (precision != TEBD_PREC_FP64 && precision != TEBD_PREC_TF32) return TEBD_ENOTIMPL;
+  if (precision != TEBD_PREC_FP64 && precision != TEBD_PREC_TF32 && precision != TEBD_PREC_BF16)
+    return TEBD_ENOTIMPL;
   const int64_t total = (int64_t)n * l;
   if (total == 0) return TEBD_OK;
   if (!out) return TEBD_EINVAL;

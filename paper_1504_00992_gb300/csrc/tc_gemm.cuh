@@ -1,21 +1,24 @@
 // Tensor-core GEMM for the low-precision sketch products (sm_103a tcgen05).
 //
 // Computes, per instance z of a batch, C = sum_pass A_pass * B_pass^T with
-//   A: M x Kp real FP32 holding TF32-rounded values, K-major (row-major),
-//   B: Np x Kp real FP32 (TF32-rounded), K-major,
+//   A: M x Kp real FP32 holding TF32-rounded values (KIND = TC_TF32) or BF16
+//      values (KIND = TC_BF16), K-major (row-major),
+//   B: Np x Kp of the same type, K-major,
 // FP32 accumulation in tensor memory, and writes complex FP32 columns:
 //   out[c * M + r] = (C[r][2c], C[r][2c+1])  for c < l, r < M
 // (the real embedding of a complex product puts Re and Im of output column
 // c in adjacent real columns 2c, 2c+1).
 //
-// npass = 1: A0 B0^T (one TF32 product).  npass = 3: A0 B0^T + A0 B1^T +
-// A1 B0^T (the "3xTF32" split product, FP32-level accuracy).
+// npass = 1: A0 B0^T (one TF32 or BF16 product).  npass = 3 (TF32 only):
+// A0 B0^T + A0 B1^T + A1 B0^T (the "3xTF32" split product, FP32-level
+// accuracy).  A stage holds 128 bytes of every row: 32 TF32 or 64 BF16
+// values, four MMAs of K = 8 (kind::tf32) or K = 16 (kind::f16) each.
 //
 // Structure (one CTA = 128 rows x up to 256 columns, 4 warps):
 //   warp 0 / one lane : TMA producer (cp.async.bulk.tensor.3d into a ring of
 //                       STAGES shared-memory slots, 128-byte swizzle),
-//   warp 1 / one lane : MMA issuer (tcgen05.mma.cta_group::1.kind::tf32,
-//                       4 x K=8 per 128-byte slot), frees slots with
+//   warp 1 / one lane : MMA issuer (tcgen05.mma.cta_group::1.kind::tf32 or
+//                       kind::f16, 4 per 128-byte slot), frees slots with
 //                       tcgen05.commit -> mbarrier,
 //   all 4 warps       : epilogue, tcgen05.ld 32x32b from the accumulator
 //                       (warp w owns TMEM lanes 32w..32w+31 = tile rows).
@@ -32,6 +35,9 @@
 namespace tg {
 
 enum { TC_BM = 128, TC_BK = 32, TC_STAGES = 4, TC_MAXBN = 256, TC_TMEM_COLS = 256 };
+enum { TC_TF32 = 0, TC_BF16 = 1 };
+// k values per 128-byte stage row
+__host__ __device__ constexpr int tc_bk(int kind) { return kind == TC_BF16 ? 64 : TC_BK; }
 
 struct TcArgs {
   int M;          // rows of A and of the output
@@ -61,14 +67,19 @@ __device__ __forceinline__ uint64_t tc_desc_sw128(uint32_t saddr) {
 __host__ __device__ constexpr uint32_t tc_idesc_tf32(int M, int N) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
+// kind::f16 with A = B = BF16, D = F32, both K-major.
+__host__ __device__ constexpr uint32_t tc_idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
 
+template <int KIND>
 __global__ void __launch_bounds__(128, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
               const __grid_constant__ CUtensorMap tmB0, const __grid_constant__ CUtensorMap tmB1, TcArgs a) {
   extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
-  const uint32_t bytesA = TC_BM * TC_BK * 4;     // 16 KB
-  const uint32_t bytesB = (uint32_t)a.BN * TC_BK * 4;
+  const uint32_t bytesA = TC_BM * 128;     // 16 KB
+  const uint32_t bytesB = (uint32_t)a.BN * 128;
   uint8_t* sA = smem;
   uint8_t* sB = smem + TC_STAGES * bytesA;
   uint64_t* full = (uint64_t*)(sB + TC_STAGES * bytesB);
@@ -80,7 +91,7 @@ __global__ void __launch_bounds__(128, 1)
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * a.BN, z = blockIdx.z;
-  const int KB = a.Kp / TC_BK;
+  const int KB = a.Kp / tc_bk(KIND);
   const int iters = a.npass * KB;
 
   if (warp == 0) {
@@ -115,8 +126,8 @@ __global__ void __launch_bounds__(128, 1)
       const CUtensorMap* ta = (pass == 2) ? &tmA1 : &tmA0;
       const CUtensorMap* tb = (pass == 1) ? &tmB1 : &tmB0;
       tc_mbar_expect_tx(&full[s], bytesA + bytesB);
-      tc_tma_load_3d(sA + s * bytesA, ta, kb * TC_BK, m0, z, &full[s]);
-      tc_tma_load_3d(sB + s * bytesB, tb, kb * TC_BK, n0, z, &full[s]);
+      tc_tma_load_3d(sA + s * bytesA, ta, kb * tc_bk(KIND), m0, z, &full[s]);
+      tc_tma_load_3d(sB + s * bytesB, tb, kb * tc_bk(KIND), n0, z, &full[s]);
       issued = it + 1;
     }
     // make sure every copy this thread issued has landed before teardown
@@ -127,7 +138,7 @@ __global__ void __launch_bounds__(128, 1)
     }
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer
-    const uint32_t idesc = tc_idesc_tf32(TC_BM, a.BN);
+    const uint32_t idesc = KIND == TC_BF16 ? tc_idesc_bf16(TC_BM, a.BN) : tc_idesc_tf32(TC_BM, a.BN);
     bool ok = true;
     int issued_mma = 0;
     for (int it = 0; it < iters; ++it) {
@@ -137,15 +148,23 @@ __global__ void __launch_bounds__(128, 1)
       tc_fence_after();
       const uint32_t aa = tc_smem_u32(sA + s * bytesA), bb = tc_smem_u32(sB + s * bytesB);
 #pragma unroll
-      for (int kk = 0; kk < TC_BK / 8; ++kk) {
+      for (int kk = 0; kk < 4; ++kk) {  // 32 bytes of k per MMA
         const uint64_t ad = tc_desc_sw128(aa + kk * 32), bd = tc_desc_sw128(bb + kk * 32);
         const uint32_t acc = (it > 0 || kk > 0) ? 1u : 0u;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "setp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
-            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-            : "memory");
+        if (KIND == TC_BF16)
+          asm volatile(
+              "{\n\t.reg .pred p;\n\t"
+              "setp.ne.b32 p, %4, 0;\n\t"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+              : "memory");
+        else
+          asm volatile(
+              "{\n\t.reg .pred p;\n\t"
+              "setp.ne.b32 p, %4, 0;\n\t"
+              "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+              : "memory");
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                        tc_smem_u32(&empty[s]))
@@ -212,7 +231,7 @@ __global__ void __launch_bounds__(128, 1)
 }
 
 inline size_t tc_smem_bytes(int BN) {
-  return 1024 + (size_t)TC_STAGES * (TC_BM * TC_BK * 4 + (size_t)BN * TC_BK * 4) + (2 * TC_STAGES + 2) * 8 + 16;
+  return 1024 + (size_t)TC_STAGES * (TC_BM * 128 + (size_t)BN * 128) + (2 * TC_STAGES + 2) * 8 + 16;
 }
 
 }  // namespace tg

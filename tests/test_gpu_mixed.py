@@ -13,6 +13,13 @@ oracle, so it is held to the FP64 method's accuracy, not to its rounding
   * where the FP64 method meets the 1e-8 bar, the mixed form meets it too;
   * the returned factors are orthonormal to 1e-11 (re-orthonormalised last Q,
     FP64 Jacobi, double-float U = Q J_k and V = Qb W_k).
+
+TEBD_PREC_BF16 runs the products before the refinement round in BF16: the
+subspace the refinement round starts from is perturbed at 2^-9, which moves
+the method's own approximation error by a few percent where that error is
+large (slowly decaying spectra, q = 1), so its first two bars read
+err_m <= 1.05 err_o + 1e-8 s_1 (and likewise for the excess error); the
+others are unchanged.
 """
 import numpy as np
 import pytest
@@ -36,12 +43,15 @@ SEED = 4321
     (1200, 400, 140, 20, 1, 12.0), # l = 160: correction read through L1 (tiled Loewdin and fold)
     (3700, 300, 30, 10, 1, 6.0),   # Y too tall for the blocked FP32 QR, l = 40: FP32 QR over many CTAs
 ])
-def test_mixed_form_meets_its_tolerances(lib, m, n, k, p, q, scale):
+@pytest.mark.parametrize("form", ["tf32", "bf16"])
+def test_mixed_form_meets_its_tolerances(lib, m, n, k, p, q, scale, form):
     from paper_1504_00992_gb300 import binding as B
     batch = 3
     sig = I.exp_spectrum(min(m, n), scale)
     theta = np.stack([I.synthetic_theta(m, n, sig, seed=200 + t) for t in range(batch)])
-    plan = B.rrsvd_plan_create(m, n, k, p, q, batch, B.TEBD_PREC_TF32, SEED)
+    prec = B.TEBD_PREC_BF16 if form == "bf16" else B.TEBD_PREC_TF32
+    rel = 1.05 if form == "bf16" else 1.0
+    plan = B.rrsvd_plan_create(m, n, k, p, q, batch, prec, SEED)
     try:
         res = rrsvd_device(B, plan, theta, chain0=2)
     finally:
@@ -56,12 +66,12 @@ def test_mixed_form_meets_its_tolerances(lib, m, n, k, p, q, scale):
         Uk, sk, Vhk, w = R.rrsvd_truncate(A, gaussian_omega(n, l, SEED, chain=2 + t), kk, q)
         err_o = np.abs(sk - sig[:kk]).max()
         err_m = np.abs(s - sig[:kk]).max()
-        assert err_m <= err_o + 1e-8 * sig[0]
+        assert err_m <= rel * err_o + 1e-8 * sig[0]
         if err_o <= 1e-8:
             assert err_m <= 1e-8
         exc_o = (np.linalg.norm(A - truncated(Uk, sk, Vhk)) - opt) / nA
         exc_m = (np.linalg.norm(A - truncated(res["U"][t], s, res["Vh"][t])) - opt) / nA
-        assert exc_m <= exc_o + 1e-8
+        assert exc_m <= rel * max(exc_o, 0.0) + 1e-8
         U = res["U"][t]
         assert np.abs(U.conj().T @ U - np.eye(kk)).max() < 1e-11
         V = res["Vh"][t]
@@ -69,8 +79,8 @@ def test_mixed_form_meets_its_tolerances(lib, m, n, k, p, q, scale):
         assert abs(res["w"][t] - w) <= 1e-8 + abs(w - (np.sum(sig[kk:] ** 2) / np.sum(sig ** 2)))
 
 
-@pytest.mark.parametrize("batch", [2, 152])
-def test_mixed_form_full_size_sampled(lib, batch):
+@pytest.mark.parametrize("batch,form", [(2, "tf32"), (152, "tf32"), (152, "bf16")])
+def test_mixed_form_full_size_sampled(lib, batch, form):
     """2000 x 2000, k=100, p=20, q=2 (the single-bond stress workload): kept
     singular values within 1e-8 of the exact spectrum and excess truncation
     error within 1e-8, on the first and last instance.  The batch of 152 (two
@@ -81,7 +91,8 @@ def test_mixed_form_full_size_sampled(lib, batch):
     m = n = 2000
     sig = I.exp_spectrum(n)
     base = [I.synthetic_theta(m, n, sig, seed=t) for t in range(2)]
-    plan = B.rrsvd_plan_create(m, n, 100, 20, 2, batch, B.TEBD_PREC_TF32, SEED)
+    prec = B.TEBD_PREC_BF16 if form == "bf16" else B.TEBD_PREC_TF32
+    plan = B.rrsvd_plan_create(m, n, 100, 20, 2, batch, prec, SEED)
     try:
         res = rrsvd_device(B, plan, repeat_on_device(base, batch))
     finally:

@@ -34,11 +34,17 @@ def _oracle(N, d, chi, delta, steps, dt, p, q, seed, chain=0):
     return np.array([ref.expect(k, sz).real for k in range(N)]), ref.mps.lam, ref.w_sum
 
 
-def test_single_chain_tf32_matches_fp64_oracle(lib):
+# (observables, Schmidt values) bars of each form after the 36 sweeps
+BARS = {"tf32": (1e-7, 2e-7), "bf16": (1e-6, 2e-6)}
+
+
+@pytest.mark.parametrize("form", ["tf32", "bf16"])
+def test_single_chain_mixed_matches_fp64_oracle(lib, form):
     from paper_1504_00992_gb300 import binding as B
     N, d, chi, delta, steps, dt, p, q, seed = 14, 2, 16, 0.5, 12, 0.05, 6, 2, 5
     hs = I.xxz_bond_terms(N, d, 1.0, delta)
-    sim = B.Tebd(N, d, chi, p, q, seed, precision=B.TEBD_PREC_TF32)
+    prec = B.TEBD_PREC_BF16 if form == "bf16" else B.TEBD_PREC_TF32
+    sim = B.Tebd(N, d, chi, p, q, seed, precision=prec)
     sim.set_product_state(I.neel_state(N, d))
     sim.set_gates(0, I.trotter_gates(hs, dt / 2))
     sim.set_gates(1, I.trotter_gates(hs, dt))
@@ -50,10 +56,13 @@ def test_single_chain_tf32_matches_fp64_oracle(lib):
     w = sim.discarded_weight()
     sim.close()
     exp, lam_o, w_o = _oracle(N, d, chi, delta, steps, dt, p, q, seed)
-    assert np.abs(got - exp).max() <= 1e-7
-    for b in range(N - 1):
-        r = min(len(lam[b]), len(lam_o[b]))
-        assert np.abs(lam[b][:r] - lam_o[b][:r]).max() <= 2e-7
+    bo, bl = BARS[form]
+    d_obs = np.abs(got - exp).max()
+    d_lam = max(np.abs(lam[b][:min(len(lam[b]), len(lam_o[b]))] - lam_o[b][:min(len(lam[b]), len(lam_o[b]))]).max()
+                for b in range(N - 1))
+    print(f"{form}: observables {d_obs:.2e}, Schmidt values {d_lam:.2e}, weight {abs(w[0] - w_o):.2e}")
+    assert d_obs <= bo
+    assert d_lam <= bl
     assert abs(w[0] - w_o) <= 1e-10
 
 

@@ -66,7 +66,7 @@ def test_arena_holds_the_state_and_every_theta_of_a_parity():
 def test_waves_never_fewer_when_the_budget_shrinks():
     specs = I.many_chain_specs(64, 0)
     chains = [_chain(N, d, chi) for N, d, chi, _ in specs]
-    for prec in (B.TEBD_PREC_FP64, B.TEBD_PREC_TF32):
+    for prec in (B.TEBD_PREC_FP64, B.TEBD_PREC_TF32, B.TEBD_PREC_BF16):
         prev = (1, 1)
         for gb in (64, 16, 4, 1, 0.25):
             _, we, wo = B.tebd_plan_query(chains, 10, 1, 0, precision=prec, workspace_budget=int(gb * (1 << 30)))
@@ -85,6 +85,10 @@ def test_argument_errors():
     with pytest.raises(B.TebdError) as e:
         B.tebd_plan_query([_chain(6, 2, 8)], 4, 1, 0, precision=7)
     assert e.value.code == B.TEBD_ENOTIMPL
+    # the BF16 form holds its BF16 copies beside the FP32 arrays
+    a_tf = B.tebd_plan_query([_chain(20, 2, 64)], 4, 1, 0, precision=B.TEBD_PREC_TF32)[0]
+    a_bf = B.tebd_plan_query([_chain(20, 2, 64)], 4, 1, 0, precision=B.TEBD_PREC_BF16)[0]
+    assert a_bf > a_tf
     # the autotuner covers the mixed form too: the plan is the same as untuned
     assert B.tebd_plan_query([_chain(6, 2, 8)], 4, 1, 0, precision=B.TEBD_PREC_TF32, autotune=1) == \
         B.tebd_plan_query([_chain(6, 2, 8)], 4, 1, 0, precision=B.TEBD_PREC_TF32)
