@@ -420,6 +420,13 @@ def roofline(res, batch):
         "k_zgemm[uv]": (8.0 * M * l * k * batch, "alu", fp64_peak, fp64_src, "kernels.cu"),
         "k_zgemm_df[project]": (8.0 * M * N_ * l * batch, "alu", df_peak, df_src, "df_proj.cu"),
         "k_oz_proj[project]": (8.0 * M * N_ * l * batch, "tensor", oz_peak, oz_src, "oz_proj.cu"),
+        # the Cholesky QR of B^H (Gram matrices, triangular products, B Qb:
+        # each n l^2 complex multiply-adds as computed) and U, V, on the same
+        # digit-pair kernel
+        "k_oz_gemm[cholqr]": (8.0 * N_ * l * l * batch, "tensor", oz_peak, oz_src, "oz_proj.cu"),
+        "k_oz_gemm[uv]": (8.0 * M * l * k * batch, "tensor", oz_peak, oz_src, "oz_proj.cu"),
+        "k_zgemm_df[cholqr]": (8.0 * N_ * l * l * batch, "alu", df_peak, df_src, "kernels.cu"),
+        "k_zgemm_df[uv]": (8.0 * M * l * k * batch, "alu", df_peak, df_src, "kernels.cu"),
         # the sketch products (one complex m x n x l product per launch; the
         # 3xTF32 launch does three TF32 products for the same algorithmic flops)
         "k_tc_gemm[tf32]": (8.0 * M * N_ * l * batch, "tensor", tf32, tf32_src, "tc_gemm.cuh"),

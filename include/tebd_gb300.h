@@ -172,11 +172,12 @@ int tebd_select_chain(tebd_t h, int chain);
 int tebd_workspace_info(tebd_t h, size_t* arena_bytes, int* waves_even, int* waves_odd);
 
 /* Plan and tuning of wave `wave` of a parity (0 <= wave < its count from
- * tebd_workspace_info).  info (16 ints): [0] bonds in the wave, [1..4] its
+ * tebd_workspace_info).  info (20 ints): [0] bonds in the wave, [1..4] its
  * capacities m, n, k, l, [5] 1 if it runs as the persistent fused launch,
  * [6..11] the GEMM tile of stages Y0, Y~, Y, B^H, U, V (0: by grid size),
- * [12..15] the mixed form's launch choices of TF32 handles (as
- * rrsvd_plan_tuning's [6..9]).  ms (2 doubles): the autotuner's timings on
+ * [12..15] the mixed form's launch choices of mixed-form handles (as
+ * rrsvd_plan_tuning's [6..9]), [16] as rrsvd_plan_tuning's [11], [17..19]
+ * zero.  ms (2 doubles): the autotuner's timings on
  * synthetic theta -- FP64: the wave's staged and fused RRSVD; TF32: the RRSVD
  * with the size rules and with the choices kept (0 when not timed).
  * Either may be NULL.  Errors: TEBD_EINVAL (parity, wave). */
@@ -375,9 +376,10 @@ const char* rrsvd_last_error(rrsvd_plan_t plan);
 /* Autotuner of a plan (the batched launches of Section IV's steps): times
  * the launch choices on the caller's theta (device, as for rrsvd_execute) and
  * keeps the fastest for later executes.  FP64 plans: the GEMM tile of every
- * stage; TF32 plans: the mixed form's choices (tensor-core tile width, CTA
- * size of the FP32 QRs, one-CTA or many-CTA QR of B^H, one-CTA or cluster
- * Jacobi), one at a time, each kept only for a clear gain.  Results of a
+ * stage; mixed-form plans: the mixed form's choices (tensor-core tile width,
+ * CTA size of the FP32 QRs, one-CTA or many-CTA QR of B^H, one-CTA or
+ * cluster Jacobi, the products after the projection on the tensor cores or
+ * the CUDA cores), one at a time, each kept only for a clear gain.  Results of a
  * tuned plan agree with an untuned one to rounding.  Synchronises `stream`.
  * Errors: as rrsvd_execute. */
 int rrsvd_plan_autotune(rrsvd_plan_t plan, const double* theta, void* workspace, size_t workspace_bytes,
@@ -386,9 +388,19 @@ int rrsvd_plan_autotune(rrsvd_plan_t plan, const double* theta, void* workspace,
 /* What the autotuner chose: info (16 ints): [0..5] the FP64 GEMM tile of
  * stages Y0, Y~, Y, B^H, U, V (0: by grid size), [6..9] the mixed form's
  * choices (tile split, FP32 QR threads, QR of B^H, Jacobi; 0: the size rule),
- * [10] 1 once tuned; ms (2 doubles, TF32 plans): the step with the size
+ * [10] 1 once tuned, [11] the FP64-accurate products after the projection
+ * (0: the size rule, 1: tensor cores from digit splits, 2: double-float
+ * CUDA-core GEMMs), [12..15] zero; ms (2 doubles, TF32 plans): the step with the size
  * rules and with the choices kept.  Either may be NULL. */
 int rrsvd_plan_tuning(rrsvd_plan_t plan, int* info, double* ms);
+
+/* Sets a plan's launch choices (info: 16 ints laid out as rrsvd_plan_tuning
+ * gives them; [10] and [12..15] are ignored), e.g. to restore choices tuned
+ * in another process or to compare two of them.  The plan counts as tuned
+ * afterwards.  Results agree with those of any other choice to rounding.
+ * Errors: TEBD_EINVAL (NULL, a tile other than 0, 16 or 32, a choice out of
+ * range: [6] 0..1, [7] 0, 128, 256 or 512, [8] 0..3, [9] 0..2, [11] 0..2). */
+int rrsvd_plan_set_tuning(rrsvd_plan_t plan, const int* info);
 
 /* Clears the plan's recorded error and its device status flags (a zero or
  * non-finite theta, an expired tensor-core wait): an execute that failed

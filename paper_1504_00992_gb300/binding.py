@@ -112,6 +112,7 @@ _SIGS = {
     "rrsvd_clear_error": (_i, [_vp]),
     "rrsvd_plan_autotune": (_i, [_vp, _vp, _vp, ctypes.c_size_t, _vp]),
     "rrsvd_plan_tuning": (_i, [_vp, _pi, _pd]),
+    "rrsvd_plan_set_tuning": (_i, [_vp, _pi]),
     "tebd_set_product_state": (_i, [_vp, _pd]),
     "tebd_set_mps": (_i, [_vp, ctypes.POINTER(_pd), ctypes.POINTER(_pd), _pi]),
     "tebd_get_mps": (_i, [_vp, ctypes.POINTER(_pd), ctypes.POINTER(_pd), _pi]),
@@ -268,12 +269,12 @@ def tebd_workspace_info(h):
 
 def tebd_wave_info(h, parity, wave):
     """Dict of one wave's plan and tuning (tebd_wave_info)."""
-    info = (ctypes.c_int * 16)()
+    info = (ctypes.c_int * 20)()
     ms = (ctypes.c_double * 2)()
     _check(h, load().tebd_wave_info(h, parity, wave, info, ms))
     return {"bonds": info[0], "m": info[1], "n": info[2], "k": info[3], "l": info[4], "fused": info[5],
             "tiles": list(info[6:12]), "mixed": {"tc_half": info[12], "qr_threads": info[13], "qrbh": info[14],
-                                                 "jacobi": info[15]},
+                                                 "jacobi": info[15], "products": info[16]},
             "tune_ms": [ms[0], ms[1]]}
 
 
@@ -532,7 +533,19 @@ def rrsvd_plan_tuning(plan):
     ms = (ctypes.c_double * 2)()
     _pcheck(plan, load().rrsvd_plan_tuning(plan, info, ms))
     return {"tiles": list(info[0:6]), "tc_half": info[6], "qr_threads": info[7], "qrbh": info[8], "jacobi": info[9],
-            "tuned": info[10], "ms_rules": ms[0], "ms_kept": ms[1]}
+            "tuned": info[10], "products": info[11], "ms_rules": ms[0], "ms_kept": ms[1]}
+
+
+def rrsvd_plan_set_tuning(plan, choices):
+    """Sets a plan's launch choices from a dict laid out as rrsvd_plan_tuning's."""
+    info = (ctypes.c_int * 16)()
+    info[0:6] = [int(x) for x in choices.get("tiles", [0] * 6)]
+    info[6] = int(choices.get("tc_half", 0))
+    info[7] = int(choices.get("qr_threads", 0))
+    info[8] = int(choices.get("qrbh", 0))
+    info[9] = int(choices.get("jacobi", 0))
+    info[11] = int(choices.get("products", 0))
+    _pcheck(plan, load().rrsvd_plan_set_tuning(plan, info))
 
 
 # ------------------------------------------------------------------ kernel timing

@@ -366,17 +366,17 @@ static int tune_knobs(Run run, cudaStream_t st, const Caps& cap, int batch, Mixe
     cudaEventElapsedTime(&ms, e0, e1);
     return true;
   };
-  best = MixedKnobs{0, 0, 0, 0};
+  best = MixedKnobs{0, 0, 0, 0, 0};
   float t_best = 0.f, t_rule = 0.f;
   bool ok = run(best) == cudaSuccess && time_of(best, t_best);  // warm-up, then the size rules
   t_rule = t_best;
   const bool multi_ok = cap.n >= 1024 && cap.l >= 16;  // the many-CTA QR's structure (its own rule adds the batch)
   const bool cl_ok = cap.l >= 64 && cap.l <= 512;
-  std::vector<std::vector<int>> cand = {{0, 1}, {0, 512, 256, 128}, {0, 1, 2, 3}, {0, 1, 2}};
-  for (int knob = 0; knob < 4 && ok; ++knob)
+  std::vector<std::vector<int>> cand = {{0, 1}, {0, 512, 256, 128}, {0, 1, 2, 3}, {0, 1, 2}, {0, 1, 2}};
+  for (int knob = 0; knob < 5 && ok; ++knob)
     for (int v : cand[knob]) {
       MixedKnobs k = best;
-      int* f = knob == 0 ? &k.tc_half : knob == 1 ? &k.qr_threads : knob == 2 ? &k.qrbh : &k.jac;
+      int* f = knob == 0 ? &k.tc_half : knob == 1 ? &k.qr_threads : knob == 2 ? &k.qrbh : knob == 3 ? &k.jac : &k.dfg;
       if (*f == v || (knob == 2 && v == 2 && !multi_ok) || (knob == 3 && v == 2 && !cl_ok)) continue;
       *f = v;
       float t = 0.f;
@@ -1210,12 +1210,13 @@ extern "C" int tebd_wave_info(tebd_t h, int parity, int wave, int* info, double*
   if (parity < 0 || parity > 1 || wave < 0 || wave >= (int)h->par[parity].waves.size()) return TEBD_EINVAL;
   const Wave& w = h->par[parity].waves[wave];
   if (info) {
-    memset(info, 0, sizeof(int) * 16);
+    memset(info, 0, sizeof(int) * 20);
     info[0] = w.count;
     info[1] = w.cap.m; info[2] = w.cap.n; info[3] = w.cap.k; info[4] = w.cap.l;
     info[5] = w.fused;
     for (int i = 0; i < 6; ++i) info[6 + i] = w.tiles[i];
     info[12] = w.mk.tc_half; info[13] = w.mk.qr_threads; info[14] = w.mk.qrbh; info[15] = w.mk.jac;
+    info[16] = w.mk.dfg;
   }
   if (ms) {
     ms[0] = w.tune_ms[0];
@@ -1769,6 +1770,20 @@ extern "C" int rrsvd_plan_autotune(rrsvd_plan_t P, const double* theta, void* wo
   return TEBD_OK;
 }
 
+extern "C" int rrsvd_plan_set_tuning(rrsvd_plan_t P, const int* info) {
+  if (!P || !info) return TEBD_EINVAL;
+  for (int i = 0; i < 6; ++i)
+    if (info[i] != 0 && info[i] != 16 && info[i] != 32) return TEBD_EINVAL;
+  const int th = info[7];
+  if (info[6] < 0 || info[6] > 1 || (th != 0 && th != 128 && th != 256 && th != 512) || info[8] < 0 ||
+      info[8] > 3 || info[9] < 0 || info[9] > 2 || info[11] < 0 || info[11] > 2)
+    return TEBD_EINVAL;
+  for (int i = 0; i < 6; ++i) P->tiles[i] = info[i];
+  P->mk = MixedKnobs{info[6], info[7], info[8], info[9], info[11]};
+  P->tuned = 1;
+  return TEBD_OK;
+}
+
 extern "C" int rrsvd_plan_tuning(rrsvd_plan_t P, int* info, double* ms) {
   if (!P) return TEBD_EINVAL;
   if (info) {
@@ -1776,6 +1791,7 @@ extern "C" int rrsvd_plan_tuning(rrsvd_plan_t P, int* info, double* ms) {
     for (int i = 0; i < 6; ++i) info[i] = P->tiles[i];
     info[6] = P->mk.tc_half; info[7] = P->mk.qr_threads; info[8] = P->mk.qrbh; info[9] = P->mk.jac;
     info[10] = P->tuned;
+    info[11] = P->mk.dfg;
   }
   if (ms) {
     ms[0] = P->tune_ms[0];

@@ -5,8 +5,9 @@
 // CholeskyQR2 (Yamamoto, Nakatsukasa, Yanagisawa, Fukaya, ETNA 44, 2015):
 //   G1 = B B^H = R1^H R1,  Q1 = B^H R1^-1,
 //   G2 = Q1^H Q1 = R2^H R2, Qb = Q1 R2^-1,
-// with the Gram matrices and the triangular products in FP64-accurate
-// double-float arithmetic (k_zgemm_df stages G_G1 .. G_X) and the Cholesky
+// with the Gram matrices and the triangular products FP64-accurate (on the
+// tensor cores from exact digit splits, k_oz_gemm, or in double-float
+// arithmetic, k_zgemm_df; stages G_G1 .. G_X) and the Cholesky
 // factorisations and triangular inverses in FP64 here.  For kappa(B) below
 // ~1e8 the two passes give an orthonormal Qb and a backward-stable
 // factorisation (residual and orthogonality at the unit-roundoff level), so
@@ -20,6 +21,7 @@
 #include <math.h>
 
 #include "internal.cuh"
+#include "mixed.cuh"
 #include "profiler.cuh"
 
 namespace tg {
@@ -123,14 +125,19 @@ static cudaError_t chol_inv(Dims* dims, const ProbPtr* ptrs, int batch, int pass
     if (e_ != cudaSuccess) return e_; \
   } while (0)
 
-cudaError_t run_cholqr_bh(Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, cudaStream_t st) {
-  CQ_TRY(launch_zgemm_df(G_G1, dims, ptrs, batch, cap, st));  // G1 = B B^H
-  CQ_TRY(chol_inv(dims, ptrs, batch, 0, st));                 // R1, J = R1^-1
-  CQ_TRY(launch_zgemm_df(G_Q1, dims, ptrs, batch, cap, st));  // Q1 = B^H R1^-1
-  CQ_TRY(launch_zgemm_df(G_G2, dims, ptrs, batch, cap, st));  // G2 = Q1^H Q1
-  CQ_TRY(chol_inv(dims, ptrs, batch, 1, st));                 // R2, J = R2^-1
-  CQ_TRY(launch_zgemm_df(G_QB, dims, ptrs, batch, cap, st));  // Qb = Q1 R2^-1
-  CQ_TRY(launch_zgemm_df(G_X, dims, ptrs, batch, cap, st));   // X = B Qb = Rb^H
+cudaError_t run_cholqr_bh(Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, cudaStream_t st,
+                          const OzScratch* oz, int* err) {
+  auto gemm = [&](int stage) {
+    return oz ? launch_oz_stage(stage, dims, ptrs, batch, cap, *oz, err, st)
+              : launch_zgemm_df(stage, dims, ptrs, batch, cap, st);
+  };
+  CQ_TRY(gemm(G_G1));                          // G1 = B B^H
+  CQ_TRY(chol_inv(dims, ptrs, batch, 0, st));  // R1, J = R1^-1
+  CQ_TRY(gemm(G_Q1));                          // Q1 = B^H R1^-1
+  CQ_TRY(gemm(G_G2));                          // G2 = Q1^H Q1
+  CQ_TRY(chol_inv(dims, ptrs, batch, 1, st));  // R2, J = R2^-1
+  CQ_TRY(gemm(G_QB));                          // Qb = Q1 R2^-1
+  CQ_TRY(gemm(G_X));                           // X = B Qb = Rb^H
   // ill-conditioned instances: Householder QR of B^H (overwrites X and Qb)
   return launch_qr(QR_BH, dims, ptrs, batch, st, 1);
 }

@@ -107,9 +107,6 @@ cudaError_t launch_qr_sized(int stage, const Dims* dims, const ProbPtr* ptrs, in
                            cudaStream_t st, int force = 0);
 // true when launch_qr_sized(stage, ..., force) runs the many-CTA form
 bool qr_multi_chosen(int stage, const Caps& cap, int batch, int force);
-// Cholesky QR (two passes) of B^H for well-conditioned instances, Householder
-// for the others (cholqr.cu); writes dims[p].qflag
-cudaError_t run_cholqr_bh(Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, cudaStream_t st);
 size_t qr_multi_scratch_r(int l);
 size_t qr_multi_scratch_j(int l);
 cudaError_t launch_jacobi(const Dims* dims, const ProbPtr* ptrs, int batch, int* status, cudaStream_t st);

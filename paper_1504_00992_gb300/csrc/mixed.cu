@@ -482,6 +482,13 @@ MixedSizes mixed_sizes(int m, int n, int k, int l, int bf16) {
   s.thfb = s.bf16 ? (size_t)m * s.K1b * 2 : 0;
   s.thab = s.bf16 ? (size_t)n * s.K2b * 2 : 0;
   s.btb = s.bf16 ? (size_t)s.Np * (s.K1b > s.K2b ? s.K1b : s.K2b) * 2 : 0;
+  {
+    const OzStageBytes ob = oz_stage_bytes(m, n, k, l);
+    s.gad = ob.ad;
+    s.gas = ob.as;
+    s.gbd = ob.bd;
+    s.gbs = ob.bs;
+  }
   const int mx = m > n ? m : n;
   s.qs = ((!qr_blk_f32_fits(m, l) && qr_multi_f32_fits(m, l)) || (!qr_blk_f32_fits(n, l) && qr_multi_f32_fits(n, l)))
              ? qr_multi_f32_scratch(mx, l) * sizeof(float2)
@@ -501,7 +508,8 @@ size_t mixed_bytes(const MixedSizes& s, int batch) {
          2 * up256(s.ytf * batch) + up256(s.df * batch) + up256(s.thd * batch) +
          up256((size_t)s.ntile * sizeof(double) * batch) + up256(s.qs * batch) + up256(s.bd * batch) +
          up256(s.bsc * batch) + up256(s.ad * batch) + up256(s.asc * batch) + up256(s.thfb * batch) +
-         up256(s.thab * batch) + up256(s.btb * batch);
+         up256(s.thab * batch) + up256(s.btb * batch) + up256(s.gad * batch) + up256(s.gas * batch) +
+         up256(s.gbd * batch) + up256(s.gbs * batch);
 }
 
 MixedPtrs mixed_carve(char* base, const MixedSizes& s, int batch) {
@@ -531,6 +539,10 @@ MixedPtrs mixed_carve(char* base, const MixedSizes& s, int batch) {
   p.thf_b = s.bf16 ? (uint16_t*)(base + o) : nullptr; o += up256(s.thfb * batch);
   p.tha_b = s.bf16 ? (uint16_t*)(base + o) : nullptr; o += up256(s.thab * batch);
   p.bt_b = s.bf16 ? (uint16_t*)(base + o) : nullptr; o += up256(s.btb * batch);
+  p.gad = (uint16_t*)(base + o); o += up256(s.gad * batch);
+  p.gas = (float*)(base + o); o += up256(s.gas * batch);
+  p.gbd = (uint16_t*)(base + o); o += up256(s.gbd * batch);
+  p.gbs = (float*)(base + o); o += up256(s.gbs * batch);
   return p;
 }
 
@@ -639,7 +651,7 @@ cudaError_t run_rrsvd_mixed(const Dims* dims, const ProbPtr* ptrs, int batch, co
                             int q, uint64_t seed, uint64_t sweep, int64_t chain0, int chain_stride, int* status,
                             int* err, cudaStream_t st, const uint64_t* sweep_dev, const MixedKnobs* knobs,
                             int bf16_form) {
-  const MixedKnobs kn = knobs ? *knobs : MixedKnobs{0, 0, 0, 0};
+  const MixedKnobs kn = knobs ? *knobs : MixedKnobs{0, 0, 0, 0, 0};
   // capacities: every FP32 array is laid out at these sizes, zero-padded past
   // each instance's own (m, n, l) from dims
   const int m = cap.m, n = cap.n, k = cap.k, l = cap.l;
@@ -710,13 +722,18 @@ cudaError_t run_rrsvd_mixed(const Dims* dims, const ProbPtr* ptrs, int batch, co
   MX_TRY(launch_proj_oz(dims, ptrs, mp.Qf, mp.Df, mp.ad, mp.asc, mp.bd, mp.bsc, m, n, l, batch, err, st));  // B^H = A^H Q
   // QR of B^H: Cholesky QR where the one-CTA Householder would run (it falls
   // back to Householder per ill-conditioned instance), else the size rule
+  // the FP64-accurate products after the projection: tensor cores from digit
+  // splits, or double-float GEMMs on the CUDA cores
+  const bool tc = kn.dfg == 1 || (kn.dfg == 0 && oz_stage_rule(cap));
+  const OzScratch oz{mp.gad, mp.gas, mp.gbd, mp.gbs};
   if (kn.qrbh == 3 || (kn.qrbh == 0 && !qr_multi_chosen(QR_BH, cap, batch, 0)))
-    MX_TRY(run_cholqr_bh(const_cast<Dims*>(dims), ptrs, batch, cap, st));
+    MX_TRY(run_cholqr_bh(const_cast<Dims*>(dims), ptrs, batch, cap, st, tc ? &oz : nullptr, err));
   else
     MX_TRY(launch_qr_sized(QR_BH, dims, ptrs, batch, cap, st, kn.qrbh));
   MX_TRY(launch_jacobi_sized(dims, ptrs, batch, cap, status, st, kn.jac));
-  MX_TRY(launch_zgemm_df(G_U, dims, ptrs, batch, cap, st));
-  MX_TRY(launch_zgemm_df(G_V, dims, ptrs, batch, cap, st));
+  for (int stage : {G_U, G_V})
+    MX_TRY(tc ? launch_oz_stage(stage, dims, ptrs, batch, cap, oz, err, st)
+              : launch_zgemm_df(stage, dims, ptrs, batch, cap, st));
   return cudaSuccess;
 }
 

@@ -18,6 +18,7 @@ struct MixedSizes {
   size_t thf, tha, bt, yf, ytf, df, thd;  // bytes per instance
   size_t bd, bsc, ad, asc;  // BF16 digits and block scales of theta and of Q_f^H (tensor-core projection)
   size_t thfb, thab, btb;   // BF16 copies of theta, theta^H and Bt (bf16 only)
+  size_t gad, gas, gbd, gbs;  // digit scratch of the other tensor-core products (oz_stage_bytes)
   size_t qs;     // bytes per instance of the many-CTA FP32 QR's scratch (0: not used)
   int ntile;     // 32 x 32 tiles of the theta conversion (partials of ||theta||_F^2)
 };
@@ -43,6 +44,10 @@ struct MixedPtrs {
   uint16_t* thf_b;  // m x K1b BF16 theta (bf16 form), or null
   uint16_t* tha_b;  // n x K2b BF16 theta^H
   uint16_t* bt_b;   // Np x max(K1b, K2b) BF16 right operand
+  uint16_t* gad;  // digit scratch of the Cholesky QR and U / V products (OzScratch)
+  float* gas;
+  uint16_t* gbd;
+  float* gbs;
   double* tpart;  // ntile partial sums of |theta|^2 per instance
   float2* qscr;   // scratch of the many-CTA FP32 QR (qs bytes per instance), or null
 };
@@ -88,6 +93,31 @@ int oz_kpad(int m);
 size_t oz_digits_bytes(int rows, int m);
 size_t oz_scales_bytes(int rows, int m);
 cudaError_t oz_prepare();
+// The other FP64-accurate products on the tensor cores (GemmStage G_G1 ..
+// G_X of the Cholesky QR, G_U, G_V): digit scratch of both operands, sized
+// by oz_stage_bytes for the capacities, reused by every stage.
+struct OzScratch {
+  uint16_t* ad;
+  float* as;
+  uint16_t* bd;
+  float* bs;
+};
+struct OzStageBytes {
+  size_t ad, as, bd, bs;  // per instance
+};
+OzStageBytes oz_stage_bytes(int m, int n, int k, int l);
+cudaError_t launch_oz_stage(int stage, const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap,
+                            const OzScratch& sc, int* err, cudaStream_t st);
+// the size rule of MixedKnobs::dfg: the tensor-core products for bonds whose
+// products are deep and wide enough to fill the digit-pair pipeline
+bool oz_stage_rule(const Caps& cap);
+
+// Cholesky QR (two passes) of B^H for well-conditioned instances, Householder
+// for the others (cholqr.cu); writes dims[p].qflag.  oz: the products on the
+// tensor cores (raising *err on a pipeline stall), or null for double-float
+// GEMMs.
+cudaError_t run_cholqr_bh(Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, cudaStream_t st,
+                          const OzScratch* oz, int* err);
 cudaError_t launch_oz_digits_theta(const Dims* dims, const ProbPtr* ptrs, uint16_t* Bd, float* Bs, int m, int n,
                                    int batch, cudaStream_t st);
 cudaError_t launch_proj_oz(const Dims* dims, const ProbPtr* ptrs, const float2* Qf, const float2* Dbuf,
@@ -101,8 +131,11 @@ cudaError_t launch_proj_oz(const Dims* dims, const ProbPtr* ptrs, const float2* 
 // Householder, 3 Cholesky QR with Householder for ill-conditioned instances;
 // the size rule takes the Cholesky QR wherever it would run the one-CTA
 // kernel); jac forces the Jacobi SVD as in launch_jacobi_sized.
+// Launch choices of the mixed form (0: the size rule).  dfg: the Cholesky QR
+// and U / V products on the tensor cores (digit splits, 0 by rule / 1) or as
+// double-float CUDA-core GEMMs (2).
 struct MixedKnobs {
-  int tc_half, qr_threads, qrbh, jac;
+  int tc_half, qr_threads, qrbh, jac, dfg;
 };
 
 // Everything that must happen outside a stream capture before

@@ -35,6 +35,14 @@
 // digits of Re and Im of Q_f^H (the conjugate folded in) and Br, Bi those of
 // A; the minus sign is the MMA's negate-A bit.
 //
+// The same kernel serves the other FP64-accurate products of the mixed form
+// (k_oz_gemm<stage>): the Cholesky QR of B^H (Gram matrices B B^H and
+// Q1^H Q1, the triangular products B^H R1^-1 and Q1 R2^-1, and B Qb) and
+// U = Q J_k, V = Qb W_k.  Their operands are FP64 (the stage table of
+// stages.cuh gives the layout); k_oz_digits_op cuts them into the same
+// digits, and a conjugated left operand flips the negate bits of the MMAs
+// that take its imaginary digits instead of negating them.
+//
 // Kernel structure (one CTA = 128 rows of C (l) x OZ_BN = 48 columns (n), all
 // k): warp 0 lane 0 streams the digit tiles of each 16-deep k step with 5-D
 // TMA loads (k, row, digit, re/im, instance; 32-byte swizzle) into a ring of
@@ -48,6 +56,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "../../include/tebd_gb300.h"
@@ -55,6 +64,7 @@
 #include "internal.cuh"
 #include "mixed.cuh"
 #include "profiler.cuh"
+#include "stages.cuh"
 #include "tc_sync.cuh"
 #include "workspace.cuh"
 
@@ -231,6 +241,108 @@ __global__ void __launch_bounds__(256) k_oz_digits_q(const Dims* __restrict__ di
 }
 
 // ---------------------------------------------------------------------------
+// Stages.  OZ_PROJ is the projection C = Q_f^H A (l x n, K = m), written as
+// B^H = C^H into Yt; the others are the GemmStage products of stages.cuh,
+// C = op(A) op(B) with op(A) conjugated where StageFlags says so and C
+// stored conjugated for G_V.
+// ---------------------------------------------------------------------------
+enum { OZ_PROJ = 100 };
+
+struct OzOp {
+  int M, N, K;  // rows and columns of C, depth
+  cplx* C;
+  int64_t crs, ccs;
+};
+
+template <int ST>
+__device__ __forceinline__ OzOp oz_op(const Dims& D, const ProbPtr& P) {
+  OzOp o;
+  if constexpr (ST == OZ_PROJ) {
+    o.M = D.l; o.N = D.n; o.K = D.m;
+    o.C = P.Yt; o.crs = D.n; o.ccs = 1;  // element (j, i) of the n x l column-major B^H
+  } else {
+    const GemmOp g = gemm_of<ST>(D, P);
+    o.M = g.M; o.N = g.N; o.K = g.K;
+    o.C = g.C; o.crs = g.crs; o.ccs = g.ccs;
+  }
+  return o;
+}
+
+template <int ST>
+struct OzConj {
+  static constexpr bool A = ST != OZ_PROJ && StageFlags<ST>::conjA;  // the projection folds it into Q's digits
+  static constexpr bool C = ST == OZ_PROJ || StageFlags<ST>::conjC;
+};
+
+// Digits of a stage operand in its K-major view: SIDE 0 the rows i of op(A)
+// (element A[i ars + k acs], not conjugated: the MMAs conjugate), SIDE 1 the
+// columns j of op(B) (element B[k brs + j bcs]); into Xd[z][reim][t][row][k]
+// (rows rc, Kp per row) and scales Xs[z][kb][row].  A CTA takes 16 rows x 64
+// k; rows and k past the instance's own extents become zero digits.
+template <int ST, int SIDE>
+__global__ void __launch_bounds__(256) k_oz_digits_op(const Dims* __restrict__ dims, const ProbPtr* __restrict__ ptrs,
+                                                      uint16_t* Xd, float* Xs, int rc, int Kp) {
+  __shared__ cplx tile[16][OZ_KB + 1];
+  __shared__ uint16_t dig[2 * OZ_S][16][OZ_KB + 2];  // [reim t][row][k]
+  const int z = blockIdx.z;
+  const Dims D = dims[z];
+  if (!D.active) return;
+  const GemmOp g = gemm_of<ST>(D, ptrs[z]);
+  const int rows = SIDE == 0 ? g.M : g.N, K = g.K;
+  const cplx* X = SIDE == 0 ? g.A : g.B;
+  const int64_t rs = SIDE == 0 ? g.ars : g.bcs;  // between rows of the K-major view
+  const int64_t ks = SIDE == 0 ? g.acs : g.brs;  // along k
+  const int r0 = blockIdx.x * 16, k0 = blockIdx.y * OZ_KB;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < 16 * OZ_KB; e += 256) {
+    int r, k;  // consecutive threads along the unit-stride direction
+    if (rs == 1) { r = e & 15; k = e >> 4; } else { k = e & (OZ_KB - 1); r = e >> 6; }
+    const int gr = r0 + r, gk = k0 + k;
+    tile[r][k] = (gr < rows && gk < K) ? X[(int64_t)gr * rs + (int64_t)gk * ks] : cmk(0.0, 0.0);
+  }
+  __syncthreads();
+  const int r = tid >> 4, pq = tid & 15;  // 16 threads per row, 4 k each
+  cplx v[4];
+  int E = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    v[q] = tile[r][pq * 4 + q];
+    const uint64_t ur = (uint64_t)__double_as_longlong(v[q].x), ui = (uint64_t)__double_as_longlong(v[q].y);
+    const int er = (int)((ur >> 52) & 0x7FF), ei = (int)((ui >> 52) & 0x7FF);
+    E = max(E, max(er == 0x7FF ? 0 : er, ei == 0x7FF ? 0 : ei));
+  }
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) E = max(E, __shfl_xor_sync(0xffffffffu, E, o));  // within the row's 16 lanes
+  const float sc = oz_scale(E, 1030);
+  const bool live = sc != 0.f;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int k = pq * 4 + q;
+    const uint64_t nr = live ? oz_n48_f64(v[q].x, E) : 0, ni = live ? oz_n48_f64(v[q].y, E) : 0;
+    const bool sr = v[q].x < 0.0, si = v[q].y < 0.0;
+#pragma unroll
+    for (int t = 0; t < OZ_S; ++t) {
+      dig[t][r][k] = oz_bf16_digit((unsigned)((nr >> (40 - 8 * t)) & 0xFF), t, sr);
+      dig[OZ_S + t][r][k] = oz_bf16_digit((unsigned)((ni >> (40 - 8 * t)) & 0xFF), t, si);
+    }
+  }
+  if (pq == 0 && r0 + r < rc) Xs[((size_t)z * (Kp / OZ_KB) + blockIdx.y) * rc + r0 + r] = live ? sc : 0.f;
+  __syncthreads();
+  uint16_t* base = Xd + (size_t)z * 2 * OZ_S * rc * Kp;
+  for (int w = tid; w < 2 * OZ_S * 16 * 8; w += 256) {
+    const int q = w & 7, row = w >> 3, rr = row & 15, rt = row >> 4;
+    if (r0 + rr >= rc) continue;
+    const uint16_t* src = &dig[rt][rr][q * 8];
+    uint4 pk;
+    pk.x = (unsigned)src[0] | ((unsigned)src[1] << 16);
+    pk.y = (unsigned)src[2] | ((unsigned)src[3] << 16);
+    pk.z = (unsigned)src[4] | ((unsigned)src[5] << 16);
+    pk.w = (unsigned)src[6] | ((unsigned)src[7] << 16);
+    *reinterpret_cast<uint4*>(base + ((size_t)rt * rc + r0 + rr) * Kp + k0 + q * 8) = pk;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // The digit-pair GEMM.
 // ---------------------------------------------------------------------------
 struct OzArgs {
@@ -308,14 +420,17 @@ __device__ __forceinline__ void oz_df_add(float& h, float& l, float hs, float ls
   l = e - (h - t);
 }
 
+template <int ST>
 __global__ void __launch_bounds__(OZ_THREADS, 1)
-    k_oz_proj(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+    k_oz_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               const Dims* __restrict__ dims, const ProbPtr* __restrict__ ptrs, OzArgs a) {
   extern __shared__ __align__(1024) uint8_t oz_smem_raw[];
   const int z = blockIdx.z;
   const Dims D = dims[z];
   const int i0 = blockIdx.y * OZ_BM, j0 = blockIdx.x * OZ_BN;
-  if (!D.active || i0 >= D.l || j0 >= D.n) return;  // uniform: before any barrier or allocation
+  if (!D.active) return;
+  const OzOp op = oz_op<ST>(D, ptrs[z]);
+  if (i0 >= op.M || j0 >= op.N) return;  // uniform: before any barrier or allocation
   uint8_t* smem = (uint8_t*)(((uintptr_t)oz_smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;
   uint8_t* sB = smem + OZ_STAGES * OZ_A_STAGE;
@@ -328,7 +443,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   volatile int* abort_flag = (volatile int*)(tmem_holder + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int nks = (min(D.m, a.Kp) + OZ_KS - 1) / OZ_KS;  // k steps of this instance
+  const int nks = (min(op.K, a.Kp) + OZ_KS - 1) / OZ_KS;  // k steps of this instance
   const int nkb = (nks + (OZ_DRAIN / OZ_KS) - 1) / (OZ_DRAIN / OZ_KS);  // exact accumulation blocks
   const int iters = nkb * (OZ_DRAIN / OZ_KS);  // whole blocks (zero digits past m)
 
@@ -410,10 +525,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
               const uint64_t ai = oz_desc_sw32(abase + (1 * OZ_S + t - 1) * OZ_A_TILE);
               const uint64_t br = oz_desc_sw32(bbase + (0 * OZ_S + u - 1) * OZ_B_TILE);
               const uint64_t bi = oz_desc_sw32(bbase + (1 * OZ_S + u - 1) * OZ_B_TILE);
-              oz_mma(dr, ar, br, ip, first ? 0u : 1u);  // C_r += Ar Br
-              oz_mma(dr, ai, bi, in, 1u);               // C_r -= Ai Bi
-              oz_mma(di, ar, bi, ip, first ? 0u : 1u);  // C_i += Ar Bi
-              oz_mma(di, ai, br, ip, 1u);               // C_i += Ai Br
+              // (conjugated left operand: C_r += Ai Bi, C_i -= Ai Br)
+              oz_mma(dr, ar, br, ip, first ? 0u : 1u);             // C_r += Ar Br
+              oz_mma(dr, ai, bi, OzConj<ST>::A ? ip : in, 1u);     // C_r -= Ai Bi
+              oz_mma(di, ar, bi, ip, first ? 0u : 1u);             // C_i += Ar Bi
+              oz_mma(di, ai, br, OzConj<ST>::A ? in : ip, 1u);     // C_i += Ai Br
               ++pi;
             }
           }
@@ -478,12 +594,14 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       __syncwarp();
       if (lane == 0) oz_arrive(accfree);  // the accumulators may be overwritten
     }
-    if (ok && i < D.l) {
-      cplx* X = ptrs[z].Yt;  // B^H = C^H: n x l column-major, element (j, i) = conj C[i][j]
+    if (ok && i < op.M) {
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
         const int j = jq + c;
-        if (j < D.n) X[(size_t)i * D.n + j] = cmk((double)hr[c] + (double)lr[c], -((double)hi[c] + (double)li[c]));
+        if (j < op.N) {
+          const double re = (double)hr[c] + (double)lr[c], im = (double)hi[c] + (double)li[c];
+          op.C[(int64_t)i * op.crs + (int64_t)j * op.ccs] = cmk(re, OzConj<ST>::C ? -im : im);
+        }
       }
     }
   }
@@ -539,15 +657,100 @@ int oz_kpad(int m) { return ((m + OZ_KB - 1) / OZ_KB) * OZ_KB; }
 size_t oz_digits_bytes(int rows, int m) { return (size_t)2 * OZ_S * rows * oz_kpad(m) * sizeof(uint16_t); }
 size_t oz_scales_bytes(int rows, int m) { return (size_t)(oz_kpad(m) / OZ_KB) * rows * sizeof(float); }
 
+template <int ST>
+static cudaError_t oz_attr() {
+  return cudaFuncSetAttribute(k_oz_gemm<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes());
+}
+
 cudaError_t oz_prepare() {
   if (!oz_encode_fn()) return cudaErrorNotSupported;
   static int done = 0;
   if (!done) {
-    const cudaError_t e = cudaFuncSetAttribute(k_oz_proj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes());
-    if (e != cudaSuccess) return e;
+    const cudaError_t es[] = {oz_attr<OZ_PROJ>(), oz_attr<G_G1>(), oz_attr<G_Q1>(), oz_attr<G_G2>(),
+                              oz_attr<G_QB>(),    oz_attr<G_X>(),  oz_attr<G_U>(),  oz_attr<G_V>()};
+    for (cudaError_t e : es)
+      if (e != cudaSuccess) return e;
     done = 1;
   }
   return cudaSuccess;
+}
+
+// Capacities (rows of C, columns of C, depth) of a stage's product.
+static void oz_stage_caps(int stage, int m, int n, int k, int l, int& Mc, int& Nc, int& Kc) {
+  switch (stage) {
+    case G_G1: case G_G2: case G_X: Mc = l; Nc = l; Kc = n; break;
+    case G_Q1: case G_QB: Mc = n; Nc = l; Kc = l; break;
+    case G_U: Mc = m; Nc = k; Kc = l; break;
+    default: Mc = n; Nc = k; Kc = l; break;  // G_V
+  }
+}
+
+bool oz_stage_rule(const Caps& cap) { return cap.l >= 48 && (cap.m >= 256 || cap.n >= 256); }
+
+static const int OZ_STAGE_LIST[] = {G_G1, G_Q1, G_G2, G_QB, G_X, G_U, G_V};
+
+OzStageBytes oz_stage_bytes(int m, int n, int k, int l) {
+  OzStageBytes b{0, 0, 0, 0};
+  for (int stage : OZ_STAGE_LIST) {
+    int Mc, Nc, Kc;
+    oz_stage_caps(stage, m, n, k, l, Mc, Nc, Kc);
+    b.ad = std::max(b.ad, oz_digits_bytes(Mc, Kc));
+    b.as = std::max(b.as, oz_scales_bytes(Mc, Kc));
+    b.bd = std::max(b.bd, oz_digits_bytes(Nc, Kc));
+    b.bs = std::max(b.bs, oz_scales_bytes(Nc, Kc));
+  }
+  return b;
+}
+
+template <int ST>
+static cudaError_t oz_stage_run(const Dims* dims, const ProbPtr* ptrs, int batch, int Mc, int Nc, int Kc,
+                                const OzScratch& sc, int* err, cudaStream_t st) {
+  const int Kp = oz_kpad(Kc);
+  // G1 and G2 multiply an operand by its own adjoint: one set of digits
+  const bool same = ST == G_G1 || ST == G_G2;
+  {
+    ProfScope ps("k_oz_digits[op]", st);
+    k_oz_digits_op<ST, 0><<<dim3((Mc + 15) / 16, Kp / OZ_KB, batch), 256, 0, st>>>(dims, ptrs, sc.ad, sc.as, Mc, Kp);
+    if (!same)
+      k_oz_digits_op<ST, 1><<<dim3((Nc + 15) / 16, Kp / OZ_KB, batch), 256, 0, st>>>(dims, ptrs, sc.bd, sc.bs, Nc,
+                                                                                      Kp);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  CUtensorMap ta, tb;
+  if (!oz_make_map(&ta, sc.ad, Kp, Mc, batch, OZ_BM) || !oz_make_map(&tb, same ? sc.ad : sc.bd, Kp, Nc, batch, OZ_BN))
+    return cudaErrorInvalidValue;
+  OzArgs oa;
+  oa.lc = Mc;
+  oa.nc = Nc;
+  oa.Kp = Kp;
+  oa.As = sc.as;
+  oa.Bs = same ? sc.as : sc.bs;
+  oa.err = err;
+  oa.poll_limit = 1u << 24;
+  oa.stall = 0;
+  ProfScope ps(ST == G_U || ST == G_V ? "k_oz_gemm[uv]" : "k_oz_gemm[cholqr]", st);
+  k_oz_gemm<ST><<<dim3((Nc + OZ_BN - 1) / OZ_BN, (Mc + OZ_BM - 1) / OZ_BM, batch), OZ_THREADS, oz_smem_bytes(), st>>>(
+      ta, tb, dims, ptrs, oa);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_oz_stage(int stage, const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap,
+                            const OzScratch& sc, int* err, cudaStream_t st) {
+  const cudaError_t e = oz_prepare();
+  if (e != cudaSuccess) return e;
+  int Mc, Nc, Kc;
+  oz_stage_caps(stage, cap.m, cap.n, cap.k, cap.l, Mc, Nc, Kc);
+  switch (stage) {
+    case G_G1: return oz_stage_run<G_G1>(dims, ptrs, batch, Mc, Nc, Kc, sc, err, st);
+    case G_Q1: return oz_stage_run<G_Q1>(dims, ptrs, batch, Mc, Nc, Kc, sc, err, st);
+    case G_G2: return oz_stage_run<G_G2>(dims, ptrs, batch, Mc, Nc, Kc, sc, err, st);
+    case G_QB: return oz_stage_run<G_QB>(dims, ptrs, batch, Mc, Nc, Kc, sc, err, st);
+    case G_X: return oz_stage_run<G_X>(dims, ptrs, batch, Mc, Nc, Kc, sc, err, st);
+    case G_U: return oz_stage_run<G_U>(dims, ptrs, batch, Mc, Nc, Kc, sc, err, st);
+    case G_V: return oz_stage_run<G_V>(dims, ptrs, batch, Mc, Nc, Kc, sc, err, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_oz_digits_theta(const Dims* dims, const ProbPtr* ptrs, uint16_t* Bd, float* Bs, int m, int n,
@@ -589,8 +792,8 @@ cudaError_t launch_proj_oz(const Dims* dims, const ProbPtr* ptrs, const float2* 
     oa.poll_limit = stall ? (1u << 12) : (1u << 24);
     oa.stall = stall ? 1 : 0;
     ProfScope ps("k_oz_proj[project]", st);
-    k_oz_proj<<<dim3((n + OZ_BN - 1) / OZ_BN, (l + OZ_BM - 1) / OZ_BM, batch), OZ_THREADS, oz_smem_bytes(), st>>>(
-        ta, tb, dims, ptrs, oa);
+    k_oz_gemm<OZ_PROJ><<<dim3((n + OZ_BN - 1) / OZ_BN, (l + OZ_BM - 1) / OZ_BM, batch), OZ_THREADS, oz_smem_bytes(),
+                         st>>>(ta, tb, dims, ptrs, oa);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

@@ -220,3 +220,39 @@ def test_mixed_qr_of_bh_cholesky_and_householder_in_one_batch(lib):
         assert np.abs(U.conj().T @ U - np.eye(r)).max() < 1e-11
         V = res["Vh"][t][:r]
         assert np.abs(V @ V.conj().T - np.eye(r)).max() < 1e-11
+
+
+def test_products_after_the_projection_on_either_unit(lib):
+    """The Cholesky QR of B^H and U = Q J_k, V = Qb W_k run on the tensor
+    cores from exact BF16 digit splits (48-bit digits, the projection's
+    kernel) or as double-float CUDA-core GEMMs; both are FP64-accurate, so a
+    plan forced to either gives the same truncation to rounding (1e-12 s_1),
+    and both meet the form's tolerances.  A choice out of range is refused."""
+    from paper_1504_00992_gb300 import binding as B
+    m, n, k, p, q, batch = 600, 520, 60, 20, 1, 3
+    sig = I.exp_spectrum(min(m, n), 10.0)
+    theta = np.stack([I.synthetic_theta(m, n, sig, seed=700 + t) for t in range(batch)])
+    out = {}
+    for unit in (1, 2):
+        plan = B.rrsvd_plan_create(m, n, k, p, q, batch, B.TEBD_PREC_TF32, SEED)
+        try:
+            B.rrsvd_plan_set_tuning(plan, {"products": unit})
+            assert B.rrsvd_plan_tuning(plan)["products"] == unit
+            with pytest.raises(B.TebdError):
+                B.rrsvd_plan_set_tuning(plan, {"products": 3})
+            out[unit] = rrsvd_device(B, plan, theta, chain0=5)
+        finally:
+            B.rrsvd_plan_destroy(plan)
+    kk, l = R.sketch_sizes(m, n, k, p)
+    for t in range(batch):
+        a, b = out[1], out[2]
+        assert np.abs(a["sigma"][t] - b["sigma"][t]).max() <= 1e-12 * sig[0]
+        ra = truncated(a["U"][t], a["sigma"][t], a["Vh"][t])
+        rb = truncated(b["U"][t], b["sigma"][t], b["Vh"][t])
+        assert np.linalg.norm(ra - rb) <= 1e-11 * np.linalg.norm(theta[t])
+        for r in (a, b):
+            U, V = r["U"][t], r["Vh"][t]
+            assert np.abs(U.conj().T @ U - np.eye(kk)).max() < 1e-11
+            assert np.abs(V @ V.conj().T - np.eye(kk)).max() < 1e-11
+            _, sk, _, _ = R.rrsvd_truncate(theta[t], gaussian_omega(n, l, SEED, chain=5 + t), kk, q)
+            assert np.abs(r["sigma"][t] - sig[:kk]).max() <= np.abs(sk - sig[:kk]).max() + 1e-8 * sig[0]

@@ -40,5 +40,7 @@ def test_argument_errors_need_no_device(libpath):
     assert L.tebd_create(4, 2, 4, 2, 1, 0, None) == binding.TEBD_EINVAL
     assert L.rrsvd_plan_create(0, 4, 2, 1, 1, 1, 0, 0, ctypes.byref(h)) == binding.TEBD_EINVAL
     assert L.rrsvd_plan_create(4, 4, 2, 1, 1, 1, 7, 0, ctypes.byref(h)) == binding.TEBD_ENOTIMPL
+    info = (ctypes.c_int * 16)()
+    assert L.rrsvd_plan_set_tuning(None, info) == binding.TEBD_EINVAL
     assert L.tebd_destroy(None) == binding.TEBD_OK
     assert L.rrsvd_plan_destroy(None) == binding.TEBD_OK
