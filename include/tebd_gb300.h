@@ -387,7 +387,9 @@ int rrsvd_plan_autotune(rrsvd_plan_t plan, const double* theta, void* workspace,
 
 /* What the autotuner chose: info (16 ints): [0..5] the FP64 GEMM tile of
  * stages Y0, Y~, Y, B^H, U, V (0: by grid size), [6..9] the mixed form's
- * choices (tile split, FP32 QR threads, QR of B^H, Jacobi; 0: the size rule),
+ * choices (tile split, FP32 QR threads, QR of B^H, Jacobi; 0: the size rule;
+ * Jacobi 1: one CTA in FP64, 2: a cluster per instance in FP64, 3: one CTA
+ * in double-float arithmetic),
  * [10] 1 once tuned, [11] the FP64-accurate products after the projection
  * (0: the size rule, 1: tensor cores from digit splits, 2: double-float
  * CUDA-core GEMMs), [12..15] zero; ms (2 doubles, TF32 plans): the step with the size
@@ -399,7 +401,7 @@ int rrsvd_plan_tuning(rrsvd_plan_t plan, int* info, double* ms);
  * in another process or to compare two of them.  The plan counts as tuned
  * afterwards.  Results agree with those of any other choice to rounding.
  * Errors: TEBD_EINVAL (NULL, a tile other than 0, 16 or 32, a choice out of
- * range: [6] 0..1, [7] 0, 128, 256 or 512, [8] 0..3, [9] 0..2, [11] 0..2). */
+ * range: [6] 0..1, [7] 0, 128, 256 or 512, [8] 0..3, [9] 0..3, [11] 0..2). */
 int rrsvd_plan_set_tuning(rrsvd_plan_t plan, const int* info);
 
 /* Clears the plan's recorded error and its device status flags (a zero or

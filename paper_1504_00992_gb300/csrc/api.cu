@@ -372,7 +372,7 @@ static int tune_knobs(Run run, cudaStream_t st, const Caps& cap, int batch, Mixe
   t_rule = t_best;
   const bool multi_ok = cap.n >= 1024 && cap.l >= 16;  // the many-CTA QR's structure (its own rule adds the batch)
   const bool cl_ok = cap.l >= 64 && cap.l <= 512;
-  std::vector<std::vector<int>> cand = {{0, 1}, {0, 512, 256, 128}, {0, 1, 2, 3}, {0, 1, 2}, {0, 1, 2}};
+  std::vector<std::vector<int>> cand = {{0, 1}, {0, 512, 256, 128}, {0, 1, 2, 3}, {0, 1, 2, 3}, {0, 1, 2}};
   for (int knob = 0; knob < 5 && ok; ++knob)
     for (int v : cand[knob]) {
       MixedKnobs k = best;
@@ -1776,7 +1776,7 @@ extern "C" int rrsvd_plan_set_tuning(rrsvd_plan_t P, const int* info) {
     if (info[i] != 0 && info[i] != 16 && info[i] != 32) return TEBD_EINVAL;
   const int th = info[7];
   if (info[6] < 0 || info[6] > 1 || (th != 0 && th != 128 && th != 256 && th != 512) || info[8] < 0 ||
-      info[8] > 3 || info[9] < 0 || info[9] > 2 || info[11] < 0 || info[11] > 2)
+      info[8] > 3 || info[9] < 0 || info[9] > 3 || info[11] < 0 || info[11] > 2)
     return TEBD_EINVAL;
   for (int i = 0; i < 6; ++i) P->tiles[i] = info[i];
   P->mk = MixedKnobs{info[6], info[7], info[8], info[9], info[11]};

@@ -187,11 +187,14 @@ __global__ void __cluster_dims__(JC_CL, 1, 1) __launch_bounds__(JC_THREADS)
   }
 }
 
+bool jacobi_cluster_chosen(const Caps& cap, int batch, int force) {
+  const bool fits = cap.l >= JC_MIN_L && cap.l <= JC_MAXL;
+  return force == 2 ? fits : (force == 0 && fits && batch <= JC_MAX_BATCH);
+}
+
 cudaError_t launch_jacobi_sized(const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, int* status,
                                 cudaStream_t st, int force) {
-  const bool fits = cap.l >= JC_MIN_L && cap.l <= JC_MAXL;
-  const bool cl = force == 2 ? fits : (force == 0 && fits && batch <= JC_MAX_BATCH);
-  if (!cl) return launch_jacobi(dims, ptrs, batch, status, st);
+  if (!jacobi_cluster_chosen(cap, batch, force)) return launch_jacobi(dims, ptrs, batch, status, st);
   ProfScope ps("k_jacobi[cluster]", st);
   k_jacobi_cl<<<batch * JC_CL, JC_THREADS, 0, st>>>(dims, ptrs, status);
   return cudaGetLastError();

@@ -730,7 +730,11 @@ cudaError_t run_rrsvd_mixed(const Dims* dims, const ProbPtr* ptrs, int batch, co
     MX_TRY(run_cholqr_bh(const_cast<Dims*>(dims), ptrs, batch, cap, st, tc ? &oz : nullptr, err));
   else
     MX_TRY(launch_qr_sized(QR_BH, dims, ptrs, batch, cap, st, kn.qrbh));
-  MX_TRY(launch_jacobi_sized(dims, ptrs, batch, cap, status, st, kn.jac));
+  // Jacobi SVD: double-float one-CTA kernel unless the cluster form is chosen
+  if (kn.jac == 3 || (kn.jac == 0 && !jacobi_cluster_chosen(cap, batch, 0)))
+    MX_TRY(launch_jacobi_df(dims, ptrs, batch, status, st));
+  else
+    MX_TRY(launch_jacobi_sized(dims, ptrs, batch, cap, status, st, kn.jac));
   for (int stage : {G_U, G_V})
     MX_TRY(tc ? launch_oz_stage(stage, dims, ptrs, batch, cap, oz, err, st)
               : launch_zgemm_df(stage, dims, ptrs, batch, cap, st));

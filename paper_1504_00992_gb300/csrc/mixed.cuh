@@ -131,7 +131,9 @@ cudaError_t launch_proj_oz(const Dims* dims, const ProbPtr* ptrs, const float2* 
 // Householder, 3 Cholesky QR with Householder for ill-conditioned instances;
 // the size rule takes the Cholesky QR wherever it would run the one-CTA
 // kernel); jac forces the Jacobi SVD as in launch_jacobi_sized.
-// Launch choices of the mixed form (0: the size rule).  dfg: the Cholesky QR
+// Launch choices of the mixed form (0: the size rule).  jac: 1 the one-CTA
+// FP64 Jacobi, 2 the cluster form, 3 the one-CTA double-float one.  dfg: the
+// Cholesky QR
 // and U / V products on the tensor cores (digit splits, 0 by rule / 1) or as
 // double-float CUDA-core GEMMs (2).
 struct MixedKnobs {

@@ -254,13 +254,15 @@ __device__ __forceinline__ double grp_sum(double v, unsigned mask) {
   return v;
 }
 
+__device__ __forceinline__ void jacobi_finish(const Dims& D, const ProbPtr& P, double* sv, int* perm);
+
 // One-sided Jacobi SVD of one problem by the whole CTA (any multiple of
 // JAC_G threads, at least 32); sv, nrm, perm >= l entries and red >= 32
 // doubles of shared memory, rotated one shared int.
 __device__ __forceinline__ void jacobi_dev(const Dims& D, const ProbPtr& P, int* status, double* sv, double* nrm,
                                            int* perm, int* rotated_p, double* red) {
   int& rotated = *rotated_p;
-  const int L = D.l, K = D.k;
+  const int L = D.l;
   cplx* X = P.R;
   cplx* J = P.J;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
@@ -338,7 +340,18 @@ __device__ __forceinline__ void jacobi_dev(const Dims& D, const ProbPtr& P, int*
     if (!any) break;
   }
   if (sweep == JAC_MAXSWEEPS && tid == 0) atomicOr(status, 2);  // not converged (non-fatal)
-  // singular values = column norms
+  jacobi_finish(D, P, sv, perm);
+}
+
+// After the sweeps (X = P.R holds X J = W S, J = P.J): singular values =
+// column norms, sorted descending (ties by lower index; a NaN value ranks
+// below every number, so perm is a permutation of 0..L-1 whatever the input),
+// Jk = the leading k normalised columns of X J, Wk = the matching columns of J.
+__device__ __forceinline__ void jacobi_finish(const Dims& D, const ProbPtr& P, double* sv, int* perm) {
+  const int L = D.l, K = D.k;
+  const cplx* X = P.R;
+  const cplx* J = P.J;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   for (int c = warp; c < L; c += nw) {
     const cplx* xc = X + (int64_t)c * L;
     double s = 0.0;
@@ -347,8 +360,6 @@ __device__ __forceinline__ void jacobi_dev(const Dims& D, const ProbPtr& P, int*
     if (lane == 0) sv[c] = sqrt(s);
   }
   __syncthreads();
-  // rank by descending value, ties by index; a NaN value ranks below every
-  // number, so perm is a permutation of 0..L-1 whatever the input
   for (int c = tid; c < L; c += blockDim.x) {
     const double s = (sv[c] == sv[c]) ? sv[c] : -1.0;
     int rk = 0;

@@ -256,3 +256,37 @@ def test_products_after_the_projection_on_either_unit(lib):
             assert np.abs(V @ V.conj().T - np.eye(kk)).max() < 1e-11
             _, sk, _, _ = R.rrsvd_truncate(theta[t], gaussian_omega(n, l, SEED, chain=5 + t), kk, q)
             assert np.abs(r["sigma"][t] - sig[:kk]).max() <= np.abs(sk - sig[:kk]).max() + 1e-8 * sig[0]
+
+
+@pytest.mark.parametrize("m,n,k,p", [(600, 520, 60, 20), (300, 260, 230, 20)])
+def test_double_float_jacobi_agrees_with_fp64(lib, m, n, k, p):
+    """The small SVD of the mixed form (one-sided Jacobi on Rb^H) in
+    double-float arithmetic against the FP64 kernel on the same B: singular
+    values within 1e-12 s_1 (2^-48 arithmetic over a few hundred rotations per
+    column), both factor sets orthonormal to 1e-11, and the same truncation.
+    The second case keeps l = 250 columns, the spectrum falling to 1e-11."""
+    from paper_1504_00992_gb300 import binding as B
+    batch = 3
+    sig = I.exp_spectrum(min(m, n), 10.0)
+    theta = np.stack([I.synthetic_theta(m, n, sig, seed=900 + t) for t in range(batch)])
+    out = {}
+    for jac in (1, 3):
+        plan = B.rrsvd_plan_create(m, n, k, p, 1, batch, B.TEBD_PREC_TF32, SEED)
+        try:
+            B.rrsvd_plan_set_tuning(plan, {"jacobi": jac})
+            out[jac] = rrsvd_device(B, plan, theta, chain0=11)
+        finally:
+            B.rrsvd_plan_destroy(plan)
+    kk, _ = R.sketch_sizes(m, n, k, p)
+    for t in range(batch):
+        a, b = out[3], out[1]
+        assert a["rank"][t] == b["rank"][t]
+        r = a["rank"][t]
+        assert np.abs(a["sigma"][t][:r] - b["sigma"][t][:r]).max() <= 1e-12 * sig[0]
+        for res in (a, b):
+            U, V = res["U"][t][:, :r], res["Vh"][t][:r]
+            assert np.abs(U.conj().T @ U - np.eye(r)).max() < 1e-11
+            assert np.abs(V @ V.conj().T - np.eye(r)).max() < 1e-11
+        ra = truncated(a["U"][t], a["sigma"][t], a["Vh"][t])
+        rb = truncated(b["U"][t], b["sigma"][t], b["Vh"][t])
+        assert np.linalg.norm(ra - rb) <= 1e-11 * np.linalg.norm(theta[t])
