@@ -18,12 +18,13 @@
 //   level 2 (t + u = 2): one digit pair, 64 products: exact;
 //   level 3: two pairs, 128 products; level 4: three pairs, 192 products;
 //   level 5: four pairs, 256 products (< 2^23.99 units): all exact;
-//   levels 6 and 7: summed together in FP32 (each rounding 2^-56 of the
-//   level-2 sum); digit pairs with t + u > 7 are dropped (2^-48 relative).
-// Each block therefore runs into ten accumulators in tensor memory (C_r and
-// C_i at levels 2, 3, 4, 5, 6+), which the epilogue warps read after every
-// block, scale by the two block scales and add into double-float (FP32 pair)
-// sums in registers.  Measured on 40-bit digits with levels 4 .. 6 in one
+//   levels 6 and 7: five and six pairs, rounded in FP32 (each rounding 2^-56
+//   of the level-2 sum or less); digit pairs with t + u > 7 are dropped
+//   (2^-48 relative).
+// Each block therefore runs into twelve accumulators in tensor memory (C_r
+// and C_i at levels 2 .. 7), which the epilogue warps read after every block,
+// scale by the two block scales and add into double-float (FP32 pair) sums in
+// registers.  Measured on 40-bit digits with levels 4 .. 6 in one
 // inexact group: ~3e-10 relative (some 10^4 roundings of 2^-40 per output of
 // a 2000-deep product add up like a random walk); with level 4 exact, 1.4e-11
 // (the 40-bit truncation of the digits).  With 48-bit digits and levels 2 .. 5
@@ -43,13 +44,17 @@
 // digits, and a conjugated left operand flips the negate bits of the MMAs
 // that take its imaginary digits instead of negating them.
 //
-// Kernel structure (one CTA = 128 rows of C (l) x OZ_BN = 48 columns (n), all
+// Kernel structure (one CTA = 128 rows of C (l) x OZ_BN = 32 columns (n), all
 // k): warp 0 lane 0 streams the digit tiles of each 16-deep k step with 5-D
 // TMA loads (k, row, digit, re/im, instance; 32-byte swizzle) into a ring of
-// OZ_STAGES stages; warp 1 lane 0 issues 84 tcgen05.mma.kind::f16 per k step
-// (21 digit pairs x 4 real products); warps 2 .. 25 read the accumulators
-// after each k block (warp w reads TMEM lanes 32 (w % 4) .. +31, a sixth of
-// the columns) and keep the double-float sums.  Every mbarrier wait is
+// OZ_STAGES stages; warp 1 lane 0 issues 24 tcgen05.mma.kind::f16 per k step:
+// the digit planes u = 1 .. 6 of a part of A's side lie one after another in
+// shared memory and the accumulators of levels 2 .. 7 one after another in
+// tensor memory, so digit t of the other operand times planes 1 .. 7 - t is
+// one MMA of N = 32 (7 - t) into the accumulators of levels t + 1 .. 7 (six
+// MMAs per real product instead of 21 small ones); warps 2 .. 17 read the
+// accumulators after each k block (warp w reads TMEM lanes 32 (w % 4) .. +31
+// and a quarter of the columns) and keep the double-float sums.  Every mbarrier wait is
 // bounded; on expiry the kernel raises *err, waits for its own copies and
 // MMAs, and frees its tensor memory.
 #include <cuda.h>
@@ -76,13 +81,12 @@ enum {
   OZ_DRAIN = 32,   // k per exact accumulation (the accumulators are read and cleared after each)
   OZ_KS = 16,      // k per MMA / TMA stage
   OZ_BM = 128,     // rows of C per CTA (TMEM lanes)
-  OZ_BN = 48,      // columns of C per CTA
+  OZ_BN = 32,      // columns of C per CTA
   OZ_STAGES = 3,
-  OZ_EPI_WARPS = 24,  // six per TMEM lane quadrant, 8 columns each
+  OZ_EPI_WARPS = 16,  // four per TMEM lane quadrant, 8 columns each
   OZ_THREADS = 64 + 32 * OZ_EPI_WARPS,
-  OZ_NPAIR = 21,
-  OZ_NGRP = 5,     // accumulators per part: levels 2, 3, 4, 5 and 6+
-  OZ_TMEM_COLS = 512  // ten 48-column accumulators, rounded up to a power of two
+  OZ_NGRP = OZ_S,  // accumulators per part: levels 2 .. 7
+  OZ_TMEM_COLS = 512  // twelve 32-column accumulators, rounded up to a power of two
 };
 
 static const uint32_t OZ_A_TILE = OZ_BM * OZ_KS * 2;  // one digit tile of Q_f^H: 4 KB
@@ -405,10 +409,17 @@ __device__ __forceinline__ bool oz_warp_wait(uint64_t* bar, uint32_t parity, uin
   return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
 }
 
-__device__ __forceinline__ float oz_ld1(uint32_t taddr) {
-  uint32_t r;
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr) : "memory");
-  return __uint_as_float(r);
+// four consecutive accumulator columns of this warp's 32 lanes
+__device__ __forceinline__ void oz_ld4(uint32_t taddr, float* v) {
+  uint32_t r0, r1, r2, r3;
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(taddr)
+               : "memory");
+  v[0] = __uint_as_float(r0);
+  v[1] = __uint_as_float(r1);
+  v[2] = __uint_as_float(r2);
+  v[3] = __uint_as_float(r3);
 }
 
 // acc (h, l) += s (hs, ls), then renormalised
@@ -491,9 +502,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     __syncwarp();
   } else if (warp == 1) {
     if (lane == 0) {
-      // ---- MMA issuer: per k step, the 21 digit pairs (t, u) with t + u <= 7
-      // in level order, four real products each
-      const uint32_t ip = oz_idesc(OZ_BM, OZ_BN, false), in = oz_idesc(OZ_BM, OZ_BN, true);
+      // ---- MMA issuer: per k step the 21 digit pairs (t, u) with t + u <= 7,
+      // as six MMAs per real product
       bool ok = true;
       int issued_mma = 0;
       for (int kb = 0; kb < nkb && ok; ++kb) {
@@ -511,29 +521,25 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           }
           tc_fence_after();
           const uint32_t abase = tc_smem_u32(sA + s * OZ_A_STAGE), bbase = tc_smem_u32(sB + s * OZ_B_STAGE);
-          int pi = 0;
+          // digit t of A times planes u = 1 .. 7 - t of B (adjacent in shared
+          // memory) into the accumulators of levels t + 1 .. 7 (adjacent in
+          // tensor memory); the t = 1 MMAs of a block's first k step cover
+          // every level and start the block's sums
+          const uint64_t br = oz_desc_sw32(bbase), bi = oz_desc_sw32(bbase + OZ_S * OZ_B_TILE);
 #pragma unroll 1
-          for (int lv = 2; lv <= OZ_S + 1; ++lv) {
-#pragma unroll 1
-            for (int t = 1; t < lv; ++t) {
-              const int u = lv - t;
-              if (t > OZ_S || u > OZ_S) continue;
-              const int g = lv <= 5 ? lv - 2 : 4;  // accumulator group of the level
-              const bool first = ks == 0 && t == 1 && lv <= 6;  // the group's first digit pair of the block
-              const uint32_t dr = tmem + (uint32_t)(OZ_BN * g), di = tmem + (uint32_t)(OZ_BN * (OZ_NGRP + g));
-              const uint64_t ar = oz_desc_sw32(abase + (0 * OZ_S + t - 1) * OZ_A_TILE);
-              const uint64_t ai = oz_desc_sw32(abase + (1 * OZ_S + t - 1) * OZ_A_TILE);
-              const uint64_t br = oz_desc_sw32(bbase + (0 * OZ_S + u - 1) * OZ_B_TILE);
-              const uint64_t bi = oz_desc_sw32(bbase + (1 * OZ_S + u - 1) * OZ_B_TILE);
-              // (conjugated left operand: C_r += Ai Bi, C_i -= Ai Br)
-              oz_mma(dr, ar, br, ip, first ? 0u : 1u);             // C_r += Ar Br
-              oz_mma(dr, ai, bi, OzConj<ST>::A ? ip : in, 1u);     // C_r -= Ai Bi
-              oz_mma(di, ar, bi, ip, first ? 0u : 1u);             // C_i += Ar Bi
-              oz_mma(di, ai, br, OzConj<ST>::A ? in : ip, 1u);     // C_i += Ai Br
-              ++pi;
-            }
+          for (int t = 1; t <= OZ_S; ++t) {
+            const int N = OZ_BN * (OZ_S + 1 - t);
+            const uint32_t ip = oz_idesc(OZ_BM, N, false), in = oz_idesc(OZ_BM, N, true);
+            const uint32_t acc0 = (ks == 0 && t == 1) ? 0u : 1u;
+            const uint32_t dr = tmem + (uint32_t)(OZ_BN * (t - 1)), di = tmem + (uint32_t)(OZ_BN * (OZ_NGRP + t - 1));
+            const uint64_t ar = oz_desc_sw32(abase + (0 * OZ_S + t - 1) * OZ_A_TILE);
+            const uint64_t ai = oz_desc_sw32(abase + (1 * OZ_S + t - 1) * OZ_A_TILE);
+            // (conjugated left operand: C_r += Ai Bi, C_i -= Ai Br)
+            oz_mma(dr, ar, br, ip, acc0);                         // C_r += Ar Br
+            oz_mma(dr, ai, bi, OzConj<ST>::A ? ip : in, 1u);     // C_r -= Ai Bi
+            oz_mma(di, ar, bi, ip, acc0);                         // C_i += Ar Bi
+            oz_mma(di, ai, br, OzConj<ST>::A ? in : ip, 1u);     // C_i += Ai Br
           }
-          (void)pi;
           oz_commit(&empty[s]);  // the stage is free once these MMAs have read it
           issued_mma = it + 1;
         }
@@ -551,7 +557,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     }
     __syncwarp();
   } else {
-    // ---- epilogue: warp w reads lanes 32 (w % 4) .. +31 and one sixth of the columns
+    // ---- epilogue: warp w reads lanes 32 (w % 4) .. +31 and a quarter of the columns
     const int ew = warp - 2, quad = warp & 3, part = ew >> 2;
     const int i = i0 + 32 * quad + lane;  // row of C
     const int jq = j0 + 8 * part;         // first column of this warp
@@ -561,32 +567,35 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     for (int c = 0; c < 8; ++c) hr[c] = lr[c] = hi[c] = li[c] = 0.f;
     bool ok = true;
     for (int kb = 0; kb < nkb; ++kb) {
-      ok = oz_warp_wait(accf, (uint32_t)kb & 1u, a.poll_limit, a.err, abort_flag);
-      if (!ok) break;
-      tc_fence_after();
+      // the block scales first: their loads overlap the wait for the MMAs
       const int sb = kb / (OZ_KB / OZ_DRAIN);  // the scale block holding this accumulation block
       const float sa = (i < a.lc) ? a.As[((size_t)z * nkbt + sb) * a.lc + i] : 0.f;
       const float* sbp = a.Bs + ((size_t)z * nkbt + sb) * a.nc;
+      float sbv[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) sbv[c] = (jq + c < a.nc) ? __ldg(sbp + jq + c) : 0.f;
+      ok = oz_warp_wait(accf, (uint32_t)kb & 1u, a.poll_limit, a.err, abort_flag);
+      if (!ok) break;
+      tc_fence_after();
       const uint32_t lanes = (uint32_t)(32 * quad) << 16;
 #pragma unroll
-      for (int c4 = 0; c4 < 8; ++c4) {
-        float v[2 * OZ_NGRP][1];
+      for (int c4 = 0; c4 < 8; c4 += 4) {  // four columns of every accumulator per load
+        float v[2 * OZ_NGRP][4];
 #pragma unroll
-        for (int g = 0; g < 2 * OZ_NGRP; ++g) v[g][0] = oz_ld1(tmem + lanes + (uint32_t)(OZ_BN * g + 8 * part + c4));
+        for (int g = 0; g < 2 * OZ_NGRP; ++g) oz_ld4(tmem + lanes + (uint32_t)(OZ_BN * g + 8 * part + c4), v[g]);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int q = 0; q < 1; ++q) {
-          const int j = jq + c4 + q;
-          const float sc = sa * ((j < a.nc) ? __ldg(sbp + j) : 0.f);
-          // levels 2, 3, 4 exactly into (s, e + e2), levels 5 and 6+ into the low part
+        for (int q = 0; q < 4; ++q) {
+          const float sc = sa * sbv[c4 + q];
+          // levels 2, 3, 4 exactly into (s, e + e2), levels 5, 6, 7 into the low part
           float s, e, s2, e2;
           two_sum(v[0][q], v[1][q], s, e);
           two_sum(s, v[2][q], s2, e2);
-          float lo = (e + e2) + (v[3][q] + v[4][q]);
+          float lo = (e + e2) + (v[3][q] + (v[4][q] + v[5][q]));
           oz_df_add(hr[c4 + q], lr[c4 + q], s2 * sc, lo * sc);
-          two_sum(v[5][q], v[6][q], s, e);
-          two_sum(s, v[7][q], s2, e2);
-          lo = (e + e2) + (v[8][q] + v[9][q]);
+          two_sum(v[6][q], v[7][q], s, e);
+          two_sum(s, v[8][q], s2, e2);
+          lo = (e + e2) + (v[9][q] + (v[10][q] + v[11][q]));
           oz_df_add(hi[c4 + q], li[c4 + q], s2 * sc, lo * sc);
         }
       }
