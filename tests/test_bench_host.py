@@ -44,10 +44,14 @@ def test_unknown_dominant_kernel_has_no_roofline():
 def test_tensor_core_projection_roofline_uses_the_digit_product_ceiling():
     r = bench.roofline(_res({"k_oz_proj[project]": (10.0, 2), "k_qr": (3.0, 1)}), 152)
     assert r["kernel"] == "k_oz_proj[project]" and r["bound"] == "tensor"
-    # 8 m n l flop per instance over the 5 ms launch, against BF16 x 8 / 120
+    # 8 m n l flop per instance over the 5 ms launch, against BF16 x 8 / 168
+    # (21 digit pairs x 4 real products x 2 flop per complex multiply-add)
     assert abs(r["achieved"] - 8.0 * 2000 * 2000 * 120 * 152 / 5e-3 / 1e12) < 1e-9
-    assert abs(r["peak"] - (bench.measured_peaks().get("bf16_tflops_sustained") or 1700.0) * 8 / 120) < 1e-9
+    assert abs(r["peak"] - (bench.measured_peaks().get("bf16_tflops_sustained") or 1700.0) * 8 / 168) < 1e-9
     assert set(r["by_kernel"]) == {"k_oz_proj[project]", "k_qr"}
+    # with the Cholesky QR of B^H in the step, k_qr (flagged instances only) has no fixed count
+    r = bench.roofline(_res({"k_oz_proj[project]": (10.0, 2), "k_qr": (0.01, 1), "k_oz_gemm[cholqr]": (3.0, 5)}), 152)
+    assert set(r["by_kernel"]) == {"k_oz_proj[project]", "k_oz_gemm[cholqr]"}
 
 
 def _bench(args, env_extra=None):
