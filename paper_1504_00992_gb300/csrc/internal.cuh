@@ -119,7 +119,10 @@ cudaError_t launch_jacobi_sized(const Dims* dims, const ProbPtr* ptrs, int batch
 bool jacobi_cluster_chosen(const Caps& cap, int batch, int force);
 // the one-CTA Jacobi SVD in double-float arithmetic (jacobi_df.cu), the mixed
 // form's: same outputs as launch_jacobi, FP64-accurate to 2^-48
-cudaError_t launch_jacobi_df(const Dims* dims, const ProbPtr* ptrs, int batch, int* status, cudaStream_t st);
+// (lcap: the widest instance's l; X is held in shared memory where it fits)
+cudaError_t launch_jacobi_df(const Dims* dims, const ProbPtr* ptrs, int batch, int lcap, int* status,
+                             cudaStream_t st);
+cudaError_t jacobi_df_prepare();
 cudaError_t launch_frob2(const Dims* dims, const ProbPtr* ptrs, int batch, cudaStream_t st);
 // identity_gate = 1 writes the pre-gate theta (reverse pass).  Otherwise a
 // bond with ptrs[p].Cpre set gets its pre-gate theta written there, and

@@ -124,26 +124,89 @@ __device__ __forceinline__ void drot(float4& u, float4& v, dfl c, dfl sr, dfl si
   v = nv;
 }
 
+enum { JD_U = 4 };  // rows of a lane loaded before any is used (loads in flight together)
+
+// g = x_a^H x_b over the rows gl, gl + JD_G, ... of this lane (lazy pair sums)
+__device__ __forceinline__ void jd_dot(const float4* xa, const float4* xb, int L, int gl, float& gr, float& grl,
+                                       float& gi, float& gil) {
+  for (int r0 = gl; r0 < L; r0 += JD_G * JD_U) {
+    float4 x[JD_U], y[JD_U];
+#pragma unroll
+    for (int u = 0; u < JD_U; ++u) {
+      const int r = r0 + u * JD_G;
+      x[u] = r < L ? xa[r] : make_float4(0.f, 0.f, 0.f, 0.f);
+      y[u] = r < L ? xb[r] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < JD_U; ++u) {
+      acc_dd(gr, grl, x[u].x, x[u].y, y[u].x, y[u].y);
+      acc_dd(gr, grl, x[u].z, x[u].w, y[u].z, y[u].w);
+      acc_dd(gi, gil, x[u].x, x[u].y, y[u].z, y[u].w);
+      acc_dd(gi, gil, -x[u].z, -x[u].w, y[u].x, y[u].y);
+    }
+  }
+}
+
+// (x_a, x_b) <- (c x_a - conj(se) x_b, se x_a + c x_b) on this lane's rows
+__device__ __forceinline__ void jd_rot(float4* xa, float4* xb, int L, int gl, dfl c, dfl sr, dfl si) {
+  for (int r0 = gl; r0 < L; r0 += JD_G * JD_U) {
+    float4 x[JD_U], y[JD_U];
+#pragma unroll
+    for (int u = 0; u < JD_U; ++u) {
+      const int r = r0 + u * JD_G;
+      if (r < L) {
+        x[u] = xa[r];
+        y[u] = xb[r];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < JD_U; ++u) {
+      const int r = r0 + u * JD_G;
+      if (r < L) {
+        drot(x[u], y[u], c, sr, si);
+        xa[r] = x[u];
+        xb[r] = y[u];
+      }
+    }
+  }
+}
+
+// Dynamic shared memory of an instance of L columns: X (XS: L^2 complex
+// double-float), squared column norms, reduction scratch, and sigma / perm
+// for jacobi_finish (in X's place once X is written back, XS).
+__host__ __device__ inline size_t jd_smem_bytes(int L, bool xs) {
+  const size_t x = xs ? (size_t)L * L * sizeof(float4) : 0;
+  const size_t tail = (size_t)L * sizeof(float2) + 32 * sizeof(double) + 32 * sizeof(int) + 16;
+  const size_t fin = (size_t)L * (sizeof(double) + sizeof(int));
+  return (xs ? (x > fin ? x : fin) : fin) + tail;
+}
+
+template <bool XS>
 __global__ void __launch_bounds__(JD_THREADS) k_jacobi_df(const Dims* __restrict__ dims,
                                                           const ProbPtr* __restrict__ ptrs, int* status) {
-  __shared__ double sv[QR_MAXL];
-  __shared__ float2 nrm[QR_MAXL];  // squared column norms, double-float
-  __shared__ int perm[QR_MAXL];
-  __shared__ int rotated;
-  __shared__ double red[32];
-  __shared__ int emax[32];
+  extern __shared__ __align__(16) unsigned char jd_smem[];
   const int p = blockIdx.x;
   const Dims D = dims[p];
   if (!D.active) return;
   const ProbPtr& P = ptrs[p];
   const int L = D.l;
+  // shared layout (this instance's L): [X or sigma / perm][norms][red][emax][rotated]
+  const size_t x_bytes = XS ? (size_t)L * L * sizeof(float4) : 0;
+  const size_t fin = (size_t)L * (sizeof(double) + sizeof(int));
+  unsigned char* tail = jd_smem + (x_bytes > fin ? x_bytes : fin);
+  float2* nrm = reinterpret_cast<float2*>(tail);  // squared column norms, double-float
+  double* red = reinterpret_cast<double*>(tail + (size_t)L * sizeof(float2));
+  int* emax = reinterpret_cast<int*>(red + 32);
+  int& rotated = emax[32];
+  double* sv = reinterpret_cast<double*>(jd_smem);
+  int* perm = reinterpret_cast<int*>(jd_smem + (size_t)L * sizeof(double));
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   const int gl = lane & (JD_G - 1);
   const int grp = tid / JD_G, ngrp = blockDim.x / JD_G;
   const unsigned gmask = ((1u << JD_G) - 1u) << (lane & ~(JD_G - 1));
   cplx* X64 = P.R;
   cplx* J64 = P.J;
-  float4* X = reinterpret_cast<float4*>(P.R);
+  float4* X = XS ? reinterpret_cast<float4*>(jd_smem) : reinterpret_cast<float4*>(P.R);
   float4* J = reinterpret_cast<float4*>(P.J);
 
   // the scale: largest biased exponent among the entries of X
@@ -230,13 +293,7 @@ __global__ void __launch_bounds__(JD_THREADS) k_jacobi_df(const Dims* __restrict
         if (na.x <= small || nb.x <= small) continue;
         // g = x_a^H x_b
         float gr = 0.f, grl = 0.f, gi = 0.f, gil = 0.f;
-        for (int r = gl; r < L; r += JD_G) {
-          const float4 x = xa[r], y = xb[r];
-          acc_dd(gr, grl, x.x, x.y, y.x, y.y);
-          acc_dd(gr, grl, x.z, x.w, y.z, y.w);
-          acc_dd(gi, gil, x.x, x.y, y.z, y.w);
-          acc_dd(gi, gil, -x.z, -x.w, y.x, y.y);
-        }
+        jd_dot(xa, xb, L, gl, gr, grl, gi, gil);
         fast2(gr, grl);
         fast2(gi, gil);
         const dfl g_r = grp_dsum(dfl{gr, grl}, gmask), g_i = grp_dsum(dfl{gi, gil}, gmask);
@@ -266,20 +323,8 @@ __global__ void __launch_bounds__(JD_THREADS) k_jacobi_df(const Dims* __restrict
         // se = s e with e = g / |g| of unit modulus to double-float accuracy
         const dfl er = dmul(gr_s, rinv), ei = dmul(gi_s, rinv);
         const dfl sr = dmul(s, er), si = dmul(s, ei);
-        for (int r = gl; r < L; r += JD_G) {
-          float4 x = xa[r], y = xb[r];
-          drot(x, y, c, sr, si);
-          xa[r] = x;
-          xb[r] = y;
-        }
-        float4* ja = J + (int64_t)a * L;
-        float4* jb = J + (int64_t)b * L;
-        for (int r = gl; r < L; r += JD_G) {
-          float4 x = ja[r], y = jb[r];
-          drot(x, y, c, sr, si);
-          ja[r] = x;
-          jb[r] = y;
-        }
+        jd_rot(xa, xb, L, gl, c, sr, si);
+        jd_rot(J + (int64_t)a * L, J + (int64_t)b * L, L, gl, c, sr, si);
         if (gl == 0) {
           // |x_a'|^2 = |x_a|^2 - t |g|, |x_b'|^2 = |x_b|^2 + t |g|
           const dfl tg = dmulf(ag, t);
@@ -307,9 +352,41 @@ __global__ void __launch_bounds__(JD_THREADS) k_jacobi_df(const Dims* __restrict
   jacobi_finish(D, P, sv, perm);
 }
 
-cudaError_t launch_jacobi_df(const Dims* dims, const ProbPtr* ptrs, int batch, int* status, cudaStream_t st) {
+static int jd_smem_limit() {
+  static int lim = -1;
+  if (lim < 0) {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+      v = 48 * 1024;
+    lim = v;
+  }
+  return lim;
+}
+
+cudaError_t jacobi_df_prepare() {
+  static int done = 0;
+  if (!done) {
+    cudaError_t e = cudaFuncSetAttribute(k_jacobi_df<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, jd_smem_limit());
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_jacobi_df<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)jd_smem_bytes(QR_MAXL, false));
+    if (e != cudaSuccess) return e;
+    done = 1;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_jacobi_df(const Dims* dims, const ProbPtr* ptrs, int batch, int lcap, int* status,
+                             cudaStream_t st) {
+  cudaError_t e = jacobi_df_prepare();
+  if (e != cudaSuccess) return e;
   ProfScope ps("k_jacobi[df]", st);
-  k_jacobi_df<<<batch, JD_THREADS, 0, st>>>(dims, ptrs, status);
+  // X in shared memory wherever the widest instance's fits (l <= 120 on GB300)
+  const size_t xs = jd_smem_bytes(lcap, true);
+  if (xs <= (size_t)jd_smem_limit())
+    k_jacobi_df<true><<<batch, JD_THREADS, xs, st>>>(dims, ptrs, status);
+  else
+    k_jacobi_df<false><<<batch, JD_THREADS, jd_smem_bytes(lcap, false), st>>>(dims, ptrs, status);
   return cudaGetLastError();
 }
 

@@ -643,6 +643,7 @@ static cudaError_t conv_bt_bf16(const float2* X, const Dims* dims, const MixedPt
 cudaError_t mixed_prepare(const Caps& cap) {
   if (!encode_fn()) return cudaErrorNotSupported;
   MX_TRY(oz_prepare());
+  MX_TRY(jacobi_df_prepare());
   MX_TRY(tc_attrs());
   return qr_blocked_prepare(cap.m, cap.n, cap.l);
 }
@@ -732,7 +733,7 @@ cudaError_t run_rrsvd_mixed(const Dims* dims, const ProbPtr* ptrs, int batch, co
     MX_TRY(launch_qr_sized(QR_BH, dims, ptrs, batch, cap, st, kn.qrbh));
   // Jacobi SVD: double-float one-CTA kernel unless the cluster form is chosen
   if (kn.jac == 3 || (kn.jac == 0 && !jacobi_cluster_chosen(cap, batch, 0)))
-    MX_TRY(launch_jacobi_df(dims, ptrs, batch, status, st));
+    MX_TRY(launch_jacobi_df(dims, ptrs, batch, cap.l, status, st));
   else
     MX_TRY(launch_jacobi_sized(dims, ptrs, batch, cap, status, st, kn.jac));
   for (int stage : {G_U, G_V})
