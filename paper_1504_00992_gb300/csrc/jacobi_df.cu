@@ -174,11 +174,15 @@ __device__ __forceinline__ void jd_rot(float4* xa, float4* xb, int L, int gl, df
 // Dynamic shared memory of an instance of L columns: X (XS: L^2 complex
 // double-float), squared column norms, reduction scratch, and sigma / perm
 // for jacobi_finish (in X's place once X is written back, XS).
-__host__ __device__ inline size_t jd_smem_bytes(int L, bool xs) {
+// Every part starts on a 16-byte boundary.
+__host__ __device__ inline size_t jd_up16(size_t x) { return (x + 15) & ~(size_t)15; }
+__host__ __device__ inline size_t jd_head_bytes(int L, bool xs) {
   const size_t x = xs ? (size_t)L * L * sizeof(float4) : 0;
-  const size_t tail = (size_t)L * sizeof(float2) + 32 * sizeof(double) + 32 * sizeof(int) + 16;
-  const size_t fin = (size_t)L * (sizeof(double) + sizeof(int));
-  return (xs ? (x > fin ? x : fin) : fin) + tail;
+  const size_t fin = jd_up16((size_t)L * (sizeof(double) + sizeof(int)));
+  return x > fin ? x : fin;
+}
+__host__ __device__ inline size_t jd_smem_bytes(int L, bool xs) {
+  return jd_head_bytes(L, xs) + jd_up16((size_t)L * sizeof(float2)) + 32 * sizeof(double) + 33 * sizeof(int);
 }
 
 template <bool XS>
@@ -191,11 +195,9 @@ __global__ void __launch_bounds__(JD_THREADS) k_jacobi_df(const Dims* __restrict
   const ProbPtr& P = ptrs[p];
   const int L = D.l;
   // shared layout (this instance's L): [X or sigma / perm][norms][red][emax][rotated]
-  const size_t x_bytes = XS ? (size_t)L * L * sizeof(float4) : 0;
-  const size_t fin = (size_t)L * (sizeof(double) + sizeof(int));
-  unsigned char* tail = jd_smem + (x_bytes > fin ? x_bytes : fin);
+  unsigned char* tail = jd_smem + jd_head_bytes(L, XS);
   float2* nrm = reinterpret_cast<float2*>(tail);  // squared column norms, double-float
-  double* red = reinterpret_cast<double*>(tail + (size_t)L * sizeof(float2));
+  double* red = reinterpret_cast<double*>(tail + jd_up16((size_t)L * sizeof(float2)));
   int* emax = reinterpret_cast<int*>(red + 32);
   int& rotated = emax[32];
   double* sv = reinterpret_cast<double*>(jd_smem);
