@@ -367,7 +367,14 @@ int rrsvd_execute(rrsvd_plan_t plan, const double* theta, int64_t chain0, double
  * the device, runs, and copies the results back, all on `stream`, and
  * synchronises.  Device staging buffers and workspace are allocated on the
  * first call and kept by the plan.  Page-locked host buffers let the copies
- * run at the link's rate; pageable ones are staged by the CUDA runtime. */
+ * run at the link's rate; pageable ones are staged by the CUDA runtime.
+ * Mixed-form plans of 16 instances or more run as four sub-batches, each on
+ * a stream of the plan's own (copy in, truncation, copy out), ordered after
+ * the work already on `stream` and before the call returns, so that copies
+ * overlap kernels; their launch choices are those of the whole batch and the
+ * results equal rrsvd_execute's bit for bit.  Errors: TEBD_EINVAL (NULL theta
+ * or sigma), TEBD_ENOMEM (staging), TEBD_ECUDA, TEBD_ETIMEOUT, TEBD_ENUMERIC
+ * (a zero or non-finite theta, a failed re-orthonormalisation). */
 int rrsvd_execute_host(rrsvd_plan_t plan, const double* theta, int64_t chain0, double* sigma, double* U,
                        double* Vh, double* w, int* rank, void* stream);
 

@@ -1483,12 +1483,16 @@ struct rrsvd_plan_s {
   // accuracy check (Alg. 2); check_r == 0: fixed rank
   int check_r = 0, l_max = 0, rounds = 0, k0 = 0, l0 = 0;
   double eps = 0.0;
-  // host-path staging (allocated on first use)
+  // host-path staging (allocated on first use) and the streams / events of
+  // its pipelined sub-batches (created on first use)
   char* stage = nullptr;
   size_t stage_bytes = 0;
+  static const int HCH = 4;
+  cudaStream_t hs[HCH] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t hev[HCH + 1] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   // autotuner choices (rrsvd_plan_autotune): FP64 GEMM tiles, mixed-form knobs
   int tiles[6] = {0, 0, 0, 0, 0, 0};
-  MixedKnobs mk{0, 0, 0, 0};
+  MixedKnobs mk{0, 0, 0, 0, 0};
   float tune_ms[2] = {0.f, 0.f};
   int tuned = 0;
 };
@@ -1584,6 +1588,10 @@ extern "C" int rrsvd_plan_destroy(rrsvd_plan_t P) {
   if (!P) return TEBD_OK;
   if (P->meta) cudaFree(P->meta);
   if (P->stage) cudaFree(P->stage);
+  for (cudaStream_t& h : P->hs)
+    if (h) cudaStreamDestroy(h);
+  for (cudaEvent_t& e : P->hev)
+    if (e) cudaEventDestroy(e);
   delete P;
   return TEBD_OK;
 }
@@ -1607,6 +1615,27 @@ extern "C" int rrsvd_plan_dims(rrsvd_plan_t P, int* k, int* l) {
   if (k) *k = P->k;
   if (l) *l = P->l;
   return TEBD_OK;
+}
+
+// The fixed-rank truncation of instances z0 .. z0 + cnt - 1 of a bound plan
+// (k_rrsvd_bind has run): sigma, Vh, w and rank point at instance z0's
+// entries.  Sub-batches of one plan may run concurrently on different streams.
+static cudaError_t exec_range(rrsvd_plan_t P, int z0, int cnt, int64_t chain0, double* sigma, double* Vh, double* w,
+                              int* rank, void* workspace, cudaStream_t st, const MixedKnobs& kn) {
+  Dims* dims = P->dims + z0;
+  const ProbPtr* ptrs = P->ptrs + z0;
+  cudaError_t e;
+  if (prec_mixed(P->precision)) {
+    const MixedPtrs mp =
+        mixed_offset(mixed_carve((char*)workspace + P->mixed_off, P->ms, P->batch), P->ms, z0);
+    e = run_rrsvd_mixed(dims, ptrs, cnt, P->cap, mp, P->q, P->seed, 0, chain0 + z0, 1, P->status, P->tcerr, st,
+                        nullptr, &kn, P->precision == TEBD_PREC_BF16);
+  } else {
+    e = run_rrsvd(dims, ptrs, cnt, P->cap, P->q, P->seed, 0, chain0 + z0, 1, P->status, st, nullptr,
+                  P->tuned ? P->tiles : nullptr);
+  }
+  if (e != cudaSuccess) return e;
+  return launch_rrsvd_finalize(dims, ptrs, cnt, P->cap, 1e-14, sigma, Vh, w, rank, P->status, st);
 }
 
 extern "C" int rrsvd_execute(rrsvd_plan_t P, const double* theta, int64_t chain0, double* sigma, double* U, double* Vh,
@@ -1641,15 +1670,7 @@ extern "C" int rrsvd_execute(rrsvd_plan_t P, const double* theta, int64_t chain0
                                      st));
     return TEBD_OK;
   }
-  if (prec_mixed(P->precision)) {
-    const MixedPtrs mp = mixed_carve((char*)workspace + P->mixed_off, P->ms, P->batch);
-    CU_OR(P, run_rrsvd_mixed(P->dims, P->ptrs, P->batch, P->cap, mp, P->q, P->seed, 0, chain0, 1, P->status,
-                             P->tcerr, st, nullptr, &P->mk, P->precision == TEBD_PREC_BF16));
-  } else {
-    CU_OR(P, run_rrsvd(P->dims, P->ptrs, P->batch, P->cap, P->q, P->seed, 0, chain0, 1, P->status, st, nullptr,
-                       P->tuned ? P->tiles : nullptr));
-  }
-  CU_OR(P, launch_rrsvd_finalize(P->dims, P->ptrs, P->batch, P->cap, 1e-14, sigma, Vh, w, rank, P->status, st));
+  CU_OR(P, exec_range(P, 0, P->batch, chain0, sigma, Vh, w, rank, workspace, st, P->mk));
   return TEBD_OK;
 }
 
@@ -1681,20 +1702,71 @@ extern "C" int rrsvd_execute_host(rrsvd_plan_t P, const double* theta, int64_t c
   int* d_r = (int*)(s + th + sg + uu + vv + ww);
   void* d_ws = s + th + sg + uu + vv + ww + rr;
   cudaStream_t st = (cudaStream_t)stream;
-  {
-    ProfScope ps("copy[h2d]", st);
-    CU_OR(P, cudaMemcpyAsync(d_th, theta, c * (size_t)P->m * P->n * B, cudaMemcpyHostToDevice, st));
-  }
-  int rc = rrsvd_execute(P, d_th, chain0, d_sg, U ? d_u : nullptr, Vh ? d_v : nullptr, w ? d_w : nullptr,
-                         rank ? d_r : nullptr, d_ws, P->ws_bytes, stream);
-  if (rc) return rc;
-  {
+  // sub-batches for mixed-form plans of 16 instances or more (their launch
+  // choices fixed as the whole batch's size rules make them, so that the
+  // results equal rrsvd_execute's bit for bit)
+  const int nch = (P->check_r > 0 || !prec_mixed(P->precision) || P->batch < 16) ? 1 : rrsvd_plan_s::HCH;
+  if (nch == 1) {
+    {
+      ProfScope ps("copy[h2d]", st);
+      CU_OR(P, cudaMemcpyAsync(d_th, theta, c * (size_t)P->m * P->n * B, cudaMemcpyHostToDevice, st));
+    }
+    int rc = rrsvd_execute(P, d_th, chain0, d_sg, U ? d_u : nullptr, Vh ? d_v : nullptr, w ? d_w : nullptr,
+                           rank ? d_r : nullptr, d_ws, P->ws_bytes, stream);
+    if (rc) return rc;
     ProfScope ps("copy[d2h]", st);
     CU_OR(P, cudaMemcpyAsync(sigma, d_sg, sizeof(double) * P->k * B, cudaMemcpyDeviceToHost, st));
     if (U) CU_OR(P, cudaMemcpyAsync(U, d_u, c * (size_t)P->m * P->k * B, cudaMemcpyDeviceToHost, st));
     if (Vh) CU_OR(P, cudaMemcpyAsync(Vh, d_v, c * (size_t)P->k * P->n * B, cudaMemcpyDeviceToHost, st));
     if (w) CU_OR(P, cudaMemcpyAsync(w, d_w, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
     if (rank) CU_OR(P, cudaMemcpyAsync(rank, d_r, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
+  } else {
+    // Pipelined: the batch in HCH sub-batches, each on a stream of its own
+    // (copy in, truncation, copy out), so that copies of one overlap the
+    // kernels of the others and the kernels of the sub-batches share the SMs.
+    if (chain0 < 0) { P->err.set(TEBD_EINVAL, "chain0 < 0"); return P->err.code; }
+    for (int i = 0; i < nch; ++i)
+      if (!P->hs[i]) CU_OR(P, cudaStreamCreateWithFlags(&P->hs[i], cudaStreamNonBlocking));
+    for (int i = 0; i <= nch; ++i)
+      if (!P->hev[i]) CU_OR(P, cudaEventCreateWithFlags(&P->hev[i], cudaEventDisableTiming));
+    {
+      ProfScope ps("k_rrsvd_bind", st);
+      k_rrsvd_bind<<<(P->batch + 127) / 128, 128, 0, st>>>(P->ptrs, P->batch, (char*)d_ws, P->per, P->lay,
+                                                         (const cplx*)d_th, (size_t)P->m * P->n,
+                                                         U ? (cplx*)d_u : nullptr, (size_t)P->m * P->k,
+                                                         Vh ? (cplx*)d_v : nullptr, (size_t)P->k * P->n, nullptr, 0,
+                                                         0, 0, 0, nullptr);
+      CU_OR(P, cudaGetLastError());
+    }
+    CU_OR(P, cudaEventRecord(P->hev[nch], st));
+    MixedKnobs kc = P->mk;
+    if (kc.qrbh == 0) kc.qrbh = qr_multi_chosen(QR_BH, P->cap, P->batch, 0) ? 2 : 3;
+    if (kc.jac == 0) kc.jac = jacobi_cluster_chosen(P->cap, P->batch, 0) ? 2 : 3;
+    const size_t mn = (size_t)P->m * P->n, mk = (size_t)P->m * P->k, kn = (size_t)P->k * P->n;
+    const int per = (P->batch + nch - 1) / nch;
+    for (int i = 0; i < nch; ++i) {
+      const int z0 = i * per, cnt = std::min(per, P->batch - z0);
+      if (cnt <= 0) break;
+      cudaStream_t hs = P->hs[i];
+      CU_OR(P, cudaStreamWaitEvent(hs, P->hev[nch], 0));
+      {
+        ProfScope ps("copy[h2d]", hs);
+        CU_OR(P, cudaMemcpyAsync(d_th + 2 * mn * z0, theta + 2 * mn * z0, c * mn * cnt, cudaMemcpyHostToDevice, hs));
+      }
+      CU_OR(P, exec_range(P, z0, cnt, chain0, d_sg + (size_t)P->k * z0, Vh ? d_v + 2 * kn * z0 : nullptr,
+                          w ? d_w + z0 : nullptr, rank ? d_r + z0 : nullptr, d_ws, hs, kc));
+      {
+        ProfScope ps("copy[d2h]", hs);
+        CU_OR(P, cudaMemcpyAsync(sigma + (size_t)P->k * z0, d_sg + (size_t)P->k * z0, sizeof(double) * P->k * cnt,
+                                 cudaMemcpyDeviceToHost, hs));
+        if (U) CU_OR(P, cudaMemcpyAsync(U + 2 * mk * z0, d_u + 2 * mk * z0, c * mk * cnt, cudaMemcpyDeviceToHost, hs));
+        if (Vh) CU_OR(P, cudaMemcpyAsync(Vh + 2 * kn * z0, d_v + 2 * kn * z0, c * kn * cnt, cudaMemcpyDeviceToHost, hs));
+        if (w) CU_OR(P, cudaMemcpyAsync(w + z0, d_w + z0, sizeof(double) * cnt, cudaMemcpyDeviceToHost, hs));
+        if (rank) CU_OR(P, cudaMemcpyAsync(rank + z0, d_r + z0, sizeof(int) * cnt, cudaMemcpyDeviceToHost, hs));
+      }
+      CU_OR(P, cudaEventRecord(P->hev[i], hs));
+      CU_OR(P, cudaStreamWaitEvent(st, P->hev[i], 0));
+    }
   }
   int stv = 0, tce = 0;
   CU_OR(P, cudaMemcpyAsync(&stv, P->status, sizeof(int), cudaMemcpyDeviceToHost, st));

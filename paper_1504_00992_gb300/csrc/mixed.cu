@@ -546,6 +546,38 @@ MixedPtrs mixed_carve(char* base, const MixedSizes& s, int batch) {
   return p;
 }
 
+MixedPtrs mixed_offset(const MixedPtrs& p, const MixedSizes& s, int z0) {
+  MixedPtrs o = p;
+  const size_t z = (size_t)z0;
+  auto adv = [z](auto* ptr, size_t bytes) { return ptr ? (decltype(ptr))((char*)ptr + z * bytes) : ptr; };
+  o.thf_hi = adv(p.thf_hi, s.thf);
+  o.thf_lo = adv(p.thf_lo, s.thf);
+  o.tha_hi = adv(p.tha_hi, s.tha);
+  o.tha_lo = adv(p.tha_lo, s.tha);
+  o.bt_hi = adv(p.bt_hi, s.bt);
+  o.bt_lo = adv(p.bt_lo, s.bt);
+  o.Yf = adv(p.Yf, s.yf);
+  o.Qf = adv(p.Qf, s.yf);
+  o.Ytf = adv(p.Ytf, s.ytf);
+  o.Qtf = adv(p.Qtf, s.ytf);
+  o.Df = adv(p.Df, s.df);
+  o.thd = adv(p.thd, s.thd);
+  o.tpart = adv(p.tpart, (size_t)s.ntile * sizeof(double));
+  o.qscr = adv(p.qscr, s.qs);
+  o.bd = adv(p.bd, s.bd);
+  o.bsc = adv(p.bsc, s.bsc);
+  o.ad = adv(p.ad, s.ad);
+  o.asc = adv(p.asc, s.asc);
+  o.thf_b = adv(p.thf_b, s.thfb);
+  o.tha_b = adv(p.tha_b, s.thab);
+  o.bt_b = adv(p.bt_b, s.btb);
+  o.gad = adv(p.gad, s.gad);
+  o.gas = adv(p.gas, s.gas);
+  o.gbd = adv(p.gbd, s.gbd);
+  o.gbs = adv(p.gbs, s.gbs);
+  return o;
+}
+
 #define MX_TRY(x)                     \
   do {                                \
     cudaError_t e_ = (x);             \

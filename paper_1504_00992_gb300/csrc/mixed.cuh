@@ -53,6 +53,9 @@ struct MixedPtrs {
 };
 
 MixedSizes mixed_sizes(int m, int n, int k, int l, int bf16 = 0);
+// The arrays of instances z0, z0 + 1, ... of a carve (every array advanced
+// by z0 instances): run_rrsvd_mixed on a sub-batch starting at instance z0.
+MixedPtrs mixed_offset(const MixedPtrs& p, const MixedSizes& s, int z0);
 size_t mixed_bytes(const MixedSizes& s, int batch);
 MixedPtrs mixed_carve(char* base, const MixedSizes& s, int batch);
 

@@ -290,3 +290,32 @@ def test_double_float_jacobi_agrees_with_fp64(lib, m, n, k, p):
         ra = truncated(a["U"][t], a["sigma"][t], a["Vh"][t])
         rb = truncated(b["U"][t], b["sigma"][t], b["Vh"][t])
         assert np.linalg.norm(ra - rb) <= 1e-11 * np.linalg.norm(theta[t])
+
+
+@pytest.mark.parametrize("form", ["tf32", "bf16"])
+def test_host_path_sub_batches_equal_device_path(lib, form):
+    """rrsvd_execute_host runs a mixed-form batch of 16 or more as four
+    sub-batches on streams of their own (copies overlapping kernels); with the
+    launch choices of the whole batch its results equal rrsvd_execute's bit
+    for bit, here with an uneven split (18 = 5 + 5 + 5 + 3)."""
+    from paper_1504_00992_gb300 import binding as B
+    m, n, k, p, q, batch = 300, 260, 40, 10, 1, 18
+    sig = I.exp_spectrum(min(m, n), 8.0)
+    theta = np.stack([I.synthetic_theta(m, n, sig, seed=40 + t) for t in range(batch)])
+    prec = B.TEBD_PREC_BF16 if form == "bf16" else B.TEBD_PREC_TF32
+    plan = B.rrsvd_plan_create(m, n, k, p, q, batch, prec, SEED)
+    try:
+        dev = rrsvd_device(B, plan, theta, chain0=3)
+        sg = np.zeros((batch, k))
+        U = np.zeros((batch, m, k), dtype=np.complex128)
+        Vh = np.zeros((batch, k, n), dtype=np.complex128)
+        w = np.zeros(batch)
+        rk = np.zeros(batch, dtype=np.int32)
+        B.rrsvd_execute_host(plan, theta, 3, sg, U, Vh, w, rk)
+        # again: the plan's streams and staging are reused
+        sg2 = np.zeros((batch, k))
+        B.rrsvd_execute_host(plan, theta, 3, sg2)
+    finally:
+        B.rrsvd_plan_destroy(plan)
+    assert np.array_equal(sg, dev["sigma"]) and np.array_equal(U, dev["U"]) and np.array_equal(Vh, dev["Vh"])
+    assert np.array_equal(w, dev["w"]) and np.array_equal(rk, dev["rank"]) and np.array_equal(sg2, sg)
