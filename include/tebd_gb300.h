@@ -378,6 +378,28 @@ int rrsvd_execute(rrsvd_plan_t plan, const double* theta, int64_t chain0, double
 int rrsvd_execute_host(rrsvd_plan_t plan, const double* theta, int64_t chain0, double* sigma, double* U,
                        double* Vh, double* w, int* rank, void* stream);
 
+/* The same truncation from and to HOST buffers without waiting for it:
+ * enqueues the copy in (on a copy stream of the plan's own, after the work
+ * already on `stream`), the truncation (on `stream`) and the copy out (on a
+ * second stream of the plan's own) and returns.  The plan keeps two staging
+ * slots used in turn, so the copy in of a call runs while the previous
+ * call's truncation computes; a call blocks only on the host while slots
+ * are busy.  theta and the outputs must stay valid, and the outputs unread,
+ * until rrsvd_host_wait.  Calls of one plan run their truncations in call
+ * order on `stream`; do not mix them with rrsvd_execute on the same plan on
+ * another stream before rrsvd_host_wait.  Errors: TEBD_EINVAL (NULL theta or
+ * sigma, chain0 < 0), TEBD_ENOMEM (two staging slots and a workspace on the
+ * first call), TEBD_ECUDA. */
+int rrsvd_execute_host_async(rrsvd_plan_t plan, const double* theta, int64_t chain0, double* sigma, double* U,
+                             double* Vh, double* w, int* rank, void* stream);
+
+/* Waits for every rrsvd_execute_host_async call of the plan since the last
+ * wait; their outputs are then in place.  Returns the first error raised by
+ * them: TEBD_ETIMEOUT (an expired tensor-core pipeline wait), TEBD_ENUMERIC
+ * (a zero or non-finite theta, a failed re-orthonormalisation), TEBD_ECUDA.
+ * rrsvd_execute_host waits for pending calls itself. */
+int rrsvd_host_wait(rrsvd_plan_t plan);
+
 const char* rrsvd_last_error(rrsvd_plan_t plan);
 
 /* Autotuner of a plan (the batched launches of Section IV's steps): times

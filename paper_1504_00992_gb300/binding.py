@@ -134,6 +134,8 @@ _SIGS = {
     "rrsvd_plan_dims": (_i, [_vp, _pi, _pi]),
     "rrsvd_execute": (_i, [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_size_t, _vp]),
     "rrsvd_execute_host": (_i, [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "rrsvd_execute_host_async": (_i, [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "rrsvd_host_wait": (_i, [_vp]),
     "rrsvd_last_error": (ctypes.c_char_p, [_vp]),
     "rrsvd_execute_noalloc": (_i, [_i, _i, _i, _i, _i, _i, _u64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "tebd_philox4x64_10": (_i, [_vp, _i64, _u64, _u64, _vp, _vp]),
@@ -478,6 +480,19 @@ def rrsvd_execute_host(plan, theta, chain0, sigma, U=None, Vh=None, w=None, rank
         return _vp(a.ctypes.data) if a is not None else None
     _pcheck(plan, load().rrsvd_execute_host(plan, hp(theta), chain0, hp(sigma), hp(U), hp(Vh), hp(w), hp(rank),
                                             _vp(int(stream_ptr)) if stream_ptr else None))
+
+
+def rrsvd_execute_host_async(plan, theta, chain0, sigma, U=None, Vh=None, w=None, rank=None, stream_ptr=0):
+    """Enqueued host-buffer call (rrsvd_execute_host_async): the arrays must
+    stay alive and unread until rrsvd_host_wait(plan)."""
+    def hp(a):
+        return _vp(a.ctypes.data) if a is not None else None
+    _pcheck(plan, load().rrsvd_execute_host_async(plan, hp(theta), chain0, hp(sigma), hp(U), hp(Vh), hp(w), hp(rank),
+                                                  _vp(int(stream_ptr)) if stream_ptr else None))
+
+
+def rrsvd_host_wait(plan):
+    _pcheck(plan, load().rrsvd_host_wait(plan))
 
 
 def rrsvd_execute_noalloc(m, n, k_max, p, q, batch, seed, chain0, theta_ptr, sigma_ptr, U_ptr=0, Vh_ptr=0,

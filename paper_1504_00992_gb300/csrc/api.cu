@@ -1490,6 +1490,15 @@ struct rrsvd_plan_s {
   static const int HCH = 4;
   cudaStream_t hs[HCH] = {nullptr, nullptr, nullptr, nullptr};
   cudaEvent_t hev[HCH + 1] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  // asynchronous host path: two staging slots (theta in, results out) used in
+  // turn, one workspace, copy-in and copy-out streams, and per slot the
+  // events "copied in", "computed", "copied out"
+  char* aslot[2] = {nullptr, nullptr};
+  char* aws = nullptr;
+  cudaStream_t acs = nullptr, aos = nullptr, astream = nullptr;
+  cudaEvent_t a_call = nullptr, a_in[2] = {nullptr, nullptr}, a_comp[2] = {nullptr, nullptr},
+              a_out[2] = {nullptr, nullptr};
+  int anext = 0, apending = 0;
   // autotuner choices (rrsvd_plan_autotune): FP64 GEMM tiles, mixed-form knobs
   int tiles[6] = {0, 0, 0, 0, 0, 0};
   MixedKnobs mk{0, 0, 0, 0, 0};
@@ -1592,6 +1601,17 @@ extern "C" int rrsvd_plan_destroy(rrsvd_plan_t P) {
     if (h) cudaStreamDestroy(h);
   for (cudaEvent_t& e : P->hev)
     if (e) cudaEventDestroy(e);
+  if (P->apending) {  // finish the pending calls before their buffers go
+    if (P->astream) cudaStreamSynchronize(P->astream);
+    if (P->aos) cudaStreamSynchronize(P->aos);
+  }
+  for (char* b : P->aslot)
+    if (b) cudaFree(b);
+  if (P->aws) cudaFree(P->aws);
+  for (cudaStream_t h : {P->acs, P->aos})
+    if (h) cudaStreamDestroy(h);
+  for (cudaEvent_t e : {P->a_call, P->a_in[0], P->a_in[1], P->a_comp[0], P->a_comp[1], P->a_out[0], P->a_out[1]})
+    if (e) cudaEventDestroy(e);
   delete P;
   return TEBD_OK;
 }
@@ -1674,9 +1694,28 @@ extern "C" int rrsvd_execute(rrsvd_plan_t P, const double* theta, int64_t chain0
   return TEBD_OK;
 }
 
+// Status flags raised by the truncations since they were last read: the
+// plan's error (and return code) for them.
+static int plan_flags(rrsvd_plan_t P, int stv, int tce) {
+  if (tce) { P->err.set(TEBD_ETIMEOUT, "a tensor-core pipeline wait expired"); return P->err.code; }
+  if (stv & 4) {
+    P->err.set(TEBD_ENUMERIC, "the re-orthonormalisation of an FP32 basis met a non-finite or far from orthonormal "
+                              "basis");
+    return P->err.code;
+  }
+  if (stv & 1) { P->err.set(TEBD_ENUMERIC, "an instance had a zero or non-finite theta"); return P->err.code; }
+  return TEBD_OK;
+}
+
+extern "C" int rrsvd_host_wait(rrsvd_plan_t P);
+
 extern "C" int rrsvd_execute_host(rrsvd_plan_t P, const double* theta, int64_t chain0, double* sigma, double* U,
                                   double* Vh, double* w, int* rank, void* stream) {
   if (!P) return TEBD_EINVAL;
+  if (P->apending) {
+    const int rc = rrsvd_host_wait(P);
+    if (rc) return rc;
+  }
   if (P->err.code) return P->err.code;
   if (!theta || !sigma) { P->err.set(TEBD_EINVAL, "NULL theta or sigma"); return P->err.code; }
   const size_t B = P->batch, c = sizeof(cplx);
@@ -1772,14 +1811,89 @@ extern "C" int rrsvd_execute_host(rrsvd_plan_t P, const double* theta, int64_t c
   CU_OR(P, cudaMemcpyAsync(&stv, P->status, sizeof(int), cudaMemcpyDeviceToHost, st));
   CU_OR(P, cudaMemcpyAsync(&tce, P->tcerr, sizeof(int), cudaMemcpyDeviceToHost, st));
   CU_OR(P, cudaStreamSynchronize(st));
-  if (tce) { P->err.set(TEBD_ETIMEOUT, "a tensor-core pipeline wait expired"); return P->err.code; }
-  if (stv & 4) {
-    P->err.set(TEBD_ENUMERIC, "the re-orthonormalisation of an FP32 basis met a non-finite or far from orthonormal "
-                              "basis");
-    return P->err.code;
+  return plan_flags(P, stv, tce);
+}
+
+extern "C" int rrsvd_execute_host_async(rrsvd_plan_t P, const double* theta, int64_t chain0, double* sigma,
+                                        double* U, double* Vh, double* w, int* rank, void* stream) {
+  if (!P) return TEBD_EINVAL;
+  if (P->err.code) return P->err.code;
+  if (!theta || !sigma || chain0 < 0) { P->err.set(TEBD_EINVAL, "NULL theta or sigma, or chain0 < 0"); return P->err.code; }
+  const size_t B = P->batch, c = sizeof(cplx);
+  const size_t th = align_up(c * (size_t)P->m * P->n * B), sg = align_up(sizeof(double) * P->k * B),
+               uu = align_up(c * (size_t)P->m * P->k * B), vv = align_up(c * (size_t)P->k * P->n * B),
+               ww = align_up(sizeof(double) * B), rr = align_up(sizeof(int) * B);
+  const size_t slot_bytes = th + sg + uu + vv + ww + rr;
+  if (!P->aws) {
+    if (fault_take(TEBD_FAULT_ALLOC) || cudaMalloc(&P->aws, P->ws_bytes) != cudaSuccess ||
+        cudaMalloc(&P->aslot[0], slot_bytes) != cudaSuccess || cudaMalloc(&P->aslot[1], slot_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      for (char*& b : P->aslot)
+        if (b) { cudaFree(b); b = nullptr; }
+      if (P->aws) { cudaFree(P->aws); P->aws = nullptr; }
+      P->err.set(TEBD_ENOMEM, "staging allocation of 2 x %zu + %zu bytes failed", slot_bytes, P->ws_bytes);
+      return P->err.code;
+    }
+    CU_OR(P, cudaStreamCreateWithFlags(&P->acs, cudaStreamNonBlocking));
+    CU_OR(P, cudaStreamCreateWithFlags(&P->aos, cudaStreamNonBlocking));
+    for (cudaEvent_t* e : {&P->a_call, &P->a_in[0], &P->a_in[1], &P->a_comp[0], &P->a_comp[1], &P->a_out[0],
+                           &P->a_out[1]})
+      CU_OR(P, cudaEventCreateWithFlags(e, cudaEventDisableTiming));
   }
-  if (stv & 1) { P->err.set(TEBD_ENUMERIC, "an instance had a zero or non-finite theta"); return P->err.code; }
+  const int slot = P->anext;
+  P->anext ^= 1;
+  char* s = P->aslot[slot];
+  double* d_th = (double*)s;
+  double* d_sg = (double*)(s + th);
+  double* d_u = (double*)(s + th + sg);
+  double* d_v = (double*)(s + th + sg + uu);
+  double* d_w = (double*)(s + th + sg + uu + vv);
+  int* d_r = (int*)(s + th + sg + uu + vv + ww);
+  cudaStream_t st = (cudaStream_t)stream;
+  // copy in once the caller's earlier work is queued and this slot's theta
+  // was last read (the truncation two calls back)
+  CU_OR(P, cudaEventRecord(P->a_call, st));
+  CU_OR(P, cudaStreamWaitEvent(P->acs, P->a_call, 0));
+  CU_OR(P, cudaStreamWaitEvent(P->acs, P->a_comp[slot], 0));
+  {
+    ProfScope ps("copy[h2d]", P->acs);
+    CU_OR(P, cudaMemcpyAsync(d_th, theta, c * (size_t)P->m * P->n * B, cudaMemcpyHostToDevice, P->acs));
+  }
+  CU_OR(P, cudaEventRecord(P->a_in[slot], P->acs));
+  // the truncation after the copy in and after this slot's results of two
+  // calls back are copied out
+  CU_OR(P, cudaStreamWaitEvent(st, P->a_in[slot], 0));
+  CU_OR(P, cudaStreamWaitEvent(st, P->a_out[slot], 0));
+  P->apending = 1;
+  P->astream = st;
+  int rc = rrsvd_execute(P, d_th, chain0, d_sg, U ? d_u : nullptr, Vh ? d_v : nullptr, w ? d_w : nullptr,
+                         rank ? d_r : nullptr, P->aws, P->ws_bytes, stream);
+  if (rc) return rc;
+  CU_OR(P, cudaEventRecord(P->a_comp[slot], st));
+  CU_OR(P, cudaStreamWaitEvent(P->aos, P->a_comp[slot], 0));
+  {
+    ProfScope ps("copy[d2h]", P->aos);
+    CU_OR(P, cudaMemcpyAsync(sigma, d_sg, sizeof(double) * P->k * B, cudaMemcpyDeviceToHost, P->aos));
+    if (U) CU_OR(P, cudaMemcpyAsync(U, d_u, c * (size_t)P->m * P->k * B, cudaMemcpyDeviceToHost, P->aos));
+    if (Vh) CU_OR(P, cudaMemcpyAsync(Vh, d_v, c * (size_t)P->k * P->n * B, cudaMemcpyDeviceToHost, P->aos));
+    if (w) CU_OR(P, cudaMemcpyAsync(w, d_w, sizeof(double) * B, cudaMemcpyDeviceToHost, P->aos));
+    if (rank) CU_OR(P, cudaMemcpyAsync(rank, d_r, sizeof(int) * B, cudaMemcpyDeviceToHost, P->aos));
+  }
+  CU_OR(P, cudaEventRecord(P->a_out[slot], P->aos));
   return TEBD_OK;
+}
+
+extern "C" int rrsvd_host_wait(rrsvd_plan_t P) {
+  if (!P) return TEBD_EINVAL;
+  if (!P->apending) return P->err.code;
+  P->apending = 0;
+  CU_OR(P, cudaStreamSynchronize(P->aos));
+  CU_OR(P, cudaStreamSynchronize(P->astream));
+  int stv = 0, tce = 0;
+  CU_OR(P, cudaMemcpy(&stv, P->status, sizeof(int), cudaMemcpyDeviceToHost));
+  CU_OR(P, cudaMemcpy(&tce, P->tcerr, sizeof(int), cudaMemcpyDeviceToHost));
+  if (P->err.code) return P->err.code;
+  return plan_flags(P, stv, tce);
 }
 
 extern "C" const char* rrsvd_last_error(rrsvd_plan_t P) { return P ? P->err.msg.c_str() : "NULL plan"; }

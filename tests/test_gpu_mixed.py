@@ -319,3 +319,37 @@ def test_host_path_sub_batches_equal_device_path(lib, form):
         B.rrsvd_plan_destroy(plan)
     assert np.array_equal(sg, dev["sigma"]) and np.array_equal(U, dev["U"]) and np.array_equal(Vh, dev["Vh"])
     assert np.array_equal(w, dev["w"]) and np.array_equal(rk, dev["rank"]) and np.array_equal(sg2, sg)
+
+
+def test_async_host_calls_overlap_and_equal_device_path(lib):
+    """rrsvd_execute_host_async: three calls in flight on one plan (two
+    staging slots used in turn, the third call waiting for the first slot),
+    each with its own chain0 and output arrays, equal the device path bit for
+    bit after rrsvd_host_wait; the wait reports nothing when nothing failed
+    and returns at once when nothing is pending."""
+    from paper_1504_00992_gb300 import binding as B
+    m, n, k, p, q, batch = 200, 180, 30, 8, 1, 5
+    sig = I.exp_spectrum(min(m, n), 6.0)
+    theta = np.stack([I.synthetic_theta(m, n, sig, seed=70 + t) for t in range(batch)])
+    plan = B.rrsvd_plan_create(m, n, k, p, q, batch, B.TEBD_PREC_TF32, SEED)
+    try:
+        outs = []
+        for call in range(3):
+            o = {"sigma": np.zeros((batch, k)), "U": np.zeros((batch, m, k), dtype=np.complex128),
+                 "Vh": np.zeros((batch, k, n), dtype=np.complex128), "w": np.zeros(batch),
+                 "rank": np.zeros(batch, dtype=np.int32)}
+            B.rrsvd_execute_host_async(plan, theta, 100 * call, o["sigma"], o["U"], o["Vh"], o["w"], o["rank"])
+            outs.append(o)
+        B.rrsvd_host_wait(plan)
+        B.rrsvd_host_wait(plan)
+        for call in range(3):
+            dev = rrsvd_device(B, plan, theta, chain0=100 * call)
+            for key in ("sigma", "U", "Vh", "w", "rank"):
+                assert np.array_equal(outs[call][key], dev[key]), (call, key)
+        # a zero theta is reported by the wait
+        B.rrsvd_execute_host_async(plan, np.zeros_like(theta), 0, np.zeros((batch, k)))
+        with pytest.raises(B.TebdError) as ei:
+            B.rrsvd_host_wait(plan)
+        assert ei.value.code == B.TEBD_ENUMERIC
+    finally:
+        B.rrsvd_plan_destroy(plan)
