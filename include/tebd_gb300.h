@@ -379,9 +379,10 @@ int rrsvd_execute_host(rrsvd_plan_t plan, const double* theta, int64_t chain0, d
                        double* Vh, double* w, int* rank, void* stream);
 
 /* The same truncation from and to HOST buffers without waiting for it:
- * enqueues the copy in (on a copy stream of the plan's own, after the work
- * already on `stream`), the truncation (on `stream`) and the copy out (on a
- * second stream of the plan's own) and returns.  The plan keeps two staging
+ * enqueues the copy in (on a copy stream of the plan's own, at once: theta
+ * must hold its values when the call is made, whatever work `stream` still
+ * has queued), the truncation (on `stream`) and the copy out (on a second
+ * stream of the plan's own) and returns.  The plan keeps two staging
  * slots used in turn, so the copy in of a call runs while the previous
  * call's truncation computes; a call blocks only on the host while slots
  * are busy.  theta and the outputs must stay valid, and the outputs unread,

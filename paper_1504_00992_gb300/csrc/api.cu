@@ -1850,10 +1850,9 @@ extern "C" int rrsvd_execute_host_async(rrsvd_plan_t P, const double* theta, int
   double* d_w = (double*)(s + th + sg + uu + vv);
   int* d_r = (int*)(s + th + sg + uu + vv + ww);
   cudaStream_t st = (cudaStream_t)stream;
-  // copy in once the caller's earlier work is queued and this slot's theta
-  // was last read (the truncation two calls back)
-  CU_OR(P, cudaEventRecord(P->a_call, st));
-  CU_OR(P, cudaStreamWaitEvent(P->acs, P->a_call, 0));
+  // copy in as soon as this slot's theta was last read (by the truncation
+  // two calls back): not ordered after the work on `stream`, so that it
+  // overlaps the previous call's truncation
   CU_OR(P, cudaStreamWaitEvent(P->acs, P->a_comp[slot], 0));
   {
     ProfScope ps("copy[h2d]", P->acs);
