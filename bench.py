@@ -438,7 +438,6 @@ def roofline(res, batch):
         # m x l complex matrix, m = n here)
         "k_qr_f32": ((16.0 * M * l * l - 16.0 * l ** 3 / 3) * batch, "alu", fp32_peak, fp32_src, "qr_blocked.cu"),
         "k_zgemm[uv]": (8.0 * M * l * k * batch, "alu", fp64_peak, fp64_src, "kernels.cu"),
-        "k_zgemm_df[project]": (8.0 * M * N_ * l * batch, "alu", df_peak, df_src, "df_proj.cu"),
         "k_oz_proj[project]": (8.0 * M * N_ * l * batch, "tensor", oz_peak, oz_src, "oz_proj.cu"),
         # the Cholesky QR of B^H (Gram matrices, triangular products, B Qb:
         # each n l^2 complex multiply-adds as computed) and U, V, on the same

@@ -57,9 +57,10 @@ __device__ __forceinline__ float tf32_rna(float x) {
 //   adjoint copy tha (n x K2), transposed through shared memory:
 //     tha[c][2r] = Re theta[r][c], tha[c][2r+1] = -Im theta[r][c], and its
 //     remainder;
-//   double-float copy of conj(theta) (m x n float4: Re hi, Re lo, -Im hi,
-//     -Im lo), when thd is set, for the projection.
-// The tiles cover the zero padding of both copies.
+//   BF16 copies of both (the BF16 form's products before the refinement
+//     round), when thf_b / tha_b are set;
+//   the tile partial sums of ||theta||_F^2 (double-float, then FP64).
+// The tiles cover the zero padding of every copy.
 // ---------------------------------------------------------------------------
 // double-float pair sum (Knuth's TwoSum on the high words)
 __device__ __forceinline__ void df_add2(float& h, float& l, float oh, float ol) {
@@ -88,7 +89,6 @@ __global__ void __launch_bounds__(256) k_conv_theta(const MixedPtrs mp, const Di
   float2* fl = reinterpret_cast<float2*>(mp.thf_lo + (size_t)z * mc * K1);
   float2* ah = reinterpret_cast<float2*>(mp.tha_hi + (size_t)z * nc * K2);
   float2* al = reinterpret_cast<float2*>(mp.tha_lo + (size_t)z * nc * K2);
-  float4* dd = mp.thd ? mp.thd + (size_t)z * mc * nc : nullptr;
   unsigned* fb = mp.thf_b ? reinterpret_cast<unsigned*>(mp.thf_b + (size_t)z * mc * K1b) : nullptr;
   unsigned* ab = mp.tha_b ? reinterpret_cast<unsigned*>(mp.tha_b + (size_t)z * nc * K2b) : nullptr;
   const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
@@ -112,7 +112,6 @@ __global__ void __launch_bounds__(256) k_conv_theta(const MixedPtrs mp, const Di
       fh[(int64_t)r * half1 + c] = make_float2(hr, hm);
       if (want_lo) fl[(int64_t)r * half1 + c] = make_float2(lr, lm);
     }
-    if (dd && r < mc && c < nc) dd[(int64_t)r * nc + c] = make_float4(xh, xl, -yh, -yl);
     // |v|^2 = xh^2 + yh^2 + 2 (xh xl + yh yl) + O(2^-48)
     const float p1 = xh * xh, e1 = fmaf(xh, xh, -p1);
     const float p2 = yh * yh, e2 = fmaf(yh, yh, -p2);
@@ -473,8 +472,6 @@ MixedSizes mixed_sizes(int m, int n, int k, int l, int bf16) {
   s.ytf = (size_t)n * l * sizeof(float2);
   s.df = (size_t)l * l * sizeof(float2);
   // the projection runs on the tensor cores from BF16 digits (oz_proj.cu)
-  // rather than from a double-float copy of theta
-  s.thd = 0;
   s.bd = oz_digits_bytes(n, m);
   s.bsc = oz_scales_bytes(n, m);
   s.ad = oz_digits_bytes(l, m);
@@ -505,7 +502,7 @@ static size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 size_t mixed_bytes(const MixedSizes& s, int batch) {
   return 2 * up256(s.thf * batch) + 2 * up256(s.tha * batch) + 2 * up256(s.bt * batch) + 2 * up256(s.yf * batch) +
-         2 * up256(s.ytf * batch) + up256(s.df * batch) + up256(s.thd * batch) +
+         2 * up256(s.ytf * batch) + up256(s.df * batch) +
          up256((size_t)s.ntile * sizeof(double) * batch) + up256(s.qs * batch) + up256(s.bd * batch) +
          up256(s.bsc * batch) + up256(s.ad * batch) + up256(s.asc * batch) + up256(s.thfb * batch) +
          up256(s.thab * batch) + up256(s.btb * batch) + up256(s.gad * batch) + up256(s.gas * batch) +
@@ -526,8 +523,6 @@ MixedPtrs mixed_carve(char* base, const MixedSizes& s, int batch) {
   p.Ytf = (float2*)(base + o); o += up256(s.ytf * batch);
   p.Qtf = (float2*)(base + o); o += up256(s.ytf * batch);
   p.Df = (float2*)(base + o); o += up256(s.df * batch);
-  p.thd = s.thd ? (float4*)(base + o) : nullptr;
-  o += up256(s.thd * batch);
   p.tpart = (double*)(base + o);
   o += up256((size_t)s.ntile * sizeof(double) * batch);
   p.qscr = s.qs ? (float2*)(base + o) : nullptr;
@@ -561,7 +556,6 @@ MixedPtrs mixed_offset(const MixedPtrs& p, const MixedSizes& s, int z0) {
   o.Ytf = adv(p.Ytf, s.ytf);
   o.Qtf = adv(p.Qtf, s.ytf);
   o.Df = adv(p.Df, s.df);
-  o.thd = adv(p.thd, s.thd);
   o.tpart = adv(p.tpart, (size_t)s.ntile * sizeof(double));
   o.qscr = adv(p.qscr, s.qs);
   o.bd = adv(p.bd, s.bd);

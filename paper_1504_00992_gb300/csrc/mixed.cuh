@@ -15,7 +15,7 @@ struct MixedSizes {
   int K1b, K2b;  // the same rounded up to 64 for the BF16 copies (128-byte rows)
   int Np;        // 2l rounded up to 16: rows of Bt (tensor-core N)
   int BN;        // tensor-core tile width, min(Np, 256)
-  size_t thf, tha, bt, yf, ytf, df, thd;  // bytes per instance
+  size_t thf, tha, bt, yf, ytf, df;  // bytes per instance
   size_t bd, bsc, ad, asc;  // BF16 digits and block scales of theta and of Q_f^H (tensor-core projection)
   size_t thfb, thab, btb;   // BF16 copies of theta, theta^H and Bt (bf16 only)
   size_t gad, gas, gbd, gbs;  // digit scratch of the other tensor-core products (oz_stage_bytes)
@@ -36,7 +36,6 @@ struct MixedPtrs {
   float2* Ytf;    // n x l
   float2* Qtf;
   float2* Df;     // l x l correction of the re-orthonormalisation
-  float4* thd;    // m x n double-float conj(theta) (Re hi, Re lo, -Im hi, -Im lo), or null
   uint16_t* bd;   // digits of theta for the tensor-core projection (oz_proj.cu)
   float* bsc;     // their block scales
   uint16_t* ad;   // digits of Q_f^H
@@ -84,10 +83,6 @@ cudaError_t launch_reorth(const float2* Qf, float2* Dbuf, const Dims* dims, cons
 // B^H <- B^H (I + D) in place on ptrs[z].Yt (qr_blocked.cu).
 cudaError_t launch_fold_bh(const float2* Dbuf, const Dims* dims, const ProbPtr* ptrs, int n, int l, int batch,
                            cudaStream_t st);
-// B^H = A^H Q_f (I + D) into ptrs[z].Yt (df_proj.cu) (n x l column-major): double-float
-// product with the FP32 Q_f, then the correction; after launch_reorth.
-cudaError_t launch_proj_df(const float4* thd, const Dims* dims, const ProbPtr* ptrs, const float2* Qf,
-                           const float2* Dbuf, int m, int n, int l, int batch, cudaStream_t st);
 
 // B^H = A^H Q_f (I + D) into ptrs[z].Yt on the tensor cores from BF16 digits
 // (oz_proj.cu): launch_oz_digits_theta once theta is in place, launch_proj_oz

@@ -1,6 +1,6 @@
 """Host-side arithmetic of bench.py's roofline object (no GPU): achieved
-flops per launch over the mean launch time, the derived double-float
-ceiling, and DRAM traffic taken from the committed ncu record only while
+flops per launch over the mean launch time, the derived ceilings, and DRAM
+traffic taken from the committed ncu record only while
 that record was captured on the current kernel source."""
 import json
 import os
@@ -14,24 +14,25 @@ def _res(prof):
     return {"prof": prof, "l": 120, "k": 100}
 
 
-def test_projection_roofline_arithmetic():
+def test_fp32_qr_roofline_arithmetic():
     batch = 152
-    # two launches of 88 ms each of the projection, smaller classes beside it
-    r = bench.roofline(_res({"k_zgemm_df[project]": (176.0, 2), "k_qr": (160.0, 2)}), batch)
-    flops = 8.0 * bench.M * bench.N_ * 120 * batch
-    assert r["kernel"] == "k_zgemm_df[project]" and r["bound"] == "alu"
-    assert r["achieved"] == pytest.approx(flops / 0.088 / 1e12)
-    assert r["peak"] == pytest.approx(152 * 128 * 2.07 / 37 * 8 / 1e3)
+    # five launches of the FP32 QRs at 4.9 ms each, the projection beside them
+    r = bench.roofline(_res({"k_qr_f32": (24.5, 5), "k_oz_proj[project]": (15.1, 1)}), batch)
+    flops = (16.0 * bench.M * 120 * 120 - 16.0 * 120 ** 3 / 3) * batch
+    assert r["kernel"] == "k_qr_f32" and r["bound"] == "alu"
+    assert r["achieved"] == pytest.approx(flops / 0.0049 / 1e12)
+    assert r["peak"] == pytest.approx(152 * 128 * 2 * 2.07 / 1e3)
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
 
 
 def test_traffic_only_from_a_matching_capture():
-    r = bench.roofline(_res({"k_zgemm_df[project]": (88.0, 1)}), 152)
-    rec = json.load(open(os.path.join(bench.ROOT, "profiles", "traffic.json")))["k_zgemm_df[project]"]
-    if rec["src_sha256_16"] == bench._src_hash("df_proj.cu"):
+    r = bench.roofline(_res({"k_oz_proj[project]": (15.0, 1)}), 152)
+    rec = json.load(open(os.path.join(bench.ROOT, "profiles", "traffic.json")))["k_oz_proj[project]"]
+    if rec["src_sha256_16"] == bench._src_hash("oz_proj.cu"):
         assert r["traffic"] == rec["dram_bytes_per_instance"] * 152
-        # the capture moved about the algorithmic bytes: double-float theta read once, Q_f, B^H
-        alg = bench.M * bench.N_ * 16 + bench.M * 120 * 8 + bench.N_ * 120 * 16
+        # the capture moved about the algorithmic bytes: theta's six digits
+        # (24 bytes per complex element, k padded to 64), Q_f's digits, B^H
+        alg = 24 * bench.N_ * 2048 + 24 * 120 * 2048 + bench.N_ * 120 * 16
         assert 0.95 * alg <= rec["dram_bytes_per_instance"] <= 1.1 * alg
     else:
         assert r["traffic"] is None
