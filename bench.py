@@ -444,6 +444,8 @@ def roofline(res, batch):
         # digit-pair kernel
         "k_oz_gemm[cholqr]": (8.0 * N_ * l * l * batch, "tensor", oz_peak, oz_src, "oz_proj.cu"),
         "k_oz_gemm[uv]": (8.0 * M * l * k * batch, "tensor", oz_peak, oz_src, "oz_proj.cu"),
+        # E = Q_f^H Q_f - I of the re-orthonormalisation (full l x l product)
+        "k_oz_gemm[gram]": (8.0 * M * l * l * batch, "tensor", oz_peak, oz_src, "oz_proj.cu"),
         "k_zgemm_df[cholqr]": (8.0 * N_ * l * l * batch, "alu", df_peak, df_src, "kernels.cu"),
         "k_zgemm_df[uv]": (8.0 * M * l * k * batch, "alu", df_peak, df_src, "kernels.cu"),
         # the sketch products (one complex m x n x l product per launch; the

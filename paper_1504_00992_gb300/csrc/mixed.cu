@@ -745,8 +745,13 @@ cudaError_t run_rrsvd_mixed(const Dims* dims, const ProbPtr* ptrs, int batch, co
   // every basis they pass fits it.
   if (!reorth_fits(m, l)) return cudaErrorInvalidValue;
   MX_TRY(qr_f32(mp.Yf, mp.Qf, m, l, batch, mp, s, dims, 0, st, kn.qr_threads));
-  MX_TRY(launch_reorth(mp.Qf, mp.Df, dims, ptrs, m, l, batch, status, st));
-  MX_TRY(launch_proj_oz(dims, ptrs, mp.Qf, mp.Df, mp.ad, mp.asc, mp.bd, mp.bsc, m, n, l, batch, err, st));  // B^H = A^H Q
+  // digits of Q_f once: the Gram of the re-orthonormalisation and the
+  // projection B^H = A^H Q both take them
+  MX_TRY(launch_oz_digits_qf(dims, mp.Qf, mp.ad, mp.asc, m, l, batch, st));
+  MX_TRY(launch_oz_gram(dims, ptrs, mp.ad, mp.asc, m, l, batch, err, st));
+  MX_TRY(launch_reorth(mp.Qf, mp.Df, dims, ptrs, m, l, batch, status, st, true));
+  MX_TRY(launch_proj_oz(dims, ptrs, mp.Qf, mp.Df, mp.ad, mp.asc, mp.bd, mp.bsc, m, n, l, batch, err, st,
+                        true));  // B^H = A^H Q
   // QR of B^H: Cholesky QR where the one-CTA Householder would run (it falls
   // back to Householder per ill-conditioned instance), else the size rule
   // the FP64-accurate products after the projection: tensor cores from digit

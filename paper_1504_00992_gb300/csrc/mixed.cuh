@@ -77,9 +77,10 @@ cudaError_t launch_qr_multi_f32(float2* A, float2* Q, float2* scr, size_t stride
                                 cudaStream_t st, const Dims* dims = nullptr, int use_n = 0);
 // Q_f (FP32, M x L) -> ptrs[z].Q (FP64) orthonormal to ~1e-13, spanning
 // range(Q_f); uses ptrs[z].R as scratch; usable when reorth_fits(M, L).
+// gram_done: E = Q_f^H Q_f - I is already in ptrs[z].R (launch_oz_gram).
 bool reorth_fits(int M, int L);
 cudaError_t launch_reorth(const float2* Qf, float2* Dbuf, const Dims* dims, const ProbPtr* ptrs, int M, int L,
-                          int batch, int* status, cudaStream_t st);
+                          int batch, int* status, cudaStream_t st, bool gram_done = false);
 // B^H <- B^H (I + D) in place on ptrs[z].Yt (qr_blocked.cu).
 cudaError_t launch_fold_bh(const float2* Dbuf, const Dims* dims, const ProbPtr* ptrs, int n, int l, int batch,
                            cudaStream_t st);
@@ -118,9 +119,17 @@ cudaError_t run_cholqr_bh(Dims* dims, const ProbPtr* ptrs, int batch, const Caps
                           const OzScratch* oz, int* err);
 cudaError_t launch_oz_digits_theta(const Dims* dims, const ProbPtr* ptrs, uint16_t* Bd, float* Bs, int m, int n,
                                    int batch, cudaStream_t st);
+// (digits_done: Q_f's digits already in Ad / As from launch_oz_digits_qf)
 cudaError_t launch_proj_oz(const Dims* dims, const ProbPtr* ptrs, const float2* Qf, const float2* Dbuf,
                            uint16_t* Ad, float* As, const uint16_t* Bd, const float* Bs, int m, int n, int l, int batch,
-                           int* err, cudaStream_t st);
+                           int* err, cudaStream_t st, bool digits_done = false);
+// Digits of conj(Q_f) (the projection's left operand) into Ad / As, and the
+// Gram matrix E = Q_f^H Q_f - I of the re-orthonormalisation from them into
+// ptrs[z].R (l x l column-major), FP64-accurate, on the tensor cores.
+cudaError_t launch_oz_digits_qf(const Dims* dims, const float2* Qf, uint16_t* Ad, float* As, int m, int l, int batch,
+                                cudaStream_t st);
+cudaError_t launch_oz_gram(const Dims* dims, const ProbPtr* ptrs, const uint16_t* Ad, const float* As, int m, int l,
+                           int batch, int* err, cudaStream_t st);
 
 // Launch choices of the mixed form that the autotuner may override (0 keeps
 // each size rule): tc_half = 1 splits the tensor-core products' columns over

@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(256) k_oz_digits_q(const Dims* __restrict__ di
 // C = op(A) op(B) with op(A) conjugated where StageFlags says so and C
 // stored conjugated for G_V.
 // ---------------------------------------------------------------------------
-enum { OZ_PROJ = 100 };
+enum { OZ_PROJ = 100, OZ_GRAM = 101 };
 
 struct OzOp {
   int M, N, K;  // rows and columns of C, depth
@@ -264,6 +264,9 @@ __device__ __forceinline__ OzOp oz_op(const Dims& D, const ProbPtr& P) {
   if constexpr (ST == OZ_PROJ) {
     o.M = D.l; o.N = D.n; o.K = D.m;
     o.C = P.Yt; o.crs = D.n; o.ccs = 1;  // element (j, i) of the n x l column-major B^H
+  } else if constexpr (ST == OZ_GRAM) {
+    o.M = D.l; o.N = D.l; o.K = D.m;
+    o.C = P.R; o.crs = 1; o.ccs = D.l;  // E = Q_f^H Q_f - I, l x l column-major
   } else {
     const GemmOp g = gemm_of<ST>(D, P);
     o.M = g.M; o.N = g.N; o.K = g.K;
@@ -274,8 +277,11 @@ __device__ __forceinline__ OzOp oz_op(const Dims& D, const ProbPtr& P) {
 
 template <int ST>
 struct OzConj {
-  static constexpr bool A = ST != OZ_PROJ && StageFlags<ST>::conjA;  // the projection folds it into Q's digits
-  static constexpr bool C = ST == OZ_PROJ || StageFlags<ST>::conjC;
+  // the projection and the Gram fold conj(Q_f) into Q_f's digits; the Gram
+  // multiplies them by their own conjugate
+  static constexpr bool A = ST != OZ_PROJ && ST != OZ_GRAM && StageFlags<ST>::conjA;
+  static constexpr bool B = ST == OZ_GRAM;
+  static constexpr bool C = ST == OZ_PROJ || (ST != OZ_GRAM && StageFlags<ST>::conjC);
 };
 
 // Digits of a stage operand in its K-major view: SIDE 0 the rows i of op(A)
@@ -534,11 +540,13 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             const uint32_t dr = tmem + (uint32_t)(OZ_BN * (t - 1)), di = tmem + (uint32_t)(OZ_BN * (OZ_NGRP + t - 1));
             const uint64_t ar = oz_desc_sw32(abase + (0 * OZ_S + t - 1) * OZ_A_TILE);
             const uint64_t ai = oz_desc_sw32(abase + (1 * OZ_S + t - 1) * OZ_A_TILE);
-            // (conjugated left operand: C_r += Ai Bi, C_i -= Ai Br)
+            // signs of a conjugated operand: C_r = Ar Br - sA sB Ai Bi,
+            // C_i = sB Ar Bi + sA Ai Br with s = -1 for a conjugated side
+            constexpr bool cA = OzConj<ST>::A, cB = OzConj<ST>::B;
             oz_mma(dr, ar, br, ip, acc0);                         // C_r += Ar Br
-            oz_mma(dr, ai, bi, OzConj<ST>::A ? ip : in, 1u);     // C_r -= Ai Bi
-            oz_mma(di, ar, bi, ip, acc0);                         // C_i += Ar Bi
-            oz_mma(di, ai, br, OzConj<ST>::A ? in : ip, 1u);     // C_i += Ai Br
+            oz_mma(dr, ai, bi, (cA != cB) ? ip : in, 1u);         // C_r -= Ai Bi
+            oz_mma(di, ar, bi, cB ? in : ip, acc0);               // C_i += Ar Bi
+            oz_mma(di, ai, br, cA ? in : ip, 1u);                 // C_i += Ai Br
           }
           oz_commit(&empty[s]);  // the stage is free once these MMAs have read it
           issued_mma = it + 1;
@@ -608,7 +616,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       for (int c = 0; c < 8; ++c) {
         const int j = jq + c;
         if (j < op.N) {
-          const double re = (double)hr[c] + (double)lr[c], im = (double)hi[c] + (double)li[c];
+          double re = (double)hr[c] + (double)lr[c];
+          const double im = (double)hi[c] + (double)li[c];
+          if (ST == OZ_GRAM && i == j) re -= 1.0;  // E = Q_f^H Q_f - I
           op.C[(int64_t)i * op.crs + (int64_t)j * op.ccs] = cmk(re, OzConj<ST>::C ? -im : im);
         }
       }
@@ -675,7 +685,7 @@ cudaError_t oz_prepare() {
   if (!oz_encode_fn()) return cudaErrorNotSupported;
   static int done = 0;
   if (!done) {
-    const cudaError_t es[] = {oz_attr<OZ_PROJ>(), oz_attr<G_G1>(), oz_attr<G_Q1>(), oz_attr<G_G2>(),
+    const cudaError_t es[] = {oz_attr<OZ_PROJ>(), oz_attr<OZ_GRAM>(), oz_attr<G_G1>(), oz_attr<G_Q1>(), oz_attr<G_G2>(),
                               oz_attr<G_QB>(),    oz_attr<G_X>(),  oz_attr<G_U>(),  oz_attr<G_V>()};
     for (cudaError_t e : es)
       if (e != cudaSuccess) return e;
@@ -770,15 +780,44 @@ cudaError_t launch_oz_digits_theta(const Dims* dims, const ProbPtr* ptrs, uint16
   return cudaGetLastError();
 }
 
+cudaError_t launch_oz_digits_qf(const Dims* dims, const float2* Qf, uint16_t* Ad, float* As, int m, int l, int batch,
+                                cudaStream_t st) {
+  const int Kp = oz_kpad(m);
+  ProfScope ps("k_oz_digits[q]", st);
+  const int warps = l * (Kp / OZ_KB);
+  k_oz_digits_q<<<dim3((warps + 7) / 8, batch), 256, 0, st>>>(dims, Qf, Ad, As, m, l, Kp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_oz_gram(const Dims* dims, const ProbPtr* ptrs, const uint16_t* Ad, const float* As, int m, int l,
+                           int batch, int* err, cudaStream_t st) {
+  const cudaError_t e = oz_prepare();
+  if (e != cudaSuccess) return e;
+  const int Kp = oz_kpad(m);
+  CUtensorMap ta, tb;
+  if (!oz_make_map(&ta, Ad, Kp, l, batch, OZ_BM) || !oz_make_map(&tb, Ad, Kp, l, batch, OZ_BN))
+    return cudaErrorInvalidValue;
+  OzArgs oa;
+  oa.lc = l;
+  oa.nc = l;
+  oa.Kp = Kp;
+  oa.As = As;
+  oa.Bs = As;
+  oa.err = err;
+  oa.poll_limit = 1u << 24;
+  oa.stall = 0;
+  ProfScope ps("k_oz_gemm[gram]", st);
+  k_oz_gemm<OZ_GRAM><<<dim3((l + OZ_BN - 1) / OZ_BN, (l + OZ_BM - 1) / OZ_BM, batch), OZ_THREADS, oz_smem_bytes(),
+                       st>>>(ta, tb, dims, ptrs, oa);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_proj_oz(const Dims* dims, const ProbPtr* ptrs, const float2* Qf, const float2* Dbuf,
                            uint16_t* Ad, float* As, const uint16_t* Bd, const float* Bs, int m, int n, int l, int batch,
-                           int* err, cudaStream_t st) {
+                           int* err, cudaStream_t st, bool digits_done) {
   const int Kp = oz_kpad(m);
-  {
-    ProfScope ps("k_oz_digits[q]", st);
-    const int warps = l * (Kp / OZ_KB);
-    k_oz_digits_q<<<dim3((warps + 7) / 8, batch), 256, 0, st>>>(dims, Qf, Ad, As, m, l, Kp);
-    cudaError_t e = cudaGetLastError();
+  if (!digits_done) {
+    cudaError_t e = launch_oz_digits_qf(dims, Qf, Ad, As, m, l, batch, st);
     if (e != cudaSuccess) return e;
   }
   {

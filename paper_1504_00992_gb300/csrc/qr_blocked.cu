@@ -938,9 +938,9 @@ cudaError_t qr_blocked_prepare(int M, int N, int L) {
 bool reorth_fits(int M, int L) { return M >= L && L <= QF_MAXL_BIG; }
 
 cudaError_t launch_reorth(const float2* Qf, float2* Dbuf, const Dims* dims, const ProbPtr* ptrs, int M, int L,
-                          int batch, int* status, cudaStream_t st) {
+                          int batch, int* status, cudaStream_t st, bool gram_done) {
   const int nt = (L + 31) / 32;
-  {
+  if (!gram_done) {
     ProfScope ps("k_gram_df", st);
     k_gram_df<<<dim3(nt * (nt + 1) / 2, batch), 256, 0, st>>>(Qf, dims, ptrs, M, L);
     cudaError_t e = cudaGetLastError();
