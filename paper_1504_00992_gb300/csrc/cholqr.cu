@@ -113,9 +113,134 @@ __global__ void __launch_bounds__(256) k_chol_inv(Dims* dims, const ProbPtr* __r
   }
 }
 
-static cudaError_t chol_inv(Dims* dims, const ProbPtr* ptrs, int batch, int pass, cudaStream_t st) {
+// The same factorisation with the Gram's upper triangle packed in shared
+// memory (element (r, c), r <= c, at c (c + 1) / 2 + r) for l <= CS_MAXL, and
+// the inverse factor by warps: warp w solves R x = e_c for the columns
+// c = w (mod warps), bottom-up, each x_i a warp-wide dot product of row i of R
+// with the x_k already found (k > i), x in shared memory.
+enum { CS_THREADS = 256, CS_MAXL = 160 };
+
+__host__ __device__ inline size_t cs_smem_bytes(int L) {
+  return (((size_t)L * (L + 1) / 2) + (size_t)(CS_THREADS / 32) * L) * sizeof(cplx);
+}
+
+__device__ __forceinline__ int cs_at(int r, int c) { return c * (c + 1) / 2 + r; }
+
+__global__ void __launch_bounds__(CS_THREADS) k_chol_inv_sm(Dims* dims, const ProbPtr* __restrict__ ptrs, int pass) {
+  extern __shared__ __align__(16) unsigned char cs_raw[];
+  __shared__ double red[32];
+  __shared__ double s_inv;
+  __shared__ int s_fail;
+  const int p = blockIdx.x;
+  const Dims D = dims[p];
+  if (!D.active) return;
+  if (pass == 1 && D.qflag) return;
+  const ProbPtr P = ptrs[p];
+  const int L = D.l, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = CS_THREADS / 32;
+  cplx* T = reinterpret_cast<cplx*>(cs_raw);
+  cplx* X = T + (size_t)L * (L + 1) / 2;  // nw x L
+  const cplx* G = P.R;
+  cplx* J = P.J;
+  double dm = 0.0;
+  for (int e = tid; e < L * L; e += CS_THREADS) {
+    const int r = e % L, c = e / L;
+    if (r <= c) {
+      const cplx v = G[(size_t)c * L + r];
+      T[cs_at(r, c)] = v;
+      if (r == c) dm = fmax(dm, v.x);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+  if (lane == 0) red[warp] = dm;
+  __syncthreads();
+  if (tid == 0) {
+    double m = 0.0;
+    for (int w = 0; w < nw; ++w) m = fmax(m, red[w]);
+    red[0] = m;
+    s_fail = !(m > 0.0) || !isfinite(m);
+  }
+  __syncthreads();
+  dm = red[0];
+  for (int j = 0; j < L && !s_fail; ++j) {
+    if (tid == 0) {
+      const double d = T[cs_at(j, j)].x;
+      if (!(d > CQ_PIVOT * dm) || !isfinite(d)) {
+        s_fail = 1;
+      } else {
+        const double r = sqrt(d);
+        T[cs_at(j, j)] = cmk(r, 0.0);
+        s_inv = 1.0 / r;
+      }
+    }
+    __syncthreads();
+    if (s_fail) break;
+    const double inv = s_inv;
+    for (int c = j + 1 + tid; c < L; c += CS_THREADS) T[cs_at(j, c)] = cscale(T[cs_at(j, c)], inv);
+    __syncthreads();
+    // G[c1][c2] -= conj(R[j][c1]) R[j][c2], j < c1 <= c2
+    const int w = L - j - 1;
+    for (int e = tid; e < w * w; e += CS_THREADS) {
+      const int c1 = j + 1 + e % w, c2 = j + 1 + e / w;
+      if (c1 > c2) continue;
+      const cplx a = T[cs_at(j, c1)], b = T[cs_at(j, c2)];
+      cplx& g = T[cs_at(c1, c2)];
+      g.x -= a.x * b.x + a.y * b.y;
+      g.y -= a.x * b.y - a.y * b.x;
+    }
+    __syncthreads();
+  }
+  const int fail = s_fail;
+  if (tid == 0) dims[p].qflag = fail ? 1 : (pass == 0 ? 0 : D.qflag);
+  if (fail) {  // identity factor: the products in between stay finite
+    for (int e = tid; e < L * L; e += CS_THREADS) J[e] = cmk((e / L) == (e % L) ? 1.0 : 0.0, 0.0);
+    return;
+  }
+  cplx* x = X + (size_t)warp * L;
+  for (int c = warp; c < L; c += nw) {
+    for (int i = c; i >= 0; --i) {
+      cplx s = cmk(0.0, 0.0);
+      for (int k = i + 1 + lane; k <= c; k += 32) {
+        const cplx r = T[cs_at(i, k)], v = x[k];
+        s.x += r.x * v.x - r.y * v.y;
+        s.y += r.x * v.y + r.y * v.x;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+        s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+      }
+      if (lane == 0) {
+        const double rii = T[cs_at(i, i)].x;  // real and positive
+        x[i] = cscale(cmk((i == c ? 1.0 : 0.0) - s.x, -s.y), 1.0 / rii);
+      }
+      __syncwarp();
+    }
+    for (int i = lane; i < L; i += 32) J[(size_t)c * L + i] = i <= c ? x[i] : cmk(0.0, 0.0);
+    __syncwarp();
+  }
+}
+
+cudaError_t cholqr_prepare() {
+  static int done = 0;
+  if (!done) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(k_chol_inv_sm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cs_smem_bytes(CS_MAXL));
+    if (e != cudaSuccess) return e;
+    done = 1;
+  }
+  return cudaSuccess;
+}
+
+static cudaError_t chol_inv(Dims* dims, const ProbPtr* ptrs, int batch, int lcap, int pass, cudaStream_t st) {
   ProfScope ps("k_chol_inv", st);
-  k_chol_inv<<<batch, 256, 0, st>>>(dims, ptrs, pass);
+  if (lcap <= CS_MAXL) {
+    const cudaError_t e = cholqr_prepare();
+    if (e != cudaSuccess) return e;
+    k_chol_inv_sm<<<batch, CS_THREADS, cs_smem_bytes(lcap), st>>>(dims, ptrs, pass);
+  } else {
+    k_chol_inv<<<batch, 256, 0, st>>>(dims, ptrs, pass);
+  }
   return cudaGetLastError();
 }
 
@@ -132,10 +257,10 @@ cudaError_t run_cholqr_bh(Dims* dims, const ProbPtr* ptrs, int batch, const Caps
               : launch_zgemm_df(stage, dims, ptrs, batch, cap, st);
   };
   CQ_TRY(gemm(G_G1));                          // G1 = B B^H
-  CQ_TRY(chol_inv(dims, ptrs, batch, 0, st));  // R1, J = R1^-1
+  CQ_TRY(chol_inv(dims, ptrs, batch, cap.l, 0, st));  // R1, J = R1^-1
   CQ_TRY(gemm(G_Q1));                          // Q1 = B^H R1^-1
   CQ_TRY(gemm(G_G2));                          // G2 = Q1^H Q1
-  CQ_TRY(chol_inv(dims, ptrs, batch, 1, st));  // R2, J = R2^-1
+  CQ_TRY(chol_inv(dims, ptrs, batch, cap.l, 1, st));  // R2, J = R2^-1
   CQ_TRY(gemm(G_QB));                          // Qb = Q1 R2^-1
   CQ_TRY(gemm(G_X));                           // X = B Qb = Rb^H
   // ill-conditioned instances: Householder QR of B^H (overwrites X and Qb)

@@ -670,6 +670,7 @@ cudaError_t mixed_prepare(const Caps& cap) {
   if (!encode_fn()) return cudaErrorNotSupported;
   MX_TRY(oz_prepare());
   MX_TRY(jacobi_df_prepare());
+  MX_TRY(cholqr_prepare());
   MX_TRY(tc_attrs());
   return qr_blocked_prepare(cap.m, cap.n, cap.l);
 }

@@ -117,6 +117,7 @@ bool oz_stage_rule(const Caps& cap);
 // GEMMs.
 cudaError_t run_cholqr_bh(Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap, cudaStream_t st,
                           const OzScratch* oz, int* err);
+cudaError_t cholqr_prepare();
 cudaError_t launch_oz_digits_theta(const Dims* dims, const ProbPtr* ptrs, uint16_t* Bd, float* Bs, int m, int n,
                                    int batch, cudaStream_t st);
 // (digits_done: Q_f's digits already in Ad / As from launch_oz_digits_qf)
