@@ -114,17 +114,28 @@ __global__ void __launch_bounds__(256) k_chol_inv(Dims* dims, const ProbPtr* __r
 }
 
 // The same factorisation with the Gram's upper triangle packed in shared
-// memory (element (r, c), r <= c, at c (c + 1) / 2 + r) for l <= CS_MAXL, and
-// the inverse factor by warps: warp w solves R x = e_c for the columns
-// c = w (mod warps), bottom-up, each x_i a warp-wide dot product of row i of R
-// with the x_k already found (k > i), x in shared memory.
+// memory (element (r, c), r <= c, at c (c + 1) / 2 + r) for l <= CS_MAXL,
+// then R^-1 in place, column by column (R X = I):
+//   X[j][j] = 1 / R[j][j],  X[0:j, j] = -X[j][j] X[0:j, 0:j] R[0:j, j],
+// the leading block X[0:j, 0:j] being the columns already inverted; each
+// column's j dot products run on the threads (row r: sum over k = r .. j-1),
+// into scratch first (they read the column they replace).  The trailing
+// updates of the factorisation enumerate the packed pairs c1 <= c2 directly,
+// so every lane does work.
 enum { CS_THREADS = 256, CS_MAXL = 160 };
 
-__host__ __device__ inline size_t cs_smem_bytes(int L) {
-  return (((size_t)L * (L + 1) / 2) + (size_t)(CS_THREADS / 32) * L) * sizeof(cplx);
-}
+__host__ __device__ inline size_t cs_smem_bytes(int L) { return ((size_t)L * (L + 1) / 2 + L) * sizeof(cplx); }
 
 __device__ __forceinline__ int cs_at(int r, int c) { return c * (c + 1) / 2 + r; }
+
+// (a, b) with a <= b from the packed index e = b (b + 1) / 2 + a
+__device__ __forceinline__ void cs_pair(int e, int& a, int& b) {
+  int c = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+  if ((c + 1) * (c + 2) / 2 <= e) ++c;
+  if (c * (c + 1) / 2 > e) --c;
+  b = c;
+  a = e - c * (c + 1) / 2;
+}
 
 __global__ void __launch_bounds__(CS_THREADS) k_chol_inv_sm(Dims* dims, const ProbPtr* __restrict__ ptrs, int pass) {
   extern __shared__ __align__(16) unsigned char cs_raw[];
@@ -138,7 +149,7 @@ __global__ void __launch_bounds__(CS_THREADS) k_chol_inv_sm(Dims* dims, const Pr
   const ProbPtr P = ptrs[p];
   const int L = D.l, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = CS_THREADS / 32;
   cplx* T = reinterpret_cast<cplx*>(cs_raw);
-  cplx* X = T + (size_t)L * (L + 1) / 2;  // nw x L
+  cplx* tmp = T + (size_t)L * (L + 1) / 2;  // L
   const cplx* G = P.R;
   cplx* J = P.J;
   double dm = 0.0;
@@ -178,15 +189,16 @@ __global__ void __launch_bounds__(CS_THREADS) k_chol_inv_sm(Dims* dims, const Pr
     const double inv = s_inv;
     for (int c = j + 1 + tid; c < L; c += CS_THREADS) T[cs_at(j, c)] = cscale(T[cs_at(j, c)], inv);
     __syncthreads();
-    // G[c1][c2] -= conj(R[j][c1]) R[j][c2], j < c1 <= c2
-    const int w = L - j - 1;
-    for (int e = tid; e < w * w; e += CS_THREADS) {
-      const int c1 = j + 1 + e % w, c2 = j + 1 + e / w;
-      if (c1 > c2) continue;
-      const cplx a = T[cs_at(j, c1)], b = T[cs_at(j, c2)];
+    // G[c1][c2] -= conj(R[j][c1]) R[j][c2], j < c1 <= c2: the packed pairs of the trailing block
+    const int w = L - j - 1, j1 = j + 1;
+    for (int e = tid; e < w * (w + 1) / 2; e += CS_THREADS) {
+      int a, b;
+      cs_pair(e, a, b);
+      const int c1 = j1 + a, c2 = j1 + b;
+      const cplx x = T[cs_at(j, c1)], y = T[cs_at(j, c2)];
       cplx& g = T[cs_at(c1, c2)];
-      g.x -= a.x * b.x + a.y * b.y;
-      g.y -= a.x * b.y - a.y * b.x;
+      g.x -= x.x * y.x + x.y * y.y;
+      g.y -= x.x * y.y - x.y * y.x;
     }
     __syncthreads();
   }
@@ -196,28 +208,25 @@ __global__ void __launch_bounds__(CS_THREADS) k_chol_inv_sm(Dims* dims, const Pr
     for (int e = tid; e < L * L; e += CS_THREADS) J[e] = cmk((e / L) == (e % L) ? 1.0 : 0.0, 0.0);
     return;
   }
-  cplx* x = X + (size_t)warp * L;
-  for (int c = warp; c < L; c += nw) {
-    for (int i = c; i >= 0; --i) {
+  // R^-1 in place
+  for (int j = 0; j < L; ++j) {
+    for (int r = tid; r < j; r += CS_THREADS) {
       cplx s = cmk(0.0, 0.0);
-      for (int k = i + 1 + lane; k <= c; k += 32) {
-        const cplx r = T[cs_at(i, k)], v = x[k];
-        s.x += r.x * v.x - r.y * v.y;
-        s.y += r.x * v.y + r.y * v.x;
+      for (int k = r; k < j; ++k) {
+        const cplx x = T[cs_at(r, k)], u = T[cs_at(k, j)];
+        s.x += x.x * u.x - x.y * u.y;
+        s.y += x.x * u.y + x.y * u.x;
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
-        s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
-      }
-      if (lane == 0) {
-        const double rii = T[cs_at(i, i)].x;  // real and positive
-        x[i] = cscale(cmk((i == c ? 1.0 : 0.0) - s.x, -s.y), 1.0 / rii);
-      }
-      __syncwarp();
+      tmp[r] = s;
     }
-    for (int i = lane; i < L; i += 32) J[(size_t)c * L + i] = i <= c ? x[i] : cmk(0.0, 0.0);
-    __syncwarp();
+    __syncthreads();
+    const double dj = 1.0 / T[cs_at(j, j)].x;
+    for (int r = tid; r <= j; r += CS_THREADS) T[cs_at(r, j)] = r == j ? cmk(dj, 0.0) : cscale(tmp[r], -dj);
+    __syncthreads();
+  }
+  for (int e = tid; e < L * L; e += CS_THREADS) {
+    const int r = e % L, c = e / L;
+    J[e] = r <= c ? T[cs_at(r, c)] : cmk(0.0, 0.0);
   }
 }
 
