@@ -534,8 +534,9 @@ static int plan_handle(tebd_s* h, int n_chains, const tebd_desc_t* descs, Handle
       Caps cp = w.cap;
       cp.m = std::max(cp.m, mc); cp.n = std::max(cp.n, nc); cp.k = std::max(cp.k, kc); cp.l = std::max(cp.l, lc);
       cp.cl = std::max(cp.cl, C.cap_ext[b]); cp.cr = std::max(cp.cr, C.cap_ext[b + 2]);
+      cp.cm = std::max(cp.cm, C.cap_ext[b + 1]);
       cp.dl = std::max(cp.dl, C.d[b]); cp.dr = std::max(cp.dr, C.d[b + 1]);
-      const size_t mix = tf32 ? mixed_bytes(mixed_sizes(cp.m, cp.n, cp.k, cp.l, bf16), w.count + 1) : 0;
+      const size_t mix = tf32 ? mixed_bytes(mixed_sizes(cp.m, cp.n, cp.k, cp.l, bf16, &cp), w.count + 1) : 0;
       if (w.count > 0 && budget > 0 && acc + pbytes[par][i] + mix > budget) {
         ps.waves.push_back(w);
         ws_max = std::max(ws_max, acc);
@@ -545,6 +546,7 @@ static int plan_handle(tebd_s* h, int n_chains, const tebd_desc_t* descs, Handle
         cp = w.cap;
         cp.m = mc; cp.n = nc; cp.k = kc; cp.l = lc;
         cp.cl = C.cap_ext[b]; cp.cr = C.cap_ext[b + 2]; cp.dl = C.d[b]; cp.dr = C.d[b + 1];
+        cp.cm = C.cap_ext[b + 1];
       }
       w.cap = cp;
       acc += pbytes[par][i];
@@ -556,7 +558,7 @@ static int plan_handle(tebd_s* h, int n_chains, const tebd_desc_t* descs, Handle
     }
     if (tf32)
       for (Wave& wv : ps.waves) {
-        wv.ms = mixed_sizes(wv.cap.m, wv.cap.n, wv.cap.k, wv.cap.l, bf16);
+        wv.ms = mixed_sizes(wv.cap.m, wv.cap.n, wv.cap.k, wv.cap.l, bf16, &wv.cap);
         mixed_max = std::max(mixed_max, mixed_bytes(wv.ms, wv.count));
       }
   }
@@ -1070,10 +1072,20 @@ static cudaError_t enqueue_sweep(tebd_t h, int parity) {
     }
     if ((e = launch_plan(ptrs, dims, w.count, h->p, h->stream)) != cudaSuccess) return e;
     if (prec_mixed(h->precision)) {
-      // bonds of large local dimensions: contraction and gate as double-float GEMMs
+      // bonds of large local dimensions: contraction and gate as GEMMs, on
+      // the tensor cores from digit splits or in double-float arithmetic
       if ((e = launch_theta(dims, ptrs, w.count, w.cap, h->stream, 0, 1)) != cudaSuccess) return e;
-      if ((e = launch_theta_df(dims, ptrs, w.count, w.cap, h->stream)) != cudaSuccess) return e;
-      if ((e = launch_gate_gemm_df(dims, ptrs, w.count, w.cap, h->stream)) != cudaSuccess) return e;
+      if (oz_gate_rule(w.cap) && w.mk.dfg != 2) {
+        const MixedPtrs mp = mixed_carve(h->mixed, w.ms, w.count);
+        const OzScratch oz{mp.gad, mp.gas, mp.gbd, mp.gbs};
+        if ((e = launch_oz_stage(OZ_THETA_STAGE, dims, ptrs, w.count, w.cap, oz, h->tcerr, h->stream)) != cudaSuccess)
+          return e;
+        if ((e = launch_oz_stage(OZ_GATE_STAGE, dims, ptrs, w.count, w.cap, oz, h->tcerr, h->stream)) != cudaSuccess)
+          return e;
+      } else {
+        if ((e = launch_theta_df(dims, ptrs, w.count, w.cap, h->stream)) != cudaSuccess) return e;
+        if ((e = launch_gate_gemm_df(dims, ptrs, w.count, w.cap, h->stream)) != cudaSuccess) return e;
+      }
     } else {
       if ((e = launch_theta(dims, ptrs, w.count, w.cap, h->stream)) != cudaSuccess) return e;
       if ((e = launch_gate_gemm(dims, ptrs, w.count, w.cap, h->stream)) != cudaSuccess) return e;

@@ -85,6 +85,7 @@ struct Caps {
   int m, n, k, l;
   int cl, cr, dl, dr;
   int r;  // accuracy-check probes per round
+  int cm;  // largest middle-bond capacity (TEBD waves)
 };
 
 // --- launchers (kernels.cu) ---------------------------------------------

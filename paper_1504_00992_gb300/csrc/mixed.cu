@@ -454,7 +454,7 @@ static bool make_map(CUtensorMap* m, const void* base, int Kp, int rows, int bat
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-MixedSizes mixed_sizes(int m, int n, int k, int l, int bf16) {
+MixedSizes mixed_sizes(int m, int n, int k, int l, int bf16, const Caps* gate) {
   MixedSizes s;
   s.bf16 = bf16 ? 1 : 0;
   s.K1 = ((2 * n + TC_BK - 1) / TC_BK) * TC_BK;
@@ -480,7 +480,7 @@ MixedSizes mixed_sizes(int m, int n, int k, int l, int bf16) {
   s.thab = s.bf16 ? (size_t)n * s.K2b * 2 : 0;
   s.btb = s.bf16 ? (size_t)s.Np * (s.K1b > s.K2b ? s.K1b : s.K2b) * 2 : 0;
   {
-    const OzStageBytes ob = oz_stage_bytes(m, n, k, l);
+    const OzStageBytes ob = oz_stage_bytes(m, n, k, l, gate);
     s.gad = ob.ad;
     s.gas = ob.as;
     s.gbd = ob.bd;

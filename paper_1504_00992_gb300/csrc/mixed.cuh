@@ -51,7 +51,7 @@ struct MixedPtrs {
   float2* qscr;   // scratch of the many-CTA FP32 QR (qs bytes per instance), or null
 };
 
-MixedSizes mixed_sizes(int m, int n, int k, int l, int bf16 = 0);
+MixedSizes mixed_sizes(int m, int n, int k, int l, int bf16 = 0, const Caps* gate = nullptr);
 // The arrays of instances z0, z0 + 1, ... of a carve (every array advanced
 // by z0 instances): run_rrsvd_mixed on a sub-batch starting at instance z0.
 MixedPtrs mixed_offset(const MixedPtrs& p, const MixedSizes& s, int z0);
@@ -104,7 +104,14 @@ struct OzScratch {
 struct OzStageBytes {
   size_t ad, as, bd, bs;  // per instance
 };
-OzStageBytes oz_stage_bytes(int m, int n, int k, int l);
+// gate: the capacities of a TEBD wave whose bonds take the contraction and
+// gate GEMMs (stages OZ_THETA, OZ_GATE of launch_oz_stage), or null
+OzStageBytes oz_stage_bytes(int m, int n, int k, int l, const Caps* gate = nullptr);
+// the contraction and gate GEMMs of a wave on the tensor cores: stages
+// OZ_THETA (into the pre-gate buffers) and OZ_GATE (into theta) of
+// launch_oz_stage; the wave's bonds without a pre-gate buffer are skipped
+enum { OZ_THETA_STAGE = 102, OZ_GATE_STAGE = 103 };
+bool oz_gate_rule(const Caps& cap);
 cudaError_t launch_oz_stage(int stage, const Dims* dims, const ProbPtr* ptrs, int batch, const Caps& cap,
                             const OzScratch& sc, int* err, cudaStream_t st);
 // the size rule of MixedKnobs::dfg: the tensor-core products for bonds whose

@@ -250,7 +250,11 @@ __global__ void __launch_bounds__(256) k_oz_digits_q(const Dims* __restrict__ di
 // C = op(A) op(B) with op(A) conjugated where StageFlags says so and C
 // stored conjugated for G_V.
 // ---------------------------------------------------------------------------
-enum { OZ_PROJ = 100, OZ_GRAM = 101 };
+// OZ_THETA, OZ_GATE: the contraction and the gate of bonds whose gate is a
+// GEMM (d_l d_r >= GATE_GEMM_MIN), the mixed forms' counterparts of
+// k_cgemm_df<DgTheta> / <DgGate> (df_gemm.cu documents the operands).
+enum { OZ_PROJ = 100, OZ_GRAM = 101, OZ_THETA = 102, OZ_GATE = 103 };
+static_assert(OZ_THETA == OZ_THETA_STAGE && OZ_GATE == OZ_GATE_STAGE, "stage ids of mixed.cuh");
 
 struct OzOp {
   int M, N, K;  // rows and columns of C, depth
@@ -267,6 +271,12 @@ __device__ __forceinline__ OzOp oz_op(const Dims& D, const ProbPtr& P) {
   } else if constexpr (ST == OZ_GRAM) {
     o.M = D.l; o.N = D.l; o.K = D.m;
     o.C = P.R; o.crs = 1; o.ccs = D.l;  // E = Q_f^H Q_f - I, l x l column-major
+  } else if constexpr (ST == OZ_THETA) {
+    o.M = D.dl * D.cl; o.N = D.dr * D.cr; o.K = D.cm;  // into the pre-gate buffer (oz_store)
+    o.C = P.Cpre; o.crs = D.n; o.ccs = 1;
+  } else if constexpr (ST == OZ_GATE) {
+    o.M = D.dl * D.dr; o.N = D.cl * D.cr; o.K = D.dl * D.dr;  // into theta (oz_store)
+    o.C = const_cast<cplx*>(P.theta); o.crs = 0; o.ccs = 0;
   } else {
     const GemmOp g = gemm_of<ST>(D, P);
     o.M = g.M; o.N = g.N; o.K = g.K;
@@ -279,9 +289,88 @@ template <int ST>
 struct OzConj {
   // the projection and the Gram fold conj(Q_f) into Q_f's digits; the Gram
   // multiplies them by their own conjugate
-  static constexpr bool A = ST != OZ_PROJ && ST != OZ_GRAM && StageFlags<ST>::conjA;
+  static constexpr bool own = ST < OZ_PROJ;  // a GemmStage of stages.cuh
+  static constexpr bool A = own && StageFlags<ST>::conjA;
   static constexpr bool B = ST == OZ_GRAM;
-  static constexpr bool C = ST == OZ_PROJ || (ST != OZ_GRAM && StageFlags<ST>::conjC);
+  static constexpr bool C = ST == OZ_PROJ || (own && StageFlags<ST>::conjC);
+};
+
+// The stages that skip a bond: the contraction and gate GEMMs run only for
+// bonds with a pre-gate buffer.
+template <int ST>
+__device__ __forceinline__ bool oz_skip(const ProbPtr& P) {
+  return (ST == OZ_THETA || ST == OZ_GATE) && P.Cpre == nullptr;
+}
+
+// Element (i, j) of C into its destination.
+template <int ST>
+__device__ __forceinline__ void oz_store(const Dims& D, const ProbPtr& P, const OzOp& op, int i, int j, double re,
+                                         double im) {
+  if constexpr (ST == OZ_THETA) {
+    // lam_l[alpha] lam_r[beta] scale the contraction (rows (i, alpha), columns (j, beta))
+    op.C[(int64_t)i * D.n + j] = cscale(cmk(re, im), P.laml[i % D.cl] * P.lamr[j % D.cr]);
+  } else if constexpr (ST == OZ_GATE) {
+    const int a = i / D.dr, b = i - a * D.dr, al = j / D.cr, be = j - al * D.cr;  // rows (i, j), columns (alpha, beta)
+    op.C[(int64_t)(a * D.cl + al) * D.n + b * D.cr + be] = cmk(re, im);
+  } else {
+    if (ST == OZ_GRAM && i == j) re -= 1.0;  // E = Q_f^H Q_f - I
+    op.C[(int64_t)i * op.crs + (int64_t)j * op.ccs] = cmk(re, OzConj<ST>::C ? -im : im);
+  }
+}
+
+// Operand sources of k_oz_digits_op in their K-major views: element (row, k)
+// of side 0 (rows of op(A)) or side 1 (columns of op(B)), and whether
+// consecutive rows are adjacent in memory (else consecutive k are).
+template <int ST, int SIDE>
+struct OzSrc {  // a GemmStage: strided operand of the stage table
+  const cplx* X;
+  int64_t rs, ks;
+  int rows, K;
+  __device__ OzSrc(const Dims& D, const ProbPtr& P) {
+    const GemmOp g = gemm_of<ST>(D, P);
+    rows = SIDE == 0 ? g.M : g.N;
+    K = g.K;
+    X = SIDE == 0 ? g.A : g.B;
+    rs = SIDE == 0 ? g.ars : g.bcs;
+    ks = SIDE == 0 ? g.acs : g.brs;
+  }
+  __device__ bool rows_contig() const { return rs == 1; }
+  __device__ cplx at(int r, int k) const { return X[(int64_t)r * rs + (int64_t)k * ks]; }
+};
+template <int SIDE>
+struct OzSrc<OZ_THETA, SIDE> {  // A = Gamma_l (rows (i, alpha)), B = lam_m Gamma_r (columns (j, beta))
+  Dims D;
+  const ProbPtr* P;
+  int rows, K;
+  __device__ OzSrc(const Dims& d, const ProbPtr& p) : D(d), P(&p) {
+    rows = SIDE == 0 ? d.dl * d.cl : d.dr * d.cr;
+    K = d.cm;
+  }
+  __device__ bool rows_contig() const { return SIDE == 1; }
+  __device__ cplx at(int r, int g) const {
+    if (SIDE == 0) {
+      const int i = r / D.cl, al = r - i * D.cl;
+      return P->gl[((int64_t)i * P->cap_l + al) * P->cap_m + g];
+    }
+    const int j = r / D.cr, be = r - j * D.cr;
+    return cscale(P->gr[((int64_t)j * P->cap_m + g) * P->cap_r + be], P->lamm[g]);
+  }
+};
+template <int SIDE>
+struct OzSrc<OZ_GATE, SIDE> {  // A = the gate (rows (i, j)), B = the (i', j') x (alpha, beta) gather of C
+  Dims D;
+  const ProbPtr* P;
+  int rows, K;
+  __device__ OzSrc(const Dims& d, const ProbPtr& p) : D(d), P(&p) {
+    rows = SIDE == 0 ? d.dl * d.dr : d.cl * d.cr;
+    K = d.dl * d.dr;
+  }
+  __device__ bool rows_contig() const { return SIDE == 1; }
+  __device__ cplx at(int r, int k) const {
+    if (SIDE == 0) return P->gate[(int64_t)r * (D.dl * D.dr) + k];
+    const int ip = k / D.dr, jp = k - ip * D.dr, al = r / D.cr, be = r - al * D.cr;
+    return P->Cpre[(int64_t)(ip * D.cl + al) * D.n + jp * D.cr + be];
+  }
 };
 
 // Digits of a stage operand in its K-major view: SIDE 0 the rows i of op(A)
@@ -296,19 +385,17 @@ __global__ void __launch_bounds__(256) k_oz_digits_op(const Dims* __restrict__ d
   __shared__ uint16_t dig[2 * OZ_S][16][OZ_KB + 2];  // [reim t][row][k]
   const int z = blockIdx.z;
   const Dims D = dims[z];
-  if (!D.active) return;
-  const GemmOp g = gemm_of<ST>(D, ptrs[z]);
-  const int rows = SIDE == 0 ? g.M : g.N, K = g.K;
-  const cplx* X = SIDE == 0 ? g.A : g.B;
-  const int64_t rs = SIDE == 0 ? g.ars : g.bcs;  // between rows of the K-major view
-  const int64_t ks = SIDE == 0 ? g.acs : g.brs;  // along k
+  if (!D.active || oz_skip<ST>(ptrs[z])) return;
+  const OzSrc<ST, SIDE> src(D, ptrs[z]);
+  const int rows = src.rows, K = src.K;
+  const bool rowc = src.rows_contig();
   const int r0 = blockIdx.x * 16, k0 = blockIdx.y * OZ_KB;
   const int tid = threadIdx.x;
   for (int e = tid; e < 16 * OZ_KB; e += 256) {
     int r, k;  // consecutive threads along the unit-stride direction
-    if (rs == 1) { r = e & 15; k = e >> 4; } else { k = e & (OZ_KB - 1); r = e >> 6; }
+    if (rowc) { r = e & 15; k = e >> 4; } else { k = e & (OZ_KB - 1); r = e >> 6; }
     const int gr = r0 + r, gk = k0 + k;
-    tile[r][k] = (gr < rows && gk < K) ? X[(int64_t)gr * rs + (int64_t)gk * ks] : cmk(0.0, 0.0);
+    tile[r][k] = (gr < rows && gk < K) ? src.at(gr, gk) : cmk(0.0, 0.0);
   }
   __syncthreads();
   const int r = tid >> 4, pq = tid & 15;  // 16 threads per row, 4 k each
@@ -445,7 +532,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   const int z = blockIdx.z;
   const Dims D = dims[z];
   const int i0 = blockIdx.y * OZ_BM, j0 = blockIdx.x * OZ_BN;
-  if (!D.active) return;
+  if (!D.active || oz_skip<ST>(ptrs[z])) return;
   const OzOp op = oz_op<ST>(D, ptrs[z]);
   if (i0 >= op.M || j0 >= op.N) return;  // uniform: before any barrier or allocation
   uint8_t* smem = (uint8_t*)(((uintptr_t)oz_smem_raw + 1023) & ~(uintptr_t)1023);
@@ -615,12 +702,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
         const int j = jq + c;
-        if (j < op.N) {
-          double re = (double)hr[c] + (double)lr[c];
-          const double im = (double)hi[c] + (double)li[c];
-          if (ST == OZ_GRAM && i == j) re -= 1.0;  // E = Q_f^H Q_f - I
-          op.C[(int64_t)i * op.crs + (int64_t)j * op.ccs] = cmk(re, OzConj<ST>::C ? -im : im);
-        }
+        if (j < op.N) oz_store<ST>(D, ptrs[z], op, i, j, (double)hr[c] + (double)lr[c], (double)hi[c] + (double)li[c]);
       }
     }
   }
@@ -686,7 +768,8 @@ cudaError_t oz_prepare() {
   static int done = 0;
   if (!done) {
     const cudaError_t es[] = {oz_attr<OZ_PROJ>(), oz_attr<OZ_GRAM>(), oz_attr<G_G1>(), oz_attr<G_Q1>(), oz_attr<G_G2>(),
-                              oz_attr<G_QB>(),    oz_attr<G_X>(),  oz_attr<G_U>(),  oz_attr<G_V>()};
+                              oz_attr<G_QB>(),    oz_attr<G_X>(),  oz_attr<G_U>(),  oz_attr<G_V>(),
+                              oz_attr<OZ_THETA>(), oz_attr<OZ_GATE>()};
     for (cudaError_t e : es)
       if (e != cudaSuccess) return e;
     done = 1;
@@ -695,12 +778,14 @@ cudaError_t oz_prepare() {
 }
 
 // Capacities (rows of C, columns of C, depth) of a stage's product.
-static void oz_stage_caps(int stage, int m, int n, int k, int l, int& Mc, int& Nc, int& Kc) {
+static void oz_stage_caps(int stage, const Caps& c, int& Mc, int& Nc, int& Kc) {
   switch (stage) {
-    case G_G1: case G_G2: case G_X: Mc = l; Nc = l; Kc = n; break;
-    case G_Q1: case G_QB: Mc = n; Nc = l; Kc = l; break;
-    case G_U: Mc = m; Nc = k; Kc = l; break;
-    default: Mc = n; Nc = k; Kc = l; break;  // G_V
+    case G_G1: case G_G2: case G_X: Mc = c.l; Nc = c.l; Kc = c.n; break;
+    case G_Q1: case G_QB: Mc = c.n; Nc = c.l; Kc = c.l; break;
+    case G_U: Mc = c.m; Nc = c.k; Kc = c.l; break;
+    case OZ_THETA: Mc = c.m; Nc = c.n; Kc = c.cm; break;  // K = chi_m, at most its bond's capacity
+    case OZ_GATE: Mc = c.dl * c.dr; Nc = c.cl * c.cr; Kc = c.dl * c.dr; break;
+    default: Mc = c.n; Nc = c.k; Kc = c.l; break;  // G_V
   }
 }
 
@@ -708,18 +793,28 @@ bool oz_stage_rule(const Caps& cap) { return cap.l >= 48 && (cap.m >= 256 || cap
 
 static const int OZ_STAGE_LIST[] = {G_G1, G_Q1, G_G2, G_QB, G_X, G_U, G_V};
 
-OzStageBytes oz_stage_bytes(int m, int n, int k, int l) {
+static void oz_grow(OzStageBytes& b, int stage, const Caps& c) {
+  int Mc, Nc, Kc;
+  oz_stage_caps(stage, c, Mc, Nc, Kc);
+  b.ad = std::max(b.ad, oz_digits_bytes(Mc, Kc));
+  b.as = std::max(b.as, oz_scales_bytes(Mc, Kc));
+  b.bd = std::max(b.bd, oz_digits_bytes(Nc, Kc));
+  b.bs = std::max(b.bs, oz_scales_bytes(Nc, Kc));
+}
+
+OzStageBytes oz_stage_bytes(int m, int n, int k, int l, const Caps* gate) {
   OzStageBytes b{0, 0, 0, 0};
-  for (int stage : OZ_STAGE_LIST) {
-    int Mc, Nc, Kc;
-    oz_stage_caps(stage, m, n, k, l, Mc, Nc, Kc);
-    b.ad = std::max(b.ad, oz_digits_bytes(Mc, Kc));
-    b.as = std::max(b.as, oz_scales_bytes(Mc, Kc));
-    b.bd = std::max(b.bd, oz_digits_bytes(Nc, Kc));
-    b.bs = std::max(b.bs, oz_scales_bytes(Nc, Kc));
+  Caps c{};
+  c.m = m; c.n = n; c.k = k; c.l = l;
+  for (int stage : OZ_STAGE_LIST) oz_grow(b, stage, c);
+  if (gate && gate->dl * gate->dr >= GATE_GEMM_MIN) {
+    oz_grow(b, OZ_THETA, *gate);
+    oz_grow(b, OZ_GATE, *gate);
   }
   return b;
 }
+
+bool oz_gate_rule(const Caps& cap) { return cap.dl * cap.dr >= GATE_GEMM_MIN; }
 
 template <int ST>
 static cudaError_t oz_stage_run(const Dims* dims, const ProbPtr* ptrs, int batch, int Mc, int Nc, int Kc,
@@ -748,7 +843,11 @@ static cudaError_t oz_stage_run(const Dims* dims, const ProbPtr* ptrs, int batch
   oa.err = err;
   oa.poll_limit = 1u << 24;
   oa.stall = 0;
-  ProfScope ps(ST == G_U || ST == G_V ? "k_oz_gemm[uv]" : "k_oz_gemm[cholqr]", st);
+  ProfScope ps(ST == G_U || ST == G_V ? "k_oz_gemm[uv]"
+               : ST == OZ_THETA          ? "k_oz_gemm[theta]"
+               : ST == OZ_GATE           ? "k_oz_gemm[gate]"
+                                         : "k_oz_gemm[cholqr]",
+               st);
   k_oz_gemm<ST><<<dim3((Nc + OZ_BN - 1) / OZ_BN, (Mc + OZ_BM - 1) / OZ_BM, batch), OZ_THREADS, oz_smem_bytes(), st>>>(
       ta, tb, dims, ptrs, oa);
   return cudaGetLastError();
@@ -759,8 +858,14 @@ cudaError_t launch_oz_stage(int stage, const Dims* dims, const ProbPtr* ptrs, in
   const cudaError_t e = oz_prepare();
   if (e != cudaSuccess) return e;
   int Mc, Nc, Kc;
-  oz_stage_caps(stage, cap.m, cap.n, cap.k, cap.l, Mc, Nc, Kc);
+  oz_stage_caps(stage, cap, Mc, Nc, Kc);
   switch (stage) {
+    case OZ_THETA:
+      if (!oz_gate_rule(cap)) return cudaSuccess;
+      return oz_stage_run<OZ_THETA>(dims, ptrs, batch, Mc, Nc, Kc, sc, err, st);
+    case OZ_GATE:
+      if (!oz_gate_rule(cap)) return cudaSuccess;
+      return oz_stage_run<OZ_GATE>(dims, ptrs, batch, Mc, Nc, Kc, sc, err, st);
     case G_G1: return oz_stage_run<G_G1>(dims, ptrs, batch, Mc, Nc, Kc, sc, err, st);
     case G_Q1: return oz_stage_run<G_Q1>(dims, ptrs, batch, Mc, Nc, Kc, sc, err, st);
     case G_G2: return oz_stage_run<G_G2>(dims, ptrs, batch, Mc, Nc, Kc, sc, err, st);
