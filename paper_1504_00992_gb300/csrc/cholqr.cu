@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include "dfsplit.cuh"
 #include "internal.cuh"
 #include "mixed.cuh"
 #include "profiler.cuh"
@@ -113,15 +114,17 @@ __global__ void __launch_bounds__(256) k_chol_inv(Dims* dims, const ProbPtr* __r
   }
 }
 
-// The same factorisation with the Gram's upper triangle packed in shared
-// memory (element (r, c), r <= c, at c (c + 1) / 2 + r) for l <= CS_MAXL,
-// then R^-1 in place, column by column (R X = I):
+// The same factorisation in double-float arithmetic (FP32 pairs, 2^-48;
+// the FP32 pipe runs 64x the FP64 one) with the Gram's upper triangle packed
+// in shared memory (element (r, c), r <= c, at c (c + 1) / 2 + r) for
+// l <= CS_MAXL, then R^-1 in place, column by column (R X = I):
 //   X[j][j] = 1 / R[j][j],  X[0:j, j] = -X[j][j] X[0:j, 0:j] R[0:j, j],
 // the leading block X[0:j, 0:j] being the columns already inverted; each
 // column's j dot products run on the threads (row r: sum over k = r .. j-1),
 // into scratch first (they read the column they replace).  The trailing
 // updates of the factorisation enumerate the packed pairs c1 <= c2 directly,
-// so every lane does work.
+// so every lane does work.  G is scaled by a power of four first, so that its
+// largest diagonal entry lies in [0.5, 4), and R^-1 scaled back.
 enum { CS_THREADS = 256, CS_MAXL = 160 };
 
 __host__ __device__ inline size_t cs_smem_bytes(int L) { return ((size_t)L * (L + 1) / 2 + L) * sizeof(cplx); }
@@ -137,10 +140,18 @@ __device__ __forceinline__ void cs_pair(int e, int& a, int& b) {
   a = e - c * (c + 1) / 2;
 }
 
+// Complex double-float entry: (Re hi, Re lo, Im hi, Im lo).
+__device__ __forceinline__ float4 cs_split(cplx v) {
+  float4 d;
+  split_bits(v.x, d.x, d.y);
+  split_bits(v.y, d.z, d.w);
+  return d;
+}
+
 __global__ void __launch_bounds__(CS_THREADS) k_chol_inv_sm(Dims* dims, const ProbPtr* __restrict__ ptrs, int pass) {
   extern __shared__ __align__(16) unsigned char cs_raw[];
   __shared__ double red[32];
-  __shared__ double s_inv;
+  __shared__ float2 s_inv;
   __shared__ int s_fail;
   const int p = blockIdx.x;
   const Dims D = dims[p];
@@ -148,19 +159,14 @@ __global__ void __launch_bounds__(CS_THREADS) k_chol_inv_sm(Dims* dims, const Pr
   if (pass == 1 && D.qflag) return;
   const ProbPtr P = ptrs[p];
   const int L = D.l, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = CS_THREADS / 32;
-  cplx* T = reinterpret_cast<cplx*>(cs_raw);
-  cplx* tmp = T + (size_t)L * (L + 1) / 2;  // L
+  float4* T = reinterpret_cast<float4*>(cs_raw);
+  float4* tmp = T + (size_t)L * (L + 1) / 2;  // L
   const cplx* G = P.R;
   cplx* J = P.J;
+  // the largest diagonal entry, then G scaled by 2^-2s (exact) to bring it
+  // into [0.5, 4): FP32's range holds the factor, R^-1 is scaled back by 2^s
   double dm = 0.0;
-  for (int e = tid; e < L * L; e += CS_THREADS) {
-    const int r = e % L, c = e / L;
-    if (r <= c) {
-      const cplx v = G[(size_t)c * L + r];
-      T[cs_at(r, c)] = v;
-      if (r == c) dm = fmax(dm, v.x);
-    }
-  }
+  for (int c = tid; c < L; c += CS_THREADS) dm = fmax(dm, G[(size_t)c * L + c].x);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
   if (lane == 0) red[warp] = dm;
@@ -173,21 +179,37 @@ __global__ void __launch_bounds__(CS_THREADS) k_chol_inv_sm(Dims* dims, const Pr
   }
   __syncthreads();
   dm = red[0];
+  int ex = 0;
+  if (!s_fail) (void)frexp(dm, &ex);  // dm = f 2^ex, f in [0.5, 1)
+  const int sh = ex >> 1;             // scale G by 2^-2 sh
+  const double gsc = ldexp(1.0, -2 * sh);
+  for (int e = tid; e < L * L; e += CS_THREADS) {
+    const int r = e % L, c = e / L;
+    if (r <= c) T[cs_at(r, c)] = cs_split(cscale(G[(size_t)c * L + r], gsc));
+  }
+  const float piv = (float)(CQ_PIVOT * dm * gsc);
+  __syncthreads();
   for (int j = 0; j < L && !s_fail; ++j) {
     if (tid == 0) {
-      const double d = T[cs_at(j, j)].x;
-      if (!(d > CQ_PIVOT * dm) || !isfinite(d)) {
+      const float4 dd = T[cs_at(j, j)];
+      const dfl d{dd.x, dd.y};
+      if (!(d.h > piv) || !isfinite(d.h)) {
         s_fail = 1;
       } else {
-        const double r = sqrt(d);
-        T[cs_at(j, j)] = cmk(r, 0.0);
-        s_inv = 1.0 / r;
+        const dfl r = dsqrt(d);
+        const dfl inv = drecip(r);
+        T[cs_at(j, j)] = make_float4(r.h, r.l, 0.f, 0.f);
+        s_inv = make_float2(inv.h, inv.l);
       }
     }
     __syncthreads();
     if (s_fail) break;
-    const double inv = s_inv;
-    for (int c = j + 1 + tid; c < L; c += CS_THREADS) T[cs_at(j, c)] = cscale(T[cs_at(j, c)], inv);
+    const dfl inv{s_inv.x, s_inv.y};
+    for (int c = j + 1 + tid; c < L; c += CS_THREADS) {
+      const float4 v = T[cs_at(j, c)];
+      const dfl re = dmul(dfl{v.x, v.y}, inv), im = dmul(dfl{v.z, v.w}, inv);
+      T[cs_at(j, c)] = make_float4(re.h, re.l, im.h, im.l);
+    }
     __syncthreads();
     // G[c1][c2] -= conj(R[j][c1]) R[j][c2], j < c1 <= c2: the packed pairs of the trailing block
     const int w = L - j - 1, j1 = j + 1;
@@ -195,10 +217,17 @@ __global__ void __launch_bounds__(CS_THREADS) k_chol_inv_sm(Dims* dims, const Pr
       int a, b;
       cs_pair(e, a, b);
       const int c1 = j1 + a, c2 = j1 + b;
-      const cplx x = T[cs_at(j, c1)], y = T[cs_at(j, c2)];
-      cplx& g = T[cs_at(c1, c2)];
-      g.x -= x.x * y.x + x.y * y.y;
-      g.y -= x.x * y.y - x.y * y.x;
+      const float4 x = T[cs_at(j, c1)], y = T[cs_at(j, c2)];
+      float4& g = T[cs_at(c1, c2)];
+      // Re -= xr yr + xi yi, Im -= xr yi - xi yr
+      float rh = g.x, rl = g.y, ih = g.z, il = g.w;
+      dfx_dd(rh, rl, -x.x, -x.y, y.x, y.y);
+      dfx_dd(rh, rl, -x.z, -x.w, y.z, y.w);
+      dfx_dd(ih, il, -x.x, -x.y, y.z, y.w);
+      dfx_dd(ih, il, x.z, x.w, y.x, y.y);
+      fast2(rh, rl);
+      fast2(ih, il);
+      g = make_float4(rh, rl, ih, il);
     }
     __syncthreads();
   }
@@ -211,22 +240,41 @@ __global__ void __launch_bounds__(CS_THREADS) k_chol_inv_sm(Dims* dims, const Pr
   // R^-1 in place
   for (int j = 0; j < L; ++j) {
     for (int r = tid; r < j; r += CS_THREADS) {
-      cplx s = cmk(0.0, 0.0);
+      float sh_ = 0.f, sl = 0.f, th = 0.f, tl = 0.f;  // Re, Im of sum_k X[r][k] R[k][j]
       for (int k = r; k < j; ++k) {
-        const cplx x = T[cs_at(r, k)], u = T[cs_at(k, j)];
-        s.x += x.x * u.x - x.y * u.y;
-        s.y += x.x * u.y + x.y * u.x;
+        const float4 x = T[cs_at(r, k)], u = T[cs_at(k, j)];
+        dfx_dd(sh_, sl, x.x, x.y, u.x, u.y);
+        dfx_dd(sh_, sl, -x.z, -x.w, u.z, u.w);
+        dfx_dd(th, tl, x.x, x.y, u.z, u.w);
+        dfx_dd(th, tl, x.z, x.w, u.x, u.y);
       }
-      tmp[r] = s;
+      fast2(sh_, sl);
+      fast2(th, tl);
+      tmp[r] = make_float4(sh_, sl, th, tl);
     }
     __syncthreads();
-    const double dj = 1.0 / T[cs_at(j, j)].x;
-    for (int r = tid; r <= j; r += CS_THREADS) T[cs_at(r, j)] = r == j ? cmk(dj, 0.0) : cscale(tmp[r], -dj);
+    const float4 djj = T[cs_at(j, j)];
+    const dfl dj = drecip(dfl{djj.x, djj.y});
+    for (int r = tid; r <= j; r += CS_THREADS) {
+      if (r == j) {
+        T[cs_at(j, j)] = make_float4(dj.h, dj.l, 0.f, 0.f);
+      } else {
+        const float4 v = tmp[r];
+        const dfl re = dmul(dfl{v.x, v.y}, dneg(dj)), im = dmul(dfl{v.z, v.w}, dneg(dj));
+        T[cs_at(r, j)] = make_float4(re.h, re.l, im.h, im.l);
+      }
+    }
     __syncthreads();
   }
+  const double back = ldexp(1.0, -sh);  // R^-1 of the unscaled G = 2^-s R'^-1
   for (int e = tid; e < L * L; e += CS_THREADS) {
     const int r = e % L, c = e / L;
-    J[e] = r <= c ? T[cs_at(r, c)] : cmk(0.0, 0.0);
+    cplx v = cmk(0.0, 0.0);
+    if (r <= c) {
+      const float4 t = T[cs_at(r, c)];
+      v = cmk(((double)t.x + (double)t.y) * back, ((double)t.z + (double)t.w) * back);
+    }
+    J[e] = v;
   }
 }
 

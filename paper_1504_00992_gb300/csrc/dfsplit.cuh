@@ -67,4 +67,49 @@ __device__ __forceinline__ void fast2(float& h, float& lo) {
   h = s;
 }
 
+// Double-float scalars (value h + l, |l| <= ulp(h) / 2) with FP32
+// arithmetic only: normalised sums and products by TwoSum and FMA splitting,
+// square root and reciprocal as one Newton step from the correctly rounded
+// FP32 operation (relative error ~2^-47).
+struct dfl {
+  float h, l;
+};
+
+__device__ __forceinline__ dfl dnorm(float s, float e) {
+  const float h = s + e;
+  return {h, e - (h - s)};
+}
+__device__ __forceinline__ dfl dadd(dfl a, dfl b) {
+  float s, e;
+  two_sum(a.h, b.h, s, e);
+  return dnorm(s, e + (a.l + b.l));
+}
+__device__ __forceinline__ dfl dmul(dfl a, dfl b) {
+  const float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  return dnorm(p, e);
+}
+__device__ __forceinline__ dfl dmulf(dfl a, float b) {  // a * b, b a single float
+  const float p = a.h * b;
+  const float e = fmaf(a.h, b, -p);
+  return dnorm(p, fmaf(a.l, b, e));
+}
+__device__ __forceinline__ dfl dneg(dfl a) { return {-a.h, -a.l}; }
+// sqrt(a), a > 0: the correctly rounded FP32 root y and one Newton step,
+// y + (a - y^2) / (2 y), the residual by FMA
+__device__ __forceinline__ dfl dsqrt(dfl a) {
+  const float y = sqrtf(a.h);
+  const float r = fmaf(-y, y, a.h) + a.l;
+  return dnorm(y, r / (2.0f * y));
+}
+// 1 / b: the correctly rounded FP32 reciprocal y and one Newton step,
+// y + y (1 - b y)
+__device__ __forceinline__ dfl drecip(dfl b) {
+  const float y = 1.0f / b.h;
+  const float r = fmaf(-b.h, y, 1.0f) - b.l * y;
+  return dnorm(y, y * r);
+}
+
 }  // namespace tg
