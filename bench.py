@@ -658,17 +658,20 @@ def run_tebd_spin_boson(B, I, torch, steps=1, warm=1, size=(100, 32, 4, 256, 64)
     whose local dimension falls from 32 to 4, couplings 1/(1+n), per-bond
     caps falling from 256 to 64, from a canonical random MPS at the caps
     (seed 0), dt = 0.05, p = 10, q = 2; the TF32 form (TF32 sketches with FP32
-    QRs, FP64-accurate projection, FP64 small SVD; the configuration's
-    precision) or the plain FP64 form, all bonds of a parity per launch
-    sequence replayed from CUDA graphs, 40 GB wave budget.  One second-order
-    step = even, odd, even sweep."""
+    QRs, FP64-accurate tail; the configuration's precision) or the plain FP64
+    form, all bonds of a parity per launch sequence replayed from CUDA graphs,
+    40 GB wave budget, launch choices autotuned per wave shape at creation.
+    One second-order step = even, odd, even sweep."""
     dims, caps = I.spin_boson_sizes(*size)
     g0, lam0 = I.random_canonical_mps(dims, caps, 0)
     hs = I.spin_boson_bond_terms(dims)
     dt, p, q = 0.05, 10, 2
     code = B.TEBD_PREC_TF32 if precision == "tf32" else B.TEBD_PREC_FP64
+    t_tune = time.perf_counter()
     sim = B.Tebd(len(dims), 2, 0, p, q, 3, d_site=dims, chi_bond=caps, precision=code, use_graph=1,
-                 workspace_budget=40 << 30)
+                 workspace_budget=40 << 30, autotune=1)
+    t_tune = time.perf_counter() - t_tune
+    table = sim.tuning_table()
     sim.set_mps(g0, lam0)
     sim.set_gates(0, I.trotter_gates(hs, dt / 2))
     sim.set_gates(1, I.trotter_gates(hs, dt))
@@ -687,9 +690,13 @@ def run_tebd_spin_boson(B, I, torch, steps=1, warm=1, size=(100, 32, 4, 256, 64)
     return {"value": upd / el, "unit": "bond updates/s", "seconds_per_step": el / steps, "steps_timed": steps,
             "precision": "tf32 (mixed form)" if precision == "tf32" else "fp64 (plain)",
             "discarded_weight": float(w[0]), "workspace": info,
+            "creation_and_tuning_seconds": t_tune,
+            "tuning": [{"parity": par, "bonds": wv["bonds"], "m": wv["m"], "n": wv["n"], "l": wv["l"],
+                        "mixed": wv["mixed"], "fused": wv["fused"], "tune_ms": wv["tune_ms"]}
+                       for par in (0, 1) for wv in table[par]],
             "workload": "spin-boson chain: spin + %d bosons, d %d -> %d, chi caps %d -> %d, dt=0.05, p=10, q=2, "
-                        "canonical random MPS at the caps (seed 0); graphs, 40 GB wave budget, after %d warm-up "
-                        "step(s)" % (tuple(size) + (warm,))}
+                        "canonical random MPS at the caps (seed 0); graphs, 40 GB wave budget, autotuned, after %d "
+                        "warm-up step(s)" % (tuple(size) + (warm,))}
 
 
 def run_tebd_gradient(B, I, torch):
