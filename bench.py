@@ -391,7 +391,7 @@ FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.07
 
 
 def measured_peaks():
-    """The driver's measured GB300 peaks (HBM GB/s, dense BF16 TFLOP/s)."""
+    """Measured GB300 peaks (HBM GB/s, dense BF16 TFLOP/s) from MEASURED_PEAKS.json, if present."""
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
