@@ -101,15 +101,21 @@ def test_coupling_gradient_matches_finite_differences(lib):
 def test_ising_n40_gradient_full_size(lib):
     """The differentiable workload at full size: transverse-field Ising chain
     N=40, chi=64, dt=0.02, 50 steps, d<sigma^z_19>/dJ_b with J ~ U[0.5, 1.5]
-    (seed 0), against central differences (h = 1e-6) of the GPU forward on
+    (seed 0), against the oracle's central differences (h = 1e-6) stored for
+    every coupling, and against central differences of the GPU forward on
     couplings near and far from the site."""
     import torch
     from paper_1504_00992_gb300.autograd import tfim_observable
+    from tests.test_oracle_c4_golden import load_c4_golden
     N, hf, dt, steps, chi, p, q, seed, site = 40, 1.0, 0.02, 50, 64, 10, 2, 0, 19
     J0 = np.random.default_rng(0).uniform(0.5, 1.5, N - 1)
     J = torch.tensor(J0, requires_grad=True)
-    tfim_observable(J, N, hf, dt, steps, chi, p, q, seed, site).backward()
+    L = tfim_observable(J, N, hf, dt, steps, chi, p, q, seed, site)
+    L.backward()
     g = J.grad.numpy()
+    L_orc, fd_orc = load_c4_golden()
+    assert abs(L.item() - L_orc) <= 1e-10
+    assert np.abs(g - fd_orc).max() <= 1e-7
     for b in (0, 17, 18, 19, 20, 38):
         Jp, Jm = J0.copy(), J0.copy()
         Jp[b] += 1e-6
