@@ -463,8 +463,13 @@ def roofline(res, batch):
     tp = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tp):
         rec = json.load(open(tp)).get(dom)
-        if rec and rec.get("src_sha256_16") == _src_hash(srcfile):
-            traffic = rec["dram_bytes_per_instance"] * batch   # counters taken on this exact kernel source
+        # counters taken on this exact kernel source; a capture at another batch
+        # only where the record states that the traffic grows in proportion
+        # (per-instance data above L2 either way), not where the batch decides
+        # what stays in L2
+        if rec and rec.get("src_sha256_16") == _src_hash(srcfile) and (
+                rec.get("captured_batch") == batch or rec.get("proportional", False)):
+            traffic = rec["dram_bytes_per_instance"] * batch
     out = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
            "frac": achieved / peak, "traffic": traffic, "peak_source": psrc}
     # every kernel class of the step against its own ceiling (same units)

@@ -38,6 +38,23 @@ def test_traffic_only_from_a_matching_capture():
         assert r["traffic"] is None
 
 
+def test_fp32_qr_traffic_only_at_its_capture_batch():
+    """The FP32 QR's DRAM traffic depends on how many instances share L2, so
+    its capture (one launch at batch 152) is reported at that batch only."""
+    rec = json.load(open(os.path.join(bench.ROOT, "profiles", "traffic.json")))["k_qr_f32"]
+    assert rec["captured_batch"] == 152 and rec["proportional"] is False
+    r152 = bench.roofline(_res({"k_qr_f32": (24.5, 5)}), 152)
+    r4 = bench.roofline(_res({"k_qr_f32": (18.7, 5)}), 4)
+    assert r4["traffic"] is None
+    if rec["src_sha256_16"] == bench._src_hash("qr_blocked.cu"):
+        assert r152["traffic"] == rec["dram_bytes_per_instance"] * 152
+        # far above the algorithmic bytes (Y read, Q written: 2 x 2000 x 120 x 8 B per instance): the
+        # trailing columns of every panel come from DRAM once the batch's working set exceeds L2
+        assert rec["dram_bytes_per_instance"] > 10 * 2 * bench.M * 120 * 8
+    else:
+        assert r152["traffic"] is None
+
+
 def test_unknown_dominant_kernel_has_no_roofline():
     assert bench.roofline(_res({"k_unlisted": (40.0, 1)}), 152) is None
 
