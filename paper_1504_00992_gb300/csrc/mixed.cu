@@ -750,7 +750,7 @@ cudaError_t run_rrsvd_mixed(const Dims* dims, const ProbPtr* ptrs, int batch, co
   // projection B^H = A^H Q both take them
   MX_TRY(launch_oz_digits_qf(dims, mp.Qf, mp.ad, mp.asc, m, l, batch, st));
   MX_TRY(launch_oz_gram(dims, ptrs, mp.ad, mp.asc, m, l, batch, err, st));
-  MX_TRY(launch_reorth(mp.Qf, mp.Df, dims, ptrs, m, l, batch, status, st, true));
+  MX_TRY(launch_reorth(mp.Qf, mp.Df, dims, ptrs, m, l, batch, status, st));
   MX_TRY(launch_proj_oz(dims, ptrs, mp.Qf, mp.Df, mp.ad, mp.asc, mp.bd, mp.bsc, m, n, l, batch, err, st,
                         true));  // B^H = A^H Q
   // QR of B^H: Cholesky QR where the one-CTA Householder would run (it falls

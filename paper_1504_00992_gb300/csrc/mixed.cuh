@@ -76,11 +76,11 @@ size_t qr_multi_f32_scratch(int M, int L);
 cudaError_t launch_qr_multi_f32(float2* A, float2* Q, float2* scr, size_t stride, int M, int L, int batch,
                                 cudaStream_t st, const Dims* dims = nullptr, int use_n = 0);
 // Q_f (FP32, M x L) -> ptrs[z].Q (FP64) orthonormal to ~1e-13, spanning
-// range(Q_f); uses ptrs[z].R as scratch; usable when reorth_fits(M, L).
-// gram_done: E = Q_f^H Q_f - I is already in ptrs[z].R (launch_oz_gram).
+// range(Q_f), from E = Q_f^H Q_f - I already in ptrs[z].R (launch_oz_gram);
+// usable when reorth_fits(M, L).
 bool reorth_fits(int M, int L);
 cudaError_t launch_reorth(const float2* Qf, float2* Dbuf, const Dims* dims, const ProbPtr* ptrs, int M, int L,
-                          int batch, int* status, cudaStream_t st, bool gram_done = false);
+                          int batch, int* status, cudaStream_t st);
 // B^H <- B^H (I + D) in place on ptrs[z].Yt (qr_blocked.cu).
 cudaError_t launch_fold_bh(const float2* Dbuf, const Dims* dims, const ProbPtr* ptrs, int n, int l, int batch,
                            cudaStream_t st);

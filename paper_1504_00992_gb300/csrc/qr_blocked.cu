@@ -13,8 +13,8 @@
 // backwards with Q <- Q - V T (V^H Q).  One CTA per instance.
 //
 // Re-orthonormalisation: the FP32 Q_f has ||Q_f^H Q_f - I|| ~ 1e-6.  With
-// E = Q_f^H Q_f - I formed exactly enough in double-float arithmetic (FP32
-// products split error-free by FMA, TwoSum accumulation), the symmetric
+// E = Q_f^H Q_f - I formed FP64-accurately (the digit-pair tensor-core Gram of
+// oz_proj.cu, from exact BF16 digit splits of Q_f), the symmetric
 // (Loewdin) orthonormalisation Q = Q_f (I + E)^{-1/2} is evaluated from the
 // binomial series (I + E)^{-1/2} = I - E/2 + 3 E^2 / 8 - ..., whose first
 // dropped term is of order ||E||^3 ~ 1e-18.  Q spans range(Q_f) and is
@@ -496,108 +496,6 @@ cudaError_t launch_qr_blk_f32(float2* A, float2* Q, int M, int L, int batch, cud
 // ---------------------------------------------------------------------------
 // Re-orthonormalisation of an FP32 Q_f (M x L column-major per instance).
 // ---------------------------------------------------------------------------
-// double-float accumulation of exact FP32 products: acc += x * y (TwoSum on
-// the high part, rounding errors gathered in the low part)
-__device__ __forceinline__ void df_acc(float& h, float& lo, float x, float y) {
-  const float ph = x * y;
-  const float pe = fmaf(x, y, -ph);
-  const float t = h + ph;
-  const float zz = t - h;
-  const float e = (h - (t - zz)) + (ph - zz);
-  h = t;
-  lo += e + pe;
-}
-
-// (H, Lo) += (h, lo), renormalised (Dekker's add): keeps the low word below
-// one ulp of the high word, so that the error stays at the u^2 level over
-// long sums instead of growing like K u^2.
-__device__ __forceinline__ void df_merge(float& H, float& Lo, float h, float lo) {
-  const float s = H + h;
-  const float v = s - H;
-  float e = (H - (s - v)) + (h - v);
-  e += Lo + lo;
-  H = s + e;
-  Lo = e - (H - s);
-}
-
-// E = Q_f^H Q_f - I on the tiles on and above the diagonal (32 x 32 tiles,
-// 2 x 2 outputs per thread), written to ptrs[z].R (L x L column-major, FP64).
-// Each 16-deep slice of the sum is accumulated afresh and merged into the
-// running double-float sum.
-// Q_f at capacity Mc x Lc per instance; the instance's own sizes come from
-// dims (rows past D.m are zero, columns past D.l are not part of its basis).
-__global__ void __launch_bounds__(256) k_gram_df(const float2* __restrict__ Qf, const Dims* __restrict__ dims,
-                                                 const ProbPtr* __restrict__ ptrs, int Mc, int Lc) {
-  constexpr int T = 32, TK = 16;
-  __shared__ float2 As[TK][T + 1];
-  __shared__ float2 Bs[TK][T + 1];
-  const int z = blockIdx.y;
-  const Dims D = dims[z];
-  if (!D.active) return;
-  const int ntc = (Lc + T - 1) / T;
-  // blockIdx.x enumerates the tile pairs (ti <= tj) of the capacity
-  int ti = 0, rem = blockIdx.x;
-  while (rem >= ntc - ti) { rem -= ntc - ti; ++ti; }
-  const int tj = ti + rem;
-  const int L = D.l, M = D.m;
-  if (ti * T >= L || tj * T >= L) return;
-  const float2* q = Qf + (size_t)z * Mc * Lc;
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  float RH[2][2], RL[2][2], IH[2][2], IL[2][2];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 2; ++j) RH[i][j] = RL[i][j] = IH[i][j] = IL[i][j] = 0.f;
-  for (int k0 = 0; k0 < M; k0 += TK) {
-    for (int e = tid; e < T * TK; e += 256) {
-      const int kk = e % TK, c = e / TK;
-      const int gk = k0 + kk;
-      const int ca = ti * T + c, cb = tj * T + c;
-      As[kk][c] = (gk < M && ca < L) ? q[(size_t)ca * Mc + gk] : make_float2(0.f, 0.f);
-      Bs[kk][c] = (gk < M && cb < L) ? q[(size_t)cb * Mc + gk] : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    float rh[2][2], rl[2][2], ih[2][2], il[2][2];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-      for (int j = 0; j < 2; ++j) rh[i][j] = rl[i][j] = ih[i][j] = il[i][j] = 0.f;
-#pragma unroll 4
-    for (int kk = 0; kk < TK; ++kk) {
-      float2 a[2], b[2];
-      a[0] = As[kk][ty]; a[1] = As[kk][ty + 16];
-      b[0] = Bs[kk][tx]; b[1] = Bs[kk][tx + 16];
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {  // conj(a) b
-          df_acc(rh[i][j], rl[i][j], a[i].x, b[j].x);
-          df_acc(rh[i][j], rl[i][j], a[i].y, b[j].y);
-          df_acc(ih[i][j], il[i][j], a[i].x, b[j].y);
-          df_acc(ih[i][j], il[i][j], -a[i].y, b[j].x);
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        df_merge(RH[i][j], RL[i][j], rh[i][j], rl[i][j]);
-        df_merge(IH[i][j], IL[i][j], ih[i][j], il[i][j]);
-      }
-    __syncthreads();
-  }
-  cplx* E = ptrs[z].R;
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int r = ti * T + ty + 16 * i, c = tj * T + tx + 16 * j;
-      if (r < L && c < L && r <= c)
-        E[(size_t)c * L + r] = cmk(((double)RH[i][j] - (r == c ? 1.0 : 0.0)) + (double)RL[i][j],
-                                   (double)IH[i][j] + (double)IL[i][j]);
-    }
-}
-
 // D = -E/2 + 3 E^2 / 8 (E Hermitian, from its upper triangle), FP32, one CTA
 // per instance; raises status bit 4 when E is not small or not finite.
 __global__ void __launch_bounds__(512) k_lowdin(const Dims* __restrict__ dims, const ProbPtr* __restrict__ ptrs,
@@ -938,14 +836,8 @@ cudaError_t qr_blocked_prepare(int M, int N, int L) {
 bool reorth_fits(int M, int L) { return M >= L && L <= QF_MAXL_BIG; }
 
 cudaError_t launch_reorth(const float2* Qf, float2* Dbuf, const Dims* dims, const ProbPtr* ptrs, int M, int L,
-                          int batch, int* status, cudaStream_t st, bool gram_done) {
+                          int batch, int* status, cudaStream_t st) {
   const int nt = (L + 31) / 32;
-  if (!gram_done) {
-    ProfScope ps("k_gram_df", st);
-    k_gram_df<<<dim3(nt * (nt + 1) / 2, batch), 256, 0, st>>>(Qf, dims, ptrs, M, L);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
   if (L > QF_MAXL) {
     {
       ProfScope ps("k_lowdin", st);
