@@ -104,3 +104,50 @@ def test_missing_renormalisation_is_caught(monkeypatch):
 def test_wrong_rebuild_division_is_caught(monkeypatch):
     monkeypatch.setattr(T, "_safe_inv", lambda lam: np.ones_like(lam))
     assert _tebd_vs_statevector_error() > 1e-6
+
+
+def _eckart_young_gap():
+    """|A - A_k|_F of the oracle's exact truncation against the closed form
+    sqrt(sum_{i>k} sigma_i^2) of a matrix built with known singular values."""
+    n, k = 60, 12
+    sig = I.exp_spectrum(n, 5.0)
+    A = I.synthetic_theta(n, n, sig, seed=4)
+    Uk, sk, Vhk, _ = R.exact_truncate(A, k)
+    return abs(np.linalg.norm(A - (Uk * sk) @ Vhk) - np.sqrt(np.sum(sig[k:] ** 2)))
+
+
+def _weight_vs_kept_norm():
+    """1 - w against the squared norm of the kept part, formed directly
+    (Eq. defdiscweigt for a normalised theta)."""
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((30, 24)) + 1j * rng.standard_normal((30, 24))
+    A /= np.linalg.norm(A)
+    Uk, sk, Vhk, w = R.exact_truncate(A, 7)
+    return abs((1.0 - w) - np.linalg.norm((Uk * sk) @ Vhk) ** 2)
+
+
+def test_unmutated_truncation_baselines():
+    assert _eckart_young_gap() < 1e-13
+    assert _weight_vs_kept_norm() < 1e-14
+
+
+def test_projection_without_conjugate_is_caught(monkeypatch):
+    def bad_rrsvd(A, Omega, q):
+        Q = R.range_finder(A, Omega, q)
+        Ut, s, Vh = np.linalg.svd(Q.T @ A, full_matrices=False)   # Q^T instead of Q^H
+        return Q @ Ut, s, Vh
+    monkeypatch.setattr(R, "rrsvd", bad_rrsvd)
+    assert _exp_spectrum_error() > 1e-8
+
+
+def test_kept_rank_off_by_one_is_caught(monkeypatch):
+    orig = R.kept_rank
+    monkeypatch.setattr(R, "kept_rank", lambda s, k, cutoff: max(orig(s, k, cutoff) - 1, 0))
+    assert _eckart_young_gap() > 1e-6
+
+
+def test_weight_from_unsquared_values_is_caught(monkeypatch):
+    def bad_weight(s_kept, normF2):
+        return 1.0 - float(np.sum(np.asarray(s_kept))) / normF2
+    monkeypatch.setattr(R, "discarded_weight", bad_weight)
+    assert _weight_vs_kept_norm() > 1e-3
