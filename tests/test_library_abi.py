@@ -40,6 +40,18 @@ def test_argument_errors_need_no_device(libpath):
     assert L.tebd_create(4, 2, 4, 2, 1, 0, None) == binding.TEBD_EINVAL
     assert L.rrsvd_plan_create(0, 4, 2, 1, 1, 1, 0, 0, ctypes.byref(h)) == binding.TEBD_EINVAL
     assert L.rrsvd_plan_create(4, 4, 2, 1, 1, 1, 7, 0, ctypes.byref(h)) == binding.TEBD_ENOTIMPL
+    # an empty batch, negative oversampling or power rounds
+    assert L.rrsvd_plan_create(8, 8, 2, 1, 1, 0, 0, 0, ctypes.byref(h)) == binding.TEBD_EINVAL
+    assert L.rrsvd_plan_create(8, 8, 2, -1, 1, 1, 0, 0, ctypes.byref(h)) == binding.TEBD_EINVAL
+    assert L.rrsvd_plan_create(8, 8, 2, 1, -1, 1, 0, 0, ctypes.byref(h)) == binding.TEBD_EINVAL
+    assert not h.value                                  # *out cleared on every refusal
+    # a sketch wider than 512 columns (l = min(k + p, m, n) = 620)
+    assert L.rrsvd_plan_create(2000, 2000, 600, 20, 2, 1, 0, 0, ctypes.byref(h)) == binding.TEBD_ENOTIMPL
+    # Alg. 2's accuracy check: FP64 only, and a positive threshold
+    assert L.rrsvd_plan_create_ex(64, 64, 8, 4, 1, 1, binding.TEBD_PREC_TF32, 0, 4, 1e-3, 32,
+                                  ctypes.byref(h)) == binding.TEBD_ENOTIMPL
+    assert L.rrsvd_plan_create_ex(64, 64, 8, 4, 1, 1, 0, 0, 4, 0.0, 32, ctypes.byref(h)) == binding.TEBD_EINVAL
+    assert L.rrsvd_plan_create_ex(64, 64, 8, 4, 1, 1, 0, 0, -1, 1e-3, 32, ctypes.byref(h)) == binding.TEBD_EINVAL
     info = (ctypes.c_int * 16)()
     assert L.rrsvd_plan_set_tuning(None, info) == binding.TEBD_EINVAL
     assert L.tebd_destroy(None) == binding.TEBD_OK
