@@ -387,8 +387,9 @@ int rrsvd_execute_host(rrsvd_plan_t plan, const double* theta, int64_t chain0, d
  * call's truncation computes; a call blocks only on the host while slots
  * are busy.  theta and the outputs must stay valid, and the outputs unread,
  * until rrsvd_host_wait.  Calls of one plan run their truncations in call
- * order on `stream`; do not mix them with rrsvd_execute on the same plan on
- * another stream before rrsvd_host_wait.  Errors: TEBD_EINVAL (NULL theta or
+ * order on `stream` and share one device workspace: pass the same stream to
+ * every call until rrsvd_host_wait, and do not mix them with rrsvd_execute on
+ * the same plan on another stream before it.  Errors: TEBD_EINVAL (NULL theta or
  * sigma, chain0 < 0), TEBD_ENOMEM (two staging slots and a workspace on the
  * first call), TEBD_ECUDA. */
 int rrsvd_execute_host_async(rrsvd_plan_t plan, const double* theta, int64_t chain0, double* sigma, double* U,
