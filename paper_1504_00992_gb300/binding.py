@@ -450,7 +450,8 @@ def rrsvd_plan_widths(plan, batch):
 
 
 def rrsvd_plan_destroy(plan):
-    load().rrsvd_plan_destroy(plan)
+    load().rrsvd_plan_destroy(plan)           # finishes pending asynchronous calls first
+    _IN_FLIGHT.pop(plan.value, None)
 
 
 def rrsvd_workspace_size(plan):
@@ -473,26 +474,69 @@ def rrsvd_execute(plan, theta_ptr, chain0, sigma_ptr, U_ptr, Vh_ptr, w_ptr, rank
                                        vp(rank_ptr), vp(ws_ptr), ws_bytes, vp(stream_ptr)))
 
 
+def _host_buffers(plan, theta, sigma, U, Vh, w, rank):
+    """Addresses of a host-buffer call's numpy arrays, after checking what the
+    library will read and write through them: theta (batch, m, n) complex128,
+    sigma (batch, k) float64, U (batch, m, k) and Vh (batch, k, n) complex128,
+    w (batch,) float64, rank (batch,) int32 (k from the plan), each C-ordered
+    and the outputs writeable; the optional ones may be None.  The library
+    reads and writes exactly these extents, so a mismatch is refused here
+    (TEBD_EINVAL) instead of touching memory past a buffer."""
+    if theta is None or sigma is None:
+        raise TebdError(TEBD_EINVAL, "theta and sigma are required")
+    if np.ndim(theta) != 3:
+        raise TebdError(TEBD_EINVAL, "theta must be (batch, m, n)")
+    k, _ = rrsvd_plan_dims(plan)
+    batch, m, n = theta.shape
+    want = (("theta", theta, np.complex128, batch * m * n, False), ("sigma", sigma, np.float64, batch * k, True),
+            ("U", U, np.complex128, batch * m * k, True), ("Vh", Vh, np.complex128, batch * k * n, True),
+            ("w", w, np.float64, batch, True), ("rank", rank, np.int32, batch, True))
+    out = []
+    for name, a, dt, size, written in want:
+        if a is None:
+            out.append(None)
+            continue
+        if not isinstance(a, np.ndarray) or a.dtype != dt or not a.flags.c_contiguous or a.size != size:
+            raise TebdError(TEBD_EINVAL, f"{name}: a C-ordered {np.dtype(dt).name} array of {size} elements is "
+                                         f"needed")
+        if written and not a.flags.writeable:
+            raise TebdError(TEBD_EINVAL, f"{name} is read-only")
+        out.append(_vp(a.ctypes.data))
+    return out
+
+
+# arrays of rrsvd_execute_host_async calls still in flight, per plan address:
+# kept alive here until the plan's next wait
+_IN_FLIGHT = {}
+
+
 def rrsvd_execute_host(plan, theta, chain0, sigma, U=None, Vh=None, w=None, rank=None, stream_ptr=0):
     """Host-buffer call: theta (batch, m, n) complex128 in, results written
-    into the given numpy arrays (contiguous; pinned memory recommended)."""
-    def hp(a):
-        return _vp(a.ctypes.data) if a is not None else None
-    _pcheck(plan, load().rrsvd_execute_host(plan, hp(theta), chain0, hp(sigma), hp(U), hp(Vh), hp(w), hp(rank),
-                                            _vp(int(stream_ptr)) if stream_ptr else None))
+    into the given numpy arrays (contiguous; pinned memory recommended).  It
+    waits for the plan's pending asynchronous calls first."""
+    bufs = _host_buffers(plan, theta, sigma, U, Vh, w, rank)
+    try:
+        _pcheck(plan, load().rrsvd_execute_host(plan, bufs[0], chain0, *bufs[1:],
+                                                _vp(int(stream_ptr)) if stream_ptr else None))
+    finally:
+        _IN_FLIGHT.pop(plan.value, None)
 
 
 def rrsvd_execute_host_async(plan, theta, chain0, sigma, U=None, Vh=None, w=None, rank=None, stream_ptr=0):
-    """Enqueued host-buffer call (rrsvd_execute_host_async): the arrays must
-    stay alive and unread until rrsvd_host_wait(plan)."""
-    def hp(a):
-        return _vp(a.ctypes.data) if a is not None else None
-    _pcheck(plan, load().rrsvd_execute_host_async(plan, hp(theta), chain0, hp(sigma), hp(U), hp(Vh), hp(w), hp(rank),
+    """Enqueued host-buffer call (rrsvd_execute_host_async): the outputs are
+    valid after rrsvd_host_wait(plan); theta must not change before then.  The
+    binding holds the arrays until that wait."""
+    bufs = _host_buffers(plan, theta, sigma, U, Vh, w, rank)
+    _IN_FLIGHT.setdefault(plan.value, []).append((theta, sigma, U, Vh, w, rank))
+    _pcheck(plan, load().rrsvd_execute_host_async(plan, bufs[0], chain0, *bufs[1:],
                                                   _vp(int(stream_ptr)) if stream_ptr else None))
 
 
 def rrsvd_host_wait(plan):
-    _pcheck(plan, load().rrsvd_host_wait(plan))
+    try:
+        _pcheck(plan, load().rrsvd_host_wait(plan))
+    finally:
+        _IN_FLIGHT.pop(plan.value, None)
 
 
 def rrsvd_execute_noalloc(m, n, k_max, p, q, batch, seed, chain0, theta_ptr, sigma_ptr, U_ptr=0, Vh_ptr=0,
